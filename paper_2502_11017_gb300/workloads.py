@@ -1,0 +1,118 @@
+"""Seeded synthetic inputs for the CUR cross (inputs only: no step of the method).
+
+Every generator draws from ``numpy.random.default_rng(seed)`` and returns host
+arrays, so the CUDA path and the FP64 oracle read identical bytes. The shapes and
+spectra follow the workloads the method is measured on:
+
+* ``lowrank_haar``: A = U diag(sigma) V^T + noise with Haar-orthonormal U, V
+  (QR of a Gaussian with the sign of R's diagonal fixed), sigma_k = 2^(-k/2),
+  noise variance 1e-8 (standard deviation 1e-4). FP64. 2000 x 1500, r = 16.
+* ``gaussian_kernel``: A_ij = exp(-|x_i - y_j|^2 / h^2), x_i and y_j uniform in
+  the unit cube, h = 0.2, evaluated in FP64 and rounded once to FP32.
+  65536 x 8192, r = 64.
+* ``hilbert`` and ``cauchy_product``: the two test families of Section 3.1 of
+  the paper (Hilbert matrices; H = A B with A(i,j) = B(i,j) = 1/(i+j), indices
+  starting at 1).
+* ``lowrank_plus_noise``: Haar factors with a chosen spectrum and noise level,
+  used for small parity cases with well separated singular values.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 11017
+
+
+def haar(rows: int, cols: int, rng: np.random.Generator) -> np.ndarray:
+    """rows x cols matrix with orthonormal columns, Haar distributed."""
+    g = rng.standard_normal((rows, cols))
+    q, rr = np.linalg.qr(g)
+    d = np.sign(np.diag(rr))
+    d[d == 0] = 1.0
+    return q * d[None, :]
+
+
+def lowrank_haar(m: int = 2000, n: int = 1500, noise_std: float = 1e-4,
+                 seed: int = SEED_BASE + 1) -> np.ndarray:
+    """U diag(2^(-k/2)) V^T + N(0, noise_std^2) noise, FP64, m x n (m >= n)."""
+    rng = np.random.default_rng(seed)
+    k = min(m, n)
+    u = haar(m, k, rng)
+    v = haar(n, k, rng)
+    sigma = 2.0 ** (-np.arange(1, k + 1) / 2.0)
+    a = (u * sigma[None, :]) @ v.T
+    if noise_std > 0:
+        a += noise_std * rng.standard_normal((m, n))
+    return np.ascontiguousarray(a)
+
+
+def lowrank_plus_noise(m: int, n: int, sigma: np.ndarray, noise_std: float,
+                       seed: int, dtype=np.float64) -> np.ndarray:
+    """X diag(sigma) Y^T + noise with Haar X (m x k), Y (n x k)."""
+    rng = np.random.default_rng(seed)
+    k = len(sigma)
+    x = haar(m, k, rng)
+    y = haar(n, k, rng)
+    a = (x * np.asarray(sigma)[None, :]) @ y.T
+    if noise_std > 0:
+        a += noise_std * rng.standard_normal((m, n))
+    return np.ascontiguousarray(a.astype(dtype))
+
+
+def gaussian_kernel(m: int = 65536, n: int = 8192, h: float = 0.2,
+                    seed: int = SEED_BASE + 2, dtype=np.float32,
+                    chunk_rows: int = 4096) -> np.ndarray:
+    """exp(-|x_i - y_j|^2 / h^2) for x (m points) and y (n points) in [0,1]^3."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((m, 3))
+    y = rng.random((n, 3))
+    out = np.empty((m, n), dtype=dtype)
+    inv_h2 = 1.0 / (h * h)
+    for s in range(0, m, chunk_rows):
+        e = min(s + chunk_rows, m)
+        d2 = ((x[s:e, None, :] - y[None, :, :]) ** 2).sum(axis=2)
+        out[s:e] = np.exp(-d2 * inv_h2).astype(dtype)
+    return out
+
+
+def hilbert(n: int) -> np.ndarray:
+    """H_ij = 1/(i+j-1) with 1-based i, j (Section 3.1, Hilbert experiment)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    return 1.0 / (i[:, None] + i[None, :] - 1.0)
+
+
+def cauchy_product(n: int, r: int) -> np.ndarray:
+    """H = A B with A (n x r), B (r x n), A(i,j) = B(i,j) = 1/(i+j), 1-based
+    (Section 3.1, synthetic low-rank experiment)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    k = np.arange(1, r + 1, dtype=np.float64)
+    a = 1.0 / (i[:, None] + k[None, :])
+    b = 1.0 / (k[:, None] + i[None, :])
+    return a @ b
+
+
+def random_gaussian(m: int, n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((m, n)).astype(dtype)
+
+
+# Named workloads: shape, rank and block counts of each measured configuration.
+CONFIGS = {
+    "lowrank_haar_2000x1500_r16": dict(kind="lowrank_haar", m=2000, n=1500, r=16,
+                                       b_r=8, b_c=8, delta=1e-2, dtype="f64"),
+    "gaussian_kernel_65536x8192_r64": dict(kind="gaussian_kernel", m=65536, n=8192,
+                                           r=64, b_r=64, b_c=8, delta=1e-2,
+                                           dtype="f32"),
+}
+
+
+def make(name: str, **over) -> np.ndarray:
+    cfg = dict(CONFIGS[name])
+    cfg.update(over)
+    if cfg["kind"] == "lowrank_haar":
+        return lowrank_haar(cfg["m"], cfg["n"], cfg.get("noise_std", 1e-4),
+                            cfg.get("seed", SEED_BASE + 1))
+    if cfg["kind"] == "gaussian_kernel":
+        return gaussian_kernel(cfg["m"], cfg["n"], cfg.get("h", 0.2),
+                               cfg.get("seed", SEED_BASE + 2))
+    raise KeyError(name)

@@ -1,0 +1,425 @@
+"""Pins of the FP64 oracle against facts fixed outside it (CPU only).
+
+Each test ties one oracle function to something the oracle does not compute
+itself: a LAPACK routine that the method reduces to (QR with column pivoting),
+exact closed forms (Cauchy determinants of Hilbert submatrices), exhaustive
+search on tiny inputs, invariants of the maximal-volume problem, and the error
+bounds of Theorems 1 and 2.
+"""
+from fractions import Fraction
+import itertools
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import cur_oracle as orc
+from paper_2502_11017_gb300 import workloads as wl
+
+
+def separated(m, n, seed):
+    """Gaussian matrix whose columns carry clearly separated scales."""
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal((m, n))
+    return a * (1.5 ** -np.arange(n))[rng.permutation(n)][None, :]
+
+
+def cauchy_logdet_hilbert(I, J):
+    """log|det H(I,J)| for H_ij = 1/(i+j+1) (0-based), by the Cauchy determinant
+    formula with x_i = i + 1, y_j = j, evaluated exactly in rationals."""
+    num, den = Fraction(1), Fraction(1)
+    for a, b in itertools.combinations(range(len(I)), 2):
+        num *= (I[b] - I[a]) * (J[b] - J[a])
+    for a in range(len(I)):
+        for b in range(len(J)):
+            den *= (I[a] + J[b] + 1)
+    v = abs(num / den)
+    return math.log(v.numerator) - math.log(v.denominator)
+
+
+# ---------------------------------------------------------------- Algorithm 3
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_aca_columns_equal_qr_column_pivoting(seed):
+    a = separated(70, 40, seed)
+    r = 12
+    sel, st = orc.aca_select(a, axis=1, r=r, nblocks=1)
+    _q, _r, piv = scipy.linalg.qr(a, pivoting=True, mode="economic")
+    assert st == orc.OK
+    assert sel == list(piv[:r])
+
+
+@pytest.mark.parametrize("seed", [3, 4])
+def test_aca_rows_equal_qr_column_pivoting_of_transpose(seed):
+    a = separated(40, 70, seed).T.copy()          # 70 x 40, separated rows
+    r = 10
+    sel, st = orc.aca_select(a, axis=0, r=r, nblocks=1)
+    _q, _r, piv = scipy.linalg.qr(a.T, pivoting=True, mode="economic")
+    assert st == orc.OK
+    assert sel == list(piv[:r])
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_aca_independent_of_block_count(axis):
+    a = separated(57, 43, 7)
+    if axis == 0:
+        a = a.T.copy()
+    ref, _ = orc.aca_select(a, axis, 9, 1)
+    for b in (2, 3, 8):
+        got, _ = orc.aca_select(a, axis, 9, b)
+        assert got == ref
+
+
+def test_aca_first_pivot_is_max_norm():
+    a = separated(30, 20, 9)
+    sel, _ = orc.aca_select(a, 1, 1, 4)
+    assert sel == [int(np.argmax((a * a).sum(axis=0)))]
+    sel, _ = orc.aca_select(a, 0, 1, 4)
+    assert sel == [int(np.argmax((a * a).sum(axis=1)))]
+
+
+def test_aca_ties_go_to_lowest_index():
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(20)
+    y = 0.5 * rng.standard_normal(20)
+    a = np.stack([y, x, y, x], axis=1)             # columns 1 and 3 tie
+    sel, st = orc.aca_select(a, 1, 2, 2)
+    assert sel[0] == 1
+    assert sel[1] == 0                              # 2 and 3 are dependent
+    assert st == orc.OK
+
+
+def test_aca_rank_deficient_stops_with_warning():
+    rng = np.random.default_rng(6)
+    a = rng.standard_normal((30, 3)) @ rng.standard_normal((3, 25))
+    sel, st = orc.aca_select(a, 1, 5, 3)
+    assert st == orc.WARN_RANK
+    assert len(sel) == 3
+    assert np.linalg.matrix_rank(a[:, sel]) == 3
+
+
+def test_aca_residual_is_projection():
+    """After the r rounds the selected columns span what was removed: the
+    volume of the Gram matrix of the selection equals the product of the pivot
+    norms (Gram-Schmidt)."""
+    a = separated(40, 25, 11)
+    sel, _ = orc.aca_select(a, 1, 6, 2)
+    q, rr = np.linalg.qr(a[:, sel])
+    pivot_norms = []
+    for t, j in enumerate(sel):
+        proj = a[:, j] - q[:, :t] @ (q[:, :t].T @ a[:, j])
+        pivot_norms.append(np.linalg.norm(proj))
+    np.testing.assert_allclose(np.abs(np.diag(rr)), pivot_norms, rtol=1e-12)
+
+
+# ---------------------------------------------------------------- LU, logvol
+
+@pytest.mark.parametrize("r", [1, 3, 8, 17])
+def test_lu_matches_lapack(r):
+    rng = np.random.default_rng(r)
+    m = rng.standard_normal((r, r))
+    lu, perm, sing = orc.lu_factor(m)
+    lu_ref, piv_ref = scipy.linalg.lu_factor(m)
+    assert not sing
+    np.testing.assert_allclose(lu, lu_ref, rtol=1e-12, atol=1e-12)
+    lower = np.tril(lu, -1) + np.eye(r)
+    np.testing.assert_allclose(m[perm], lower @ np.triu(lu), rtol=1e-10, atol=1e-10)
+    inv = orc.lu_inverse(lu, perm)
+    np.testing.assert_allclose(inv, np.linalg.inv(m), rtol=1e-9, atol=1e-9)
+
+
+def test_lu_flags_singular():
+    rng = np.random.default_rng(1)
+    m = rng.standard_normal((6, 6))
+    m[:, 4] = m[:, 1] + m[:, 2]
+    _lu, _perm, sing = orc.lu_factor(m)
+    assert sing
+
+
+@pytest.mark.parametrize("I,J", [([0, 1, 2], [0, 1, 2]), ([3, 7, 11, 20], [0, 5, 9, 30]),
+                                 ([1, 4], [2, 3]), ([0, 10, 20, 30, 40], [1, 2, 3, 4, 5])])
+def test_logvol_equals_cauchy_closed_form(I, J):
+    h = wl.hilbert(48)
+    got = orc.logvol(h[np.ix_(I, J)])
+    assert got == pytest.approx(cauchy_logdet_hilbert(I, J), rel=1e-9, abs=1e-9)
+
+
+# ---------------------------------------------------------------- maxvol
+
+def _swap_gain(cb, S, i, j):
+    m = cb[S, :].copy()
+    m2 = m.copy()
+    m2[j] = cb[i]
+    return abs(np.linalg.det(m2)) / abs(np.linalg.det(m))
+
+
+@pytest.mark.parametrize("seed,p,r", [(0, 10, 2), (1, 12, 3), (2, 9, 3), (3, 11, 1),
+                                      (4, 12, 2), (5, 8, 3)])
+def test_maxvol_against_bruteforce(seed, p, r):
+    rng = np.random.default_rng(seed)
+    cb = rng.standard_normal((p, r))
+    delta = 1e-2
+    start, _ = orc.aca_select(cb, 0, r, 1)
+    S, lv, sw, st = orc.maxvol(cb, start, delta)
+    assert st == orc.OK
+    # (i) no single swap gains more than 1 + delta (determinants, not B)
+    for i in set(range(p)) - set(S):
+        for j in range(r):
+            assert _swap_gain(cb, S, i, j) <= (1 + delta) * (1 + 1e-12)
+    # (ii) Hadamard bound against the exhaustive maximum
+    _best_s, best = orc.bruteforce_rows(cb, r)
+    vol = abs(np.linalg.det(cb[S, :]))
+    assert vol >= best / ((1 + delta) * math.sqrt(r)) ** r * (1 - 1e-12)
+    # (v) logvol is log|det| of the selected rows
+    assert lv == pytest.approx(np.linalg.slogdet(cb[S, :])[1], abs=1e-10)
+
+
+def test_maxvol_coefficients_identity_on_selected_rows():
+    rng = np.random.default_rng(8)
+    cb = rng.standard_normal((40, 6))
+    S = [3, 9, 17, 22, 30, 38]
+    B, Minv, lv, sing = orc.coefficients(cb, S)
+    assert not sing
+    np.testing.assert_allclose(B[S, :], np.eye(6), atol=1e-12)
+    np.testing.assert_allclose(B, np.linalg.solve(cb[S, :].T, cb.T).T, rtol=1e-10, atol=1e-10)
+
+
+def test_sherman_morrison_equals_recompute():
+    rng = np.random.default_rng(9)
+    cb = rng.standard_normal((50, 7))
+    S = list(range(7))
+    B, Minv, lv, _ = orc.coefficients(cb, S)
+    i, j = orc.argmax_abs(B)
+    assert abs(B[i, j]) > 1.5
+    b = orc.sm_swap(B, Minv, i, j)
+    S2 = list(S)
+    S2[j] = i
+    B2, Minv2, lv2, _ = orc.coefficients(cb, S2)
+    np.testing.assert_allclose(B, B2, rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(Minv, Minv2, rtol=1e-10, atol=1e-10)
+    assert lv + math.log(abs(b)) == pytest.approx(lv2, abs=1e-10)
+
+
+def test_maxvol_finds_planted_rows_from_any_start():
+    rng = np.random.default_rng(10)
+    cb = rng.standard_normal((30, 3))
+    planted = [4, 17, 25]
+    cb[planted] *= 1e3
+    for start in ([0, 1, 2], [5, 6, 7], [29, 28, 4], [17, 0, 9]):
+        S, _lv, _sw, st = orc.maxvol(cb, start)
+        assert st == orc.OK
+        assert sorted(S) == planted
+
+
+def test_maxvol_square_and_errors():
+    rng = np.random.default_rng(11)
+    cb = rng.standard_normal((5, 5))
+    S, _lv, sw, st = orc.maxvol(cb, [4, 2, 0, 1, 3])
+    assert (sw, st) == (0, orc.OK)
+    tall = rng.standard_normal((20, 4))
+    tall[7] = tall[3]
+    assert orc.maxvol(tall, [3, 7, 1, 2])[3] == orc.ERR_SINGULAR
+    assert orc.maxvol(tall, [3, 3, 1, 2])[3] == orc.ERR_ARG
+    tall[12] *= 1e3
+    assert orc.maxvol(tall, [0, 1, 2, 4], max_swaps=0)[3] == orc.ERR_NOCONV
+
+
+def test_maxvol_on_hilbert_matches_exhaustive_search():
+    h = wl.hilbert(12)[:, :3]
+    start, _ = orc.aca_select(h, 0, 3, 1)
+    S, lv, _sw, _st = orc.maxvol(h, start, delta=0.0)
+    best_s, _best = orc.bruteforce_rows(h, 3)
+    assert sorted(S) == best_s
+    assert lv == pytest.approx(cauchy_logdet_hilbert(sorted(S), [0, 1, 2]), abs=1e-9)
+
+
+# ---------------------------------------------------------------- merge
+
+def test_merge_single_set_and_self_merge_are_identity():
+    rng = np.random.default_rng(12)
+    c = rng.standard_normal((40, 4))
+    s = [5, 9, 20, 33]
+    assert orc.merge(c, [s])[0] == s
+    out, sw = orc.merge(c, [s, s])
+    assert out == s and sw == 0
+
+
+@pytest.mark.parametrize("nsets", [2, 3, 5, 8])
+def test_merge_finds_planted_set(nsets):
+    rng = np.random.default_rng(13 + nsets)
+    p, r = 16 * nsets, 3
+    c = rng.standard_normal((p, r))
+    planted = [2, p // 2 + 1, p - 3]
+    c[planted] *= 1e3
+    blocks = orc.balanced_blocks(p, nsets)
+    sets = [list(range(s, s + r)) for (s, e) in blocks]
+    out, _sw = orc.merge(c, sets)
+    # every planted row lives in some set only if it was started there; merge then
+    # polish (maxvol on all rows) must recover the planted set
+    S, _lv, _sw2, st = orc.maxvol(c, out)
+    assert sorted(S) == planted
+
+
+def test_merge_node_is_dominant_on_union():
+    rng = np.random.default_rng(14)
+    c = rng.standard_normal((24, 3))
+    left, right = [0, 1, 2], [12, 13, 14]
+    out, _ = orc.merge(c, [left, right])
+    union = left + right
+    m = c[out]
+    for i in union:
+        for j in range(3):
+            m2 = m.copy()
+            m2[j] = c[i]
+            assert abs(np.linalg.det(m2)) <= 1.01 * abs(np.linalg.det(m)) * (1 + 1e-12)
+
+
+# ---------------------------------------------------------------- rows / cols
+
+def test_block_rows_polish_is_globally_dominant():
+    a = wl.lowrank_plus_noise(300, 80, 0.7 ** np.arange(30), 1e-6, seed=15)
+    J, _ = orc.aca_select(a, 1, 8, 2)
+    I, lv, _sw, st, info = orc.maxvol_rows(a, J, 5)
+    assert st == orc.OK
+    c = a[:, J]
+    coef = np.linalg.solve(c[I].T, c.T).T
+    assert np.abs(coef).max() <= 1.01 + 1e-9
+    assert lv == pytest.approx(np.linalg.slogdet(c[I])[1], abs=1e-9)
+    assert len(info["block_sets"]) == 5
+
+
+def test_block_rows_rejects_small_blocks():
+    a = np.random.default_rng(16).standard_normal((40, 30))
+    assert orc.maxvol_rows(a, list(range(8)), 6)[3] == orc.ERR_ARG
+
+
+def test_cols_are_rows_of_transpose():
+    a = wl.lowrank_plus_noise(120, 90, 0.6 ** np.arange(20), 1e-7, seed=17)
+    I = [3, 50, 77, 101, 9]
+    J1 = orc.maxvol_cols(a, I, 3)[0]
+    J2 = orc.maxvol_rows(a.T.copy(), I, 3)[0]
+    assert J1 == J2
+
+
+# ---------------------------------------------------------------- cross
+
+@pytest.mark.parametrize("seed,m,n,r", [(20, 7, 6, 2), (21, 6, 7, 2), (22, 6, 6, 3),
+                                        (23, 8, 5, 1)])
+def test_theorems_hold_for_bruteforce_maximiser(seed, m, n, r):
+    a = np.random.default_rng(seed).standard_normal((m, n))
+    I, J, _best = orc.bruteforce_cross(a, r)
+    C, U, R, _rc, _p = orc.assemble(a, I, J)
+    cheb, _ = orc.residual(a, C, U, R)
+    s = np.linalg.svd(a, compute_uv=False)
+    assert cheb <= orc.theorem2_bound(s, r) * (1 + 1e-10)
+    assert orc.theorem2_bound(s, r) <= orc.theorem1_bound(s, r)
+
+
+def test_cross_finds_planted_submatrix():
+    rng = np.random.default_rng(24)
+    a = rng.standard_normal((9, 8)) * 0.1
+    a[np.ix_([1, 6], [2, 5])] = np.array([[9.0, 1.0], [-2.0, 8.0]])
+    I, J, info = orc.cross(a, 2, 2, 2)
+    Ib, Jb, _ = orc.bruteforce_cross(a, 2)
+    assert (sorted(I), sorted(J)) == (Ib, Jb)
+    assert info["status"] == orc.OK
+
+
+@pytest.mark.parametrize("seed", [25, 26, 27])
+def test_cross_two_sided_dominance_and_sweeps(seed):
+    a = wl.lowrank_plus_noise(200, 150, 0.8 ** np.arange(40), 1e-8, seed=seed)
+    I, J, info = orc.cross(a, 10, 4, 3)
+    assert info["status"] == orc.OK
+    M = a[np.ix_(I, J)]
+    rows = np.abs(np.linalg.solve(M.T, a[:, J].T)).max()
+    cols = np.abs(np.linalg.solve(M, a[I, :])).max()
+    assert rows <= 1.01 + 1e-9 and cols <= 1.01 + 1e-9
+    assert info["sweep_swaps"][-1] == 0
+    assert orc.dominance(a, I, J) == pytest.approx((rows, cols), rel=1e-9)
+
+
+def test_cross_rank_one_is_rook_pivot():
+    a = np.random.default_rng(28).standard_normal((30, 20))
+    I, J, _ = orc.cross(a, 1, 3, 2)
+    v = abs(a[I[0], J[0]])
+    assert v * 1.01 >= np.abs(a[:, J[0]]).max()
+    assert v * 1.01 >= np.abs(a[I[0], :]).max()
+
+
+def test_cross_rejects_bad_input():
+    a = np.ones((10, 8))
+    assert orc.cross(a, 8, 1, 1)[2]["status"] == orc.ERR_ARG
+    a[3, 3] = np.nan
+    assert orc.cross(a, 2, 1, 1)[2]["status"] == orc.ERR_NONFINITE
+
+
+# ---------------------------------------------------------------- assemble / residual
+
+def test_exact_rank_r_reconstruction():
+    rng = np.random.default_rng(29)
+    a = rng.standard_normal((60, 6)) @ rng.standard_normal((6, 45))
+    I, J, _ = orc.cross(a, 6, 2, 2)
+    C, U, R, rc, used_pinv = orc.assemble(a, I, J)
+    cheb, fro = orc.residual(a, C, U, R)
+    assert not used_pinv
+    assert cheb <= 1e3 * orc.EPS * np.abs(a).max()
+    assert fro <= 1e3 * orc.EPS
+
+
+def test_residual_vanishes_on_the_cross():
+    a = wl.lowrank_plus_noise(70, 50, 0.5 ** np.arange(20), 1e-3, seed=30)
+    I, J = [1, 20, 33, 60], [0, 7, 19, 44]
+    C, U, R, _rc, _p = orc.assemble(a, I, J)
+    e = a - C @ U @ R
+    assert np.abs(e[I, :]).max() < 1e-10 and np.abs(e[:, J]).max() < 1e-10
+    cheb, fro = orc.residual(a, C, U, R)
+    assert cheb == pytest.approx(np.abs(e).max(), rel=1e-12)
+    assert fro == pytest.approx(np.linalg.norm(e) / np.linalg.norm(a), rel=1e-10)
+
+
+def test_jacobi_svd_and_pinv_match_lapack():
+    rng = np.random.default_rng(31)
+    m = rng.standard_normal((9, 9))
+    m[:, 8] = m[:, 0] - 2 * m[:, 3]          # rank 8
+    u, s, v = orc.jacobi_svd(m)
+    np.testing.assert_allclose(s, np.linalg.svd(m, compute_uv=False), atol=1e-12)
+    np.testing.assert_allclose((u * s) @ v.T, m, atol=1e-12)
+    np.testing.assert_allclose(orc.pinv(m), np.linalg.pinv(m, rcond=9 * orc.EPS), atol=1e-9)
+
+
+def test_assemble_falls_back_to_pinv_when_singular():
+    rng = np.random.default_rng(32)
+    a = rng.standard_normal((12, 10))
+    a[:, 4] = a[:, 2]
+    C, U, R, rc, used = orc.assemble(a, [0, 1, 5], [2, 4, 7])
+    assert used
+    np.testing.assert_allclose(U, np.linalg.pinv(a[np.ix_([0, 1, 5], [2, 4, 7])], rcond=3 * orc.EPS),
+                               atol=1e-9)
+
+
+def test_balanced_blocks():
+    assert orc.balanced_blocks(10, 3) == [(0, 4), (4, 7), (7, 10)]
+    assert orc.balanced_blocks(8, 8) == [(k, k + 1) for k in range(8)]
+
+
+# ---------------------------------------------------------------- Section 3.1 behaviour
+
+def test_hilbert_error_decreases_with_rank():
+    """Qualitative only: the paper's Hilbert figure prints no values."""
+    h = wl.hilbert(128)
+    errs = []
+    for r in (2, 4, 6, 8, 10):
+        I, J, _ = orc.cross(h, r, 2, 2)
+        C, U, R, _rc, _p = orc.assemble(h, I, J)
+        errs.append(orc.residual(h, C, U, R)[1])
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-5
+
+
+def test_cauchy_product_is_recovered_at_its_rank():
+    """Qualitative only: near-zero error once r reaches the rank (Section 3.1)."""
+    hm = wl.cauchy_product(128, 5)
+    I, J, _ = orc.cross(hm, 5, 2, 2)
+    C, U, R, _rc, _p = orc.assemble(hm, I, J)
+    assert orc.residual(hm, C, U, R)[1] < 1e-6     # cond(A(I,J)) ~ 1e10
