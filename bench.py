@@ -1,0 +1,368 @@
+"""Throughput of the scalable binary CUR cross on one GB300 (or N, as replicas).
+
+A step is one pass of the whole hot path on the Gaussian-kernel workload
+(65536 x 8192 FP32, r = 64, 64 row blocks, 8 column blocks, delta = 1e-2):
+Algorithm 3 on the columns, block maxvol + binary merge + polish for the rows and
+then the columns, global sweeps, assembly of C, U, R and the Chebyshev /
+Frobenius residual on the full matrix. The metric is complete crosses per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) each rank computes its own crosses on
+its own copy of the matrix: the crosses are independent units, no data crosses
+ranks, and the value is the units of all ranks over the slowest rank's time.
+The reference arm times the FP64 oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CUR selections/s and HBM roofline % vs plain FP32 maxvol at equal volume"
+UNIT = "selections/s"
+WORKLOAD = dict(name="gaussian_kernel_65536x8192_r64", m=65536, n=8192, r=64, b_r=64, b_c=8,
+                delta=1e-2, h=0.2, seed=11019)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def traffic_record():
+    """ncu DRAM bytes per launch of the pass kernel, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "aca_cols_pass_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_2502_11017_gb300", "csrc", "aca.cu"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("traffic_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_input():
+    from paper_2502_11017_gb300 import workloads as wl
+    w = WORKLOAD
+    return wl.gaussian_kernel(w["m"], w["n"], w["h"], seed=w["seed"], chunk_rows=1024)
+
+
+# ---------------------------------------------------------------- oracle timing (CPU)
+
+def oracle_sample(rounds: int, stage: bool) -> dict:
+    """Runs in a child process: times Algorithm 3 rounds of the oracle on the full
+    matrix and (optionally) the oracle's row and column maxvol stages once."""
+    import numpy as np
+    from oracle import cur_oracle as orc
+    w = WORKLOAD
+    a = make_input()
+    out = {}
+    t_rounds = []
+    for _ in range(rounds):
+        t0 = time.perf_counter()
+        orc.aca_select(a, 1, 1, w["b_c"])
+        t_rounds.append(time.perf_counter() - t0)
+    out["round_s"] = t_rounds
+    if stage:
+        J0 = list(range(0, w["n"], w["n"] // w["r"]))[: w["r"]]
+        t0 = time.perf_counter()
+        I, _lv, _sw, _st, _ = orc.maxvol_rows(a, J0, w["b_r"])
+        t1 = time.perf_counter()
+        orc.maxvol_cols(a, I, w["b_c"])
+        t2 = time.perf_counter()
+        out["rows_s"] = t1 - t0
+        out["cols_s"] = t2 - t1
+    return out
+
+
+def run_oracle_child(rounds: int, stage: bool, threads: int) -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = (f"import sys, json; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"print(json.dumps(bench.oracle_sample({rounds}, {stage})))")
+    res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_estimate(rounds: int = 2) -> dict:
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    s = run_oracle_child(rounds, True, threads)
+    wall = time.perf_counter() - t0
+    r = WORKLOAD["r"]
+    per_round = statistics.median(s["round_s"])
+    est = r * per_round + s["rows_s"] + s["cols_s"]
+    return {"value": 1.0 / est, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"{rounds} of the {r} Algorithm 3 rounds on the full 65536x8192 matrix "
+                       f"({per_round:.2f} s/round) plus one oracle row stage (64 blocks, merge, "
+                       f"polish) and one column stage (8 blocks) from evenly spaced columns "
+                       f"({s['rows_s'] + s['cols_s']:.2f} s); seconds per cross estimated as "
+                       f"r x round + stages = {est:.1f} s (later sweeps not counted); "
+                       f"{wall:.0f} s of CPU wall time"),
+            "seconds_per_selection": est}
+
+
+# ---------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    # untimed: the row / column stages once; then W + K Algorithm 3 rounds, one per step
+    s = run_oracle_child(args.warmup + args.steps, True, threads)
+    rounds = s["round_s"][args.warmup:]
+    per_round = statistics.median(rounds)
+    r = WORKLOAD["r"]
+    est = r * per_round + s["rows_s"] + s["cols_s"]
+    value = 1.0 / est
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * statistics.mean(rounds), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], **{k: WORKLOAD[k] for k in ("m", "n", "r", "b_r", "b_c", "delta")},
+                   "step": "one Algorithm 3 round of the FP64 oracle on the full matrix"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": (f"each step is one of the {r} Algorithm 3 rounds on the full "
+                                    f"matrix ({per_round:.2f} s); row and column maxvol stages "
+                                    f"timed once ({s['rows_s'] + s['cols_s']:.2f} s); value = "
+                                    f"1 / (r x round + stages)")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2502_11017_gb300 as cur
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not os.path.exists(cur.LIB_PATH):
+        cur.build()
+    w = WORKLOAD
+    m, n, r, b_r, b_c = w["m"], w["n"], w["r"], w["b_r"], w["b_c"]
+
+    a_host = make_input()
+    A = torch.from_numpy(a_host).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    hd = cur.Handle(m, n, r, cur.CUR_F32)
+    h = hd.h
+    o = cur.opts(delta=w["delta"])
+    I = torch.empty(r, dtype=torch.int32, device=dev)
+    J = torch.empty(r, dtype=torch.int32, device=dev)
+    info = torch.zeros(64, dtype=torch.uint8, device=dev)
+    C = torch.empty((m, r), dtype=torch.float32, device=dev)
+    R = torch.empty((r, n), dtype=torch.float32, device=dev)
+    U = torch.empty((r, r), dtype=torch.float64, device=dev)
+    rc = torch.empty(1, dtype=torch.float64, device=dev)
+    cheb = torch.empty(1, dtype=torch.float64, device=dev)
+    fro = torch.empty(1, dtype=torch.float64, device=dev)
+
+    def step(Ain):
+        cur.cur_cross(h, Ain, r, b_r, b_c, o, I, J, info)
+        cur.cur_assemble(h, Ain, I, J, r, C, U, R, rc)
+        cur.cur_residual_cheb(h, Ain, C, U, R, r, cheb, fro)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step(A)
+    st = cur.cur_sync_status(h)
+    if st != cur.CUR_OK:
+        raise RuntimeError(f"device status {st} during warm-up")
+    cur.cur_prof_enable(h, True)
+    cur.cur_prof_read(h)
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(gpu_index) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(A)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    pass_ms, pass_n, launches = cur.cur_prof_read(h)
+    cur.cur_prof_enable(h, False)
+    st = cur.cur_sync_status(h)
+    if st != cur.CUR_OK:
+        raise RuntimeError(f"device status {st} in the timed region")
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = t.item()
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # end to end: A from pinned host memory each step, I, J and the residual back
+    a_pin = torch.from_numpy(a_host).pin_memory()
+    A2 = torch.empty_like(A)
+    I_h = torch.empty(r, dtype=torch.int32).pin_memory()
+    J_h = torch.empty(r, dtype=torch.int32).pin_memory()
+    c_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        A2.copy_(a_pin, non_blocking=True)
+        step(A2)
+        I_h.copy_(I, non_blocking=True)
+        J_h.copy_(J, non_blocking=True)
+        c_h.copy_(cheb, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_value = world * e2e_steps / (t2.item() / 1000.0)
+
+    inf = cur.info_from_tensor(info)
+    peaks, kind = measured_peaks()
+    bytes_per_pass = m * n * 4
+    avg_pass_ms = pass_ms / max(1, pass_n)
+    achieved = bytes_per_pass / (avg_pass_ms / 1000.0) / 1e9 if pass_n else None
+    roof = {"bound": "hbm", "kernel": "aca_cols_pass (Algorithm 3 pass, A^T q)",
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"] if achieved else None,
+            "peak_kind": kind, "traffic": traffic_record(),
+            "algorithmic_bytes_per_launch": bytes_per_pass, "launches": pass_n,
+            "avg_launch_ms": avg_pass_ms,
+            "share_of_step": pass_ms / ms if ms > 0 else None}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w["name"], "m": m, "n": n, "r": r, "b_r": b_r, "b_c": b_c,
+                       "delta": w["delta"], "h": w["h"], "seed": w["seed"],
+                       "parallelism": f"replicas x{world} (independent crosses per GPU)",
+                       "l2": "A is 2.15 GB (> 129 MB L2) and is streamed each step; no flush",
+                       "step": "cur_cross + cur_assemble + cur_residual_cheb"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
+                    "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": 2 * r * 4 + 8},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "quality": {"logvol": inf.logvol, "sweeps": inf.sweeps, "swaps": inf.swaps_total,
+                        "cheb": cheb.item(), "fro_rel": fro.item()},
+        }
+        if world == 1 and not args.no_cpu:
+            try:
+                line["cpu_baseline"] = cpu_baseline_estimate()
+            except Exception as e:  # the GPU line still stands
+                line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+        print(json.dumps(line), flush=True)
+    hd.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * cur.h - C ABI of libcur, a GB300 (sm_103a) implementation of the scalable
+ * binary CUR cross: A ~ C U R with C = A(:,J), U = A(I,J)^dagger, R = A(I,:)
+ * (arXiv 2502.11017, Section 1.1), where I and J are chosen by the blockwise
+ * adaptive cross approximation (Algorithm 3), refined by block-wise maximal-volume
+ * swaps (Section 1.2, Definition 1) and combined by a binary pairwise merge.
+ *
+ * Conventions shared by every call
+ *  - Matrices are dense, row-major, in device memory of the handle's device:
+ *    element (i, j) of a cur_mat lives at data + i*ld + j (elements, ld >= cols).
+ *    Element offsets are 64-bit. Supported element types: CUR_F64, CUR_F32,
+ *    CUR_BF16 (BF16 is read and widened to FP32).
+ *  - Index vectors are int32, 0-based, device memory. Index sets are returned in
+ *    submatrix-position order (position k of I is row k of A(I,J)).
+ *  - Ownership: the caller allocates every input and output buffer. The library
+ *    owns only the handle and the workspace allocated once by cur_create; no call
+ *    allocates device memory.
+ *  - Streams: work is enqueued on `stream`. cur_aca_select, cur_assemble and
+ *    cur_residual_cheb are asynchronous. cur_maxvol_rows, cur_maxvol_cols,
+ *    cur_merge and cur_cross read small per-cycle counters back to the host and
+ *    therefore synchronise `stream` between refresh cycles; their outputs are
+ *    complete when they return.
+ *  - Errors: argument errors (CUR_ERR_ARG), workspace exhaustion (CUR_ERR_NOMEM)
+ *    and CUDA launch errors (CUR_ERR_CUDA) are returned at once. Errors found on
+ *    the device (CUR_ERR_SINGULAR, CUR_ERR_NONFINITE, CUR_ERR_NOCONV,
+ *    CUR_ERR_TIMEOUT) and the early stop of the selection (CUR_WARN_RANK) are
+ *    recorded in the handle's device status word; cur_sync_status returns the
+ *    first one recorded since the previous cur_sync_status.
+ *  - A handle serves one stream at a time; calls on one handle do not overlap.
+ */
+#ifndef CUR_H
+#define CUR_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CUR_OK = 0,
+    CUR_ERR_ARG = 1,        /* invalid argument: shape, rank, block size, pointer */
+    CUR_ERR_SINGULAR = 2,   /* numerically singular A(I,J) where an inverse is needed */
+    CUR_ERR_NONFINITE = 3,  /* NaN or Inf met in the data */
+    CUR_ERR_NOCONV = 4,     /* maxvol did not converge within opts.max_swaps */
+    CUR_ERR_TIMEOUT = 5,    /* a device-side wait ran out of time (no hang) */
+    CUR_ERR_NOMEM = 6,      /* the handle's workspace is too small for this call */
+    CUR_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+    CUR_WARN_RANK = 8       /* the residual reached rounding level before r picks */
+} cur_status;
+
+typedef enum { CUR_F64 = 0, CUR_F32 = 1, CUR_BF16 = 2 } cur_dtype;
+
+/* A dense row-major matrix view (device memory). */
+typedef struct {
+    const void* data;
+    int64_t rows, cols, ld;
+    cur_dtype dtype;
+} cur_mat;
+
+/* Maxvol options. delta: swap while max|B_ij| > 1 + delta (default 1e-2).
+ * max_swaps: cap on swaps per maxvol problem (<= 0 means 100 r).
+ * nblocks: number of contiguous balanced row blocks of the tall basis.
+ * flags: CUR_FLAG_POLISH runs maxvol over all rows after the merge (default on). */
+typedef struct {
+    double delta;
+    int32_t max_swaps, nblocks;
+    uint32_t flags;
+} cur_opts;
+
+#define CUR_FLAG_POLISH 1u
+
+/* Summary of one cur_cross call, written to DEVICE memory by cur_cross. */
+typedef struct {
+    double logvol;            /* log|det A(I,J)| of the returned cross */
+    int32_t sweeps;           /* sweeps made (1..max) */
+    int32_t swaps_total;      /* maxvol swaps over all stages */
+    int32_t sweep_swaps[8];   /* swaps per sweep */
+    int32_t aca_selected;     /* indices Algorithm 3 returned before padding */
+    int32_t status;           /* cur_status of the whole call */
+} cur_cross_info;
+
+typedef struct cur_handle cur_handle;
+
+/* Handle with `workspace_bytes` of device workspace on the current device.
+ * cur_workspace_size gives the amount a problem of the given size needs. */
+cur_status cur_create(cur_handle** h, size_t workspace_bytes);
+cur_status cur_destroy(cur_handle* h);
+size_t cur_workspace_size(int64_t m, int64_t n, int32_t r, cur_dtype dtype);
+
+/* Algorithm 3 (Blockwise Adaptive Cross Approximation, Section 2.2).
+ * axis = 1 selects r columns of A, axis = 0 selects r rows. Each round takes the
+ * unselected row/column with the largest squared residual norm (lowest index on
+ * ties) and projects it out of the residual. The residual is kept implicitly
+ * (squared norms downdated by the projections onto an orthonormal basis of the
+ * picks), which equals the paper's explicit blockwise projection up to rounding.
+ * nblocks (>= 1) is Algorithm 3's block count; the result does not depend on it.
+ * idx_out: r int32 (device); entries after an early stop are -1 and the status
+ * word records CUR_WARN_RANK. */
+cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r,
+                          int32_t nblocks, int32_t* idx_out, cudaStream_t stream);
+
+/* Row selection for given columns J (r int32, device): maxvol on C = A(:,J).
+ * C is split into opts->nblocks contiguous balanced row blocks (each >= r rows,
+ * else CUR_ERR_ARG); each block starts from Algorithm 3 on its rows and runs
+ * maxvol (B = C_k M^-1, swap while max|B_ij| > 1 + delta, Sherman-Morrison
+ * updates, refresh every r swaps); the block sets are merged pairwise (binary
+ * tournament, cur_merge) and, with CUR_FLAG_POLISH, refined by maxvol over all
+ * rows. Outputs (device): I_out r int32, logvol_out 1 double (log|det C(I,:)|),
+ * swaps_out 1 int32. */
+cur_status cur_maxvol_rows(cur_handle* h, const cur_mat* A, const int32_t* J, int32_t r,
+                           const cur_opts* opts, int32_t* I_out, double* logvol_out,
+                           int32_t* swaps_out, cudaStream_t stream);
+
+/* Column selection for given rows I: the same as cur_maxvol_rows on A(I,:)^T. */
+cur_status cur_maxvol_cols(cur_handle* h, const cur_mat* A, const int32_t* I, int32_t r,
+                           const cur_opts* opts, int32_t* J_out, double* logvol_out,
+                           int32_t* swaps_out, cudaStream_t stream);
+
+/* One level of the binary merge. basis: p x r tall basis (device); cand: nsets x r
+ * row indices of the basis (device, set t in row t). Node t merges sets 2t and
+ * 2t+1 by maxvol on their 2r rows (left set first) started at the left set (the
+ * right set if the left one is singular, Algorithm 3 on the union if both are);
+ * an odd last set passes through. out: ceil(nsets/2) x r int32 (device). */
+cur_status cur_merge(cur_handle* h, const cur_mat* basis, const int32_t* cand, int32_t nsets,
+                     int32_t r, const cur_opts* opts, int32_t* out, cudaStream_t stream);
+
+/* CUR assembly (Section 1.1): C = A(:,J) (m x r, A's dtype), R = A(I,:) (r x n, A's
+ * dtype), U = A(I,J)^dagger (r x r double, row-major): the LU inverse (FP64,
+ * partial pivoting) when rcond = 1/(|M|_1 |M^-1|_1) >= 1e-13, else the
+ * pseudo-inverse by a one-sided Jacobi SVD with cutoff r eps s_max.
+ * rcond_out: 1 double (device; 0 when M is singular). */
+cur_status cur_assemble(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
+                        int32_t r, void* C_out, double* U_out, void* R_out,
+                        double* rcond_out, cudaStream_t stream);
+
+/* Residual of the cross (Theorem 1; Section 3.1 error measure):
+ * cheb_out = max_ij |A - C (U R)|, fro_rel_out = ||A - CUR||_F / ||A||_F (may be
+ * NULL). C: m x r and R: r x n in A's dtype (as cur_assemble writes them), U: r x r
+ * double. Arithmetic in FP32 for FP32/BF16 data, FP64 for FP64 data; sums are
+ * carried in FP64. Outputs are device doubles. */
+cur_status cur_residual_cheb(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                             const void* R, int32_t r, double* cheb_out, double* fro_rel_out,
+                             cudaStream_t stream);
+
+/* The whole cross (Algorithm 2 with blockwise maxvol refinement): J0 = Algorithm 3
+ * on the columns (b_c blocks; padded with the lowest unused columns after an early
+ * stop), sweep 1 = {I = cur_maxvol_rows(J0, b_r), J = cur_maxvol_cols(I, b_c)},
+ * sweeps 2..8 = {maxvol on all rows of A(:,J) from I, maxvol on all columns of
+ * A(I,:) from J} until a sweep makes no swap. I_out, J_out: r int32 (device);
+ * info_out: one cur_cross_info (device, may be NULL). */
+cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, int32_t b_c,
+                     const cur_opts* opts, int32_t* I_out, int32_t* J_out,
+                     cur_cross_info* info_out, cudaStream_t stream);
+
+/* Synchronise `stream` and return (and clear) the first device-side status. */
+cur_status cur_sync_status(cur_handle* h, cudaStream_t stream);
+
+/* Instrumentation (no counterpart in the paper). With cur_prof_enable(h, 1) the
+ * library brackets every launch of the Algorithm 3 streaming pass with CUDA events
+ * on the caller's stream. cur_prof_read synchronises `stream`, returns the summed
+ * duration of those launches (pass_ms) and their number (pass_launches), the number
+ * of kernels this library launched since the last read (kernel_launches, all
+ * handles), and resets the three. Any output pointer may be NULL (host memory). */
+cur_status cur_prof_enable(cur_handle* h, int on);
+cur_status cur_prof_read(cur_handle* h, cudaStream_t stream, double* pass_ms,
+                         int32_t* pass_launches, int64_t* kernel_launches);
+
+/* Default options: delta 1e-2, max_swaps 100 r, nblocks 1, CUR_FLAG_POLISH. */
+cur_opts cur_default_opts(void);
+
+const char* cur_status_string(cur_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUR_H */

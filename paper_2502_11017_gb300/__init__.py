@@ -1,0 +1,258 @@
+"""GB300 (sm_103a) scalable binary CUR cross: Python binding of libcur.
+
+The functions below carry the names of the C ABI in include/cur.h and only
+marshal arguments: PyTorch tensors supply device memory and the stream, every
+step runs in libcur's CUDA kernels. If the library is missing the calls raise
+instead of falling back to anything else; build it with ``build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libcur.so")
+
+CUR_OK, CUR_ERR_ARG, CUR_ERR_SINGULAR, CUR_ERR_NONFINITE, CUR_ERR_NOCONV = 0, 1, 2, 3, 4
+CUR_ERR_TIMEOUT, CUR_ERR_NOMEM, CUR_ERR_CUDA, CUR_WARN_RANK = 5, 6, 7, 8
+CUR_F64, CUR_F32, CUR_BF16 = 0, 1, 2
+CUR_FLAG_POLISH = 1
+
+# Every symbol include/cur.h declares.
+EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select",
+           "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
+           "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
+           "cur_status_string", "cur_prof_enable", "cur_prof_read"]
+
+
+class CurMat(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("dtype", ctypes.c_int)]
+
+
+class CurOpts(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("max_swaps", ctypes.c_int32),
+                ("nblocks", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class CurCrossInfo(ctypes.Structure):
+    _fields_ = [("logvol", ctypes.c_double), ("sweeps", ctypes.c_int32),
+                ("swaps_total", ctypes.c_int32), ("sweep_swaps", ctypes.c_int32 * 8),
+                ("aca_selected", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def build(verbose: bool = False) -> str:
+    from . import build as _b
+    return _b.build(verbose=verbose)
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libcur.so and declare its signatures. Raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libcur.so not found at {path}: run "
+                           "paper_2502_11017_gb300.build() first (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    pmat, popts = ctypes.POINTER(CurMat), ctypes.POINTER(CurOpts)
+    sig = {
+        "cur_create": ([ctypes.POINTER(P), ctypes.c_size_t], ctypes.c_int),
+        "cur_destroy": ([P], ctypes.c_int),
+        "cur_workspace_size": ([I64, I64, I32, ctypes.c_int], ctypes.c_size_t),
+        "cur_aca_select": ([P, pmat, ctypes.c_int, I32, I32, P, P], ctypes.c_int),
+        "cur_maxvol_rows": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
+        "cur_maxvol_cols": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
+        "cur_merge": ([P, pmat, P, I32, I32, popts, P, P], ctypes.c_int),
+        "cur_assemble": ([P, pmat, P, P, I32, P, P, P, P, P], ctypes.c_int),
+        "cur_residual_cheb": ([P, pmat, P, P, P, I32, P, P, P], ctypes.c_int),
+        "cur_cross": ([P, pmat, I32, I32, I32, popts, P, P, P, P], ctypes.c_int),
+        "cur_sync_status": ([P, P], ctypes.c_int),
+        "cur_default_opts": ([], CurOpts),
+        "cur_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "cur_prof_enable": ([P, ctypes.c_int], ctypes.c_int),
+        "cur_prof_read": ([P, P, ctypes.POINTER(D), ctypes.POINTER(I32),
+                           ctypes.POINTER(I64)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+class CurError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = load().cur_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})")
+
+
+def _check(st: int, what: str) -> int:
+    if st not in (CUR_OK, CUR_WARN_RANK):
+        raise CurError(st, what)
+    return st
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return CUR_F64
+    if t.dtype == torch.float32:
+        return CUR_F32
+    if t.dtype == torch.bfloat16:
+        return CUR_BF16
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def mat(t) -> CurMat:
+    """cur_mat view of a 2-D row-major CUDA tensor (unit stride in columns)."""
+    if t.dim() != 2 or t.stride(1) != 1 or not t.is_cuda:
+        raise ValueError("expected a 2-D CUDA tensor with unit column stride")
+    return CurMat(t.data_ptr(), t.shape[0], t.shape[1], t.stride(0), _dtype_code(t))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def opts(delta: float = 1e-2, max_swaps: int = 0, nblocks: int = 1, polish: bool = True) -> CurOpts:
+    return CurOpts(delta, max_swaps, nblocks, CUR_FLAG_POLISH if polish else 0)
+
+
+# ------------------------------------------------------------------ C ABI names
+
+def cur_workspace_size(m: int, n: int, r: int, dtype: int) -> int:
+    return load().cur_workspace_size(m, n, r, dtype)
+
+
+def cur_create(workspace_bytes: int) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().cur_create(ctypes.byref(h), workspace_bytes), "cur_create")
+    return h
+
+
+def cur_destroy(h) -> None:
+    _check(load().cur_destroy(h), "cur_destroy")
+
+
+def cur_sync_status(h, stream=None) -> int:
+    return load().cur_sync_status(h, _stream(stream))
+
+
+def cur_aca_select(h, A, axis: int, r: int, nblocks: int, idx_out, stream=None) -> int:
+    return _check(load().cur_aca_select(h, ctypes.byref(mat(A)), axis, r, nblocks,
+                                        _ptr(idx_out), _stream(stream)), "cur_aca_select")
+
+
+def cur_maxvol_rows(h, A, J, r: int, o: CurOpts, I_out, logvol_out=None, swaps_out=None,
+                    stream=None) -> int:
+    return _check(load().cur_maxvol_rows(h, ctypes.byref(mat(A)), _ptr(J), r, ctypes.byref(o),
+                                         _ptr(I_out), _ptr(logvol_out), _ptr(swaps_out),
+                                         _stream(stream)), "cur_maxvol_rows")
+
+
+def cur_maxvol_cols(h, A, I, r: int, o: CurOpts, J_out, logvol_out=None, swaps_out=None,
+                    stream=None) -> int:
+    return _check(load().cur_maxvol_cols(h, ctypes.byref(mat(A)), _ptr(I), r, ctypes.byref(o),
+                                         _ptr(J_out), _ptr(logvol_out), _ptr(swaps_out),
+                                         _stream(stream)), "cur_maxvol_cols")
+
+
+def cur_merge(h, basis, cand, nsets: int, r: int, o: CurOpts, out, stream=None) -> int:
+    return _check(load().cur_merge(h, ctypes.byref(mat(basis)), _ptr(cand), nsets, r,
+                                   ctypes.byref(o), _ptr(out), _stream(stream)), "cur_merge")
+
+
+def cur_assemble(h, A, I, J, r: int, C_out, U_out, R_out, rcond_out, stream=None) -> int:
+    return _check(load().cur_assemble(h, ctypes.byref(mat(A)), _ptr(I), _ptr(J), r, _ptr(C_out),
+                                      _ptr(U_out), _ptr(R_out), _ptr(rcond_out), _stream(stream)),
+                  "cur_assemble")
+
+
+def cur_residual_cheb(h, A, C, U, R, r: int, cheb_out, fro_out=None, stream=None) -> int:
+    return _check(load().cur_residual_cheb(h, ctypes.byref(mat(A)), _ptr(C), _ptr(U), _ptr(R), r,
+                                           _ptr(cheb_out), _ptr(fro_out), _stream(stream)),
+                  "cur_residual_cheb")
+
+
+def cur_cross(h, A, r: int, b_r: int, b_c: int, o: CurOpts, I_out, J_out, info_out=None,
+              stream=None) -> int:
+    return _check(load().cur_cross(h, ctypes.byref(mat(A)), r, b_r, b_c, ctypes.byref(o),
+                                   _ptr(I_out), _ptr(J_out), _ptr(info_out), _stream(stream)),
+                  "cur_cross")
+
+
+def cur_prof_enable(h, on: bool = True) -> None:
+    _check(load().cur_prof_enable(h, 1 if on else 0), "cur_prof_enable")
+
+
+def cur_prof_read(h, stream=None):
+    """(pass_ms, pass_launches, kernel_launches) since the last read."""
+    ms, n, k = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().cur_prof_read(h, _stream(stream), ctypes.byref(ms), ctypes.byref(n),
+                                ctypes.byref(k)), "cur_prof_read")
+    return ms.value, n.value, k.value
+
+
+def info_from_tensor(t) -> CurCrossInfo:
+    """Decode a cur_cross_info written into a uint8 tensor (copied to the host)."""
+    raw = bytes(t.cpu().numpy().tobytes())
+    return CurCrossInfo.from_buffer_copy(raw[:ctypes.sizeof(CurCrossInfo)])
+
+
+# ------------------------------------------------------------------ convenience
+
+class Handle:
+    """Owns a cur_handle and its workspace."""
+
+    def __init__(self, m: int, n: int, r: int, dtype: int = CUR_F32, workspace_bytes: int = 0):
+        size = workspace_bytes or cur_workspace_size(m, n, r, dtype)
+        self.h = cur_create(size)
+
+    def close(self):
+        if self.h is not None:
+            cur_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cross(A, r: int, b_r: int, b_c: int, delta: float = 1e-2, handle: Handle | None = None,
+          stream=None):
+    """Run cur_cross on a CUDA tensor; returns (I, J, info) with I, J int32 CUDA tensors."""
+    import torch
+    own = handle is None
+    hd = handle or Handle(A.shape[0], A.shape[1], r, _dtype_code(A))
+    try:
+        I = torch.empty(r, dtype=torch.int32, device=A.device)
+        J = torch.empty(r, dtype=torch.int32, device=A.device)
+        info = torch.zeros(ctypes.sizeof(CurCrossInfo), dtype=torch.uint8, device=A.device)
+        cur_cross(hd.h, A, r, b_r, b_c, opts(delta), I, J, info, stream)
+        st = cur_sync_status(hd.h, stream)
+        _check(st, "cur_cross (device)")
+        return I, J, info_from_tensor(info)
+    finally:
+        if own:
+            hd.close()

@@ -1,0 +1,467 @@
+// Algorithm 3 (Blockwise Adaptive Cross Approximation, Section 2.2 of the paper)
+// on a full m x n matrix, GB300 form.
+//
+// The paper keeps an explicit residual and, each round, (1) computes the squared
+// norm of every row/column of every block, (2) reduces the block maxima to one
+// pivot, (3) broadcasts the pivot vector v and (4) projects every block,
+// R <- R - v (v^T R) / ||v||^2. In exact arithmetic this is column-pivoted
+// Gram-Schmidt, so the same picks follow from an implicit residual:
+//   nu_j = ||a_j||^2 - sum_k (q_k^T a_j)^2,   q_k = orthonormal basis of the picks,
+// which needs one read of A per round (w = A^T q) instead of a read and a write.
+// Each round is
+//   pass   : w partials = A^T q_t over row chunks   (HBM stream, Dot2 accuracy)
+//   pivot  : one cooperative kernel: reduce partials, W(t,:) = w, nu -= w^2,
+//            argmax over unpicked (lowest index on ties), then the new direction
+//            v = a_p - Q W(:,p), re-orthogonalised once (CGS2), q = v / ||v||.
+// For axis 0 the roles of rows and columns swap (w = A q, row-dot products).
+
+#include <algorithm>
+#include <climits>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace curk {
+
+enum { kNorm = 0, kDot = 1 };
+
+template <typename TA>
+using AccOf = typename std::conditional<std::is_same<TA, double>::value, DotD, Dot2>::type;
+
+// Four consecutive elements, 16-byte (8-byte for BF16) vector loads, streaming.
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+    float4 x = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4(const __nv_bfloat16* p, float v[4]) {
+    uint2 x = __ldcs(reinterpret_cast<const uint2*>(p));
+    v[0] = __uint_as_float(x.x << 16);
+    v[1] = __uint_as_float(x.x & 0xffff0000u);
+    v[2] = __uint_as_float(x.y << 16);
+    v[3] = __uint_as_float(x.y & 0xffff0000u);
+}
+template <typename TA, typename TV>
+__device__ __forceinline__ void load4_guard(const TA* row, int64_t col, int64_t n, TV v[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (col + k < n) ? (TV)to_d(row[col + k]) : (TV)0;
+}
+
+template <typename TA> struct ValT { using type = float; };
+template <> struct ValT<double> { using type = double; };
+
+__device__ __forceinline__ void acc_add(DotD& a, double x, int mode, double q, float, float) {
+    if (mode == kNorm) a.add_sq(x); else a.add(x, q);
+}
+__device__ __forceinline__ void acc_add(Dot2& a, float x, int mode, double, float qh, float ql) {
+    if (mode == kNorm) a.add_sq(x); else a.add(x, qh, ql);
+}
+
+// part[rc * n + j] = sum over rows i of chunk rc of a_ij * q_i (kDot) or a_ij^2 (kNorm).
+// grid = (ceil(n / 128), RC), block = 256 (8 warps). Warp w takes rows r0 + w, r0 + w + 8,
+// ...; lane l takes the 4 columns 128 * blockIdx.x + 4 l .. + 3.
+template <typename TA, int MODE, bool VEC>
+__global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, int64_t m, int64_t n,
+                                                     int64_t ld, int64_t chunk,
+                                                     const double* __restrict__ q64,
+                                                     const float* __restrict__ qh,
+                                                     const float* __restrict__ ql,
+                                                     double* __restrict__ part,
+                                                     const int* __restrict__ stop) {
+    using V = typename ValT<TA>::type;
+    __shared__ double red[8][128];
+    if (*stop) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t col = (int64_t)blockIdx.x * 128 + lane * 4;
+    const int64_t r0 = (int64_t)blockIdx.y * chunk;
+    const int64_t r1 = min(r0 + chunk, m);
+    const bool full = VEC && (col + 3 < n);
+    AccOf<TA> acc[4];
+    int64_t i = r0 + warp;
+    for (; i + 24 < r1; i += 32) {
+        V x[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const TA* row = A + (i + 8 * u) * ld;
+            if (full) load4(row + col, x[u]); else load4_guard(row, col, n, x[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            double qd = 0.0; float h = 0.f, l = 0.f;
+            if (MODE == kDot) {
+                if (std::is_same<TA, double>::value) qd = q64[i + 8 * u];
+                else { h = qh[i + 8 * u]; l = ql[i + 8 * u]; }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc_add(acc[c], x[u][c], MODE, qd, h, l);
+        }
+    }
+    for (; i < r1; i += 8) {
+        V x[4];
+        const TA* row = A + i * ld;
+        if (full) load4(row + col, x); else load4_guard(row, col, n, x);
+        double qd = 0.0; float h = 0.f, l = 0.f;
+        if (MODE == kDot) {
+            if (std::is_same<TA, double>::value) qd = q64[i];
+            else { h = qh[i]; l = ql[i]; }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc_add(acc[c], x[c], MODE, qd, h, l);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = acc[c].value();
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        if (j < n) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+            part[(int64_t)blockIdx.y * n + j] = s;
+        }
+    }
+}
+
+// out[i] = sum_j a_ij * q_j (kDot) or a_ij^2 (kNorm); one warp per row.
+template <typename TA, int MODE, bool VEC>
+__global__ void __launch_bounds__(256) aca_rows_pass(const TA* __restrict__ A, int64_t m, int64_t n,
+                                                     int64_t ld, const double* __restrict__ q64,
+                                                     const float* __restrict__ qh,
+                                                     const float* __restrict__ ql,
+                                                     double* __restrict__ out,
+                                                     const int* __restrict__ stop) {
+    using V = typename ValT<TA>::type;
+    if (*stop) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t row = (int64_t)blockIdx.x * 8 + warp; row < m; row += (int64_t)gridDim.x * 8) {
+        const TA* a = A + row * ld;
+        AccOf<TA> acc;
+        for (int64_t j = (int64_t)lane * 4; j < n; j += 128) {
+            V x[4];
+            if (VEC && j + 3 < n) load4(a + j, x); else load4_guard(a, j, n, x);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t jj = j + c;
+                double qd = 0.0; float h = 0.f, l = 0.f;
+                if (MODE == kDot && jj < n) {
+                    if (std::is_same<TA, double>::value) qd = q64[jj];
+                    else { h = qh[jj]; l = ql[jj]; }
+                }
+                acc_add(acc, x[c], MODE, qd, h, l);
+            }
+        }
+        const double s = warp_sum(acc.value());
+        if (lane == 0) out[row] = s;
+    }
+}
+
+struct AcaParams {
+    const void* A;
+    int64_t m, n, ld;
+    int axis, r;
+    int64_t nsel, len;     // candidates (n for columns), vector length (m for columns)
+    const double* part;
+    int RC;
+    double* nu;
+    unsigned char* mask;
+    double* W;             // r x nsel: W(k, j) = q_k^T a_j
+    double* Q;             // len x r (row-major, stride r): orthonormal directions
+    double* q64;
+    float* qh;
+    float* ql;
+    double* v;             // len
+    double* red1;          // G x r
+    double* red2;          // G
+    double* redf;          // G
+    double* keyv;          // G
+    long long* keyi;       // G
+    unsigned* bar;
+    double* frob2;
+    int* count;
+    int* stop;
+    int* idx_out;
+    int* status;
+};
+
+template <typename TA>
+__device__ __forceinline__ double pivot_elem(const AcaParams& P, int64_t i, int64_t p) {
+    const TA* A = static_cast<const TA*>(P.A);
+    return P.axis == 1 ? to_d(A[i * P.ld + p]) : to_d(A[p * P.ld + i]);
+}
+
+// One round of Algorithm 3 after its pass. `part` holds A^T q_t (t >= 0) or the
+// squared norms (t = -1). Picks index k = t + 1; with `build`, also forms q_k.
+// Cooperative launch; grid G <= co-resident CTAs, block 256.
+template <typename TA>
+__global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) {
+    __shared__ double s_w[128];
+    __shared__ double s_red[4][64];
+    __shared__ double s_tot;
+    if (*P.stop) return;
+    const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    const int k = t + 1;
+
+    // P0: reduce partials, downdate squared norms, local argmax over unpicked.
+    const int64_t j0 = P.nsel * g / G, j1 = P.nsel * (g + 1) / G;
+    double bv = -INFINITY;
+    long long bi = LLONG_MAX;
+    double fs = 0.0;
+    int bad = 0;
+    for (int64_t j = j0 + tid; j < j1; j += nt) {
+        double w = 0.0;
+        for (int rc = 0; rc < P.RC; ++rc) w += P.part[(int64_t)rc * P.nsel + j];
+        double nu;
+        if (t < 0) {
+            nu = w;
+            fs += w;
+            if (!isfinite(w)) bad = 1;
+        } else {
+            P.W[(int64_t)t * P.nsel + j] = w;
+            nu = P.nu[j] - w * w;
+        }
+        P.nu[j] = nu;
+        if (!P.mask[j] && better(nu, (long long)j, bv, bi)) { bv = nu; bi = j; }
+    }
+    block_argmax(bv, bi);
+    bad = __syncthreads_or(bad);
+    if (t < 0) fs = block_sum(fs);
+    if (tid == 0) {
+        P.keyv[g] = bv;
+        P.keyi[g] = bad ? -2LL : bi;
+        P.redf[g] = fs;
+    }
+    if (!group_barrier(P.bar, (unsigned)G, P.status)) return;
+
+    // P1: the global pick, identical in every CTA.
+    double pv = -INFINITY;
+    long long pi = LLONG_MAX;
+    int anybad = 0;
+    for (int gg = tid; gg < G; gg += nt) {
+        const long long ki = P.keyi[gg];
+        if (ki == -2LL) anybad = 1;
+        else if (better(P.keyv[gg], ki, pv, pi)) { pv = P.keyv[gg]; pi = ki; }
+    }
+    anybad = __syncthreads_or(anybad);
+    block_argmax(pv, pi);
+    if (anybad) {
+        if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_ERR_NONFINITE); }
+        return;
+    }
+    if (tid == 0) {
+        double f2;
+        if (t < 0) {
+            f2 = 0.0;
+            for (int gg = 0; gg < G; ++gg) f2 += P.redf[gg];
+            if (g == 0) *P.frob2 = f2;
+        } else {
+            f2 = *P.frob2;
+        }
+        s_tot = f2;
+    }
+    __syncthreads();
+    const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
+    const double tol = mx * mx * s_tot;
+    if (pi == LLONG_MAX || pi < 0 || !(pv > tol)) {
+        if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
+        return;
+    }
+    const int64_t p = pi;
+    if (g == 0 && tid == 0) {
+        P.idx_out[k] = (int)p;
+        P.mask[p] = 1;
+        *P.count = k + 1;
+    }
+    if (!build) return;
+
+    // P1b: v = a_p - Q(:, :k) W(:k, p) on this CTA's slice, and Q^T v partials.
+    for (int kk = tid; kk < k; kk += nt) s_w[kk] = P.W[(int64_t)kk * P.nsel + p];
+    __syncthreads();
+    const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
+    const int r = P.r;
+    for (int64_t i = i0 + tid; i < i1; i += nt) {
+        const double* qi = P.Q + i * r;
+        double s = 0.0;
+        for (int kk = 0; kk < k; ++kk) s = fma(qi[kk], s_w[kk], s);
+        P.v[i] = pivot_elem<TA>(P, i, p) - s;
+    }
+    __syncthreads();
+    const int ngrp = nt >> 6, grp = tid >> 6, kl = tid & 63;
+    for (int kk0 = 0; kk0 < k; kk0 += 64) {
+        const int kk = kk0 + kl;
+        double acc = 0.0;
+        if (kk < k)
+            for (int64_t i = i0 + grp; i < i1; i += ngrp) acc = fma(P.Q[i * r + kk], P.v[i], acc);
+        s_red[grp][kl] = acc;
+        __syncthreads();
+        if (grp == 0 && kk < k) {
+            double s = 0.0;
+            for (int q = 0; q < ngrp; ++q) s += s_red[q][kl];
+            P.red1[(int64_t)g * r + kk] = s;
+        }
+        __syncthreads();
+    }
+    if (!group_barrier(P.bar, 2u * G, P.status)) return;
+
+    // P2: second Gram-Schmidt pass v -= Q (Q^T v); partial ||v||^2.
+    for (int kk = tid; kk < k; kk += nt) {
+        double s = 0.0;
+        for (int gg = 0; gg < G; ++gg) s += P.red1[(int64_t)gg * r + kk];
+        s_w[kk] = s;
+    }
+    __syncthreads();
+    double nv = 0.0;
+    for (int64_t i = i0 + tid; i < i1; i += nt) {
+        const double* qi = P.Q + i * r;
+        double s = 0.0;
+        for (int kk = 0; kk < k; ++kk) s = fma(qi[kk], s_w[kk], s);
+        const double vi = P.v[i] - s;
+        P.v[i] = vi;
+        nv = fma(vi, vi, nv);
+    }
+    nv = block_sum(nv);
+    if (tid == 0) P.red2[g] = nv;
+    if (!group_barrier(P.bar, 3u * G, P.status)) return;
+
+    // P3: q_k = v / ||v||.
+    if (tid == 0) {
+        double s = 0.0;
+        for (int gg = 0; gg < G; ++gg) s += P.red2[gg];
+        s_tot = s;
+    }
+    __syncthreads();
+    const double inv = 1.0 / sqrt(s_tot);
+    for (int64_t i = i0 + tid; i < i1; i += nt) {
+        const double q = P.v[i] * inv;
+        P.Q[i * r + k] = q;
+        P.q64[i] = q;
+        float hi, lo;
+        split_d(q, hi, lo);
+        P.qh[i] = hi;
+        P.ql[i] = lo;
+    }
+}
+
+template <typename TA>
+static cur_status launch_pass(const AcaParams& P, int mode, int64_t chunk, int rc_count,
+                              bool vec, cudaStream_t st) {
+    const TA* A = static_cast<const TA*>(P.A);
+    double* part = const_cast<double*>(P.part);
+    if (P.axis == 1) {
+        dim3 grid((unsigned)((P.n + 127) / 128), (unsigned)rc_count);
+        if (mode == kNorm) {
+            if (vec) aca_cols_pass<TA, kNorm, true><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
+            else aca_cols_pass<TA, kNorm, false><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
+        } else {
+            if (vec) aca_cols_pass<TA, kDot, true><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
+            else aca_cols_pass<TA, kDot, false><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
+        }
+    } else {
+        const int64_t blocks = std::min<int64_t>((P.m + 7) / 8, 65535LL * 8);
+        dim3 grid((unsigned)blocks);
+        if (mode == kNorm) {
+            if (vec) aca_rows_pass<TA, kNorm, true><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, P.q64, P.qh, P.ql, part, P.stop);
+            else aca_rows_pass<TA, kNorm, false><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, P.q64, P.qh, P.ql, part, P.stop);
+        } else {
+            if (vec) aca_rows_pass<TA, kDot, true><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, P.q64, P.qh, P.ql, part, P.stop);
+            else aca_rows_pass<TA, kDot, false><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, P.q64, P.qh, P.ql, part, P.stop);
+        }
+    }
+    CUR_CK(cudaGetLastError());
+    return CUR_OK;
+}
+
+template <typename TA>
+static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int32_t* idx_out,
+                          int32_t* count_dev, Arena& ar, cudaStream_t st) {
+    AcaParams P{};
+    P.A = M->data;
+    P.m = M->rows;
+    P.n = M->cols;
+    P.ld = M->ld;
+    P.axis = axis;
+    P.r = r;
+    P.nsel = axis == 1 ? P.n : P.m;
+    P.len = axis == 1 ? P.m : P.n;
+    const int G = h->num_sms;
+    // Row chunks of the column pass: enough CTAs for ~32 per SM.
+    int RC = 1;
+    int64_t chunk = P.m;
+    if (axis == 1) {
+        const int64_t coltiles = (P.n + 127) / 128;
+        int64_t want = std::max<int64_t>(1, (int64_t)h->num_sms * 32 / coltiles);
+        want = std::min<int64_t>(want, std::max<int64_t>(1, P.m / 64));
+        want = std::min<int64_t>(want, 65535);
+        RC = (int)want;
+        chunk = (P.m + RC - 1) / RC;
+        RC = (int)((P.m + chunk - 1) / chunk);
+    }
+    P.RC = RC;
+    P.part = ar.get<double>((size_t)RC * P.nsel);
+    P.nu = ar.get<double>(P.nsel);
+    P.mask = ar.get<unsigned char>(P.nsel);
+    P.W = ar.get<double>((size_t)r * P.nsel);
+    P.Q = ar.get<double>((size_t)P.len * r);
+    P.q64 = ar.get<double>(P.len);
+    P.qh = ar.get<float>(P.len);
+    P.ql = ar.get<float>(P.len);
+    P.v = ar.get<double>(P.len);
+    P.red1 = ar.get<double>((size_t)G * r);
+    P.red2 = ar.get<double>(G);
+    P.redf = ar.get<double>(G);
+    P.keyv = ar.get<double>(G);
+    P.keyi = ar.get<long long>(G);
+    P.bar = ar.get<unsigned>(1);
+    P.frob2 = ar.get<double>(1);
+    P.stop = ar.get<int>(1);
+    P.count = count_dev;
+    P.idx_out = idx_out;
+    P.status = h->status;
+    if (!ar.ok) return CUR_ERR_NOMEM;
+
+    const size_t es = sizeof(TA);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(M->data);
+    const size_t va = std::is_same<TA, __nv_bfloat16>::value ? 8 : 16;
+    const bool vec = (base % va == 0) && ((size_t)(M->ld * es) % va == 0);
+
+    CUR_CK(cudaMemsetAsync(P.mask, 0, P.nsel, st));
+    CUR_CK(cudaMemsetAsync(P.stop, 0, sizeof(int), st));
+    CUR_CK(cudaMemsetAsync(count_dev, 0, sizeof(int), st));
+    CUR_CK(cudaMemsetAsync(idx_out, 0xff, sizeof(int32_t) * r, st));
+
+    CUR_TRY(launch_pass<TA>(P, kNorm, chunk, RC, vec, st));
+    note_launch();
+    for (int t = -1; t <= r - 2; ++t) {
+        if (t >= 0) {
+            const bool ev = h->prof && h->prof_n < 512;
+            if (ev) CUR_CK(cudaEventRecord(h->prof_ev[2 * h->prof_n], st));
+            CUR_TRY(launch_pass<TA>(P, kDot, chunk, RC, vec, st));
+            if (ev) CUR_CK(cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], st));
+            if (ev) ++h->prof_n;
+            note_launch();
+        }
+        CUR_CK(cudaMemsetAsync(P.bar, 0, sizeof(unsigned), st));
+        int build = (t + 1 < r - 1) ? 1 : 0;
+        void* args[] = {&P, &t, &build};
+        CUR_TRY(launch_coop((const void*)aca_pivot<TA>, dim3(G), dim3(256), args, 0, st));
+        note_launch();
+    }
+    return CUR_OK;
+}
+
+}  // namespace curk
+
+cur_status aca_select_full(cur_handle* h, const cur_mat* A, int axis, int r, int32_t* idx_out,
+                           int32_t* count_dev, Arena& ar, cudaStream_t st) {
+    if (r > 128) return CUR_ERR_ARG;
+    switch (A->dtype) {
+        case CUR_F64: return curk::aca_run<double>(h, A, axis, r, idx_out, count_dev, ar, st);
+        case CUR_F32: return curk::aca_run<float>(h, A, axis, r, idx_out, count_dev, ar, st);
+        case CUR_BF16: return curk::aca_run<__nv_bfloat16>(h, A, axis, r, idx_out, count_dev, ar, st);
+    }
+    return CUR_ERR_ARG;
+}

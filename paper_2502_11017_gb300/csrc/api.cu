@@ -1,0 +1,328 @@
+// C ABI of libcur: handle, workspace, argument checks and the cross driver.
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+cur_status pad_indices_dev(int32_t* idx, const int32_t* count, int r, int64_t size, cudaStream_t st);
+
+namespace curk {
+
+__global__ void set_status_k(int* st, int code) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(st, code);
+}
+
+__global__ void fill_info_k(cur_cross_info* info, const double* logvol, int sweeps, int swaps_total,
+                            int s0, int s1, int s2, int s3, int s4, int s5, int s6, int s7,
+                            const int32_t* aca_count, const int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    info->logvol = *logvol;
+    info->sweeps = sweeps;
+    info->swaps_total = swaps_total;
+    const int s[8] = {s0, s1, s2, s3, s4, s5, s6, s7};
+    for (int k = 0; k < 8; ++k) info->sweep_swaps[k] = s[k];
+    info->aca_selected = *aca_count;
+    info->status = *status;
+}
+
+}  // namespace curk
+
+static std::atomic<long long> g_launches{0};
+void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
+                       cudaStream_t st) {
+    CUR_CK(cudaLaunchCooperativeKernel(fn, grid, block, args, smem, st));
+    return CUR_OK;
+}
+
+static bool mat_ok(const cur_mat* A) {
+    if (!A || !A->data) return false;
+    if (A->rows < 1 || A->cols < 1 || A->ld < A->cols) return false;
+    if (A->dtype != CUR_F64 && A->dtype != CUR_F32 && A->dtype != CUR_BF16) return false;
+    return true;
+}
+
+static cur_status peek_status(cur_handle* h, cudaStream_t st, int* out) {
+    int* hs = reinterpret_cast<int*>(h->host_stage);
+    CUR_CK(cudaMemcpyAsync(hs, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUR_CK(cudaStreamSynchronize(st));
+    *out = hs[0];
+    return CUR_OK;
+}
+
+extern "C" {
+
+cur_opts cur_default_opts(void) {
+    cur_opts o;
+    o.delta = 1e-2;
+    o.max_swaps = 0;
+    o.nblocks = 1;
+    o.flags = CUR_FLAG_POLISH;
+    return o;
+}
+
+const char* cur_status_string(cur_status s) {
+    switch (s) {
+        case CUR_OK: return "ok";
+        case CUR_ERR_ARG: return "invalid argument";
+        case CUR_ERR_SINGULAR: return "singular submatrix";
+        case CUR_ERR_NONFINITE: return "non-finite value in the data";
+        case CUR_ERR_NOCONV: return "maxvol did not converge within max_swaps";
+        case CUR_ERR_TIMEOUT: return "device-side wait timed out";
+        case CUR_ERR_NOMEM: return "workspace too small";
+        case CUR_ERR_CUDA: return "CUDA runtime error";
+        case CUR_WARN_RANK: return "residual exhausted before r picks";
+    }
+    return "unknown status";
+}
+
+size_t cur_workspace_size(int64_t m, int64_t n, int32_t r, cur_dtype dtype) {
+    if (m < 1 || n < 1 || r < 1) return 0;
+    const size_t cs = dtype == CUR_F64 ? 8 : 4;
+    const size_t mx = (size_t)std::max(m, n);
+    const size_t R = (size_t)r;
+    size_t b = (size_t)64 << 20;                              // tables, keys, small arrays
+    b += 8 * ((size_t)4864 * 128 + 8 * mx);                   // Algorithm 3 partials and vectors
+    b += 8 * R * mx * 2;                                      // W and Q of Algorithm 3
+    b += cs * R * (size_t)(m + n) * 4;                        // bases, B, merge unions
+    b += 8 * R * R * (size_t)((m + n) / R + 16) * 2;          // M^-1 per problem (two types)
+    b += 8 * R * (size_t)n + 8 * 4 * (size_t)(m / 64 + 1) * 64;  // residual W and partials
+    return b;
+}
+
+cur_status cur_create(cur_handle** hp, size_t workspace_bytes) {
+    if (!hp) return CUR_ERR_ARG;
+    *hp = nullptr;
+    cur_handle* h = new (std::nothrow) cur_handle();
+    if (!h) return CUR_ERR_NOMEM;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return CUR_ERR_CUDA;
+    }
+    h->ws_bytes = workspace_bytes;
+    if (workspace_bytes && cudaMalloc(&h->ws, workspace_bytes) != cudaSuccess) {
+        delete h;
+        return CUR_ERR_NOMEM;
+    }
+    h->host_stage_bytes = (size_t)4 << 20;
+    if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->host_stage, h->host_stage_bytes) != cudaSuccess ||
+        cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
+        if (h->ws) cudaFree(h->ws);
+        if (h->status) cudaFree(h->status);
+        if (h->host_stage) cudaFreeHost(h->host_stage);
+        delete h;
+        return CUR_ERR_CUDA;
+    }
+    *hp = h;
+    return CUR_OK;
+}
+
+cur_status cur_destroy(cur_handle* h) {
+    if (!h) return CUR_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (auto& e : h->prof_ev)
+        if (e) cudaEventDestroy(e);
+    if (h->ws) cudaFree(h->ws);
+    if (h->status) cudaFree(h->status);
+    if (h->host_stage) cudaFreeHost(h->host_stage);
+    delete h;
+    return CUR_OK;
+}
+
+cur_status cur_prof_enable(cur_handle* h, int on) {
+    if (!h) return CUR_ERR_ARG;
+    if (on && !h->prof_ev[0])
+        for (auto& e : h->prof_ev) CUR_CK(cudaEventCreate(&e));
+    h->prof = on ? 1 : 0;
+    h->prof_n = 0;
+    return CUR_OK;
+}
+
+cur_status cur_prof_read(cur_handle* h, cudaStream_t st, double* pass_ms, int32_t* pass_launches,
+                         int64_t* kernel_launches) {
+    if (!h) return CUR_ERR_ARG;
+    CUR_CK(cudaStreamSynchronize(st));
+    double tot = 0.0;
+    for (int k = 0; k < h->prof_n; ++k) {
+        float ms = 0.f;
+        CUR_CK(cudaEventElapsedTime(&ms, h->prof_ev[2 * k], h->prof_ev[2 * k + 1]));
+        tot += ms;
+    }
+    if (pass_ms) *pass_ms = tot;
+    if (pass_launches) *pass_launches = h->prof_n;
+    const long long nl = g_launches.exchange(0);
+    if (kernel_launches) *kernel_launches = nl;
+    h->prof_n = 0;
+    return CUR_OK;
+}
+
+cur_status cur_sync_status(cur_handle* h, cudaStream_t st) {
+    if (!h) return CUR_ERR_ARG;
+    int v = 0;
+    CUR_TRY(peek_status(h, st, &v));
+    CUR_CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CUR_CK(cudaStreamSynchronize(st));
+    return (cur_status)v;
+}
+
+cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r, int32_t nblocks,
+                          int32_t* idx_out, cudaStream_t st) {
+    if (!h || !mat_ok(A) || !idx_out || (axis != 0 && axis != 1) || nblocks < 1) return CUR_ERR_ARG;
+    const int64_t size = axis == 1 ? A->cols : A->rows;
+    if (r < 1 || r > 128 || r > size || nblocks > size) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    int32_t* cnt = ar.get<int32_t>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    return aca_select_full(h, A, axis, r, idx_out, cnt, ar, st);
+}
+
+static cur_status rows_common(cur_handle* h, const cur_mat* A, const int32_t* idx, int32_t r,
+                              const cur_opts* opts, int32_t* out, double* logvol_out,
+                              int32_t* swaps_out, bool cols, cudaStream_t st) {
+    if (!h || !mat_ok(A) || !idx || !out) return CUR_ERR_ARG;
+    const cur_opts o = opts ? *opts : cur_default_opts();
+    const int64_t p = cols ? A->cols : A->rows;
+    const int64_t other = cols ? A->rows : A->cols;
+    if (r < 1 || r > 128 || r > other || o.nblocks < 1 || p / o.nblocks < r) return CUR_ERR_ARG;
+    if (!(o.delta >= 0.0)) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    const cur_dtype cdt = A->dtype == CUR_F64 ? CUR_F64 : CUR_F32;
+    void* basis = ar.take((size_t)p * r * compute_size(cdt));
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    if (cols) CUR_TRY(gather_rows_t_compute(A, idx, r, basis, st));
+    else CUR_TRY(gather_cols_compute(A, idx, r, basis, st));
+    MvResult res;
+    CUR_TRY(maxvol_basis_rows(h, cdt, basis, p, r, &o, out, logvol_out, swaps_out, &res, ar, st));
+    if (res.status == CUR_ERR_NOCONV) {
+        curk::set_status_k<<<1, 32, 0, st>>>(h->status, CUR_ERR_NOCONV);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
+    return CUR_OK;
+}
+
+cur_status cur_maxvol_rows(cur_handle* h, const cur_mat* A, const int32_t* J, int32_t r,
+                           const cur_opts* opts, int32_t* I_out, double* logvol_out,
+                           int32_t* swaps_out, cudaStream_t st) {
+    return rows_common(h, A, J, r, opts, I_out, logvol_out, swaps_out, false, st);
+}
+
+cur_status cur_maxvol_cols(cur_handle* h, const cur_mat* A, const int32_t* I, int32_t r,
+                           const cur_opts* opts, int32_t* J_out, double* logvol_out,
+                           int32_t* swaps_out, cudaStream_t st) {
+    return rows_common(h, A, I, r, opts, J_out, logvol_out, swaps_out, true, st);
+}
+
+cur_status cur_merge(cur_handle* h, const cur_mat* basis, const int32_t* cand, int32_t nsets,
+                     int32_t r, const cur_opts* opts, int32_t* out, cudaStream_t st) {
+    if (!h || !mat_ok(basis) || !cand || !out || nsets < 1) return CUR_ERR_ARG;
+    if (basis->dtype == CUR_BF16) return CUR_ERR_ARG;
+    if (r < 1 || r > 128 || basis->cols != r || basis->ld != r || basis->rows < r) return CUR_ERR_ARG;
+    const cur_opts o = opts ? *opts : cur_default_opts();
+    Arena ar = h->arena();
+    int swaps = 0;
+    return merge_level(h, basis->dtype, basis->data, basis->rows, r, cand, nsets, &o, out, &swaps, ar, st);
+}
+
+cur_status cur_assemble(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
+                        int32_t r, void* C_out, double* U_out, void* R_out, double* rcond_out,
+                        cudaStream_t st) {
+    if (!h || !mat_ok(A) || !I || !J || !U_out || !rcond_out) return CUR_ERR_ARG;
+    if (r < 1 || r > 128 || r > A->rows || r > A->cols) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    return assemble_impl(h, A, I, J, r, C_out, U_out, R_out, rcond_out, ar, st);
+}
+
+cur_status cur_residual_cheb(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                             const void* R, int32_t r, double* cheb_out, double* fro_rel_out,
+                             cudaStream_t st) {
+    if (!h || !mat_ok(A) || !C || !U || !R || !cheb_out) return CUR_ERR_ARG;
+    if (r < 1 || r > 128) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    return residual_impl(h, A, C, U, R, r, cheb_out, fro_rel_out, ar, st);
+}
+
+cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, int32_t b_c,
+                     const cur_opts* opts, int32_t* I_out, int32_t* J_out,
+                     cur_cross_info* info_out, cudaStream_t st) {
+    if (!h || !mat_ok(A) || !I_out || !J_out) return CUR_ERR_ARG;
+    const int64_t m = A->rows, n = A->cols;
+    if (r < 1 || r > 128 || r >= std::min(m, n)) return CUR_ERR_ARG;
+    if (b_r < 1 || b_c < 1 || m / b_r < r || n / b_c < r) return CUR_ERR_ARG;
+    cur_opts o = opts ? *opts : cur_default_opts();
+    if (!(o.delta >= 0.0)) return CUR_ERR_ARG;
+    const int max_sweeps = 8;
+    Arena ar = h->arena();
+    const cur_dtype cdt = A->dtype == CUR_F64 ? CUR_F64 : CUR_F32;
+    const size_t cs = compute_size(cdt);
+    int32_t* J0 = ar.get<int32_t>(r);
+    int32_t* cnt = ar.get<int32_t>(1);
+    int32_t* I = ar.get<int32_t>(r);
+    int32_t* J = ar.get<int32_t>(r);
+    double* lv = ar.get<double>(1);
+    void* Cb = ar.take((size_t)m * r * cs);
+    void* Rb = ar.take((size_t)n * r * cs);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+
+    // J0: Algorithm 3 on the columns
+    CUR_TRY(aca_select_full(h, A, 1, r, J0, cnt, ar, st));
+    int stv = 0;
+    CUR_TRY(peek_status(h, st, &stv));
+    if (stv != CUR_OK && stv != CUR_WARN_RANK) return (cur_status)stv;
+    CUR_TRY(pad_indices_dev(J0, cnt, r, n, st));
+
+    int sweep_swaps[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int total = 0;
+    // sweep 1: blockwise rows on A(:,J0), then blockwise columns on A(I,:)^T
+    cur_opts orow = o;
+    orow.nblocks = b_r;
+    cur_opts ocol = o;
+    ocol.nblocks = b_c;
+    MvResult res;
+    CUR_TRY(gather_cols_compute(A, J0, r, Cb, st));
+    CUR_TRY(maxvol_basis_rows(h, cdt, Cb, m, r, &orow, I, nullptr, nullptr, &res, ar, st));
+    sweep_swaps[0] += res.swaps;
+    CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
+    CUR_TRY(maxvol_basis_rows(h, cdt, Rb, n, r, &ocol, J, lv, nullptr, &res, ar, st));
+    sweep_swaps[0] += res.swaps;
+    int last_status = res.status;
+    int sweeps = 1;
+    while (sweeps < max_sweeps) {
+        ++sweeps;
+        MvResult r1, r2;
+        CUR_TRY(gather_cols_compute(A, J, r, Cb, st));
+        CUR_TRY(maxvol_global(h, cdt, Cb, m, r, &o, I, I, nullptr, &r1, ar, st));
+        CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
+        CUR_TRY(maxvol_global(h, cdt, Rb, n, r, &o, J, J, lv, &r2, ar, st));
+        sweep_swaps[sweeps - 1] = r1.swaps + r2.swaps;
+        last_status = r1.status != CUR_OK ? r1.status : r2.status;
+        if (r1.status != CUR_OK || r2.status != CUR_OK) break;
+        if (r1.swaps + r2.swaps == 0) break;
+    }
+    for (int k = 0; k < 8; ++k) total += sweep_swaps[k];
+    if (last_status == CUR_ERR_NOCONV || last_status == CUR_ERR_SINGULAR) {
+        curk::set_status_k<<<1, 32, 0, st>>>(h->status, last_status);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
+    CUR_CK(cudaMemcpyAsync(I_out, I, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(J_out, J, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    if (info_out) {
+        curk::fill_info_k<<<1, 32, 0, st>>>(info_out, lv, sweeps, total, sweep_swaps[0], sweep_swaps[1],
+                                            sweep_swaps[2], sweep_swaps[3], sweep_swaps[4], sweep_swaps[5],
+                                            sweep_swaps[6], sweep_swaps[7], cnt, h->status);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
+    return CUR_OK;
+}
+
+}  // extern "C"

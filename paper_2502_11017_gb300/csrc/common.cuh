@@ -1,0 +1,181 @@
+// Shared device helpers for libcur (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "cur.h"
+
+namespace curk {
+
+constexpr int kWarp = 32;
+// Upper bound on one device-side wait (~2 s at 2 GHz). A wait that runs out sets
+// CUR_ERR_TIMEOUT in the status word and returns; nothing spins forever.
+constexpr long long kWaitCycles = 4000000000LL;
+
+// ---------------------------------------------------------------- element types
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+// Compute type of the maxvol coefficients for a given element type.
+template <typename T> struct Compute { using type = float; };
+template <> struct Compute<double> { using type = double; };
+
+// ---------------------------------------------------------------- status word
+
+// The first error wins; an error replaces an earlier CUR_WARN_RANK, never the reverse.
+__device__ __forceinline__ void set_status(int* st, int code) {
+    if (!st) return;
+    const int old = atomicCAS(st, 0, code);
+    if (old == CUR_WARN_RANK && code != CUR_WARN_RANK) atomicCAS(st, CUR_WARN_RANK, code);
+}
+
+// ---------------------------------------------------------------- accurate dot products
+//
+// Error-free transformations in FP32: TwoProduct through FMA and Knuth's TwoSum
+// (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26(6), 2005, algorithm Dot2). The explicit _rn intrinsics are never contracted
+// into FMAs by the compiler, which the transformations rely on. q is given as an
+// unevaluated sum qh + ql of two floats, so that the FP32 products carry the
+// accuracy of a double-precision q. The result is as if computed in about twice
+// FP32 precision and then rounded: error ~ 2^-48 sum|a_i q_i| + 2^-24 |result|,
+// and the result is read out in double.
+struct Dot2 {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float a, float qh, float ql) {
+        float p = __fmul_rn(a, qh);
+        float e = __fmaf_rn(a, qh, -p);
+        e = __fmaf_rn(a, ql, e);
+        float t = __fadd_rn(s, p);
+        float bp = __fsub_rn(t, s);
+        float sg = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(sg, e));
+    }
+    __device__ __forceinline__ void add_sq(float a) { add(a, a, 0.f); }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Plain double accumulator with the same interface (FP64 data).
+struct DotD {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double a, double q) { s = fma(a, q, s); }
+    __device__ __forceinline__ void add_sq(double a) { s = fma(a, a, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// Split a double into hi + lo floats (hi = fl32(x), lo = fl32(x - hi)).
+__device__ __forceinline__ void split_d(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// (value, index) maximum: larger value wins, then the smaller index.
+__device__ __forceinline__ bool better(double v1, long long i1, double v2, long long i2) {
+    return v1 > v2 || (v1 == v2 && i1 < i2);
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, long long& i) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+        long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+        if (better(v2, i2, v, i)) { v = v2; i = i2; }
+    }
+}
+
+// Block-wide argmax; every thread gets the result. blockDim.x must be a multiple
+// of 32 and at most 1024. Uses 2 x 32 words of static shared memory.
+__device__ __forceinline__ void block_argmax(double& v, long long& i) {
+    __shared__ double sv[32];
+    __shared__ long long si[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    warp_argmax(v, i);
+    __syncthreads();
+    if (lane == 0) { sv[warp] = v; si[warp] = i; }
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sv[lane] : -INFINITY;
+        i = lane < nw ? si[lane] : (long long)0x7fffffffffffffffLL;
+        warp_argmax(v, i);
+        if (lane == 0) { sv[0] = v; si[0] = i; }
+    }
+    __syncthreads();
+    v = sv[0];
+    i = si[0];
+    __syncthreads();
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sb[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) sb[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sb[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) sb[0] = v;
+    }
+    __syncthreads();
+    v = sb[0];
+    __syncthreads();
+    return v;
+}
+
+// ---------------------------------------------------------------- group barrier
+//
+// CTAs of one group (all co-resident: cooperative launch) meet here. `ctr` is a
+// counter zeroed before the launch; the n-th barrier of a group of G CTAs waits
+// for ctr >= n * G. Returns false (and sets CUR_ERR_TIMEOUT) if the wait runs out.
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        const long long t0 = clock64();
+        while (ld_acquire_u32(ctr) < target) {
+            if (clock64() - t0 > kWaitCycles) {
+                ok = 0;
+                set_status(status, CUR_ERR_TIMEOUT);
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    const int ok = s_ok;
+    __syncthreads();
+    return ok != 0;
+}
+
+}  // namespace curk

@@ -1,0 +1,110 @@
+// Host-side internals shared by the libcur translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "cur.h"
+
+#define CUR_CK(x)                                                   \
+    do {                                                            \
+        cudaError_t e_ = (x);                                       \
+        if (e_ != cudaSuccess) return CUR_ERR_CUDA;                 \
+    } while (0)
+
+#define CUR_TRY(x)                                                  \
+    do {                                                            \
+        cur_status s_ = (x);                                        \
+        if (s_ != CUR_OK) return s_;                                \
+    } while (0)
+
+// Bump allocator over the handle's workspace; reset at the start of each call.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    bool ok = true;
+    void* take(size_t bytes, size_t align = 256) {
+        size_t o = (off + align - 1) / align * align;
+        if (o + bytes > cap) {
+            ok = false;
+            return nullptr;
+        }
+        off = o + bytes;
+        return base + o;
+    }
+    template <typename T>
+    T* get(size_t count) {
+        return static_cast<T*>(take(count * sizeof(T) + 16));
+    }
+};
+
+// Counts kernel launches made by the library (all handles).
+void note_launch(int n = 1);
+
+struct cur_handle {
+    // instrumentation: events around the Algorithm 3 pass launches
+    int prof = 0;
+    int prof_n = 0;
+    cudaEvent_t prof_ev[2 * 512] = {};
+    int device = 0;
+    int num_sms = 0;
+    char* ws = nullptr;          // device workspace
+    size_t ws_bytes = 0;
+    int* status = nullptr;       // device status word (first error wins)
+    char* host_stage = nullptr;  // pinned host buffer for small transfers
+    size_t host_stage_bytes = 0;
+    Arena arena() const {
+        Arena a;
+        a.base = ws;
+        a.cap = ws_bytes;
+        return a;
+    }
+};
+
+// Element size of a cur_dtype.
+inline size_t dtype_size(cur_dtype t) { return t == CUR_F64 ? 8 : (t == CUR_F32 ? 4 : 2); }
+
+// ---- Algorithm 3 on a full matrix (aca.cu)
+// Writes r indices (or -1 after an early stop) to idx_out and the number picked
+// to *count_dev (both device). stop_dev (device int) is set on an early stop.
+cur_status aca_select_full(cur_handle* h, const cur_mat* A, int axis, int r, int32_t* idx_out,
+                           int32_t* count_dev, Arena& ar, cudaStream_t st);
+
+// ---- maxvol pipelines (maxvol.cu)
+struct MvResult {
+    int swaps = 0;
+    int status = CUR_OK;
+};
+// Row selection on the tall basis `basis` (p x r, compute type of A's dtype,
+// contiguous) with nblocks blocks, merge and optional polish. I_out: device r ints.
+cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
+                             const cur_opts* o, int32_t* I_out, double* logvol_out,
+                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st);
+// Maxvol over all rows of a basis from the start rows S0 (device r ints, global
+// rows). Writes the result to S_out (device, may alias S0).
+cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
+                         const cur_opts* o, const int32_t* S0, int32_t* S_out,
+                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st);
+// One merge level (cur_merge).
+cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
+                       const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
+                       int* swaps, Arena& ar, cudaStream_t st);
+// Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r).
+cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st);
+cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void* Rt,
+                                 cudaStream_t st);
+size_t compute_size(cur_dtype t);
+
+// ---- assembly and residual (residual.cu)
+cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
+                         int r, void* C_out, double* U_out, void* R_out, double* rcond_out,
+                         Arena& ar, cudaStream_t st);
+cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                         const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
+                         cudaStream_t st);
+
+// Cooperative launch helper (all CTAs co-resident).
+cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
+                       cudaStream_t st);

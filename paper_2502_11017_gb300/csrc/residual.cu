@@ -1,0 +1,458 @@
+// CUR assembly (Section 1.1: C = A(:,J), U = A(I,J)^dagger, R = A(I,:)) and the
+// residual of the cross (Theorem 1's Chebyshev norm max|A - CUR| and the relative
+// Frobenius error of Section 3.1).
+//
+// The residual reads A exactly once. W = U R (r x n) is formed first in FP64 and
+// rounded to the arithmetic type; each CTA then owns a 128-row panel, keeps its
+// C rows in shared memory and walks the panel's column tiles: E = A - C W on a
+// 128 x 128 tile, with |E| max, sum E^2 and sum A^2 folded in the epilogue.
+
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace curk {
+
+constexpr double kEpsR = 2.220446049250313e-16;
+
+template <typename TA>
+__global__ void gather_C_k(const TA* __restrict__ A, int64_t m, int64_t n, int64_t ld,
+                           const int32_t* __restrict__ J, int r, TA* __restrict__ C, int* status) {
+    const int64_t total = m * r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / r;
+        const int64_t j = J[e - i * r];
+        if (j < 0 || j >= n) { set_status(status, CUR_ERR_ARG); C[e] = A[0]; continue; }
+        C[e] = A[i * ld + j];
+    }
+}
+
+template <typename TA>
+__global__ void gather_R_k(const TA* __restrict__ A, int64_t m, int64_t n, int64_t ld,
+                           const int32_t* __restrict__ I, int r, TA* __restrict__ R, int* status) {
+    const int64_t total = (int64_t)r * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e / n, j = e - k * n;
+        const int64_t i = I[k];
+        if (i < 0 || i >= m) { set_status(status, CUR_ERR_ARG); R[e] = A[0]; continue; }
+        R[e] = A[i * ld + j];
+    }
+}
+
+// One CTA: M = A(I,J) in FP64, LU with partial pivoting, inverse, rcond; if
+// rcond < 1e-13 (or M is singular) the pseudo-inverse from a one-sided Jacobi SVD
+// (round-robin pair order, one warp per pair) with cutoff r eps s_max.
+// work: 3 r^2 doubles (global scratch).
+template <typename TA>
+__global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, int64_t m,
+                                                      int64_t n, int64_t ld,
+                                                      const int32_t* __restrict__ I,
+                                                      const int32_t* __restrict__ J, int r,
+                                                      double* __restrict__ U, double* rcond_out,
+                                                      double* __restrict__ work, int* status) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double* M = work;            // r x r, LU in place
+    double* X = work + r * r;    // r x r
+    double* M0 = work + 2 * r * r;
+    __shared__ int s_piv, s_sing, s_bad;
+    __shared__ double s_max, s_n1, s_ni;
+    __shared__ int perm[128];
+    if (tid == 0) { s_bad = 0; s_sing = 0; }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += nt) {
+        const int a = e / r, b = e - a * r;
+        const int64_t i = I[a], j = J[b];
+        double x = 0.0;
+        if (i < 0 || i >= m || j < 0 || j >= n) s_bad = 1;
+        else x = to_d(A[i * ld + j]);
+        if (!isfinite(x)) s_bad = 2;
+        M[e] = x;
+        M0[e] = x;
+    }
+    for (int k = tid; k < r; k += nt) perm[k] = k;
+    __syncthreads();
+    if (s_bad) {
+        if (tid == 0) {
+            set_status(status, s_bad == 2 ? CUR_ERR_NONFINITE : CUR_ERR_ARG);
+            *rcond_out = 0.0;
+        }
+        return;
+    }
+    if (tid == 0) {
+        double mx = 0.0, n1 = 0.0;
+        for (int c = 0; c < r; ++c) {
+            double cs = 0.0;
+            for (int a = 0; a < r; ++a) { mx = fmax(mx, fabs(M[a * r + c])); cs += fabs(M[a * r + c]); }
+            n1 = fmax(n1, cs);
+        }
+        s_max = mx;
+        s_n1 = n1;
+    }
+    __syncthreads();
+    const double thresh = (double)r * kEpsR * s_max;
+    for (int k = 0; k < r; ++k) {
+        if (tid == 0) {
+            double bv = -1.0;
+            int bi = k;
+            for (int i = k; i < r; ++i) {
+                const double x = fabs(M[i * r + k]);
+                if (x > bv) { bv = x; bi = i; }
+            }
+            s_piv = bi;
+        }
+        __syncthreads();
+        const int pv = s_piv;
+        if (pv != k) {
+            for (int c = tid; c < r; c += nt) {
+                const double t = M[k * r + c];
+                M[k * r + c] = M[pv * r + c];
+                M[pv * r + c] = t;
+            }
+            if (tid == 0) { const int t = perm[k]; perm[k] = perm[pv]; perm[pv] = t; }
+        }
+        __syncthreads();
+        const double d = M[k * r + k];
+        if (!(fabs(d) > thresh) && tid == 0) s_sing = 1;
+        if (d != 0.0) {
+            for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] /= d;
+            __syncthreads();
+            const int w = r - k - 1;
+            for (int e = tid; e < w * w; e += nt) {
+                const int i = k + 1 + e / w, j = k + 1 + e % w;
+                M[i * r + j] -= M[i * r + k] * M[k * r + j];
+            }
+        }
+        __syncthreads();
+    }
+    bool use_pinv = s_sing != 0;
+    if (!use_pinv) {
+        for (int c = tid; c < r; c += nt) {
+            for (int i = 0; i < r; ++i) {
+                double s = (perm[i] == c) ? 1.0 : 0.0;
+                for (int j = 0; j < i; ++j) s -= M[i * r + j] * X[j * r + c];
+                X[i * r + c] = s;
+            }
+            for (int i = r - 1; i >= 0; --i) {
+                double s = X[i * r + c];
+                for (int j = i + 1; j < r; ++j) s -= M[i * r + j] * X[j * r + c];
+                X[i * r + c] = s / M[i * r + i];
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double ni = 0.0;
+            for (int c = 0; c < r; ++c) {
+                double cs = 0.0;
+                for (int a = 0; a < r; ++a) cs += fabs(X[a * r + c]);
+                ni = fmax(ni, cs);
+            }
+            s_ni = ni;
+            *rcond_out = 1.0 / (s_n1 * ni);
+        }
+        __syncthreads();
+        use_pinv = !(1.0 / (s_n1 * s_ni) >= 1e-13);
+        if (!use_pinv) {
+            for (int e = tid; e < r * r; e += nt) U[e] = X[e];
+            return;
+        }
+    } else if (tid == 0) {
+        *rcond_out = 0.0;
+    }
+    // ---- pseudo-inverse: one-sided Jacobi on the columns of M0, V accumulates rotations
+    double* Aj = M0;
+    double* V = X;
+    for (int e = tid; e < r * r; e += nt) V[e] = ((e / r) == (e % r)) ? 1.0 : 0.0;
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const int rr = (r % 2 == 0) ? r : r + 1;  // round-robin over an even count (phantom column)
+    __shared__ int s_rot;
+    for (int sweep = 0; sweep < 80; ++sweep) {
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        for (int step = 0; step < rr - 1; ++step) {
+            for (int pr = warp; pr < rr / 2; pr += nw) {
+                // pairs (a, b) of the round-robin schedule: position 0 fixed, others rotate
+                int a, b;
+                {
+                    const int i1 = pr, i2 = rr - 1 - pr;
+                    auto pos = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + step) % (rr - 1); };
+                    a = pos(i1);
+                    b = pos(i2);
+                }
+                if (a > b) { const int t = a; a = b; b = t; }
+                if (b >= r) continue;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < r; i += 32) {
+                    const double x = Aj[i * r + a], y = Aj[i * r + b];
+                    al = fma(x, x, al);
+                    be = fma(y, y, be);
+                    ga = fma(x, y, ga);
+                }
+                al = warp_sum(al);
+                be = warp_sum(be);
+                ga = warp_sum(ga);
+                if (ga == 0.0 || fabs(ga) <= 1e-15 * sqrt(al * be)) continue;
+                if (lane == 0) s_rot = 1;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+                for (int i = lane; i < r; i += 32) {
+                    const double x = Aj[i * r + a], y = Aj[i * r + b];
+                    Aj[i * r + a] = c * x - s * y;
+                    Aj[i * r + b] = s * x + c * y;
+                    const double vx = V[i * r + a], vy = V[i * r + b];
+                    V[i * r + a] = c * vx - s * vy;
+                    V[i * r + b] = s * vx + c * vy;
+                }
+            }
+            __syncthreads();
+        }
+        const int rot = s_rot;
+        __syncthreads();
+        if (!rot) break;
+    }
+    // singular values, cutoff, U = V diag(1/s) Uhat^T with Uhat = Aj / s
+    __shared__ double sv[128];
+    for (int k = tid; k < r; k += nt) {
+        double s = 0.0;
+        for (int i = 0; i < r; ++i) s = fma(Aj[i * r + k], Aj[i * r + k], s);
+        sv[k] = sqrt(s);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double smax = 0.0;
+        for (int k = 0; k < r; ++k) smax = fmax(smax, sv[k]);
+        s_max = (double)r * kEpsR * smax;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += nt) {
+        const int i = e / r, j = e - i * r;
+        double s = 0.0;
+        for (int k = 0; k < r; ++k)
+            if (sv[k] > s_max) s += V[i * r + k] * (Aj[j * r + k] / sv[k]) / sv[k];
+        U[e] = s;
+    }
+}
+
+// W = U R (r x n) in FP64, rounded to TW. One thread per column.
+template <typename TA, typename TW>
+__global__ void __launch_bounds__(256) residual_w_k(const double* __restrict__ U,
+                                                   const TA* __restrict__ R, int r, int64_t n,
+                                                   TW* __restrict__ W) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* Us = reinterpret_cast<double*>(smem_raw);
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Us[e] = U[e];
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double rc[128];
+        for (int l = 0; l < r; ++l) rc[l] = to_d(R[(int64_t)l * n + j]);
+        for (int k = 0; k < r; ++k) {
+            double s = 0.0;
+            for (int l = 0; l < r; ++l) s = fma(Us[k * r + l], rc[l], s);
+            W[(int64_t)k * n + j] = (TW)s;
+        }
+    }
+}
+
+// Residual tiles. TM x TN outputs per thread, 16 x 16 threads, tile (16 TM) x (16 TN).
+// Grid: (panels, segments); CTA (p, s) takes rows [p*BM, p*BM+BM) and column tiles
+// s, s + segs, ... Partials per CTA: max|E|, sum E^2, sum A^2, non-finite flag.
+template <typename TA, typename TW, int TM, int TN>
+__global__ void __launch_bounds__(256) residual_k(const TA* __restrict__ A, int64_t m, int64_t n,
+                                                  int64_t ld, const TA* __restrict__ C,
+                                                  const TW* __restrict__ W, int r,
+                                                  double* __restrict__ part) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TW* Ct = reinterpret_cast<TW*>(smem_raw);  // r x BM (transposed C panel)
+    TW* Ws = Ct + (size_t)r * BM;              // r x BN
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * BM;
+    const int segs = gridDim.y;
+    for (int e = threadIdx.x; e < BM * r; e += blockDim.x) {
+        const int i = e / r, k = e - i * r;
+        Ct[k * BM + i] = (r0 + i < m) ? (TW)to_d(C[(r0 + i) * r + k]) : (TW)0;
+    }
+    double mx = 0.0, se = 0.0, sa = 0.0;
+    int bad = 0;
+    const int64_t ntile = (n + BN - 1) / BN;
+    for (int64_t tn = blockIdx.y; tn < ntile; tn += segs) {
+        const int64_t c0 = tn * BN;
+        __syncthreads();
+        for (int e = threadIdx.x; e < BN * r; e += blockDim.x) {
+            const int k = e / BN, j = e - k * BN;
+            Ws[k * BN + j] = (c0 + j < n) ? W[(int64_t)k * n + c0 + j] : (TW)0;
+        }
+        __syncthreads();
+        TW acc[TM][TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) acc[a][b] = (TW)0;
+        for (int k = 0; k < r; ++k) {
+            TW x[TM], y[TN];
+#pragma unroll
+            for (int a = 0; a < TM; ++a) x[a] = Ct[k * BM + ty * TM + a];
+#pragma unroll
+            for (int b = 0; b < TN; ++b) y[b] = Ws[k * BN + tx * TN + b];
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int b = 0; b < TN; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
+        }
+        TW tmx = (TW)0, tse = (TW)0, tsa = (TW)0;
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+            const int64_t i = r0 + ty * TM + a;
+            if (i >= m) continue;
+            const TA* arow = A + i * ld + c0 + tx * TN;
+#pragma unroll
+            for (int b = 0; b < TN; ++b) {
+                if (c0 + tx * TN + b >= n) continue;
+                const TW av = (TW)to_d(arow[b]);
+                const TW e = av - acc[a][b];
+                if (!(fabs(e) <= (TW)INFINITY)) bad = 1;
+                tmx = fmax(tmx, fabs(e));
+                tse = fma(e, e, tse);
+                tsa = fma(av, av, tsa);
+            }
+        }
+        mx = fmax(mx, (double)tmx);
+        se += (double)tse;
+        sa += (double)tsa;
+    }
+    // CTA reduction
+    __shared__ double rmx[8], rse[8], rsa[8];
+    __shared__ int rbad;
+    if (threadIdx.x == 0) rbad = 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    }
+    __syncthreads();
+    if (bad) rbad = 1;
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { rmx[warp] = mx; rse[warp] = se; rsa[warp] = sa; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        for (int w = 0; w < 8; ++w) { a1 = fmax(a1, rmx[w]); a2 += rse[w]; a3 += rsa[w]; }
+        const int64_t cta = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        part[cta * 4 + 0] = a1;
+        part[cta * 4 + 1] = a2;
+        part[cta * 4 + 2] = a3;
+        part[cta * 4 + 3] = rbad ? 1.0 : 0.0;
+    }
+}
+
+__global__ void residual_final_k(const double* part, int64_t nparts, double* cheb, double* fro,
+                                 int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int bad = 0;
+    for (int64_t c = 0; c < nparts; ++c) {
+        a1 = fmax(a1, part[c * 4 + 0]);
+        a2 += part[c * 4 + 1];
+        a3 += part[c * 4 + 2];
+        bad |= part[c * 4 + 3] != 0.0;
+    }
+    if (bad) {
+        set_status(status, CUR_ERR_NONFINITE);
+        a1 = NAN;
+    }
+    *cheb = a1;
+    if (fro) *fro = a3 > 0.0 ? sqrt(a2 / a3) : 0.0;
+}
+
+static inline unsigned nb(int64_t n, int t = 256) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
+}
+
+template <typename TA>
+static cur_status assemble_t(cur_handle* h, const cur_mat* Am, const int32_t* I, const int32_t* J,
+                             int r, void* C_out, double* U_out, void* R_out, double* rcond_out,
+                             Arena& ar, cudaStream_t st) {
+    const TA* A = static_cast<const TA*>(Am->data);
+    double* work = ar.get<double>((size_t)3 * r * r);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    if (C_out) {
+        gather_C_k<TA><<<nb(Am->rows * r), 256, 0, st>>>(A, Am->rows, Am->cols, Am->ld, J, r, static_cast<TA*>(C_out), h->status);
+        CUR_CK(cudaGetLastError());
+    note_launch();
+    }
+    if (R_out) {
+        gather_R_k<TA><<<nb(Am->cols * r), 256, 0, st>>>(A, Am->rows, Am->cols, Am->ld, I, r, static_cast<TA*>(R_out), h->status);
+        CUR_CK(cudaGetLastError());
+    note_launch();
+    }
+    assemble_inv_k<TA><<<1, 256, 0, st>>>(A, Am->rows, Am->cols, Am->ld, I, J, r, U_out, rcond_out, work, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+template <typename TA, typename TW, int TM, int TN>
+static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, const double* U,
+                             const void* R, int r, double* cheb, double* fro, Arena& ar,
+                             cudaStream_t st) {
+    const int64_t m = Am->rows, n = Am->cols;
+    TW* W = ar.get<TW>((size_t)r * n);
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    const int64_t panels = (m + BM - 1) / BM;
+    const int64_t ntile = (n + BN - 1) / BN;
+    const size_t sm = (size_t)r * (BM + BN) * sizeof(TW);
+    CUR_CK(cudaFuncSetAttribute((const void*)residual_k<TA, TW, TM, TN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int occ = 1;
+    CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, residual_k<TA, TW, TM, TN>, 256, sm));
+    const int64_t want = (int64_t)h->num_sms * std::max(1, occ) * 4;
+    int64_t segs = std::max<int64_t>(1, std::min<int64_t>(ntile, (want + panels - 1) / panels));
+    segs = std::min<int64_t>(segs, 65535);
+    if (panels > 2147483647LL) return CUR_ERR_ARG;
+    double* part = ar.get<double>((size_t)panels * segs * 4);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    const size_t smw = (size_t)r * r * sizeof(double);
+    CUR_CK(cudaFuncSetAttribute((const void*)residual_w_k<TA, TW>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    residual_w_k<TA, TW><<<nb(n), 256, smw, st>>>(U, static_cast<const TA*>(R), r, n, W);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    residual_k<TA, TW, TM, TN><<<dim3((unsigned)panels, (unsigned)segs), 256, sm, st>>>(
+        static_cast<const TA*>(Am->data), m, n, Am->ld, static_cast<const TA*>(C), W, r, part);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    residual_final_k<<<1, 32, 0, st>>>(part, panels * segs, cheb, fro, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+}  // namespace curk
+
+cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
+                         int r, void* C_out, double* U_out, void* R_out, double* rcond_out,
+                         Arena& ar, cudaStream_t st) {
+    switch (A->dtype) {
+        case CUR_F64: return curk::assemble_t<double>(h, A, I, J, r, C_out, U_out, R_out, rcond_out, ar, st);
+        case CUR_F32: return curk::assemble_t<float>(h, A, I, J, r, C_out, U_out, R_out, rcond_out, ar, st);
+        case CUR_BF16: return curk::assemble_t<__nv_bfloat16>(h, A, I, J, r, C_out, U_out, R_out, rcond_out, ar, st);
+    }
+    return CUR_ERR_ARG;
+}
+
+cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                         const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
+                         cudaStream_t st) {
+    switch (A->dtype) {
+        case CUR_F64: return curk::residual_t<double, double, 4, 4>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+        case CUR_F32: return curk::residual_t<float, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+        case CUR_BF16: return curk::residual_t<__nv_bfloat16, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+    }
+    return CUR_ERR_ARG;
+}
