@@ -45,8 +45,8 @@ _lib = None
 
 
 def build(verbose: bool = False) -> str:
-    from . import build as _b
-    return _b.build(verbose=verbose)
+    from . import buildlib
+    return buildlib.build(verbose=verbose)
 
 
 def load(path: str = LIB_PATH) -> ctypes.CDLL:

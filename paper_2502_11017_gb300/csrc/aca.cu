@@ -252,31 +252,16 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_ERR_NONFINITE); }
         return;
     }
-    if (tid == 0) {
-        double f2;
-        if (t < 0) {
-            f2 = 0.0;
-            for (int gg = 0; gg < G; ++gg) f2 += P.redf[gg];
-            if (g == 0) *P.frob2 = f2;
-        } else {
-            f2 = *P.frob2;
-        }
-        s_tot = f2;
+    if (t < 0 && g == 0 && tid == 0) {
+        double f2 = 0.0;
+        for (int gg = 0; gg < G; ++gg) f2 += P.redf[gg];
+        *P.frob2 = f2;
     }
-    __syncthreads();
-    const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
-    const double tol = mx * mx * s_tot;
-    if (pi == LLONG_MAX || pi < 0 || !(pv > tol)) {
+    if (pi == LLONG_MAX || pi < 0) {
         if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
         return;
     }
     const int64_t p = pi;
-    if (g == 0 && tid == 0) {
-        P.idx_out[k] = (int)p;
-        P.mask[p] = 1;
-        *P.count = k + 1;
-    }
-    if (!build) return;
 
     // P1b: v = a_p - Q(:, :k) W(:k, p) on this CTA's slice, and Q^T v partials.
     for (int kk = tid; kk < k; kk += nt) s_w[kk] = P.W[(int64_t)kk * P.nsel + p];
@@ -327,13 +312,27 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     if (tid == 0) P.red2[g] = nv;
     if (!group_barrier(P.bar, 3u * G, P.status)) return;
 
-    // P3: q_k = v / ||v||.
+    // P3: the residual norm of the pick, recomputed (||v||^2 after two Gram-Schmidt
+    // passes), decides an early stop exactly as the explicit residual would:
+    // ||v||^2 <= (max(m,n) eps)^2 ||A||_F^2 ends the selection before recording p.
+    // Otherwise p is recorded and q_k = v / ||v||.
     if (tid == 0) {
         double s = 0.0;
         for (int gg = 0; gg < G; ++gg) s += P.red2[gg];
         s_tot = s;
     }
     __syncthreads();
+    const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
+    if (!(s_tot > mx * mx * (*P.frob2))) {
+        if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
+        return;
+    }
+    if (g == 0 && tid == 0) {
+        P.idx_out[k] = (int)p;
+        P.mask[p] = 1;
+        *P.count = k + 1;
+    }
+    if (!build) return;
     const double inv = 1.0 / sqrt(s_tot);
     for (int64_t i = i0 + tid; i < i1; i += nt) {
         const double q = P.v[i] * inv;

@@ -225,18 +225,14 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
                 for (int g = 0; g < G; ++g) f += a.aux[(pr.group0 + g) * 2];
                 s_frob = f;
             }
-            const double mx = (double)max(pr.p, r) * kEps;
-            s_stop = (pi == LLONG_MAX || !(pv > mx * mx * s_frob)) ? 1 : 0;
+            s_stop = (pi == LLONG_MAX) ? 1 : 0;
             s_p = s_stop ? 0 : (int)pi;
         }
         __syncthreads();
         if (s_stop) break;
         const int p = s_p;
-        if (part == 0 && tid == 0) Sout[k] = p;
-        if (p >= lo && p < hi && tid == 0) msk[p - lo] = 1;
-        picked = k + 1;
-        if (k == r - 1) break;
-        // new direction: v = c_p - Q Q^T c_p, twice (CGS2), then q_k = v / ||v||
+        // new direction: v = c_p - Q Q^T c_p, twice (CGS2); its norm is the recomputed
+        // residual norm of row p, which decides an early stop before p is recorded
         const TB* cp = basis + (int64_t)p * r;
         for (int c = tid; c < r; c += nt) v[c] = to_d(cp[c]);
         __syncthreads();
@@ -259,9 +255,16 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
         if (tid == 0) {
             double s = 0.0;
             for (int c = 0; c < r; ++c) s = fma(v[c], v[c], s);
+            const double mx = (double)max(pr.p, r) * kEps;
+            s_stop = !(s > mx * mx * s_frob) ? 1 : 0;
             scr[1] = 1.0 / sqrt(s);
         }
         __syncthreads();
+        if (s_stop) break;
+        if (part == 0 && tid == 0) Sout[k] = p;
+        if (p >= lo && p < hi && tid == 0) msk[p - lo] = 1;
+        picked = k + 1;
+        if (k == r - 1) break;
         for (int c = tid; c < r; c += nt) {
             const double q = v[c] * scr[1];
             Q[k * r + c] = q;
