@@ -170,7 +170,7 @@ struct AcaParams {
     double* nu;
     unsigned char* mask;
     double* W;             // r x nsel: W(k, j) = q_k^T a_j
-    double* Q;             // len x r (row-major, stride r): orthonormal directions
+    double* Q;             // r x len (column k contiguous): orthonormal directions
     double* q64;
     float* qh;
     float* ql;
@@ -200,32 +200,48 @@ __device__ __forceinline__ double pivot_elem(const AcaParams& P, int64_t i, int6
 template <typename TA>
 __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) {
     __shared__ double s_w[128];
-    __shared__ double s_red[4][64];
+    __shared__ double s_q[4][64];
     __shared__ double s_tot;
     if (*P.stop) return;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int k = t + 1;
 
-    // P0: reduce partials, downdate squared norms, local argmax over unpicked.
+    // P0: reduce partials, downdate squared norms, local argmax over unpicked. The RC
+    // partials of each column are summed by 4 threads in fixed order (deterministic).
     const int64_t j0 = P.nsel * g / G, j1 = P.nsel * (g + 1) / G;
     double bv = -INFINITY;
     long long bi = LLONG_MAX;
     double fs = 0.0;
     int bad = 0;
-    for (int64_t j = j0 + tid; j < j1; j += nt) {
-        double w = 0.0;
-        for (int rc = 0; rc < P.RC; ++rc) w += P.part[(int64_t)rc * P.nsel + j];
-        double nu;
-        if (t < 0) {
-            nu = w;
-            fs += w;
-            if (!isfinite(w)) bad = 1;
-        } else {
-            P.W[(int64_t)t * P.nsel + j] = w;
-            nu = P.nu[j] - w * w;
+    {
+        const int lane64 = tid & 63, q4 = tid >> 6;   // 64 columns x 4 quarter-sums per pass
+        for (int64_t jb = j0; jb < j1; jb += 64) {
+            const int64_t j = jb + lane64;
+            double w = 0.0;
+            if (j < j1) {
+                const int rc0 = P.RC * q4 / 4, rc1 = P.RC * (q4 + 1) / 4;
+                const double* src = P.part + j;
+#pragma unroll 4
+                for (int rc = rc0; rc < rc1; ++rc) w += src[(int64_t)rc * P.nsel];
+            }
+            s_q[q4][lane64] = w;
+            __syncthreads();
+            if (q4 == 0 && j < j1) {
+                w = ((s_q[0][lane64] + s_q[1][lane64]) + s_q[2][lane64]) + s_q[3][lane64];
+                double nu;
+                if (t < 0) {
+                    nu = w;
+                    fs += w;
+                    if (!isfinite(w)) bad = 1;
+                } else {
+                    P.W[(int64_t)t * P.nsel + j] = w;
+                    nu = P.nu[j] - w * w;
+                }
+                P.nu[j] = nu;
+                if (!P.mask[j] && better(nu, (long long)j, bv, bi)) { bv = nu; bi = j; }
+            }
+            __syncthreads();
         }
-        P.nu[j] = nu;
-        if (!P.mask[j] && better(nu, (long long)j, bv, bi)) { bv = nu; bi = j; }
     }
     block_argmax(bv, bi);
     bad = __syncthreads_or(bad);
@@ -252,10 +268,9 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_ERR_NONFINITE); }
         return;
     }
-    if (t < 0 && g == 0 && tid == 0) {
-        double f2 = 0.0;
-        for (int gg = 0; gg < G; ++gg) f2 += P.redf[gg];
-        *P.frob2 = f2;
+    if (t < 0 && g == 0 && tid < 32) {
+        const double f2 = warp_sum_strided(P.redf, G);
+        if (tid == 0) *P.frob2 = f2;
     }
     if (pi == LLONG_MAX || pi < 0) {
         if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
@@ -268,42 +283,38 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     __syncthreads();
     const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
     const int r = P.r;
+    const int64_t len = P.len;
     for (int64_t i = i0 + tid; i < i1; i += nt) {
-        const double* qi = P.Q + i * r;
         double s = 0.0;
-        for (int kk = 0; kk < k; ++kk) s = fma(qi[kk], s_w[kk], s);
+        for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
         P.v[i] = pivot_elem<TA>(P, i, p) - s;
     }
     __syncthreads();
-    const int ngrp = nt >> 6, grp = tid >> 6, kl = tid & 63;
-    for (int kk0 = 0; kk0 < k; kk0 += 64) {
-        const int kk = kk0 + kl;
-        double acc = 0.0;
-        if (kk < k)
-            for (int64_t i = i0 + grp; i < i1; i += ngrp) acc = fma(P.Q[i * r + kk], P.v[i], acc);
-        s_red[grp][kl] = acc;
-        __syncthreads();
-        if (grp == 0 && kk < k) {
-            double s = 0.0;
-            for (int q = 0; q < ngrp; ++q) s += s_red[q][kl];
-            P.red1[(int64_t)g * r + kk] = s;
+    {
+        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+        for (int kk = warp; kk < k; kk += nw) {
+            const double* qk = P.Q + (int64_t)kk * len;
+            double acc = 0.0;
+            for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(qk[i], P.v[i], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
         }
-        __syncthreads();
     }
     if (!group_barrier(P.bar, 2u * G, P.status)) return;
 
     // P2: second Gram-Schmidt pass v -= Q (Q^T v); partial ||v||^2.
-    for (int kk = tid; kk < k; kk += nt) {
-        double s = 0.0;
-        for (int gg = 0; gg < G; ++gg) s += P.red1[(int64_t)gg * r + kk];
-        s_w[kk] = s;
+    {
+        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+        for (int kk = warp; kk < k; kk += nw) {
+            const double s = warp_sum_strided(P.red1 + kk, G, r);
+            if (lane == 0) s_w[kk] = s;
+        }
     }
     __syncthreads();
     double nv = 0.0;
     for (int64_t i = i0 + tid; i < i1; i += nt) {
-        const double* qi = P.Q + i * r;
         double s = 0.0;
-        for (int kk = 0; kk < k; ++kk) s = fma(qi[kk], s_w[kk], s);
+        for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
         const double vi = P.v[i] - s;
         P.v[i] = vi;
         nv = fma(vi, vi, nv);
@@ -316,10 +327,9 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     // passes), decides an early stop exactly as the explicit residual would:
     // ||v||^2 <= (max(m,n) eps)^2 ||A||_F^2 ends the selection before recording p.
     // Otherwise p is recorded and q_k = v / ||v||.
-    if (tid == 0) {
-        double s = 0.0;
-        for (int gg = 0; gg < G; ++gg) s += P.red2[gg];
-        s_tot = s;
+    if (tid < 32) {
+        const double s = warp_sum_strided(P.red2, G);
+        if (tid == 0) s_tot = s;
     }
     __syncthreads();
     const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
@@ -336,7 +346,7 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     const double inv = 1.0 / sqrt(s_tot);
     for (int64_t i = i0 + tid; i < i1; i += nt) {
         const double q = P.v[i] * inv;
-        P.Q[i * r + k] = q;
+        P.Q[(int64_t)k * len + i] = q;
         P.q64[i] = q;
         float hi, lo;
         split_d(q, hi, lo);

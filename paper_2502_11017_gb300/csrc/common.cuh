@@ -141,6 +141,32 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
+// Sum of x[0..n) by one warp: lane l adds x[l], x[l+32], ... in order, then a fixed
+// xor tree. Every lane returns the same value, identical in every CTA that calls it.
+__device__ __forceinline__ double warp_sum_strided(const double* x, int n, int64_t stride = 1) {
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int g = lane; g < n; g += 32) s += x[(int64_t)g * stride];
+    return warp_sum(s);
+}
+
+// Walks the flat index e = tid, tid + nt, ... of an nloc x r array as (row, column)
+// without a division per step.
+struct Walk2 {
+    int i, c, di, dc, r;
+    __device__ __forceinline__ Walk2(int e0, int step, int r_) : r(r_) {
+        i = e0 / r_;
+        c = e0 - i * r_;
+        di = step / r_;
+        dc = step - di * r_;
+    }
+    __device__ __forceinline__ void next() {
+        i += di;
+        c += dc;
+        if (c >= r) { c -= r; ++i; }
+    }
+};
+
 // ---------------------------------------------------------------- group barrier
 //
 // CTAs of one group (all co-resident: cooperative launch) meet here. `ctr` is a
@@ -176,6 +202,84 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
     const int ok = s_ok;
     __syncthreads();
     return ok != 0;
+}
+
+// ---------------------------------------------------------------- small dense inverse
+//
+// In-place Gauss-Jordan inverse of the r x r row-major matrix A (shared memory),
+// FP64, partial pivoting by rows (first maximum |a_ik|, i >= k). The k-th pivot is
+// the k-th pivot of LU with partial pivoting, so |pivot| <= thresh flags the same
+// numerical singularity and sum log|pivot| = log|det A|. Columns are unscrambled at
+// the end in the reverse order of the row interchanges. colk: r doubles, piv: r ints
+// of shared memory. Returns 1 if singular (A then holds no inverse).
+__device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
+                                          double thresh, double* logabsdet) {
+    __shared__ int s_p, s_sing;
+    __shared__ double s_d, s_lv;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) { s_sing = 0; s_lv = 0.0; }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (tid < 32) {
+            double bv = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < r; i += 32) {
+                const double x = fabs(A[i * r + k]);
+                if (x > bv) { bv = x; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+            }
+            if (tid == 0) s_p = bi;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < r; j += nt) {
+                const double t = A[k * r + j];
+                A[k * r + j] = A[p * r + j];
+                A[p * r + j] = t;
+            }
+        __syncthreads();
+        if (tid == 0) {
+            piv[k] = p;
+            const double d = A[k * r + k];
+            s_d = d;
+            if (!(fabs(d) > thresh)) s_sing = 1;
+            s_lv += log(fabs(d));
+        }
+        __syncthreads();
+        if (s_sing) return 1;
+        const double dinv = 1.0 / s_d;
+        for (int i = tid; i < r; i += nt) {
+            colk[i] = A[i * r + k];
+            if (i != k) A[i * r + k] = 0.0;
+        }
+        __syncthreads();
+        if (tid == 0) A[k * r + k] = 1.0;
+        __syncthreads();
+        for (int j = tid; j < r; j += nt) A[k * r + j] *= dinv;
+        __syncthreads();
+        for (int e = tid; e < r * r; e += nt) {
+            const int i = e / r, j = e - i * r;
+            if (i != k) A[e] = fma(-colk[i], A[k * r + j], A[e]);
+        }
+        __syncthreads();
+    }
+    for (int k = r - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k)
+            for (int i = tid; i < r; i += nt) {
+                const double t = A[i * r + k];
+                A[i * r + k] = A[i * r + p];
+                A[i * r + p] = t;
+            }
+        __syncthreads();
+    }
+    if (logabsdet) *logabsdet = s_lv;
+    return 0;
 }
 
 }  // namespace curk

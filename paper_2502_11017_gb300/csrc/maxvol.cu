@@ -5,19 +5,21 @@
 // every entry B_ij is the factor by which |det M| changes when row i of C
 // replaces position j of S. While max|B_ij| > 1 + delta the best swap is made
 // and B is updated by Sherman-Morrison, B <- B - B(:,j) (B(i,:) - e_j^T) / B_ij;
-// every r swaps, and before declaring convergence, M^-1 and B are recomputed.
+// every r swaps, and before convergence is declared, B is recomputed from M^-1.
 //
 // Work is organised as "problems" (a row block of C, a merge node, or all of C),
-// each handled by a group of CTAs:
-//   mv_start : Algorithm 3 (axis 0) on the problem's rows -> start set S
-//              (implicit Gram-Schmidt, one group barrier per pick)
-//   mv_lu    : one CTA per problem, FP64 LU with partial pivoting of C(S,:),
-//              inverse and log|det|
-//   mv_coef  : B = C M^-1 for all problems (the coefficient product)
-//   mv_swap  : the swap loop; each CTA keeps its slice of B in shared memory,
-//              the group agrees on the argmax through one barrier per swap
-// A host loop repeats lu -> coef -> swap until every problem has converged on a
-// freshly recomputed B.
+// each handled by a group of co-resident CTAs:
+//   mv_start  : Algorithm 3 (axis 0) on the problem's rows -> start set S
+//               (implicit Gram-Schmidt, one group barrier per pick)
+//   mv_lu     : one CTA per problem, FP64 Gauss-Jordan inverse of C(S,:) with
+//               partial pivoting, log|det|
+//   mv_engine : the whole swap iteration of a stage in one launch. Each CTA keeps
+//               its slice of B in shared memory (FP32 for FP32/BF16 data, FP64 for
+//               FP64 data) and the group agrees on argmax|B_ij| through one barrier
+//               per swap. The group's first CTA recomputes the winning row of B in
+//               FP64 and keeps M^-1 (FP64) current by the Sherman-Morrison update,
+//               so a refresh is B = C M^-1 from that FP64 inverse, with no new
+//               factorisation. A merge node starts from its left child's M^-1.
 
 #include <algorithm>
 #include <climits>
@@ -44,9 +46,7 @@ struct MvProb {
 
 struct MvArgs {
     const void* basis;  // rows x r (compute type), contiguous
-    void* B;            // rows x r (compute type)
-    void* minv;         // P x r x r (compute type)
-    double* minv64;     // P x r x r (FP64 inverse)
+    double* minv64;     // P x r x r: FP64 M^-1 of each problem
     const MvProb* prob;
     int P, r;
     double delta;
@@ -54,15 +54,13 @@ struct MvArgs {
     const int32_t* cta_prob;   // per CTA slot
     const int32_t* cta_part;
     int cta_base;              // first slot of this launch (waves)
-    const int32_t* tile_prob;  // coef tiles
-    const int32_t* tile_row0;
+    const int32_t* lu_mask;    // P: 1 = factorise C(S,:) in mv_lu
     int32_t* S;                // P x r local positions
     double* logvol;            // P
     int32_t* swaps;            // P
     int32_t* pstatus;          // P
     int32_t* done;             // P
     unsigned* bar;             // P
-    int* pending;              // 1
     double* keyv;              // slots x 2
     long long* keyi;           // slots x 2
     void* pub;                 // slots x 2 x r (compute type)
@@ -147,12 +145,49 @@ struct StartSmem {
         size_t b = (size_t)nloc * r * sizeof(TB);
         b = (b + 15) / 16 * 16 + (size_t)nloc * sizeof(double);
         b += (size_t)r * r * sizeof(double);        // Q
-        b += (size_t)4 * r * sizeof(double);        // v, s, scratch
+        b += (size_t)6 * r * sizeof(double);        // v, sd, partial sums (4 r)
         b += (size_t)2 * r * sizeof(float);         // qh, ql
         b += (size_t)nloc + 16;                     // mask
         return b;
     }
 };
+
+// nu[i] = sum_c rows(i,c) * q(c) (mode 1) or rows(i,c)^2 (mode 0), each row split over 4
+// consecutive lanes (Dot2 for FP32 data, FP64 for FP64 data), combined by shuffles.
+template <typename TB>
+__device__ __forceinline__ void rows_dot4(const TB* rows, int nloc, int r, const double* q64,
+                                          const float* qh, const float* ql, int mode,
+                                          double* out, bool downdate) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int it0 = 0; it0 < 4 * nloc; it0 += nt) {
+        const int it = it0 + tid;
+        const int row = it >> 2, qt = it & 3;
+        double v = 0.0;
+        if (row < nloc) {
+            const int c0 = r * qt / 4, c1 = r * (qt + 1) / 4;
+            const TB* x = rows + (size_t)row * r;
+            if (std::is_same<TB, double>::value) {
+                DotD d;
+                for (int c = c0; c < c1; ++c) {
+                    if (mode == 0) d.add_sq(to_d(x[c])); else d.add(to_d(x[c]), q64[c]);
+                }
+                v = d.value();
+            } else {
+                Dot2 d;
+                for (int c = c0; c < c1; ++c) {
+                    if (mode == 0) d.add_sq(to_f(x[c])); else d.add(to_f(x[c]), qh[c], ql[c]);
+                }
+                v = d.value();
+            }
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (row < nloc && qt == 0) {
+            if (downdate) out[row] -= v * v;
+            else out[row] = v;
+        }
+    }
+}
 
 template <typename TB>
 __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
@@ -169,34 +204,23 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     double* Q = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * r * sizeof(double);
     double* v = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * sizeof(double);
     double* sd = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * sizeof(double);
-    double* scr = reinterpret_cast<double*>(smem_raw + off); off += (size_t)2 * r * sizeof(double);
+    double* red = reinterpret_cast<double*>(smem_raw + off); off += (size_t)4 * r * sizeof(double);
     float* qh = reinterpret_cast<float*>(smem_raw + off); off += (size_t)r * sizeof(float);
     float* ql = reinterpret_cast<float*>(smem_raw + off); off += (size_t)r * sizeof(float);
     unsigned char* msk = smem_raw + off;
-    __shared__ double s_frob;
+    __shared__ double s_frob, s_inv;
     __shared__ int s_stop, s_p;
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     int32_t* Sout = a.S + (int64_t)pb * r;
 
     for (int e = tid; e < nloc * r; e += nt) rows[e] = basis[(int64_t)lo * r + e];
     for (int i = tid; i < nloc; i += nt) msk[i] = 0;
     __syncthreads();
-    // squared norms of the rows
+    rows_dot4<TB>(rows, nloc, r, v, qh, ql, 0, nu, false);
+    __syncthreads();
     double fs = 0.0;
-    for (int i = tid; i < nloc; i += nt) {
-        double s;
-        if (std::is_same<TB, double>::value) {
-            DotD d;
-            for (int c = 0; c < r; ++c) d.add_sq(to_d(rows[i * r + c]));
-            s = d.value();
-        } else {
-            Dot2 d;
-            for (int c = 0; c < r; ++c) d.add_sq(to_f(rows[i * r + c]));
-            s = d.value();
-        }
-        nu[i] = s;
-        fs += s;
-    }
+    for (int i = tid; i < nloc; i += nt) fs += nu[i];
     fs = block_sum(fs);
     int picked = 0;
     for (int k = 0; k < r; ++k) {
@@ -212,21 +236,23 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
             if (k == 0) a.aux[(pr.group0 + part) * 2] = fs;
         }
         if (!group_barrier(&a.bar[pb], (unsigned)(G * (k + 1)), a.status)) return;
-        if (tid == 0) {
+        if (warp == 0) {
             double pv = -INFINITY;
             long long pi = LLONG_MAX;
-            for (int g = 0; g < G; ++g) {
+            for (int g = lane; g < G; g += 32) {
                 const double kv = a.keyv[(pr.group0 + g) * 2 + par];
                 const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
                 if (better(kv, ki, pv, pi)) { pv = kv; pi = ki; }
             }
+            warp_argmax(pv, pi);
             if (k == 0) {
-                double f = 0.0;
-                for (int g = 0; g < G; ++g) f += a.aux[(pr.group0 + g) * 2];
-                s_frob = f;
+                const double f = warp_sum_strided(a.aux + (int64_t)pr.group0 * 2, G, 2);
+                if (lane == 0) s_frob = f;
             }
-            s_stop = (pi == LLONG_MAX) ? 1 : 0;
-            s_p = s_stop ? 0 : (int)pi;
+            if (lane == 0) {
+                s_stop = (pi == LLONG_MAX) ? 1 : 0;
+                s_p = s_stop ? 0 : (int)pi;
+            }
         }
         __syncthreads();
         if (s_stop) break;
@@ -237,27 +263,33 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
         for (int c = tid; c < r; c += nt) v[c] = to_d(cp[c]);
         __syncthreads();
         for (int pass = 0; pass < 2; ++pass) {
-            for (int kk = tid; kk < k; kk += nt) {
+            for (int kk = warp; kk < k; kk += nw) {
                 double s = 0.0;
-                for (int c = 0; c < r; ++c) s = fma(Q[kk * r + c], v[c], s);
-                sd[kk] = s;
+                for (int c = lane; c < r; c += 32) s = fma(Q[kk * r + c], v[c], s);
+                s = warp_sum(s);
+                if (lane == 0) sd[kk] = s;
             }
             __syncthreads();
-            for (int c = tid; c < r; c += nt) {
+            for (int it = tid; it < 4 * r; it += nt) {
+                const int c = it % r, qt = it / r;
                 double s = 0.0;
-                for (int kk = 0; kk < k; ++kk) s = fma(Q[kk * r + c], sd[kk], s);
-                scr[r + c] = v[c] - s;
+                for (int kk = k * qt / 4; kk < k * (qt + 1) / 4; ++kk) s = fma(Q[kk * r + c], sd[kk], s);
+                red[qt * r + c] = s;
             }
             __syncthreads();
-            for (int c = tid; c < r; c += nt) v[c] = scr[r + c];
+            for (int c = tid; c < r; c += nt)
+                v[c] -= ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
             __syncthreads();
         }
-        if (tid == 0) {
+        if (warp == 0) {
             double s = 0.0;
-            for (int c = 0; c < r; ++c) s = fma(v[c], v[c], s);
-            const double mx = (double)max(pr.p, r) * kEps;
-            s_stop = !(s > mx * mx * s_frob) ? 1 : 0;
-            scr[1] = 1.0 / sqrt(s);
+            for (int c = lane; c < r; c += 32) s = fma(v[c], v[c], s);
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double mx = (double)max(pr.p, r) * kEps;
+                s_stop = !(s > mx * mx * s_frob) ? 1 : 0;
+                s_inv = 1.0 / sqrt(s);
+            }
         }
         __syncthreads();
         if (s_stop) break;
@@ -266,25 +298,14 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
         picked = k + 1;
         if (k == r - 1) break;
         for (int c = tid; c < r; c += nt) {
-            const double q = v[c] * scr[1];
+            const double q = v[c] * s_inv;
             Q[k * r + c] = q;
+            v[c] = q;
             split_d(q, qh[c], ql[c]);
         }
         __syncthreads();
         // downdate: nu_i -= (c_i . q_k)^2
-        for (int i = tid; i < nloc; i += nt) {
-            double w;
-            if (std::is_same<TB, double>::value) {
-                DotD d;
-                for (int c = 0; c < r; ++c) d.add(to_d(rows[i * r + c]), Q[k * r + c]);
-                w = d.value();
-            } else {
-                Dot2 d;
-                for (int c = 0; c < r; ++c) d.add(to_f(rows[i * r + c]), qh[c], ql[c]);
-                w = d.value();
-            }
-            nu[i] -= w * w;
-        }
+        rows_dot4<TB>(rows, nloc, r, v, qh, ql, 1, nu, true);
         __syncthreads();
     }
     // pad a short selection with the lowest unselected local rows
@@ -298,19 +319,18 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     }
 }
 
-// ---------------------------------------------------------------- FP64 LU and inverse
+// ---------------------------------------------------------------- FP64 inverse of C(S,:)
 
 template <typename TB>
 __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pb = blockIdx.x;
-    if (a.done[pb]) return;
+    if (a.done[pb] || !a.lu_mask[pb]) return;
     const MvProb pr = a.prob[pb];
     const int r = a.r, tid = threadIdx.x, nt = blockDim.x;
-    double* M = reinterpret_cast<double*>(smem_raw);  // r x r
-    int* perm = reinterpret_cast<int*>(M + r * r);
-    double* X = a.minv64 + (int64_t)pb * r * r;       // r x r (inverse, one column per thread)
-    __shared__ int s_piv, s_sing;
+    double* M = reinterpret_cast<double*>(smem_raw);  // r x r, inverted in place
+    double* colk = M + r * r;
+    int* piv = reinterpret_cast<int*>(colk + r);
     __shared__ double s_max;
     const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
     const int32_t* S = a.S + (int64_t)pb * r;
@@ -325,7 +345,6 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
         M[e] = x;
         mx = fmax(mx, fabs(x));
     }
-    for (int k = tid; k < r; k += nt) perm[k] = k;
     bad = __syncthreads_or(bad);
     {
         __shared__ double sm[32];
@@ -336,7 +355,6 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
             double t = 0.0;
             for (int w = 0; w < (nt >> 5); ++w) t = fmax(t, sm[w]);
             s_max = t;
-            s_sing = 0;
         }
         __syncthreads();
     }
@@ -348,118 +366,49 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
         }
         return;
     }
-    const double thresh = (double)r * kEps * s_max;
-    for (int k = 0; k < r; ++k) {
-        if (tid < 32) {
-            double bv = -1.0;
-            int bi = k;
-            for (int i = k + tid; i < r; i += 32) {
-                const double x = fabs(M[i * r + k]);
-                if (x > bv) { bv = x; bi = i; }
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
-            }
-            if (tid == 0) s_piv = bi;
-        }
-        __syncthreads();
-        const int pv = s_piv;
-        if (pv != k) {
-            for (int c = tid; c < r; c += nt) {
-                const double t = M[k * r + c];
-                M[k * r + c] = M[pv * r + c];
-                M[pv * r + c] = t;
-            }
-            if (tid == 0) { const int t = perm[k]; perm[k] = perm[pv]; perm[pv] = t; }
-        }
-        __syncthreads();
-        const double d = M[k * r + k];
-        if (!(fabs(d) > thresh)) {
-            if (tid == 0) s_sing = 1;
-        }
-        if (d != 0.0) {
-            for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] /= d;
-            __syncthreads();
-            const int w = r - k - 1;
-            for (int e = tid; e < w * w; e += nt) {
-                const int i = k + 1 + e / w, j = k + 1 + e % w;
-                M[i * r + j] -= M[i * r + k] * M[k * r + j];
-            }
-        }
-        __syncthreads();
-    }
-    if (s_sing) {
+    double lv = 0.0;
+    const int sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
+    if (sing) {
         if (tid == 0) { a.pstatus[pb] = CUR_ERR_SINGULAR; a.done[pb] = 1; }
         return;
     }
-    if (tid == 0) {
-        double lv = 0.0;
-        for (int k = 0; k < r; ++k) lv += log(fabs(M[k * r + k]));
-        a.logvol[pb] = lv;
-    }
-    // inverse: column c solves L y = P e_c, U x = y
-    for (int c = tid; c < r; c += nt) {
-        for (int i = 0; i < r; ++i) {
-            double s = (perm[i] == c) ? 1.0 : 0.0;
-            for (int j = 0; j < i; ++j) s -= M[i * r + j] * X[j * r + c];
-            X[i * r + c] = s;
-        }
-        for (int i = r - 1; i >= 0; --i) {
-            double s = X[i * r + c];
-            for (int j = i + 1; j < r; ++j) s -= M[i * r + j] * X[j * r + c];
-            X[i * r + c] = s / M[i * r + i];
-        }
-    }
-    __syncthreads();
-    TB* out = static_cast<TB*>(a.minv) + (int64_t)pb * r * r;
-    for (int e = tid; e < r * r; e += nt) out[e] = (TB)X[e];
+    if (tid == 0) a.logvol[pb] = lv;
+    double* out64 = a.minv64 + (int64_t)pb * r * r;
+    for (int e = tid; e < r * r; e += nt) out64[e] = M[e];
 }
 
-// ---------------------------------------------------------------- coefficients B = C M^-1
+// ---------------------------------------------------------------- the swap iteration
 
 template <typename TB>
-__global__ void __launch_bounds__(256) mv_coef(MvArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int pb = a.tile_prob[blockIdx.x];
-    if (a.done[pb]) return;
-    const MvProb pr = a.prob[pb];
-    const int r = a.r, tid = threadIdx.x, nt = blockDim.x;
-    const int row0 = a.tile_row0[blockIdx.x];
-    const int nrow = min(64, pr.p - row0);
-    TB* Mi = reinterpret_cast<TB*>(smem_raw);  // r x r
-    TB* Ct = Mi + r * r;                       // 64 x r
-    const TB* src = static_cast<const TB*>(a.minv) + (int64_t)pb * r * r;
-    for (int e = tid; e < r * r; e += nt) Mi[e] = src[e];
-    const TB* basis = static_cast<const TB*>(a.basis) + (pr.base + row0) * r;
-    for (int e = tid; e < nrow * r; e += nt) Ct[e] = basis[e];
-    __syncthreads();
-    TB* B = static_cast<TB*>(a.B) + (pr.base + row0) * r;
-    for (int e = tid; e < nrow * r; e += nt) {
-        const int i = e / r, c = e - i * r;
-        TB s = (TB)0;
-        for (int k = 0; k < r; ++k) s = fma(Ct[i * r + k], Mi[k * r + c], s);
-        B[e] = s;
+struct EngineSmem {
+    static size_t bytes(int nloc, int r) {
+        size_t b = ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
+        b = (b + 15) / 16 * 16 + (size_t)7 * r * sizeof(double) + 64;
+        return b;
     }
-}
+};
 
-// ---------------------------------------------------------------- swap loop
-
+// Local argmax of |B| over the slice in the compute type; ties to the lowest index.
 template <typename TB>
-__device__ __forceinline__ void scan_slice(const TB* Bs, int nloc, int r, int lo, double& bv,
-                                           long long& bi, int& nan) {
-    for (int e = threadIdx.x; e < nloc * r; e += blockDim.x) {
-        const double x = fabs(to_d(Bs[e]));
-        if (!(x <= INFINITY)) nan = 1;
-        const int i = e / r, c = e - i * r;
-        const long long idx = (long long)(lo + i) * r + c;
-        if (better(x, idx, bv, bi)) { bv = x; bi = idx; }
+__device__ __forceinline__ void engine_scan(const TB* Bs, int nloc, int r, int lo, double& bv,
+                                            long long& bi, int& nan) {
+    TB v = (TB)-1;
+    int idx = INT_MAX;
+    int bad = 0;
+    Walk2 w(threadIdx.x, blockDim.x, r);
+    for (int e = threadIdx.x; e < nloc * r; e += blockDim.x, w.next()) {
+        const TB x = fabs(Bs[e]);
+        if (!(x <= (TB)INFINITY)) bad = 1;
+        const int id = (lo + w.i) * r + w.c;
+        if (x > v || (x == v && id < idx)) { v = x; idx = id; }
     }
+    bv = idx == INT_MAX ? -INFINITY : (double)v;
+    bi = idx == INT_MAX ? LLONG_MAX : (long long)idx;
+    nan = bad;
 }
 
 template <typename TB>
-__global__ void __launch_bounds__(256) mv_swap(MvArgs a) {
+__global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
@@ -467,25 +416,31 @@ __global__ void __launch_bounds__(256) mv_swap(MvArgs a) {
     const MvProb pr = a.prob[pb];
     const int r = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
-    TB* Bs = reinterpret_cast<TB*>(smem_raw);
-    TB* colj = Bs + (size_t)nloc * r;
-    TB* wrow = colj + nloc;
+    TB* Bs = reinterpret_cast<TB*>(smem_raw);   // nloc x r slice of B
+    TB* Mi = Bs + (size_t)nloc * r;             // r x r: M^-1 in the compute type
+    TB* colj = Mi + (size_t)r * r;              // nloc
+    TB* wrow = colj + nloc;                     // r: winning row of B, then B(i,:) - e_j
+    size_t off = (((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB) + 15) / 16 * 16;
+    double* crow = reinterpret_cast<double*>(smem_raw + off);   // r: C(i*,:)
+    double* b64 = crow + r;                                     // r: FP64 row of B
+    double* cj64 = b64 + r;                                     // r: column j* of M^-1
+    double* red = cj64 + r;                                     // 4 r
     __shared__ double s_b;
     __shared__ long long s_w;
-    __shared__ int s_state, s_nan;
+    __shared__ int s_nan;
+    __shared__ double s_lv;
     TB* pub = static_cast<TB*>(a.pub);
-    const TB* Bg = static_cast<const TB*>(a.B) + (pr.base + lo) * r;
-    for (int e = tid; e < nloc * r; e += nt) Bs[e] = Bg[e];
-    __syncthreads();
-
-    double bv = -INFINITY;
-    long long bi = LLONG_MAX;
-    int nan = 0;
-    scan_slice(Bs, nloc, r, lo, bv, bi, nan);
-    nan = __syncthreads_or(nan);
-    block_argmax(bv, bi);
-    int par = 0;
+    const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
+    double* Minv = a.minv64 + (int64_t)pb * r * r;
     const int myslot = pr.group0 + part;
+    if (tid == 0) s_lv = a.logvol[pb];
+
+    double bv;
+    long long bi;
+    int nan;
+    int par = 0, total = a.swaps[pb];
+    unsigned epoch = 0;
+    int fin = 0, fstat = CUR_OK;
     auto publish = [&](int pp) {
         if (tid == 0) {
             a.keyv[myslot * 2 + pp] = bv;
@@ -496,83 +451,139 @@ __global__ void __launch_bounds__(256) mv_swap(MvArgs a) {
             for (int c = tid; c < r; c += nt) pub[((int64_t)myslot * 2 + pp) * r + c] = Bs[il * r + c];
         }
     };
-    publish(par);
-
-    int made = 0, total = a.swaps[pb];
-    double lv_inc = 0.0;
-    unsigned epoch = 0;
-    int fin = 0;  // 0 running, 1 converged, 2 refresh, 3 error
-    int fstat = CUR_OK;
     while (true) {
-        ++epoch;
-        if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
-        if (tid == 0) {
-            double wv = -INFINITY;
-            long long wi = LLONG_MAX;
-            int anynan = 0;
-            for (int g = 0; g < G; ++g) {
-                const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
-                const double kv = a.keyv[(pr.group0 + g) * 2 + par];
-                if (ki == -2LL) anynan = 1;
-                else if (better(kv, ki, wv, wi)) { wv = kv; wi = ki; }
+        // refresh: B slice = C slice M^-1
+        for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)Minv[e];
+        __syncthreads();
+        {
+            const TB* Cs = basis + (int64_t)lo * r;
+            Walk2 w(tid, nt, r);
+            for (int e = tid; e < nloc * r; e += nt, w.next()) {
+                const TB* ci = Cs + (int64_t)w.i * r;
+                TB s = (TB)0;
+                for (int k = 0; k < r; ++k) s = fma(ci[k], Mi[k * r + w.c], s);
+                Bs[e] = s;
             }
-            s_nan = anynan;
-            s_w = wi;
-            s_b = wv;
         }
         __syncthreads();
-        if (s_nan) { fin = 3; fstat = CUR_ERR_NONFINITE; break; }
-        const long long wi = s_w;
-        const double wv = s_b;
-        if (wi == LLONG_MAX || !(wv > 1.0 + a.delta)) { fin = made == 0 ? 1 : 2; break; }
-        if (total >= a.max_swaps) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
-        const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
-        const int owner = istar / pr.rpc;
-        const TB* wsrc = pub + ((int64_t)(pr.group0 + owner) * 2 + par) * r;
-        for (int c = tid; c < r; c += nt) wrow[c] = wsrc[c];
-        for (int i = tid; i < nloc; i += nt) colj[i] = Bs[i * r + jstar];
-        __syncthreads();
-        const TB b = wrow[jstar];
-        if (part == 0 && tid == 0) {
-            a.S[(int64_t)pb * r + jstar] = istar;
-            lv_inc += log(fabs(to_d(b)));
-        }
-        __syncthreads();
-        if (tid == 0) wrow[jstar] = wrow[jstar] - (TB)1;
-        __syncthreads();
-        ++made;
-        ++total;
-        // B <- B - B(:,j) (B(i,:) - e_j^T) / B_ij, fused with the next local argmax
-        bv = -INFINITY;
-        bi = LLONG_MAX;
-        nan = 0;
-        for (int e = tid; e < nloc * r; e += nt) {
-            const int i = e / r, c = e - i * r;
-            const TB f = colj[i] / b;
-            const TB x = fma(-f, wrow[c], Bs[e]);
-            Bs[e] = x;
-            const double ax = fabs(to_d(x));
-            if (!(ax <= INFINITY)) nan = 1;
-            const long long idx = (long long)(lo + i) * r + c;
-            if (better(ax, idx, bv, bi)) { bv = ax; bi = idx; }
-        }
+        engine_scan(Bs, nloc, r, lo, bv, bi, nan);
         nan = __syncthreads_or(nan);
         block_argmax(bv, bi);
-        par ^= 1;
         publish(par);
-        if (made == r) { fin = 2; break; }
+        int made = 0;
+        while (true) {
+            ++epoch;
+            if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+            if (tid < 32) {
+                double wv = -INFINITY;
+                long long wi = LLONG_MAX;
+                int anynan = 0;
+                for (int g = tid; g < G; g += 32) {
+                    const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
+                    const double kv = a.keyv[(pr.group0 + g) * 2 + par];
+                    if (ki == -2LL) anynan = 1;
+                    else if (better(kv, ki, wv, wi)) { wv = kv; wi = ki; }
+                }
+                anynan = __any_sync(0xffffffffu, anynan);
+                warp_argmax(wv, wi);
+                if (tid == 0) {
+                    s_nan = anynan;
+                    s_w = wi;
+                    s_b = wv;
+                }
+            }
+            __syncthreads();
+            if (s_nan) { fin = 3; fstat = CUR_ERR_NONFINITE; break; }
+            const long long wi = s_w;
+            const double wv = s_b;
+            if (wi == LLONG_MAX || !(wv > 1.0 + a.delta)) { fin = made == 0 ? 1 : 2; break; }
+            if (total >= a.max_swaps) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
+            const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
+            const int owner = istar / pr.rpc;
+            const TB* wsrc = pub + ((int64_t)(pr.group0 + owner) * 2 + par) * r;
+            for (int c = tid; c < r; c += nt) wrow[c] = wsrc[c];
+            if (part == 0)
+                for (int c = tid; c < r; c += nt) crow[c] = to_d(basis[(int64_t)istar * r + c]);
+            __syncthreads();
+            const TB b = wrow[jstar];
+            for (int i = tid; i < nloc; i += nt) colj[i] = Bs[i * r + jstar] / b;
+            if (part == 0) {
+                // FP64 row of B: b64 = C(i*,:) M^-1, four partial sums per column in fixed order
+                for (int it = tid; it < 4 * r; it += nt) {
+                    const int c = it % r, qt = it / r;
+                    double s = 0.0;
+                    for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k) s = fma(crow[k], Minv[k * r + c], s);
+                    red[qt * r + c] = s;
+                }
+                for (int k = tid; k < r; k += nt) cj64[k] = Minv[k * r + jstar];
+                __syncthreads();
+                for (int c = tid; c < r; c += nt)
+                    b64[c] = ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
+                __syncthreads();
+                const double bb = b64[jstar];
+                // M^-1 <- M^-1 - M^-1(:,j) (B(i,:) - e_j^T) / B_ij
+                for (int e = tid; e < r * r; e += nt) {
+                    const int k = e / r, c = e - k * r;
+                    const double w = b64[c] - (c == jstar ? 1.0 : 0.0);
+                    Minv[e] -= cj64[k] * w / bb;
+                }
+                if (tid == 0) {
+                    a.S[(int64_t)pb * r + jstar] = istar;
+                    s_lv += log(fabs(bb));
+                }
+            }
+            if (tid == 0) wrow[jstar] = wrow[jstar] - (TB)1;
+            __syncthreads();
+            ++made;
+            ++total;
+            // B <- B - (B(:,j) / B_ij) (B(i,:) - e_j^T), fused with the next local argmax
+            {
+                TB v = (TB)-1;
+                int idx = INT_MAX, bad = 0;
+                Walk2 w(tid, nt, r);
+                for (int e = tid; e < nloc * r; e += nt, w.next()) {
+                    const TB x = fma(-colj[w.i], wrow[w.c], Bs[e]);
+                    Bs[e] = x;
+                    const TB ax = fabs(x);
+                    if (!(ax <= (TB)INFINITY)) bad = 1;
+                    const int id = (lo + w.i) * r + w.c;
+                    if (ax > v || (ax == v && id < idx)) { v = ax; idx = id; }
+                }
+                bv = idx == INT_MAX ? -INFINITY : (double)v;
+                bi = idx == INT_MAX ? LLONG_MAX : (long long)idx;
+                nan = bad;
+            }
+            nan = __syncthreads_or(nan);
+            block_argmax(bv, bi);
+            par ^= 1;
+            publish(par);
+            if (made == r) { fin = 2; break; }
+        }
+        if (fin != 2) break;
+        // every CTA refreshes from the M^-1 that the first CTA has finished updating
+        ++epoch;
+        if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+        fin = 0;
     }
     if (part == 0 && tid == 0) {
         a.swaps[pb] = total;
-        a.logvol[pb] += lv_inc;
-        if (fin == 1) { a.done[pb] = 1; a.pstatus[pb] = CUR_OK; }
-        else if (fin == 3) {
-            a.done[pb] = 1;
-            a.pstatus[pb] = fstat;
-            if (fstat != CUR_ERR_NOCONV) set_status(a.status, fstat);
-        } else {
-            atomicAdd(a.pending, 1);
-        }
+        a.logvol[pb] = s_lv;
+        a.done[pb] = 1;
+        a.pstatus[pb] = fin == 1 ? CUR_OK : fstat;
+        if (fin == 3 && fstat != CUR_ERR_NOCONV) set_status(a.status, fstat);
+    }
+}
+
+// Node t of a merge level starts from its left child's M^-1 (same rows, same order).
+__global__ void mv_inherit(const double* child_minv, const double* child_lv, const int32_t* valid,
+                           int P, int r, double* minv, double* lv) {
+    const int64_t rr = (int64_t)r * r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)P * rr;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e / rr);
+        if (!valid[t]) continue;
+        minv[e] = child_minv[2 * (int64_t)t * rr + (e - t * rr)];
+        if (e - t * rr == 0) lv[t] = child_lv[2 * t];
     }
 }
 
@@ -617,9 +628,6 @@ __global__ void pad_indices_k(int32_t* idx, const int32_t* count, int r, int64_t
 
 // ---------------------------------------------------------------- host side
 
-template <typename TB>
-static size_t swap_smem(int nloc, int r) { return ((size_t)nloc * r + nloc + r) * sizeof(TB) + 64; }
-
 static const size_t kSmemBudget = 200 * 1024;
 
 template <typename TB>
@@ -627,7 +635,7 @@ static int rows_cap(int r) {
     int lo = 1, hi = 1 << 20;
     while (lo < hi) {
         const int mid = (lo + hi + 1) / 2;
-        if (swap_smem<TB>(mid, r) <= kSmemBudget && StartSmem<TB>::bytes(mid, r) <= kSmemBudget) lo = mid;
+        if (EngineSmem<TB>::bytes(mid, r) <= kSmemBudget && StartSmem<TB>::bytes(mid, r) <= kSmemBudget) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -639,31 +647,38 @@ static cur_status set_smem_attr(K* fn, size_t bytes) {
     return CUR_OK;
 }
 
-struct Stage {
-    std::vector<MvProb> probs;  // base, gid_base, gid_arr, p filled by the caller
-};
+static inline unsigned nblk(int64_t n, int t = 256) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
+}
 
-// Runs maxvol on every problem of the stage. S (device, P x r local positions) holds
-// the start unless aca_start. skip (host, may be empty) marks problems to leave alone.
-// Per-problem results stay in the arrays of `out`.
-struct StageOut {
-    int32_t* S;
-    double* logvol;
-    int32_t* swaps;
-    int32_t* pstatus;
-    int32_t* done;
-    MvProb* dprob;
-    int P;
+// One stage: a set of problems on one basis buffer. The caller fills probs (base,
+// gid_base, gid_arr, p); stage_setup plans the CTA groups and allocates per-problem
+// state; stage_run runs the optional Algorithm 3 start, the FP64 inverse where
+// lu_mask is set, and the engine.
+template <typename TB>
+struct Stage {
+    std::vector<MvProb> probs;
+    int P = 0, slots = 0, max_rpc = 1;
+    MvProb* dprob = nullptr;
+    int32_t* dtab = nullptr;   // cta_prob | cta_part | lu_mask
+    int32_t* S = nullptr;      // P x r
+    double* minv64 = nullptr;  // P x r x r
+    double* logvol = nullptr;
+    int32_t* swaps = nullptr;
+    int32_t* pstatus = nullptr;
+    int32_t* done = nullptr;
+    unsigned* bar = nullptr;
+    double* keyv = nullptr;
+    long long* keyi = nullptr;
+    TB* pub = nullptr;
+    double* aux = nullptr;
+    std::vector<int> stat, sw;  // host copies after read()
 };
 
 template <typename TB>
-static cur_status run_stage(cur_handle* h, const TB* basis, int64_t total_rows, int r,
-                            const cur_opts* o, Stage& sg, bool aca_start,
-                            const std::vector<int>& skip, int32_t* S, StageOut* so, Arena& ar,
-                            cudaStream_t st, bool lu_only = false) {
+static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     const int P = (int)sg.probs.size();
-    if (P == 0) return CUR_OK;
-    // group sizes
+    sg.P = P;
     const int cap = rows_cap<TB>(r);
     int64_t tot_p = 0;
     for (auto& pr : sg.probs) tot_p += pr.p;
@@ -673,98 +688,98 @@ static cur_status run_stage(cur_handle* h, const TB* basis, int64_t total_rows, 
         const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
                                                  (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
         G = std::max<int64_t>(G, std::max<int64_t>(1, spread));
-        int rpc = (int)((pr.p + G - 1) / G);
+        const int rpc = (int)((pr.p + G - 1) / G);
         G = (pr.p + rpc - 1) / rpc;
         pr.G = (int)G;
         pr.rpc = rpc;
         pr.group0 = slots;
         slots += (int)G;
+        sg.max_rpc = std::max(sg.max_rpc, rpc);
     }
-    int max_rpc = 1;
-    for (auto& pr : sg.probs) max_rpc = std::max(max_rpc, pr.rpc);
-    std::vector<int32_t> cta_prob(slots), cta_part(slots);
-    for (int pb = 0; pb < P; ++pb)
-        for (int g = 0; g < sg.probs[pb].G; ++g) {
-            cta_prob[sg.probs[pb].group0 + g] = pb;
-            cta_part[sg.probs[pb].group0 + g] = g;
-        }
-    std::vector<int32_t> tile_prob, tile_row0;
-    for (int pb = 0; pb < P; ++pb)
-        for (int row0 = 0; row0 < sg.probs[pb].p; row0 += 64) {
-            tile_prob.push_back(pb);
-            tile_row0.push_back(row0);
-        }
-    const int ntiles = (int)tile_prob.size();
-
-    MvArgs a{};
-    a.basis = basis;
-    a.B = ar.get<TB>((size_t)total_rows * r);
-    a.minv = ar.get<TB>((size_t)P * r * r);
-    a.minv64 = ar.get<double>((size_t)P * r * r);
-    MvProb* dprob = ar.get<MvProb>(P);
-    int32_t* d_tables = ar.get<int32_t>((size_t)2 * slots + 2 * ntiles);
-    a.prob = dprob;
-    a.P = P;
-    a.r = r;
-    a.delta = o->delta;
-    a.max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
-    a.cta_prob = d_tables;
-    a.cta_part = d_tables + slots;
-    a.tile_prob = d_tables + 2 * slots;
-    a.tile_row0 = d_tables + 2 * slots + ntiles;
-    a.S = S;
-    a.logvol = ar.get<double>(P);
-    a.swaps = ar.get<int32_t>(P);
-    a.pstatus = ar.get<int32_t>(P);
-    a.done = ar.get<int32_t>(P);
-    a.bar = ar.get<unsigned>(P);
-    a.pending = ar.get<int>(1);
-    a.keyv = ar.get<double>((size_t)2 * slots);
-    a.keyi = ar.get<long long>((size_t)2 * slots);
-    a.pub = ar.get<TB>((size_t)2 * slots * r);
-    a.aux = ar.get<double>((size_t)2 * slots);
-    a.status = h->status;
+    sg.slots = slots;
+    sg.dprob = ar.get<MvProb>(P);
+    sg.dtab = ar.get<int32_t>((size_t)2 * slots + P);
+    sg.S = ar.get<int32_t>((size_t)P * r);
+    sg.minv64 = ar.get<double>((size_t)P * r * r);
+    sg.logvol = ar.get<double>(P);
+    sg.swaps = ar.get<int32_t>(P);
+    sg.pstatus = ar.get<int32_t>(P);
+    sg.done = ar.get<int32_t>(P);
+    sg.bar = ar.get<unsigned>(P);
+    sg.keyv = ar.get<double>((size_t)2 * slots);
+    sg.keyi = ar.get<long long>((size_t)2 * slots);
+    sg.pub = ar.get<TB>((size_t)2 * slots * r);
+    sg.aux = ar.get<double>((size_t)2 * slots);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    return CUR_OK;
+}
 
-    // upload descriptors and tables through the pinned staging buffer
-    const size_t need = sizeof(MvProb) * P + sizeof(int32_t) * (2 * slots + 2 * ntiles) +
-                        sizeof(int32_t) * P + 64;
+// lu_mask / skip: host vectors of length P (empty = all 1 / all 0).
+template <typename TB>
+static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opts* o, Stage<TB>& sg,
+                            bool aca_start, const std::vector<int>& lu_mask,
+                            const std::vector<int>& skip, cudaStream_t st) {
+    const int P = sg.P, slots = sg.slots;
+    const size_t tab_bytes = sizeof(int32_t) * (2 * (size_t)slots + P);
+    const size_t need = sizeof(MvProb) * P + tab_bytes + sizeof(int32_t) * P + 64;
     if (need > h->host_stage_bytes) return CUR_ERR_NOMEM;
     CUR_CK(cudaStreamSynchronize(st));  // the staging buffer may still feed an earlier copy
     char* hs = h->host_stage;
     std::memcpy(hs, sg.probs.data(), sizeof(MvProb) * P);
     int32_t* ht = reinterpret_cast<int32_t*>(hs + sizeof(MvProb) * P);
-    std::memcpy(ht, cta_prob.data(), sizeof(int32_t) * slots);
-    std::memcpy(ht + slots, cta_part.data(), sizeof(int32_t) * slots);
-    std::memcpy(ht + 2 * slots, tile_prob.data(), sizeof(int32_t) * ntiles);
-    std::memcpy(ht + 2 * slots + ntiles, tile_row0.data(), sizeof(int32_t) * ntiles);
-    int32_t* hdone = ht + 2 * slots + 2 * ntiles;
+    for (int pb = 0; pb < P; ++pb)
+        for (int g = 0; g < sg.probs[pb].G; ++g) {
+            ht[sg.probs[pb].group0 + g] = pb;
+            ht[slots + sg.probs[pb].group0 + g] = g;
+        }
+    for (int pb = 0; pb < P; ++pb) ht[2 * slots + pb] = lu_mask.empty() ? 1 : lu_mask[pb];
+    int32_t* hdone = ht + 2 * slots + P;
     for (int pb = 0; pb < P; ++pb) hdone[pb] = (!skip.empty() && skip[pb]) ? 1 : 0;
-    CUR_CK(cudaMemcpyAsync(dprob, hs, sizeof(MvProb) * P, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaMemcpyAsync(d_tables, ht, sizeof(int32_t) * (2 * slots + 2 * ntiles),
-                           cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaMemcpyAsync(a.done, hdone, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaMemsetAsync(a.swaps, 0, sizeof(int32_t) * P, st));
-    CUR_CK(cudaMemsetAsync(a.pstatus, 0, sizeof(int32_t) * P, st));
-    CUR_CK(cudaMemsetAsync(a.logvol, 0, sizeof(double) * P, st));
+    CUR_CK(cudaMemcpyAsync(sg.dprob, hs, sizeof(MvProb) * P, cudaMemcpyHostToDevice, st));
+    CUR_CK(cudaMemcpyAsync(sg.dtab, ht, tab_bytes, cudaMemcpyHostToDevice, st));
+    CUR_CK(cudaMemcpyAsync(sg.done, hdone, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+    CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
+    CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
 
-    // kernel attributes and co-residency per launch wave
-    const size_t sm_swap = swap_smem<TB>(max_rpc, r);
-    const size_t sm_start = StartSmem<TB>::bytes(max_rpc, r);
-    const size_t sm_lu = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(int) + 64;
-    const size_t sm_coef = ((size_t)r * r + 64 * (size_t)r) * sizeof(TB) + 64;
-    CUR_TRY(set_smem_attr(mv_swap<TB>, sm_swap));
+    MvArgs a{};
+    a.basis = basis;
+    a.minv64 = sg.minv64;
+    a.prob = sg.dprob;
+    a.P = P;
+    a.r = r;
+    a.delta = o->delta;
+    a.max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
+    a.cta_prob = sg.dtab;
+    a.cta_part = sg.dtab + slots;
+    a.lu_mask = sg.dtab + 2 * slots;
+    a.S = sg.S;
+    a.logvol = sg.logvol;
+    a.swaps = sg.swaps;
+    a.pstatus = sg.pstatus;
+    a.done = sg.done;
+    a.bar = sg.bar;
+    a.keyv = sg.keyv;
+    a.keyi = sg.keyi;
+    a.pub = sg.pub;
+    a.aux = sg.aux;
+    a.status = h->status;
+
+    const size_t sm_eng = EngineSmem<TB>::bytes(sg.max_rpc, r);
+    const size_t sm_start = StartSmem<TB>::bytes(sg.max_rpc, r);
+    const size_t sm_lu = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
+    CUR_TRY(set_smem_attr(mv_engine<TB>, sm_eng));
     CUR_TRY(set_smem_attr(mv_start<TB>, sm_start));
     CUR_TRY(set_smem_attr(mv_lu<TB>, sm_lu));
-    CUR_TRY(set_smem_attr(mv_coef<TB>, sm_coef));
-    int occ_swap = 0, occ_start = 0;
-    CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_swap, mv_swap<TB>, 256, sm_swap));
+    int occ_eng = 0, occ_start = 0;
+    CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_eng, mv_engine<TB>, 256, sm_eng));
     CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_start, mv_start<TB>, 256, sm_start));
-    const int cap_swap = std::max(1, occ_swap) * h->num_sms;
+    const int cap_eng = std::max(1, occ_eng) * h->num_sms;
     const int cap_start = std::max(1, occ_start) * h->num_sms;
-    // waves: consecutive whole groups within the capacity
+    for (auto& pr : sg.probs)
+        if (pr.G > cap_eng || pr.G > cap_start) return CUR_ERR_ARG;
+    // waves: consecutive whole groups within the co-residency capacity
     auto waves = [&](int capc) {
-        std::vector<std::pair<int, int>> w;  // (first slot, count)
+        std::vector<std::pair<int, int>> w;
         int first = 0, cnt = 0;
         for (int pb = 0; pb < P; ++pb) {
             const int G = sg.probs[pb].G;
@@ -774,11 +789,8 @@ static cur_status run_stage(cur_handle* h, const TB* basis, int64_t total_rows, 
         if (cnt > 0) w.push_back({first, cnt});
         return w;
     };
-    for (auto& pr : sg.probs)
-        if (pr.G > cap_swap || pr.G > cap_start) return CUR_ERR_ARG;
-
     if (aca_start) {
-        CUR_CK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * P, st));
+        CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
         for (auto& w : waves(cap_start)) {
             MvArgs aw = a;
             aw.cta_base = w.first;
@@ -787,169 +799,162 @@ static cur_status run_stage(cur_handle* h, const TB* basis, int64_t total_rows, 
             note_launch();
         }
     }
-    const int max_cycles = a.max_swaps / r + 4;
-    int* hpend = reinterpret_cast<int*>(hs + need - 32);
-    for (int cyc = 0; cyc < max_cycles; ++cyc) {
-        mv_lu<TB><<<P, 256, sm_lu, st>>>(a);
-        CUR_CK(cudaGetLastError());
+    mv_lu<TB><<<P, 256, sm_lu, st>>>(a);
+    CUR_CK(cudaGetLastError());
     note_launch();
-        if (lu_only) break;
-        mv_coef<TB><<<ntiles, 256, sm_coef, st>>>(a);
-        CUR_CK(cudaGetLastError());
-    note_launch();
-        CUR_CK(cudaMemsetAsync(a.bar, 0, sizeof(unsigned) * P, st));
-        CUR_CK(cudaMemsetAsync(a.pending, 0, sizeof(int), st));
-        for (auto& w : waves(cap_swap)) {
-            MvArgs aw = a;
-            aw.cta_base = w.first;
-            void* args[] = {&aw};
-            CUR_TRY(launch_coop((const void*)mv_swap<TB>, dim3(w.second), dim3(256), args, sm_swap, st));
-            note_launch();
-        }
-        CUR_CK(cudaMemcpyAsync(hpend, a.pending, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CUR_CK(cudaStreamSynchronize(st));
-        if (*hpend == 0) break;
+    CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
+    for (auto& w : waves(cap_eng)) {
+        MvArgs aw = a;
+        aw.cta_base = w.first;
+        void* args[] = {&aw};
+        CUR_TRY(launch_coop((const void*)mv_engine<TB>, dim3(w.second), dim3(256), args, sm_eng, st));
+        note_launch();
     }
-    so->S = S;
-    so->logvol = a.logvol;
-    so->swaps = a.swaps;
-    so->pstatus = a.pstatus;
-    so->done = a.done;
-    so->dprob = dprob;
-    so->P = P;
     return CUR_OK;
 }
 
-// Reads per-problem statuses and swap counts to the host (stream synchronised).
-static cur_status read_stage(cur_handle* h, const StageOut& so, std::vector<int>& stat,
-                             std::vector<int>& sw, cudaStream_t st) {
-    const int P = so.P;
+// Per-problem statuses and swap counts to the host (synchronises the stream).
+template <typename TB>
+static cur_status stage_read(cur_handle* h, Stage<TB>& sg, cudaStream_t st) {
+    const int P = sg.P;
     if ((size_t)P * 8 + 64 > h->host_stage_bytes) return CUR_ERR_NOMEM;
     int32_t* hs = reinterpret_cast<int32_t*>(h->host_stage);
-    CUR_CK(cudaMemcpyAsync(hs, so.pstatus, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
-    CUR_CK(cudaMemcpyAsync(hs + P, so.swaps, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
+    CUR_CK(cudaMemcpyAsync(hs, sg.pstatus, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
+    CUR_CK(cudaMemcpyAsync(hs + P, sg.swaps, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
     CUR_CK(cudaStreamSynchronize(st));
-    stat.assign(hs, hs + P);
-    sw.assign(hs + P, hs + 2 * P);
+    sg.stat.assign(hs, hs + P);
+    sg.sw.assign(hs + P, hs + 2 * P);
     return CUR_OK;
 }
 
-static inline unsigned nblk(int64_t n, int t = 256) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
-}
-
+// One merge level on `basis` (p x r): sets in cand (nsets x r, global rows). in_minv /
+// in_lv give, per input set, the device address of its M^-1 (rows in set order) and
+// log|det| when known (null otherwise); node t then starts from its left set's M^-1
+// instead of a new factorisation. out_minv / out_lv describe the output sets.
 template <typename TB>
 static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r,
                                 const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
-                                int* swaps, Arena& ar, cudaStream_t st) {
+                                int* swaps, const std::vector<const double*>& in_minv,
+                                const std::vector<const double*>& in_lv, Stage<TB>& lv,
+                                std::vector<const double*>& out_minv,
+                                std::vector<const double*>& out_lv, Arena& ar, cudaStream_t st) {
     const int npairs = nsets / 2;
     *swaps = 0;
+    out_minv.clear();
+    out_lv.clear();
     if (npairs == 0) {
         CUR_CK(cudaMemcpyAsync(out, cand, sizeof(int32_t) * r * nsets, cudaMemcpyDeviceToDevice, st));
+        out_minv = in_minv;
+        out_lv = in_lv;
         return CUR_OK;
     }
-    const size_t mark = ar.off;
     const int64_t nrows = (int64_t)npairs * 2 * r;
     TB* U = ar.get<TB>((size_t)nrows * r);
-    int32_t* S = ar.get<int32_t>((size_t)npairs * r);
     int32_t* S2 = ar.get<int32_t>((size_t)npairs * r);
     if (!ar.ok) return CUR_ERR_NOMEM;
-    // the union of pair t is cand rows 2t, 2t+1: contiguous in cand
     gather_union_k<TB><<<nblk(nrows * r), 256, 0, st>>>(basis, p, r, cand, nrows, U, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
-    Stage sg;
+    lv.probs.clear();
     for (int t = 0; t < npairs; ++t) {
         MvProb pr{};
         pr.base = (int64_t)t * 2 * r;
         pr.gid_arr = cand + (int64_t)t * 2 * r;
         pr.gid_base = 0;
         pr.p = 2 * r;
-        sg.probs.push_back(pr);
+        lv.probs.push_back(pr);
     }
-    mv_iota<<<nblk(npairs * r), 256, 0, st>>>(S, npairs, r, 0);
+    CUR_TRY(stage_setup<TB>(h, r, lv, ar));
+    mv_iota<<<nblk(npairs * r), 256, 0, st>>>(lv.S, npairs, r, 0);
     CUR_CK(cudaGetLastError());
     note_launch();
-    StageOut so{};
-    std::vector<int> none;
-    CUR_TRY(run_stage<TB>(h, U, nrows, r, o, sg, false, none, S, &so, ar, st));
-    std::vector<int> stat, sw;
-    CUR_TRY(read_stage(h, so, stat, sw, st));
-    for (int v : sw) *swaps += v;
-    // singular left start: start at the right child; then Algorithm 3 on the union
+    std::vector<int> lu_mask(npairs, 1), none;
+    for (int t = 0; t < npairs; ++t) {
+        const int k = 2 * t;
+        if (k < (int)in_minv.size() && in_minv[k] && in_lv[k]) {
+            lu_mask[t] = 0;
+            CUR_CK(cudaMemcpyAsync(lv.minv64 + (int64_t)t * r * r, in_minv[k], sizeof(double) * r * r,
+                                   cudaMemcpyDeviceToDevice, st));
+            CUR_CK(cudaMemcpyAsync(lv.logvol + t, in_lv[k], sizeof(double), cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    CUR_TRY(stage_run<TB>(h, U, r, o, lv, false, lu_mask, none, st));
+    CUR_TRY(stage_read<TB>(h, lv, st));
+    for (int v : lv.sw) *swaps += v;
+    // singular left start: start at the right set; then Algorithm 3 on the union
     std::vector<int> skip(npairs, 1);
     bool any = false;
     for (int t = 0; t < npairs; ++t)
-        if (stat[t] == CUR_ERR_SINGULAR) { skip[t] = 0; any = true; }
-    if (any) {
-        mv_iota<<<nblk(npairs * r), 256, 0, st>>>(S2, npairs, r, r);
-        CUR_CK(cudaGetLastError());
-    note_launch();
-        Stage sg2 = sg;
-        StageOut so2{};
-        CUR_TRY(run_stage<TB>(h, U, nrows, r, o, sg2, false, skip, S2, &so2, ar, st));
-        std::vector<int> stat2, sw2;
-        CUR_TRY(read_stage(h, so2, stat2, sw2, st));
-        std::vector<int> skip3(npairs, 1);
-        bool any3 = false;
-        for (int t = 0; t < npairs; ++t) {
-            if (skip[t]) continue;
-            *swaps += sw2[t];
-            if (stat2[t] == CUR_ERR_SINGULAR) { skip3[t] = 0; any3 = true; }
-            CUR_CK(cudaMemcpyAsync(S + (int64_t)t * r, S2 + (int64_t)t * r, sizeof(int32_t) * r,
-                                   cudaMemcpyDeviceToDevice, st));
+        if (lv.stat[t] == CUR_ERR_SINGULAR) { skip[t] = 0; any = true; }
+    for (int attempt = 0; attempt < 2 && any; ++attempt) {
+        if (attempt == 0) {
+            mv_iota<<<nblk(npairs * r), 256, 0, st>>>(S2, npairs, r, r);
+            CUR_CK(cudaGetLastError());
+            note_launch();
+            for (int t = 0; t < npairs; ++t)
+                if (!skip[t])
+                    CUR_CK(cudaMemcpyAsync(lv.S + (int64_t)t * r, S2 + (int64_t)t * r,
+                                           sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
         }
-        if (any3) {
-            Stage sg3 = sg;
-            StageOut so3{};
-            CUR_TRY(run_stage<TB>(h, U, nrows, r, o, sg3, true, skip3, S2, &so3, ar, st));
-            std::vector<int> stat3, sw3;
-            CUR_TRY(read_stage(h, so3, stat3, sw3, st));
-            for (int t = 0; t < npairs; ++t) {
-                if (skip3[t]) continue;
-                *swaps += sw3[t];
-                CUR_CK(cudaMemcpyAsync(S + (int64_t)t * r, S2 + (int64_t)t * r, sizeof(int32_t) * r,
-                                       cudaMemcpyDeviceToDevice, st));
-            }
+        const std::vector<int> save = lv.stat, savesw = lv.sw;
+        CUR_TRY(stage_run<TB>(h, U, r, o, lv, attempt == 1, none, skip, st));
+        CUR_TRY(stage_read<TB>(h, lv, st));
+        any = false;
+        for (int t = 0; t < npairs; ++t) {
+            if (skip[t]) { lv.stat[t] = save[t]; lv.sw[t] = savesw[t]; continue; }
+            *swaps += lv.sw[t];
+            if (lv.stat[t] == CUR_ERR_SINGULAR) any = true; else skip[t] = 1;
         }
     }
-    mv_emit<<<nblk(npairs * r), 256, 0, st>>>(so.dprob, S, npairs, r, out);
+    mv_emit<<<nblk(npairs * r), 256, 0, st>>>(lv.dprob, lv.S, npairs, r, out);
     CUR_CK(cudaGetLastError());
     note_launch();
-    if (nsets % 2 == 1)
+    for (int t = 0; t < npairs; ++t) {
+        const bool ok = lv.stat[t] == CUR_OK || lv.stat[t] == CUR_ERR_NOCONV;
+        out_minv.push_back(ok ? lv.minv64 + (int64_t)t * r * r : nullptr);
+        out_lv.push_back(ok ? lv.logvol + t : nullptr);
+    }
+    if (nsets % 2 == 1) {
         CUR_CK(cudaMemcpyAsync(out + (int64_t)npairs * r, cand + (int64_t)(nsets - 1) * r,
                                sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    ar.off = mark;
-    ar.ok = true;
+        out_minv.push_back(nsets - 1 < (int)in_minv.size() ? in_minv[nsets - 1] : nullptr);
+        out_lv.push_back(nsets - 1 < (int)in_lv.size() ? in_lv[nsets - 1] : nullptr);
+    }
     return CUR_OK;
 }
 
+// Maxvol over all p rows of the basis, started at S0 (global rows). With `inherit`
+// (one problem's M^-1 and log|det| for exactly the rows S0 in that order) no new
+// factorisation is made.
 template <typename TB>
 static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, const cur_opts* o,
                            const int32_t* S0, int32_t* S_out, double* logvol_out, MvResult* res,
-                           Arena& ar, cudaStream_t st, bool lu_only = false) {
+                           Arena& ar, cudaStream_t st, const double* inherit_minv = nullptr,
+                           const double* inherit_lv = nullptr) {
     const size_t mark = ar.off;
-    int32_t* S = ar.get<int32_t>(r);
-    if (!ar.ok) return CUR_ERR_NOMEM;
-    Stage sg;
+    Stage<TB> sg;
     MvProb pr{};
     pr.base = 0;
     pr.gid_base = 0;
     pr.gid_arr = nullptr;
     pr.p = (int32_t)p;
     sg.probs.push_back(pr);
-    CUR_CK(cudaMemcpyAsync(S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    StageOut so{};
-    std::vector<int> none;
-    CUR_TRY(run_stage<TB>(h, basis, p, r, o, sg, false, none, S, &so, ar, st, lu_only));
-    std::vector<int> stat, sw;
-    CUR_TRY(read_stage(h, so, stat, sw, st));
-    if (res) { res->swaps = sw[0]; res->status = stat[0]; }
-    if (stat[0] != CUR_ERR_SINGULAR && stat[0] != CUR_ERR_ARG)
-        CUR_CK(cudaMemcpyAsync(S_out, S, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    CUR_TRY(stage_setup<TB>(h, r, sg, ar));
+    CUR_CK(cudaMemcpyAsync(sg.S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    std::vector<int> lu_mask(1, 1), none;
+    if (inherit_minv) {
+        lu_mask[0] = 0;
+        CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+        CUR_CK(cudaMemcpyAsync(sg.logvol, inherit_lv, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    CUR_TRY(stage_run<TB>(h, basis, r, o, sg, false, lu_mask, none, st));
+    CUR_TRY(stage_read<TB>(h, sg, st));
+    if (res) { res->swaps = sg.sw[0]; res->status = sg.stat[0]; }
+    if (sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG)
+        CUR_CK(cudaMemcpyAsync(S_out, sg.S, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     else if (S_out != S0)
         CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, so.logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, sg.logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
     CUR_CK(cudaStreamSynchronize(st));
     ar.off = mark;
     ar.ok = true;
@@ -964,11 +969,15 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
     const int64_t base_sz = p / nb, extra = p % nb;
     if (base_sz < r) return CUR_ERR_ARG;
     const size_t mark = ar.off;
-    int32_t* S = ar.get<int32_t>((size_t)nb * r);
     int32_t* setsA = ar.get<int32_t>((size_t)nb * r);
     int32_t* setsB = ar.get<int32_t>((size_t)nb * r);
     if (!ar.ok) return CUR_ERR_NOMEM;
-    Stage sg;
+    // Stage objects (and their workspace) stay alive until the end of the call, so a
+    // merge node can start from its left set's M^-1.
+    std::vector<Stage<TB>> stages;
+    stages.reserve(64);
+    stages.emplace_back();
+    Stage<TB>& sb = stages[0];
     int64_t s0 = 0;
     for (int k = 0; k < nb; ++k) {
         const int64_t sz = base_sz + (k < extra ? 1 : 0);
@@ -977,43 +986,58 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         pr.gid_base = s0;
         pr.gid_arr = nullptr;
         pr.p = (int32_t)sz;
-        sg.probs.push_back(pr);
+        sb.probs.push_back(pr);
         s0 += sz;
     }
-    StageOut so{};
+    CUR_TRY(stage_setup<TB>(h, r, sb, ar));
     std::vector<int> none;
-    CUR_TRY(run_stage<TB>(h, basis, p, r, o, sg, true, none, S, &so, ar, st));
-    std::vector<int> stat, sw;
-    CUR_TRY(read_stage(h, so, stat, sw, st));
+    CUR_TRY(stage_run<TB>(h, basis, r, o, sb, true, none, none, st));
+    CUR_TRY(stage_read<TB>(h, sb, st));
     int total = 0;
-    for (int v : sw) total += v;
-    mv_emit<<<nblk(nb * r), 256, 0, st>>>(so.dprob, S, nb, r, setsA);
+    for (int v : sb.sw) total += v;
+    mv_emit<<<nblk(nb * r), 256, 0, st>>>(sb.dprob, sb.S, nb, r, setsA);
     CUR_CK(cudaGetLastError());
     note_launch();
+    std::vector<const double*> mv, lvp, mv2, lvp2;
+    for (int k = 0; k < nb; ++k) {
+        const bool ok = sb.stat[k] == CUR_OK || sb.stat[k] == CUR_ERR_NOCONV;
+        mv.push_back(ok ? sb.minv64 + (int64_t)k * r * r : nullptr);
+        lvp.push_back(ok ? sb.logvol + k : nullptr);
+    }
     int nsets = nb;
     int32_t* cur = setsA;
     int32_t* nxt = setsB;
     while (nsets > 1) {
         int msw = 0;
-        CUR_TRY(merge_level_t<TB>(h, basis, p, r, cur, nsets, o, nxt, &msw, ar, st));
+        stages.emplace_back();
+        CUR_TRY(merge_level_t<TB>(h, basis, p, r, cur, nsets, o, nxt, &msw, mv, lvp, stages.back(),
+                                  mv2, lvp2, ar, st));
         total += msw;
         nsets = (nsets + 1) / 2;
         std::swap(cur, nxt);
+        mv.swap(mv2);
+        lvp.swap(lvp2);
     }
     int fstat = CUR_OK;
     if (o->flags & CUR_FLAG_POLISH) {
         MvResult gr;
-        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st));
+        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st,
+                             mv.empty() ? nullptr : mv[0], lvp.empty() ? nullptr : lvp[0]));
         total += gr.swaps;
         fstat = gr.status;
     } else {
         CUR_CK(cudaMemcpyAsync(I_out, cur, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
         if (logvol_out) {
-            // log|det| of the merged set through one LU
-            MvResult gr;
-            int32_t* tmp = ar.get<int32_t>(r);
-            if (!ar.ok) return CUR_ERR_NOMEM;
-            CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, tmp, logvol_out, &gr, ar, st, true));
+            if (!mv.empty() && lvp[0]) {
+                CUR_CK(cudaMemcpyAsync(logvol_out, lvp[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
+            } else {
+                MvResult gr;
+                cur_opts o2 = *o;
+                o2.delta = 1e300;   // no swap: one factorisation for log|det|
+                int32_t* tmp = ar.get<int32_t>(r);
+                if (!ar.ok) return CUR_ERR_NOMEM;
+                CUR_TRY(global_t<TB>(h, basis, p, r, &o2, cur, tmp, logvol_out, &gr, ar, st));
+            }
         }
     }
     if (swaps_out) {
@@ -1049,12 +1073,22 @@ cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t
     return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st);
 }
 
+template <typename TB>
+static cur_status merge_one(cur_handle* h, const TB* basis, int64_t p, int r, const int32_t* cand,
+                            int nsets, const cur_opts* o, int32_t* out, int* swaps, Arena& ar,
+                            cudaStream_t st) {
+    curk::Stage<TB> lv;
+    std::vector<const double*> none, om, ol;
+    return curk::merge_level_t<TB>(h, basis, p, r, cand, nsets, o, out, swaps, none, none, lv, om, ol,
+                                   ar, st);
+}
+
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
                        int* swaps, Arena& ar, cudaStream_t st) {
     if (dt == CUR_F64)
-        return curk::merge_level_t<double>(h, static_cast<const double*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
-    return curk::merge_level_t<float>(h, static_cast<const float*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
+        return merge_one<double>(h, static_cast<const double*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
+    return merge_one<float>(h, static_cast<const float*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
 }
 
 template <typename TA>

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "common.cuh"
 #include "internal.h"
@@ -54,14 +55,16 @@ __global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, 
                                                       const int32_t* __restrict__ J, int r,
                                                       double* __restrict__ U, double* rcond_out,
                                                       double* __restrict__ work, int* status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, nt = blockDim.x;
-    double* M = work;            // r x r, LU in place
-    double* X = work + r * r;    // r x r
+    double* M = reinterpret_cast<double*>(smem_raw);  // r x r, inverted in place
+    double* colk = M + r * r;
+    int* piv = reinterpret_cast<int*>(colk + r);
+    double* X = work + r * r;    // r x r (Jacobi V)
     double* M0 = work + 2 * r * r;
-    __shared__ int s_piv, s_sing, s_bad;
+    __shared__ int s_bad;
     __shared__ double s_max, s_n1, s_ni;
-    __shared__ int perm[128];
-    if (tid == 0) { s_bad = 0; s_sing = 0; }
+    if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int e = tid; e < r * r; e += nt) {
         const int a = e / r, b = e - a * r;
@@ -73,7 +76,6 @@ __global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, 
         M[e] = x;
         M0[e] = x;
     }
-    for (int k = tid; k < r; k += nt) perm[k] = k;
     __syncthreads();
     if (s_bad) {
         if (tid == 0) {
@@ -93,61 +95,14 @@ __global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, 
         s_n1 = n1;
     }
     __syncthreads();
-    const double thresh = (double)r * kEpsR * s_max;
-    for (int k = 0; k < r; ++k) {
-        if (tid == 0) {
-            double bv = -1.0;
-            int bi = k;
-            for (int i = k; i < r; ++i) {
-                const double x = fabs(M[i * r + k]);
-                if (x > bv) { bv = x; bi = i; }
-            }
-            s_piv = bi;
-        }
-        __syncthreads();
-        const int pv = s_piv;
-        if (pv != k) {
-            for (int c = tid; c < r; c += nt) {
-                const double t = M[k * r + c];
-                M[k * r + c] = M[pv * r + c];
-                M[pv * r + c] = t;
-            }
-            if (tid == 0) { const int t = perm[k]; perm[k] = perm[pv]; perm[pv] = t; }
-        }
-        __syncthreads();
-        const double d = M[k * r + k];
-        if (!(fabs(d) > thresh) && tid == 0) s_sing = 1;
-        if (d != 0.0) {
-            for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] /= d;
-            __syncthreads();
-            const int w = r - k - 1;
-            for (int e = tid; e < w * w; e += nt) {
-                const int i = k + 1 + e / w, j = k + 1 + e % w;
-                M[i * r + j] -= M[i * r + k] * M[k * r + j];
-            }
-        }
-        __syncthreads();
-    }
-    bool use_pinv = s_sing != 0;
+    const int sing = gj_inverse(M, r, colk, piv, (double)r * kEpsR * s_max, nullptr);
+    bool use_pinv = sing != 0;
     if (!use_pinv) {
-        for (int c = tid; c < r; c += nt) {
-            for (int i = 0; i < r; ++i) {
-                double s = (perm[i] == c) ? 1.0 : 0.0;
-                for (int j = 0; j < i; ++j) s -= M[i * r + j] * X[j * r + c];
-                X[i * r + c] = s;
-            }
-            for (int i = r - 1; i >= 0; --i) {
-                double s = X[i * r + c];
-                for (int j = i + 1; j < r; ++j) s -= M[i * r + j] * X[j * r + c];
-                X[i * r + c] = s / M[i * r + i];
-            }
-        }
-        __syncthreads();
         if (tid == 0) {
             double ni = 0.0;
             for (int c = 0; c < r; ++c) {
                 double cs = 0.0;
-                for (int a = 0; a < r; ++a) cs += fabs(X[a * r + c]);
+                for (int a = 0; a < r; ++a) cs += fabs(M[a * r + c]);
                 ni = fmax(ni, cs);
             }
             s_ni = ni;
@@ -156,7 +111,7 @@ __global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, 
         __syncthreads();
         use_pinv = !(1.0 / (s_n1 * s_ni) >= 1e-13);
         if (!use_pinv) {
-            for (int e = tid; e < r * r; e += nt) U[e] = X[e];
+            for (int e = tid; e < r * r; e += nt) U[e] = M[e];
             return;
         }
     } else if (tid == 0) {
@@ -259,14 +214,26 @@ __global__ void __launch_bounds__(256) residual_w_k(const double* __restrict__ U
     }
 }
 
+// N consecutive elements from 16-byte aligned memory as 16-byte loads.
+template <typename T, int N>
+__device__ __forceinline__ void ld_vec(const T* p, T (&x)[N]) {
+    static_assert((N * sizeof(T)) % 16 == 0, "16-byte multiple");
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int c = 0; c < (int)(N * sizeof(T) / 16); ++c) {
+        const uint4 v = q[c];
+        memcpy(&x[c * (16 / sizeof(T))], &v, 16);
+    }
+}
+
 // Residual tiles. TM x TN outputs per thread, 16 x 16 threads, tile (16 TM) x (16 TN).
 // Grid: (panels, segments); CTA (p, s) takes rows [p*BM, p*BM+BM) and column tiles
 // s, s + segs, ... Partials per CTA: max|E|, sum E^2, sum A^2, non-finite flag.
 template <typename TA, typename TW, int TM, int TN>
-__global__ void __launch_bounds__(256) residual_k(const TA* __restrict__ A, int64_t m, int64_t n,
+__global__ void __launch_bounds__(256, 2) residual_k(const TA* __restrict__ A, int64_t m, int64_t n,
                                                   int64_t ld, const TA* __restrict__ C,
                                                   const TW* __restrict__ W, int r,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, int vec) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TW* Ct = reinterpret_cast<TW*>(smem_raw);  // r x BM (transposed C panel)
@@ -294,27 +261,34 @@ __global__ void __launch_bounds__(256) residual_k(const TA* __restrict__ A, int6
         for (int a = 0; a < TM; ++a)
 #pragma unroll
             for (int b = 0; b < TN; ++b) acc[a][b] = (TW)0;
+#pragma unroll 4
         for (int k = 0; k < r; ++k) {
             TW x[TM], y[TN];
-#pragma unroll
-            for (int a = 0; a < TM; ++a) x[a] = Ct[k * BM + ty * TM + a];
-#pragma unroll
-            for (int b = 0; b < TN; ++b) y[b] = Ws[k * BN + tx * TN + b];
+            ld_vec<TW, TM>(Ct + k * BM + ty * TM, x);
+            ld_vec<TW, TN>(Ws + k * BN + tx * TN, y);
 #pragma unroll
             for (int a = 0; a < TM; ++a)
 #pragma unroll
                 for (int b = 0; b < TN; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
         }
         TW tmx = (TW)0, tse = (TW)0, tsa = (TW)0;
+        const bool fullc = vec && (c0 + tx * TN + TN <= n);
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
             const int64_t i = r0 + ty * TM + a;
             if (i >= m) continue;
             const TA* arow = A + i * ld + c0 + tx * TN;
+            TA araw[TN];
+            if (fullc) {
+                ld_vec<TA, TN>(arow, araw);
+            } else {
+#pragma unroll
+                for (int b = 0; b < TN; ++b) araw[b] = (c0 + tx * TN + b < n) ? arow[b] : arow[0];
+            }
 #pragma unroll
             for (int b = 0; b < TN; ++b) {
                 if (c0 + tx * TN + b >= n) continue;
-                const TW av = (TW)to_d(arow[b]);
+                const TW av = (TW)to_d(araw[b]);
                 const TW e = av - acc[a][b];
                 if (!(fabs(e) <= (TW)INFINITY)) bad = 1;
                 tmx = fmax(tmx, fabs(e));
@@ -351,23 +325,39 @@ __global__ void __launch_bounds__(256) residual_k(const TA* __restrict__ A, int6
     }
 }
 
+// Combines the per-CTA partials in a fixed order (one CTA of 256 threads).
 __global__ void residual_final_k(const double* part, int64_t nparts, double* cheb, double* fro,
                                  int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double s1[256], s2[256], s3[256];
+    __shared__ int sb[256];
+    const int tid = threadIdx.x;
     double a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int bad = 0;
-    for (int64_t c = 0; c < nparts; ++c) {
+    for (int64_t c = tid; c < nparts; c += blockDim.x) {
         a1 = fmax(a1, part[c * 4 + 0]);
         a2 += part[c * 4 + 1];
         a3 += part[c * 4 + 2];
         bad |= part[c * 4 + 3] != 0.0;
     }
-    if (bad) {
+    s1[tid] = a1; s2[tid] = a2; s3[tid] = a3; sb[tid] = bad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            s1[tid] = fmax(s1[tid], s1[tid + o]);
+            s2[tid] += s2[tid + o];
+            s3[tid] += s3[tid + o];
+            sb[tid] |= sb[tid + o];
+        }
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    a1 = s1[0];
+    if (sb[0]) {
         set_status(status, CUR_ERR_NONFINITE);
         a1 = NAN;
     }
     *cheb = a1;
-    if (fro) *fro = a3 > 0.0 ? sqrt(a2 / a3) : 0.0;
+    if (fro) *fro = s3[0] > 0.0 ? sqrt(s2[0] / s3[0]) : 0.0;
 }
 
 static inline unsigned nb(int64_t n, int t = 256) {
@@ -391,7 +381,10 @@ static cur_status assemble_t(cur_handle* h, const cur_mat* Am, const int32_t* I,
         CUR_CK(cudaGetLastError());
     note_launch();
     }
-    assemble_inv_k<TA><<<1, 256, 0, st>>>(A, Am->rows, Am->cols, Am->ld, I, J, r, U_out, rcond_out, work, h->status);
+    const size_t sm = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
+    CUR_CK(cudaFuncSetAttribute((const void*)assemble_inv_k<TA>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    assemble_inv_k<TA><<<1, 256, sm, st>>>(A, Am->rows, Am->cols, Am->ld, I, J, r, U_out, rcond_out, work, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
@@ -423,11 +416,13 @@ static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, co
     residual_w_k<TA, TW><<<nb(n), 256, smw, st>>>(U, static_cast<const TA*>(R), r, n, W);
     CUR_CK(cudaGetLastError());
     note_launch();
+    const uintptr_t base = reinterpret_cast<uintptr_t>(Am->data);
+    const int vec = (base % 16 == 0) && ((size_t)Am->ld * sizeof(TA)) % 16 == 0 ? 1 : 0;
     residual_k<TA, TW, TM, TN><<<dim3((unsigned)panels, (unsigned)segs), 256, sm, st>>>(
-        static_cast<const TA*>(Am->data), m, n, Am->ld, static_cast<const TA*>(C), W, r, part);
+        static_cast<const TA*>(Am->data), m, n, Am->ld, static_cast<const TA*>(C), W, r, part, vec);
     CUR_CK(cudaGetLastError());
     note_launch();
-    residual_final_k<<<1, 32, 0, st>>>(part, panels * segs, cheb, fro, h->status);
+    residual_final_k<<<1, 256, 0, st>>>(part, panels * segs, cheb, fro, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
