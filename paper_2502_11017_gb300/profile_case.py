@@ -1,0 +1,86 @@
+"""Runs one library call on a Gaussian-kernel matrix for profiling (e.g. under ncu).
+
+    python -m paper_2502_11017_gb300.profile_case --call aca --m 16384 --n 8192 --r 3
+    python -m paper_2502_11017_gb300.profile_case --call residual --m 16384 --n 8192 --r 64
+    python -m paper_2502_11017_gb300.profile_case --call cross --m 65536 --n 8192 --r 64
+
+The matrix is exp(-|x_i - y_j|^2 / h^2) with uniform points (the generator of the
+65536 x 8192 workload, at any size). --reps calls are made after --warmup calls;
+each call is timed with CUDA events and printed.
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import numpy as np
+import torch
+
+import paper_2502_11017_gb300 as cur
+from paper_2502_11017_gb300 import workloads as wl
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols"], required=True)
+    ap.add_argument("--m", type=int, default=16384)
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--r", type=int, default=64)
+    ap.add_argument("--b_r", type=int, default=16)
+    ap.add_argument("--b_c", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=11019)
+    a = ap.parse_args()
+    dev = torch.device("cuda:0")
+    A = torch.from_numpy(wl.gaussian_kernel(a.m, a.n, 0.2, seed=a.seed, chunk_rows=1024)).to(dev)
+    m, n, r = a.m, a.n, a.r
+    hd = cur.Handle(m, n, max(r, 64), cur.CUR_F32)
+    h = hd.h
+    idx = torch.empty(r, dtype=torch.int32, device=dev)
+    I = torch.empty(r, dtype=torch.int32, device=dev)
+    J = torch.empty(r, dtype=torch.int32, device=dev)
+    C = torch.empty((m, r), dtype=torch.float32, device=dev)
+    R = torch.empty((r, n), dtype=torch.float32, device=dev)
+    U = torch.empty((r, r), dtype=torch.float64, device=dev)
+    rc = torch.empty(1, dtype=torch.float64, device=dev)
+    cheb = torch.empty(1, dtype=torch.float64, device=dev)
+    fro = torch.empty(1, dtype=torch.float64, device=dev)
+    o = cur.opts()
+    if a.call in ("residual", "rows", "cols"):
+        cur.cur_cross(h, A, r, a.b_r, a.b_c, o, I, J)
+        cur.cur_assemble(h, A, I, J, r, C, U, R, rc)
+        cur.cur_aca_select(h, A, 1, r, 1, idx)
+
+    def call():
+        if a.call == "aca":
+            cur.cur_aca_select(h, A, 1, r, 1, idx)
+        elif a.call == "residual":
+            cur.cur_residual_cheb(h, A, C, U, R, r, cheb, fro)
+        elif a.call == "cross":
+            cur.cur_cross(h, A, r, a.b_r, a.b_c, o, I, J)
+        elif a.call == "rows":
+            cur.cur_maxvol_rows(h, A, idx, r, cur.opts(nblocks=a.b_r), I)
+        elif a.call == "cols":
+            cur.cur_maxvol_cols(h, A, I, r, cur.opts(nblocks=a.b_c), J)
+
+    for _ in range(a.warmup):
+        call()
+    torch.cuda.synchronize()
+    for _ in range(a.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        call()
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"{a.call} m={m} n={n} r={r}: {e0.elapsed_time(e1):.3f} ms (host {1e3 * (time.perf_counter() - t0):.3f} ms)")
+    st = cur.cur_sync_status(h)
+    if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
+        raise SystemExit(f"device status {st}")
+    hd.close()
+
+
+if __name__ == "__main__":
+    main()
