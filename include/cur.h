@@ -145,6 +145,24 @@ cur_status cur_residual_cheb(cur_handle* h, const cur_mat* A, const void* C, con
                              const void* R, int32_t r, double* cheb_out, double* fro_rel_out,
                              cudaStream_t stream);
 
+/* Allocation-free residual (the paper has no counterpart; the arithmetic is that of
+ * cur_residual_cheb, with the same arguments and outputs but no handle). It is for
+ * callers that cannot allocate device memory where they need the residual, e.g. after
+ * handing all device memory to their own pool, or inside a loop that must not hit
+ * cudaMalloc's implicit synchronisation. Its scratch (W = U R, r x n in the arithmetic
+ * type, plus 32 bytes per CTA) lives in one 16 MiB array compiled into the library,
+ * present on every device that loads it until the process exits; larger problems
+ * (about r n > 4e6 for FP32/BF16 data, 2e6 for FP64) return CUR_ERR_NOMEM before any
+ * launch. The array is shared by every call and keeps the last call's contents; calls
+ * whose work overlaps on the GPU (other streams, other threads) race on it, so order
+ * them. The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture. It calls no
+ * cudaMalloc or cudaFree. A non-finite value in the data gives cheb_out = NaN (there
+ * is no handle status word to record it). */
+cur_status cur_residual_cheb_noalloc(const cur_mat* A, const void* C, const double* U,
+                                     const void* R, int32_t r, double* cheb_out,
+                                     double* fro_rel_out, cudaStream_t stream);
+
 /* The whole cross (Algorithm 2 with blockwise maxvol refinement): J0 = Algorithm 3
  * on the columns (b_c blocks; padded with the lowest unused columns after an early
  * stop), sweep 1 = {I = cur_maxvol_rows(J0, b_r), J = cur_maxvol_cols(I, b_c)},

@@ -22,7 +22,8 @@ CUR_FLAG_POLISH = 1
 EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select",
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
-           "cur_status_string", "cur_prof_enable", "cur_prof_read"]
+           "cur_status_string", "cur_prof_enable", "cur_prof_read",
+           "cur_residual_cheb_noalloc"]
 
 
 class CurMat(ctypes.Structure):
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_default_opts": ([], CurOpts),
         "cur_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "cur_prof_enable": ([P, ctypes.c_int], ctypes.c_int),
+        "cur_residual_cheb_noalloc": ([pmat, P, P, P, I32, P, P, P], ctypes.c_int),
         "cur_prof_read": ([P, P, ctypes.POINTER(D), ctypes.POINTER(I32),
                            ctypes.POINTER(I64)], ctypes.c_int),
     }
@@ -185,6 +187,13 @@ def cur_residual_cheb(h, A, C, U, R, r: int, cheb_out, fro_out=None, stream=None
     return _check(load().cur_residual_cheb(h, ctypes.byref(mat(A)), _ptr(C), _ptr(U), _ptr(R), r,
                                            _ptr(cheb_out), _ptr(fro_out), _stream(stream)),
                   "cur_residual_cheb")
+
+
+def cur_residual_cheb_noalloc(A, C, U, R, r: int, cheb_out, fro_out=None, stream=None) -> int:
+    """The residual without a handle or any allocation (scratch compiled into libcur)."""
+    return _check(load().cur_residual_cheb_noalloc(ctypes.byref(mat(A)), _ptr(C), _ptr(U), _ptr(R),
+                                                   r, _ptr(cheb_out), _ptr(fro_out),
+                                                   _stream(stream)), "cur_residual_cheb_noalloc")
 
 
 def cur_cross(h, A, r: int, b_r: int, b_c: int, o: CurOpts, I_out, J_out, info_out=None,

@@ -451,3 +451,96 @@ cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const d
     }
     return CUR_ERR_ARG;
 }
+
+// ---------------------------------------------------------------- allocation-free residual
+//
+// cur_residual_cheb needs a handle, and a handle allocates its workspace with cudaMalloc.
+// Some callers cannot do that where they need the residual: code that runs after its
+// device memory has been handed to a pool or allocator of its own, or a loop that must
+// not hit cudaMalloc's implicit device synchronisation. For them
+// cur_residual_cheb_noalloc keeps its scratch (W = U R and the per-CTA partial sums) in
+// one array compiled into this library. The array's device address is looked up once
+// per device, on the first call made with that device current.
+
+#include <mutex>
+
+namespace curk {
+constexpr size_t kNoallocScratchBytes = (size_t)16 << 20;  // 16 MiB on every device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+}  // namespace curk
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (set up on first use).
+static cur_status noalloc_scratch(void** out) {
+    int dev = 0;
+    CUR_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return CUR_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, curk::g_noalloc_scratch) != cudaSuccess || !p) return CUR_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CUR_OK;
+}
+
+template <typename TA, typename TW, int TM, int TN>
+static cur_status residual_noalloc_t(const cur_mat* Am, const void* C, const double* U,
+                                     const void* R, int r, double* cheb, double* fro,
+                                     cudaStream_t st) {
+    using namespace curk;
+    const int64_t m = Am->rows, n = Am->cols;
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    const int64_t panels = (m + BM - 1) / BM;
+    const int64_t ntile = (n + BN - 1) / BN;
+    if (panels > 65535LL * 32768LL) return CUR_ERR_ARG;
+    int dev = 0, sms = 0;
+    CUR_CK(cudaGetDevice(&dev));
+    CUR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t sm = (size_t)r * (BM + BN) * sizeof(TW);
+    CUR_CK(cudaFuncSetAttribute((const void*)residual_k<TA, TW, TM, TN>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int occ = 1;
+    CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, residual_k<TA, TW, TM, TN>, 256, sm));
+    const int64_t want = (int64_t)sms * std::max(1, occ) * 4;
+    int64_t segs = std::max<int64_t>(1, std::min<int64_t>(ntile, (want + panels - 1) / panels));
+    segs = std::min<int64_t>(segs, 65535);
+    if (panels > 2147483647LL) return CUR_ERR_ARG;
+    // scratch: W (r x n) then the partials (4 doubles per CTA), 256-byte aligned
+    const size_t w_bytes = ((size_t)r * n * sizeof(TW) + 255) / 256 * 256;
+    const size_t p_bytes = (size_t)panels * segs * 4 * sizeof(double);
+    if (w_bytes + p_bytes > kNoallocScratchBytes) return CUR_ERR_NOMEM;
+    void* base = nullptr;
+    CUR_TRY(noalloc_scratch(&base));
+    TW* W = static_cast<TW*>(base);
+    double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + w_bytes);
+    const size_t smw = (size_t)r * r * sizeof(double);
+    CUR_CK(cudaFuncSetAttribute((const void*)residual_w_k<TA, TW>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    residual_w_k<TA, TW><<<nb(n), 256, smw, st>>>(U, static_cast<const TA*>(R), r, n, W);
+    CUR_CK(cudaGetLastError());
+    const uintptr_t abase = reinterpret_cast<uintptr_t>(Am->data);
+    const int vec = (abase % 16 == 0) && ((size_t)Am->ld * sizeof(TA)) % 16 == 0 ? 1 : 0;
+    residual_k<TA, TW, TM, TN><<<dim3((unsigned)panels, (unsigned)segs), 256, sm, st>>>(
+        static_cast<const TA*>(Am->data), m, n, Am->ld, static_cast<const TA*>(C), W, r, part, vec);
+    CUR_CK(cudaGetLastError());
+    residual_final_k<<<1, 256, 0, st>>>(part, panels * segs, cheb, fro, nullptr);
+    CUR_CK(cudaGetLastError());
+    return CUR_OK;
+}
+
+extern "C" cur_status cur_residual_cheb_noalloc(const cur_mat* A, const void* C, const double* U,
+                                                const void* R, int32_t r, double* cheb_out,
+                                                double* fro_rel_out, cudaStream_t stream) {
+    if (!A || !A->data || A->rows < 1 || A->cols < 1 || A->ld < A->cols) return CUR_ERR_ARG;
+    if (!C || !U || !R || !cheb_out || r < 1 || r > 128) return CUR_ERR_ARG;
+    switch (A->dtype) {
+        case CUR_F64: return residual_noalloc_t<double, double, 4, 4>(A, C, U, R, r, cheb_out, fro_rel_out, stream);
+        case CUR_F32: return residual_noalloc_t<float, float, 8, 8>(A, C, U, R, r, cheb_out, fro_rel_out, stream);
+        case CUR_BF16: return residual_noalloc_t<__nv_bfloat16, float, 8, 8>(A, C, U, R, r, cheb_out, fro_rel_out, stream);
+    }
+    return CUR_ERR_ARG;
+}
