@@ -167,6 +167,27 @@ struct Walk2 {
     }
 };
 
+__device__ __forceinline__ double block_max(double v) {
+    __shared__ double sb[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sb[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < nw ? sb[lane] : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sb[0] = v;
+    }
+    __syncthreads();
+    v = sb[0];
+    __syncthreads();
+    return v;
+}
+
 // ---------------------------------------------------------------- group barrier
 //
 // CTAs of one group (all co-resident: cooperative launch) meet here. `ctr` is a
@@ -262,9 +283,10 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
         __syncthreads();
         for (int j = tid; j < r; j += nt) A[k * r + j] *= dinv;
         __syncthreads();
-        for (int e = tid; e < r * r; e += nt) {
-            const int i = e / r, j = e - i * r;
-            if (i != k) A[e] = fma(-colk[i], A[k * r + j], A[e]);
+        {
+            Walk2 w(tid, nt, r);
+            for (int e = tid; e < r * r; e += nt, w.next())
+                if (w.i != k) A[e] = fma(-colk[w.i], A[k * r + w.c], A[e]);
         }
         __syncthreads();
     }

@@ -76,17 +76,26 @@ cur_status aca_select_full(cur_handle* h, const cur_mat* A, int axis, int r, int
 struct MvResult {
     int swaps = 0;
     int status = CUR_OK;
+    int minv_valid = 0;   // minv_out holds the final FP64 M^-1
 };
 // Row selection on the tall basis `basis` (p x r, compute type of A's dtype,
 // contiguous) with nblocks blocks, merge and optional polish. I_out: device r ints.
+// With minv_out (r x r doubles, device), the final FP64 M^-1 = C(I,:)^-1 is written
+// there (res->minv_valid says whether it is valid).
 cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                              const cur_opts* o, int32_t* I_out, double* logvol_out,
-                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st);
+                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st,
+                             double* minv_out = nullptr);
 // Maxvol over all rows of a basis from the start rows S0 (device r ints, global
 // rows). Writes the result to S_out (device, may alias S0).
+// minv_in / lv_in (optional): M^-1 and log|det| of the start rows, given as is or as the
+// transpose of the inverse (transpose_in) — a column stage's M^-1 is the transpose of the
+// next row stage's; no factorisation is made then. minv_out as for maxvol_basis_rows.
 cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
-                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st);
+                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
+                         const double* minv_in = nullptr, const double* lv_in = nullptr,
+                         bool transpose_in = false, double* minv_out = nullptr);
 // One merge level (cur_merge).
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,

@@ -574,6 +574,14 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     }
 }
 
+// dst = src^T (r x r).
+__global__ void mv_transpose(const double* src, int r, double* dst) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+        const int a = e / r, b = e - a * r;
+        dst[e] = src[b * r + a];
+    }
+}
+
 // Node t of a merge level starts from its left child's M^-1 (same rows, same order).
 __global__ void mv_inherit(const double* child_minv, const double* child_lv, const int32_t* valid,
                            int P, int r, double* minv, double* lv) {
@@ -924,13 +932,14 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
 }
 
 // Maxvol over all p rows of the basis, started at S0 (global rows). With `inherit`
-// (one problem's M^-1 and log|det| for exactly the rows S0 in that order) no new
-// factorisation is made.
+// (M^-1 and log|det| of exactly the rows S0 in that order, or the transpose of that
+// inverse) no new factorisation is made. minv_out receives the final M^-1.
 template <typename TB>
 static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, const cur_opts* o,
                            const int32_t* S0, int32_t* S_out, double* logvol_out, MvResult* res,
                            Arena& ar, cudaStream_t st, const double* inherit_minv = nullptr,
-                           const double* inherit_lv = nullptr) {
+                           const double* inherit_lv = nullptr, bool transpose = false,
+                           double* minv_out = nullptr) {
     const size_t mark = ar.off;
     Stage<TB> sg;
     MvProb pr{};
@@ -942,19 +951,28 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     CUR_TRY(stage_setup<TB>(h, r, sg, ar));
     CUR_CK(cudaMemcpyAsync(sg.S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     std::vector<int> lu_mask(1, 1), none;
-    if (inherit_minv) {
+    if (inherit_minv && inherit_lv) {
         lu_mask[0] = 0;
-        CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+        if (transpose) {
+            mv_transpose<<<nblk((int64_t)r * r), 256, 0, st>>>(inherit_minv, r, sg.minv64);
+            CUR_CK(cudaGetLastError());
+            note_launch();
+        } else {
+            CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+        }
         CUR_CK(cudaMemcpyAsync(sg.logvol, inherit_lv, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
     CUR_TRY(stage_run<TB>(h, basis, r, o, sg, false, lu_mask, none, st));
     CUR_TRY(stage_read<TB>(h, sg, st));
-    if (res) { res->swaps = sg.sw[0]; res->status = sg.stat[0]; }
+    const bool ok = sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG &&
+                    sg.stat[0] != CUR_ERR_NONFINITE && sg.stat[0] != CUR_ERR_TIMEOUT;
+    if (res) { res->swaps = sg.sw[0]; res->status = sg.stat[0]; res->minv_valid = ok && minv_out; }
     if (sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG)
         CUR_CK(cudaMemcpyAsync(S_out, sg.S, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     else if (S_out != S0)
         CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, sg.logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (minv_out && ok) CUR_CK(cudaMemcpyAsync(minv_out, sg.minv64, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
     CUR_CK(cudaStreamSynchronize(st));
     ar.off = mark;
     ar.ok = true;
@@ -964,7 +982,7 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
 template <typename TB>
 static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const cur_opts* o,
                          int32_t* I_out, double* logvol_out, int32_t* swaps_out, MvResult* res,
-                         Arena& ar, cudaStream_t st) {
+                         Arena& ar, cudaStream_t st, double* minv_out = nullptr) {
     const int nb = std::max(1, o->nblocks);
     const int64_t base_sz = p / nb, extra = p % nb;
     if (base_sz < r) return CUR_ERR_ARG;
@@ -1019,13 +1037,20 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         lvp.swap(lvp2);
     }
     int fstat = CUR_OK;
+    int mvalid = 0;
     if (o->flags & CUR_FLAG_POLISH) {
         MvResult gr;
         CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st,
-                             mv.empty() ? nullptr : mv[0], lvp.empty() ? nullptr : lvp[0]));
+                             mv.empty() ? nullptr : mv[0], lvp.empty() ? nullptr : lvp[0], false,
+                             minv_out));
         total += gr.swaps;
         fstat = gr.status;
+        mvalid = gr.minv_valid;
     } else {
+        if (minv_out && !mv.empty() && mv[0]) {
+            CUR_CK(cudaMemcpyAsync(minv_out, mv[0], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+            mvalid = 1;
+        }
         CUR_CK(cudaMemcpyAsync(I_out, cur, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
         if (logvol_out) {
             if (!mv.empty() && lvp[0]) {
@@ -1047,7 +1072,7 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         CUR_CK(cudaMemcpyAsync(swaps_out, hs, sizeof(int32_t), cudaMemcpyHostToDevice, st));
         CUR_CK(cudaStreamSynchronize(st));
     }
-    if (res) { res->swaps = total; res->status = fstat; }
+    if (res) { res->swaps = total; res->status = fstat; res->minv_valid = mvalid; }
     ar.off = mark;
     ar.ok = true;
     return CUR_OK;
@@ -1059,18 +1084,21 @@ size_t compute_size(cur_dtype t) { return t == CUR_F64 ? 8 : 4; }
 
 cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                              const cur_opts* o, int32_t* I_out, double* logvol_out,
-                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st) {
+                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st,
+                             double* minv_out) {
     if (dt == CUR_F64)
-        return curk::rows_t<double>(h, static_cast<const double*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st);
-    return curk::rows_t<float>(h, static_cast<const float*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st);
+        return curk::rows_t<double>(h, static_cast<const double*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st, minv_out);
+    return curk::rows_t<float>(h, static_cast<const float*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st, minv_out);
 }
 
 cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
-                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st) {
+                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
+                         const double* minv_in, const double* lv_in, bool transpose_in,
+                         double* minv_out) {
     if (dt == CUR_F64)
-        return curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st);
-    return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st);
+        return curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out);
+    return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out);
 }
 
 template <typename TB>

@@ -84,29 +84,32 @@ __global__ void __launch_bounds__(256) assemble_inv_k(const TA* __restrict__ A, 
         }
         return;
     }
-    if (tid == 0) {
-        double mx = 0.0, n1 = 0.0;
-        for (int c = 0; c < r; ++c) {
-            double cs = 0.0;
-            for (int a = 0; a < r; ++a) { mx = fmax(mx, fabs(M[a * r + c])); cs += fabs(M[a * r + c]); }
-            n1 = fmax(n1, cs);
+    {
+        // max |M| and the 1-norm (largest column sum), one column per thread
+        double mx = 0.0, cs = 0.0;
+        for (int c = tid; c < r; c += nt) {
+            double s = 0.0;
+            for (int a = 0; a < r; ++a) { mx = fmax(mx, fabs(M[a * r + c])); s += fabs(M[a * r + c]); }
+            cs = fmax(cs, s);
         }
-        s_max = mx;
-        s_n1 = n1;
+        mx = block_max(mx);
+        cs = block_max(cs);
+        if (tid == 0) { s_max = mx; s_n1 = cs; }
+        __syncthreads();
     }
-    __syncthreads();
     const int sing = gj_inverse(M, r, colk, piv, (double)r * kEpsR * s_max, nullptr);
     bool use_pinv = sing != 0;
     if (!use_pinv) {
+        double cs = 0.0;
+        for (int c = tid; c < r; c += nt) {
+            double s = 0.0;
+            for (int a = 0; a < r; ++a) s += fabs(M[a * r + c]);
+            cs = fmax(cs, s);
+        }
+        cs = block_max(cs);
         if (tid == 0) {
-            double ni = 0.0;
-            for (int c = 0; c < r; ++c) {
-                double cs = 0.0;
-                for (int a = 0; a < r; ++a) cs += fabs(M[a * r + c]);
-                ni = fmax(ni, cs);
-            }
-            s_ni = ni;
-            *rcond_out = 1.0 / (s_n1 * ni);
+            s_ni = cs;
+            *rcond_out = 1.0 / (s_n1 * cs);
         }
         __syncthreads();
         use_pinv = !(1.0 / (s_n1 * s_ni) >= 1e-13);
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(256, 2) residual_k(const TA* __restrict__ A, i
     const int64_t r0 = (int64_t)blockIdx.x * BM;
     const int segs = gridDim.y;
     for (int e = threadIdx.x; e < BM * r; e += blockDim.x) {
-        const int i = e / r, k = e - i * r;
+        const int k = e / BM, i = e - k * BM;
         Ct[k * BM + i] = (r0 + i < m) ? (TW)to_d(C[(r0 + i) * r + k]) : (TW)0;
     }
     double mx = 0.0, se = 0.0, sa = 0.0;
@@ -265,29 +268,33 @@ __global__ void __launch_bounds__(256, 2) residual_k(const TA* __restrict__ A, i
         for (int k = 0; k < r; ++k) {
             TW x[TM], y[TN];
             ld_vec<TW, TM>(Ct + k * BM + ty * TM, x);
-            ld_vec<TW, TN>(Ws + k * BN + tx * TN, y);
+            // column pairs 2 tx + 32 b (+1): a half-warp reads 128 contiguous bytes per load
+#pragma unroll
+            for (int b = 0; b < TN / 2; ++b) {
+                const TW* q = Ws + k * BN + 2 * tx + 32 * b;
+                y[2 * b] = q[0];
+                y[2 * b + 1] = q[1];
+            }
 #pragma unroll
             for (int a = 0; a < TM; ++a)
 #pragma unroll
                 for (int b = 0; b < TN; ++b) acc[a][b] = fma(x[a], y[b], acc[a][b]);
         }
         TW tmx = (TW)0, tse = (TW)0, tsa = (TW)0;
-        const bool fullc = vec && (c0 + tx * TN + TN <= n);
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
             const int64_t i = r0 + ty * TM + a;
             if (i >= m) continue;
-            const TA* arow = A + i * ld + c0 + tx * TN;
+            const TA* arow = A + i * ld + c0;
             TA araw[TN];
-            if (fullc) {
-                ld_vec<TA, TN>(arow, araw);
-            } else {
 #pragma unroll
-                for (int b = 0; b < TN; ++b) araw[b] = (c0 + tx * TN + b < n) ? arow[b] : arow[0];
+            for (int b = 0; b < TN; ++b) {
+                const int64_t cc = 2 * tx + 32 * (b >> 1) + (b & 1);
+                araw[b] = (c0 + cc < n) ? arow[cc] : arow[0];
             }
 #pragma unroll
             for (int b = 0; b < TN; ++b) {
-                if (c0 + tx * TN + b >= n) continue;
+                if (c0 + 2 * tx + 32 * (b >> 1) + (b & 1) >= n) continue;
                 const TW av = (TW)to_d(araw[b]);
                 const TW e = av - acc[a][b];
                 if (!(fabs(e) <= (TW)INFINITY)) bad = 1;
