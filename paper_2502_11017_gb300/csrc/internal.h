@@ -114,6 +114,11 @@ cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const d
                          const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
                          cudaStream_t st);
 
+// tcgen05 residual for FP32 data, r = 32 or 64 (residual_tc.cu); CUR_ERR_ARG: not applicable.
+cur_status residual_tc_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                            const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
+                            cudaStream_t st);
+
 // Cooperative launch helper (all CTAs co-resident).
 cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
                        cudaStream_t st);

@@ -451,6 +451,14 @@ cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, cons
 cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
                          const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
                          cudaStream_t st) {
+    if (A->dtype == CUR_F32) {
+        // tensor-core (tcgen05) form where it applies; CUR_ERR_ARG means it does not
+        const size_t mark = ar.off;
+        const cur_status s = residual_tc_impl(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+        if (s != CUR_ERR_ARG) return s;
+        ar.off = mark;
+        ar.ok = true;
+    }
     switch (A->dtype) {
         case CUR_F64: return curk::residual_t<double, double, 4, 4>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
         case CUR_F32: return curk::residual_t<float, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);

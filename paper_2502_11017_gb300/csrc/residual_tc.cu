@@ -1,0 +1,426 @@
+// Residual of the cross on the tensor cores (tcgen05, sm_103a): max|A - C W| and
+// sum (A - C W)^2, sum A^2 with W = U R, for FP32 data and r = 32 or 64 (whole
+// 128-byte swizzle rows); other shapes use the CUDA-core kernel of residual.cu.
+//
+// The product D = C W (m x n, K = r) runs as 3xTF32 on tcgen05.mma (kind::tf32):
+// C = Ch + Cl and W = Wh + Wl with Ch, Wh rounded to TF32 and Cl, Wl the rounded
+// remainders; D = Ch Wh + Ch Wl + Cl Wh keeps ~22 bits, i.e. FP32-level accuracy
+// (the dropped Cl Wl term is ~2^-22 relative). The MMA computes D^T tile by tile
+// (M = 128 columns of A, N = 128 rows, K = r) so that a TMEM lane is a column of A:
+// the epilogue thread of lane j reads A(i, j) for the tile's rows, coalesced across
+// the warp, and A is read from HBM exactly once.
+//
+// Per CTA (persistent, one per SM, 320 threads):
+//   warp 0      TMA producer: the C panel (128 rows x r, hi and lo, resident while
+//               the CTA stays on the panel) and a 2-stage ring of W^T tiles (128 x r,
+//               hi and lo), 128-byte swizzled, K-major
+//   warp 1      MMA issuer (one thread): 3 passes x r/8 MMAs per tile into one of two
+//               TMEM accumulators (128 lanes x 128 FP32 columns each)
+//   warps 2..9  epilogue: two warps per TMEM lane quarter, each taking 64 of the tile's
+//               rows; a thread loads its column of those rows of the next tile while it
+//               folds the current one (64 + 64 loads in flight), reads the accumulator
+//               with tcgen05.ld and folds max|E|, sum E^2, sum A^2
+// Waits are bounded; on a timeout the CTA records CUR_ERR_TIMEOUT, waits (bounded) for
+// the copies and MMAs it issued, frees its TMEM and returns.
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace curk {
+
+constexpr int kTcBM = 128;            // rows of A per tile (MMA N)
+constexpr int kTcBN = 128;            // columns of A per tile (MMA M)
+constexpr int kChunk = 16384;         // one 128-row x 32-element FP32 swizzled chunk
+
+// Wt[j][k] = (U R)(k, j) in FP64, split into TF32 hi and lo, rows padded to ldk.
+template <typename TA>
+__global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, const TA* __restrict__ R,
+                                                 int r, int64_t n, int ldk, float* __restrict__ Wh,
+                                                 float* __restrict__ Wl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* Us = reinterpret_cast<double*>(smem_raw);
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Us[e] = U[e];
+    __syncthreads();
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double rc[64];
+        for (int l = 0; l < r; ++l) rc[l] = to_d(R[(int64_t)l * n + j]);
+        for (int k = 0; k < ldk; ++k) {
+            float hi = 0.f, lo = 0.f;
+            if (k < r) {
+                double s = 0.0;
+                for (int l = 0; l < r; ++l) s = fma(Us[k * r + l], rc[l], s);
+                hi = to_tf32((float)s);
+                lo = to_tf32((float)(s - (double)hi));
+            }
+            Wh[j * ldk + k] = hi;
+            Wl[j * ldk + k] = lo;
+        }
+    }
+}
+
+// Ch/Cl (m x ldk): C split into TF32 hi and lo, rows padded to ldk.
+template <typename TA>
+__global__ void tc_prep_c(const TA* __restrict__ C, int64_t m, int r, int ldk, float* __restrict__ Ch,
+                          float* __restrict__ Cl) {
+    const int64_t total = m * ldk;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldk;
+        const int k = (int)(e - i * ldk);
+        float hi = 0.f, lo = 0.f;
+        if (k < r) {
+            const float c = to_f(C[i * r + k]);
+            hi = to_tf32(c);
+            lo = to_tf32(c - hi);
+        }
+        Ch[e] = hi;
+        Cl[e] = lo;
+    }
+}
+
+struct TcArgs {
+    const float* A;
+    int64_t m, n, ld;
+    int r, nch, ksteps;
+    int64_t ntile_n, ntiles;
+    double* part;   // 4 doubles per CTA
+    int* status;
+};
+
+__global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ CUtensorMap mWh,
+                                                        const __grid_constant__ CUtensorMap mWl,
+                                                        const __grid_constant__ CUtensorMap mCh,
+                                                        const __grid_constant__ CUtensorMap mCl,
+                                                        TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int nch = a.nch;
+    unsigned char* CH = sm;
+    unsigned char* CL = CH + nch * kChunk;
+    // W^T stage s: hi at WH(s), lo at WH(s) + nch chunks
+    unsigned char* const W0 = CL + nch * kChunk;
+    const int wstride = 2 * nch * kChunk;
+    __shared__ __align__(8) uint64_t full[2], empty[2], cfull, cempty, afull[2], aempty[2];
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    __shared__ double rmx[8], rse[8], rsa[8];
+    __shared__ int rbad[8];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t G = gridDim.x;
+    const int64_t t0 = a.ntiles * blockIdx.x / G, t1 = a.ntiles * (blockIdx.x + 1) / G;
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+            mbar_init(&afull[s], 1);
+            mbar_init(&aempty[s], 8);
+        }
+        mbar_init(&cfull, 1);
+        mbar_init(&cempty, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(&tslot, 256);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int64_t cur_panel = -1;
+            int cuse = 0;
+            int64_t it = 0;
+            const uint32_t wbytes = 2u * nch * kChunk, cbytes = 2u * nch * kChunk;
+            bool ok = true;
+            for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
+                const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
+                if (panel != cur_panel) {
+                    if (cuse > 0 && !mbar_wait(&cempty, (cuse - 1) & 1)) { ok = false; break; }
+                    mbar_expect_tx(&cfull, cbytes);
+                    for (int c = 0; c < nch; ++c) {
+                        tma_load_2d(CH + c * kChunk, &mCh, &cfull, 32 * c, (int)(panel * kTcBM));
+                        tma_load_2d(CL + c * kChunk, &mCl, &cfull, 32 * c, (int)(panel * kTcBM));
+                    }
+                    ++cuse;
+                    cur_panel = panel;
+                }
+                const int s = (int)(it & 1);
+                const int64_t u = it >> 1;
+                if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { ok = false; break; }
+                mbar_expect_tx(&full[s], wbytes);
+                for (int c = 0; c < nch; ++c) {
+                    unsigned char* wh = W0 + s * wstride;
+                    tma_load_2d(wh + c * kChunk, &mWh, &full[s], 32 * c, (int)(ct * kTcBN));
+                    tma_load_2d(wh + (nch + c) * kChunk, &mWl, &full[s], 32 * c, (int)(ct * kTcBN));
+                }
+            }
+            if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
+            // every copy issued has completed before the CTA may leave: the MMA warp
+            // consumed (waited on) each full barrier, except after an abort
+            if (!ok || abort_flag) {
+                for (int s = 0; s < 2; ++s) mbar_wait(&full[s], (uint32_t)(((it - 1 - s) >> 1) & 1));
+                mbar_wait(&cfull, (cuse - 1) & 1);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(kTcBN, kTcBM);
+            int64_t cur_panel = -1;
+            int cuse = 0;
+            int64_t it = 0;
+            bool ok = true;
+            const uint32_t ch = su32(CH), cl = su32(CL);
+            for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
+                const int64_t panel = t / a.ntile_n;
+                if (panel != cur_panel) {
+                    if (cuse > 0) mma_commit(&cempty);
+                    if (!mbar_wait(&cfull, cuse & 1)) { ok = false; break; }
+                    ++cuse;
+                    cur_panel = panel;
+                }
+                const int s = (int)(it & 1), b = (int)(it & 1);
+                const int64_t u = it >> 1;
+                if (!mbar_wait(&full[s], (uint32_t)(u & 1))) { ok = false; break; }
+                if (u > 0 && !mbar_wait(&aempty[b], (uint32_t)((u - 1) & 1))) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t wh = su32(W0 + s * wstride), wl = wh + (uint32_t)(nch * kChunk);
+                const uint32_t d = tmem + (uint32_t)(b * kTcBM);
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t aop = pass == 2 ? wl : wh;
+                    const uint32_t bop = pass == 1 ? cl : ch;
+                    for (int k = 0; k < a.ksteps; ++k) {
+                        const uint32_t off = (uint32_t)((k >> 2) * kChunk + (k & 3) * 32);
+                        mma_tf32(d, sdesc_k128(aop + off), sdesc_k128(bop + off), idesc, (pass | k) != 0);
+                    }
+                }
+                mma_commit(&empty[s]);
+                mma_commit(&afull[b]);
+            }
+            if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
+            // the last commits complete when every MMA issued has finished
+            if (it > 0) mbar_wait(&afull[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        constexpr int HR = kTcBM / 2;      // rows per epilogue warp
+        const int q = warp & 3;            // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;  // which 64 rows of the tile
+        const int jl = 32 * q + lane;      // column within the tile = TMEM lane
+        const int ew = warp - 2;           // epilogue warp index 0..7
+        float mx = 0.f;
+        double se = 0.0, sa = 0.0;
+        int bad = 0;
+        float cur[HR], nxt[HR];
+        // first strip of column jl (rows half*64 .. +63 of tile t) of this CTA's range
+        if (t0 < t1) {
+            const int64_t panel = t0 / a.ntile_n, ct = t0 - panel * a.ntile_n;
+            const int64_t i0 = panel * kTcBM + half * HR, j = ct * kTcBN + jl;
+            const bool jv = j < a.n;
+            const float* col = a.A + i0 * a.ld + (jv ? j : 0);
+#pragma unroll
+            for (int rr = 0; rr < HR; ++rr)
+                cur[rr] = (jv && i0 + rr < a.m) ? __ldcs(col + (int64_t)rr * a.ld) : 0.f;
+        }
+        int64_t it = 0;
+        for (int64_t t = t0; t < t1; ++t, ++it) {
+            if (t + 1 < t1) {
+                const int64_t pn = (t + 1) / a.ntile_n, cn = (t + 1) - pn * a.ntile_n;
+                const int64_t in0 = pn * kTcBM + half * HR, jn = cn * kTcBN + jl;
+                const bool jnv = jn < a.n;
+                const float* col = a.A + in0 * a.ld + (jnv ? jn : 0);
+#pragma unroll
+                for (int rr = 0; rr < HR; ++rr)
+                    nxt[rr] = (jnv && in0 + rr < a.m) ? __ldcs(col + (int64_t)rr * a.ld) : 0.f;
+            }
+            const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
+            const int64_t i0 = panel * kTcBM + half * HR, j = ct * kTcBN + jl;
+            const bool jv = j < a.n;
+            const int b = (int)(it & 1);
+            if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1))) {
+                abort_flag = 1;
+                set_status(a.status, CUR_ERR_TIMEOUT);
+                break;
+            }
+            tc_fence_after();
+            float tse = 0.f, tsa = 0.f;
+#pragma unroll
+            for (int c = 0; c < HR / 16; ++c) {
+                float dv[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + half * HR + 16 * c), dv);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int rr = 16 * c + i;
+                    if (jv && i0 + rr < a.m) {
+                        const float e = cur[rr] - dv[i];
+                        if (!(fabsf(e) <= INFINITY)) bad = 1;
+                        mx = fmaxf(mx, fabsf(e));
+                        tse = fmaf(e, e, tse);
+                        tsa = fmaf(cur[rr], cur[rr], tsa);
+                    }
+                }
+            }
+            se += (double)tse;
+            sa += (double)tsa;
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&aempty[b]);
+#pragma unroll
+            for (int rr = 0; rr < HR; ++rr) cur[rr] = nxt[rr];
+            if (abort_flag) break;
+        }
+        // reduce over the 256 epilogue threads
+        double dmx = mx;
+        for (int o = 16; o > 0; o >>= 1) {
+            dmx = fmax(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
+            se += __shfl_xor_sync(0xffffffffu, se, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        if (lane == 0) { rmx[ew] = dmx; rse[ew] = se; rsa[ew] = sa; rbad[ew] = bad; }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+        double m1 = 0.0, m2 = 0.0, m3 = 0.0;
+        int bd = 0;
+        for (int w = 0; w < 8; ++w) { m1 = fmax(m1, rmx[w]); m2 += rse[w]; m3 += rsa[w]; bd |= rbad[w]; }
+        a.part[blockIdx.x * 4 + 0] = m1;
+        a.part[blockIdx.x * 4 + 1] = m2;
+        a.part[blockIdx.x * 4 + 2] = m3;
+        a.part[blockIdx.x * 4 + 3] = bd ? 1.0 : 0.0;
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 256);
+    }
+}
+
+// Combines the per-CTA partials (same as the SIMT path's final step).
+__global__ void tc_final_k(const double* part, int64_t nparts, double* cheb, double* fro, int* status) {
+    __shared__ double s1[256], s2[256], s3[256];
+    __shared__ int sb[256];
+    const int tid = threadIdx.x;
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int bad = 0;
+    for (int64_t c = tid; c < nparts; c += blockDim.x) {
+        a1 = fmax(a1, part[c * 4 + 0]);
+        a2 += part[c * 4 + 1];
+        a3 += part[c * 4 + 2];
+        bad |= part[c * 4 + 3] != 0.0;
+    }
+    s1[tid] = a1; s2[tid] = a2; s3[tid] = a3; sb[tid] = bad;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            s1[tid] = fmax(s1[tid], s1[tid + o]);
+            s2[tid] += s2[tid + o];
+            s3[tid] += s3[tid + o];
+            sb[tid] |= sb[tid + o];
+        }
+        __syncthreads();
+    }
+    if (tid != 0) return;
+    a1 = s1[0];
+    if (sb[0]) {
+        set_status(status, CUR_ERR_NONFINITE);
+        a1 = NAN;
+    }
+    *cheb = a1;
+    if (fro) *fro = s3[0] > 0.0 ? sqrt(s2[0] / s3[0]) : 0.0;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// rows x ldk FP32, boxes of 32 elements x 128 rows, 128-byte swizzle.
+static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int r, int ldk) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)r, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)ldk * sizeof(float)};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static inline unsigned nbk(int64_t n, int t = 256) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
+}
+
+}  // namespace curk
+
+// Returns CUR_ERR_ARG when this path does not apply (the caller then uses the SIMT path).
+cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, const double* U,
+                            const void* R, int r, double* cheb, double* fro, Arena& ar,
+                            cudaStream_t st) {
+    using namespace curk;
+    if (Am->dtype != CUR_F32 || (r != 32 && r != 64)) return CUR_ERR_ARG;
+    const int64_t m = Am->rows, n = Am->cols;
+    if ((m + kTcBM - 1) / kTcBM > INT_MAX / kTcBM || (n + kTcBN - 1) / kTcBN > INT_MAX / kTcBN) return CUR_ERR_ARG;
+    const int ldk = (r + 3) / 4 * 4;           // 16-byte row pitch for the tensor maps
+    const int nch = (r + 31) / 32;
+    float* Wh = ar.get<float>((size_t)n * ldk);
+    float* Wl = ar.get<float>((size_t)n * ldk);
+    float* Ch = ar.get<float>((size_t)m * ldk);
+    float* Cl = ar.get<float>((size_t)m * ldk);
+    const int G = h->num_sms;
+    double* part = ar.get<double>((size_t)G * 4);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUtensorMap mWh, mWl, mCh, mCl;
+    if (!make_map(&mWh, Wh, n, r, ldk) || !make_map(&mWl, Wl, n, r, ldk) || !make_map(&mCh, Ch, m, r, ldk) ||
+        !make_map(&mCl, Cl, m, r, ldk))
+        return CUR_ERR_ARG;
+    const size_t smw = (size_t)r * r * sizeof(double);
+    CUR_CK(cudaFuncSetAttribute((const void*)tc_prep_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    tc_prep_w<float><<<nbk(n), 256, smw, st>>>(U, static_cast<const float*>(R), r, n, ldk, Wh, Wl);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    tc_prep_c<float><<<nbk(m * ldk), 256, 0, st>>>(static_cast<const float*>(C), m, r, ldk, Ch, Cl);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    TcArgs a{};
+    a.A = static_cast<const float*>(Am->data);
+    a.m = m;
+    a.n = n;
+    a.ld = Am->ld;
+    a.r = r;
+    a.nch = nch;
+    a.ksteps = (r + 7) / 8;
+    a.ntile_n = (n + kTcBN - 1) / kTcBN;
+    a.ntiles = ((m + kTcBM - 1) / kTcBM) * a.ntile_n;
+    a.part = part;
+    a.status = h->status;
+    const int grid = (int)std::min<int64_t>(G, a.ntiles);
+    const size_t sm = (size_t)6 * nch * kChunk + 1024;
+    CUR_CK(cudaFuncSetAttribute((const void*)residual_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    residual_tc_k<<<grid, 320, sm, st>>>(mWh, mWl, mCh, mCl, a);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    tc_final_k<<<1, 256, 0, st>>>(part, grid, cheb, fro, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}

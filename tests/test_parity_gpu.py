@@ -288,3 +288,26 @@ def test_cross_nonfinite(dev, handle):
     with pytest.raises(cur.CurError):
         cur.cur_cross(handle, A, 8, 2, 2, cur.opts(), I, J)
     sync(handle)
+
+
+@pytest.mark.parametrize("m,n,r", [(1000, 700, 32), (1000, 700, 64), (300, 2050, 64), (129, 129, 32)])
+def test_residual_tensor_core_path_matches_oracle(dev, handle, m, n, r):
+    """FP32 data with r = 32 or 64 runs the tcgen05 residual (3xTF32); tiles are ragged."""
+    a = wl.lowrank_plus_noise(m, n, 0.9 ** np.arange(min(m, n) - 1), 1e-3, seed=m + n + r).astype(np.float32)
+    J, _ = orc.aca_select(a, 1, r, 1)
+    I, _ = orc.aca_select(a[:, J], 0, r, 1)
+    C_ref, U_ref, R_ref, _, _ = orc.assemble(a, I, J)
+    cheb_ref, fro_ref = orc.residual(a, C_ref, U_ref, R_ref)
+    A = to_dev(a, dev)
+    C = torch.empty((m, r), dtype=torch.float32, device=dev)
+    R = torch.empty((r, n), dtype=torch.float32, device=dev)
+    U = torch.empty((r, r), dtype=torch.float64, device=dev)
+    rc = torch.empty(1, dtype=torch.float64, device=dev)
+    cur.cur_assemble(handle, A, torch.tensor(I, dtype=torch.int32, device=dev),
+                     torch.tensor(J, dtype=torch.int32, device=dev), r, C, U, R, rc)
+    cheb = torch.empty(1, dtype=torch.float64, device=dev)
+    fro = torch.empty(1, dtype=torch.float64, device=dev)
+    cur.cur_residual_cheb(handle, A, C, U, R, r, cheb, fro)
+    assert sync(handle) == cur.CUR_OK
+    assert abs(cheb.item() - cheb_ref) <= 1e-5 * np.abs(a).max()
+    assert fro.item() == pytest.approx(fro_ref, rel=1e-3)
