@@ -7,6 +7,7 @@
 #include <math.h>
 
 #include "cur.h"
+#include "df64.cuh"
 
 namespace curk {
 
@@ -236,9 +237,10 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
                                           double thresh, double* logabsdet) {
     __shared__ int s_p, s_sing;
-    __shared__ double s_d, s_lv;
+    __shared__ double s_d;
+    __shared__ LogAcc s_lacc;   // log|det| without a logarithm per step
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) { s_sing = 0; s_lv = 0.0; }
+    if (tid == 0) { s_sing = 0; s_lacc.init(); }
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (tid < 32) {
@@ -269,7 +271,7 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
             const double d = A[k * r + k];
             s_d = d;
             if (!(fabs(d) > thresh)) s_sing = 1;
-            s_lv += log(fabs(d));
+            else s_lacc.mul(df_from_d(d));
         }
         __syncthreads();
         if (s_sing) return 1;
@@ -300,7 +302,7 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
             }
         __syncthreads();
     }
-    if (logabsdet) *logabsdet = s_lv;
+    if (logabsdet) *logabsdet = s_lacc.log_value();
     return 0;
 }
 

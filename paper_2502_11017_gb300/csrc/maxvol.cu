@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace curk {
@@ -47,6 +48,7 @@ struct MvProb {
 struct MvArgs {
     const void* basis;  // rows x r (compute type), contiguous
     double* minv64;     // P x r x r: FP64 M^-1 of each problem
+    float* mdf;         // P x 2 r^2: double-float working copy when r > kMsMax (FP32 data)
     const MvProb* prob;
     int P, r;
     double delta;
@@ -379,11 +381,15 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
 
 // ---------------------------------------------------------------- the swap iteration
 
+// The first CTA of a group keeps M^-1 (FP64) in shared memory when r <= kMsMax.
+constexpr int kMsMax = 64;
+
 template <typename TB>
 struct EngineSmem {
     static size_t bytes(int nloc, int r) {
         size_t b = ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
-        b = (b + 15) / 16 * 16 + (size_t)7 * r * sizeof(double) + 64;
+        b = (b + 15) / 16 * 16 + (size_t)8 * r * sizeof(double) + 64;
+        if (r <= kMsMax) b += (size_t)r * r * sizeof(double);
         return b;
     }
 };
@@ -407,6 +413,125 @@ __device__ __forceinline__ void engine_scan(const TB* Bs, int nloc, int r, int l
     nan = bad;
 }
 
+// The first CTA's copy of M^-1 and its Sherman-Morrison update. For FP32/BF16 data it
+// is kept in double-float (two FP32 words per entry, error-free transformations on the
+// FP32 pipes; GB300's FP64 units run at ~1/64 of FP32 with 64-cycle latency); for
+// FP64 data it stays in FP64. |det| is tracked as mantissa * 2^exponent.
+template <typename TB>
+struct MinvKeeper;
+
+template <>
+struct MinvKeeper<float> {
+    float* Mh;
+    float* Ml;
+    df64* crow;   // r: C(i*,:)
+    df64* brow;   // r: row i* of B
+    df64* cj;     // r: column j* of M^-1, then divided by B(i*,j*)
+    df64* red;    // 4 r
+    LogAcc lacc;
+    __device__ void setup(unsigned char* base, int r, double* Mg, bool in_smem, float* gdf) {
+        crow = reinterpret_cast<df64*>(base);
+        brow = crow + r;
+        cj = brow + r;
+        red = cj + r;
+        Mh = in_smem ? reinterpret_cast<float*>(red + 4 * r) : gdf;
+        Ml = Mh + r * r;
+        lacc.init();
+    }
+    __device__ void load(const double* Mg, int r) {
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const df64 v = df_from_d(Mg[e]);
+            Mh[e] = v.h;
+            Ml[e] = v.l;
+        }
+    }
+    __device__ void store(double* Mg, int r) const {
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) Mg[e] = df_to_d(df64{Mh[e], Ml[e]});
+    }
+    __device__ float value(int e) const { return __fadd_rn(Mh[e], Ml[e]); }
+    // winner (i*, j*) with C row `ci`: updates M^-1 and the |det| product
+    __device__ void swap(const float* ci, int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        for (int c = tid; c < r; c += nt) crow[c] = df64{ci[c], 0.f};
+        __syncthreads();
+        for (int it = tid; it < 4 * r; it += nt) {
+            const int c = it % r, qt = it / r;
+            df64 s{0.f, 0.f};
+            for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k)
+                s = df_add(s, df_mul_f(df64{Mh[k * r + c], Ml[k * r + c]}, crow[k].h));
+            red[qt * r + c] = s;
+        }
+        for (int k = tid; k < r; k += nt) cj[k] = df64{Mh[k * r + jstar], Ml[k * r + jstar]};
+        __syncthreads();
+        for (int c = tid; c < r; c += nt)
+            brow[c] = df_add(df_add(df_add(red[c], red[r + c]), red[2 * r + c]), red[3 * r + c]);
+        __syncthreads();
+        const df64 bb = brow[jstar];
+        for (int k = tid; k < r; k += nt) cj[k] = df_div(cj[k], bb);
+        __syncthreads();
+        // M^-1 <- M^-1 - (M^-1(:,j) / B_ij) (B(i,:) - e_j^T)
+        Walk2 w(tid, nt, r);
+        for (int e = tid; e < r * r; e += nt, w.next()) {
+            const df64 wv = w.c == jstar ? df_sub(brow[w.c], df64{1.f, 0.f}) : brow[w.c];
+            const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[w.i], wv));
+            Mh[e] = mv.h;
+            Ml[e] = mv.l;
+        }
+        if (tid == 0) lacc.mul(bb);
+    }
+    __device__ double dlog() const { return lacc.log_value(); }
+};
+
+template <>
+struct MinvKeeper<double> {
+    double* M;
+    double* crow;
+    double* brow;
+    double* cj;
+    double* red;
+    LogAcc lacc;
+    __device__ void setup(unsigned char* base, int r, double* Mg, bool in_smem, float*) {
+        crow = reinterpret_cast<double*>(base);
+        brow = crow + r;
+        cj = brow + r;
+        red = cj + r;
+        M = in_smem ? red + 4 * r : Mg;
+        lacc.init();
+    }
+    __device__ void load(const double* Mg, int r) {
+        if (M != Mg)
+            for (int e = threadIdx.x; e < r * r; e += blockDim.x) M[e] = Mg[e];
+    }
+    __device__ void store(double* Mg, int r) const {
+        if (M != Mg)
+            for (int e = threadIdx.x; e < r * r; e += blockDim.x) Mg[e] = M[e];
+    }
+    __device__ double value(int e) const { return M[e]; }
+    __device__ void swap(const double* ci, int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        for (int c = tid; c < r; c += nt) crow[c] = ci[c];
+        __syncthreads();
+        for (int it = tid; it < 4 * r; it += nt) {
+            const int c = it % r, qt = it / r;
+            double s = 0.0;
+            for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k) s = fma(crow[k], M[k * r + c], s);
+            red[qt * r + c] = s;
+        }
+        for (int k = tid; k < r; k += nt) cj[k] = M[k * r + jstar];
+        __syncthreads();
+        for (int c = tid; c < r; c += nt) brow[c] = ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
+        __syncthreads();
+        const double bb = brow[jstar];
+        Walk2 w(tid, nt, r);
+        for (int e = tid; e < r * r; e += nt, w.next()) {
+            const double wv = brow[w.c] - (w.c == jstar ? 1.0 : 0.0);
+            M[e] -= cj[w.i] * wv / bb;
+        }
+        if (tid == 0) lacc.mul(df_from_d(bb));
+    }
+    __device__ double dlog() const { return lacc.log_value(); }
+};
+
 template <typename TB>
 __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -415,25 +540,27 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     if (a.done[pb]) return;
     const MvProb pr = a.prob[pb];
     const int r = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
+    const bool solo = G == 1;                   // one CTA: no inter-CTA exchange at all
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
     TB* Bs = reinterpret_cast<TB*>(smem_raw);   // nloc x r slice of B
     TB* Mi = Bs + (size_t)nloc * r;             // r x r: M^-1 in the compute type
     TB* colj = Mi + (size_t)r * r;              // nloc
     TB* wrow = colj + nloc;                     // r: winning row of B, then B(i,:) - e_j
     size_t off = (((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB) + 15) / 16 * 16;
-    double* crow = reinterpret_cast<double*>(smem_raw + off);   // r: C(i*,:)
-    double* b64 = crow + r;                                     // r: FP64 row of B
-    double* cj64 = b64 + r;                                     // r: column j* of M^-1
-    double* red = cj64 + r;                                     // 4 r
+    double* Mg = a.minv64 + (int64_t)pb * r * r;                // M^-1 in global memory (FP64)
     __shared__ double s_b;
     __shared__ long long s_w;
     __shared__ int s_nan;
-    __shared__ double s_lv;
+    __shared__ MinvKeeper<TB> keep;
     TB* pub = static_cast<TB*>(a.pub);
     const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
-    double* Minv = a.minv64 + (int64_t)pb * r * r;
     const int myslot = pr.group0 + part;
-    if (tid == 0) s_lv = a.logvol[pb];
+    if (part == 0) {
+        if (tid == 0)
+            keep.setup(smem_raw + off, r, Mg, r <= kMsMax, a.mdf ? a.mdf + (int64_t)pb * 2 * r * r : nullptr);
+        __syncthreads();
+        keep.load(Mg, r);
+    }
 
     double bv;
     long long bi;
@@ -442,6 +569,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     unsigned epoch = 0;
     int fin = 0, fstat = CUR_OK;
     auto publish = [&](int pp) {
+        if (solo) return;
         if (tid == 0) {
             a.keyv[myslot * 2 + pp] = bv;
             a.keyi[myslot * 2 + pp] = nan ? -2LL : bi;
@@ -453,7 +581,12 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     };
     while (true) {
         // refresh: B slice = C slice M^-1
-        for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)Minv[e];
+        __syncthreads();
+        if (part == 0) {
+            for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)keep.value(e);
+        } else {
+            for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)Mg[e];
+        }
         __syncthreads();
         {
             const TB* Cs = basis + (int64_t)lo * r;
@@ -472,24 +605,29 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         publish(par);
         int made = 0;
         while (true) {
-            ++epoch;
-            if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
-            if (tid < 32) {
-                double wv = -INFINITY;
-                long long wi = LLONG_MAX;
-                int anynan = 0;
-                for (int g = tid; g < G; g += 32) {
-                    const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
-                    const double kv = a.keyv[(pr.group0 + g) * 2 + par];
-                    if (ki == -2LL) anynan = 1;
-                    else if (better(kv, ki, wv, wi)) { wv = kv; wi = ki; }
-                }
-                anynan = __any_sync(0xffffffffu, anynan);
-                warp_argmax(wv, wi);
-                if (tid == 0) {
-                    s_nan = anynan;
-                    s_w = wi;
-                    s_b = wv;
+            if (solo) {
+                // the CTA's own argmax is the group's
+                if (tid == 0) { s_nan = nan; s_w = bi; s_b = bv; }
+            } else {
+                ++epoch;
+                if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+                if (tid < 32) {
+                    double wv = -INFINITY;
+                    long long wi = LLONG_MAX;
+                    int anynan = 0;
+                    for (int g = tid; g < G; g += 32) {
+                        const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
+                        const double kv = a.keyv[(pr.group0 + g) * 2 + par];
+                        if (ki == -2LL) anynan = 1;
+                        else if (better(kv, ki, wv, wi)) { wv = kv; wi = ki; }
+                    }
+                    anynan = __any_sync(0xffffffffu, anynan);
+                    warp_argmax(wv, wi);
+                    if (tid == 0) {
+                        s_nan = anynan;
+                        s_w = wi;
+                        s_b = wv;
+                    }
                 }
             }
             __syncthreads();
@@ -500,37 +638,15 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
             if (total >= a.max_swaps) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
             const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
             const int owner = istar / pr.rpc;
-            const TB* wsrc = pub + ((int64_t)(pr.group0 + owner) * 2 + par) * r;
+            const TB* wsrc = solo ? Bs + (size_t)(istar - lo) * r
+                                  : pub + ((int64_t)(pr.group0 + owner) * 2 + par) * r;
             for (int c = tid; c < r; c += nt) wrow[c] = wsrc[c];
-            if (part == 0)
-                for (int c = tid; c < r; c += nt) crow[c] = to_d(basis[(int64_t)istar * r + c]);
             __syncthreads();
             const TB b = wrow[jstar];
             for (int i = tid; i < nloc; i += nt) colj[i] = Bs[i * r + jstar] / b;
             if (part == 0) {
-                // FP64 row of B: b64 = C(i*,:) M^-1, four partial sums per column in fixed order
-                for (int it = tid; it < 4 * r; it += nt) {
-                    const int c = it % r, qt = it / r;
-                    double s = 0.0;
-                    for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k) s = fma(crow[k], Minv[k * r + c], s);
-                    red[qt * r + c] = s;
-                }
-                for (int k = tid; k < r; k += nt) cj64[k] = Minv[k * r + jstar];
-                __syncthreads();
-                for (int c = tid; c < r; c += nt)
-                    b64[c] = ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
-                __syncthreads();
-                const double bb = b64[jstar];
-                // M^-1 <- M^-1 - M^-1(:,j) (B(i,:) - e_j^T) / B_ij
-                for (int e = tid; e < r * r; e += nt) {
-                    const int k = e / r, c = e - k * r;
-                    const double w = b64[c] - (c == jstar ? 1.0 : 0.0);
-                    Minv[e] -= cj64[k] * w / bb;
-                }
-                if (tid == 0) {
-                    a.S[(int64_t)pb * r + jstar] = istar;
-                    s_lv += log(fabs(bb));
-                }
+                keep.swap(basis + (int64_t)istar * r, r, jstar);
+                if (tid == 0) a.S[(int64_t)pb * r + jstar] = istar;
             }
             if (tid == 0) wrow[jstar] = wrow[jstar] - (TB)1;
             __syncthreads();
@@ -561,16 +677,26 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         }
         if (fin != 2) break;
         // every CTA refreshes from the M^-1 that the first CTA has finished updating
-        ++epoch;
-        if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+        if (part == 0 && !solo) {
+            __syncthreads();
+            keep.store(Mg, r);
+        }
+        if (!solo) {
+            ++epoch;
+            if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+        }
         fin = 0;
     }
-    if (part == 0 && tid == 0) {
-        a.swaps[pb] = total;
-        a.logvol[pb] = s_lv;
-        a.done[pb] = 1;
-        a.pstatus[pb] = fin == 1 ? CUR_OK : fstat;
-        if (fin == 3 && fstat != CUR_ERR_NOCONV) set_status(a.status, fstat);
+    if (part == 0) {
+        __syncthreads();
+        keep.store(Mg, r);
+        if (tid == 0) {
+            a.swaps[pb] = total;
+            a.logvol[pb] += keep.dlog();
+            a.done[pb] = 1;
+            a.pstatus[pb] = fin == 1 ? CUR_OK : fstat;
+            if (fin == 3 && fstat != CUR_ERR_NOCONV) set_status(a.status, fstat);
+        }
     }
 }
 
@@ -671,6 +797,7 @@ struct Stage {
     int32_t* dtab = nullptr;   // cta_prob | cta_part | lu_mask
     int32_t* S = nullptr;      // P x r
     double* minv64 = nullptr;  // P x r x r
+    float* mdf = nullptr;      // P x 2 r^2 (r > kMsMax only)
     double* logvol = nullptr;
     int32_t* swaps = nullptr;
     int32_t* pstatus = nullptr;
@@ -692,10 +819,14 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     for (auto& pr : sg.probs) tot_p += pr.p;
     int slots = 0;
     for (auto& pr : sg.probs) {
+        // one CTA when the problem fits (no inter-CTA exchange); otherwise spread large
+        // problems over the SMs in proportion to their size
         int64_t G = (pr.p + cap - 1) / cap;
-        const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
-                                                 (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
-        G = std::max<int64_t>(G, std::max<int64_t>(1, spread));
+        if (G > 1) {
+            const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
+                                                     (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
+            G = std::max<int64_t>(G, spread);
+        }
         const int rpc = (int)((pr.p + G - 1) / G);
         G = (pr.p + rpc - 1) / rpc;
         pr.G = (int)G;
@@ -709,6 +840,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     sg.dtab = ar.get<int32_t>((size_t)2 * slots + P);
     sg.S = ar.get<int32_t>((size_t)P * r);
     sg.minv64 = ar.get<double>((size_t)P * r * r);
+    sg.mdf = r > kMsMax ? ar.get<float>((size_t)P * 2 * r * r) : nullptr;
     sg.logvol = ar.get<double>(P);
     sg.swaps = ar.get<int32_t>(P);
     sg.pstatus = ar.get<int32_t>(P);
@@ -752,6 +884,7 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     MvArgs a{};
     a.basis = basis;
     a.minv64 = sg.minv64;
+    a.mdf = sg.mdf;
     a.prob = sg.dprob;
     a.P = P;
     a.r = r;
