@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.h"
 
 namespace curk {
@@ -170,11 +171,13 @@ struct AcaParams {
     double* nu;
     unsigned char* mask;
     double* W;             // r x nsel: W(k, j) = q_k^T a_j
-    double* Q;             // r x len (column k contiguous): orthonormal directions
+    double* Q;             // r x len (column k contiguous): orthonormal directions; for
+                           // FP32/BF16 data the same bytes hold them as double-float
+                           // (r x len high words, then r x len low words)
     double* q64;
     float* qh;
     float* ql;
-    double* v;             // len
+    double* v;             // len (double-float pairs for FP32/BF16 data)
     double* red1;          // G x r
     double* red2;          // G
     double* redf;          // G
@@ -278,80 +281,180 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     }
     const int64_t p = pi;
 
-    // P1b: v = a_p - Q(:, :k) W(:k, p) on this CTA's slice, and Q^T v partials.
-    for (int kk = tid; kk < k; kk += nt) s_w[kk] = P.W[(int64_t)kk * P.nsel + p];
-    __syncthreads();
-    const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
-    const int r = P.r;
-    const int64_t len = P.len;
-    for (int64_t i = i0 + tid; i < i1; i += nt) {
-        double s = 0.0;
-        for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
-        P.v[i] = pivot_elem<TA>(P, i, p) - s;
-    }
-    __syncthreads();
-    {
-        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-        for (int kk = warp; kk < k; kk += nw) {
-            const double* qk = P.Q + (int64_t)kk * len;
-            double acc = 0.0;
-            for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(qk[i], P.v[i], acc);
-            acc = warp_sum(acc);
-            if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
+    if constexpr (!std::is_same<TA, double>::value) {
+        // Double-float form (FP32/BF16 data): the same Gram-Schmidt steps on the FP32
+        // pipes; Q and v are stored as (high, low) FP32 pairs.
+        const int64_t len = P.len;
+        const int r = P.r;
+        float* Qh = reinterpret_cast<float*>(P.Q);
+        float* Ql = Qh + (int64_t)r * len;
+        float* vh = reinterpret_cast<float*>(P.v);
+        float* vl = vh + len;
+        __shared__ df64 s_df[128];
+        const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
+        for (int kk = tid; kk < k; kk += nt) s_df[kk] = df_from_d(P.W[(int64_t)kk * P.nsel + p]);
+        __syncthreads();
+        // P1b: v = a_p - Q W(:,p)
+        // acc -= sum_kk Q(kk, i) s(kk), the loads of 16 directions issued together
+        auto qsub = [&](int64_t i, df64 acc) {
+            for (int kk0 = 0; kk0 < k; kk0 += 16) {
+                float h[16], l[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const bool ok = kk0 + u < k;
+                    h[u] = ok ? Qh[(int64_t)(kk0 + u) * len + i] : 0.f;
+                    l[u] = ok ? Ql[(int64_t)(kk0 + u) * len + i] : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u)
+                    if (kk0 + u < k) acc = df_sub(acc, df_mul(df64{h[u], l[u]}, s_df[kk0 + u]));
+            }
+            return acc;
+        };
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            const df64 acc = qsub(i, df64{(float)pivot_elem<TA>(P, i, p), 0.f});
+            vh[i] = acc.h;
+            vl[i] = acc.l;
         }
-    }
-    if (!group_barrier(P.bar, 2u * G, P.status)) return;
-
-    // P2: second Gram-Schmidt pass v -= Q (Q^T v); partial ||v||^2.
-    {
-        const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-        for (int kk = warp; kk < k; kk += nw) {
-            const double s = warp_sum_strided(P.red1 + kk, G, r);
-            if (lane == 0) s_w[kk] = s;
+        __syncthreads();
+        {
+            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            for (int kk = warp; kk < k; kk += nw) {
+                df64 acc{0.f, 0.f};
+                const float* qhk = Qh + (int64_t)kk * len;
+                const float* qlk = Ql + (int64_t)kk * len;
+#pragma unroll 4
+                for (int64_t i = i0 + lane; i < i1; i += 32)
+                    acc = df_add(acc, df_mul(df64{qhk[i], qlk[i]}, df64{vh[i], vl[i]}));
+                double d = df_to_d(acc);
+                d = warp_sum(d);
+                if (lane == 0) P.red1[(int64_t)g * r + kk] = d;
+            }
         }
-    }
-    __syncthreads();
-    double nv = 0.0;
-    for (int64_t i = i0 + tid; i < i1; i += nt) {
-        double s = 0.0;
-        for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
-        const double vi = P.v[i] - s;
-        P.v[i] = vi;
-        nv = fma(vi, vi, nv);
-    }
-    nv = block_sum(nv);
-    if (tid == 0) P.red2[g] = nv;
-    if (!group_barrier(P.bar, 3u * G, P.status)) return;
-
-    // P3: the residual norm of the pick, recomputed (||v||^2 after two Gram-Schmidt
-    // passes), decides an early stop exactly as the explicit residual would:
-    // ||v||^2 <= (max(m,n) eps)^2 ||A||_F^2 ends the selection before recording p.
-    // Otherwise p is recorded and q_k = v / ||v||.
-    if (tid < 32) {
-        const double s = warp_sum_strided(P.red2, G);
-        if (tid == 0) s_tot = s;
-    }
-    __syncthreads();
-    const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
-    if (!(s_tot > mx * mx * (*P.frob2))) {
-        if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
+        if (!group_barrier(P.bar, 2u * G, P.status)) return;
+        // P2: second pass v -= Q (Q^T v); partial ||v||^2
+        {
+            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            for (int kk = warp; kk < k; kk += nw) {
+                const double sk = warp_sum_strided(P.red1 + kk, G, r);
+                if (lane == 0) s_df[kk] = df_from_d(sk);
+            }
+        }
+        __syncthreads();
+        double nv = 0.0;
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            const df64 acc = qsub(i, df64{vh[i], vl[i]});
+            vh[i] = acc.h;
+            vl[i] = acc.l;
+            nv += df_to_d(df_mul(acc, acc));
+        }
+        nv = block_sum(nv);
+        if (tid == 0) P.red2[g] = nv;
+        if (!group_barrier(P.bar, 3u * G, P.status)) return;
+        // P3: early-stop test on the recomputed norm, record p, q_k = v / ||v||
+        if (tid < 32) {
+            const double sv = warp_sum_strided(P.red2, G);
+            if (tid == 0) s_tot = sv;
+        }
+        __syncthreads();
+        const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
+        if (!(s_tot > mx * mx * (*P.frob2))) {
+            if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
+            return;
+        }
+        if (g == 0 && tid == 0) {
+            P.idx_out[k] = (int)p;
+            P.mask[p] = 1;
+            *P.count = k + 1;
+        }
+        if (!build) return;
+        if (tid == 0) s_df[0] = df_from_d(1.0 / sqrt(s_tot));
+        __syncthreads();
+        const df64 inv = s_df[0];
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            const df64 q = df_mul(df64{vh[i], vl[i]}, inv);
+            Qh[(int64_t)k * len + i] = q.h;
+            Ql[(int64_t)k * len + i] = q.l;
+            P.qh[i] = q.h;
+            P.ql[i] = q.l;
+        }
         return;
-    }
-    if (g == 0 && tid == 0) {
-        P.idx_out[k] = (int)p;
-        P.mask[p] = 1;
-        *P.count = k + 1;
-    }
-    if (!build) return;
-    const double inv = 1.0 / sqrt(s_tot);
-    for (int64_t i = i0 + tid; i < i1; i += nt) {
-        const double q = P.v[i] * inv;
-        P.Q[(int64_t)k * len + i] = q;
-        P.q64[i] = q;
-        float hi, lo;
-        split_d(q, hi, lo);
-        P.qh[i] = hi;
-        P.ql[i] = lo;
+    } else {
+    // P1b: v = a_p - Q(:, :k) W(:k, p) on this CTA's slice, and Q^T v partials.
+        for (int kk = tid; kk < k; kk += nt) s_w[kk] = P.W[(int64_t)kk * P.nsel + p];
+        __syncthreads();
+        const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
+        const int r = P.r;
+        const int64_t len = P.len;
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            double s = 0.0;
+            for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
+            P.v[i] = pivot_elem<TA>(P, i, p) - s;
+        }
+        __syncthreads();
+        {
+            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            for (int kk = warp; kk < k; kk += nw) {
+                const double* qk = P.Q + (int64_t)kk * len;
+                double acc = 0.0;
+                for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(qk[i], P.v[i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
+            }
+        }
+        if (!group_barrier(P.bar, 2u * G, P.status)) return;
+
+        // P2: second Gram-Schmidt pass v -= Q (Q^T v); partial ||v||^2.
+        {
+            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+            for (int kk = warp; kk < k; kk += nw) {
+                const double s = warp_sum_strided(P.red1 + kk, G, r);
+                if (lane == 0) s_w[kk] = s;
+            }
+        }
+        __syncthreads();
+        double nv = 0.0;
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            double s = 0.0;
+            for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
+            const double vi = P.v[i] - s;
+            P.v[i] = vi;
+            nv = fma(vi, vi, nv);
+        }
+        nv = block_sum(nv);
+        if (tid == 0) P.red2[g] = nv;
+        if (!group_barrier(P.bar, 3u * G, P.status)) return;
+
+        // P3: the residual norm of the pick, recomputed (||v||^2 after two Gram-Schmidt
+        // passes), decides an early stop exactly as the explicit residual would:
+        // ||v||^2 <= (max(m,n) eps)^2 ||A||_F^2 ends the selection before recording p.
+        // Otherwise p is recorded and q_k = v / ||v||.
+        if (tid < 32) {
+            const double s = warp_sum_strided(P.red2, G);
+            if (tid == 0) s_tot = s;
+        }
+        __syncthreads();
+        const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
+        if (!(s_tot > mx * mx * (*P.frob2))) {
+            if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_WARN_RANK); }
+            return;
+        }
+        if (g == 0 && tid == 0) {
+            P.idx_out[k] = (int)p;
+            P.mask[p] = 1;
+            *P.count = k + 1;
+        }
+        if (!build) return;
+        const double inv = 1.0 / sqrt(s_tot);
+        for (int64_t i = i0 + tid; i < i1; i += nt) {
+            const double q = P.v[i] * inv;
+            P.Q[(int64_t)k * len + i] = q;
+            P.q64[i] = q;
+            float hi, lo;
+            split_d(q, hi, lo);
+            P.qh[i] = hi;
+            P.ql[i] = lo;
+        }
     }
 }
 

@@ -260,52 +260,117 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
         if (s_stop) break;
         const int p = s_p;
         // new direction: v = c_p - Q Q^T c_p, twice (CGS2); its norm is the recomputed
-        // residual norm of row p, which decides an early stop before p is recorded
+        // residual norm of row p, which decides an early stop before p is recorded.
+        // FP32/BF16 data: double-float (Q, v and the dot products as FP32 pairs).
         const TB* cp = basis + (int64_t)p * r;
-        for (int c = tid; c < r; c += nt) v[c] = to_d(cp[c]);
-        __syncthreads();
-        for (int pass = 0; pass < 2; ++pass) {
-            for (int kk = warp; kk < k; kk += nw) {
+        if constexpr (std::is_same<TB, double>::value) {
+            for (int c = tid; c < r; c += nt) v[c] = to_d(cp[c]);
+            __syncthreads();
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int kk = warp; kk < k; kk += nw) {
+                    double s = 0.0;
+                    for (int c = lane; c < r; c += 32) s = fma(Q[kk * r + c], v[c], s);
+                    s = warp_sum(s);
+                    if (lane == 0) sd[kk] = s;
+                }
+                __syncthreads();
+                for (int it = tid; it < 4 * r; it += nt) {
+                    const int c = it % r, qt = it / r;
+                    double s = 0.0;
+                    for (int kk = k * qt / 4; kk < k * (qt + 1) / 4; ++kk) s = fma(Q[kk * r + c], sd[kk], s);
+                    red[qt * r + c] = s;
+                }
+                __syncthreads();
+                for (int c = tid; c < r; c += nt)
+                    v[c] -= ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
+                __syncthreads();
+            }
+            if (warp == 0) {
                 double s = 0.0;
-                for (int c = lane; c < r; c += 32) s = fma(Q[kk * r + c], v[c], s);
+                for (int c = lane; c < r; c += 32) s = fma(v[c], v[c], s);
                 s = warp_sum(s);
-                if (lane == 0) sd[kk] = s;
+                if (lane == 0) {
+                    const double mx = (double)max(pr.p, r) * kEps;
+                    s_stop = !(s > mx * mx * s_frob) ? 1 : 0;
+                    s_inv = 1.0 / sqrt(s);
+                }
             }
             __syncthreads();
-            for (int it = tid; it < 4 * r; it += nt) {
-                const int c = it % r, qt = it / r;
-                double s = 0.0;
-                for (int kk = k * qt / 4; kk < k * (qt + 1) / 4; ++kk) s = fma(Q[kk * r + c], sd[kk], s);
-                red[qt * r + c] = s;
+            if (s_stop) break;
+            if (part == 0 && tid == 0) Sout[k] = p;
+            if (p >= lo && p < hi && tid == 0) msk[p - lo] = 1;
+            picked = k + 1;
+            if (k == r - 1) break;
+            for (int c = tid; c < r; c += nt) {
+                const double q = v[c] * s_inv;
+                Q[k * r + c] = q;
+                v[c] = q;
+                split_d(q, qh[c], ql[c]);
             }
             __syncthreads();
-            for (int c = tid; c < r; c += nt)
-                v[c] -= ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
+        } else {
+            df64* Qd = reinterpret_cast<df64*>(Q);      // r x r pairs (same bytes as doubles)
+            df64* vd = reinterpret_cast<df64*>(v);
+            df64* sdd = reinterpret_cast<df64*>(sd);
+            df64* redd = reinterpret_cast<df64*>(red);
+            for (int c = tid; c < r; c += nt) vd[c] = df64{to_f(cp[c]), 0.f};
+            __syncthreads();
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int kk = warp; kk < k; kk += nw) {
+                    df64 s{0.f, 0.f};
+                    for (int c = lane; c < r; c += 32) s = df_add(s, df_mul(Qd[kk * r + c], vd[c]));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const df64 t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
+                        s = df_add(s, t);
+                    }
+                    if (lane == 0) sdd[kk] = s;
+                }
+                __syncthreads();
+                for (int it = tid; it < 4 * r; it += nt) {
+                    const int c = it % r, qt = it / r;
+                    df64 s{0.f, 0.f};
+                    for (int kk = k * qt / 4; kk < k * (qt + 1) / 4; ++kk) s = df_add(s, df_mul(Qd[kk * r + c], sdd[kk]));
+                    redd[qt * r + c] = s;
+                }
+                __syncthreads();
+                for (int c = tid; c < r; c += nt)
+                    vd[c] = df_sub(vd[c], df_add(df_add(df_add(redd[c], redd[r + c]), redd[2 * r + c]), redd[3 * r + c]));
+                __syncthreads();
+            }
+            if (warp == 0) {
+                df64 s{0.f, 0.f};
+                for (int c = lane; c < r; c += 32) s = df_add(s, df_mul(vd[c], vd[c]));
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const df64 t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
+                    s = df_add(s, t);
+                }
+                if (lane == 0) {
+                    const double sn = df_to_d(s);
+                    const double mx = (double)max(pr.p, r) * kEps;
+                    s_stop = !(sn > mx * mx * s_frob) ? 1 : 0;
+                    s_inv = 1.0 / sqrt(sn);
+                }
+            }
+            __syncthreads();
+            if (s_stop) break;
+            if (part == 0 && tid == 0) Sout[k] = p;
+            if (p >= lo && p < hi && tid == 0) msk[p - lo] = 1;
+            picked = k + 1;
+            if (k == r - 1) break;
+            if (tid == 0) sdd[0] = df_from_d(s_inv);
+            __syncthreads();
+            const df64 inv = sdd[0];
+            __syncthreads();
+            for (int c = tid; c < r; c += nt) {
+                const df64 q = df_mul(vd[c], inv);
+                Qd[k * r + c] = q;
+                qh[c] = q.h;
+                ql[c] = q.l;
+            }
             __syncthreads();
         }
-        if (warp == 0) {
-            double s = 0.0;
-            for (int c = lane; c < r; c += 32) s = fma(v[c], v[c], s);
-            s = warp_sum(s);
-            if (lane == 0) {
-                const double mx = (double)max(pr.p, r) * kEps;
-                s_stop = !(s > mx * mx * s_frob) ? 1 : 0;
-                s_inv = 1.0 / sqrt(s);
-            }
-        }
-        __syncthreads();
-        if (s_stop) break;
-        if (part == 0 && tid == 0) Sout[k] = p;
-        if (p >= lo && p < hi && tid == 0) msk[p - lo] = 1;
-        picked = k + 1;
-        if (k == r - 1) break;
-        for (int c = tid; c < r; c += nt) {
-            const double q = v[c] * s_inv;
-            Q[k * r + c] = q;
-            v[c] = q;
-            split_d(q, qh[c], ql[c]);
-        }
-        __syncthreads();
         // downdate: nu_i -= (c_i . q_k)^2
         rows_dot4<TB>(rows, nloc, r, v, qh, ql, 1, nu, true);
         __syncthreads();
@@ -589,13 +654,35 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         }
         __syncthreads();
         {
+            // C rows pass through shared memory a chunk at a time (coalesced loads), then
+            // B rows = C rows M^-1 with 8 outputs per thread in registers; the chunk's
+            // own rows of Bs serve as the staging area.
             const TB* Cs = basis + (int64_t)lo * r;
-            Walk2 w(tid, nt, r);
-            for (int e = tid; e < nloc * r; e += nt, w.next()) {
-                const TB* ci = Cs + (int64_t)w.i * r;
-                TB s = (TB)0;
-                for (int k = 0; k < r; ++k) s = fma(ci[k], Mi[k * r + w.c], s);
-                Bs[e] = s;
+            const int chunk = max(1, min(32, 8 * nt / r));
+            for (int i0 = 0; i0 < nloc; i0 += chunk) {
+                const int nr = min(chunk, nloc - i0);
+                TB* stage = Bs + (size_t)i0 * r;
+                for (int e = tid; e < nr * r; e += nt) stage[e] = Cs[(int64_t)i0 * r + e];
+                __syncthreads();
+                TB out[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + u * nt;
+                    TB sum = (TB)0;
+                    if (e < nr * r) {
+                        const int i = e / r, c = e - i * r;
+                        const TB* ci = stage + (size_t)i * r;
+                        for (int k = 0; k < r; ++k) sum = fma(ci[k], Mi[k * r + c], sum);
+                    }
+                    out[u] = sum;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = tid + u * nt;
+                    if (e < nr * r) stage[e] = out[u];
+                }
+                __syncthreads();
             }
         }
         __syncthreads();
