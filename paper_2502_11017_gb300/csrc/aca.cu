@@ -63,6 +63,29 @@ __device__ __forceinline__ void acc_add(Dot2& a, float x, int mode, double, floa
     if (mode == kNorm) a.add_sq(x); else a.add(x, qh, ql);
 }
 
+// Partial sums travel as FP64 for FP64 data and as double-float pairs otherwise.
+template <typename TA>
+using PartT = typename std::conditional<std::is_same<TA, double>::value, double, df64>::type;
+
+__device__ __forceinline__ df64 part_value(const Dot2& a) { return fast_two_sum(a.s, a.c); }
+__device__ __forceinline__ double part_value(const DotD& a) { return a.s; }
+__device__ __forceinline__ df64 part_add(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ double part_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double part_to_d(df64 a) { return df_to_d(a); }
+__device__ __forceinline__ double part_to_d(double a) { return a; }
+__device__ __forceinline__ df64 part_zero(df64) { return df64{0.f, 0.f}; }
+__device__ __forceinline__ double part_zero(double) { return 0.0; }
+__device__ __forceinline__ df64 shfl_xor(df64 v, int o) {
+    return df64{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = part_add(v, shfl_xor(v, o));
+    return v;
+}
+
 // part[rc * n + j] = sum over rows i of chunk rc of a_ij * q_i (kDot) or a_ij^2 (kNorm).
 // grid = (ceil(n / 128), RC), block = 256 (8 warps). Warp w takes rows r0 + w, r0 + w + 8,
 // ...; lane l takes the 4 columns 128 * blockIdx.x + 4 l .. + 3.
@@ -72,10 +95,11 @@ __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, i
                                                      const double* __restrict__ q64,
                                                      const float* __restrict__ qh,
                                                      const float* __restrict__ ql,
-                                                     double* __restrict__ part,
+                                                     PartT<TA>* __restrict__ part,
                                                      const int* __restrict__ stop) {
     using V = typename ValT<TA>::type;
-    __shared__ double red[8][128];
+    using PT = PartT<TA>;
+    __shared__ PT red[8][128];
     if (*stop) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t col = (int64_t)blockIdx.x * 128 + lane * 4;
@@ -115,15 +139,16 @@ __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, i
         for (int c = 0; c < 4; ++c) acc_add(acc[c], x[c], MODE, qd, h, l);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = acc[c].value();
+    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = part_value(acc[c]);
     __syncthreads();
     if (threadIdx.x < 128) {
         const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
         if (j < n) {
-            double s = 0.0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-            part[(int64_t)blockIdx.y * n + j] = s;
+            PT s0 = part_add(red[0][threadIdx.x], red[1][threadIdx.x]);
+            PT s1 = part_add(red[2][threadIdx.x], red[3][threadIdx.x]);
+            PT s2 = part_add(red[4][threadIdx.x], red[5][threadIdx.x]);
+            PT s3 = part_add(red[6][threadIdx.x], red[7][threadIdx.x]);
+            part[(int64_t)blockIdx.y * n + j] = part_add(part_add(s0, s1), part_add(s2, s3));
         }
     }
 }
@@ -134,7 +159,7 @@ __global__ void __launch_bounds__(256) aca_rows_pass(const TA* __restrict__ A, i
                                                      int64_t ld, const double* __restrict__ q64,
                                                      const float* __restrict__ qh,
                                                      const float* __restrict__ ql,
-                                                     double* __restrict__ out,
+                                                     PartT<TA>* __restrict__ out,
                                                      const int* __restrict__ stop) {
     using V = typename ValT<TA>::type;
     if (*stop) return;
@@ -156,7 +181,7 @@ __global__ void __launch_bounds__(256) aca_rows_pass(const TA* __restrict__ A, i
                 acc_add(acc, x[c], MODE, qd, h, l);
             }
         }
-        const double s = warp_sum(acc.value());
+        const PartT<TA> s = warp_sum_t(part_value(acc));
         if (lane == 0) out[row] = s;
     }
 }
@@ -166,11 +191,11 @@ struct AcaParams {
     int64_t m, n, ld;
     int axis, r;
     int64_t nsel, len;     // candidates (n for columns), vector length (m for columns)
-    const double* part;
+    const void* part;      // RC x nsel partials (PartT)
     int RC;
     double* nu;
     unsigned char* mask;
-    double* W;             // r x nsel: W(k, j) = q_k^T a_j
+    void* W;               // r x nsel: W(k, j) = q_k^T a_j (PartT)
     double* Q;             // r x len (column k contiguous): orthonormal directions; for
                            // FP32/BF16 data the same bytes hold them as double-float
                            // (r x len high words, then r x len low words)
@@ -178,7 +203,7 @@ struct AcaParams {
     float* qh;
     float* ql;
     double* v;             // len (double-float pairs for FP32/BF16 data)
-    double* red1;          // G x r
+    double* red1;          // G x r (double-float pairs for FP32/BF16 data)
     double* red2;          // G
     double* redf;          // G
     double* keyv;          // G
@@ -197,17 +222,43 @@ __device__ __forceinline__ double pivot_elem(const AcaParams& P, int64_t i, int6
     return P.axis == 1 ? to_d(A[i * P.ld + p]) : to_d(A[p * P.ld + i]);
 }
 
+// acc_a -= sum_kk Q(kk, ia) s(kk) and acc_b likewise for row ib, two interleaved chains
+// per row (even and odd kk) so that four independent dependency chains are in flight.
+__device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int64_t len, int k,
+                                          const df64* s, int64_t ia, int64_t ib, bool vb,
+                                          df64& acc_a, df64& acc_b) {
+    df64 a1{0.f, 0.f}, b1{0.f, 0.f};
+    const int64_t ibb = vb ? ib : ia;
+#pragma unroll 2
+    for (int kk = 0; kk < k; kk += 2) {
+        const bool two = kk + 1 < k;
+        const int64_t o0 = (int64_t)kk * len, o1 = two ? (int64_t)(kk + 1) * len : o0;
+        const df64 qa0{Qh[o0 + ia], Ql[o0 + ia]}, qb0{Qh[o0 + ibb], Ql[o0 + ibb]};
+        const df64 qa1{Qh[o1 + ia], Ql[o1 + ia]}, qb1{Qh[o1 + ibb], Ql[o1 + ibb]};
+        const df64 s0 = s[kk], s1 = two ? s[kk + 1] : df64{0.f, 0.f};
+        acc_a = df_sub(acc_a, df_mul(qa0, s0));
+        acc_b = df_sub(acc_b, df_mul(qb0, s0));
+        a1 = df_sub(a1, df_mul(qa1, s1));
+        b1 = df_sub(b1, df_mul(qb1, s1));
+    }
+    acc_a = df_add(acc_a, a1);
+    acc_b = df_add(acc_b, b1);
+}
+
 // One round of Algorithm 3 after its pass. `part` holds A^T q_t (t >= 0) or the
 // squared norms (t = -1). Picks index k = t + 1; with `build`, also forms q_k.
 // Cooperative launch; grid G <= co-resident CTAs, block 256.
 template <typename TA>
 __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) {
+    using PT = PartT<TA>;
     __shared__ double s_w[128];
-    __shared__ double s_q[4][64];
+    __shared__ PT s_q[4][64];
     __shared__ double s_tot;
     if (*P.stop) return;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
     const int k = t + 1;
+    const PT* part = static_cast<const PT*>(P.part);
+    PT* W = static_cast<PT*>(P.W);
 
     // P0: reduce partials, downdate squared norms, local argmax over unpicked. The RC
     // partials of each column are summed by 4 threads in fixed order (deterministic).
@@ -220,25 +271,31 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         const int lane64 = tid & 63, q4 = tid >> 6;   // 64 columns x 4 quarter-sums per pass
         for (int64_t jb = j0; jb < j1; jb += 64) {
             const int64_t j = jb + lane64;
-            double w = 0.0;
+            PT w0 = part_zero(PT{}), w1 = part_zero(PT{});
             if (j < j1) {
                 const int rc0 = P.RC * q4 / 4, rc1 = P.RC * (q4 + 1) / 4;
-                const double* src = P.part + j;
-#pragma unroll 4
-                for (int rc = rc0; rc < rc1; ++rc) w += src[(int64_t)rc * P.nsel];
+                const PT* src = part + j;
+                int rc = rc0;
+                for (; rc + 1 < rc1; rc += 2) {
+                    w0 = part_add(w0, src[(int64_t)rc * P.nsel]);
+                    w1 = part_add(w1, src[(int64_t)(rc + 1) * P.nsel]);
+                }
+                if (rc < rc1) w0 = part_add(w0, src[(int64_t)rc * P.nsel]);
             }
-            s_q[q4][lane64] = w;
+            s_q[q4][lane64] = part_add(w0, w1);
             __syncthreads();
             if (q4 == 0 && j < j1) {
-                w = ((s_q[0][lane64] + s_q[1][lane64]) + s_q[2][lane64]) + s_q[3][lane64];
+                const PT w = part_add(part_add(s_q[0][lane64], s_q[1][lane64]),
+                                      part_add(s_q[2][lane64], s_q[3][lane64]));
+                const double wd = part_to_d(w);
                 double nu;
                 if (t < 0) {
-                    nu = w;
-                    fs += w;
-                    if (!isfinite(w)) bad = 1;
+                    nu = wd;
+                    fs += wd;
+                    if (!isfinite(wd)) bad = 1;
                 } else {
-                    P.W[(int64_t)t * P.nsel + j] = w;
-                    nu = P.nu[j] - w * w;
+                    W[(int64_t)t * P.nsel + j] = w;
+                    nu = P.nu[j] - wd * wd;
                 }
                 P.nu[j] = nu;
                 if (!P.mask[j] && better(nu, (long long)j, bv, bi)) { bv = nu; bi = j; }
@@ -280,76 +337,87 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         return;
     }
     const int64_t p = pi;
+    const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
+    const int64_t len = P.len;
+    const int r = P.r;
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
 
     if constexpr (!std::is_same<TA, double>::value) {
-        // Double-float form (FP32/BF16 data): the same Gram-Schmidt steps on the FP32
-        // pipes; Q and v are stored as (high, low) FP32 pairs.
-        const int64_t len = P.len;
-        const int r = P.r;
+        // Double-float form (FP32/BF16 data): the Gram-Schmidt steps on the FP32 pipes;
+        // Q, v and the partial dot products are stored as (high, low) FP32 pairs.
         float* Qh = reinterpret_cast<float*>(P.Q);
         float* Ql = Qh + (int64_t)r * len;
         float* vh = reinterpret_cast<float*>(P.v);
         float* vl = vh + len;
+        df64* red1 = reinterpret_cast<df64*>(P.red1);
         __shared__ df64 s_df[128];
-        const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
-        for (int kk = tid; kk < k; kk += nt) s_df[kk] = df_from_d(P.W[(int64_t)kk * P.nsel + p]);
+        __shared__ df64 s_wred[8];
+        for (int kk = tid; kk < k; kk += nt) s_df[kk] = W[(int64_t)kk * P.nsel + p];
         __syncthreads();
-        // P1b: v = a_p - Q W(:,p)
-        // acc -= sum_kk Q(kk, i) s(kk), the loads of 16 directions issued together
-        auto qsub = [&](int64_t i, df64 acc) {
-            for (int kk0 = 0; kk0 < k; kk0 += 16) {
-                float h[16], l[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const bool ok = kk0 + u < k;
-                    h[u] = ok ? Qh[(int64_t)(kk0 + u) * len + i] : 0.f;
-                    l[u] = ok ? Ql[(int64_t)(kk0 + u) * len + i] : 0.f;
-                }
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    if (kk0 + u < k) acc = df_sub(acc, df_mul(df64{h[u], l[u]}, s_df[kk0 + u]));
-            }
-            return acc;
-        };
-        for (int64_t i = i0 + tid; i < i1; i += nt) {
-            const df64 acc = qsub(i, df64{(float)pivot_elem<TA>(P, i, p), 0.f});
-            vh[i] = acc.h;
-            vl[i] = acc.l;
+        // P1b: v = a_p - Q W(:,p), two rows per thread
+        for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
+            const int64_t ib = ia + nt;
+            const bool vb = ib < i1;
+            df64 acc_a{(float)pivot_elem<TA>(P, ia, p), 0.f};
+            df64 acc_b{vb ? (float)pivot_elem<TA>(P, ib, p) : 0.f, 0.f};
+            qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
+            vh[ia] = acc_a.h;
+            vl[ia] = acc_a.l;
+            if (vb) { vh[ib] = acc_b.h; vl[ib] = acc_b.l; }
         }
         __syncthreads();
-        {
-            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-            for (int kk = warp; kk < k; kk += nw) {
-                df64 acc{0.f, 0.f};
-                const float* qhk = Qh + (int64_t)kk * len;
-                const float* qlk = Ql + (int64_t)kk * len;
-#pragma unroll 4
-                for (int64_t i = i0 + lane; i < i1; i += 32)
-                    acc = df_add(acc, df_mul(df64{qhk[i], qlk[i]}, df64{vh[i], vl[i]}));
-                double d = df_to_d(acc);
-                d = warp_sum(d);
-                if (lane == 0) P.red1[(int64_t)g * r + kk] = d;
+        // partial dots Q^T v: one warp per direction, four interleaved chains per lane
+        for (int kk = warp; kk < k; kk += nw) {
+            const float* qhk = Qh + (int64_t)kk * len;
+            const float* qlk = Ql + (int64_t)kk * len;
+            df64 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+            for (int64_t i = i0 + lane; i < i1; i += 128) {
+                a0 = df_add(a0, df_mul(df64{qhk[i], qlk[i]}, df64{vh[i], vl[i]}));
+                if (i + 32 < i1) a1 = df_add(a1, df_mul(df64{qhk[i + 32], qlk[i + 32]}, df64{vh[i + 32], vl[i + 32]}));
+                if (i + 64 < i1) a2 = df_add(a2, df_mul(df64{qhk[i + 64], qlk[i + 64]}, df64{vh[i + 64], vl[i + 64]}));
+                if (i + 96 < i1) a3 = df_add(a3, df_mul(df64{qhk[i + 96], qlk[i + 96]}, df64{vh[i + 96], vl[i + 96]}));
             }
+            const df64 acc = warp_sum_t(df_add(df_add(a0, a1), df_add(a2, a3)));
+            if (lane == 0) red1[(int64_t)g * r + kk] = acc;
         }
         if (!group_barrier(P.bar, 2u * G, P.status)) return;
         // P2: second pass v -= Q (Q^T v); partial ||v||^2
-        {
-            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-            for (int kk = warp; kk < k; kk += nw) {
-                const double sk = warp_sum_strided(P.red1 + kk, G, r);
-                if (lane == 0) s_df[kk] = df_from_d(sk);
+        for (int kk = warp; kk < k; kk += nw) {
+            df64 a0{0.f, 0.f}, a1{0.f, 0.f};
+            int gg = lane;
+            for (; gg + 32 < G; gg += 64) {
+                a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
+                a1 = df_add(a1, red1[(int64_t)(gg + 32) * r + kk]);
             }
+            if (gg < G) a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
+            const df64 sk = warp_sum_t(df_add(a0, a1));
+            if (lane == 0) s_df[kk] = sk;
         }
         __syncthreads();
-        double nv = 0.0;
-        for (int64_t i = i0 + tid; i < i1; i += nt) {
-            const df64 acc = qsub(i, df64{vh[i], vl[i]});
-            vh[i] = acc.h;
-            vl[i] = acc.l;
-            nv += df_to_d(df_mul(acc, acc));
+        df64 nv{0.f, 0.f};
+        for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
+            const int64_t ib = ia + nt;
+            const bool vb = ib < i1;
+            df64 acc_a{vh[ia], vl[ia]};
+            df64 acc_b = vb ? df64{vh[ib], vl[ib]} : df64{0.f, 0.f};
+            qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
+            vh[ia] = acc_a.h;
+            vl[ia] = acc_a.l;
+            nv = df_add(nv, df_mul(acc_a, acc_a));
+            if (vb) {
+                vh[ib] = acc_b.h;
+                vl[ib] = acc_b.l;
+                nv = df_add(nv, df_mul(acc_b, acc_b));
+            }
         }
-        nv = block_sum(nv);
-        if (tid == 0) P.red2[g] = nv;
+        nv = warp_sum_t(nv);
+        if (lane == 0) s_wred[warp] = nv;
+        __syncthreads();
+        if (tid == 0) {
+            df64 s{0.f, 0.f};
+            for (int w = 0; w < nw; ++w) s = df_add(s, s_wred[w]);
+            P.red2[g] = df_to_d(s);
+        }
         if (!group_barrier(P.bar, 3u * G, P.status)) return;
         // P3: early-stop test on the recomputed norm, record p, q_k = v / ||v||
         if (tid < 32) {
@@ -378,39 +446,28 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
             P.qh[i] = q.h;
             P.ql[i] = q.l;
         }
-        return;
     } else {
-    // P1b: v = a_p - Q(:, :k) W(:k, p) on this CTA's slice, and Q^T v partials.
-        for (int kk = tid; kk < k; kk += nt) s_w[kk] = P.W[(int64_t)kk * P.nsel + p];
+        // FP64 data: the same steps in FP64.
+        const double* Wd = reinterpret_cast<const double*>(W);
+        for (int kk = tid; kk < k; kk += nt) s_w[kk] = Wd[(int64_t)kk * P.nsel + p];
         __syncthreads();
-        const int64_t i0 = P.len * g / G, i1 = P.len * (g + 1) / G;
-        const int r = P.r;
-        const int64_t len = P.len;
         for (int64_t i = i0 + tid; i < i1; i += nt) {
             double s = 0.0;
             for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
             P.v[i] = pivot_elem<TA>(P, i, p) - s;
         }
         __syncthreads();
-        {
-            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-            for (int kk = warp; kk < k; kk += nw) {
-                const double* qk = P.Q + (int64_t)kk * len;
-                double acc = 0.0;
-                for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(qk[i], P.v[i], acc);
-                acc = warp_sum(acc);
-                if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
-            }
+        for (int kk = warp; kk < k; kk += nw) {
+            const double* qk = P.Q + (int64_t)kk * len;
+            double acc = 0.0;
+            for (int64_t i = i0 + lane; i < i1; i += 32) acc = fma(qk[i], P.v[i], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
         }
         if (!group_barrier(P.bar, 2u * G, P.status)) return;
-
-        // P2: second Gram-Schmidt pass v -= Q (Q^T v); partial ||v||^2.
-        {
-            const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-            for (int kk = warp; kk < k; kk += nw) {
-                const double s = warp_sum_strided(P.red1 + kk, G, r);
-                if (lane == 0) s_w[kk] = s;
-            }
+        for (int kk = warp; kk < k; kk += nw) {
+            const double sk = warp_sum_strided(P.red1 + kk, G, r);
+            if (lane == 0) s_w[kk] = sk;
         }
         __syncthreads();
         double nv = 0.0;
@@ -424,14 +481,9 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         nv = block_sum(nv);
         if (tid == 0) P.red2[g] = nv;
         if (!group_barrier(P.bar, 3u * G, P.status)) return;
-
-        // P3: the residual norm of the pick, recomputed (||v||^2 after two Gram-Schmidt
-        // passes), decides an early stop exactly as the explicit residual would:
-        // ||v||^2 <= (max(m,n) eps)^2 ||A||_F^2 ends the selection before recording p.
-        // Otherwise p is recorded and q_k = v / ||v||.
         if (tid < 32) {
-            const double s = warp_sum_strided(P.red2, G);
-            if (tid == 0) s_tot = s;
+            const double sv = warp_sum_strided(P.red2, G);
+            if (tid == 0) s_tot = sv;
         }
         __syncthreads();
         const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
@@ -462,7 +514,7 @@ template <typename TA>
 static cur_status launch_pass(const AcaParams& P, int mode, int64_t chunk, int rc_count,
                               bool vec, cudaStream_t st) {
     const TA* A = static_cast<const TA*>(P.A);
-    double* part = const_cast<double*>(P.part);
+    PartT<TA>* part = static_cast<PartT<TA>*>(const_cast<void*>(P.part));
     if (P.axis == 1) {
         dim3 grid((unsigned)((P.n + 127) / 128), (unsigned)rc_count);
         if (mode == kNorm) {
@@ -513,7 +565,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
         RC = (int)((P.m + chunk - 1) / chunk);
     }
     P.RC = RC;
-    P.part = ar.get<double>((size_t)RC * P.nsel);
+    P.part = ar.get<double>((size_t)RC * P.nsel);   // PartT is 8 bytes either way
     P.nu = ar.get<double>(P.nsel);
     P.mask = ar.get<unsigned char>(P.nsel);
     P.W = ar.get<double>((size_t)r * P.nsel);
