@@ -601,7 +601,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
     note_launch();
     for (int t = -1; t <= r - 2; ++t) {
         if (t >= 0) {
-            const bool ev = h->prof && h->prof_n < 512;
+            const bool ev = h->prof && h->prof_n < 4096;
             if (ev) CUR_CK(cudaEventRecord(h->prof_ev[2 * h->prof_n], st));
             CUR_TRY(launch_pass<TA>(P, kDot, chunk, RC, vec, st));
             if (ev) CUR_CK(cudaEventRecord(h->prof_ev[2 * h->prof_n + 1], st));

@@ -47,7 +47,7 @@ struct cur_handle {
     // instrumentation: events around the Algorithm 3 pass launches
     int prof = 0;
     int prof_n = 0;
-    cudaEvent_t prof_ev[2 * 512] = {};
+    cudaEvent_t prof_ev[2 * 4096] = {};
     int device = 0;
     int num_sms = 0;
     char* ws = nullptr;          // device workspace
