@@ -204,6 +204,18 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- our arm
 
+def aggregate(ms_local: float, units_local: int, world: int, device=None):
+    """Slowest rank's time and the whole-job rate: (max ms over ranks, units of all ranks
+    per second). Every rank gets the same answer; one collective, no data exchange."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_local / (ms_max / 1000.0)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -274,11 +286,7 @@ def run_ours(args):
     st = cur.cur_sync_status(h)
     if st != cur.CUR_OK:
         raise RuntimeError(f"device status {st} in the timed region")
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = t.item()
-    value = world * args.steps / (ms_max / 1000.0)
+    ms_max, value = aggregate(ms, args.steps, world, dev)
 
     # end to end: A from pinned host memory each step, I, J and the residual back
     a_pin = torch.from_numpy(a_host).pin_memory()
@@ -300,10 +308,7 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    t2 = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-    e2e_value = world * e2e_steps / (t2.item() / 1000.0)
+    _e2e_max, e2e_value = aggregate(e2e_ms, e2e_steps, world, dev)
 
     inf = cur.info_from_tensor(info)
     peaks, kind = measured_peaks()

@@ -186,6 +186,13 @@ cur_status cur_prof_enable(cur_handle* h, int on);
 cur_status cur_prof_read(cur_handle* h, cudaStream_t stream, double* pass_ms,
                          int32_t* pass_launches, int64_t* kernel_launches);
 
+/* Self-test of the bounded device waits (no counterpart in the paper): launches one CTA
+ * that waits at a group barrier for a partner that does not exist. The wait gives up
+ * after ~50 ms and records CUR_ERR_TIMEOUT in the status word (read it with
+ * cur_sync_status); the context stays usable. Every spin-wait in this library has such a
+ * limit (about 1-2 s in normal calls). */
+cur_status cur_selftest_wait_timeout(cur_handle* h, cudaStream_t stream);
+
 /* Default options: delta 1e-2, max_swaps 100 r, nblocks 1, CUR_FLAG_POLISH. */
 cur_opts cur_default_opts(void);
 

@@ -23,7 +23,7 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select",
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
-           "cur_residual_cheb_noalloc"]
+           "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout"]
 
 
 class CurMat(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "cur_prof_enable": ([P, ctypes.c_int], ctypes.c_int),
         "cur_residual_cheb_noalloc": ([pmat, P, P, P, I32, P, P, P], ctypes.c_int),
+        "cur_selftest_wait_timeout": ([P, P], ctypes.c_int),
         "cur_prof_read": ([P, P, ctypes.POINTER(D), ctypes.POINTER(I32),
                            ctypes.POINTER(I64)], ctypes.c_int),
     }
@@ -213,6 +214,11 @@ def cur_prof_read(h, stream=None):
     _check(load().cur_prof_read(h, _stream(stream), ctypes.byref(ms), ctypes.byref(n),
                                 ctypes.byref(k)), "cur_prof_read")
     return ms.value, n.value, k.value
+
+
+def cur_selftest_wait_timeout(h, stream=None) -> None:
+    """Launch a device wait that must run out; its timeout lands in the status word."""
+    _check(load().cur_selftest_wait_timeout(h, _stream(stream)), "cur_selftest_wait_timeout")
 
 
 def info_from_tensor(t) -> CurCrossInfo:

@@ -30,6 +30,12 @@ __global__ void fill_info_k(cur_cross_info* info, const double* logvol, int swee
     info->status = *status;
 }
 
+// One CTA waits at a group barrier for a second CTA that is never launched: the
+// bounded wait must run out, record CUR_ERR_TIMEOUT and return.
+__global__ void selftest_wait_k(unsigned* ctr, int* status, long long limit) {
+    group_barrier(ctr, 2u, status, limit);
+}
+
 }  // namespace curk
 
 static std::atomic<long long> g_launches{0};
@@ -161,6 +167,18 @@ cur_status cur_prof_read(cur_handle* h, cudaStream_t st, double* pass_ms, int32_
     const long long nl = g_launches.exchange(0);
     if (kernel_launches) *kernel_launches = nl;
     h->prof_n = 0;
+    return CUR_OK;
+}
+
+cur_status cur_selftest_wait_timeout(cur_handle* h, cudaStream_t st) {
+    if (!h) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    unsigned* ctr = ar.get<unsigned>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_CK(cudaMemsetAsync(ctr, 0, sizeof(unsigned), st));
+    curk::selftest_wait_k<<<1, 32, 0, st>>>(ctr, h->status, 100000000LL);   // ~50 ms
+    CUR_CK(cudaGetLastError());
+    note_launch();
     return CUR_OK;
 }
 

@@ -201,7 +201,8 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* status) {
+__device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, int* status,
+                                              long long limit = kWaitCycles) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -210,7 +211,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
         atomicAdd(ctr, 1u);
         const long long t0 = clock64();
         while (ld_acquire_u32(ctr) < target) {
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > limit) {
                 ok = 0;
                 set_status(status, CUR_ERR_TIMEOUT);
                 break;

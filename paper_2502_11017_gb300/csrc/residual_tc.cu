@@ -30,6 +30,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "df64.cuh"
 #include "internal.h"
 #include "tc.cuh"
 
@@ -39,30 +40,38 @@ constexpr int kTcBM = 128;            // rows of A per tile (MMA N)
 constexpr int kTcBN = 128;            // columns of A per tile (MMA M)
 constexpr int kChunk = 16384;         // one 128-row x 32-element FP32 swizzled chunk
 
-// Wt[j][k] = (U R)(k, j) in FP64, split into TF32 hi and lo, rows padded to ldk.
+// Wt[j][k] = (U R)(k, j), split into TF32 hi and lo, rows padded to ldk. One thread per
+// entry (k fastest, so the stores are coalesced); the r-term sum runs in double-float
+// (U converted once per CTA), i.e. on the FP32 pipes with ~48-bit accuracy.
 template <typename TA>
 __global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, const TA* __restrict__ R,
                                                  int r, int64_t n, int ldk, float* __restrict__ Wh,
                                                  float* __restrict__ Wl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* Us = reinterpret_cast<double*>(smem_raw);
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Us[e] = U[e];
+    df64* Us = reinterpret_cast<df64*>(smem_raw);
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Us[e] = df_from_d(U[e]);
     __syncthreads();
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        double rc[64];
-        for (int l = 0; l < r; ++l) rc[l] = to_d(R[(int64_t)l * n + j]);
-        for (int k = 0; k < ldk; ++k) {
-            float hi = 0.f, lo = 0.f;
-            if (k < r) {
-                double s = 0.0;
-                for (int l = 0; l < r; ++l) s = fma(Us[k * r + l], rc[l], s);
-                hi = to_tf32((float)s);
-                lo = to_tf32((float)(s - (double)hi));
+    const int64_t total = n * ldk;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / ldk;
+        const int k = (int)(e - j * ldk);
+        float hi = 0.f, lo = 0.f;
+        if (k < r) {
+            df64 s0{0.f, 0.f}, s1{0.f, 0.f};
+            int l = 0;
+            for (; l + 1 < r; l += 2) {
+                s0 = df_add(s0, df_mul_f(Us[k * r + l], to_f(R[(int64_t)l * n + j])));
+                s1 = df_add(s1, df_mul_f(Us[k * r + l + 1], to_f(R[(int64_t)(l + 1) * n + j])));
             }
-            Wh[j * ldk + k] = hi;
-            Wl[j * ldk + k] = lo;
+            if (l < r) s0 = df_add(s0, df_mul_f(Us[k * r + l], to_f(R[(int64_t)l * n + j])));
+            const df64 w = df_add(s0, s1);
+            hi = to_tf32(__fadd_rn(w.h, w.l));
+            const df64 rem = df_sub(w, df64{hi, 0.f});
+            lo = to_tf32(__fadd_rn(rem.h, rem.l));
         }
+        Wh[e] = hi;
+        Wl[e] = lo;
     }
 }
 
@@ -393,9 +402,10 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     if (!make_map(&mWh, Wh, n, r, ldk) || !make_map(&mWl, Wl, n, r, ldk) || !make_map(&mCh, Ch, m, r, ldk) ||
         !make_map(&mCl, Cl, m, r, ldk))
         return CUR_ERR_ARG;
-    const size_t smw = (size_t)r * r * sizeof(double);
+    const size_t smw = (size_t)r * r * sizeof(df64);
     CUR_CK(cudaFuncSetAttribute((const void*)tc_prep_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
-    tc_prep_w<float><<<nbk(n), 256, smw, st>>>(U, static_cast<const float*>(R), r, n, ldk, Wh, Wl);
+    tc_prep_w<float><<<(unsigned)std::min<int64_t>((n * ldk + 255) / 256, 8 * G), 256, smw, st>>>(
+        U, static_cast<const float*>(R), r, n, ldk, Wh, Wl);
     CUR_CK(cudaGetLastError());
     note_launch();
     tc_prep_c<float><<<nbk(m * ldk), 256, 0, st>>>(static_cast<const float*>(C), m, r, ldk, Ch, Cl);

@@ -311,3 +311,45 @@ def test_residual_tensor_core_path_matches_oracle(dev, handle, m, n, r):
     assert sync(handle) == cur.CUR_OK
     assert abs(cheb.item() - cheb_ref) <= 1e-5 * np.abs(a).max()
     assert fro.item() == pytest.approx(fro_ref, rel=1e-3)
+
+
+@pytest.mark.parametrize("m,n,r,dtype", [(40, 30, 1, np.float64), (300, 1200, 12, np.float32),
+                                         (25, 21, 4, np.float64)])
+def test_cross_edge_shapes(dev, handle, m, n, r, dtype):
+    """r = 1, a wide matrix, and a matrix barely larger than r (ragged single blocks)."""
+    a = wl.lowrank_plus_noise(m, n, 0.7 ** np.arange(min(m, n) - 1), 1e-5, seed=m * n + r).astype(dtype)
+    b_r, b_c = max(1, min(4, m // r)), max(1, min(2, n // r))
+    I_ref, J_ref, info_ref = orc.cross(a, r, b_r, b_c)
+    I, J, info = cur.cross(to_dev(a, dev), r, b_r, b_c)
+    Ig, Jg = I.cpu().tolist(), J.cpu().tolist()
+    same = sorted(Ig) == sorted(I_ref) and sorted(Jg) == sorted(J_ref)
+    lv = orc.logvol(a.astype(np.float64)[np.ix_(Ig, Jg)])
+    assert same or math.exp(lv - info_ref["logvol"]) >= 0.999
+
+
+def test_cross_on_a_strided_view(dev, handle):
+    """A with a leading dimension larger than its column count."""
+    a = wl.gaussian_kernel(900, 700, seed=91)
+    wide = np.zeros((900, 768), dtype=np.float32)
+    wide[:, :700] = a
+    W = to_dev(wide, dev)
+    A = W[:, :700]
+    assert A.stride(0) == 768
+    I_ref, J_ref, _ = orc.cross(a, 10, 3, 2)
+    I, J, _ = cur.cross(A, 10, 3, 2)
+    lv = orc.logvol(a.astype(np.float64)[np.ix_(I.cpu().tolist(), J.cpu().tolist())])
+    lv_ref = orc.logvol(a.astype(np.float64)[np.ix_(I_ref, J_ref)])
+    assert math.exp(lv - lv_ref) >= 0.999
+
+
+def test_cross_bf16(dev, handle):
+    """BF16 data: the oracle reads the same BF16 values widened to FP64."""
+    a = wl.gaussian_kernel(1200, 800, seed=93)
+    t = torch.from_numpy(a).to(torch.bfloat16)
+    a_bf = t.to(torch.float32).numpy()
+    I_ref, J_ref, info_ref = orc.cross(a_bf, 12, 3, 2)
+    I, J, _ = cur.cross(t.to(dev), 12, 3, 2)
+    Ig, Jg = I.cpu().tolist(), J.cpu().tolist()
+    lv = orc.logvol(a_bf.astype(np.float64)[np.ix_(Ig, Jg)])
+    same = sorted(Ig) == sorted(I_ref) and sorted(Jg) == sorted(J_ref)
+    assert same or math.exp(lv - info_ref["logvol"]) >= 0.999
