@@ -102,6 +102,10 @@ def _check(st: int, what: str) -> int:
     return st
 
 
+def cur_status_string(status: int) -> str:
+    return load().cur_status_string(status).decode()
+
+
 def _dtype_code(t) -> int:
     import torch
     if t.dtype == torch.float64:

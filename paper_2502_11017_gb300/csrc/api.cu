@@ -306,36 +306,45 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
     ocol.nblocks = b_c;
     // M^-1 of the last row stage (Mr = C(I,:)^-1) and column stage (Mc = R^T(J,:)^-1 =
     // (A(I,J)^T)^-1); each stage of a sweep starts from the other's inverse, transposed.
-    double* Mr = ar.get<double>((size_t)r * r);
-    double* Mc = ar.get<double>((size_t)r * r);
+    double* Mr = ar.get<double>((size_t)minv_stride(r));
+    double* Mc = ar.get<double>((size_t)minv_stride(r));
     double* lvr = ar.get<double>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     MvResult res;
     CUR_TRY(gather_cols_compute(A, J0, r, Cb, st));
+    // status of the cross: a stage that ends NOCONV or SINGULAR marks it (the later
+    // stage's mark wins within sweep 1; a later sweep that does so ends the loop)
+    int last_status = CUR_OK;
     CUR_TRY(maxvol_basis_rows(h, cdt, Cb, m, r, &orow, I, nullptr, nullptr, &res, ar, st));
     sweep_swaps[0] += res.swaps;
+    if (res.status != CUR_OK) last_status = res.status;
     CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
     CUR_TRY(maxvol_basis_rows(h, cdt, Rb, n, r, &ocol, J, lv, nullptr, &res, ar, st, Mc));
     sweep_swaps[0] += res.swaps;
+    if (res.status != CUR_OK) last_status = res.status;
     int mc_valid = res.minv_valid;
-    int last_status = res.status;
     int sweeps = 1;
     while (sweeps < max_sweeps) {
         ++sweeps;
         MvResult r1, r2;
         CUR_TRY(gather_cols_compute(A, J, r, Cb, st));
         CUR_TRY(maxvol_global(h, cdt, Cb, m, r, &o, I, I, lvr, &r1, ar, st,
-                              mc_valid ? Mc : nullptr, mc_valid ? lv : nullptr, true, Mr));
+                              mc_valid ? Mc : nullptr, mc_valid ? lv : nullptr, true, Mr, true));
         CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
         CUR_TRY(maxvol_global(h, cdt, Rb, n, r, &o, J, J, lv, &r2, ar, st,
-                              r1.minv_valid ? Mr : nullptr, r1.minv_valid ? lvr : nullptr, true, Mc));
+                              r1.minv_valid ? Mr : nullptr, r1.minv_valid ? lvr : nullptr, true, Mc, true));
         mc_valid = r2.minv_valid;
         sweep_swaps[sweeps - 1] = r1.swaps + r2.swaps;
-        last_status = r1.status != CUR_OK ? r1.status : r2.status;
-        if (r1.status != CUR_OK || r2.status != CUR_OK) break;
+        if (r1.status != CUR_OK || r2.status != CUR_OK) {
+            last_status = r1.status != CUR_OK ? r1.status : r2.status;
+            break;
+        }
         if (r1.swaps + r2.swaps == 0) break;
     }
     for (int k = 0; k < 8; ++k) total += sweep_swaps[k];
+    // A stage that ended singular leaves no log|det| of its own: the log-volume of the
+    // returned cross, |det A(I,J)| = |det Rb(J,:)| with Rb = A(I,:)^T, is taken directly.
+    if (last_status != CUR_OK) CUR_TRY(logvol_rows(cdt, Rb, r, J, lv, st));
     if (last_status == CUR_ERR_NOCONV || last_status == CUR_ERR_SINGULAR) {
         curk::set_status_k<<<1, 32, 0, st>>>(h->status, last_status);
         CUR_CK(cudaGetLastError());

@@ -78,9 +78,14 @@ struct MvResult {
     int status = CUR_OK;
     int minv_valid = 0;   // minv_out holds the final FP64 M^-1
 };
+// An inverse handed between stages is minv_stride(r) doubles: M^-1 (r x r, row-major),
+// then a bound on the rounding drift that Sherman-Morrison updates have added to it since
+// it was last factorised (sum over swaps of kappa_inf(M)).
+inline __host__ __device__ int64_t minv_stride(int r) { return (int64_t)r * r + 1; }
+
 // Row selection on the tall basis `basis` (p x r, compute type of A's dtype,
 // contiguous) with nblocks blocks, merge and optional polish. I_out: device r ints.
-// With minv_out (r x r doubles, device), the final FP64 M^-1 = C(I,:)^-1 is written
+// With minv_out (minv_stride(r) doubles, device), the final FP64 M^-1 = C(I,:)^-1 is written
 // there (res->minv_valid says whether it is valid).
 cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                              const cur_opts* o, int32_t* I_out, double* logvol_out,
@@ -91,17 +96,24 @@ cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int
 // minv_in / lv_in (optional): M^-1 and log|det| of the start rows, given as is or as the
 // transpose of the inverse (transpose_in) — a column stage's M^-1 is the transpose of the
 // next row stage's; no factorisation is made then. minv_out as for maxvol_basis_rows.
+// If the set turns numerically singular, S_out is the start set, or with
+// keep_singular_set the set reached at that point (the swap iteration's own result).
 cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
                          double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
                          const double* minv_in = nullptr, const double* lv_in = nullptr,
-                         bool transpose_in = false, double* minv_out = nullptr);
+                         bool transpose_in = false, double* minv_out = nullptr,
+                         bool keep_singular_set = false);
 // One merge level (cur_merge).
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
                        int* swaps, Arena& ar, cudaStream_t st);
 // Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r).
 cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st);
+// log|det basis(rows,:)| (rows: device r ints) into *out (device), -inf for an exactly
+// singular matrix; basis p x r contiguous in the compute type of dt.
+cur_status logvol_rows(cur_dtype dt, const void* basis, int r, const int32_t* rows, double* out,
+                       cudaStream_t st);
 cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void* Rt,
                                  cudaStream_t st);
 size_t compute_size(cur_dtype t);

@@ -47,12 +47,14 @@ struct MvProb {
 
 struct MvArgs {
     const void* basis;  // rows x r (compute type), contiguous
-    double* minv64;     // P x r x r: FP64 M^-1 of each problem
+    double* minv64;     // P x minv_stride(r): FP64 M^-1 of each problem, then its drift bound
     float* mdf;         // P x 2 r^2: double-float working copy when r > kMsMax (FP32 data)
     const MvProb* prob;
     int P, r;
     double delta;
     int max_swaps;
+    double drift_max;          // refactorise once sum(swaps * kappa(M)) since the last factorisation exceeds it
+    int keep_singular_set;     // 1: a set that turns singular stays as it is; 0: back to the start set
     const int32_t* cta_prob;   // per CTA slot
     const int32_t* cta_part;
     int cta_base;              // first slot of this launch (waves)
@@ -436,12 +438,13 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
     double lv = 0.0;
     const int sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
     if (sing) {
-        if (tid == 0) { a.pstatus[pb] = CUR_ERR_SINGULAR; a.done[pb] = 1; }
+        if (tid == 0) { a.pstatus[pb] = CUR_ERR_SINGULAR; a.done[pb] = 1; a.logvol[pb] = -INFINITY; }
         return;
     }
     if (tid == 0) a.logvol[pb] = lv;
-    double* out64 = a.minv64 + (int64_t)pb * r * r;
+    double* out64 = a.minv64 + (int64_t)pb * minv_stride(r);
     for (int e = tid; e < r * r; e += nt) out64[e] = M[e];
+    if (tid == 0) out64[r * r] = 0.0;   // fresh: no drift
 }
 
 // ---------------------------------------------------------------- the swap iteration
@@ -449,11 +452,18 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
 // The first CTA of a group keeps M^-1 (FP64) in shared memory when r <= kMsMax.
 constexpr int kMsMax = 64;
 
+// Layout: [B slice | M^-1 (compute type) | colj | wrow] or, while M^-1 is being
+// refactorised, [C(S,:) in FP64 | pivot column | pivots] over the same bytes (both are
+// dead then); after it the first CTA's MinvKeeper.
 template <typename TB>
 struct EngineSmem {
+    __host__ __device__ static size_t head(int nloc, int r) {
+        const size_t b = ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
+        const size_t gj = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int);
+        return ((b > gj ? b : gj) + 15) / 16 * 16;
+    }
     static size_t bytes(int nloc, int r) {
-        size_t b = ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
-        b = (b + 15) / 16 * 16 + (size_t)8 * r * sizeof(double) + 64;
+        size_t b = head(nloc, r) + (size_t)8 * r * sizeof(double) + 64;
         if (r <= kMsMax) b += (size_t)r * r * sizeof(double);
         return b;
     }
@@ -597,6 +607,49 @@ struct MinvKeeper<double> {
     __device__ double dlog() const { return lacc.log_value(); }
 };
 
+// M^-1 of C(S,:) from scratch (FP64 Gauss-Jordan, the singularity rule of the start
+// factorisation) into the keeper; W, colk, piv: shared scratch of r*r + r doubles and
+// r ints. Returns 1 if C(S,:) is numerically singular. All threads of the CTA call it.
+template <typename TB>
+__device__ int engine_refactor(MinvKeeper<TB>& keep, const TB* basis, const int32_t* S, int r,
+                               double* W, double* colk, int* piv, double* lv) {
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int k = e / r, c = e - k * r;
+        const double x = to_d(basis[(int64_t)S[k] * r + c]);
+        W[e] = x;
+        mx = fmax(mx, fabs(x));
+    }
+    mx = block_max(mx);
+    const int sing = gj_inverse(W, r, colk, piv, (double)r * kEps * mx, lv);
+    if (!sing) {
+        keep.load(W, r);
+        if (threadIdx.x == 0) keep.lacc.init();
+    }
+    __syncthreads();
+    return sing;
+}
+
+// kappa_inf(M) = ||C(S,:)||_inf ||M^-1||_inf with the kept inverse (all threads call it).
+template <typename TB>
+__device__ double engine_kappa(const MinvKeeper<TB>& keep, const TB* basis, const int32_t* S, int r) {
+    double sm = 0.0, sx = 0.0;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = threadIdx.x >> 5; k < r; k += nw) {   // a warp per row
+        double a = 0.0, x = 0.0;
+        const TB* row = basis + (int64_t)S[k] * r;
+        for (int c = lane; c < r; c += 32) {
+            a += fabs(to_d(row[c]));
+            x += fabs((double)keep.value(k * r + c));
+        }
+        sm = fmax(sm, warp_sum(a));
+        sx = fmax(sx, warp_sum(x));
+    }
+    sm = block_max(sm);
+    sx = block_max(sx);
+    return sm * sx;
+}
+
 template <typename TB>
 __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -611,12 +664,15 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     TB* Mi = Bs + (size_t)nloc * r;             // r x r: M^-1 in the compute type
     TB* colj = Mi + (size_t)r * r;              // nloc
     TB* wrow = colj + nloc;                     // r: winning row of B, then B(i,:) - e_j
-    size_t off = (((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB) + 15) / 16 * 16;
-    double* Mg = a.minv64 + (int64_t)pb * r * r;                // M^-1 in global memory (FP64)
+    const size_t off = EngineSmem<TB>::head(nloc, r);
+    double* Mg = a.minv64 + (int64_t)pb * minv_stride(r);       // M^-1 in global memory (FP64)
     __shared__ double s_b;
     __shared__ long long s_w;
     __shared__ int s_nan;
     __shared__ MinvKeeper<TB> keep;
+    __shared__ int32_t S0[128];      // the start set, restored if C(S,:) turns singular (unless kept)
+    __shared__ double s_lv0;         // log|det| of the last factorisation
+    __shared__ double s_drift;       // sum of swaps * kappa(M) since the last factorisation
     TB* pub = static_cast<TB*>(a.pub);
     const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
     const int myslot = pr.group0 + part;
@@ -625,12 +681,26 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
             keep.setup(smem_raw + off, r, Mg, r <= kMsMax, a.mdf ? a.mdf + (int64_t)pb * 2 * r * r : nullptr);
         __syncthreads();
         keep.load(Mg, r);
+        for (int k = tid; k < r; k += nt) S0[k] = a.S[(int64_t)pb * r + k];
+        // the inverse arrives with its drift bound (0 when just factorised)
+        if (tid == 0) { s_lv0 = a.logvol[pb]; s_drift = Mg[(size_t)r * r]; }
     }
+    int32_t* Sg = a.S + (int64_t)pb * r;
+    double* gjw = reinterpret_cast<double*>(smem_raw);   // refactorisation scratch over the B slice
+    // First CTA only: M^-1 of C(S,:) afresh into the keeper; 1 if C(S,:) is singular.
+    auto refactor = [&]() -> int {
+        double lv = 0.0;
+        const int sing = engine_refactor(keep, basis, Sg, r, gjw, gjw + (size_t)r * r,
+                                         reinterpret_cast<int*>(gjw + (size_t)r * r + r), &lv);
+        if (tid == 0 && !sing) { s_lv0 = lv; s_drift = 0.0; }
+        __syncthreads();
+        return sing;
+    };
 
     double bv;
     long long bi;
     int nan;
-    int par = 0, total = a.swaps[pb];
+    int par = 0, total = a.swaps[pb], made_last = 0;
     unsigned epoch = 0;
     int fin = 0, fstat = CUR_OK;
     auto publish = [&](int pp) {
@@ -762,49 +832,75 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
             publish(par);
             if (made == r) { fin = 2; break; }
         }
+        made_last = made;
         if (fin != 2) break;
-        // every CTA refreshes from the M^-1 that the first CTA has finished updating
-        if (part == 0 && !solo) {
+        // A new cycle starts from M = C(S,:) factorised afresh once the Sherman-Morrison
+        // updates carried since the last factorisation may have drifted: each swap adds
+        // about kappa(M) u (u = unit roundoff of the kept inverse) to the refreshed B. With
+        // drift_max = 0 (FP64 data) every cycle refactorises, as the iteration is stated;
+        // for FP32 B the bound 2^18 keeps the drift below 2^-30. The first CTA decides and
+        // refactorises; every CTA then refreshes from its M^-1.
+        int sing = 0;
+        if (part == 0) {
             __syncthreads();
-            keep.store(Mg, r);
+            double drift = 0.0;
+            if (a.drift_max > 0.0) {
+                const double kap = engine_kappa(keep, basis, Sg, r);
+                if (tid == 0) s_drift += (double)made * kap;
+                __syncthreads();
+                drift = s_drift;
+            }
+            if (a.drift_max <= 0.0 || !(drift <= a.drift_max)) {
+                sing = refactor();
+                if (tid == 0 && sing) a.pstatus[pb] = CUR_ERR_SINGULAR;   // seen by the group after the barrier
+            }
+            if (!solo && !sing) keep.store(Mg, r);
         }
         if (!solo) {
             ++epoch;
             if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
+            if (part != 0) sing = *reinterpret_cast<volatile int32_t*>(a.pstatus + pb) == CUR_ERR_SINGULAR;
         }
+        if (sing) { fin = 3; fstat = CUR_ERR_SINGULAR; break; }
         fin = 0;
     }
     if (part == 0) {
         __syncthreads();
-        keep.store(Mg, r);
+        // the stored inverse (inherited by merge nodes and later sweeps) leaves with its
+        // drift bound, never above drift_max; only the swap cap can end a cycle with swaps
+        if (fin == 3 && fstat == CUR_ERR_NOCONV && made_last > 0) {
+            double drift = 0.0;
+            if (a.drift_max > 0.0) {
+                const double kap = engine_kappa(keep, basis, Sg, r);
+                if (tid == 0) s_drift += (double)made_last * kap;
+                __syncthreads();
+                drift = s_drift;
+            }
+            if ((a.drift_max <= 0.0 || !(drift <= a.drift_max)) && refactor()) fstat = CUR_ERR_SINGULAR;
+        }
+        const bool sing = fin == 3 && fstat == CUR_ERR_SINGULAR;
+        if (sing) {
+            if (!a.keep_singular_set)
+                for (int k = tid; k < r; k += nt) a.S[(int64_t)pb * r + k] = S0[k];
+        } else {
+            keep.store(Mg, r);
+            if (tid == 0) Mg[(size_t)r * r] = s_drift;
+        }
         if (tid == 0) {
             a.swaps[pb] = total;
-            a.logvol[pb] += keep.dlog();
+            a.logvol[pb] = sing ? -INFINITY : s_lv0 + keep.dlog();
             a.done[pb] = 1;
             a.pstatus[pb] = fin == 1 ? CUR_OK : fstat;
-            if (fin == 3 && fstat != CUR_ERR_NOCONV) set_status(a.status, fstat);
+            if (fin == 3 && fstat != CUR_ERR_NOCONV && fstat != CUR_ERR_SINGULAR) set_status(a.status, fstat);
         }
     }
 }
 
-// dst = src^T (r x r).
+// dst = src^T (r x r), with the drift bound that follows the matrix.
 __global__ void mv_transpose(const double* src, int r, double* dst) {
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < r * r; e += gridDim.x * blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= r * r; e += gridDim.x * blockDim.x) {
         const int a = e / r, b = e - a * r;
-        dst[e] = src[b * r + a];
-    }
-}
-
-// Node t of a merge level starts from its left child's M^-1 (same rows, same order).
-__global__ void mv_inherit(const double* child_minv, const double* child_lv, const int32_t* valid,
-                           int P, int r, double* minv, double* lv) {
-    const int64_t rr = (int64_t)r * r;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)P * rr;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(e / rr);
-        if (!valid[t]) continue;
-        minv[e] = child_minv[2 * (int64_t)t * rr + (e - t * rr)];
-        if (e - t * rr == 0) lv[t] = child_lv[2 * t];
+        dst[e] = e == r * r ? src[e] : src[b * r + a];
     }
 }
 
@@ -837,6 +933,66 @@ __global__ void mv_iota(int32_t* S, int P, int r, int off) {
 }
 
 // Pad idx (r entries, count valid, -1 after) with the lowest unused ids < size.
+// log|det basis(rows,:)| (r x r) by LU with partial pivoting (first maximum |a_ik|,
+// i >= k), the log-volume of Definition 1 for a set that may be numerically singular:
+// a pivot that is exactly zero gives -inf, any other pivot counts however small.
+template <typename TB>
+__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int r, const int32_t* rows,
+                                                     double* out) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* M = reinterpret_cast<double*>(smem_raw);
+    __shared__ int s_p, s_zero;
+    __shared__ LogAcc s_acc;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < r * r; e += nt) {
+        const int k = e / r, c = e - k * r;
+        M[e] = to_d(basis[(int64_t)rows[k] * r + c]);
+    }
+    if (tid == 0) { s_zero = 0; s_acc.init(); }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (tid < 32) {
+            double bv = -1.0;
+            int bi = k;
+            for (int i = k + tid; i < r; i += 32) {
+                const double x = fabs(M[i * r + k]);
+                if (x > bv) { bv = x; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
+            }
+            if (tid == 0) s_p = bi;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < r; j += nt) {
+                const double t = M[k * r + j];
+                M[k * r + j] = M[p * r + j];
+                M[p * r + j] = t;
+            }
+        __syncthreads();
+        const double d = M[k * r + k];
+        if (d == 0.0 || !isfinite(d)) {
+            if (tid == 0) s_zero = 1;
+            continue;   // no elimination past a zero pivot (uniform: d is read by all)
+        }
+        if (tid == 0) s_acc.mul(df_from_d(d));
+        for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] /= d;
+        __syncthreads();
+        const int w = r - k - 1;
+        for (int e = tid; e < w * w; e += nt) {
+            const int i = k + 1 + e / w, j = k + 1 + e % w;
+            M[i * r + j] = fma(-M[i * r + k], M[k * r + j], M[i * r + j]);
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (tid == 0) *out = s_zero ? -INFINITY : s_acc.log_value();
+}
+
 __global__ void pad_indices_k(int32_t* idx, const int32_t* count, int r, int64_t size) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int fill = *count;
@@ -883,7 +1039,7 @@ struct Stage {
     MvProb* dprob = nullptr;
     int32_t* dtab = nullptr;   // cta_prob | cta_part | lu_mask
     int32_t* S = nullptr;      // P x r
-    double* minv64 = nullptr;  // P x r x r
+    double* minv64 = nullptr;  // P x minv_stride(r)
     float* mdf = nullptr;      // P x 2 r^2 (r > kMsMax only)
     double* logvol = nullptr;
     int32_t* swaps = nullptr;
@@ -895,6 +1051,7 @@ struct Stage {
     TB* pub = nullptr;
     double* aux = nullptr;
     std::vector<int> stat, sw;  // host copies after read()
+    bool keep_singular_set = false;
 };
 
 template <typename TB>
@@ -926,7 +1083,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     sg.dprob = ar.get<MvProb>(P);
     sg.dtab = ar.get<int32_t>((size_t)2 * slots + P);
     sg.S = ar.get<int32_t>((size_t)P * r);
-    sg.minv64 = ar.get<double>((size_t)P * r * r);
+    sg.minv64 = ar.get<double>((size_t)P * minv_stride(r));
     sg.mdf = r > kMsMax ? ar.get<float>((size_t)P * 2 * r * r) : nullptr;
     sg.logvol = ar.get<double>(P);
     sg.swaps = ar.get<int32_t>(P);
@@ -977,6 +1134,10 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     a.r = r;
     a.delta = o->delta;
     a.max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
+    // FP64 data: a fresh factorisation every cycle. FP32 B (double-float inverse,
+    // u = 2^-48): the carried inverse while sum(swaps * kappa) <= 2^18, i.e. drift <= 2^-30.
+    a.drift_max = std::is_same<TB, double>::value ? 0.0 : 262144.0;
+    a.keep_singular_set = sg.keep_singular_set ? 1 : 0;
     a.cta_prob = sg.dtab;
     a.cta_part = sg.dtab + slots;
     a.lu_mask = sg.dtab + 2 * slots;
@@ -1101,19 +1262,21 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
         const int k = 2 * t;
         if (k < (int)in_minv.size() && in_minv[k] && in_lv[k]) {
             lu_mask[t] = 0;
-            CUR_CK(cudaMemcpyAsync(lv.minv64 + (int64_t)t * r * r, in_minv[k], sizeof(double) * r * r,
+            CUR_CK(cudaMemcpyAsync(lv.minv64 + (int64_t)t * minv_stride(r), in_minv[k], sizeof(double) * minv_stride(r),
                                    cudaMemcpyDeviceToDevice, st));
             CUR_CK(cudaMemcpyAsync(lv.logvol + t, in_lv[k], sizeof(double), cudaMemcpyDeviceToDevice, st));
         }
     }
     CUR_TRY(stage_run<TB>(h, U, r, o, lv, false, lu_mask, none, st));
     CUR_TRY(stage_read<TB>(h, lv, st));
-    for (int v : lv.sw) *swaps += v;
-    // singular left start: start at the right set; then Algorithm 3 on the union
+    // singular left start: start at the right set; then Algorithm 3 on the union. The
+    // swaps of an attempt that is abandoned for the next one are not counted.
     std::vector<int> skip(npairs, 1);
     bool any = false;
-    for (int t = 0; t < npairs; ++t)
+    for (int t = 0; t < npairs; ++t) {
         if (lv.stat[t] == CUR_ERR_SINGULAR) { skip[t] = 0; any = true; }
+        else *swaps += lv.sw[t];
+    }
     for (int attempt = 0; attempt < 2 && any; ++attempt) {
         if (attempt == 0) {
             mv_iota<<<nblk(npairs * r), 256, 0, st>>>(S2, npairs, r, r);
@@ -1130,8 +1293,9 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
         any = false;
         for (int t = 0; t < npairs; ++t) {
             if (skip[t]) { lv.stat[t] = save[t]; lv.sw[t] = savesw[t]; continue; }
+            if (lv.stat[t] == CUR_ERR_SINGULAR && attempt == 0) { any = true; continue; }
             *swaps += lv.sw[t];
-            if (lv.stat[t] == CUR_ERR_SINGULAR) any = true; else skip[t] = 1;
+            skip[t] = 1;
         }
     }
     mv_emit<<<nblk(npairs * r), 256, 0, st>>>(lv.dprob, lv.S, npairs, r, out);
@@ -1139,7 +1303,7 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
     note_launch();
     for (int t = 0; t < npairs; ++t) {
         const bool ok = lv.stat[t] == CUR_OK || lv.stat[t] == CUR_ERR_NOCONV;
-        out_minv.push_back(ok ? lv.minv64 + (int64_t)t * r * r : nullptr);
+        out_minv.push_back(ok ? lv.minv64 + (int64_t)t * minv_stride(r) : nullptr);
         out_lv.push_back(ok ? lv.logvol + t : nullptr);
     }
     if (nsets % 2 == 1) {
@@ -1159,9 +1323,10 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
                            const int32_t* S0, int32_t* S_out, double* logvol_out, MvResult* res,
                            Arena& ar, cudaStream_t st, const double* inherit_minv = nullptr,
                            const double* inherit_lv = nullptr, bool transpose = false,
-                           double* minv_out = nullptr) {
+                           double* minv_out = nullptr, bool keep_singular_set = false) {
     const size_t mark = ar.off;
     Stage<TB> sg;
+    sg.keep_singular_set = keep_singular_set;
     MvProb pr{};
     pr.base = 0;
     pr.gid_base = 0;
@@ -1174,11 +1339,11 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     if (inherit_minv && inherit_lv) {
         lu_mask[0] = 0;
         if (transpose) {
-            mv_transpose<<<nblk((int64_t)r * r), 256, 0, st>>>(inherit_minv, r, sg.minv64);
+            mv_transpose<<<nblk(minv_stride(r)), 256, 0, st>>>(inherit_minv, r, sg.minv64);
             CUR_CK(cudaGetLastError());
             note_launch();
         } else {
-            CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+            CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
         }
         CUR_CK(cudaMemcpyAsync(sg.logvol, inherit_lv, sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
@@ -1187,12 +1352,12 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     const bool ok = sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG &&
                     sg.stat[0] != CUR_ERR_NONFINITE && sg.stat[0] != CUR_ERR_TIMEOUT;
     if (res) { res->swaps = sg.sw[0]; res->status = sg.stat[0]; res->minv_valid = ok && minv_out; }
-    if (sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG)
+    if ((sg.stat[0] != CUR_ERR_SINGULAR || keep_singular_set) && sg.stat[0] != CUR_ERR_ARG)
         CUR_CK(cudaMemcpyAsync(S_out, sg.S, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     else if (S_out != S0)
         CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, sg.logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (minv_out && ok) CUR_CK(cudaMemcpyAsync(minv_out, sg.minv64, sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+    if (minv_out && ok) CUR_CK(cudaMemcpyAsync(minv_out, sg.minv64, sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
     CUR_CK(cudaStreamSynchronize(st));
     ar.off = mark;
     ar.ok = true;
@@ -1239,7 +1404,7 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
     std::vector<const double*> mv, lvp, mv2, lvp2;
     for (int k = 0; k < nb; ++k) {
         const bool ok = sb.stat[k] == CUR_OK || sb.stat[k] == CUR_ERR_NOCONV;
-        mv.push_back(ok ? sb.minv64 + (int64_t)k * r * r : nullptr);
+        mv.push_back(ok ? sb.minv64 + (int64_t)k * minv_stride(r) : nullptr);
         lvp.push_back(ok ? sb.logvol + k : nullptr);
     }
     int nsets = nb;
@@ -1268,7 +1433,7 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         mvalid = gr.minv_valid;
     } else {
         if (minv_out && !mv.empty() && mv[0]) {
-            CUR_CK(cudaMemcpyAsync(minv_out, mv[0], sizeof(double) * r * r, cudaMemcpyDeviceToDevice, st));
+            CUR_CK(cudaMemcpyAsync(minv_out, mv[0], sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
             mvalid = 1;
         }
         CUR_CK(cudaMemcpyAsync(I_out, cur, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
@@ -1276,12 +1441,8 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
             if (!mv.empty() && lvp[0]) {
                 CUR_CK(cudaMemcpyAsync(logvol_out, lvp[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
             } else {
-                MvResult gr;
-                cur_opts o2 = *o;
-                o2.delta = 1e300;   // no swap: one factorisation for log|det|
-                int32_t* tmp = ar.get<int32_t>(r);
-                if (!ar.ok) return CUR_ERR_NOMEM;
-                CUR_TRY(global_t<TB>(h, basis, p, r, &o2, cur, tmp, logvol_out, &gr, ar, st));
+                CUR_TRY(logvol_rows(std::is_same<TB, double>::value ? CUR_F64 : CUR_F32, basis, r, cur,
+                                    logvol_out, st));
             }
         }
     }
@@ -1315,10 +1476,10 @@ cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
                          double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
                          const double* minv_in, const double* lv_in, bool transpose_in,
-                         double* minv_out) {
+                         double* minv_out, bool keep_singular_set) {
     if (dt == CUR_F64)
-        return curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out);
-    return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out);
+        return curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out, keep_singular_set);
+    return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out, keep_singular_set);
 }
 
 template <typename TB>
@@ -1386,6 +1547,21 @@ cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void
         case CUR_BF16: return gather_rows_t_t<__nv_bfloat16>(A, I, r, Rt, st);
     }
     return CUR_ERR_ARG;
+}
+
+cur_status logvol_rows(cur_dtype dt, const void* basis, int r, const int32_t* rows, double* out,
+                       cudaStream_t st) {
+    const size_t sm = (size_t)r * r * sizeof(double);
+    if (dt == CUR_F64) {
+        CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<double>, sm));
+        curk::logvol_rows_k<double><<<1, 256, sm, st>>>(static_cast<const double*>(basis), r, rows, out);
+    } else {
+        CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<float>, sm));
+        curk::logvol_rows_k<float><<<1, 256, sm, st>>>(static_cast<const float*>(basis), r, rows, out);
+    }
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
 }
 
 cur_status pad_indices_dev(int32_t* idx, const int32_t* count, int r, int64_t size, cudaStream_t st) {

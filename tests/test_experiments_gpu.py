@@ -1,0 +1,96 @@
+"""Section 3.1's error study (Hilbert matrices, low-rank 1/(i+j) products) on the GPU
+path against the oracle. The paper prints no values, so the oracle is the reference.
+
+Where every decision is well separated the cross must be the oracle's. Beyond that,
+Algorithm 3 on a numerically low-rank block picks among residual norms whose relative
+rounding error is eps ||a|| / ||residual||, so the start sets (and with them the
+maxvol local optimum) are decided by rounding; there the GPU cross must be a valid
+fixed point (both dominance checks within 1 + delta, in FP64 by the oracle) with a
+volume and an error close to the oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2502_11017_gb300 as cur
+from paper_2502_11017_gb300 import experiments as ex
+from paper_2502_11017_gb300 import workloads as wl
+from oracle import cur_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cur.load()
+    return torch.device("cuda:0")
+
+
+def _oracle(a, r, blocks=4):
+    m, n = a.shape
+    I, J, info = orc.cross(a, r, min(blocks, m // r), min(blocks, n // r))
+    C, U, R, _, _ = orc.assemble(a, I, J)
+    return sorted(I), sorted(J), info, orc.residual(a, C, U, R)[1]
+
+
+@pytest.mark.parametrize("r", [1, 2, 3, 4, 5])
+def test_hilbert_small_rank_is_the_oracles_cross(dev, r):
+    a = wl.hilbert(256)
+    hd = cur.Handle(256, 256, 32, cur.CUR_F64)
+    e, _, st, I, J = ex.rel_error(torch.from_numpy(a).to(dev), r, hd)
+    hd.close()
+    Io, Jo, info, eo = _oracle(a, r)
+    assert st == cur.CUR_OK and info["status"] == orc.OK
+    assert sorted(I.tolist()) == Io and sorted(J.tolist()) == Jo
+    assert e == pytest.approx(eo, rel=1e-9)
+
+
+def test_hilbert_up_to_rank_12_valid_and_close(dev):
+    a = wl.hilbert(256)
+    A = torch.from_numpy(a).to(dev)
+    hd = cur.Handle(256, 256, 32, cur.CUR_F64)
+    errs = []
+    for r in range(6, 13):
+        e, _, st, I, J = ex.rel_error(A, r, hd)
+        Ig, Jg = I.tolist(), J.tolist()
+        Io, Jo, info, eo = _oracle(a, r)
+        assert st == cur.CUR_OK and info["status"] == orc.OK, r
+        dr, dc = orc.dominance(a, Ig, Jg)
+        assert dr <= 1.01 * (1 + 1e-4) and dc <= 1.01 * (1 + 1e-4), (r, dr, dc)
+        lv = orc.logvol(a[np.ix_(Ig, Jg)])
+        assert lv >= info["logvol"] - 0.01, (r, lv, info["logvol"])   # volume ratio >= 0.99
+        assert e <= 1.5 * eo, (r, e, eo)
+        errs.append(e)
+    hd.close()
+    assert all(b < x for x, b in zip(errs, errs[1:]))
+
+
+@pytest.mark.parametrize("k,rmax", [(5, 5), (10, 4)])
+def test_lowrank_product_matches_oracle(dev, k, rmax):
+    # an error below 1e-6 sits at the rounding floor of C U R (rcond A(I,J) <= 1e-9
+    # there), so the two evaluations of the same cross agree to 1 %, not to 1e-6
+    h = wl.cauchy_product(256, k)
+    H = torch.from_numpy(h).to(dev)
+    hd = cur.Handle(256, 256, 32, cur.CUR_F64)
+    for r in range(1, rmax + 1):
+        e, _, st, I, J = ex.rel_error(H, r, hd)
+        Io, Jo, info, eo = _oracle(h, r)
+        assert st == cur.CUR_OK
+        assert sorted(I.tolist()) == Io and sorted(J.tolist()) == Jo, r
+        assert e == pytest.approx(eo, rel=1e-6 if eo > 1e-6 else 1e-2)
+    hd.close()
+
+
+def test_rank_5_product_beyond_its_rank_reports_singular(dev):
+    # A(I,J) of a rank-5 matrix with r = 6 is singular: both sides say so, and the
+    # assembled cross (pseudo-inverse U) is still exact to rounding.
+    h = wl.cauchy_product(256, 5)
+    hd = cur.Handle(256, 256, 32, cur.CUR_F64)
+    e, _, st, _, _ = ex.rel_error(torch.from_numpy(h).to(dev), 6, hd)
+    hd.close()
+    _, _, info, eo = _oracle(h, 6)
+    assert st == cur.CUR_ERR_SINGULAR and info["status"] == orc.ERR_SINGULAR
+    assert e < 1e-6 and eo < 1e-6
