@@ -24,6 +24,9 @@ Algorithm", arXiv 2502.11017):
 * ``assemble``: C = A(:,J), U = A(I,J)^dagger, R = A(I,:) (Section 1.1).
 * ``residual``: Chebyshev norm max|A - CUR| (Theorem 1) and the relative
   Frobenius error ||A - CUR||_F / ||A||_F (Section 3.1).
+* ``aca_full``: Algorithm 1 (adaptive cross approximation with full pivoting),
+  Section 1.3: r steps of {global argmax |R_k(i,j)|, rank-1 elimination of the
+  pivot's row and column}; the paper's sequential baseline.
 * ``bruteforce_*``: exhaustive maximal-volume search for tiny inputs.
 
 Readings where the paper is silent or ambiguous (Algorithm 3 uses squared norms;
@@ -115,6 +118,38 @@ def aca_select(A, axis: int, r: int, nblocks: int = 1):
         selected.append(max_idx)
         mask[max_idx] = True
     return selected, OK
+
+
+def aca_full(A, r: int):
+    """Algorithm 1 (ACA with full pivoting). Returns (I, J, pivots, R, status).
+
+    R_0 = A; step k takes (i, j) = argmax |R_k(i,j)| (first maximum in row-major
+    order, i.e. the smallest row, then the smallest column), appends i to I and j to
+    J, and eliminates: R_{k+1} = R_k - R_k(:,j) R_k(i,:) / R_k(i,j). Row i and
+    column j of R_{k+1} are zero in exact arithmetic and are set to zero. The loop
+    runs r steps (the pseudocode's bound m - 1 read as r); a pivot at rounding level,
+    |R_k(i,j)| <= max(m,n) eps max|A|, stops it early with WARN_RANK. R is returned
+    as the residual after the last step.
+    """
+    R = np.array(A, dtype=np.float64, copy=True)
+    m, n = R.shape
+    if not (1 <= r <= min(m, n)):
+        return [], [], [], R, ERR_ARG
+    tol = max(m, n) * EPS * (np.abs(R).max() if R.size else 0.0)
+    I, J, piv = [], [], []
+    for _k in range(r):
+        flat = int(np.argmax(np.abs(R)))
+        i, j = divmod(flat, n)
+        p = R[i, j]
+        if not abs(p) > tol:
+            return I, J, piv, R, WARN_RANK
+        R -= np.outer(R[:, j], R[i, :]) / p
+        R[i, :] = 0.0
+        R[:, j] = 0.0
+        I.append(i)
+        J.append(j)
+        piv.append(float(p))
+    return I, J, piv, R, OK
 
 
 def pad_indices(idx, size: int, r: int) -> list[int]:

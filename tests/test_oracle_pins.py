@@ -423,3 +423,61 @@ def test_cauchy_product_is_recovered_at_its_rank():
     I, J, _ = orc.cross(hm, 5, 2, 2)
     C, U, R, _rc, _p = orc.assemble(hm, I, J)
     assert orc.residual(hm, C, U, R)[1] < 1e-6     # cond(A(I,J)) ~ 1e10
+
+
+# ---------------------------------------------------------------- Algorithm 1 (ACA, full pivoting)
+
+def _gecp_pivots(a):
+    """Pivot positions (original row, column) and values of LAPACK's LU with complete
+    pivoting (dgetc2), step by step (SciPy returns the interchanges 0-based)."""
+    lu, ipiv, jpiv, info = scipy.linalg.lapack.dgetc2(np.array(a, dtype=np.float64, order="F"))
+    assert info == 0
+    n = a.shape[0]
+    rows, cols = list(range(n)), list(range(n))
+    out = []
+    for k in range(n):
+        p, q = ipiv[k], jpiv[k]
+        rows[k], rows[p] = rows[p], rows[k]
+        cols[k], cols[q] = cols[q], cols[k]
+        out.append((rows[k], cols[k], lu[k, k]))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_aca_full_equals_lapack_complete_pivoting(seed):
+    a = np.random.default_rng(seed).standard_normal((12, 12))
+    I, J, piv, _R, st = orc.aca_full(a, 8)
+    assert st == orc.OK
+    ref = _gecp_pivots(a)[:8]
+    assert I == [x[0] for x in ref] and J == [x[1] for x in ref]
+    np.testing.assert_allclose(piv, [x[2] for x in ref], rtol=1e-12)
+
+
+def test_aca_full_residual_is_schur_complement():
+    # R_k = A - A(:,J) A(I,J)^-1 A(I,:), the k-th Schur complement, at every k
+    a = wl.lowrank_plus_noise(40, 30, 2.0 ** -np.arange(8), 1e-6, seed=5)
+    for k in (1, 3, 5, 7):
+        I, J, _p, R, st = orc.aca_full(a, k)
+        assert st == orc.OK
+        schur = a - a[:, J] @ np.linalg.solve(a[np.ix_(I, J)], a[I, :])
+        np.testing.assert_allclose(R, schur, atol=1e-10 * np.abs(a).max())
+        assert np.all(R[I, :] == 0.0) and np.all(R[:, J] == 0.0)
+
+
+def test_aca_full_first_pivot_and_ties():
+    a = np.random.default_rng(3).standard_normal((9, 7))
+    I, J, _p, _R, _st = orc.aca_full(a, 1)
+    assert (I[0], J[0]) == np.unravel_index(np.argmax(np.abs(a)), a.shape)
+    t = np.zeros((5, 5))
+    t[3, 1] = t[1, 4] = t[1, 2] = -2.0   # equal magnitudes: smallest row, then column
+    I, J, _p, _R, _st = orc.aca_full(t, 1)
+    assert (I[0], J[0]) == (1, 2)
+
+
+def test_aca_full_rank_r_exact_and_early_stop():
+    rng = np.random.default_rng(7)
+    a = rng.standard_normal((30, 4)) @ rng.standard_normal((4, 25))
+    I, J, _p, R, st = orc.aca_full(a, 4)
+    assert st == orc.OK and np.abs(R).max() <= 1e-12 * np.abs(a).max()
+    I, J, _p, R, st = orc.aca_full(a, 6)
+    assert st == orc.WARN_RANK and len(I) == 4
