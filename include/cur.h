@@ -102,11 +102,27 @@ size_t cur_workspace_size(int64_t m, int64_t n, int32_t r, cur_dtype dtype);
 cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r,
                           int32_t nblocks, int32_t* idx_out, cudaStream_t stream);
 
+/* Algorithm 1 (Section 1.3): adaptive cross approximation with full pivoting, the
+ * paper's sequential baseline. From R_0 = A, step k takes (i, j) = argmax |R_k(i,j)|
+ * (ties: the smallest row, then the smallest column) and eliminates
+ * R_{k+1} = R_k - R_k(:,j) R_k(i,:) / R_k(i,j); r steps.
+ * R_work: m x n row-major, contiguous device buffer of the compute type (double for
+ * CUR_F64 data, float for CUR_F32 and CUR_BF16), owned by the caller; it receives the
+ * residual R_r (rows I and columns J exactly zero). I_out, J_out: r int32 (device), the
+ * pivots in selection order; piv_out: r doubles (device, may be NULL), the pivot values
+ * R_k(i_k, j_k). A pivot at rounding level, |R_k(i,j)| <= max(m,n) eps max|A| with
+ * eps = 2^-52, ends the loop: the remaining entries are -1 and the status word records
+ * CUR_WARN_RANK; non-finite data records CUR_ERR_NONFINITE. 1 <= r <= min(m,n), else
+ * CUR_ERR_ARG. Asynchronous. */
+cur_status cur_aca_full(cur_handle* h, const cur_mat* A, int32_t r, void* R_work,
+                        int32_t* I_out, int32_t* J_out, double* piv_out, cudaStream_t stream);
+
 /* Row selection for given columns J (r int32, device): maxvol on C = A(:,J).
  * C is split into opts->nblocks contiguous balanced row blocks (each >= r rows,
  * else CUR_ERR_ARG); each block starts from Algorithm 3 on its rows and runs
  * maxvol (B = C_k M^-1, swap while max|B_ij| > 1 + delta, Sherman-Morrison
- * updates, refresh every r swaps); the block sets are merged pairwise (binary
+ * updates; every r swaps a new cycle from C_k(S,:) factorised afresh); the block
+ * sets are merged pairwise (binary
  * tournament, cur_merge) and, with CUR_FLAG_POLISH, refined by maxvol over all
  * rows. Outputs (device): I_out r int32, logvol_out 1 double (log|det C(I,:)|),
  * swaps_out 1 int32. */

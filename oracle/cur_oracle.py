@@ -152,6 +152,22 @@ def aca_full(A, r: int):
     return I, J, piv, R, OK
 
 
+def aca_full_replay(A, I, J):
+    """Algorithm 1's elimination along a given pivot sequence (for checking a run whose
+    near-tied choices were decided by rounding). Returns (pivot values, max |R_k| before
+    each step, R after the last step)."""
+    R = np.array(A, dtype=np.float64, copy=True)
+    piv, mx = [], []
+    for i, j in zip(I, J):
+        mx.append(float(np.abs(R).max()))
+        p = R[i, j]
+        piv.append(float(p))
+        R -= np.outer(R[:, j], R[i, :]) / p
+        R[i, :] = 0.0
+        R[:, j] = 0.0
+    return piv, mx, R
+
+
 def pad_indices(idx, size: int, r: int) -> list[int]:
     """Fill a short selection up to r with the lowest unselected indices."""
     out = list(idx)

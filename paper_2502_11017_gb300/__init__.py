@@ -19,7 +19,7 @@ CUR_F64, CUR_F32, CUR_BF16 = 0, 1, 2
 CUR_FLAG_POLISH = 1
 
 # Every symbol include/cur.h declares.
-EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select",
+EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", "cur_aca_full",
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_destroy": ([P], ctypes.c_int),
         "cur_workspace_size": ([I64, I64, I32, ctypes.c_int], ctypes.c_size_t),
         "cur_aca_select": ([P, pmat, ctypes.c_int, I32, I32, P, P], ctypes.c_int),
+        "cur_aca_full": ([P, pmat, I32, P, P, P, P, P], ctypes.c_int),
         "cur_maxvol_rows": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
         "cur_maxvol_cols": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
         "cur_merge": ([P, pmat, P, I32, I32, popts, P, P], ctypes.c_int),
@@ -161,6 +162,11 @@ def cur_sync_status(h, stream=None) -> int:
 def cur_aca_select(h, A, axis: int, r: int, nblocks: int, idx_out, stream=None) -> int:
     return _check(load().cur_aca_select(h, ctypes.byref(mat(A)), axis, r, nblocks,
                                         _ptr(idx_out), _stream(stream)), "cur_aca_select")
+
+
+def cur_aca_full(h, A, r: int, R_work, I_out, J_out, piv_out=None, stream=None) -> int:
+    return _check(load().cur_aca_full(h, ctypes.byref(mat(A)), r, _ptr(R_work), _ptr(I_out),
+                                      _ptr(J_out), _ptr(piv_out), _stream(stream)), "cur_aca_full")
 
 
 def cur_maxvol_rows(h, A, J, r: int, o: CurOpts, I_out, logvol_out=None, swaps_out=None,

@@ -202,6 +202,14 @@ cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r, 
     return aca_select_full(h, A, axis, r, idx_out, cnt, ar, st);
 }
 
+cur_status cur_aca_full(cur_handle* h, const cur_mat* A, int32_t r, void* R_work, int32_t* I_out,
+                        int32_t* J_out, double* piv_out, cudaStream_t st) {
+    if (!h || !mat_ok(A) || !R_work || !I_out || !J_out) return CUR_ERR_ARG;
+    if (r < 1 || r > std::min(A->rows, A->cols)) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    return aca_full_impl(h, A, r, R_work, I_out, J_out, piv_out, ar, st);
+}
+
 static cur_status rows_common(cur_handle* h, const cur_mat* A, const int32_t* idx, int32_t r,
                               const cur_opts* opts, int32_t* out, double* logvol_out,
                               int32_t* swaps_out, bool cols, cudaStream_t st) {

@@ -3,6 +3,7 @@
     python -m paper_2502_11017_gb300.profile_case --call aca --m 16384 --n 8192 --r 3
     python -m paper_2502_11017_gb300.profile_case --call residual --m 16384 --n 8192 --r 64
     python -m paper_2502_11017_gb300.profile_case --call cross --m 65536 --n 8192 --r 64
+    python -m paper_2502_11017_gb300.profile_case --call alg1 --m 65536 --n 8192 --r 64
 
 The matrix is exp(-|x_i - y_j|^2 / h^2) with uniform points (the generator of the
 65536 x 8192 workload, at any size). --reps calls are made after --warmup calls;
@@ -22,7 +23,7 @@ from paper_2502_11017_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols"], required=True)
+    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols", "alg1"], required=True)
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--r", type=int, default=64)
@@ -47,6 +48,8 @@ def main():
     cheb = torch.empty(1, dtype=torch.float64, device=dev)
     fro = torch.empty(1, dtype=torch.float64, device=dev)
     o = cur.opts()
+    Rw = torch.empty((m, n), dtype=torch.float32, device=dev) if a.call == "alg1" else None
+    piv = torch.empty(r, dtype=torch.float64, device=dev)
     if a.call in ("residual", "rows", "cols"):
         cur.cur_cross(h, A, r, a.b_r, a.b_c, o, I, J)
         cur.cur_assemble(h, A, I, J, r, C, U, R, rc)
@@ -63,6 +66,8 @@ def main():
             cur.cur_maxvol_rows(h, A, idx, r, cur.opts(nblocks=a.b_r), I)
         elif a.call == "cols":
             cur.cur_maxvol_cols(h, A, I, r, cur.opts(nblocks=a.b_c), J)
+        elif a.call == "alg1":
+            cur.cur_aca_full(h, A, r, Rw, I, J, piv)
 
     for _ in range(a.warmup):
         call()
@@ -76,6 +81,16 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         print(f"{a.call} m={m} n={n} r={r}: {e0.elapsed_time(e1):.3f} ms (host {1e3 * (time.perf_counter() - t0):.3f} ms)")
+    if a.call == "alg1":
+        # per-step update pass (read + write of the m x n FP32 residual), CUDA events
+        cur.cur_prof_enable(h, 1)
+        call()
+        torch.cuda.synchronize()
+        tot_ms, npass, _k = cur.cur_prof_read(h)
+        if npass:
+            avg = tot_ms / npass
+            gbs = 2 * m * n * 4 / (avg * 1e-3) / 1e9
+            print(f"alg1 update pass: {npass} launches, {avg:.4f} ms average, {gbs:.0f} GB/s (2 m n 4 bytes)")
     st = cur.cur_sync_status(h)
     if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
         raise SystemExit(f"device status {st}")

@@ -481,3 +481,11 @@ def test_aca_full_rank_r_exact_and_early_stop():
     assert st == orc.OK and np.abs(R).max() <= 1e-12 * np.abs(a).max()
     I, J, _p, R, st = orc.aca_full(a, 6)
     assert st == orc.WARN_RANK and len(I) == 4
+
+
+def test_aca_full_replay_reproduces_its_own_run():
+    a = np.random.default_rng(11).standard_normal((20, 15))
+    I, J, piv, R, _st = orc.aca_full(a, 6)
+    piv2, mx, R2 = orc.aca_full_replay(a, I, J)
+    assert piv2 == piv and np.array_equal(R, R2)
+    assert all(abs(p) == m for p, m in zip(piv, mx))   # each pivot is the step's maximum
