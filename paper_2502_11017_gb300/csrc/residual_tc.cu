@@ -6,20 +6,22 @@
 // C = Ch + Cl and W = Wh + Wl with Ch, Wh rounded to TF32 and Cl, Wl the rounded
 // remainders; D = Ch Wh + Ch Wl + Cl Wh keeps ~22 bits, i.e. FP32-level accuracy
 // (the dropped Cl Wl term is ~2^-22 relative). The MMA computes D^T tile by tile
-// (M = 128 columns of A, N = 128 rows, K = r) so that a TMEM lane is a column of A:
-// the epilogue thread of lane j reads A(i, j) for the tile's rows, coalesced across
-// the warp, and A is read from HBM exactly once.
+// (M = 128 columns of A, N = 128 rows, K = r) so that a TMEM lane is a column of A.
 //
-// Per CTA (persistent, one per SM, 320 threads):
-//   warp 0      TMA producer: the C panel (128 rows x r, hi and lo, resident while
-//               the CTA stays on the panel) and a 2-stage ring of W^T tiles (128 x r,
-//               hi and lo), 128-byte swizzled, K-major
-//   warp 1      MMA issuer (one thread): 3 passes x r/8 MMAs per tile into one of two
-//               TMEM accumulators (128 lanes x 128 FP32 columns each)
-//   warps 2..9  epilogue: two warps per TMEM lane quarter, each taking 64 of the tile's
-//               rows; a thread loads its column of those rows of the next tile while it
-//               folds the current one (64 + 64 loads in flight), reads the accumulator
-//               with tcgen05.ld and folds max|E|, sum E^2, sum A^2
+// Per CTA (persistent, one per SM, 608 threads):
+//   warp 0       TMA producer: the C panel (128 rows x r, hi and lo, resident while
+//                the CTA stays on the panel) and the tile's W^T (128 x r) as two
+//                buffers, hi (released after MMA passes 0 and 1) and lo (after pass 2),
+//                128-byte swizzled, K-major
+//   warp 1       MMA issuer (one thread): 3 passes x r/8 MMAs per tile into one of two
+//                TMEM accumulators (128 lanes x 128 FP32 columns each)
+//   warp 18      TMA producer of A: 32-row x 128-column sub-tiles (16 KB, unswizzled)
+//                into a ring of up to 8 slots (6 for r = 64), so A stays in flight
+//                while earlier ones are folded; A is read from HBM exactly once
+//   warps 2..17  epilogue: warp (sub-tile k, column quarter q) reads its 32 accumulator
+//                columns with tcgen05.ld, its column of the staged A rows from shared
+//                memory (conflict-free), and folds max|E|, sum E^2, sum A^2 with
+//                independent chains
 // Waits are bounded; on a timeout the CTA records CUR_ERR_TIMEOUT, waits (bounded) for
 // the copies and MMAs it issued, frees its TMEM and returns.
 
@@ -48,8 +50,11 @@ __global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, c
                                                  int r, int64_t n, int ldk, float* __restrict__ Wh,
                                                  float* __restrict__ Wl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    df64* Us = reinterpret_cast<df64*>(smem_raw);
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) Us[e] = df_from_d(U[e]);
+    df64* Ut = reinterpret_cast<df64*>(smem_raw);   // U^T: lanes with consecutive k read consecutive words
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int k = e / r, l = e - k * r;
+        Ut[l * r + k] = df_from_d(U[e]);
+    }
     __syncthreads();
     const int64_t total = n * ldk;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -61,10 +66,10 @@ __global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, c
             df64 s0{0.f, 0.f}, s1{0.f, 0.f};
             int l = 0;
             for (; l + 1 < r; l += 2) {
-                s0 = df_add(s0, df_mul_f(Us[k * r + l], to_f(R[(int64_t)l * n + j])));
-                s1 = df_add(s1, df_mul_f(Us[k * r + l + 1], to_f(R[(int64_t)(l + 1) * n + j])));
+                s0 = df_add(s0, df_mul_f(Ut[l * r + k], to_f(R[(int64_t)l * n + j])));
+                s1 = df_add(s1, df_mul_f(Ut[(l + 1) * r + k], to_f(R[(int64_t)(l + 1) * n + j])));
             }
-            if (l < r) s0 = df_add(s0, df_mul_f(Us[k * r + l], to_f(R[(int64_t)l * n + j])));
+            if (l < r) s0 = df_add(s0, df_mul_f(Ut[l * r + k], to_f(R[(int64_t)l * n + j])));
             const df64 w = df_add(s0, s1);
             hi = to_tf32(__fadd_rn(w.h, w.l));
             const df64 rem = df_sub(w, df64{hi, 0.f});
@@ -95,46 +100,59 @@ __global__ void tc_prep_c(const TA* __restrict__ C, int64_t m, int r, int ldk, f
     }
 }
 
+constexpr int kAR = 32;                     // rows of A per staged sub-tile
+constexpr int kASub = kAR * kTcBN * 4;      // 16 KB: 32 rows x 128 columns, FP32
+constexpr int kNAMax = 8;                   // A ring slots at most
+constexpr int kEpiWarps = 16;               // epilogue: 4 row sub-tiles x 4 column quarters
+
 struct TcArgs {
-    const float* A;
-    int64_t m, n, ld;
-    int r, nch, ksteps;
+    int64_t m, n;
+    int r, nch, ksteps, na;
     int64_t ntile_n, ntiles;
     double* part;   // 4 doubles per CTA
     int* status;
 };
 
-__global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ CUtensorMap mWh,
+__global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ CUtensorMap mWh,
                                                         const __grid_constant__ CUtensorMap mWl,
                                                         const __grid_constant__ CUtensorMap mCh,
                                                         const __grid_constant__ CUtensorMap mCl,
+                                                        const __grid_constant__ CUtensorMap mA,
                                                         TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int nch = a.nch;
-    unsigned char* CH = sm;
-    unsigned char* CL = CH + nch * kChunk;
-    // W^T stage s: hi at WH(s), lo at WH(s) + nch chunks
-    unsigned char* const W0 = CL + nch * kChunk;
-    const int wstride = 2 * nch * kChunk;
-    __shared__ __align__(8) uint64_t full[2], empty[2], cfull, cempty, afull[2], aempty[2];
+    const int nch = a.nch, na = a.na;
+    unsigned char* CH = sm;                     // C panel, TF32 hi (resident per row panel)
+    unsigned char* CL = CH + nch * kChunk;      // C panel, TF32 lo
+    unsigned char* WH = CL + nch * kChunk;      // W^T tile, hi (released after MMA passes 0, 1)
+    unsigned char* WL = WH + nch * kChunk;      // W^T tile, lo (released after pass 2)
+    unsigned char* AS = WL + nch * kChunk;      // ring of na A sub-tiles (32 x 128 FP32)
+    __shared__ __align__(8) uint64_t whf, whe, wlf, wle, cfull, cempty, accf[2], acce[2], af[kNAMax],
+        ae[kNAMax];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    __shared__ double rmx[8], rse[8], rsa[8];
-    __shared__ int rbad[8];
+    __shared__ double rmx[kEpiWarps], rse[kEpiWarps], rsa[kEpiWarps];
+    __shared__ int rbad[kEpiWarps];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t G = gridDim.x;
     const int64_t t0 = a.ntiles * blockIdx.x / G, t1 = a.ntiles * (blockIdx.x + 1) / G;
+    const uint32_t half_bytes = (uint32_t)nch * kChunk;
 
     if (tid == 0) {
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
-            mbar_init(&afull[s], 1);
-            mbar_init(&aempty[s], 8);
-        }
+        mbar_init(&whf, 1);
+        mbar_init(&whe, 1);
+        mbar_init(&wlf, 1);
+        mbar_init(&wle, 1);
         mbar_init(&cfull, 1);
         mbar_init(&cempty, 1);
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&accf[s], 1);
+            mbar_init(&acce[s], kEpiWarps);
+        }
+        for (int s = 0; s < na; ++s) {
+            mbar_init(&af[s], 1);
+            mbar_init(&ae[s], 4);   // the four column-quarter warps of one row sub-tile
+        }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -145,18 +163,16 @@ __global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ 
     const uint32_t tmem = tslot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ TMA producer
+        // ------------------------------------------------------------ C panel and W^T producer
         if (lane == 0) {
-            int64_t cur_panel = -1;
+            int64_t cur_panel = -1, it = 0, nwh = 0, nwl = 0;   // tiles, hi and lo loads issued
             int cuse = 0;
-            int64_t it = 0;
-            const uint32_t wbytes = 2u * nch * kChunk, cbytes = 2u * nch * kChunk;
             bool ok = true;
-            for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
+            for (int64_t t = t0; t < t1 && ok && !abort_flag; ++t, ++it) {
                 const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
                 if (panel != cur_panel) {
                     if (cuse > 0 && !mbar_wait(&cempty, (cuse - 1) & 1)) { ok = false; break; }
-                    mbar_expect_tx(&cfull, cbytes);
+                    mbar_expect_tx(&cfull, 2 * half_bytes);
                     for (int c = 0; c < nch; ++c) {
                         tma_load_2d(CH + c * kChunk, &mCh, &cfull, 32 * c, (int)(panel * kTcBM));
                         tma_load_2d(CL + c * kChunk, &mCl, &cfull, 32 * c, (int)(panel * kTcBM));
@@ -164,34 +180,37 @@ __global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ 
                     ++cuse;
                     cur_panel = panel;
                 }
-                const int s = (int)(it & 1);
-                const int64_t u = it >> 1;
-                if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { ok = false; break; }
-                mbar_expect_tx(&full[s], wbytes);
-                for (int c = 0; c < nch; ++c) {
-                    unsigned char* wh = W0 + s * wstride;
-                    tma_load_2d(wh + c * kChunk, &mWh, &full[s], 32 * c, (int)(ct * kTcBN));
-                    tma_load_2d(wh + (nch + c) * kChunk, &mWl, &full[s], 32 * c, (int)(ct * kTcBN));
+                // hi, then lo, in the order the MMAs free them
+                for (int part = 0; part < 2; ++part) {
+                    uint64_t* fb = part ? &wlf : &whf;
+                    uint64_t* eb = part ? &wle : &whe;
+                    if (it > 0 && !mbar_wait(eb, (uint32_t)((it - 1) & 1))) { ok = false; break; }
+                    mbar_expect_tx(fb, half_bytes);
+                    for (int c = 0; c < nch; ++c)
+                        tma_load_2d((part ? WL : WH) + c * kChunk, part ? &mWl : &mWh, fb, 32 * c, (int)(ct * kTcBN));
+                    ++(part ? nwl : nwh);
                 }
             }
             if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
-            // every copy issued has completed before the CTA may leave: the MMA warp
-            // consumed (waited on) each full barrier, except after an abort
-            if (!ok || abort_flag) {
-                for (int s = 0; s < 2; ++s) mbar_wait(&full[s], (uint32_t)(((it - 1 - s) >> 1) & 1));
-                mbar_wait(&cfull, (cuse - 1) & 1);
+            // after an abort, wait (bounded) for the last copy into each buffer: the MMA
+            // warp consumed every full barrier otherwise
+            if (abort_flag) {
+                if (nwh > 0) mbar_wait(&whf, (uint32_t)((nwh - 1) & 1));
+                if (nwl > 0) mbar_wait(&wlf, (uint32_t)((nwl - 1) & 1));
+                if (cuse > 0) mbar_wait(&cfull, (uint32_t)((cuse - 1) & 1));
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(kTcBN, kTcBM);
-            int64_t cur_panel = -1;
+            int64_t cur_panel = -1, it = 0;
             int cuse = 0;
-            int64_t it = 0;
             bool ok = true;
-            const uint32_t ch = su32(CH), cl = su32(CL);
-            for (int64_t t = t0; t < t1 && ok; ++t, ++it) {
+            const uint32_t ch = su32(CH), cl = su32(CL), wh = su32(WH), wl = su32(WL);
+            uint64_t* last_bar = nullptr;   // the barrier of the last commit and its phase
+            uint32_t last_par = 0;
+            for (int64_t t = t0; t < t1 && !abort_flag; ++t, ++it) {
                 const int64_t panel = t / a.ntile_n;
                 if (panel != cur_panel) {
                     if (cuse > 0) mma_commit(&cempty);
@@ -199,97 +218,138 @@ __global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ 
                     ++cuse;
                     cur_panel = panel;
                 }
-                const int s = (int)(it & 1), b = (int)(it & 1);
+                const int b = (int)(it & 1);
                 const int64_t u = it >> 1;
-                if (!mbar_wait(&full[s], (uint32_t)(u & 1))) { ok = false; break; }
-                if (u > 0 && !mbar_wait(&aempty[b], (uint32_t)((u - 1) & 1))) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t wh = su32(W0 + s * wstride), wl = wh + (uint32_t)(nch * kChunk);
+                if (u > 0 && !mbar_wait(&acce[b], (uint32_t)((u - 1) & 1))) { ok = false; break; }
                 const uint32_t d = tmem + (uint32_t)(b * kTcBM);
-                for (int pass = 0; pass < 3; ++pass) {
-                    const uint32_t aop = pass == 2 ? wl : wh;
-                    const uint32_t bop = pass == 1 ? cl : ch;
-                    for (int k = 0; k < a.ksteps; ++k) {
-                        const uint32_t off = (uint32_t)((k >> 2) * kChunk + (k & 3) * 32);
-                        mma_tf32(d, sdesc_k128(aop + off), sdesc_k128(bop + off), idesc, (pass | k) != 0);
+                bool fine = true;
+                // passes 0 and 1 (Wh Ch, Wh Cl) release the hi buffer; pass 2 (Wl Ch) the lo
+                for (int part = 0; part < 2; ++part) {
+                    uint64_t* fb = part ? &wlf : &whf;
+                    uint64_t* eb = part ? &wle : &whe;
+                    if (!mbar_wait(fb, (uint32_t)(it & 1))) { fine = false; break; }
+                    tc_fence_after();
+                    const uint32_t wop = part ? wl : wh;
+                    for (int pass = part ? 2 : 0; pass < (part ? 3 : 2); ++pass) {
+                        const uint32_t bop = pass == 1 ? cl : ch;
+                        for (int k = 0; k < a.ksteps; ++k) {
+                            const uint32_t off = (uint32_t)((k >> 2) * kChunk + (k & 3) * 32);
+                            mma_tf32(d, sdesc_k128(wop + off), sdesc_k128(bop + off), idesc, (pass | k) != 0);
+                        }
                     }
+                    mma_commit(eb);
+                    last_bar = eb;
+                    last_par = (uint32_t)(it & 1);
                 }
-                mma_commit(&empty[s]);
-                mma_commit(&afull[b]);
+                if (!fine) { ok = false; break; }
+                mma_commit(&accf[b]);
+                last_bar = &accf[b];
+                last_par = (uint32_t)(u & 1);
             }
             if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
-            // the last commits complete when every MMA issued has finished
-            if (it > 0) mbar_wait(&afull[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1));
+            // every MMA issued has finished once the last commit has arrived
+            if (last_bar) mbar_wait(last_bar, last_par);
+        }
+    } else if (warp == 2 + kEpiWarps) {
+        // ------------------------------------------------------------ A producer
+        if (lane == 0) {
+            int64_t idx = 0;
+            bool ok = true;
+            for (int64_t t = t0; t < t1 && ok && !abort_flag; ++t) {
+                const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
+                for (int k = 0; k < kTcBM / kAR; ++k, ++idx) {
+                    const int slot = (int)(idx % na);
+                    const int64_t use = idx / na;
+                    if (use > 0 && !mbar_wait(&ae[slot], (uint32_t)((use - 1) & 1))) { ok = false; break; }
+                    mbar_expect_tx(&af[slot], (uint32_t)kASub);
+                    tma_load_2d(AS + (size_t)slot * kASub, &mA, &af[slot], (int)(ct * kTcBN),
+                                (int)(panel * kTcBM + kAR * k));
+                }
+            }
+            if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
+            if (abort_flag)
+                for (int64_t q = idx - 1; q >= 0 && q >= idx - na; --q)
+                    mbar_wait(&af[q % na], (uint32_t)((q / na) & 1));
         }
     } else {
-        // ------------------------------------------------------------ epilogue
-        constexpr int HR = kTcBM / 2;      // rows per epilogue warp
-        const int q = warp & 3;            // TMEM lane quarter of this warp
-        const int half = (warp - 2) >> 2;  // which 64 rows of the tile
-        const int jl = 32 * q + lane;      // column within the tile = TMEM lane
-        const int ew = warp - 2;           // epilogue warp index 0..7
+        // ------------------------------------------------------------ epilogue (warps 2..17)
+        const int q = warp & 3;              // TMEM lane quarter of this warp = column quarter
+        const int k = (warp - 2) >> 2;       // row sub-tile: rows 32 k .. 32 k + 31 of the tile
+        const int jl = 32 * q + lane;        // column within the tile = TMEM lane
+        const int ew = warp - 2;
         float mx = 0.f;
         double se = 0.0, sa = 0.0;
         int bad = 0;
-        float cur[HR], nxt[HR];
-        // first strip of column jl (rows half*64 .. +63 of tile t) of this CTA's range
-        if (t0 < t1) {
-            const int64_t panel = t0 / a.ntile_n, ct = t0 - panel * a.ntile_n;
-            const int64_t i0 = panel * kTcBM + half * HR, j = ct * kTcBN + jl;
-            const bool jv = j < a.n;
-            const float* col = a.A + i0 * a.ld + (jv ? j : 0);
-#pragma unroll
-            for (int rr = 0; rr < HR; ++rr)
-                cur[rr] = (jv && i0 + rr < a.m) ? __ldcs(col + (int64_t)rr * a.ld) : 0.f;
-        }
         int64_t it = 0;
         for (int64_t t = t0; t < t1; ++t, ++it) {
-            if (t + 1 < t1) {
-                const int64_t pn = (t + 1) / a.ntile_n, cn = (t + 1) - pn * a.ntile_n;
-                const int64_t in0 = pn * kTcBM + half * HR, jn = cn * kTcBN + jl;
-                const bool jnv = jn < a.n;
-                const float* col = a.A + in0 * a.ld + (jnv ? jn : 0);
-#pragma unroll
-                for (int rr = 0; rr < HR; ++rr)
-                    nxt[rr] = (jnv && in0 + rr < a.m) ? __ldcs(col + (int64_t)rr * a.ld) : 0.f;
-            }
             const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
-            const int64_t i0 = panel * kTcBM + half * HR, j = ct * kTcBN + jl;
+            const int64_t j = ct * kTcBN + jl;
+            const int64_t rbase = panel * kTcBM + kAR * k;
             const bool jv = j < a.n;
+            const bool full = jv && rbase + kAR <= a.m;   // every row of the sub-tile exists
             const int b = (int)(it & 1);
-            if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1))) {
+            if (!mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1))) {
                 abort_flag = 1;
                 set_status(a.status, CUR_ERR_TIMEOUT);
                 break;
             }
+            const int64_t idx = 4 * it + k;
+            const int slot = (int)(idx % na);
+            if (!mbar_wait(&af[slot], (uint32_t)((idx / na) & 1))) {
+                abort_flag = 1;
+                set_status(a.status, CUR_ERR_TIMEOUT);
+                break;
+            }
+            __syncwarp();
             tc_fence_after();
+            const float* As = reinterpret_cast<const float*>(AS + (size_t)slot * kASub) + jl;
             float tse = 0.f, tsa = 0.f;
 #pragma unroll
-            for (int c = 0; c < HR / 16; ++c) {
+            for (int c = 0; c < 2; ++c) {
                 float dv[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + half * HR + 16 * c), dv);
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + kAR * k + 16 * c), dv);
+                if (full) {
+                    // four independent chains per sum; a NaN anywhere makes the group's
+                    // sum of squares NaN (fmaxf alone would drop it)
+                    float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f},
+                          a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const int rr = 16 * c + i;
-                    if (jv && i0 + rr < a.m) {
-                        const float e = cur[rr] - dv[i];
-                        if (!(fabsf(e) <= INFINITY)) bad = 1;
-                        mx = fmaxf(mx, fabsf(e));
-                        tse = fmaf(e, e, tse);
-                        tsa = fmaf(cur[rr], cur[rr], tsa);
+                    for (int i = 0; i < 16; ++i) {
+                        const float x = As[(16 * c + i) * kTcBN];
+                        const float e = x - dv[i];
+                        m4[i & 3] = fmaxf(m4[i & 3], fabsf(e));
+                        s4[i & 3] = fmaf(e, e, s4[i & 3]);
+                        a4[i & 3] = fmaf(x, x, a4[i & 3]);
+                    }
+                    const float gs = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                    if (gs != gs) bad = 1;
+                    mx = fmaxf(mx, fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])));
+                    tse += gs;
+                    tsa += (a4[0] + a4[1]) + (a4[2] + a4[3]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float x = As[(16 * c + i) * kTcBN];
+                        if (jv && rbase + 16 * c + i < a.m) {
+                            const float e = x - dv[i];
+                            if (!(fabsf(e) <= INFINITY)) bad = 1;
+                            mx = fmaxf(mx, fabsf(e));
+                            tse = fmaf(e, e, tse);
+                            tsa = fmaf(x, x, tsa);
+                        }
                     }
                 }
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ae[slot]);
             se += (double)tse;
             sa += (double)tsa;
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&aempty[b]);
-#pragma unroll
-            for (int rr = 0; rr < HR; ++rr) cur[rr] = nxt[rr];
+            if (lane == 0) mbar_arrive(&acce[b]);
             if (abort_flag) break;
         }
-        // reduce over the 256 epilogue threads
+        // reduce over the epilogue threads
         double dmx = mx;
         for (int o = 16; o > 0; o >>= 1) {
             dmx = fmax(dmx, __shfl_xor_sync(0xffffffffu, dmx, o));
@@ -304,7 +364,7 @@ __global__ void __launch_bounds__(320, 1) residual_tc_k(const __grid_constant__ 
     if (tid == 0) {
         double m1 = 0.0, m2 = 0.0, m3 = 0.0;
         int bd = 0;
-        for (int w = 0; w < 8; ++w) { m1 = fmax(m1, rmx[w]); m2 += rse[w]; m3 += rsa[w]; bd |= rbad[w]; }
+        for (int w = 0; w < kEpiWarps; ++w) { m1 = fmax(m1, rmx[w]); m2 += rse[w]; m3 += rsa[w]; bd |= rbad[w]; }
         a.part[blockIdx.x * 4 + 0] = m1;
         a.part[blockIdx.x * 4 + 1] = m2;
         a.part[blockIdx.x * 4 + 2] = m3;
@@ -362,6 +422,22 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// A (m x n FP32, leading dimension ld), boxes of 128 columns x 32 rows, no swizzle:
+// a staged sub-tile is row-major 32 x 128 in shared memory. Needs a 16-byte aligned base
+// and ld % 4 == 0.
+static bool make_map_a(CUtensorMap* map, const float* base, int64_t m, int64_t n, int64_t ld) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld & 3) != 0) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
+    cuuint64_t gstr[1] = {(cuuint64_t)ld * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBN, (cuuint32_t)kAR};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // rows x ldk FP32, boxes of 32 elements x 128 rows, 128-byte swizzle.
 static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int r, int ldk) {
     auto enc = encode_fn();
@@ -398,7 +474,8 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     const int G = h->num_sms;
     double* part = ar.get<double>((size_t)G * 4);
     if (!ar.ok) return CUR_ERR_NOMEM;
-    CUtensorMap mWh, mWl, mCh, mCl;
+    CUtensorMap mWh, mWl, mCh, mCl, mA;
+    if (!make_map_a(&mA, static_cast<const float*>(Am->data), m, n, Am->ld)) return CUR_ERR_ARG;
     if (!make_map(&mWh, Wh, n, r, ldk) || !make_map(&mWl, Wl, n, r, ldk) || !make_map(&mCh, Ch, m, r, ldk) ||
         !make_map(&mCl, Cl, m, r, ldk))
         return CUR_ERR_ARG;
@@ -412,10 +489,8 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     CUR_CK(cudaGetLastError());
     note_launch();
     TcArgs a{};
-    a.A = static_cast<const float*>(Am->data);
     a.m = m;
     a.n = n;
-    a.ld = Am->ld;
     a.r = r;
     a.nch = nch;
     a.ksteps = (r + 7) / 8;
@@ -424,9 +499,14 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     a.part = part;
     a.status = h->status;
     const int grid = (int)std::min<int64_t>(G, a.ntiles);
-    const size_t sm = (size_t)6 * nch * kChunk + 1024;
+    // C panel and W^T tile (hi and lo each), then as many 16 KB A slots as fit
+    const size_t fixed = (size_t)4 * nch * kChunk + 1024;
+    const size_t budget = 225 * 1024;
+    a.na = (int)std::min<size_t>(kNAMax, (budget - fixed) / kASub);
+    if (a.na < 4) return CUR_ERR_ARG;
+    const size_t sm = fixed + (size_t)a.na * kASub;
     CUR_CK(cudaFuncSetAttribute((const void*)residual_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    residual_tc_k<<<grid, 320, sm, st>>>(mWh, mWl, mCh, mCl, a);
+    residual_tc_k<<<grid, 32 * (3 + kEpiWarps), sm, st>>>(mWh, mWl, mCh, mCl, mA, a);
     CUR_CK(cudaGetLastError());
     note_launch();
     tc_final_k<<<1, 256, 0, st>>>(part, grid, cheb, fro, h->status);
