@@ -536,12 +536,19 @@ def residual(A, C, U, R, chunk_rows: int = 4096):
 def dominance(A, I, J):
     """(max|A(:,J) A(I,J)^-1|, max|A(I,J)^-1 A(I,:)|): both are <= 1 + delta for a
     cross that maxvol leaves unchanged on both sides."""
-    A64 = np.asarray(A, dtype=np.float64)
-    M = A64[np.ix_(list(I), list(J))]
-    lu, perm, _ = lu_factor(M)
+    A = np.asarray(A)
+    CJ = np.asarray(A[:, list(J)], dtype=np.float64)
+    RI = np.asarray(A[list(I), :], dtype=np.float64)
+    return dominance_parts(CJ, RI, CJ[list(I), :])
+
+
+def dominance_parts(CJ, RI, M):
+    """dominance() from the parts C = A(:,J), R = A(I,:) and M = A(I,J), for matrices too
+    large to convert whole."""
+    lu, perm, _ = lu_factor(np.asarray(M, dtype=np.float64))
     Minv = lu_inverse(lu, perm)
-    rows = np.abs(A64[:, list(J)] @ Minv).max()
-    cols = np.abs(Minv @ A64[list(I), :]).max()
+    rows = np.abs(np.asarray(CJ, dtype=np.float64) @ Minv).max()
+    cols = np.abs(Minv @ np.asarray(RI, dtype=np.float64)).max()
     return float(rows), float(cols)
 
 

@@ -97,6 +97,7 @@ size_t cur_workspace_size(int64_t m, int64_t n, int32_t r, cur_dtype dtype) {
     b += 8 * ((size_t)4864 * 128 + 8 * mx);                   // Algorithm 3 partials and vectors
     b += 8 * R * mx * 2;                                      // W and Q of Algorithm 3
     b += cs * R * (size_t)(m + n) * 4;                        // bases, B, merge unions
+    b += cs * R * mx;                                         // B in global memory for large r
     b += 8 * R * R * (size_t)((m + n) / R + 16) * 2;          // M^-1 per problem (two types)
     b += 8 * R * (size_t)n + 8 * 4 * (size_t)(m / 64 + 1) * 64;  // residual W and partials
     return b;

@@ -55,6 +55,7 @@ struct MvArgs {
     int max_swaps;
     double drift_max;          // refactorise once sum(swaps * kappa(M)) since the last factorisation exceeds it
     int keep_singular_set;     // 1: a set that turns singular stays as it is; 0: back to the start set
+    void* bglob;               // rows x r B in global memory (compute type), or null: B in shared memory
     const int32_t* cta_prob;   // per CTA slot
     const int32_t* cta_part;
     int cta_base;              // first slot of this launch (waves)
@@ -452,18 +453,23 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
 // The first CTA of a group keeps M^-1 (FP64) in shared memory when r <= kMsMax.
 constexpr int kMsMax = 64;
 
-// Layout: [B slice | M^-1 (compute type) | colj | wrow] or, while M^-1 is being
-// refactorised, [C(S,:) in FP64 | pivot column | pivots] over the same bytes (both are
-// dead then); after it the first CTA's MinvKeeper.
+// Layout: [B slice | M^-1 (compute type) | colj | wrow] or, with the B slice in global
+// memory (a stage whose B does not fit in the shared memory of co-resident CTAs),
+// [M^-1 | colj | wrow | staging of kEngStage C rows]; while M^-1 is being refactorised,
+// [C(S,:) in FP64 | pivot column | pivots] over the same bytes (all dead then); after it
+// the first CTA's MinvKeeper.
+constexpr int kEngStage = 32;
+
 template <typename TB>
 struct EngineSmem {
-    __host__ __device__ static size_t head(int nloc, int r) {
-        const size_t b = ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
+    __host__ __device__ static size_t head(int nloc, int r, bool gmode = false) {
+        const size_t b = gmode ? ((size_t)r * r + nloc + r + (size_t)kEngStage * r) * sizeof(TB)
+                               : ((size_t)nloc * r + (size_t)r * r + nloc + r) * sizeof(TB);
         const size_t gj = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int);
         return ((b > gj ? b : gj) + 15) / 16 * 16;
     }
-    static size_t bytes(int nloc, int r) {
-        size_t b = head(nloc, r) + (size_t)8 * r * sizeof(double) + 64;
+    static size_t bytes(int nloc, int r, bool gmode = false) {
+        size_t b = head(nloc, r, gmode) + (size_t)8 * r * sizeof(double) + 64;
         if (r <= kMsMax) b += (size_t)r * r * sizeof(double);
         return b;
     }
@@ -660,11 +666,14 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     const int r = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
     const bool solo = G == 1;                   // one CTA: no inter-CTA exchange at all
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
-    TB* Bs = reinterpret_cast<TB*>(smem_raw);   // nloc x r slice of B
-    TB* Mi = Bs + (size_t)nloc * r;             // r x r: M^-1 in the compute type
+    const bool gmode = a.bglob != nullptr;
+    TB* Bs = gmode ? static_cast<TB*>(a.bglob) + (pr.base + lo) * r   // nloc x r slice of B
+                   : reinterpret_cast<TB*>(smem_raw);
+    TB* Mi = gmode ? reinterpret_cast<TB*>(smem_raw) : Bs + (size_t)nloc * r;   // r x r: M^-1 (compute type)
     TB* colj = Mi + (size_t)r * r;              // nloc
     TB* wrow = colj + nloc;                     // r: winning row of B, then B(i,:) - e_j
-    const size_t off = EngineSmem<TB>::head(nloc, r);
+    TB* cstage = wrow + r;                      // global-memory mode: kEngStage C rows
+    const size_t off = EngineSmem<TB>::head(nloc, r, gmode);
     double* Mg = a.minv64 + (int64_t)pb * minv_stride(r);       // M^-1 in global memory (FP64)
     __shared__ double s_b;
     __shared__ long long s_w;
@@ -726,12 +735,12 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         {
             // C rows pass through shared memory a chunk at a time (coalesced loads), then
             // B rows = C rows M^-1 with 8 outputs per thread in registers; the chunk's
-            // own rows of Bs serve as the staging area.
+            // own rows of Bs serve as the staging area (a separate one when B is global).
             const TB* Cs = basis + (int64_t)lo * r;
-            const int chunk = max(1, min(32, 8 * nt / r));
+            const int chunk = max(1, min(kEngStage, 8 * nt / r));
             for (int i0 = 0; i0 < nloc; i0 += chunk) {
                 const int nr = min(chunk, nloc - i0);
-                TB* stage = Bs + (size_t)i0 * r;
+                TB* stage = gmode ? cstage : Bs + (size_t)i0 * r;
                 for (int e = tid; e < nr * r; e += nt) stage[e] = Cs[(int64_t)i0 * r + e];
                 __syncthreads();
                 TB out[8];
@@ -747,10 +756,11 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
                     out[u] = sum;
                 }
                 __syncthreads();
+                TB* dst = Bs + (size_t)i0 * r;
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int e = tid + u * nt;
-                    if (e < nr * r) stage[e] = out[u];
+                    if (e < nr * r) dst[e] = out[u];
                 }
                 __syncthreads();
             }
@@ -1052,6 +1062,7 @@ struct Stage {
     double* aux = nullptr;
     std::vector<int> stat, sw;  // host copies after read()
     bool keep_singular_set = false;
+    TB* bglob = nullptr;        // B in global memory when it cannot live in shared memory
 };
 
 template <typename TB>
@@ -1061,16 +1072,25 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     const int cap = rows_cap<TB>(r);
     int64_t tot_p = 0;
     for (auto& pr : sg.probs) tot_p += pr.p;
+    // B in shared memory needs ceil(p / cap) co-resident CTAs per problem; a problem that
+    // would need more than one per SM puts the stage's B in global memory instead
+    bool gmode = false;
+    int64_t rows_end = 0;
+    for (auto& pr : sg.probs) {
+        if ((pr.p + cap - 1) / cap > h->num_sms) gmode = true;
+        rows_end = std::max<int64_t>(rows_end, pr.base + pr.p);
+    }
     int slots = 0;
     for (auto& pr : sg.probs) {
         // one CTA when the problem fits (no inter-CTA exchange); otherwise spread large
         // problems over the SMs in proportion to their size
-        int64_t G = (pr.p + cap - 1) / cap;
-        if (G > 1) {
+        int64_t G = gmode ? 1 : (pr.p + cap - 1) / cap;
+        if (G > 1 || gmode) {
             const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
                                                      (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
             G = std::max<int64_t>(G, spread);
         }
+        G = std::max<int64_t>(1, G);
         const int rpc = (int)((pr.p + G - 1) / G);
         G = (pr.p + rpc - 1) / rpc;
         pr.G = (int)G;
@@ -1094,6 +1114,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     sg.keyi = ar.get<long long>((size_t)2 * slots);
     sg.pub = ar.get<TB>((size_t)2 * slots * r);
     sg.aux = ar.get<double>((size_t)2 * slots);
+    sg.bglob = gmode ? ar.get<TB>((size_t)rows_end * r) : nullptr;
     if (!ar.ok) return CUR_ERR_NOMEM;
     return CUR_OK;
 }
@@ -1138,6 +1159,7 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     // u = 2^-48): the carried inverse while sum(swaps * kappa) <= 2^18, i.e. drift <= 2^-30.
     a.drift_max = std::is_same<TB, double>::value ? 0.0 : 262144.0;
     a.keep_singular_set = sg.keep_singular_set ? 1 : 0;
+    a.bglob = sg.bglob;
     a.cta_prob = sg.dtab;
     a.cta_part = sg.dtab + slots;
     a.lu_mask = sg.dtab + 2 * slots;
@@ -1153,19 +1175,21 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     a.aux = sg.aux;
     a.status = h->status;
 
-    const size_t sm_eng = EngineSmem<TB>::bytes(sg.max_rpc, r);
+    const size_t sm_eng = EngineSmem<TB>::bytes(sg.max_rpc, r, sg.bglob != nullptr);
     const size_t sm_start = StartSmem<TB>::bytes(sg.max_rpc, r);
     const size_t sm_lu = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
     CUR_TRY(set_smem_attr(mv_engine<TB>, sm_eng));
-    CUR_TRY(set_smem_attr(mv_start<TB>, sm_start));
     CUR_TRY(set_smem_attr(mv_lu<TB>, sm_lu));
-    int occ_eng = 0, occ_start = 0;
+    int occ_eng = 0, occ_start = 1;
     CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_eng, mv_engine<TB>, 256, sm_eng));
-    CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_start, mv_start<TB>, 256, sm_start));
+    if (aca_start) {
+        CUR_TRY(set_smem_attr(mv_start<TB>, sm_start));
+        CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_start, mv_start<TB>, 256, sm_start));
+    }
     const int cap_eng = std::max(1, occ_eng) * h->num_sms;
     const int cap_start = std::max(1, occ_start) * h->num_sms;
     for (auto& pr : sg.probs)
-        if (pr.G > cap_eng || pr.G > cap_start) return CUR_ERR_ARG;
+        if (pr.G > cap_eng || (aca_start && pr.G > cap_start)) return CUR_ERR_ARG;
     // waves: consecutive whole groups within the co-residency capacity
     auto waves = [&](int capc) {
         std::vector<std::pair<int, int>> w;

@@ -75,6 +75,30 @@ def gaussian_kernel(m: int = 65536, n: int = 8192, h: float = 0.2,
     return out
 
 
+def bf16_factor_product(m: int = 262144, n: int = 16384, k: int = 128, noise_std: float = 1e-2,
+                        seed: int = SEED_BASE + 4, device="cuda", chunk_rows: int = 16384):
+    """A = X diag(sigma) Y^T + noise rounded once to BF16, as a torch tensor on `device`:
+    X (m x k), Y (n x k) i.i.d. N(0,1) from numpy (seeded), sigma_j = exp(-j/20) for
+    j = 1..k, noise i.i.d. N(0, noise_std^2) from torch's counter-based generator on the
+    device (seeded). The matrix is formed row chunk by row chunk on the device (8.6 GB at
+    the default size; the host never holds it)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    x = torch.from_numpy(rng.standard_normal((m, k)).astype(np.float32)).to(device)
+    y = torch.from_numpy(rng.standard_normal((n, k)).astype(np.float32)).to(device)
+    sig = torch.from_numpy(np.exp(-np.arange(1, k + 1) / 20.0).astype(np.float32)).to(device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    out = torch.empty((m, n), dtype=torch.bfloat16, device=device)
+    ys = (y * sig).t().contiguous()
+    for s in range(0, m, chunk_rows):
+        e = min(s + chunk_rows, m)
+        blk = x[s:e] @ ys
+        blk += noise_std * torch.randn((e - s, n), generator=g, device=device, dtype=torch.float32)
+        out[s:e] = blk.to(torch.bfloat16)
+    return out
+
+
 def hilbert(n: int) -> np.ndarray:
     """H_ij = 1/(i+j-1) with 1-based i, j (Section 3.1, Hilbert experiment)."""
     i = np.arange(1, n + 1, dtype=np.float64)
