@@ -53,6 +53,26 @@ __device__ __forceinline__ void load4_guard(const TA* row, int64_t col, int64_t 
     for (int k = 0; k < 4; ++k) v[k] = (col + k < n) ? (TV)to_d(row[col + k]) : (TV)0;
 }
 
+// Columns per lane of the column pass: 16 bytes of A per lane and row (8 for BF16).
+template <typename TA> struct ColsPerLane { static constexpr int v = sizeof(TA) == 2 ? 8 : 4; };
+
+__device__ __forceinline__ void loadc(const float* p, float* v) { load4(p, v); }
+__device__ __forceinline__ void loadc(const double* p, double* v) { load4(p, v); }
+__device__ __forceinline__ void loadc(const __nv_bfloat16* p, float* v) {
+    const uint4 x = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = __uint_as_float(w[k] << 16);
+        v[2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+}
+template <int CPL, typename TA, typename TV>
+__device__ __forceinline__ void loadc_guard(const TA* row, int64_t col, int64_t n, TV* v) {
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) v[k] = (col + k < n) ? (TV)to_d(row[col + k]) : (TV)0;
+}
+
 template <typename TA> struct ValT { using type = float; };
 template <> struct ValT<double> { using type = double; };
 
@@ -87,8 +107,9 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 }
 
 // part[rc * n + j] = sum over rows i of chunk rc of a_ij * q_i (kDot) or a_ij^2 (kNorm).
-// grid = (ceil(n / 128), RC), block = 256 (8 warps). Warp w takes rows r0 + w, r0 + w + 8,
-// ...; lane l takes the 4 columns 128 * blockIdx.x + 4 l .. + 3.
+// grid = (ceil(n / (32 CPL)), RC), block = 256 (8 warps). Warp w takes rows r0 + w,
+// r0 + w + 8, ...; lane l takes the CPL columns 32 CPL blockIdx.x + CPL l .. (CPL = 4,
+// or 8 for BF16: 16 bytes per lane and row either way).
 template <typename TA, int MODE, bool VEC>
 __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, int64_t m, int64_t n,
                                                      int64_t ld, int64_t chunk,
@@ -99,21 +120,22 @@ __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, i
                                                      const int* __restrict__ stop) {
     using V = typename ValT<TA>::type;
     using PT = PartT<TA>;
-    __shared__ PT red[8][128];
+    constexpr int CPL = ColsPerLane<TA>::v, TW = 32 * CPL;
+    __shared__ PT red[8][TW];
     if (*stop) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t col = (int64_t)blockIdx.x * 128 + lane * 4;
+    const int64_t col = (int64_t)blockIdx.x * TW + lane * CPL;
     const int64_t r0 = (int64_t)blockIdx.y * chunk;
     const int64_t r1 = min(r0 + chunk, m);
-    const bool full = VEC && (col + 3 < n);
-    AccOf<TA> acc[4];
+    const bool full = VEC && (col + CPL - 1 < n);
+    AccOf<TA> acc[CPL];
     int64_t i = r0 + warp;
     for (; i + 24 < r1; i += 32) {
-        V x[4][4];
+        V x[4][CPL];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const TA* row = A + (i + 8 * u) * ld;
-            if (full) load4(row + col, x[u]); else load4_guard(row, col, n, x[u]);
+            if (full) loadc(row + col, x[u]); else loadc_guard<CPL>(row, col, n, x[u]);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -123,26 +145,26 @@ __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, i
                 else { h = qh[i + 8 * u]; l = ql[i + 8 * u]; }
             }
 #pragma unroll
-            for (int c = 0; c < 4; ++c) acc_add(acc[c], x[u][c], MODE, qd, h, l);
+            for (int c = 0; c < CPL; ++c) acc_add(acc[c], x[u][c], MODE, qd, h, l);
         }
     }
     for (; i < r1; i += 8) {
-        V x[4];
+        V x[CPL];
         const TA* row = A + i * ld;
-        if (full) load4(row + col, x); else load4_guard(row, col, n, x);
+        if (full) loadc(row + col, x); else loadc_guard<CPL>(row, col, n, x);
         double qd = 0.0; float h = 0.f, l = 0.f;
         if (MODE == kDot) {
             if (std::is_same<TA, double>::value) qd = q64[i];
             else { h = qh[i]; l = ql[i]; }
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc_add(acc[c], x[c], MODE, qd, h, l);
+        for (int c = 0; c < CPL; ++c) acc_add(acc[c], x[c], MODE, qd, h, l);
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) red[warp][lane * 4 + c] = part_value(acc[c]);
+    for (int c = 0; c < CPL; ++c) red[warp][lane * CPL + c] = part_value(acc[c]);
     __syncthreads();
-    if (threadIdx.x < 128) {
-        const int64_t j = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (threadIdx.x < TW) {
+        const int64_t j = (int64_t)blockIdx.x * TW + threadIdx.x;
         if (j < n) {
             PT s0 = part_add(red[0][threadIdx.x], red[1][threadIdx.x]);
             PT s1 = part_add(red[2][threadIdx.x], red[3][threadIdx.x]);
@@ -222,24 +244,34 @@ __device__ __forceinline__ double pivot_elem(const AcaParams& P, int64_t i, int6
     return P.axis == 1 ? to_d(A[i * P.ld + p]) : to_d(A[p * P.ld + i]);
 }
 
-// acc_a -= sum_kk Q(kk, ia) s(kk) and acc_b likewise for row ib, two interleaved chains
-// per row (even and odd kk) so that four independent dependency chains are in flight.
+// acc_a -= sum_kk Q(kk, ia) s(kk) and acc_b likewise for row ib. The Q values of eight
+// directions are loaded before any arithmetic (32 loads in flight per thread), and two
+// interleaved chains per row (even and odd kk) keep four dependency chains in flight.
+constexpr int kQB = 8;
 __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int64_t len, int k,
                                           const df64* s, int64_t ia, int64_t ib, bool vb,
                                           df64& acc_a, df64& acc_b) {
     df64 a1{0.f, 0.f}, b1{0.f, 0.f};
     const int64_t ibb = vb ? ib : ia;
-#pragma unroll 2
-    for (int kk = 0; kk < k; kk += 2) {
-        const bool two = kk + 1 < k;
-        const int64_t o0 = (int64_t)kk * len, o1 = two ? (int64_t)(kk + 1) * len : o0;
-        const df64 qa0{Qh[o0 + ia], Ql[o0 + ia]}, qb0{Qh[o0 + ibb], Ql[o0 + ibb]};
-        const df64 qa1{Qh[o1 + ia], Ql[o1 + ia]}, qb1{Qh[o1 + ibb], Ql[o1 + ibb]};
-        const df64 s0 = s[kk], s1 = two ? s[kk + 1] : df64{0.f, 0.f};
-        acc_a = df_sub(acc_a, df_mul(qa0, s0));
-        acc_b = df_sub(acc_b, df_mul(qb0, s0));
-        a1 = df_sub(a1, df_mul(qa1, s1));
-        b1 = df_sub(b1, df_mul(qb1, s1));
+    for (int k0 = 0; k0 < k; k0 += kQB) {
+        float ha[kQB], la[kQB], hb[kQB], lb[kQB];
+#pragma unroll
+        for (int u = 0; u < kQB; ++u) {
+            const int64_t o = (int64_t)min(k0 + u, k - 1) * len;
+            ha[u] = Qh[o + ia];
+            la[u] = Ql[o + ia];
+            hb[u] = Qh[o + ibb];
+            lb[u] = Ql[o + ibb];
+        }
+#pragma unroll
+        for (int u = 0; u < kQB; u += 2) {
+            const df64 s0 = k0 + u < k ? s[k0 + u] : df64{0.f, 0.f};
+            const df64 s1 = k0 + u + 1 < k ? s[k0 + u + 1] : df64{0.f, 0.f};
+            acc_a = df_sub(acc_a, df_mul(df64{ha[u], la[u]}, s0));
+            acc_b = df_sub(acc_b, df_mul(df64{hb[u], lb[u]}, s0));
+            a1 = df_sub(a1, df_mul(df64{ha[u + 1], la[u + 1]}, s1));
+            b1 = df_sub(b1, df_mul(df64{hb[u + 1], lb[u + 1]}, s1));
+        }
     }
     acc_a = df_add(acc_a, a1);
     acc_b = df_add(acc_b, b1);
@@ -366,19 +398,43 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
             if (vb) { vh[ib] = acc_b.h; vl[ib] = acc_b.l; }
         }
         __syncthreads();
-        // partial dots Q^T v: one warp per direction, four interleaved chains per lane
-        for (int kk = warp; kk < k; kk += nw) {
-            const float* qhk = Qh + (int64_t)kk * len;
-            const float* qlk = Ql + (int64_t)kk * len;
-            df64 a0{0.f, 0.f}, a1{0.f, 0.f}, a2{0.f, 0.f}, a3{0.f, 0.f};
+        // partial dots Q^T v: one warp per pair of directions; per iteration a lane loads
+        // four rows of v and of both directions before the arithmetic (24 loads in flight)
+        for (int kk = 2 * warp; kk < k; kk += 2 * nw) {
+            const bool two = kk + 1 < k;
+            const float* qh0 = Qh + (int64_t)kk * len;
+            const float* ql0 = Ql + (int64_t)kk * len;
+            const float* qh1 = Qh + (int64_t)(two ? kk + 1 : kk) * len;
+            const float* ql1 = Ql + (int64_t)(two ? kk + 1 : kk) * len;
+            df64 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
             for (int64_t i = i0 + lane; i < i1; i += 128) {
-                a0 = df_add(a0, df_mul(df64{qhk[i], qlk[i]}, df64{vh[i], vl[i]}));
-                if (i + 32 < i1) a1 = df_add(a1, df_mul(df64{qhk[i + 32], qlk[i + 32]}, df64{vh[i + 32], vl[i + 32]}));
-                if (i + 64 < i1) a2 = df_add(a2, df_mul(df64{qhk[i + 64], qlk[i + 64]}, df64{vh[i + 64], vl[i + 64]}));
-                if (i + 96 < i1) a3 = df_add(a3, df_mul(df64{qhk[i + 96], qlk[i + 96]}, df64{vh[i + 96], vl[i + 96]}));
+                float xh[4], xl[4], ph[4], pl[4], qh_[4], ql_[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t ii = i + 32 * u < i1 ? i + 32 * u : i;
+                    xh[u] = vh[ii]; xl[u] = vl[ii];
+                    ph[u] = qh0[ii]; pl[u] = ql0[ii];
+                    qh_[u] = qh1[ii]; ql_[u] = ql1[ii];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (i + 32 * u >= i1) break;
+                    const df64 x{xh[u], xl[u]};
+                    if (u & 1) {
+                        a1 = df_add(a1, df_mul(df64{ph[u], pl[u]}, x));
+                        b1 = df_add(b1, df_mul(df64{qh_[u], ql_[u]}, x));
+                    } else {
+                        a0 = df_add(a0, df_mul(df64{ph[u], pl[u]}, x));
+                        b0 = df_add(b0, df_mul(df64{qh_[u], ql_[u]}, x));
+                    }
+                }
             }
-            const df64 acc = warp_sum_t(df_add(df_add(a0, a1), df_add(a2, a3)));
-            if (lane == 0) red1[(int64_t)g * r + kk] = acc;
+            const df64 acc0 = warp_sum_t(df_add(a0, a1));
+            const df64 acc1 = warp_sum_t(df_add(b0, b1));
+            if (lane == 0) {
+                red1[(int64_t)g * r + kk] = acc0;
+                if (two) red1[(int64_t)g * r + kk + 1] = acc1;
+            }
         }
         if (!group_barrier(P.bar, 2u * G, P.status)) return;
         // P2: second pass v -= Q (Q^T v); partial ||v||^2
@@ -516,7 +572,8 @@ static cur_status launch_pass(const AcaParams& P, int mode, int64_t chunk, int r
     const TA* A = static_cast<const TA*>(P.A);
     PartT<TA>* part = static_cast<PartT<TA>*>(const_cast<void*>(P.part));
     if (P.axis == 1) {
-        dim3 grid((unsigned)((P.n + 127) / 128), (unsigned)rc_count);
+        constexpr int TW = 32 * ColsPerLane<TA>::v;
+        dim3 grid((unsigned)((P.n + TW - 1) / TW), (unsigned)rc_count);
         if (mode == kNorm) {
             if (vec) aca_cols_pass<TA, kNorm, true><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
             else aca_cols_pass<TA, kNorm, false><<<grid, 256, 0, st>>>(A, P.m, P.n, P.ld, chunk, P.q64, P.qh, P.ql, part, P.stop);
@@ -556,7 +613,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
     int RC = 1;
     int64_t chunk = P.m;
     if (axis == 1) {
-        const int64_t coltiles = (P.n + 127) / 128;
+        const int64_t coltiles = (P.n + 32 * ColsPerLane<TA>::v - 1) / (32 * ColsPerLane<TA>::v);
         int64_t want = std::max<int64_t>(1, (int64_t)h->num_sms * 32 / coltiles);
         want = std::min<int64_t>(want, std::max<int64_t>(1, P.m / 64));
         want = std::min<int64_t>(want, 65535);
@@ -589,7 +646,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
 
     const size_t es = sizeof(TA);
     const uintptr_t base = reinterpret_cast<uintptr_t>(M->data);
-    const size_t va = std::is_same<TA, __nv_bfloat16>::value ? 8 : 16;
+    const size_t va = 16;   // 16-byte vector loads on every row (8 columns of BF16, 4 of FP32)
     const bool vec = (base % va == 0) && ((size_t)(M->ld * es) % va == 0);
 
     CUR_CK(cudaMemsetAsync(P.mask, 0, P.nsel, st));

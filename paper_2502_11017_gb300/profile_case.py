@@ -32,17 +32,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=11019)
+    ap.add_argument("--data", choices=["gaussian", "bf16product"], default="gaussian",
+                    help="Gaussian kernel (FP32) or the rank-r factor product plus noise in BF16")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
-    A = torch.from_numpy(wl.gaussian_kernel(a.m, a.n, 0.2, seed=a.seed, chunk_rows=1024)).to(dev)
+    if a.data == "bf16product":
+        A = wl.bf16_factor_product(a.m, a.n, a.r, 1e-2, device=dev)
+    else:
+        A = torch.from_numpy(wl.gaussian_kernel(a.m, a.n, 0.2, seed=a.seed, chunk_rows=1024)).to(dev)
     m, n, r = a.m, a.n, a.r
-    hd = cur.Handle(m, n, max(r, 64), cur.CUR_F32)
+    hd = cur.Handle(m, n, max(r, 64), cur.CUR_BF16 if a.data == "bf16product" else cur.CUR_F32)
     h = hd.h
     idx = torch.empty(r, dtype=torch.int32, device=dev)
     I = torch.empty(r, dtype=torch.int32, device=dev)
     J = torch.empty(r, dtype=torch.int32, device=dev)
-    C = torch.empty((m, r), dtype=torch.float32, device=dev)
-    R = torch.empty((r, n), dtype=torch.float32, device=dev)
+    C = torch.empty((m, r), dtype=A.dtype, device=dev)
+    R = torch.empty((r, n), dtype=A.dtype, device=dev)
     U = torch.empty((r, r), dtype=torch.float64, device=dev)
     rc = torch.empty(1, dtype=torch.float64, device=dev)
     cheb = torch.empty(1, dtype=torch.float64, device=dev)
