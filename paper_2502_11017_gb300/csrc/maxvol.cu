@@ -37,6 +37,8 @@ constexpr double kEps = 2.220446049250313e-16;
 
 struct MvProb {
     int64_t base;      // first row of the problem in the basis / B buffers
+    int64_t boff;      // element offset of its basis rows (p x r, contiguous)
+    int32_t r;         // its rank (<= the stage's r, which is the stride of per-problem arrays)
     int64_t gid_base;  // global id of local row i = gid_base + i (when gid_arr == null)
     const int32_t* gid_arr;
     int32_t p;         // rows
@@ -200,9 +202,9 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
     const MvProb pr = a.prob[pb];
-    const int r = a.r, G = pr.G;
+    const int r = pr.r, rs = a.r, G = pr.G;
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
-    const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
+    const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
     TB* rows = reinterpret_cast<TB*>(smem_raw);
     size_t off = ((size_t)nloc * r * sizeof(TB) + 15) / 16 * 16;
     double* nu = reinterpret_cast<double*>(smem_raw + off); off += (size_t)nloc * sizeof(double);
@@ -217,7 +219,7 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     __shared__ int s_stop, s_p;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    int32_t* Sout = a.S + (int64_t)pb * r;
+    int32_t* Sout = a.S + (int64_t)pb * rs;
 
     for (int e = tid; e < nloc * r; e += nt) rows[e] = basis[(int64_t)lo * r + e];
     for (int i = tid; i < nloc; i += nt) msk[i] = 0;
@@ -397,13 +399,13 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
     const int pb = blockIdx.x;
     if (a.done[pb] || !a.lu_mask[pb]) return;
     const MvProb pr = a.prob[pb];
-    const int r = a.r, tid = threadIdx.x, nt = blockDim.x;
+    const int r = pr.r, rs = a.r, tid = threadIdx.x, nt = blockDim.x;
     double* M = reinterpret_cast<double*>(smem_raw);  // r x r, inverted in place
     double* colk = M + r * r;
     int* piv = reinterpret_cast<int*>(colk + r);
     __shared__ double s_max;
-    const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
-    const int32_t* S = a.S + (int64_t)pb * r;
+    const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
+    const int32_t* S = a.S + (int64_t)pb * rs;
     double mx = 0.0;
     int bad = 0;
     for (int e = tid; e < r * r; e += nt) {
@@ -443,7 +445,7 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
         return;
     }
     if (tid == 0) a.logvol[pb] = lv;
-    double* out64 = a.minv64 + (int64_t)pb * minv_stride(r);
+    double* out64 = a.minv64 + (int64_t)pb * minv_stride(rs);
     for (int e = tid; e < r * r; e += nt) out64[e] = M[e];
     if (tid == 0) out64[r * r] = 0.0;   // fresh: no drift
 }
@@ -663,18 +665,18 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
     if (a.done[pb]) return;
     const MvProb pr = a.prob[pb];
-    const int r = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
+    const int r = pr.r, rs = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
     const bool solo = G == 1;                   // one CTA: no inter-CTA exchange at all
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
     const bool gmode = a.bglob != nullptr;
-    TB* Bs = gmode ? static_cast<TB*>(a.bglob) + (pr.base + lo) * r   // nloc x r slice of B
+    TB* Bs = gmode ? static_cast<TB*>(a.bglob) + pr.boff + (int64_t)lo * r   // nloc x r slice of B
                    : reinterpret_cast<TB*>(smem_raw);
     TB* Mi = gmode ? reinterpret_cast<TB*>(smem_raw) : Bs + (size_t)nloc * r;   // r x r: M^-1 (compute type)
     TB* colj = Mi + (size_t)r * r;              // nloc
     TB* wrow = colj + nloc;                     // r: winning row of B, then B(i,:) - e_j
     TB* cstage = wrow + r;                      // global-memory mode: kEngStage C rows
     const size_t off = EngineSmem<TB>::head(nloc, r, gmode);
-    double* Mg = a.minv64 + (int64_t)pb * minv_stride(r);       // M^-1 in global memory (FP64)
+    double* Mg = a.minv64 + (int64_t)pb * minv_stride(rs);      // M^-1 in global memory (FP64)
     __shared__ double s_b;
     __shared__ long long s_w;
     __shared__ int s_nan;
@@ -683,18 +685,18 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     __shared__ double s_lv0;         // log|det| of the last factorisation
     __shared__ double s_drift;       // sum of swaps * kappa(M) since the last factorisation
     TB* pub = static_cast<TB*>(a.pub);
-    const TB* basis = static_cast<const TB*>(a.basis) + pr.base * r;
+    const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
     const int myslot = pr.group0 + part;
     if (part == 0) {
         if (tid == 0)
-            keep.setup(smem_raw + off, r, Mg, r <= kMsMax, a.mdf ? a.mdf + (int64_t)pb * 2 * r * r : nullptr);
+            keep.setup(smem_raw + off, r, Mg, r <= kMsMax, a.mdf ? a.mdf + (int64_t)pb * 2 * rs * rs : nullptr);
         __syncthreads();
         keep.load(Mg, r);
-        for (int k = tid; k < r; k += nt) S0[k] = a.S[(int64_t)pb * r + k];
+        for (int k = tid; k < r; k += nt) S0[k] = a.S[(int64_t)pb * rs + k];
         // the inverse arrives with its drift bound (0 when just factorised)
         if (tid == 0) { s_lv0 = a.logvol[pb]; s_drift = Mg[(size_t)r * r]; }
     }
-    int32_t* Sg = a.S + (int64_t)pb * r;
+    int32_t* Sg = a.S + (int64_t)pb * rs;
     double* gjw = reinterpret_cast<double*>(smem_raw);   // refactorisation scratch over the B slice
     // First CTA only: M^-1 of C(S,:) afresh into the keeper; 1 if C(S,:) is singular.
     auto refactor = [&]() -> int {
@@ -720,7 +722,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         }
         if (!nan && bi != LLONG_MAX) {
             const int il = (int)(bi / r) - lo;
-            for (int c = tid; c < r; c += nt) pub[((int64_t)myslot * 2 + pp) * r + c] = Bs[il * r + c];
+            for (int c = tid; c < r; c += nt) pub[((int64_t)myslot * 2 + pp) * rs + c] = Bs[il * r + c];
         }
     };
     while (true) {
@@ -806,14 +808,14 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
             const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
             const int owner = istar / pr.rpc;
             const TB* wsrc = solo ? Bs + (size_t)(istar - lo) * r
-                                  : pub + ((int64_t)(pr.group0 + owner) * 2 + par) * r;
+                                  : pub + ((int64_t)(pr.group0 + owner) * 2 + par) * rs;
             for (int c = tid; c < r; c += nt) wrow[c] = wsrc[c];
             __syncthreads();
             const TB b = wrow[jstar];
             for (int i = tid; i < nloc; i += nt) colj[i] = Bs[i * r + jstar] / b;
             if (part == 0) {
                 keep.swap(basis + (int64_t)istar * r, r, jstar);
-                if (tid == 0) a.S[(int64_t)pb * r + jstar] = istar;
+                if (tid == 0) a.S[(int64_t)pb * rs + jstar] = istar;
             }
             if (tid == 0) wrow[jstar] = wrow[jstar] - (TB)1;
             __syncthreads();
@@ -891,7 +893,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
         const bool sing = fin == 3 && fstat == CUR_ERR_SINGULAR;
         if (sing) {
             if (!a.keep_singular_set)
-                for (int k = tid; k < r; k += nt) a.S[(int64_t)pb * r + k] = S0[k];
+                for (int k = tid; k < r; k += nt) a.S[(int64_t)pb * rs + k] = S0[k];
         } else {
             keep.store(Mg, r);
             if (tid == 0) Mg[(size_t)r * r] = s_drift;
@@ -1075,10 +1077,10 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     // B in shared memory needs ceil(p / cap) co-resident CTAs per problem; a problem that
     // would need more than one per SM puts the stage's B in global memory instead
     bool gmode = false;
-    int64_t rows_end = 0;
+    int64_t elems_end = 0;
     for (auto& pr : sg.probs) {
         if ((pr.p + cap - 1) / cap > h->num_sms) gmode = true;
-        rows_end = std::max<int64_t>(rows_end, pr.base + pr.p);
+        elems_end = std::max<int64_t>(elems_end, pr.boff + (int64_t)pr.p * pr.r);
     }
     int slots = 0;
     for (auto& pr : sg.probs) {
@@ -1114,7 +1116,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     sg.keyi = ar.get<long long>((size_t)2 * slots);
     sg.pub = ar.get<TB>((size_t)2 * slots * r);
     sg.aux = ar.get<double>((size_t)2 * slots);
-    sg.bglob = gmode ? ar.get<TB>((size_t)rows_end * r) : nullptr;
+    sg.bglob = gmode ? ar.get<TB>((size_t)elems_end) : nullptr;
     if (!ar.ok) return CUR_ERR_NOMEM;
     return CUR_OK;
 }
@@ -1272,6 +1274,8 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
     for (int t = 0; t < npairs; ++t) {
         MvProb pr{};
         pr.base = (int64_t)t * 2 * r;
+        pr.boff = pr.base * r;
+        pr.r = r;
         pr.gid_arr = cand + (int64_t)t * 2 * r;
         pr.gid_base = 0;
         pr.p = 2 * r;
@@ -1353,6 +1357,8 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     sg.keep_singular_set = keep_singular_set;
     MvProb pr{};
     pr.base = 0;
+    pr.boff = 0;
+    pr.r = r;
     pr.gid_base = 0;
     pr.gid_arr = nullptr;
     pr.p = (int32_t)p;
@@ -1410,6 +1416,8 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         const int64_t sz = base_sz + (k < extra ? 1 : 0);
         MvProb pr{};
         pr.base = s0;
+        pr.boff = s0 * r;
+        pr.r = r;
         pr.gid_base = s0;
         pr.gid_arr = nullptr;
         pr.p = (int32_t)sz;
