@@ -117,6 +117,36 @@ cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r,
 cur_status cur_aca_full(cur_handle* h, const cur_mat* A, int32_t r, void* R_work,
                         int32_t* I_out, int32_t* J_out, double* piv_out, cudaStream_t stream);
 
+/* One matrix of a batch for cur_cross_batched. */
+typedef struct {
+    int64_t offset;              /* element offset of the matrix in the batch buffer */
+    int64_t rows, cols, ld;      /* shape and leading dimension (row-major) */
+    int32_t r, b_r, b_c;         /* rank, row blocks and column blocks of its cross */
+} cur_batch_item;
+
+/* Workspace bytes that cur_cross_batched needs for these items (host array). */
+size_t cur_batch_workspace_size(const cur_batch_item* items, int32_t count);
+
+/* The cross of every matrix of a batch: for each matrix what cur_cross computes (J0 by
+ * Algorithm 3 on the columns, blockwise maxvol rows and columns with the binary merge,
+ * global sweeps until none swaps), with every stage shared by all matrices: one launch
+ * of Algorithm 3 for the whole batch, then the row selection (all blocks of all matrices
+ * in one stage, each merge level of all matrices in one stage, all polishes in one
+ * stage), the column selection the same way, and each half-sweep over the matrices that
+ * have not converged. data: device buffer, CUR_F32 only; matrix t at data +
+ * items[t].offset with leading dimension items[t].ld. items: host array of count entries
+ * (count <= 65535), each with 1 <= r <= 64, r < min(rows, cols), rows <= 4096,
+ * cols <= 1024, rows / b_r >= r and cols / b_c >= r, else CUR_ERR_ARG. IJ_out: device
+ * int32; matrix t's I (r row ids) then J (r column ids) start at 2 (r_0 + ... + r_{t-1}).
+ * info_out: device array of count cur_cross_info (may be NULL), each with that matrix's
+ * status, log-volume, sweeps and swaps. The handle's status word records
+ * CUR_ERR_SINGULAR or CUR_ERR_NOCONV if any matrix ended so, else CUR_WARN_RANK if
+ * Algorithm 3 ran out early on any. Synchronises the stream; outputs are complete on
+ * return. */
+cur_status cur_cross_batched(cur_handle* h, const void* data, cur_dtype dtype,
+                             const cur_batch_item* items, int32_t count, const cur_opts* opts,
+                             int32_t* IJ_out, cur_cross_info* info_out, cudaStream_t stream);
+
 /* Row selection for given columns J (r int32, device): maxvol on C = A(:,J).
  * C is split into opts->nblocks contiguous balanced row blocks (each >= r rows,
  * else CUR_ERR_ARG); each block starts from Algorithm 3 on its rows and runs

@@ -448,6 +448,12 @@ def cross(A, r: int, b_r: int, b_c: int, delta: float = 1e-2,
     return list(I), list(J), info
 
 
+def cross_batched(mats, ranks, blocks, delta: float = 1e-2):
+    """The cross of every matrix of a batch, one after another: mats[t] with rank
+    ranks[t] and (b_r, b_c) = blocks[t]. Returns a list of (I, J, info)."""
+    return [cross(A, r, br, bc, delta) for A, r, (br, bc) in zip(mats, ranks, blocks)]
+
+
 # --------------------------------------------------------------------------
 # Assembly and residual
 # --------------------------------------------------------------------------

@@ -20,6 +20,7 @@ CUR_FLAG_POLISH = 1
 
 # Every symbol include/cur.h declares.
 EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", "cur_aca_full",
+           "cur_batch_workspace_size", "cur_cross_batched",
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
@@ -40,6 +41,11 @@ class CurCrossInfo(ctypes.Structure):
     _fields_ = [("logvol", ctypes.c_double), ("sweeps", ctypes.c_int32),
                 ("swaps_total", ctypes.c_int32), ("sweep_swaps", ctypes.c_int32 * 8),
                 ("aca_selected", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class CurBatchItem(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_int64), ("rows", ctypes.c_int64), ("cols", ctypes.c_int64),
+                ("ld", ctypes.c_int64), ("r", ctypes.c_int32), ("b_r", ctypes.c_int32), ("b_c", ctypes.c_int32)]
 
 
 _lib = None
@@ -67,6 +73,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_workspace_size": ([I64, I64, I32, ctypes.c_int], ctypes.c_size_t),
         "cur_aca_select": ([P, pmat, ctypes.c_int, I32, I32, P, P], ctypes.c_int),
         "cur_aca_full": ([P, pmat, I32, P, P, P, P, P], ctypes.c_int),
+        "cur_batch_workspace_size": ([ctypes.POINTER(CurBatchItem), I32], ctypes.c_size_t),
+        "cur_cross_batched": ([P, P, ctypes.c_int, ctypes.POINTER(CurBatchItem), I32, popts, P, P, P],
+                              ctypes.c_int),
         "cur_maxvol_rows": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
         "cur_maxvol_cols": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
         "cur_merge": ([P, pmat, P, I32, I32, popts, P, P], ctypes.c_int),
@@ -167,6 +176,26 @@ def cur_aca_select(h, A, axis: int, r: int, nblocks: int, idx_out, stream=None) 
 def cur_aca_full(h, A, r: int, R_work, I_out, J_out, piv_out=None, stream=None) -> int:
     return _check(load().cur_aca_full(h, ctypes.byref(mat(A)), r, _ptr(R_work), _ptr(I_out),
                                       _ptr(J_out), _ptr(piv_out), _stream(stream)), "cur_aca_full")
+
+
+def batch_items(shapes, offsets):
+    """ctypes array of cur_batch_item from (rows, cols, r, b_r, b_c) tuples and element offsets
+    (contiguous rows: ld = cols)."""
+    arr = (CurBatchItem * len(shapes))()
+    for t, ((m, n, r, br, bc), off) in enumerate(zip(shapes, offsets)):
+        arr[t] = CurBatchItem(int(off), int(m), int(n), int(n), int(r), int(br), int(bc))
+    return arr
+
+
+def cur_batch_workspace_size(items) -> int:
+    return load().cur_batch_workspace_size(items, len(items))
+
+
+def cur_cross_batched(h, data, items, opts_, IJ_out, info_out=None, stream=None) -> int:
+    """data: packed device tensor; items: a batch_items() array."""
+    return _check(load().cur_cross_batched(h, _ptr(data), _dtype_code(data), items, len(items),
+                                           ctypes.byref(opts_), _ptr(IJ_out), _ptr(info_out),
+                                           _stream(stream)), "cur_cross_batched")
 
 
 def cur_maxvol_rows(h, A, J, r: int, o: CurOpts, I_out, logvol_out=None, swaps_out=None,

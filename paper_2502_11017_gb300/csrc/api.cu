@@ -203,6 +203,40 @@ cur_status cur_aca_select(cur_handle* h, const cur_mat* A, int axis, int32_t r, 
     return aca_select_full(h, A, axis, r, idx_out, cnt, ar, st);
 }
 
+size_t cur_batch_workspace_size(const cur_batch_item* items, int32_t count) {
+    if (!items || count < 1) return 0;
+    int rs = 1;
+    for (int t = 0; t < count; ++t) rs = std::max(rs, (int)items[t].r);
+    size_t b = (size_t)64 << 20;
+    const size_t minv = ((size_t)rs * rs + 1) * 8 + (size_t)rs * 64;   // per stage problem
+    for (int t = 0; t < count; ++t) {
+        const cur_batch_item& it = items[t];
+        if (it.r < 1 || it.rows < 1 || it.cols < 1) return 0;
+        b += (size_t)(it.rows + it.cols) * it.r * 4 * 4;             // bases, unions, B
+        b += minv * (size_t)(2 * (std::max(1, it.b_r) + std::max(1, it.b_c)) + 4);
+        b += 512;
+    }
+    b += (size_t)std::min(count, 256) * 2 * 64 * 4096 * sizeof(float);   // Algorithm 3's Q slices
+    return b;
+}
+
+cur_status cur_cross_batched(cur_handle* h, const void* data, cur_dtype dtype, const cur_batch_item* items,
+                             int32_t count, const cur_opts* opts, int32_t* IJ_out, cur_cross_info* info_out,
+                             cudaStream_t st) {
+    if (!h || !data || !items || !IJ_out || count < 1 || count > 65535) return CUR_ERR_ARG;
+    if (dtype != CUR_F32) return CUR_ERR_ARG;
+    for (int t = 0; t < count; ++t) {
+        const cur_batch_item& it = items[t];
+        if (it.r < 1 || it.r > 64 || it.rows > 4096 || it.cols > 1024 || it.ld < it.cols || it.offset < 0) return CUR_ERR_ARG;
+        if (it.r >= std::min(it.rows, it.cols) || it.b_r < 1 || it.b_c < 1) return CUR_ERR_ARG;
+        if (it.rows / it.b_r < it.r || it.cols / it.b_c < it.r) return CUR_ERR_ARG;
+    }
+    cur_opts o = opts ? *opts : cur_default_opts();
+    if (!(o.delta >= 0.0)) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    return cross_batched_impl(h, static_cast<const float*>(data), items, count, &o, IJ_out, info_out, ar, st);
+}
+
 cur_status cur_aca_full(cur_handle* h, const cur_mat* A, int32_t r, void* R_work, int32_t* I_out,
                         int32_t* J_out, double* piv_out, cudaStream_t st) {
     if (!h || !mat_ok(A) || !R_work || !I_out || !J_out) return CUR_ERR_ARG;

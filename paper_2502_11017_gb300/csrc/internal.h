@@ -110,6 +110,10 @@ cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p
                        int* swaps, Arena& ar, cudaStream_t st);
 // Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r).
 cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st);
+// The cross of every matrix of a batch (cur_cross_batched), FP32 data.
+cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_item* items, int T,
+                              const cur_opts* o, int32_t* IJ_out, cur_cross_info* info_out, Arena& ar,
+                              cudaStream_t st);
 // Algorithm 1 (ACA with full pivoting) into the caller's residual buffer R (m x n,
 // compute type); see cur_aca_full.
 cur_status aca_full_impl(cur_handle* h, const cur_mat* A, int r, void* R, int32_t* I, int32_t* J,

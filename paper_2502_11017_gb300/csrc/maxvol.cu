@@ -22,6 +22,7 @@
 //               factorisation. A merge node starts from its left child's M^-1.
 
 #include <algorithm>
+#include <array>
 #include <climits>
 #include <cstring>
 #include <type_traits>
@@ -1600,5 +1601,570 @@ cur_status pad_indices_dev(int32_t* idx, const int32_t* count, int r, int64_t si
     curk::pad_indices_k<<<1, 32, 0, st>>>(idx, count, r, size);
     CUR_CK(cudaGetLastError());
     note_launch();
+    return CUR_OK;
+}
+
+// ================================================================ batches of matrices
+//
+// The cross of every matrix of a batch with each stage shared by all matrices: one launch
+// of Algorithm 3 for all of them (batched_aca.cu), then the row selection (every block of
+// every matrix in one stage, each merge level of all matrices in one stage, every polish
+// in one stage), the column selection the same way, and the sweeps (one stage per
+// half-sweep over the matrices that have not converged). FP32 data; each problem keeps
+// its own rank, the stage's stride is the largest.
+
+namespace curk {
+
+struct BatGItem {         // matrix t of the batch, for the gathers
+    int64_t aoff, m, n, ld;
+    int32_t r;
+    int64_t coff;         // its basis at C + coff (m x r for columns J, n x r for rows I)
+    int64_t ioff;         // its indices at idx + ioff
+};
+
+// C(i, k) = A(i, J_k), m x r, for matrix blockIdx.y.
+__global__ void bat_gather_cols_k(const float* __restrict__ data, const BatGItem* items,
+                                  const int32_t* __restrict__ J, float* __restrict__ C) {
+    const BatGItem b = items[blockIdx.y];
+    const int64_t total = b.m * b.r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / b.r;
+        const int k = (int)(e - i * b.r);
+        C[b.coff + e] = data[b.aoff + i * b.ld + J[b.ioff + k]];
+    }
+}
+
+// Rt(j, k) = A(I_k, j), n x r, for matrix blockIdx.y (reads along rows of A).
+__global__ void bat_gather_rows_t_k(const float* __restrict__ data, const BatGItem* items,
+                                    const int32_t* __restrict__ I, float* __restrict__ Rt) {
+    const BatGItem b = items[blockIdx.y];
+    const int64_t total = b.n * b.r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / b.n);
+        const int64_t j = e - (int64_t)k * b.n;
+        Rt[b.coff + j * b.r + k] = data[b.aoff + (int64_t)I[b.ioff + k] * b.ld + j];
+    }
+}
+
+// out[pb rs + k] = global id of S[pb rs + k] for k < r(pb), -1 after.
+__global__ void bat_emit_k(const MvProb* prob, const int32_t* S, int P, int rs, int32_t* out) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P * rs; e += gridDim.x * blockDim.x) {
+        const int pb = e / rs, k = e - pb * rs;
+        const MvProb pr = prob[pb];
+        if (k >= pr.r) { out[e] = -1; continue; }
+        const int s = S[e];
+        out[e] = pr.gid_arr ? pr.gid_arr[s] : (int32_t)(pr.gid_base + s);
+    }
+}
+
+// Start rows of the flagged problems: k (left set) or r(pb) + k (right set).
+__global__ void bat_iota_k(const int32_t* rr, const int32_t* flag, int P, int rs, int right, int32_t* S) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P * rs; e += gridDim.x * blockDim.x) {
+        const int pb = e / rs, k = e - pb * rs;
+        if (flag && !flag[pb]) continue;
+        S[e] = right ? rr[pb] + k : k;
+    }
+}
+
+// dst row d (rs entries) = src row idx[d].
+__global__ void bat_rows_copy_k(const int32_t* src, const int32_t* idx, int D, int rs, int32_t* dst) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D * rs; e += gridDim.x * blockDim.x) {
+        const int d = e / rs, k = e - d * rs;
+        dst[e] = src[(int64_t)idx[d] * rs + k];
+    }
+}
+
+// dst row idx[d] = src row d.
+__global__ void bat_rows_scatter_k(const int32_t* src, const int32_t* idx, int D, int rs, int32_t* dst) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D * rs; e += gridDim.x * blockDim.x) {
+        const int d = e / rs, k = e - d * rs;
+        dst[(int64_t)idx[d] * rs + k] = src[e];
+    }
+}
+
+struct BatUnion {
+    int64_t uoff;     // union rows at U + uoff (2 r x r)
+    int64_t boff;     // the matrix's basis at basis + boff (p x r)
+    int32_t r, p;
+    int32_t left, right;   // set rows in the current set array
+};
+
+// cand[q 2rs + x] = left set (x < r), right set (r <= x < 2r); U = basis rows of cand.
+__global__ void bat_union_k(const float* __restrict__ basis, const BatUnion* un, const int32_t* sets, int rs,
+                            int32_t* cand, float* __restrict__ U, int* status) {
+    const BatUnion u = un[blockIdx.y];
+    int32_t* cq = cand + (int64_t)blockIdx.y * 2 * rs;
+    for (int x = threadIdx.x; x < 2 * u.r; x += blockDim.x)
+        cq[x] = x < u.r ? sets[(int64_t)u.left * rs + x] : sets[(int64_t)u.right * rs + x - u.r];
+    __syncthreads();
+    const int64_t total = (int64_t)2 * u.r * u.r;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(e / u.r), c = (int)(e - (int64_t)x * u.r);
+        const int32_t g = cq[x];
+        if (g < 0 || g >= u.p) { set_status(status, CUR_ERR_ARG); U[u.uoff + e] = 0.f; continue; }
+        U[u.uoff + e] = basis[u.boff + (int64_t)g * u.r + c];
+    }
+}
+
+// Pad J0 of each matrix (count[t] valid entries) with its lowest unused column ids.
+__global__ void bat_pad_k(int32_t* J, const int64_t* joff, const int32_t* rr, const int64_t* nn,
+                          const int32_t* count, int T) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        int32_t* j = J + joff[t];
+        const int r = rr[t];
+        int fill = count[t];
+        for (int64_t cand = 0; cand < nn[t] && fill < r; ++cand) {
+            bool used = false;
+            for (int q = 0; q < fill; ++q) used |= j[q] == cand;
+            if (!used) j[fill++] = (int32_t)cand;
+        }
+    }
+}
+
+// Unpacked per-matrix indices (stride rs) to the packed output and back.
+__global__ void bat_pack_k(const int32_t* src, const int64_t* off, const int32_t* rr, int T, int rs,
+                           int32_t* dst, int to_packed) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < T * rs; e += gridDim.x * blockDim.x) {
+        const int t = e / rs, k = e - t * rs;
+        if (k >= rr[t]) continue;
+        if (to_packed) dst[off[t] + k] = src[e];
+        else dst[e] = src[off[t] + k];
+    }
+}
+
+struct BatBasis {
+    int64_t boff;       // basis of matrix t at basis + boff, p x r
+    int32_t p, r, nb;   // rows, rank, blocks
+};
+
+__global__ void bat_set_status_k(int* status, int code) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(status, code);
+}
+static cur_status set_status_host(cur_handle* h, int code, cudaStream_t st) {
+    bat_set_status_k<<<1, 32, 0, st>>>(h->status, code);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+// Uploads `bytes` from host memory through the handle's pinned staging buffer.
+static cur_status bat_upload(cur_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    if (bytes > h->host_stage_bytes) return CUR_ERR_NOMEM;
+    CUR_CK(cudaStreamSynchronize(st));
+    std::memcpy(h->host_stage, src, bytes);
+    CUR_CK(cudaMemcpyAsync(dst, h->host_stage, bytes, cudaMemcpyHostToDevice, st));
+    CUR_CK(cudaStreamSynchronize(st));
+    return CUR_OK;
+}
+
+// Maxvol row selection (blocks, binary merge, polish) on every basis of `bs`. out: device,
+// row t at t rs (local row ids); logvol: device, one double per matrix. stat and swaps
+// receive each matrix's polish status and its swaps.
+static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<BatBasis>& bs, int rs,
+                           const cur_opts* o, int32_t* out, double* logvol, std::vector<int>& stat,
+                           std::vector<int>& swaps, Arena& ar, cudaStream_t st) {
+    const int T = (int)bs.size();
+    const size_t mark = ar.off;
+    std::vector<int> none;
+    stat.assign(T, CUR_OK);
+    swaps.assign(T, 0);
+    // ---- blocks: Algorithm 3 start and maxvol on each block of each matrix
+    std::vector<std::vector<int>> sets(T);
+    Stage<float> sb;
+    for (int t = 0; t < T; ++t) {
+        const int64_t base_sz = bs[t].p / bs[t].nb, extra = bs[t].p % bs[t].nb;
+        int64_t s0 = 0;
+        for (int k = 0; k < bs[t].nb; ++k) {
+            const int64_t sz = base_sz + (k < extra ? 1 : 0);
+            MvProb pr{};
+            pr.base = s0;
+            pr.boff = bs[t].boff + s0 * bs[t].r;
+            pr.r = bs[t].r;
+            pr.p = (int32_t)sz;
+            pr.gid_base = s0;
+            sets[t].push_back((int)sb.probs.size());
+            sb.probs.push_back(pr);
+            s0 += sz;
+        }
+    }
+    CUR_TRY(stage_setup<float>(h, rs, sb, ar));
+    CUR_TRY(stage_run<float>(h, basis, rs, o, sb, true, none, none, st));
+    CUR_TRY(stage_read<float>(h, sb, st));
+    for (int t = 0; t < T; ++t)
+        for (int q : sets[t]) swaps[t] += sb.sw[q];
+    int32_t* cur = ar.get<int32_t>((size_t)sb.P * rs);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    bat_emit_k<<<nblk((int64_t)sb.P * rs), 256, 0, st>>>(sb.dprob, sb.S, sb.P, rs, cur);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    // ---- merge levels: node (2u, 2u+1) of every matrix that still has two sets or more
+    std::vector<Stage<float>> keep;   // stages stay alive while their memory is in use
+    keep.reserve(16);
+    while (true) {
+        std::vector<BatUnion> un;
+        std::vector<int> node_item, pass_src;
+        std::vector<std::vector<int>> nsets(T);
+        int64_t uoff = 0;
+        for (int t = 0; t < T; ++t) {
+            const auto& L = sets[t];
+            for (size_t u = 0; u + 1 < L.size(); u += 2) {
+                BatUnion b{};
+                b.uoff = uoff;
+                b.boff = bs[t].boff;
+                b.r = bs[t].r;
+                b.p = bs[t].p;
+                b.left = L[u];
+                b.right = L[u + 1];
+                nsets[t].push_back((int)un.size());
+                un.push_back(b);
+                node_item.push_back(t);
+                uoff += (int64_t)2 * b.r * b.r;
+            }
+        }
+        const int Q = (int)un.size();
+        if (Q == 0) break;
+        for (int t = 0; t < T; ++t)
+            if (sets[t].size() % 2 == 1 && sets[t].size() > 1) {
+                nsets[t].push_back(Q + (int)pass_src.size());
+                pass_src.push_back(sets[t].back());
+            } else if (sets[t].size() == 1) {
+                nsets[t].push_back(Q + (int)pass_src.size());
+                pass_src.push_back(sets[t][0]);
+            }
+        BatUnion* dun = ar.get<BatUnion>(Q);
+        int32_t* cand = ar.get<int32_t>((size_t)Q * 2 * rs);
+        float* U = ar.get<float>((size_t)uoff);
+        int32_t* rr = ar.get<int32_t>(Q);
+        int32_t* flag = ar.get<int32_t>(Q);
+        int32_t* nxt = ar.get<int32_t>((size_t)(Q + pass_src.size()) * rs);
+        int32_t* psrc = ar.get<int32_t>(pass_src.size() + 1);
+        if (!ar.ok) return CUR_ERR_NOMEM;
+        CUR_TRY(bat_upload(h, dun, un.data(), sizeof(BatUnion) * Q, st));
+        {
+            std::vector<int32_t> hr(Q);
+            for (int q = 0; q < Q; ++q) hr[q] = un[q].r;
+            CUR_TRY(bat_upload(h, rr, hr.data(), sizeof(int32_t) * Q, st));
+        }
+        bat_union_k<<<dim3(4, Q), 256, 0, st>>>(basis, dun, cur, rs, cand, U, h->status);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        keep.emplace_back();
+        Stage<float>& lv = keep.back();
+        for (int q = 0; q < Q; ++q) {
+            MvProb pr{};
+            pr.base = 0;
+            pr.boff = un[q].uoff;
+            pr.r = un[q].r;
+            pr.p = 2 * un[q].r;
+            pr.gid_arr = cand + (int64_t)q * 2 * rs;
+            lv.probs.push_back(pr);
+        }
+        CUR_TRY(stage_setup<float>(h, rs, lv, ar));
+        bat_iota_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(rr, nullptr, Q, rs, 0, lv.S);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        CUR_TRY(stage_run<float>(h, U, rs, o, lv, false, none, none, st));
+        CUR_TRY(stage_read<float>(h, lv, st));
+        // a singular left start: the right set, then Algorithm 3 on the union; the swaps of
+        // an abandoned attempt are not counted
+        std::vector<int> skip(Q, 1), fl(Q, 0);
+        bool any = false;
+        for (int q = 0; q < Q; ++q) {
+            if (lv.stat[q] == CUR_ERR_SINGULAR) { skip[q] = 0; fl[q] = 1; any = true; }
+            else swaps[node_item[q]] += lv.sw[q];
+        }
+        for (int attempt = 0; attempt < 2 && any; ++attempt) {
+            if (attempt == 0) {
+                CUR_TRY(bat_upload(h, flag, fl.data(), sizeof(int32_t) * Q, st));
+                bat_iota_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(rr, flag, Q, rs, 1, lv.S);
+                CUR_CK(cudaGetLastError());
+                note_launch();
+            }
+            const std::vector<int> save = lv.stat, savesw = lv.sw;
+            CUR_TRY(stage_run<float>(h, U, rs, o, lv, attempt == 1, none, skip, st));
+            CUR_TRY(stage_read<float>(h, lv, st));
+            any = false;
+            for (int q = 0; q < Q; ++q) {
+                if (skip[q]) { lv.stat[q] = save[q]; lv.sw[q] = savesw[q]; continue; }
+                if (lv.stat[q] == CUR_ERR_SINGULAR && attempt == 0) { any = true; continue; }
+                swaps[node_item[q]] += lv.sw[q];
+                skip[q] = 1;
+            }
+        }
+        bat_emit_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(lv.dprob, lv.S, Q, rs, nxt);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        if (!pass_src.empty()) {
+            CUR_TRY(bat_upload(h, psrc, pass_src.data(), sizeof(int32_t) * pass_src.size(), st));
+            bat_rows_copy_k<<<nblk((int64_t)pass_src.size() * rs), 256, 0, st>>>(cur, psrc, (int)pass_src.size(), rs,
+                                                                                nxt + (int64_t)Q * rs);
+            CUR_CK(cudaGetLastError());
+            note_launch();
+        }
+        cur = nxt;
+        sets.swap(nsets);
+    }
+    // ---- polish: maxvol over all rows of each matrix from its merged set
+    Stage<float> sp;
+    std::vector<int32_t> src(T);
+    for (int t = 0; t < T; ++t) {
+        MvProb pr{};
+        pr.base = 0;
+        pr.boff = bs[t].boff;
+        pr.r = bs[t].r;
+        pr.p = bs[t].p;
+        sp.probs.push_back(pr);
+        src[t] = sets[t][0];
+    }
+    CUR_TRY(stage_setup<float>(h, rs, sp, ar));
+    int32_t* dsrc = ar.get<int32_t>(T);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(bat_upload(h, dsrc, src.data(), sizeof(int32_t) * T, st));
+    bat_rows_copy_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(cur, dsrc, T, rs, sp.S);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    if (o->flags & CUR_FLAG_POLISH) {
+        CUR_TRY(stage_run<float>(h, basis, rs, o, sp, false, none, none, st));
+    } else {
+        cur_opts o2 = *o;
+        o2.delta = 1e300;   // no swap: one factorisation for log|det|
+        CUR_TRY(stage_run<float>(h, basis, rs, &o2, sp, false, none, none, st));
+    }
+    CUR_TRY(stage_read<float>(h, sp, st));
+    for (int t = 0; t < T; ++t) {
+        stat[t] = sp.stat[t];
+        swaps[t] += sp.sw[t];
+    }
+    CUR_CK(cudaMemcpyAsync(out, sp.S, sizeof(int32_t) * T * rs, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(logvol, sp.logvol, sizeof(double) * T, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaStreamSynchronize(st));
+    ar.off = mark;
+    ar.ok = true;
+    return CUR_OK;
+}
+
+// Global maxvol over all rows of the active bases from S (device, row t at t rs), in place;
+// a set that turns singular stays as reached (the swap iteration's own result).
+static cur_status bat_global(cur_handle* h, const float* basis, const std::vector<BatBasis>& bs,
+                             const std::vector<int>& active, int rs, const cur_opts* o, int32_t* S,
+                             double* logvol, std::vector<int>& stat, std::vector<int>& swaps, Arena& ar,
+                             cudaStream_t st) {
+    const int D = (int)active.size();
+    if (D == 0) return CUR_OK;
+    const size_t mark = ar.off;
+    Stage<float> sg;
+    sg.keep_singular_set = true;
+    for (int d = 0; d < D; ++d) {
+        const BatBasis& b = bs[active[d]];
+        MvProb pr{};
+        pr.boff = b.boff;
+        pr.r = b.r;
+        pr.p = b.p;
+        sg.probs.push_back(pr);
+    }
+    CUR_TRY(stage_setup<float>(h, rs, sg, ar));
+    int32_t* idx = ar.get<int32_t>(D);
+    double* lvd = ar.get<double>(D);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(bat_upload(h, idx, active.data(), sizeof(int32_t) * D, st));
+    bat_rows_copy_k<<<nblk((int64_t)D * rs), 256, 0, st>>>(S, idx, D, rs, sg.S);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    std::vector<int> none;
+    CUR_TRY(stage_run<float>(h, basis, rs, o, sg, false, none, none, st));
+    CUR_TRY(stage_read<float>(h, sg, st));
+    bat_rows_scatter_k<<<nblk((int64_t)D * rs), 256, 0, st>>>(sg.S, idx, D, rs, S);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    CUR_CK(cudaMemcpyAsync(lvd, sg.logvol, sizeof(double) * D, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> hl(D);
+    CUR_CK(cudaStreamSynchronize(st));
+    CUR_CK(cudaMemcpy(hl.data(), lvd, sizeof(double) * D, cudaMemcpyDeviceToHost));
+    for (int d = 0; d < D; ++d) {
+        stat[active[d]] = sg.stat[d];
+        swaps[active[d]] = sg.sw[d];
+        if (logvol) logvol[active[d]] = hl[d];
+    }
+    ar.off = mark;
+    ar.ok = true;
+    return CUR_OK;
+}
+
+}  // namespace curk
+
+size_t bat_aca_workspace(int grid);
+size_t bat_aca_item_size();
+cur_status bat_aca_launch(const float* data, const void* items_dev, int count, int32_t* J, int32_t* counts,
+                          float* Qws, int grid, int* status, cudaStream_t st);
+
+// The cross of every matrix of the batch (see cur_cross_batched).
+cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_item* items, int T,
+                              const cur_opts* o, int32_t* IJ_out, cur_cross_info* info_out, Arena& ar,
+                              cudaStream_t st) {
+    using namespace curk;
+    int rs = 1;
+    int64_t sum_r = 0, sum_mr = 0, sum_nr = 0;
+    for (int t = 0; t < T; ++t) {
+        rs = std::max(rs, (int)items[t].r);
+        sum_r += items[t].r;
+        sum_mr += items[t].rows * items[t].r;
+        sum_nr += items[t].cols * items[t].r;
+    }
+    // ---- per-matrix tables
+    struct AcaIt { int64_t aoff, m, n, ld; int32_t r; int64_t joff; };
+    std::vector<AcaIt> ai(T);
+    std::vector<BatGItem> gc(T), gr(T);
+    std::vector<BatBasis> bc(T), brt(T);
+    std::vector<int64_t> joff(T), nn(T);
+    std::vector<int32_t> rr(T);
+    int64_t jo = 0, co = 0, ro = 0;
+    for (int t = 0; t < T; ++t) {
+        const cur_batch_item& b = items[t];
+        ai[t] = AcaIt{b.offset, b.rows, b.cols, b.ld, b.r, jo};
+        joff[t] = jo;
+        nn[t] = b.cols;
+        rr[t] = b.r;
+        gc[t] = BatGItem{b.offset, b.rows, b.cols, b.ld, b.r, co, (int64_t)t * rs};
+        gr[t] = BatGItem{b.offset, b.rows, b.cols, b.ld, b.r, ro, (int64_t)t * rs};
+        bc[t] = BatBasis{co, (int32_t)b.rows, b.r, b.b_r};
+        brt[t] = BatBasis{ro, (int32_t)b.cols, b.r, b.b_c};
+        jo += b.r;
+        co += b.rows * b.r;
+        ro += b.cols * b.r;
+    }
+    static_assert(sizeof(AcaIt) == 48, "BatAcaItem layout");
+    if (bat_aca_item_size() != sizeof(AcaIt)) return CUR_ERR_ARG;
+    const int grid = std::min(T, h->num_sms);
+    void* dai = ar.take(sizeof(AcaIt) * T);
+    BatGItem* dgc = ar.get<BatGItem>(T);
+    BatGItem* dgr = ar.get<BatGItem>(T);
+    int64_t* djoff = ar.get<int64_t>(T);
+    int64_t* dnn = ar.get<int64_t>(T);
+    int32_t* drr = ar.get<int32_t>(T);
+    int32_t* J0 = ar.get<int32_t>(sum_r);
+    int32_t* cnt = ar.get<int32_t>(T);
+    float* Qws = static_cast<float*>(ar.take(bat_aca_workspace(grid)));
+    float* C = ar.get<float>(sum_mr);
+    float* Rt = ar.get<float>(sum_nr);
+    int32_t* I = ar.get<int32_t>((size_t)T * rs);
+    int32_t* J = ar.get<int32_t>((size_t)T * rs);
+    double* lvc = ar.get<double>(T);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(bat_upload(h, dai, ai.data(), sizeof(AcaIt) * T, st));
+    CUR_TRY(bat_upload(h, dgc, gc.data(), sizeof(BatGItem) * T, st));
+    CUR_TRY(bat_upload(h, dgr, gr.data(), sizeof(BatGItem) * T, st));
+    CUR_TRY(bat_upload(h, djoff, joff.data(), sizeof(int64_t) * T, st));
+    CUR_TRY(bat_upload(h, dnn, nn.data(), sizeof(int64_t) * T, st));
+    CUR_TRY(bat_upload(h, drr, rr.data(), sizeof(int32_t) * T, st));
+    // ---- J0: Algorithm 3 on the columns of every matrix, padded per matrix
+    CUR_TRY(bat_aca_launch(data, dai, T, J0, cnt, Qws, grid, h->status, st));
+    std::vector<int32_t> hcnt(T);
+    CUR_CK(cudaStreamSynchronize(st));
+    CUR_CK(cudaMemcpy(hcnt.data(), cnt, sizeof(int32_t) * T, cudaMemcpyDeviceToHost));
+    bat_pad_k<<<nblk(T, 128), 128, 0, st>>>(J0, djoff, drr, dnn, cnt, T);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(J0, djoff, drr, T, rs, J, 0);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    std::vector<int> status(T, CUR_OK), sw_r, sw_c, st_r, st_c;
+    std::vector<std::array<int, 8>> ssw(T);
+    for (auto& a : ssw) a.fill(0);
+    bool any_warn = false;
+    for (int t = 0; t < T; ++t)
+        if (hcnt[t] < items[t].r) { status[t] = CUR_WARN_RANK; any_warn = true; }
+    auto gather_c = [&](const int32_t* Jd) -> cur_status {
+        bat_gather_cols_k<<<dim3(8, T), 256, 0, st>>>(data, dgc, Jd, C);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        return CUR_OK;
+    };
+    auto gather_r = [&](const int32_t* Id) -> cur_status {
+        bat_gather_rows_t_k<<<dim3(8, T), 256, 0, st>>>(data, dgr, Id, Rt);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        return CUR_OK;
+    };
+    // ---- sweep 1: blockwise rows on A(:,J0), then blockwise columns on A(I,:)^T
+    cur_opts orow = *o, ocol = *o;
+    CUR_TRY(gather_c(J));
+    CUR_TRY(bat_rows(h, C, bc, rs, &orow, I, lvc, st_r, sw_r, ar, st));
+    CUR_TRY(gather_r(I));
+    CUR_TRY(bat_rows(h, Rt, brt, rs, &ocol, J, lvc, st_c, sw_c, ar, st));
+    std::vector<double> lv(T);
+    CUR_CK(cudaMemcpy(lv.data(), lvc, sizeof(double) * T, cudaMemcpyDeviceToHost));
+    std::vector<int> sweeps(T, 1), active;
+    for (int t = 0; t < T; ++t) {
+        ssw[t][0] = sw_r[t] + sw_c[t];
+        if (st_r[t] != CUR_OK) status[t] = st_r[t];
+        if (st_c[t] != CUR_OK) status[t] = st_c[t];
+        active.push_back(t);
+    }
+    // ---- sweeps 2..8: global rows from I, global columns from J
+    std::vector<int> s1(T, 0), s2(T, 0), q1(T, CUR_OK), q2(T, CUR_OK);
+    for (int sweep = 2; sweep <= 8 && !active.empty(); ++sweep) {
+        CUR_TRY(gather_c(J));
+        CUR_TRY(bat_global(h, C, bc, active, rs, o, I, nullptr, q1, s1, ar, st));
+        CUR_TRY(gather_r(I));
+        CUR_TRY(bat_global(h, Rt, brt, active, rs, o, J, lv.data(), q2, s2, ar, st));
+        std::vector<int> still;
+        for (int t : active) {
+            sweeps[t] = sweep;
+            ssw[t][sweep - 1] = s1[t] + s2[t];
+            if (q1[t] != CUR_OK || q2[t] != CUR_OK) {
+                status[t] = q1[t] != CUR_OK ? q1[t] : q2[t];
+                continue;
+            }
+            if (s1[t] + s2[t] == 0) continue;
+            still.push_back(t);
+        }
+        active.swap(still);
+    }
+    // ---- outputs
+    int32_t* ptmp = ar.get<int32_t>(2 * sum_r);
+    int64_t* dio = ar.get<int64_t>(T);
+    int64_t* djo = ar.get<int64_t>(T);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    {
+        std::vector<int64_t> io(T), jo2(T);
+        for (int t = 0; t < T; ++t) { io[t] = 2 * joff[t]; jo2[t] = 2 * joff[t] + items[t].r; }
+        CUR_TRY(bat_upload(h, dio, io.data(), sizeof(int64_t) * T, st));
+        CUR_TRY(bat_upload(h, djo, jo2.data(), sizeof(int64_t) * T, st));
+    }
+    bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(I, dio, drr, T, rs, IJ_out, 1);
+    bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(J, djo, drr, T, rs, IJ_out, 1);
+    CUR_CK(cudaGetLastError());
+    note_launch(2);
+    // a matrix whose cross did not end OK reports log|det A(I,J)| taken directly
+    for (int t = 0; t < T; ++t)
+        if (status[t] != CUR_OK && status[t] != CUR_WARN_RANK)
+            CUR_TRY(logvol_rows(CUR_F32, Rt + brt[t].boff, items[t].r, J + (int64_t)t * rs, lvc + t, st));
+    std::vector<double> lvf(T);
+    CUR_CK(cudaStreamSynchronize(st));
+    CUR_CK(cudaMemcpy(lvf.data(), lvc, sizeof(double) * T, cudaMemcpyDeviceToHost));
+    int worst = CUR_OK;
+    for (int t = 0; t < T; ++t)
+        if (status[t] == CUR_ERR_SINGULAR || status[t] == CUR_ERR_NOCONV) worst = status[t];
+    if (worst != CUR_OK) {
+        CUR_TRY(set_status_host(h, worst, st));
+    } else if (any_warn) {
+        CUR_TRY(set_status_host(h, CUR_WARN_RANK, st));
+    }
+    if (info_out) {
+        std::vector<cur_cross_info> inf(T);
+        for (int t = 0; t < T; ++t) {
+            cur_cross_info& f = inf[t];
+            std::memset(&f, 0, sizeof(f));
+            f.logvol = (status[t] != CUR_OK && status[t] != CUR_WARN_RANK) ? lvf[t] : lv[t];
+            f.sweeps = sweeps[t];
+            for (int k = 0; k < 8; ++k) { f.sweep_swaps[k] = ssw[t][k]; f.swaps_total += ssw[t][k]; }
+            f.aca_selected = hcnt[t];
+            f.status = status[t];
+        }
+        CUR_TRY(bat_upload(h, info_out, inf.data(), sizeof(cur_cross_info) * T, st));
+    }
     return CUR_OK;
 }

@@ -4,6 +4,7 @@
     python -m paper_2502_11017_gb300.profile_case --call residual --m 16384 --n 8192 --r 64
     python -m paper_2502_11017_gb300.profile_case --call cross --m 65536 --n 8192 --r 64
     python -m paper_2502_11017_gb300.profile_case --call alg1 --m 65536 --n 8192 --r 64
+    python -m paper_2502_11017_gb300.profile_case --call batch --count 4096
 
 The matrix is exp(-|x_i - y_j|^2 / h^2) with uniform points (the generator of the
 65536 x 8192 workload, at any size). --reps calls are made after --warmup calls;
@@ -23,7 +24,8 @@ from paper_2502_11017_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols", "alg1"], required=True)
+    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols", "alg1", "batch"], required=True)
+    ap.add_argument("--count", type=int, default=4096, help="matrices of the batched workload (--call batch)")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--r", type=int, default=64)
@@ -36,6 +38,8 @@ def main():
                     help="Gaussian kernel (FP32) or the rank-r factor product plus noise in BF16")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
+    if a.call == "batch":
+        return batch(a)
     if a.data == "bf16product":
         A = wl.bf16_factor_product(a.m, a.n, a.r, 1e-2, device=dev)
     else:
@@ -99,6 +103,41 @@ def main():
     st = cur.cur_sync_status(h)
     if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
         raise SystemExit(f"device status {st}")
+    hd.close()
+
+
+def batch(a):
+    """cur_cross_batched on the uneven batch: m ~ U[256, 4096], n ~ U[128, 1024], r ~ U{8..64}."""
+    import ctypes
+    dev = torch.device("cuda:0")
+    shapes = wl.uneven_batch_shapes(a.count)
+    data, offs = wl.uneven_batch_device(shapes, device=dev)
+    items = cur.batch_items(shapes, offs)
+    hd = cur.Handle(1, 1, 1, workspace_bytes=cur.cur_batch_workspace_size(items))
+    total = sum(s[2] for s in shapes)
+    IJ = torch.empty(2 * total, dtype=torch.int32, device=dev)
+    info = torch.zeros(len(shapes) * ctypes.sizeof(cur.CurCrossInfo), dtype=torch.uint8, device=dev)
+    a_bytes = sum(m * n * 4 for (m, n, _r, _b, _c) in shapes)
+    a_rounds = sum(m * n * 4 * r for (m, n, r, _b, _c) in shapes)
+    for rep in range(a.warmup + a.reps):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record()
+        cur.cur_cross_batched(hd.h, data, items, cur.opts(), IJ, info)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= a.warmup:
+            ms = e0.elapsed_time(e1)
+            print(f"batch of {a.count}: {ms:.3f} ms = {1000.0 * a.count / ms:.1f} crosses/s "
+                  f"(host {1e3 * (time.perf_counter() - t0):.3f} ms); A {a_bytes / 1e9:.2f} GB, "
+                  f"Algorithm 3 streams {a_rounds / 1e12:.3f} TB -> {a_rounds / (ms * 1e-3) / 1e9:.0f} GB/s if all from HBM")
+    st = cur.cur_sync_status(hd.h)
+    raw = info.cpu().numpy().tobytes()
+    sz = ctypes.sizeof(cur.CurCrossInfo)
+    stats = [cur.CurCrossInfo.from_buffer_copy(raw[t * sz:(t + 1) * sz]).status for t in range(len(shapes))]
+    print("status", st, "per-matrix statuses", {s: stats.count(s) for s in set(stats)})
     hd.close()
 
 

@@ -99,6 +99,66 @@ def bf16_factor_product(m: int = 262144, n: int = 16384, k: int = 128, noise_std
     return out
 
 
+def uneven_batch_shapes(count: int, seed: int = SEED_BASE + 3, m_range=(256, 4096), n_range=(128, 1024),
+                        r_range=(8, 64)):
+    """Shapes of the batched workload: m ~ U[m_range], n ~ U[n_range], r ~ U{r_range}
+    (inclusive), with b_r = max(1, m // 512) row and b_c = max(1, n // 512) column blocks."""
+    rng = np.random.default_rng(seed)
+    ms = rng.integers(m_range[0], m_range[1] + 1, size=count)
+    ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
+    rs = rng.integers(r_range[0], r_range[1] + 1, size=count)
+    return [(int(m), int(n), int(r), max(1, int(m) // 512), max(1, int(n) // 512))
+            for m, n, r in zip(ms, ns, rs)]
+
+
+def uneven_batch_matrix(m: int, n: int, seed: int, rank: int = 96, noise_std: float = 1e-6) -> np.ndarray:
+    """One matrix of the batched workload (FP32): U diag(sigma) V^T + noise with Haar U
+    (m x k), V (n x k), k = min(rank, m, n), sigma_j = j^-2, i.i.d. noise of std noise_std."""
+    rng = np.random.default_rng(seed)
+    k = min(rank, m, n)
+    u = haar(m, k, rng)
+    v = haar(n, k, rng)
+    s = 1.0 / np.arange(1, k + 1, dtype=np.float64) ** 2
+    a = (u * s) @ v.T + noise_std * rng.standard_normal((m, n))
+    return a.astype(np.float32)
+
+
+def uneven_batch(count: int, seed: int = SEED_BASE + 3, **kw):
+    """(shapes, matrices) of the batched workload; matrix t uses seed + 1 + t."""
+    shapes = uneven_batch_shapes(count, seed, **kw)
+    mats = [uneven_batch_matrix(m, n, seed + 1 + t) for t, (m, n, _r, _br, _bc) in enumerate(shapes)]
+    return shapes, mats
+
+
+def uneven_batch_device(shapes, seed: int = SEED_BASE + 3, rank: int = 96, noise_std: float = 1e-6,
+                        device="cuda"):
+    """The batched workload built on the device (a packed FP32 tensor and the element
+    offsets), for batches too large to build on the host in reasonable time: matrix t is
+    U diag(j^-2) V^T + noise with U, V from the QR of Gaussian matrices (sign-fixed, i.e.
+    Haar), all drawn from torch's counter-based generator seeded with seed + 1 + t."""
+    import torch
+    offs, total = [], 0
+    for (m, n, _r, _br, _bc) in shapes:
+        offs.append(total)
+        total += m * n
+    out = torch.empty(total, dtype=torch.float32, device=device)
+    for t, (m, n, _r, _br, _bc) in enumerate(shapes):
+        g = torch.Generator(device=device)
+        g.manual_seed(seed + 1 + t)
+        k = min(rank, m, n)
+        fac = []
+        for rows in (m, n):
+            q, rr = torch.linalg.qr(torch.randn((rows, k), generator=g, device=device, dtype=torch.float64))
+            d = torch.sign(torch.diagonal(rr))
+            d[d == 0] = 1.0
+            fac.append(q * d)
+        s = 1.0 / torch.arange(1, k + 1, device=device, dtype=torch.float64) ** 2
+        a = (fac[0] * s) @ fac[1].t()
+        a += noise_std * torch.randn((m, n), generator=g, device=device, dtype=torch.float64)
+        out[offs[t]:offs[t] + m * n] = a.reshape(-1).float()
+    return out, offs
+
+
 def hilbert(n: int) -> np.ndarray:
     """H_ij = 1/(i+j-1) with 1-based i, j (Section 3.1, Hilbert experiment)."""
     i = np.arange(1, n + 1, dtype=np.float64)

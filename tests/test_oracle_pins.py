@@ -489,3 +489,12 @@ def test_aca_full_replay_reproduces_its_own_run():
     piv2, mx, R2 = orc.aca_full_replay(a, I, J)
     assert piv2 == piv and np.array_equal(R, R2)
     assert all(abs(p) == m for p, m in zip(piv, mx))   # each pivot is the step's maximum
+
+
+def test_cross_batched_is_the_cross_of_each_matrix():
+    shapes = [(60, 40, 3, 2, 1), (50, 45, 4, 1, 2)]
+    mats = [wl.uneven_batch_matrix(m, n, 7 + t) for t, (m, n, _r, _b, _c) in enumerate(shapes)]
+    out = orc.cross_batched(mats, [s[2] for s in shapes], [(s[3], s[4]) for s in shapes])
+    for a, (m, n, r, br, bc), (I, J, info) in zip(mats, shapes, out):
+        I2, J2, info2 = orc.cross(a, r, br, bc)
+        assert I == I2 and J == J2 and info["logvol"] == info2["logvol"]
