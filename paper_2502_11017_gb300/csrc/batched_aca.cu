@@ -118,9 +118,11 @@ __device__ void bat_project(const float* Qh, const float* Ql, int64_t m, int t, 
     __syncthreads();
 }
 
+// order: the matrices by decreasing cost (r m n); queue: a zeroed counter. A CTA takes
+// the next matrix of the order when it finishes one (largest first, so the tail is short).
 __global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ data, const BatAcaItem* items,
-                                                       int count, int32_t* J, int32_t* counts, float* Qws,
-                                                       int* status) {
+                                                       const int32_t* order, int* queue, int count, int32_t* J,
+                                                       int32_t* counts, float* Qws, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* nu = reinterpret_cast<double*>(smem_raw);
     df64* part = reinterpret_cast<df64*>(nu + kBA_MaxN);               // 4 x n
@@ -130,11 +132,18 @@ __global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ 
     df64* qs = reinterpret_cast<df64*>(ql + kBA_MaxM);                   // r
     unsigned char* mask = reinterpret_cast<unsigned char*>(qs + kBA_MaxR);
     __shared__ double s_frob2;
+    __shared__ int s_next;
     const int tid = threadIdx.x;
     float* Qh = Qws + (int64_t)blockIdx.x * 2 * kBA_MaxR * kBA_MaxM;
     float* Ql = Qh + (int64_t)kBA_MaxR * kBA_MaxM;
 
-    for (int it = blockIdx.x; it < count; it += gridDim.x) {
+    while (true) {
+        if (tid == 0) s_next = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_next;
+        __syncthreads();
+        if (q >= count) break;
+        const int it = order[q];
         const BatAcaItem b = items[it];
         const float* A = data + b.aoff;
         const int64_t m = b.m, n = b.n, ld = b.ld;
@@ -251,13 +260,14 @@ size_t bat_aca_workspace(int grid) {
     return (size_t)grid * 2 * curk::kBA_MaxR * curk::kBA_MaxM * sizeof(float);
 }
 
-cur_status bat_aca_launch(const float* data, const void* items_dev, int count, int32_t* J, int32_t* counts,
-                          float* Qws, int grid, int* status, cudaStream_t st) {
+cur_status bat_aca_launch(const float* data, const void* items_dev, const int32_t* order, int* queue, int count,
+                          int32_t* J, int32_t* counts, float* Qws, int grid, int* status, cudaStream_t st) {
     using namespace curk;
     const size_t sm = bat_aca_smem();
     CUR_CK(cudaFuncSetAttribute((const void*)bat_aca_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    bat_aca_k<<<grid, kBA_T, sm, st>>>(data, static_cast<const BatAcaItem*>(items_dev), count, J, counts, Qws,
-                                       status);
+    CUR_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
+    bat_aca_k<<<grid, kBA_T, sm, st>>>(data, static_cast<const BatAcaItem*>(items_dev), order, queue, count, J,
+                                       counts, Qws, status);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;

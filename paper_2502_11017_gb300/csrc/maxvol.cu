@@ -40,6 +40,7 @@ struct MvProb {
     int64_t base;      // first row of the problem in the basis / B buffers
     int64_t boff;      // element offset of its basis rows (p x r, contiguous)
     int32_t r;         // its rank (<= the stage's r, which is the stride of per-problem arrays)
+    int32_t gmode;     // 1: its B lives in global memory (a problem too large for shared memory)
     int64_t gid_base;  // global id of local row i = gid_base + i (when gid_arr == null)
     const int32_t* gid_arr;
     int32_t p;         // rows
@@ -669,7 +670,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     const int r = pr.r, rs = a.r, G = pr.G, tid = threadIdx.x, nt = blockDim.x;
     const bool solo = G == 1;                   // one CTA: no inter-CTA exchange at all
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
-    const bool gmode = a.bglob != nullptr;
+    const bool gmode = a.bglob != nullptr && pr.gmode;
     TB* Bs = gmode ? static_cast<TB*>(a.bglob) + pr.boff + (int64_t)lo * r   // nloc x r slice of B
                    : reinterpret_cast<TB*>(smem_raw);
     TB* Mi = gmode ? reinterpret_cast<TB*>(smem_raw) : Bs + (size_t)nloc * r;   // r x r: M^-1 (compute type)
@@ -1064,43 +1065,63 @@ struct Stage {
     TB* pub = nullptr;
     double* aux = nullptr;
     std::vector<int> stat, sw;  // host copies after read()
+    int coop_slots = 0;         // slots [0, coop_slots) hold groups of several CTAs
     bool keep_singular_set = false;
     TB* bglob = nullptr;        // B in global memory when it cannot live in shared memory
 };
 
 template <typename TB>
-static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
+// starts: the stage runs the Algorithm 3 start (mv_start), which keeps each CTA's rows in
+// shared memory, so its problems never take the global-memory form.
+static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar, bool starts = false) {
     const int P = (int)sg.probs.size();
     sg.P = P;
-    const int cap = rows_cap<TB>(r);
+    int capr[129] = {0};   // rows per CTA with B in shared memory, by rank
+    auto cap_of = [&](int rr) {
+        if (!capr[rr]) capr[rr] = rows_cap<TB>(rr);
+        return capr[rr];
+    };
     int64_t tot_p = 0;
     for (auto& pr : sg.probs) tot_p += pr.p;
-    // B in shared memory needs ceil(p / cap) co-resident CTAs per problem; a problem that
-    // would need more than one per SM puts the stage's B in global memory instead
-    bool gmode = false;
+    // A problem whose B does not fit one CTA's shared memory is spread over a group of
+    // co-resident CTAs; with many problems in the stage (a batch), or when it would need
+    // more than one CTA per SM, its B goes to global memory and one CTA takes it.
+    const bool many = P >= 2 * h->num_sms;
     int64_t elems_end = 0;
+    bool anyg = false;
     for (auto& pr : sg.probs) {
-        if ((pr.p + cap - 1) / cap > h->num_sms) gmode = true;
-        elems_end = std::max<int64_t>(elems_end, pr.boff + (int64_t)pr.p * pr.r);
-    }
-    int slots = 0;
-    for (auto& pr : sg.probs) {
-        // one CTA when the problem fits (no inter-CTA exchange); otherwise spread large
-        // problems over the SMs in proportion to their size
-        int64_t G = gmode ? 1 : (pr.p + cap - 1) / cap;
-        if (G > 1 || gmode) {
+        const int cap = cap_of(pr.r);
+        int64_t G = (pr.p + cap - 1) / cap;
+        pr.gmode = 0;
+        if (G > 1 && (many || G > h->num_sms) && !starts) pr.gmode = 1;
+        if (pr.gmode && many) {
+            G = 1;
+        } else if (G > 1 || pr.gmode) {
+            // spread large problems over the SMs in proportion to their size
             const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
                                                      (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
-            G = std::max<int64_t>(G, spread);
+            G = std::max<int64_t>(pr.gmode ? 1 : G, spread);
+            G = std::min<int64_t>(G, h->num_sms);
         }
         G = std::max<int64_t>(1, G);
         const int rpc = (int)((pr.p + G - 1) / G);
         G = (pr.p + rpc - 1) / rpc;
         pr.G = (int)G;
         pr.rpc = rpc;
-        pr.group0 = slots;
-        slots += (int)G;
         sg.max_rpc = std::max(sg.max_rpc, rpc);
+        anyg |= pr.gmode != 0;
+        elems_end = std::max<int64_t>(elems_end, pr.boff + (int64_t)pr.p * pr.r);
+    }
+    int slots = 0;
+    // slots: the groups of several CTAs first (cooperative launches, co-resident), then
+    // the single-CTA problems (one plain launch: they never wait on another CTA)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (auto& pr : sg.probs)
+            if ((pr.G > 1) == (pass == 0)) {
+                pr.group0 = slots;
+                slots += pr.G;
+            }
+        if (pass == 0) sg.coop_slots = slots;
     }
     sg.slots = slots;
     sg.dprob = ar.get<MvProb>(P);
@@ -1117,7 +1138,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar) {
     sg.keyi = ar.get<long long>((size_t)2 * slots);
     sg.pub = ar.get<TB>((size_t)2 * slots * r);
     sg.aux = ar.get<double>((size_t)2 * slots);
-    sg.bglob = gmode ? ar.get<TB>((size_t)elems_end) : nullptr;
+    sg.bglob = anyg ? ar.get<TB>((size_t)elems_end) : nullptr;
     if (!ar.ok) return CUR_ERR_NOMEM;
     return CUR_OK;
 }
@@ -1178,8 +1199,12 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     a.aux = sg.aux;
     a.status = h->status;
 
-    const size_t sm_eng = EngineSmem<TB>::bytes(sg.max_rpc, r, sg.bglob != nullptr);
-    const size_t sm_start = StartSmem<TB>::bytes(sg.max_rpc, r);
+    // shared memory of a launch: the largest any of its problems needs
+    size_t sm_eng = 0, sm_start = 0;
+    for (const auto& pr : sg.probs) {
+        sm_eng = std::max(sm_eng, EngineSmem<TB>::bytes(pr.rpc, pr.r, pr.gmode != 0));
+        sm_start = std::max(sm_start, StartSmem<TB>::bytes(pr.rpc, pr.r));
+    }
     const size_t sm_lu = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
     CUR_TRY(set_smem_attr(mv_engine<TB>, sm_eng));
     CUR_TRY(set_smem_attr(mv_lu<TB>, sm_lu));
@@ -1194,17 +1219,20 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     for (auto& pr : sg.probs)
         if (pr.G > cap_eng || (aca_start && pr.G > cap_start)) return CUR_ERR_ARG;
     // waves: consecutive whole groups within the co-residency capacity
+    // cooperative waves of whole multi-CTA groups, then one plain launch of the rest
     auto waves = [&](int capc) {
         std::vector<std::pair<int, int>> w;
         int first = 0, cnt = 0;
         for (int pb = 0; pb < P; ++pb) {
             const int G = sg.probs[pb].G;
+            if (G == 1) continue;
             if (cnt + G > capc && cnt > 0) { w.push_back({first, cnt}); first += cnt; cnt = 0; }
             cnt += G;
         }
         if (cnt > 0) w.push_back({first, cnt});
         return w;
     };
+    const int solo_slots = slots - sg.coop_slots;
     if (aca_start) {
         CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
         for (auto& w : waves(cap_start)) {
@@ -1214,11 +1242,25 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
             CUR_TRY(launch_coop((const void*)mv_start<TB>, dim3(w.second), dim3(256), args, sm_start, st));
             note_launch();
         }
+        if (solo_slots > 0) {
+            MvArgs aw = a;
+            aw.cta_base = sg.coop_slots;
+            mv_start<TB><<<solo_slots, 256, sm_start, st>>>(aw);
+            CUR_CK(cudaGetLastError());
+            note_launch();
+        }
     }
     mv_lu<TB><<<P, 256, sm_lu, st>>>(a);
     CUR_CK(cudaGetLastError());
     note_launch();
     CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
+    if (solo_slots > 0) {
+        MvArgs aw = a;
+        aw.cta_base = sg.coop_slots;
+        mv_engine<TB><<<solo_slots, 256, sm_eng, st>>>(aw);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
     for (auto& w : waves(cap_eng)) {
         MvArgs aw = a;
         aw.cta_base = w.first;
@@ -1425,7 +1467,7 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         sb.probs.push_back(pr);
         s0 += sz;
     }
-    CUR_TRY(stage_setup<TB>(h, r, sb, ar));
+    CUR_TRY(stage_setup<TB>(h, r, sb, ar, true));
     std::vector<int> none;
     CUR_TRY(stage_run<TB>(h, basis, r, o, sb, true, none, none, st));
     CUR_TRY(stage_read<TB>(h, sb, st));
@@ -1790,7 +1832,7 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
             s0 += sz;
         }
     }
-    CUR_TRY(stage_setup<float>(h, rs, sb, ar));
+    CUR_TRY(stage_setup<float>(h, rs, sb, ar, true));
     CUR_TRY(stage_run<float>(h, basis, rs, o, sb, true, none, none, st));
     CUR_TRY(stage_read<float>(h, sb, st));
     for (int t = 0; t < T; ++t)
@@ -1997,8 +2039,8 @@ static cur_status bat_global(cur_handle* h, const float* basis, const std::vecto
 
 size_t bat_aca_workspace(int grid);
 size_t bat_aca_item_size();
-cur_status bat_aca_launch(const float* data, const void* items_dev, int count, int32_t* J, int32_t* counts,
-                          float* Qws, int grid, int* status, cudaStream_t st);
+cur_status bat_aca_launch(const float* data, const void* items_dev, const int32_t* order, int* queue, int count,
+                          int32_t* J, int32_t* counts, float* Qws, int grid, int* status, cudaStream_t st);
 
 // The cross of every matrix of the batch (see cur_cross_batched).
 cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_item* items, int T,
@@ -2052,7 +2094,17 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     int32_t* I = ar.get<int32_t>((size_t)T * rs);
     int32_t* J = ar.get<int32_t>((size_t)T * rs);
     double* lvc = ar.get<double>(T);
+    int32_t* dorder = ar.get<int32_t>(T);
+    int* queue = ar.get<int>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    {
+        std::vector<int32_t> order(T);
+        for (int t = 0; t < T; ++t) order[t] = t;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return items[x].rows * items[x].cols * items[x].r > items[y].rows * items[y].cols * items[y].r;
+        });
+        CUR_TRY(bat_upload(h, dorder, order.data(), sizeof(int32_t) * T, st));
+    }
     CUR_TRY(bat_upload(h, dai, ai.data(), sizeof(AcaIt) * T, st));
     CUR_TRY(bat_upload(h, dgc, gc.data(), sizeof(BatGItem) * T, st));
     CUR_TRY(bat_upload(h, dgr, gr.data(), sizeof(BatGItem) * T, st));
@@ -2060,7 +2112,7 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     CUR_TRY(bat_upload(h, dnn, nn.data(), sizeof(int64_t) * T, st));
     CUR_TRY(bat_upload(h, drr, rr.data(), sizeof(int32_t) * T, st));
     // ---- J0: Algorithm 3 on the columns of every matrix, padded per matrix
-    CUR_TRY(bat_aca_launch(data, dai, T, J0, cnt, Qws, grid, h->status, st));
+    CUR_TRY(bat_aca_launch(data, dai, dorder, queue, T, J0, cnt, Qws, grid, h->status, st));
     std::vector<int32_t> hcnt(T);
     CUR_CK(cudaStreamSynchronize(st));
     CUR_CK(cudaMemcpy(hcnt.data(), cnt, sizeof(int32_t) * T, cudaMemcpyDeviceToHost));

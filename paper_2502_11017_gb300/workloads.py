@@ -102,12 +102,13 @@ def bf16_factor_product(m: int = 262144, n: int = 16384, k: int = 128, noise_std
 def uneven_batch_shapes(count: int, seed: int = SEED_BASE + 3, m_range=(256, 4096), n_range=(128, 1024),
                         r_range=(8, 64)):
     """Shapes of the batched workload: m ~ U[m_range], n ~ U[n_range], r ~ U{r_range}
-    (inclusive), with b_r = max(1, m // 512) row and b_c = max(1, n // 512) column blocks."""
+    (inclusive), with b_r = ceil(m / 512) row and b_c = ceil(n / 512) column blocks (blocks
+    of at most 512 rows or columns)."""
     rng = np.random.default_rng(seed)
     ms = rng.integers(m_range[0], m_range[1] + 1, size=count)
     ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
     rs = rng.integers(r_range[0], r_range[1] + 1, size=count)
-    return [(int(m), int(n), int(r), max(1, int(m) // 512), max(1, int(n) // 512))
+    return [(int(m), int(n), int(r), -(-int(m) // 512), -(-int(n) // 512))
             for m, n, r in zip(ms, ns, rs)]
 
 
@@ -148,7 +149,12 @@ def uneven_batch_device(shapes, seed: int = SEED_BASE + 3, rank: int = 96, noise
         k = min(rank, m, n)
         fac = []
         for rows in (m, n):
-            q, rr = torch.linalg.qr(torch.randn((rows, k), generator=g, device=device, dtype=torch.float64))
+            gm = torch.randn((rows, k), generator=g, device=device, dtype=torch.float64)
+            try:
+                q, rr = torch.linalg.qr(gm)
+            except RuntimeError:    # no device linear-algebra library in this process
+                q, rr = torch.linalg.qr(gm.cpu())
+                q, rr = q.to(device), rr.to(device)
             d = torch.sign(torch.diagonal(rr))
             d[d == 0] = 1.0
             fac.append(q * d)
