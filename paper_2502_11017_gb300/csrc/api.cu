@@ -216,7 +216,7 @@ size_t cur_batch_workspace_size(const cur_batch_item* items, int32_t count) {
         b += minv * (size_t)(2 * (std::max(1, it.b_r) + std::max(1, it.b_c)) + 4);
         b += 512;
     }
-    b += (size_t)std::min(count, 256) * 2 * 64 * 4096 * sizeof(float);   // Algorithm 3's Q slices
+    b += (size_t)std::min(count, 512) * 2 * 64 * 4096 * sizeof(float);   // Algorithm 3's Q slices
     return b;
 }
 

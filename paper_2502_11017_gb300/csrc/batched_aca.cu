@@ -6,7 +6,8 @@
 // synchronisation. The rounds are those of the full-matrix kernels (the implicit
 // residual nu_j = ||a_j||^2 - sum_k (q_k^T a_j)^2, one read of the matrix per round):
 //   pass   : w_j = a_j^T q_t for every column (Dot2 with q as FP32 hi/lo pairs), the
-//            1024 threads split into 4 row groups x 256 four-column groups
+//            512 threads split into 2 row groups x 256 four-column groups; two CTAs
+//            per SM, so one streams its matrix while the other runs its pivot step
 //   pick   : nu_j -= w_j^2, masked argmax (lowest index on ties)
 //   vector : v = a_p orthogonalised twice against q_1..q_t (double-float), the early stop
 //            on the recomputed ||v||^2 <= (max(m,n) eps ||A||_F)^2, q = v / ||v||
@@ -22,7 +23,8 @@
 
 namespace curk {
 
-constexpr int kBA_T = 1024;     // threads per CTA
+constexpr int kBA_T = 512;      // threads per CTA (two CTAs per SM: one streams while the other pivots)
+constexpr int kBA_RG = kBA_T / 256;   // row groups of the pass
 constexpr int kBA_MaxM = 4096;
 constexpr int kBA_MaxN = 1024;
 constexpr int kBA_MaxR = 64;
@@ -33,10 +35,10 @@ struct BatAcaItem {
     int64_t joff;             // its J0 at J + joff (r entries)
 };
 
-// shared-memory layout (bytes): nu n x 8 | part 4 x n x 8 | v m x 8 | qh m x 4 | ql m x 4 |
+// shared-memory layout (bytes): nu n x 8 | part RG x n x 8 | v m x 8 | qh m x 4 | ql m x 4 |
 // s kBA_MaxR x 8 | mask n
 __host__ __device__ constexpr size_t bat_aca_smem() {
-    return (size_t)kBA_MaxN * 8 + (size_t)4 * kBA_MaxN * 8 + (size_t)kBA_MaxM * 8 + (size_t)kBA_MaxM * 8 +
+    return (size_t)kBA_MaxN * 8 + (size_t)kBA_RG * kBA_MaxN * 8 + (size_t)kBA_MaxM * 8 + (size_t)kBA_MaxM * 8 +
            (size_t)kBA_MaxR * 8 + kBA_MaxN + 64;
 }
 
@@ -120,13 +122,13 @@ __device__ void bat_project(const float* Qh, const float* Ql, int64_t m, int t, 
 
 // order: the matrices by decreasing cost (r m n); queue: a zeroed counter. A CTA takes
 // the next matrix of the order when it finishes one (largest first, so the tail is short).
-__global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ data, const BatAcaItem* items,
+__global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ data, const BatAcaItem* items,
                                                        const int32_t* order, int* queue, int count, int32_t* J,
                                                        int32_t* counts, float* Qws, int* status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* nu = reinterpret_cast<double*>(smem_raw);
-    df64* part = reinterpret_cast<df64*>(nu + kBA_MaxN);               // 4 x n
-    df64* v = part + 4 * kBA_MaxN;                                       // m
+    df64* part = reinterpret_cast<df64*>(nu + kBA_MaxN);               // RG x n
+    df64* v = part + kBA_RG * kBA_MaxN;                                  // m
     float* qh = reinterpret_cast<float*>(v + kBA_MaxM);                  // m
     float* ql = qh + kBA_MaxM;                                           // m
     df64* qs = reinterpret_cast<df64*>(ql + kBA_MaxM);                   // r
@@ -157,12 +159,12 @@ __global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ 
             const int64_t c0 = 4 * (int64_t)cg;
             Dot2 acc[4];
             if (c0 < n) {
-                // four rows (16 apart) loaded before they are folded: 64 bytes in flight per thread
-                for (int64_t i0 = rg; i0 < m; i0 += 16) {
+                // four rows loaded before they are folded: 64 bytes in flight per thread
+                for (int64_t i0 = rg; i0 < m; i0 += 4 * kBA_RG) {
                     float x[4][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int64_t i = i0 + 4 * u;
+                        const int64_t i = i0 + kBA_RG * u;
                         const float* row = A + (i < m ? i : i0) * ld + c0;
                         if (vec) {
                             const float4 y = __ldcs(reinterpret_cast<const float4*>(row));
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ 
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int64_t i = i0 + 4 * u;
+                        const int64_t i = i0 + kBA_RG * u;
                         if (i >= m) break;
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -193,8 +195,9 @@ __global__ void __launch_bounds__(kBA_T, 1) bat_aca_k(const float* __restrict__ 
             int bi = INT_MAX;
             double fs = 0.0;
             for (int j = tid; j < n; j += blockDim.x) {
-                const df64 w = df_add(df_add(part[j], part[kBA_MaxN + j]),
-                                      df_add(part[2 * kBA_MaxN + j], part[3 * kBA_MaxN + j]));
+                df64 w = part[j];
+#pragma unroll
+                for (int g = 1; g < kBA_RG; ++g) w = df_add(w, part[g * kBA_MaxN + j]);
                 const double wd = df_to_d(w);
                 double nuj;
                 if (t < 0) {

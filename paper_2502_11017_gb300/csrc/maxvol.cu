@@ -2079,7 +2079,7 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     }
     static_assert(sizeof(AcaIt) == 48, "BatAcaItem layout");
     if (bat_aca_item_size() != sizeof(AcaIt)) return CUR_ERR_ARG;
-    const int grid = std::min(T, h->num_sms);
+    const int grid = std::min(T, 2 * h->num_sms);
     void* dai = ar.take(sizeof(AcaIt) * T);
     BatGItem* dgc = ar.get<BatGItem>(T);
     BatGItem* dgr = ar.get<BatGItem>(T);
