@@ -161,19 +161,19 @@ struct StartSmem {
     }
 };
 
-// nu[i] = sum_c rows(i,c) * q(c) (mode 1) or rows(i,c)^2 (mode 0), each row split over 4
+// nu[i] = sum_c rows(i,c) * q(c) (mode 1) or rows(i,c)^2 (mode 0), each row split over 8
 // consecutive lanes (Dot2 for FP32 data, FP64 for FP64 data), combined by shuffles.
 template <typename TB>
 __device__ __forceinline__ void rows_dot4(const TB* rows, int nloc, int r, const double* q64,
                                           const float* qh, const float* ql, int mode,
                                           double* out, bool downdate) {
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int it0 = 0; it0 < 4 * nloc; it0 += nt) {
+    for (int it0 = 0; it0 < 8 * nloc; it0 += nt) {
         const int it = it0 + tid;
-        const int row = it >> 2, qt = it & 3;
+        const int row = it >> 3, qt = it & 7;
         double v = 0.0;
         if (row < nloc) {
-            const int c0 = r * qt / 4, c1 = r * (qt + 1) / 4;
+            const int c0 = r * qt / 8, c1 = r * (qt + 1) / 8;
             const TB* x = rows + (size_t)row * r;
             if (std::is_same<TB, double>::value) {
                 DotD d;
@@ -191,6 +191,7 @@ __device__ __forceinline__ void rows_dot4(const TB* rows, int nloc, int r, const
         }
         v += __shfl_xor_sync(0xffffffffu, v, 1);
         v += __shfl_xor_sync(0xffffffffu, v, 2);
+        v += __shfl_xor_sync(0xffffffffu, v, 4);
         if (row < nloc && qt == 0) {
             if (downdate) out[row] -= v * v;
             else out[row] = v;
@@ -227,6 +228,10 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     for (int i = tid; i < nloc; i += nt) msk[i] = 0;
     __syncthreads();
     rows_dot4<TB>(rows, nloc, r, v, qh, ql, 0, nu, false);
+    if constexpr (!std::is_same<TB, double>::value) {
+        df64* Pd = reinterpret_cast<df64*>(Q);
+        for (int e = tid; e < r * r; e += nt) Pd[e] = df64{(e / r == e % r) ? 1.f : 0.f, 0.f};
+    }
     __syncthreads();
     double fs = 0.0;
     for (int i = tid; i < nloc; i += nt) fs += nu[i];
@@ -316,33 +321,31 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
             }
             __syncthreads();
         } else {
-            df64* Qd = reinterpret_cast<df64*>(Q);      // r x r pairs (same bytes as doubles)
+            // The projector P = I - sum_k q_k q_k^T (r x r, double-float, in the bytes of Q)
+            // is kept current, so the two Gram-Schmidt sweeps are two products v <- P v with
+            // all threads busy, instead of k dependent dot products each.
+            df64* Pd = reinterpret_cast<df64*>(Q);
             df64* vd = reinterpret_cast<df64*>(v);
             df64* sdd = reinterpret_cast<df64*>(sd);
             df64* redd = reinterpret_cast<df64*>(red);
             for (int c = tid; c < r; c += nt) vd[c] = df64{to_f(cp[c]), 0.f};
             __syncthreads();
-            for (int pass = 0; pass < 2; ++pass) {
-                for (int kk = warp; kk < k; kk += nw) {
-                    df64 s{0.f, 0.f};
-                    for (int c = lane; c < r; c += 32) s = df_add(s, df_mul(Qd[kk * r + c], vd[c]));
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const df64 t{__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
-                        s = df_add(s, t);
-                    }
-                    if (lane == 0) sdd[kk] = s;
-                }
-                __syncthreads();
+            for (int pass = 0; pass < 2 && k > 0; ++pass) {
                 for (int it = tid; it < 4 * r; it += nt) {
                     const int c = it % r, qt = it / r;
-                    df64 s{0.f, 0.f};
-                    for (int kk = k * qt / 4; kk < k * (qt + 1) / 4; ++kk) s = df_add(s, df_mul(Qd[kk * r + c], sdd[kk]));
-                    redd[qt * r + c] = s;
+                    df64 s0{0.f, 0.f}, s1{0.f, 0.f};
+                    const int d0 = r * qt / 4, d1 = r * (qt + 1) / 4;
+                    int d = d0;
+                    for (; d + 1 < d1; d += 2) {   // P symmetric: column c read as row c
+                        s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
+                        s1 = df_add(s1, df_mul(Pd[(d + 1) * r + c], vd[d + 1]));
+                    }
+                    if (d < d1) s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
+                    redd[qt * r + c] = df_add(s0, s1);
                 }
                 __syncthreads();
                 for (int c = tid; c < r; c += nt)
-                    vd[c] = df_sub(vd[c], df_add(df_add(df_add(redd[c], redd[r + c]), redd[2 * r + c]), redd[3 * r + c]));
+                    vd[c] = df_add(df_add(redd[c], redd[r + c]), df_add(redd[2 * r + c], redd[3 * r + c]));
                 __syncthreads();
             }
             if (warp == 0) {
@@ -372,9 +375,14 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
             __syncthreads();
             for (int c = tid; c < r; c += nt) {
                 const df64 q = df_mul(vd[c], inv);
-                Qd[k * r + c] = q;
+                vd[c] = q;
                 qh[c] = q.h;
                 ql[c] = q.l;
+            }
+            __syncthreads();
+            for (int e = tid; e < r * r; e += nt) {   // P -= q q^T
+                const int i = e / r, c = e - i * r;
+                Pd[e] = df_sub(Pd[e], df_mul(vd[i], vd[c]));
             }
             __syncthreads();
         }
