@@ -5,21 +5,27 @@
 // every entry B_ij is the factor by which |det M| changes when row i of C
 // replaces position j of S. While max|B_ij| > 1 + delta the best swap is made
 // and B is updated by Sherman-Morrison, B <- B - B(:,j) (B(i,:) - e_j^T) / B_ij;
-// every r swaps, and before convergence is declared, B is recomputed from M^-1.
+// every r swaps, and before convergence is declared, a new cycle starts from B
+// recomputed as C M^-1.
 //
 // Work is organised as "problems" (a row block of C, a merge node, or all of C),
-// each handled by a group of co-resident CTAs:
+// each handled by one CTA or by a group of co-resident CTAs:
 //   mv_start  : Algorithm 3 (axis 0) on the problem's rows -> start set S
 //               (implicit Gram-Schmidt, one group barrier per pick)
 //   mv_lu     : one CTA per problem, FP64 Gauss-Jordan inverse of C(S,:) with
 //               partial pivoting, log|det|
 //   mv_engine : the whole swap iteration of a stage in one launch. Each CTA keeps
 //               its slice of B in shared memory (FP32 for FP32/BF16 data, FP64 for
-//               FP64 data) and the group agrees on argmax|B_ij| through one barrier
-//               per swap. The group's first CTA recomputes the winning row of B in
-//               FP64 and keeps M^-1 (FP64) current by the Sherman-Morrison update,
-//               so a refresh is B = C M^-1 from that FP64 inverse, with no new
-//               factorisation. A merge node starts from its left child's M^-1.
+//               FP64 data; in global memory for a problem too large for that), and
+//               a group agrees on argmax|B_ij| through one barrier per swap. The
+//               first CTA recomputes the winning row of B from C and M^-1 and keeps
+//               M^-1 current by the Sherman-Morrison update (double-float for FP32
+//               data, FP64 for FP64 data). A cycle refactorises C(S,:) (FP64 data:
+//               always; FP32 data: once the kept inverse's drift bound exceeds its
+//               limit) and refreshes B = C M^-1. A merge node starts from its left
+//               child's M^-1.
+// A stage's problems may have different ranks (batches); single-CTA problems go in one
+// plain launch, multi-CTA groups in cooperative launches of co-resident waves.
 
 #include <algorithm>
 #include <array>
@@ -153,7 +159,7 @@ struct StartSmem {
     static size_t bytes(int nloc, int r) {
         size_t b = (size_t)nloc * r * sizeof(TB);
         b = (b + 15) / 16 * 16 + (size_t)nloc * sizeof(double);
-        b += (size_t)r * r * sizeof(double);        // Q
+        b += (size_t)r * r * sizeof(double);        // Q (FP64 data) or the projector P
         b += (size_t)6 * r * sizeof(double);        // v, sd, partial sums (4 r)
         b += (size_t)2 * r * sizeof(float);         // qh, ql
         b += (size_t)nloc + 16;                     // mask
