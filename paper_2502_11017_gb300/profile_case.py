@@ -34,18 +34,22 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=11019)
-    ap.add_argument("--data", choices=["gaussian", "bf16product"], default="gaussian",
-                    help="Gaussian kernel (FP32) or the rank-r factor product plus noise in BF16")
+    ap.add_argument("--data", choices=["gaussian", "bf16product", "haar"], default="gaussian",
+                    help="Gaussian kernel (FP32), the rank-r factor product plus noise in BF16, or "
+                         "the FP64 low-rank Haar matrix (2000 x 1500, sigma_k = 2^(-k/2))")
     a = ap.parse_args()
     dev = torch.device("cuda:0")
     if a.call == "batch":
         return batch(a)
     if a.data == "bf16product":
         A = wl.bf16_factor_product(a.m, a.n, a.r, 1e-2, device=dev)
+    elif a.data == "haar":
+        A = torch.from_numpy(wl.lowrank_haar()).to(dev)
+        a.m, a.n = A.shape
     else:
         A = torch.from_numpy(wl.gaussian_kernel(a.m, a.n, 0.2, seed=a.seed, chunk_rows=1024)).to(dev)
     m, n, r = a.m, a.n, a.r
-    hd = cur.Handle(m, n, max(r, 64), cur.CUR_BF16 if a.data == "bf16product" else cur.CUR_F32)
+    hd = cur.Handle(m, n, max(r, 64), {"bf16product": cur.CUR_BF16, "haar": cur.CUR_F64}.get(a.data, cur.CUR_F32))
     h = hd.h
     idx = torch.empty(r, dtype=torch.int32, device=dev)
     I = torch.empty(r, dtype=torch.int32, device=dev)
@@ -57,7 +61,8 @@ def main():
     cheb = torch.empty(1, dtype=torch.float64, device=dev)
     fro = torch.empty(1, dtype=torch.float64, device=dev)
     o = cur.opts()
-    Rw = torch.empty((m, n), dtype=torch.float32, device=dev) if a.call == "alg1" else None
+    Rw = torch.empty((m, n), dtype=torch.float64 if A.dtype == torch.float64 else torch.float32,
+                     device=dev) if a.call == "alg1" else None
     piv = torch.empty(r, dtype=torch.float64, device=dev)
     if a.call in ("residual", "rows", "cols"):
         cur.cur_cross(h, A, r, a.b_r, a.b_c, o, I, J)
