@@ -487,7 +487,7 @@ struct EngineSmem {
         return ((b > gj ? b : gj) + 15) / 16 * 16;
     }
     static size_t bytes(int nloc, int r, bool gmode = false) {
-        size_t b = head(nloc, r, gmode) + (size_t)8 * r * sizeof(double) + 64;
+        size_t b = head(nloc, r, gmode) + (size_t)12 * r * sizeof(double) + 64;   // keeper vectors
         if (r <= kMsMax) b += (size_t)r * r * sizeof(double);
         return b;
     }
@@ -526,14 +526,14 @@ struct MinvKeeper<float> {
     df64* crow;   // r: C(i*,:)
     df64* brow;   // r: row i* of B
     df64* cj;     // r: column j* of M^-1, then divided by B(i*,j*)
-    df64* red;    // 4 r
+    df64* red;    // 8 r: eighth-sums of brow
     LogAcc lacc;
     __device__ void setup(unsigned char* base, int r, double* Mg, bool in_smem, float* gdf) {
         crow = reinterpret_cast<df64*>(base);
         brow = crow + r;
         cj = brow + r;
         red = cj + r;
-        Mh = in_smem ? reinterpret_cast<float*>(red + 4 * r) : gdf;
+        Mh = in_smem ? reinterpret_cast<float*>(red + 8 * r) : gdf;
         Ml = Mh + r * r;
         lacc.init();
     }
@@ -553,17 +553,19 @@ struct MinvKeeper<float> {
         const int tid = threadIdx.x, nt = blockDim.x;
         for (int c = tid; c < r; c += nt) crow[c] = df64{ci[c], 0.f};
         __syncthreads();
-        for (int it = tid; it < 4 * r; it += nt) {
+        // brow = crow M^-1: eight partial sums per column, so each dependent chain is r/8 long
+        for (int it = tid; it < 8 * r; it += nt) {
             const int c = it % r, qt = it / r;
             df64 s{0.f, 0.f};
-            for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k)
+            for (int k = r * qt / 8; k < r * (qt + 1) / 8; ++k)
                 s = df_add(s, df_mul_f(df64{Mh[k * r + c], Ml[k * r + c]}, crow[k].h));
             red[qt * r + c] = s;
         }
         for (int k = tid; k < r; k += nt) cj[k] = df64{Mh[k * r + jstar], Ml[k * r + jstar]};
         __syncthreads();
         for (int c = tid; c < r; c += nt)
-            brow[c] = df_add(df_add(df_add(red[c], red[r + c]), red[2 * r + c]), red[3 * r + c]);
+            brow[c] = df_add(df_add(df_add(red[c], red[r + c]), df_add(red[2 * r + c], red[3 * r + c])),
+                             df_add(df_add(red[4 * r + c], red[5 * r + c]), df_add(red[6 * r + c], red[7 * r + c])));
         __syncthreads();
         const df64 bb = brow[jstar];
         for (int k = tid; k < r; k += nt) cj[k] = df_div(cj[k], bb);
@@ -594,7 +596,7 @@ struct MinvKeeper<double> {
         brow = crow + r;
         cj = brow + r;
         red = cj + r;
-        M = in_smem ? red + 4 * r : Mg;
+        M = in_smem ? red + 8 * r : Mg;
         lacc.init();
     }
     __device__ void load(const double* Mg, int r) {
@@ -610,15 +612,17 @@ struct MinvKeeper<double> {
         const int tid = threadIdx.x, nt = blockDim.x;
         for (int c = tid; c < r; c += nt) crow[c] = ci[c];
         __syncthreads();
-        for (int it = tid; it < 4 * r; it += nt) {
+        for (int it = tid; it < 8 * r; it += nt) {
             const int c = it % r, qt = it / r;
             double s = 0.0;
-            for (int k = r * qt / 4; k < r * (qt + 1) / 4; ++k) s = fma(crow[k], M[k * r + c], s);
+            for (int k = r * qt / 8; k < r * (qt + 1) / 8; ++k) s = fma(crow[k], M[k * r + c], s);
             red[qt * r + c] = s;
         }
         for (int k = tid; k < r; k += nt) cj[k] = M[k * r + jstar];
         __syncthreads();
-        for (int c = tid; c < r; c += nt) brow[c] = ((red[c] + red[r + c]) + red[2 * r + c]) + red[3 * r + c];
+        for (int c = tid; c < r; c += nt)
+            brow[c] = (((red[c] + red[r + c]) + (red[2 * r + c] + red[3 * r + c])) +
+                       ((red[4 * r + c] + red[5 * r + c]) + (red[6 * r + c] + red[7 * r + c])));
         __syncthreads();
         const double bb = brow[jstar];
         Walk2 w(tid, nt, r);
