@@ -304,10 +304,12 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
             tc_fence_after();
             const float* As = reinterpret_cast<const float*>(AS + (size_t)slot * kASub) + jl;
             float tse = 0.f, tsa = 0.f;
+            // the sub-tile's 32 accumulator columns in one TMEM load (one wait)
+            float dall[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + kAR * k), dall);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
-                float dv[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + kAR * k + 16 * c), dv);
+                const float* dv = dall + 16 * c;
                 if (full) {
                     // four independent chains per sum; a NaN anywhere makes the group's
                     // sum of squares NaN (fmaxf alone would drop it)
