@@ -121,10 +121,12 @@ cur_status cur_create(cur_handle** hp, size_t workspace_bytes) {
     h->host_stage_bytes = (size_t)4 << 20;
     if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->host_stage, h->host_stage_bytes) != cudaSuccess ||
-        cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
         if (h->ws) cudaFree(h->ws);
         if (h->status) cudaFree(h->status);
         if (h->host_stage) cudaFreeHost(h->host_stage);
+        if (h->stage_ev) cudaEventDestroy(h->stage_ev);
         delete h;
         return CUR_ERR_CUDA;
     }
@@ -140,6 +142,7 @@ cur_status cur_destroy(cur_handle* h) {
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
     if (h->host_stage) cudaFreeHost(h->host_stage);
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     delete h;
     return CUR_OK;
 }

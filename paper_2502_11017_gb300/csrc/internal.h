@@ -55,6 +55,7 @@ struct cur_handle {
     int* status = nullptr;       // device status word (first error wins)
     char* host_stage = nullptr;  // pinned host buffer for small transfers
     size_t host_stage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;  // recorded after the last copy that reads host_stage
     Arena arena() const {
         Arena a;
         a.base = ws;

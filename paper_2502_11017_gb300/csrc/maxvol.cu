@@ -1170,7 +1170,9 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     const size_t tab_bytes = sizeof(int32_t) * (2 * (size_t)slots + P);
     const size_t need = sizeof(MvProb) * P + tab_bytes + sizeof(int32_t) * P + 64;
     if (need > h->host_stage_bytes) return CUR_ERR_NOMEM;
-    CUR_CK(cudaStreamSynchronize(st));  // the staging buffer may still feed an earlier copy
+    // the staging buffer may still feed the previous stage's table copy: wait for that
+    // copy only, not for the kernels queued since
+    CUR_CK(cudaEventSynchronize(h->stage_ev));
     char* hs = h->host_stage;
     std::memcpy(hs, sg.probs.data(), sizeof(MvProb) * P);
     int32_t* ht = reinterpret_cast<int32_t*>(hs + sizeof(MvProb) * P);
@@ -1185,6 +1187,7 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     CUR_CK(cudaMemcpyAsync(sg.dprob, hs, sizeof(MvProb) * P, cudaMemcpyHostToDevice, st));
     CUR_CK(cudaMemcpyAsync(sg.dtab, ht, tab_bytes, cudaMemcpyHostToDevice, st));
     CUR_CK(cudaMemcpyAsync(sg.done, hdone, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
+    CUR_CK(cudaEventRecord(h->stage_ev, st));
     CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
     CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
 
