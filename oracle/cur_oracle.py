@@ -27,6 +27,9 @@ Algorithm", arXiv 2502.11017):
 * ``aca_full``: Algorithm 1 (adaptive cross approximation with full pivoting),
   Section 1.3: r steps of {global argmax |R_k(i,j)|, rank-1 elimination of the
   pivot's row and column}; the paper's sequential baseline.
+* ``sketch`` / ``mlp_*`` / ``propose`` / ``cross_from``: the learned proposal's parts
+  (sketch features, a 2-layer scoring network with its cross-entropy gradients, top-r
+  proposal, maxvol refinement of a proposed cross).
 * ``bruteforce_*``: exhaustive maximal-volume search for tiny inputs.
 
 Readings where the paper is silent or ambiguous (Algorithm 3 uses squared norms;
@@ -452,6 +455,80 @@ def cross_batched(mats, ranks, blocks, delta: float = 1e-2):
     """The cross of every matrix of a batch, one after another: mats[t] with rank
     ranks[t] and (b_r, b_c) = blocks[t]. Returns a list of (I, J, info)."""
     return [cross(A, r, br, bc, delta) for A, r, (br, bc) in zip(mats, ranks, blocks)]
+
+
+# --------------------------------------------------------------------------
+# Learned proposal: sketch features and a 2-layer scoring network
+# --------------------------------------------------------------------------
+
+def sketch(A, S, T):
+    """Row features A S (m x k) and column features (T^T A)^T (n x k) for Gaussian test
+    matrices S (n x k) and T (m x k)."""
+    A = np.asarray(A, dtype=np.float64)
+    return A @ np.asarray(S, np.float64), (np.asarray(T, np.float64).T @ A).T
+
+
+def proposal_features(Y):
+    """Features of the rows of a sketch: each row divided by the largest row norm."""
+    Y = np.asarray(Y, dtype=np.float64)
+    mx = np.sqrt((Y * Y).sum(axis=1)).max()
+    return Y / mx if mx > 0 else Y
+
+
+def mlp_forward(X, W1, b1, w2, b2):
+    """Scores s = relu(X W1 + b1) w2 + b2 and the hidden layer H."""
+    H = np.maximum(np.asarray(X, np.float64) @ W1 + b1, 0.0)
+    return H @ w2 + b2, H
+
+
+def mlp_loss_grad(X, y, W1, b1, w2, b2, pos_weight: float = 1.0):
+    """Mean binary cross-entropy of the scores against labels y (0/1), positives weighted
+    by pos_weight, and its gradients (loss, dW1, db1, dw2, db2)."""
+    X = np.asarray(X, np.float64)
+    y = np.asarray(y, np.float64)
+    s, H = mlp_forward(X, W1, b1, w2, b2)
+    wt = np.where(y > 0.5, pos_weight, 1.0)
+    N = X.shape[0]
+    # log(1 + e^-s) for y = 1, log(1 + e^s) for y = 0, in a stable form
+    loss = float((wt * (np.logaddexp(0.0, -s) * y + np.logaddexp(0.0, s) * (1.0 - y))).sum() / N)
+    ds = wt * (1.0 / (1.0 + np.exp(-s)) - y) / N
+    dw2 = H.T @ ds
+    db2 = float(ds.sum())
+    dH = np.outer(ds, w2) * (H > 0.0)
+    dW1 = X.T @ dH
+    db1 = dH.sum(axis=0)
+    return loss, dW1, db1, dw2, db2
+
+
+def propose(scores, r: int):
+    """The r highest scores (ties: the lowest index), in decreasing score."""
+    order = np.lexsort((np.arange(len(scores)), -np.asarray(scores, np.float64)))
+    return [int(i) for i in order[:r]]
+
+
+def cross_from(A, r: int, I0, J0, delta: float = 1e-2, max_sweeps: int = 8):
+    """Maxvol refinement of a proposed cross (I0, J0): sweeps of global maxvol on the rows
+    of A(:,J), then on the columns of A(I,:), until a sweep makes no swap. Returns
+    (I, J, info); status SINGULAR when A(I0,J0) is singular (the caller falls back)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    I, J = list(I0), list(J0)
+    lu, _p, sing = lu_factor(A64[np.ix_(I, J)])
+    if sing:
+        return I, J, dict(status=ERR_SINGULAR, sweeps=0, sweep_swaps=[], logvol=-math.inf)
+    sweeps, sweep_swaps, status = 0, [], OK
+    while sweeps < max_sweeps:
+        sweeps += 1
+        I, _lv, s1, st1 = maxvol(A64[:, J], I, delta)
+        J, lv, s2, st2 = maxvol(A64[I, :].T, J, delta)
+        sweep_swaps.append(s1 + s2)
+        if st1 != OK or st2 != OK:
+            status = st1 if st1 != OK else st2
+            break
+        if s1 + s2 == 0:
+            break
+    info = dict(status=status, sweeps=sweeps, sweep_swaps=sweep_swaps,
+                logvol=logvol(A64[np.ix_(I, J)]))
+    return I, J, info
 
 
 # --------------------------------------------------------------------------

@@ -498,3 +498,54 @@ def test_cross_batched_is_the_cross_of_each_matrix():
     for a, (m, n, r, br, bc), (I, J, info) in zip(mats, shapes, out):
         I2, J2, info2 = orc.cross(a, r, br, bc)
         assert I == I2 and J == J2 and info["logvol"] == info2["logvol"]
+
+
+# ---------------------------------------------------------------- learned proposal parts
+
+def _mlp_params(rng, k=5, hdim=7):
+    return (rng.standard_normal((k, hdim)) * 0.5, rng.standard_normal(hdim) * 0.1,
+            rng.standard_normal(hdim) * 0.5, 0.3)
+
+
+def test_mlp_gradients_match_finite_differences():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((9, 5))
+    y = (rng.random(9) < 0.4).astype(float)
+    W1, b1, w2, b2 = _mlp_params(rng)
+    loss, dW1, db1, dw2, db2 = orc.mlp_loss_grad(X, y, W1, b1, w2, b2, pos_weight=3.0)
+    f = lambda W1_, b1_, w2_, b2_: orc.mlp_loss_grad(X, y, W1_, b1_, w2_, b2_, pos_weight=3.0)[0]
+    h = 1e-6
+    for (i, j) in [(0, 0), (2, 5), (4, 6)]:
+        E = np.zeros_like(W1); E[i, j] = h
+        assert (f(W1 + E, b1, w2, b2) - f(W1 - E, b1, w2, b2)) / (2 * h) == pytest.approx(dW1[i, j], rel=1e-5, abs=1e-9)
+    for j in (0, 3):
+        e = np.zeros_like(b1); e[j] = h
+        assert (f(W1, b1 + e, w2, b2) - f(W1, b1 - e, w2, b2)) / (2 * h) == pytest.approx(db1[j], rel=1e-5, abs=1e-9)
+        e = np.zeros_like(w2); e[j] = h
+        assert (f(W1, b1, w2 + e, b2) - f(W1, b1, w2 - e, b2)) / (2 * h) == pytest.approx(dw2[j], rel=1e-5, abs=1e-9)
+    assert (f(W1, b1, w2, b2 + h) - f(W1, b1, w2, b2 - h)) / (2 * h) == pytest.approx(db2, rel=1e-5)
+
+
+def test_mlp_loss_closed_form_and_sketch_of_rank_one():
+    # zero weights: every score is b2, the loss is log(1 + e^-b2) on positives, log(1 + e^b2) else
+    X = np.ones((4, 3))
+    y = np.array([1.0, 0.0, 0.0, 1.0])
+    z = np.zeros((3, 2))
+    loss = orc.mlp_loss_grad(X, y, z, np.zeros(2), np.zeros(2), 0.7)[0]
+    assert loss == pytest.approx((2 * math.log1p(math.exp(-0.7)) + 2 * math.log1p(math.exp(0.7))) / 4)
+    rng = np.random.default_rng(1)
+    u, v = rng.standard_normal(6), rng.standard_normal(5)
+    S, T = rng.standard_normal((5, 3)), rng.standard_normal((6, 3))
+    Y, Z = orc.sketch(np.outer(u, v), S, T)
+    np.testing.assert_allclose(Y, np.outer(u, v @ S), rtol=1e-12)
+    np.testing.assert_allclose(Z, np.outer(v, u @ T), rtol=1e-12)
+
+
+def test_propose_and_cross_from():
+    assert orc.propose([0.5, 2.0, 2.0, -1.0, 3.0], 3) == [4, 1, 2]
+    a = wl.gaussian_kernel(300, 120, 0.25, seed=3, dtype=np.float64)
+    I, J, info = orc.cross(a, 6, 2, 1)
+    I2, J2, info2 = orc.cross_from(a, 6, I, J)       # a converged cross stays put
+    assert sorted(I2) == sorted(I) and sorted(J2) == sorted(J) and info2["sweep_swaps"] == [0]
+    _, _, bad = orc.cross_from(a, 6, [0] * 6, list(range(6)))
+    assert bad["status"] == orc.ERR_SINGULAR
