@@ -219,6 +219,63 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
                      const cur_opts* opts, int32_t* I_out, int32_t* J_out,
                      cur_cross_info* info_out, cudaStream_t stream);
 
+/* ---- Learned proposal (where the maxvol sweeps of Algorithm 2 start)
+ *
+ * A scoring network ranks the rows and the columns of A from a Gaussian sketch; the
+ * r best-ranked of each are a proposed cross (I0, J0), which cur_cross_from refines by
+ * the sweeps of global maxvol that end the cross (Section 3). Nothing here changes what
+ * a converged cross is; the proposal only sets where the sweeps begin. */
+
+/* Sketch features: Y = A S (m x k) and Zt = A^T T (n x k), row-major FP32, device, for
+ * S (n x k) and T (m x k) row-major FP32 on the device (the caller draws them, e.g.
+ * i.i.d. N(0, 1/k)). With normalize != 0, Y is divided by its largest row norm and Zt by
+ * its own (unchanged if that is 0). A: any supported dtype (read as FP32). k must be 32;
+ * S, T, Y, Zt 16-byte aligned; else CUR_ERR_ARG. FP32 accumulation, deterministic
+ * (fixed summation order). Asynchronous. */
+cur_status cur_sketch(cur_handle* h, const cur_mat* A, const float* S, const float* T, int32_t k,
+                      float* Y, float* Zt, int32_t normalize, cudaStream_t stream);
+
+/* The scoring network's parameters are one FP32 array of k*H + 2*H + 1 values: W1 (k x H,
+ * row-major), b1 (H), w2 (H), b2. score(x) = relu(x W1 + b1) . w2 + b2 for a feature row
+ * x (k values). k must be 32 and H a multiple of 32 in [32, 256]; X 16-byte aligned. */
+
+/* scores[s] = score(X[s]) for the N rows of X (N x k, device). Asynchronous. */
+cur_status cur_mlp_forward(cur_handle* h, const float* X, int64_t N, int32_t k, int32_t H,
+                           const float* params, float* scores, cudaStream_t stream);
+
+/* Gradient of the weighted mean binary cross-entropy
+ *   L = (1/N) sum_s w_s [ y_s log(1 + e^-score_s) + (1 - y_s) log(1 + e^score_s) ],
+ * w_s = pos_weight for y_s = 1 and 1 for y_s = 0, over the samples s = idx[0..N) (rows of
+ * X and entries of y; idx NULL: 0..N-1). grads: same layout as params (device); loss: one
+ * double (device, may be NULL). Deterministic. Asynchronous. */
+cur_status cur_mlp_grad(cur_handle* h, const float* X, const float* y, const int64_t* idx, int64_t N,
+                        int32_t k, int32_t H, const float* params, float pos_weight, float* grads,
+                        double* loss, cudaStream_t stream);
+
+/* One Adam step (Kingma and Ba, 2015) at step t >= 1 on count parameters, in place:
+ * m1 = b1 m1 + (1 - b1) g, m2 = b2 m2 + (1 - b2) g^2,
+ * params -= lr (m1 / (1 - b1^t)) / (sqrt(m2 / (1 - b2^t)) + eps). Asynchronous. */
+cur_status cur_adam_step(cur_handle* h, float* params, const float* grads, float* m1, float* m2,
+                         int64_t count, int32_t t, float lr, float beta1, float beta2, float eps,
+                         cudaStream_t stream);
+
+/* idx_out (r int32, device) = the indices of the r largest scores (N of them, device), in
+ * decreasing score, equal scores by increasing index, NaN below every number.
+ * 1 <= r <= N < 2^31. Asynchronous. */
+cur_status cur_propose(cur_handle* h, const float* scores, int64_t N, int32_t r, int32_t* idx_out,
+                       cudaStream_t stream);
+
+/* Refinement of a proposed cross (I0, J0) (r int32 each, device): sweeps of global maxvol
+ * on A(:,J) from I, then on A(I,:)^T from J, until a sweep makes no swap (at most 8), as
+ * the sweeps that end cur_cross. If A(I0,J0) is singular nothing is refined: I = I0,
+ * J = J0, info logvol = -inf, and CUR_ERR_SINGULAR is recorded (the caller falls back to
+ * cur_cross). A sweep stage that ends SINGULAR or NOCONV records that status. info_out:
+ * one cur_cross_info (device, may be NULL; aca_selected = 0, status = the end status).
+ * 1 <= r <= 128, r < min(m, n). Synchronises the stream. */
+cur_status cur_cross_from(cur_handle* h, const cur_mat* A, int32_t r, const int32_t* I0,
+                          const int32_t* J0, const cur_opts* opts, int32_t* I_out, int32_t* J_out,
+                          cur_cross_info* info_out, cudaStream_t stream);
+
 /* Synchronise `stream` and return (and clear) the first device-side status. */
 cur_status cur_sync_status(cur_handle* h, cudaStream_t stream);
 

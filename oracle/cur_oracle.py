@@ -500,6 +500,16 @@ def mlp_loss_grad(X, y, W1, b1, w2, b2, pos_weight: float = 1.0):
     return loss, dW1, db1, dw2, db2
 
 
+def adam_step(p, g, m1, m2, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam step (Kingma and Ba, 2015): returns the new (p, m1, m2)."""
+    m1 = beta1 * np.asarray(m1, np.float64) + (1 - beta1) * np.asarray(g, np.float64)
+    m2 = beta2 * np.asarray(m2, np.float64) + (1 - beta2) * np.asarray(g, np.float64) ** 2
+    mh = m1 / (1 - beta1 ** t)
+    vh = m2 / (1 - beta2 ** t)
+    return np.asarray(p, np.float64) - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
 def propose(scores, r: int):
     """The r highest scores (ties: the lowest index), in decreasing score."""
     order = np.lexsort((np.arange(len(scores)), -np.asarray(scores, np.float64)))

@@ -24,7 +24,9 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", 
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
-           "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout"]
+           "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout",
+           "cur_sketch", "cur_mlp_forward", "cur_mlp_grad", "cur_adam_step", "cur_propose",
+           "cur_cross_from"]
 
 
 class CurMat(ctypes.Structure):
@@ -90,6 +92,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_selftest_wait_timeout": ([P, P], ctypes.c_int),
         "cur_prof_read": ([P, P, ctypes.POINTER(D), ctypes.POINTER(I32),
                            ctypes.POINTER(I64)], ctypes.c_int),
+        "cur_sketch": ([P, pmat, P, P, I32, P, P, I32, P], ctypes.c_int),
+        "cur_mlp_forward": ([P, P, I64, I32, I32, P, P, P], ctypes.c_int),
+        "cur_mlp_grad": ([P, P, P, P, I64, I32, I32, P, ctypes.c_float, P, P, P], ctypes.c_int),
+        "cur_adam_step": ([P, P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, P], ctypes.c_int),
+        "cur_propose": ([P, P, I64, I32, P, P], ctypes.c_int),
+        "cur_cross_from": ([P, pmat, I32, P, P, popts, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -310,3 +319,47 @@ def cross(A, r: int, b_r: int, b_c: int, delta: float = 1e-2, handle: Handle | N
     finally:
         if own:
             hd.close()
+
+
+# ------------------------------------------------------------------ learned proposal
+
+def mlp_param_count(k: int = 32, H: int = 256) -> int:
+    """Length of the scoring network's parameter array: W1 (k x H), b1, w2, b2."""
+    return k * H + 2 * H + 1
+
+
+def cur_sketch(h, A, S, T, Y_out, Zt_out, normalize: bool = True, stream=None) -> int:
+    """Y = A S (m x k) and Zt = A^T T (n x k); S: n x k, T: m x k, FP32 CUDA tensors."""
+    return _check(load().cur_sketch(h, ctypes.byref(mat(A)), _ptr(S), _ptr(T), S.shape[1], _ptr(Y_out),
+                                    _ptr(Zt_out), 1 if normalize else 0, _stream(stream)), "cur_sketch")
+
+
+def cur_mlp_forward(h, X, params, scores_out, H: int = 256, stream=None) -> int:
+    return _check(load().cur_mlp_forward(h, _ptr(X), X.shape[0], X.shape[1], H, _ptr(params),
+                                         _ptr(scores_out), _stream(stream)), "cur_mlp_forward")
+
+
+def cur_mlp_grad(h, X, y, params, grads_out, loss_out=None, idx=None, N=None, pos_weight: float = 1.0,
+                 H: int = 256, stream=None) -> int:
+    """Gradient over the samples idx[0..N) (all rows of X when idx is None)."""
+    n = (X.shape[0] if idx is None else idx.shape[0]) if N is None else N
+    return _check(load().cur_mlp_grad(h, _ptr(X), _ptr(y), _ptr(idx), n, X.shape[1], H, _ptr(params),
+                                      pos_weight, _ptr(grads_out), _ptr(loss_out), _stream(stream)),
+                  "cur_mlp_grad")
+
+
+def cur_adam_step(h, params, grads, m1, m2, t: int, lr: float = 1e-3, beta1: float = 0.9,
+                  beta2: float = 0.999, eps: float = 1e-8, stream=None) -> int:
+    return _check(load().cur_adam_step(h, _ptr(params), _ptr(grads), _ptr(m1), _ptr(m2), params.numel(), t,
+                                       lr, beta1, beta2, eps, _stream(stream)), "cur_adam_step")
+
+
+def cur_propose(h, scores, r: int, idx_out, stream=None) -> int:
+    return _check(load().cur_propose(h, _ptr(scores), scores.numel(), r, _ptr(idx_out), _stream(stream)),
+                  "cur_propose")
+
+
+def cur_cross_from(h, A, r: int, I0, J0, o: CurOpts, I_out, J_out, info_out=None, stream=None) -> int:
+    return _check(load().cur_cross_from(h, ctypes.byref(mat(A)), r, _ptr(I0), _ptr(J0), ctypes.byref(o),
+                                        _ptr(I_out), _ptr(J_out), _ptr(info_out), _stream(stream)),
+                  "cur_cross_from")

@@ -100,6 +100,7 @@ size_t cur_workspace_size(int64_t m, int64_t n, int32_t r, cur_dtype dtype) {
     b += cs * R * mx;                                         // B in global memory for large r
     b += 8 * R * R * (size_t)((m + n) / R + 16) * 2;          // M^-1 per problem (two types)
     b += 8 * R * (size_t)n + 8 * 4 * (size_t)(m / 64 + 1) * 64;  // residual W and partials
+    b += sketch_workspace_size(256, m, n);                    // sketch partials (<= 256 SMs)
     return b;
 }
 

@@ -127,6 +127,10 @@ cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void
                                  cudaStream_t st);
 size_t compute_size(cur_dtype t);
 
+// ---- learned proposal (proposal.cu)
+// Workspace bytes of cur_sketch's split partials on a device with num_sms SMs.
+size_t sketch_workspace_size(int num_sms, int64_t m, int64_t n);
+
 // ---- assembly and residual (residual.cu)
 cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
                          int r, void* C_out, double* U_out, void* R_out, double* rcond_out,

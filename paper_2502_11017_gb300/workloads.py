@@ -75,6 +75,38 @@ def gaussian_kernel(m: int = 65536, n: int = 8192, h: float = 0.2,
     return out
 
 
+def gaussian_kernel_device(m: int, n: int, h: float, seed: int, device="cuda"):
+    """gaussian_kernel(m, n, h, seed) formed on `device` as an FP32 torch tensor: the same
+    points (numpy, seeded), the distances and exp in FP64 on the device, rounded once."""
+    import torch
+    rng = np.random.default_rng(seed)
+    x = torch.from_numpy(rng.random((m, 3))).to(device)
+    y = torch.from_numpy(rng.random((n, 3))).to(device)
+    d2 = ((x[:, None, :] - y[None, :, :]) ** 2).sum(dim=2)
+    return torch.exp(-d2 / (h * h)).to(torch.float32)
+
+
+# The learned proposal's training family: Gaussian-kernel matrices (points in [0,1]^3) with
+# bandwidth h ~ U[0.1, 0.4]; m x n = 4096 x 1024 and r = 16 keep the proportions r/m = 1/256
+# and r/n = 1/64 of the 16384 x 4096, r = 64 workload.
+PROPOSAL_FAMILY = dict(m=4096, n=1024, r=16, b_r=16, b_c=4, k=32, h_range=(0.1, 0.4))
+
+
+def proposal_family(count: int, seed: int = SEED_BASE + 5, h_range=(0.1, 0.4)):
+    """(matrix seed, h) for `count` members of the Gaussian-kernel family."""
+    rng = np.random.default_rng(seed)
+    hs = rng.uniform(h_range[0], h_range[1], size=count)
+    return [(seed * 1000 + t, float(hs[t])) for t in range(count)]
+
+
+def sketch_matrices(m: int, n: int, k: int = 32, seed: int = SEED_BASE + 6):
+    """Gaussian test matrices S (n x k) and T (m x k), i.i.d. N(0, 1/k), FP32."""
+    rng = np.random.default_rng(seed)
+    s = (rng.standard_normal((n, k)) / np.sqrt(k)).astype(np.float32)
+    t = (rng.standard_normal((m, k)) / np.sqrt(k)).astype(np.float32)
+    return s, t
+
+
 def bf16_factor_product(m: int = 262144, n: int = 16384, k: int = 128, noise_std: float = 1e-2,
                         seed: int = SEED_BASE + 4, device="cuda", chunk_rows: int = 16384):
     """A = X diag(sigma) Y^T + noise rounded once to BF16, as a torch tensor on `device`:

@@ -549,3 +549,16 @@ def test_propose_and_cross_from():
     assert sorted(I2) == sorted(I) and sorted(J2) == sorted(J) and info2["sweep_swaps"] == [0]
     _, _, bad = orc.cross_from(a, 6, [0] * 6, list(range(6)))
     assert bad["status"] == orc.ERR_SINGULAR
+
+
+def test_adam_first_step_moves_by_lr_and_follows_its_recurrence():
+    # step 1 from zero moments: m1/c1 = g and sqrt(m2/c2) = |g|, so each parameter moves
+    # by lr * g / (|g| + eps), i.e. by about lr against the sign of its gradient
+    g = np.array([3.0, -0.5, 1e-3, 0.0])
+    p1, m1, m2 = orc.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01)
+    np.testing.assert_allclose(p1, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    # a constant gradient keeps m1/c1 = g and m2/c2 = g^2 at every step
+    p, a, b = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 6):
+        p, a, b = orc.adam_step(p, g, a, b, t, lr=0.01)
+    np.testing.assert_allclose(p, -5 * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-10)

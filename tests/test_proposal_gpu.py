@@ -1,0 +1,207 @@
+"""Parity of the learned proposal's kernels with the FP64 oracle: sketch features, the
+scoring network's forward pass, its cross-entropy gradients and the Adam step, the top-r
+proposal (exact), and maxvol refinement from a given cross (cur_cross_from).
+
+Tolerances come from the arithmetic: an FP32 sum of products over a length-L contraction
+is within about L * 2^-24 * sum |terms| of the exact value, so each element is checked
+against 1e-5 (sketch, L <= 1000) or 1e-4 (gradients, summed over whole batches) times the
+sum of the magnitudes of its terms, evaluated in FP64 by the oracle's inputs.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2502_11017_gb300 as cur
+from paper_2502_11017_gb300 import proposal as prop
+from paper_2502_11017_gb300 import workloads as wl
+from oracle import cur_oracle as orc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cur.load()
+    h = cur.Handle(4096, 2048, 32, cur.CUR_F32)
+    yield h
+    h.close()
+
+
+DEV = "cuda:0"
+
+
+def _sketch(hd, A_t, S, T, normalize):
+    m, n = A_t.shape
+    Y = torch.empty((m, 32), dtype=torch.float32, device=DEV)
+    Z = torch.empty((n, 32), dtype=torch.float32, device=DEV)
+    cur.cur_sketch(hd.h, A_t, torch.from_numpy(S).to(DEV), torch.from_numpy(T).to(DEV), Y, Z, normalize)
+    assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    return Y.cpu().numpy().astype(np.float64), Z.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("m,n,dtype,pad", [(1000, 700, torch.float32, 0), (515, 2049, torch.float32, 3),
+                                           (300, 260, torch.bfloat16, 0), (257, 129, torch.float64, 1),
+                                           (33, 5, torch.float32, 0)])
+def test_sketch_matches_oracle(hd, m, n, dtype, pad):
+    a = wl.gaussian_kernel(m, n, 0.3, seed=m + n)
+    S, T = wl.sketch_matrices(m, n, 32, seed=7)
+    buf = torch.zeros((m, n + pad), dtype=dtype, device=DEV)   # pad: a leading dimension off 4
+    A_t = buf[:, :n]
+    A_t.copy_(torch.from_numpy(a).to(DEV).to(dtype))
+    a_used = A_t.float().cpu().numpy().astype(np.float64)       # the values the kernel reads
+    Y, Z = _sketch(hd, A_t, S, T, False)
+    Yo, Zo = orc.sketch(a_used, S, T)
+    np.testing.assert_array_less(np.abs(Y - Yo), 1e-5 * (np.abs(a_used) @ np.abs(S)) + 1e-30)
+    np.testing.assert_array_less(np.abs(Z - Zo), 1e-5 * (np.abs(a_used).T @ np.abs(T)) + 1e-30)
+    Yn, Zn = _sketch(hd, A_t, S, T, True)
+    np.testing.assert_allclose(Yn, orc.proposal_features(Yo), atol=2e-5)
+    np.testing.assert_allclose(Zn, orc.proposal_features(Zo), atol=2e-5)
+
+
+def _params(seed, H=256):
+    return prop.init_params(seed, 32, H) + np.random.default_rng(seed + 1).normal(
+        0, 0.05, cur.mlp_param_count(32, H)).astype(np.float32)
+
+
+def _split(p, H=256):
+    p = p.astype(np.float64)
+    k = 32
+    return p[:k * H].reshape(k, H), p[k * H:k * H + H], p[k * H + H:k * H + 2 * H], p[-1]
+
+
+@pytest.mark.parametrize("N,H", [(1000, 256), (33, 64), (4096, 128)])
+def test_mlp_forward_matches_oracle(hd, N, H):
+    rng = np.random.default_rng(N)
+    X = rng.standard_normal((N, 32)).astype(np.float32) * 0.3
+    p = _params(N, H)
+    s = torch.empty(N, dtype=torch.float32, device=DEV)
+    cur.cur_mlp_forward(hd.h, torch.from_numpy(X).to(DEV), torch.from_numpy(p).to(DEV), s, H=H)
+    W1, b1, w2, b2 = _split(p, H)
+    so, Ho = orc.mlp_forward(X, W1, b1, w2, b2)
+    bound = (np.maximum(np.abs(X.astype(np.float64)) @ np.abs(W1) + np.abs(b1), 0) @ np.abs(w2)) + abs(b2)
+    np.testing.assert_array_less(np.abs(s.cpu().numpy() - so), 1e-5 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("N,sub,pw", [(3000, None, 1.0), (5000, 1777, 40.0)])
+def test_mlp_gradients_match_oracle(hd, N, sub, pw):
+    rng = np.random.default_rng(N)
+    X = (rng.standard_normal((N, 32)) * 0.3).astype(np.float32)
+    y = (rng.random(N) < 0.1).astype(np.float32)
+    p = _params(N + 1)
+    idx = None if sub is None else rng.permutation(N)[:sub].astype(np.int64)
+    g = torch.empty(p.size, dtype=torch.float32, device=DEV)
+    loss = torch.zeros(1, dtype=torch.float64, device=DEV)
+    cur.cur_mlp_grad(hd.h, torch.from_numpy(X).to(DEV), torch.from_numpy(y).to(DEV), torch.from_numpy(p).to(DEV),
+                     g, loss, idx=None if idx is None else torch.from_numpy(idx).to(DEV), pos_weight=pw)
+    assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    Xs, ys = (X, y) if idx is None else (X[idx], y[idx])
+    W1, b1, w2, b2 = _split(p)
+    lo, dW1, db1, dw2, db2 = orc.mlp_loss_grad(Xs, ys, W1, b1, w2, b2, pos_weight=pw)
+    gg = g.cpu().numpy().astype(np.float64)
+    go = np.concatenate([dW1.ravel(), db1, dw2, [db2]])
+    # each gradient entry sums |ds| * |x| * |w| terms bounded by the per-sample weight / N
+    scale = np.abs(go).max()
+    np.testing.assert_allclose(gg, go, rtol=1e-3, atol=1e-4 * scale)
+    assert loss.item() == pytest.approx(lo, rel=1e-5)
+
+
+def test_adam_matches_oracle(hd):
+    rng = np.random.default_rng(3)
+    P = 8449
+    p = rng.standard_normal(P).astype(np.float32)
+    gs = [rng.standard_normal(P).astype(np.float32) for _ in range(3)]
+    pt = torch.from_numpy(p).to(DEV)
+    m1 = torch.zeros(P, device=DEV)
+    m2 = torch.zeros(P, device=DEV)
+    po, a, b = p.astype(np.float64), np.zeros(P), np.zeros(P)
+    for t, g in enumerate(gs, start=1):
+        cur.cur_adam_step(hd.h, pt, torch.from_numpy(g).to(DEV), m1, m2, t, lr=1e-2)
+        po, a, b = orc.adam_step(po, g, a, b, t, lr=1e-2)
+    np.testing.assert_allclose(pt.cpu().numpy(), po, rtol=1e-5, atol=1e-6)
+
+
+def test_propose_is_exact(hd):
+    rng = np.random.default_rng(5)
+    for N, r in [(16384, 64), (1000, 1), (50, 50), (3001, 17)]:
+        s = rng.standard_normal(N).astype(np.float32)
+        s[rng.integers(0, N, N // 4)] = 0.5                     # ties: the lower index first
+        s[rng.integers(0, N, 3)] = np.nan                       # NaN ranks last
+        if N > 10:
+            s[7], s[9] = -0.0, 0.0                               # -0 ranks as +0
+        idx = torch.empty(r, dtype=torch.int32, device=DEV)
+        cur.cur_propose(hd.h, torch.from_numpy(s).to(DEV), r, idx)
+        assert idx.tolist() == orc.propose(np.where(s == 0, 0.0, s), r)
+
+
+def _cross_from(hd, A_t, r, I0, J0):
+    I = torch.empty(r, dtype=torch.int32, device=DEV)
+    J = torch.empty(r, dtype=torch.int32, device=DEV)
+    info = torch.zeros(ctypes.sizeof(cur.CurCrossInfo), dtype=torch.uint8, device=DEV)
+    cur.cur_cross_from(hd.h, A_t, r, torch.tensor(I0, dtype=torch.int32, device=DEV),
+                       torch.tensor(J0, dtype=torch.int32, device=DEV), cur.opts(1e-2), I, J, info)
+    st = cur.cur_sync_status(hd.h)
+    return I.tolist(), J.tolist(), cur.info_from_tensor(info), st
+
+
+@pytest.mark.parametrize("m,n,r,seed", [(1200, 500, 12, 1), (2049, 777, 24, 2)])
+def test_cross_from_matches_oracle(hd, m, n, r, seed):
+    a = wl.gaussian_kernel(m, n, 0.3, seed=seed)
+    A_t = torch.from_numpy(a).to(DEV)
+    rng = np.random.default_rng(seed)
+    I0 = rng.choice(m, r, replace=False).tolist()
+    J0 = rng.choice(n, r, replace=False).tolist()
+    I, J, inf, st = _cross_from(hd, A_t, r, I0, J0)
+    Io, Jo, info_o = orc.cross_from(a, r, I0, J0)
+    assert st == cur.CUR_OK and inf.status == cur.CUR_OK and info_o["status"] == orc.OK
+    lv = orc.logvol(a[np.ix_(I, J)].astype(np.float64))
+    assert inf.logvol == pytest.approx(lv, abs=1e-6 * max(1.0, abs(lv)))
+    if not (sorted(I) == sorted(Io) and sorted(J) == sorted(Jo)):
+        assert lv >= info_o["logvol"] + math.log(0.999)
+    dr, dc = orc.dominance(a, I, J)
+    assert dr <= 1.01 * (1 + 1e-4) and dc <= 1.01 * (1 + 1e-4)
+    assert inf.sweep_swaps[inf.sweeps - 1] == 0
+    # a converged cross stays where it is
+    I2, J2, inf2, _ = _cross_from(hd, A_t, r, I, J)
+    assert sorted(I2) == sorted(I) and sorted(J2) == sorted(J) and inf2.swaps_total == 0
+
+
+def test_cross_from_singular_proposal_is_reported(hd):
+    a = wl.gaussian_kernel(600, 300, 0.3, seed=9)
+    A_t = torch.from_numpy(a).to(DEV)
+    I0 = [5] * 2 + list(range(10, 18))                      # a repeated row: det A(I0, J0) = 0
+    J0 = list(range(10))
+    I, J, inf, st = _cross_from(hd, A_t, 10, I0, J0)
+    assert st == cur.CUR_ERR_SINGULAR and inf.status == cur.CUR_ERR_SINGULAR
+    assert I == I0 and J == J0 and inf.logvol == -math.inf and inf.swaps_total == 0
+
+
+def test_training_lowers_the_loss_and_proposal_runs(hd):
+    lab = np.load(prop_labels_path())
+    F = wl.PROPOSAL_FAMILY
+    items = list(zip(lab["seed"][:8].tolist(), lab["h"][:8].tolist()))
+    Xr, Xc = prop.family_features(hd, items, DEV)
+    yr, yc = prop.labels(lab["I"][:8], lab["J"][:8])
+    net = prop.Net(1, DEV)
+    hist = prop.train(hd, net, Xr, torch.from_numpy(yr).to(DEV), (F["m"] - F["r"]) / F["r"], 4, 4096, 2e-3, 0)
+    assert hist[-1] < hist[0]
+    cols = prop.Net(2, DEV)
+    prop.train(hd, cols, Xc, torch.from_numpy(yc).to(DEV), (F["n"] - F["r"]) / F["r"], 2, 4096, 2e-3, 0)
+    seed, h = int(lab["seed"][-1]), float(lab["h"][-1])
+    A = wl.gaussian_kernel_device(F["m"], F["n"], h, seed, DEV)
+    s, t = wl.sketch_matrices(F["m"], F["n"], 32, seed=seed + 1)
+    I, J, inf, fb = prop.propose_cross(hd, A, F["r"], net, cols, torch.from_numpy(s).to(DEV),
+                                       torch.from_numpy(t).to(DEV), F["b_r"], F["b_c"])
+    a = A.cpu().numpy()
+    dr, dc = orc.dominance(a, I.tolist(), J.tolist())
+    assert inf.status == cur.CUR_OK and dr <= 1.01 * (1 + 1e-4) and dc <= 1.01 * (1 + 1e-4)
+
+
+def prop_labels_path():
+    import os
+    return os.path.join(os.path.dirname(__file__), "golden", "proposal_labels_4096x1024_r16.npz")
