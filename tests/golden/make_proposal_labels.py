@@ -11,7 +11,10 @@ import multiprocessing as mp
 import os
 import sys
 
-import numpy as np
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")          # one BLAS thread per worker process
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
@@ -36,8 +39,12 @@ def main():
     ap.add_argument("--procs", type=int, default=os.cpu_count())
     args = ap.parse_args()
     fam = wl.proposal_family(args.count, h_range=F["h_range"])
+    res = []
     with mp.get_context("spawn").Pool(args.procs) as pool:
-        res = pool.map(one, fam, chunksize=4)
+        for r in pool.imap(one, fam, chunksize=4):
+            res.append(r)
+            if len(res) % 256 == 0:
+                print(f"{len(res)} / {len(fam)}", flush=True)
     np.savez_compressed(
         OUT, seed=np.array([s for s, _ in fam], np.int64), h=np.array([h for _, h in fam]),
         I=np.array([r[0] for r in res], np.int32), J=np.array([r[1] for r in res], np.int32),
