@@ -19,8 +19,8 @@ import numpy as np
 
 from . import workloads as wl
 from . import (CUR_ERR_SINGULAR, CUR_F32, CurCrossInfo, Handle, cur_adam_step, cur_cross, cur_cross_from,
-               cur_mlp_forward, cur_mlp_grad, cur_propose, cur_sketch, cur_sync_status, info_from_tensor,
-               mlp_param_count, opts)
+               cur_maxvol_cols, cur_maxvol_rows, cur_mlp_forward, cur_mlp_grad, cur_propose, cur_sketch,
+               cur_sync_status, info_from_tensor, opts)
 
 K, H = 32, 256
 
@@ -110,9 +110,22 @@ def scores(hd, net: Net, X):
     return out
 
 
+def _refine(hd, A, r: int, I0, J0, delta: float):
+    dev = A.device
+    import torch
+    I = torch.empty(r, dtype=torch.int32, device=dev)
+    J = torch.empty(r, dtype=torch.int32, device=dev)
+    info = torch.zeros(ctypes.sizeof(CurCrossInfo), dtype=torch.uint8, device=dev)
+    cur_cross_from(hd.h, A, r, I0, J0, opts(delta), I, J, info)
+    inf = info_from_tensor(info)
+    cur_sync_status(hd.h)          # clears a SINGULAR / NOCONV mark; info carries it
+    return I, J, inf
+
+
 def propose_cross(hd, A, r: int, rows: Net, cols: Net, S, T, b_r: int, b_c: int, delta: float = 1e-2):
-    """The learned cross of A: proposal, refinement, and cur_cross when the proposal is
-    singular. Returns (I, J, info, fell_back)."""
+    """The learned cross of A: the r best-scored rows and columns, refined by maxvol sweeps;
+    the plain cross when the proposal (or its refinement) is singular. Returns
+    (I, J, info, fell_back)."""
     import torch
     dev = A.device
     Y, Zt = features(hd, A, S, T)
@@ -120,16 +133,30 @@ def propose_cross(hd, A, r: int, rows: Net, cols: Net, S, T, b_r: int, b_c: int,
     J0 = torch.empty(r, dtype=torch.int32, device=dev)
     cur_propose(hd.h, scores(hd, rows, Y), r, I0)
     cur_propose(hd.h, scores(hd, cols, Zt), r, J0)
-    I = torch.empty(r, dtype=torch.int32, device=dev)
-    J = torch.empty(r, dtype=torch.int32, device=dev)
-    info = torch.zeros(ctypes.sizeof(CurCrossInfo), dtype=torch.uint8, device=dev)
-    cur_cross_from(hd.h, A, r, I0, J0, opts(delta), I, J, info)
-    inf = info_from_tensor(info)
-    cur_sync_status(hd.h)          # clears a SINGULAR / NOCONV mark; info carries it
-    if inf.status == CUR_ERR_SINGULAR and inf.swaps_total == 0:
-        cur_cross(hd.h, A, r, b_r, b_c, opts(delta), I, J, info)
-        cur_sync_status(hd.h)
-        return I, J, info_from_tensor(info), True
+    I, J, inf = _refine(hd, A, r, I0, J0, delta)
+    if inf.status == CUR_ERR_SINGULAR:
+        I, J, inf = plain_cross(hd, A, r, b_r, b_c, delta)
+        return I, J, inf, True
+    return I, J, inf, False
+
+
+def propose_columns_cross(hd, A, r: int, cols: Net, S, T, b_r: int, b_c: int, delta: float = 1e-2):
+    """The cross with the learned columns in place of Algorithm 3's J0: blockwise maxvol rows
+    on A(:,J0), blockwise columns on A(I,:), then the sweeps. Returns (I, J, info, fell_back)."""
+    import torch
+    dev = A.device
+    Y, Zt = features(hd, A, S, T)
+    J0 = torch.empty(r, dtype=torch.int32, device=dev)
+    cur_propose(hd.h, scores(hd, cols, Zt), r, J0)
+    I1 = torch.empty(r, dtype=torch.int32, device=dev)
+    J1 = torch.empty(r, dtype=torch.int32, device=dev)
+    cur_maxvol_rows(hd.h, A, J0, r, opts(delta, nblocks=b_r), I1)
+    cur_maxvol_cols(hd.h, A, I1, r, opts(delta, nblocks=b_c), J1)
+    cur_sync_status(hd.h)
+    I, J, inf = _refine(hd, A, r, I1, J1, delta)
+    if inf.status == CUR_ERR_SINGULAR:
+        I, J, inf = plain_cross(hd, A, r, b_r, b_c, delta)
+        return I, J, inf, True
     return I, J, inf, False
 
 
@@ -152,12 +179,7 @@ def random_cross(hd, A, r: int, seed: int, delta: float = 1e-2):
     rng = np.random.default_rng(seed)
     I0 = torch.from_numpy(rng.choice(m, r, replace=False).astype(np.int32)).to(dev)
     J0 = torch.from_numpy(rng.choice(n, r, replace=False).astype(np.int32)).to(dev)
-    I = torch.empty(r, dtype=torch.int32, device=dev)
-    J = torch.empty(r, dtype=torch.int32, device=dev)
-    info = torch.zeros(ctypes.sizeof(CurCrossInfo), dtype=torch.uint8, device=dev)
-    cur_cross_from(hd.h, A, r, I0, J0, opts(delta), I, J, info)
-    cur_sync_status(hd.h)
-    return I, J, info_from_tensor(info)
+    return _refine(hd, A, r, I0, J0, delta)
 
 
 def _timed(fn):
@@ -170,9 +192,10 @@ def _timed(fn):
 
 
 def evaluate(hd, rows: Net, cols: Net, items, m: int, n: int, r: int, b_r: int, b_c: int, device,
-             oracle_logvol=None):
-    """Per matrix: the plain cross, the learned one and a random start, with swaps,
-    log-volumes and wall times."""
+             oracle=None):
+    """Per matrix: the plain cross, the learned cross, the learned-columns cross and a
+    refinement from a random start, with swaps, log-volumes and wall times. oracle: the
+    oracle's (I, J, logvol) per matrix, when known."""
     import torch
     out = []
     for t, (seed, h) in enumerate(items):
@@ -180,15 +203,19 @@ def evaluate(hd, rows: Net, cols: Net, items, m: int, n: int, r: int, b_r: int, 
         s, tt = wl.sketch_matrices(m, n, K, seed=seed + 1)
         S, T = torch.from_numpy(s).to(device), torch.from_numpy(tt).to(device)
         plain_cross(hd, A, r, b_r, b_c)                      # warm
-        (_, _, ip), tp = _timed(lambda: plain_cross(hd, A, r, b_r, b_c))
+        (Ip, Jp, ip), tp = _timed(lambda: plain_cross(hd, A, r, b_r, b_c))
         (_, _, il, fb), tl = _timed(lambda: propose_cross(hd, A, r, rows, cols, S, T, b_r, b_c))
+        (_, _, ic, fc), tc = _timed(lambda: propose_columns_cross(hd, A, r, cols, S, T, b_r, b_c))
         (_, _, ir), tr = _timed(lambda: random_cross(hd, A, r, seed + 2))
         row = dict(seed=seed, h=h, plain_logvol=ip.logvol, plain_swaps=ip.swaps_total, plain_ms=tp,
-                   learned_logvol=il.logvol, learned_swaps=il.swaps_total, learned_sweeps=il.sweeps,
-                   learned_fallback=fb, learned_ms=tl, random_logvol=ir.logvol, random_swaps=ir.swaps_total,
-                   random_ms=tr)
-        if oracle_logvol is not None:
-            row["oracle_logvol"] = float(oracle_logvol[t])
+                   learned_logvol=il.logvol, learned_swaps=il.swaps_total, learned_fallback=fb, learned_ms=tl,
+                   learned_cols_logvol=ic.logvol, learned_cols_swaps=ic.swaps_total, learned_cols_fallback=fc,
+                   learned_cols_ms=tc, random_logvol=ir.logvol, random_swaps=ir.swaps_total,
+                   random_singular=ir.status == CUR_ERR_SINGULAR, random_ms=tr)
+        if oracle is not None:
+            Io, Jo, lvo = oracle[t]
+            row["oracle_logvol"] = float(lvo)
+            row["plain_is_oracle"] = (sorted(Ip.tolist()) == sorted(Io)) and (sorted(Jp.tolist()) == sorted(Jo))
         out.append(row)
     return out
 
@@ -229,18 +256,22 @@ def time_parts(hd, rows: Net, cols: Net, m: int, n: int, r: int, device, reps: i
 
 def summarise(rows):
     a = {k: np.array([r[k] for r in rows], dtype=float) for k in rows[0] if k not in ("seed",)}
-    s = dict(count=len(rows),
-             plain_swaps_mean=float(a["plain_swaps"].mean()), learned_swaps_mean=float(a["learned_swaps"].mean()),
-             random_swaps_mean=float(a["random_swaps"].mean()),
-             learned_vs_plain_logvol_mean=float((a["learned_logvol"] - a["plain_logvol"]).mean()),
-             learned_vs_plain_logvol_min=float((a["learned_logvol"] - a["plain_logvol"]).min()),
-             random_vs_plain_logvol_mean=float((a["random_logvol"] - a["plain_logvol"]).mean()),
-             fallbacks=int(a["learned_fallback"].sum()),
-             plain_ms_median=float(np.median(a["plain_ms"])), learned_ms_median=float(np.median(a["learned_ms"])),
-             random_ms_median=float(np.median(a["random_ms"])))
+    s = dict(count=len(rows))
+    for v in ("plain", "learned", "learned_cols", "random"):
+        s[f"{v}_swaps_mean"] = float(a[f"{v}_swaps"].mean())
+        s[f"{v}_ms_median"] = float(np.median(a[f"{v}_ms"]))
+        if v != "plain":
+            d = a[f"{v}_logvol"] - a["plain_logvol"]
+            fin = np.isfinite(d)
+            s[f"{v}_minus_plain_logvol_mean"] = float(d[fin].mean()) if fin.any() else None
+            s[f"{v}_minus_plain_logvol_max"] = float(d[fin].max()) if fin.any() else None
+            s[f"{v}_vol_ratio_ge_0999"] = int((d[fin] >= np.log(0.999)).sum())
+    s["learned_fallbacks"] = int(a["learned_fallback"].sum())
+    s["learned_cols_fallbacks"] = int(a["learned_cols_fallback"].sum())
+    s["random_singular"] = int(a["random_singular"].sum())
     if "oracle_logvol" in a:
-        s["plain_vs_oracle_logvol_mean"] = float((a["plain_logvol"] - a["oracle_logvol"]).mean())
-        s["learned_vs_oracle_logvol_mean"] = float((a["learned_logvol"] - a["oracle_logvol"]).mean())
+        s["plain_minus_oracle_logvol_max_abs"] = float(np.abs(a["plain_logvol"] - a["oracle_logvol"]).max())
+        s["plain_sets_equal_oracle"] = int(a["plain_is_oracle"].sum())
     return s
 
 
@@ -250,7 +281,7 @@ def main(argv=None):
     ap.add_argument("--labels", required=True)
     ap.add_argument("--train", type=int, default=2048)
     ap.add_argument("--test", type=int, default=128)
-    ap.add_argument("--epochs", type=int, default=6)
+    ap.add_argument("--epochs", type=int, default=24)
     ap.add_argument("--batch", type=int, default=65536)
     ap.add_argument("--lr", type=float, default=2e-3)
     ap.add_argument("--large", type=int, default=8, help="matrices of 16384 x 4096, r = 64, to evaluate")
@@ -278,8 +309,10 @@ def main(argv=None):
     t_train = time.perf_counter() - t0
     res = dict(family=dict(F, train=ntr, test=len(te_items)), features_s=t_feat, train_s=t_train,
                loss_rows=hr, loss_cols=hc)
-    ev = evaluate(hd, rows, cols, te_items, m, n, r, F["b_r"], F["b_c"], dev,
-                  oracle_logvol=lab["logvol"][len(items) - args.test:])
+    k0 = len(items) - args.test
+    orc_sets = [(lab["I"][k0 + t].tolist(), lab["J"][k0 + t].tolist(), lab["logvol"][k0 + t])
+                for t in range(args.test)]
+    ev = evaluate(hd, rows, cols, te_items, m, n, r, F["b_r"], F["b_c"], dev, oracle=orc_sets)
     res["heldout"] = summarise(ev)
     res["parts_16384x4096"] = time_parts(hd, rows, cols, 16384, 4096, 64, dev)
     if args.large:
