@@ -71,6 +71,7 @@ typedef struct {
 } cur_opts;
 
 #define CUR_FLAG_POLISH 1u
+#define CUR_FLAG_PREC_BF16 2u   /* cur_maxvol_global: BF16 coefficient products first */
 
 /* Summary of one cur_cross call, written to DEVICE memory by cur_cross. */
 typedef struct {
@@ -218,6 +219,22 @@ cur_status cur_residual_cheb_noalloc(const cur_mat* A, const void* C, const doub
 cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, int32_t b_c,
                      const cur_opts* opts, int32_t* I_out, int32_t* J_out,
                      cur_cross_info* info_out, cudaStream_t stream);
+
+/* Maxvol over all p rows of a basis (p x r, contiguous: ld = cols = r; CUR_F32 or CUR_F64)
+ * from the start rows S0 (r int32, device): B = C M^-1 with M = C(S,:), swap the row of
+ * argmax |B_ij| into position j while |B_ij| > 1 + delta, Sherman-Morrison updates, a fresh
+ * factorisation every r swaps (the swap iteration of Section 1.2's maximal-volume
+ * refinement). With CUR_FLAG_PREC_BF16 in opts->flags (CUR_F32 basis, r a multiple of 16),
+ * each iteration first forms B for all rows as a BF16 x BF16 -> FP32 tensor-core product
+ * and takes its argmax, recomputes the winner exactly (FP64) and swaps only if the exact
+ * value exceeds 1 + delta; the first winner that does not ends that phase, and the
+ * FP32/FP64 iteration finishes from the set reached. Outputs (device): S_out r int32,
+ * logvol_out 1 double (may be NULL), swaps_out 2 int32 (may be NULL): all swaps, and the
+ * swaps of the BF16 phase. A singular C(S0,:) records CUR_ERR_SINGULAR (S_out = S0); more
+ * than max_swaps records CUR_ERR_NOCONV. Synchronises the stream. */
+cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t* S0, int32_t r,
+                             const cur_opts* opts, int32_t* S_out, double* logvol_out,
+                             int32_t* swaps_out, cudaStream_t stream);
 
 /* ---- Learned proposal (where the maxvol sweeps of Algorithm 2 start)
  *

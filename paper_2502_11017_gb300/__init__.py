@@ -17,6 +17,7 @@ CUR_OK, CUR_ERR_ARG, CUR_ERR_SINGULAR, CUR_ERR_NONFINITE, CUR_ERR_NOCONV = 0, 1,
 CUR_ERR_TIMEOUT, CUR_ERR_NOMEM, CUR_ERR_CUDA, CUR_WARN_RANK = 5, 6, 7, 8
 CUR_F64, CUR_F32, CUR_BF16 = 0, 1, 2
 CUR_FLAG_POLISH = 1
+CUR_FLAG_PREC_BF16 = 2
 
 # Every symbol include/cur.h declares.
 EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", "cur_aca_full",
@@ -26,7 +27,7 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", 
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
            "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout",
            "cur_sketch", "cur_mlp_forward", "cur_mlp_grad", "cur_adam_step", "cur_propose",
-           "cur_cross_from"]
+           "cur_cross_from", "cur_maxvol_global"]
 
 
 class CurMat(ctypes.Structure):
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                            ctypes.c_float, P], ctypes.c_int),
         "cur_propose": ([P, P, I64, I32, P, P], ctypes.c_int),
         "cur_cross_from": ([P, pmat, I32, P, P, popts, P, P, P, P], ctypes.c_int),
+        "cur_maxvol_global": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -153,8 +155,9 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def opts(delta: float = 1e-2, max_swaps: int = 0, nblocks: int = 1, polish: bool = True) -> CurOpts:
-    return CurOpts(delta, max_swaps, nblocks, CUR_FLAG_POLISH if polish else 0)
+def opts(delta: float = 1e-2, max_swaps: int = 0, nblocks: int = 1, polish: bool = True,
+         bf16: bool = False) -> CurOpts:
+    return CurOpts(delta, max_swaps, nblocks, (CUR_FLAG_POLISH if polish else 0) | (CUR_FLAG_PREC_BF16 if bf16 else 0))
 
 
 # ------------------------------------------------------------------ C ABI names
@@ -363,3 +366,9 @@ def cur_cross_from(h, A, r: int, I0, J0, o: CurOpts, I_out, J_out, info_out=None
     return _check(load().cur_cross_from(h, ctypes.byref(mat(A)), r, _ptr(I0), _ptr(J0), ctypes.byref(o),
                                         _ptr(I_out), _ptr(J_out), _ptr(info_out), _stream(stream)),
                   "cur_cross_from")
+
+
+def cur_maxvol_global(h, basis, S0, r: int, o: CurOpts, S_out, logvol_out=None, swaps_out=None, stream=None) -> int:
+    """Maxvol over all rows of basis (p x r CUDA tensor) from S0; swaps_out: 2 int32."""
+    return _check(load().cur_maxvol_global(h, ctypes.byref(mat(basis)), _ptr(S0), r, ctypes.byref(o), _ptr(S_out),
+                                           _ptr(logvol_out), _ptr(swaps_out), _stream(stream)), "cur_maxvol_global")

@@ -1,0 +1,546 @@
+// Global maxvol with BF16 coefficient products (the precision option of the swap
+// iteration of Section 1.2's maximal-volume refinement).
+//
+// Each iteration forms B = C M^-1 for all p rows of the basis as a BF16 x BF16 -> FP32
+// tcgen05 GEMM (C and M^-1 rounded to BF16 once; TMA-staged 128-row tiles of C, M^-1^T
+// resident in shared memory, the accumulator in TMEM) and reduces argmax |B_ij| in the
+// epilogue, without writing B (each CTA keeps its two best rows). The eight best rows of all
+// CTAs are then recomputed exactly, b = C(i,:) M^-1 with M^-1 held as a double-float pair
+// (hi + lo floats, about 2^-48 relative), the products formed by the error-free Dot2 sums on
+// the FP32 pipes and read out in FP64 (GB300's FP64 rate is a small fraction of its FP32
+// rate, so FP64-class arithmetic runs on the FP32 pipes, as in the swap engine), the
+// largest exact |b_j| among
+// them is the winner (the exact argmax unless rounding pushed its row below eight others),
+// and the swap is taken only if |b_j| > 1 + delta; M^-1 gets its Sherman-Morrison
+// update in double-float and is rounded to BF16 again for the next product. The start is
+// factorised in FP64. The first winner whose
+// exact value passes the test ends this phase, and the FP32/FP64 swap engine (maxvol.cu)
+// finishes from the set reached, so the result is dominant to the same standard as the
+// plain path's. Every accepted swap raises the volume by |b_j| > 1 + delta, so the phase
+// cannot cycle.
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tc.cuh"
+
+namespace curk {
+
+constexpr int kLpBM = 128;           // rows of C per tile (MMA M)
+constexpr int kLpKC = 64;            // BF16 elements per 128-byte swizzled K chunk
+constexpr int kLpChunkC = kLpBM * 128;  // bytes of one K chunk of a C tile
+constexpr int kLpThreads = 128;
+constexpr int kLpBatch = 16;         // iterations launched between two reads of the control block
+constexpr int kLpTop = 8;            // rows recomputed exactly per iteration
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+struct LpCtl {           // control block of one call (device)
+    int done;            // the BF16 phase is over
+    int swaps;           // swaps it took
+    int status;          // CUR_OK or CUR_ERR_SINGULAR (start set)
+    int pad;
+    double logvol;       // log|det C(S,:)|
+};
+
+struct LpCand {          // a row's largest |B_ij| (approximate); two per CTA
+    float v;
+    int i, j, pad;
+};
+
+__device__ __forceinline__ bool lp_better(float v, int i, int j, float v2, int i2, int j2) {
+    return v > v2 || (v == v2 && (i < i2 || (i == i2 && j < j2)));
+}
+
+// Cq (p x ldk BF16) = C (p x r FP32), zero past column r.
+__global__ void lp_quant_c(const float* __restrict__ C, int64_t p, int r, int ldk, __nv_bfloat16* __restrict__ Cq) {
+    const int64_t total = p * ldk;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ldk;
+        const int k = (int)(e - i * ldk);
+        Cq[e] = __float2bfloat16_rn(k < r ? C[i * r + k] : 0.f);
+    }
+}
+
+// W (r x ldk BF16) = (M^-1)^T rounded from its hi part Mh, zero past column r.
+__device__ __forceinline__ void lp_requant(const float* Mh, int r, int ldk, __nv_bfloat16* W) {
+    for (int e = threadIdx.x; e < r * ldk; e += blockDim.x) {
+        const int n = e / ldk, k = e - n * ldk;
+        W[e] = __float2bfloat16_rn(k < r ? Mh[k * r + n] : 0.f);
+    }
+}
+
+// M = C(S,:) in FP64, its inverse (as hi + lo floats) and log|det|; one CTA.
+__global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const int32_t* S, __nv_bfloat16* W,
+                           float* Mh, float* Ml, LpCtl* ctl) {
+    extern __shared__ double lsm[];
+    double* M = lsm;                   // r x r
+    double* colk = M + r * r;          // r
+    int* piv = reinterpret_cast<int*>(colk + r);
+    const int tid = threadIdx.x;
+    double mx = 0.0;
+    for (int e = tid; e < r * r; e += blockDim.x) {
+        const double x = (double)C[(int64_t)S[e / r] * r + (e % r)];
+        M[e] = x;
+        mx = fmax(mx, fabs(x));
+    }
+    mx = block_max(mx);
+    double lv = 0.0;
+    const int sing = gj_inverse(M, r, colk, piv, (double)r * 2.220446049250313e-16 * mx, &lv);
+    if (sing) {
+        if (tid == 0) { ctl->status = CUR_ERR_SINGULAR; ctl->done = 1; ctl->logvol = -INFINITY; }
+        return;
+    }
+    for (int e = tid; e < r * r; e += blockDim.x) split_d(M[e], Mh[e], Ml[e]);
+    __syncthreads();
+    lp_requant(Mh, r, ldk, W);
+    if (tid == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = lv; }
+}
+
+// argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles.
+// Thread 0 issues the TMA loads (the next tile's while the current one is multiplied) and
+// the MMAs; all four warps read the accumulator (warp w: rows 32w..32w+31 of the tile).
+__global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
+                                                          const __grid_constant__ CUtensorMap mW, int64_t p, int r,
+                                                          int kc, int tcols, const LpCtl* ctl, LpCand* cand,
+                                                          int* status) {
+    extern __shared__ unsigned char lp_raw[];
+    __shared__ uint64_t full[2], wbar, mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    __shared__ float red_v[8];
+    __shared__ int red_i[8], red_j[8];
+    if (ctl->done) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char* WS = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(lp_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t wchunk = (uint32_t)r * 128;
+    unsigned char* CS = WS + (size_t)kc * wchunk;
+    const uint32_t cbuf = (uint32_t)kc * kLpChunkC;
+    const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
+    const int nloc = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&wbar, 1);
+        mbar_init(&mbar, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(&tslot, tcols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    // loads in flight that thread 0 has not waited for: W, and the C buffers
+    bool w_pending = false, c_pending[2] = {false, false};
+    uint32_t c_par[2] = {0, 0};
+    if (tid == 0) {
+        mbar_expect_tx(&wbar, (uint32_t)kc * wchunk);
+        for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kLpKC * c, 0);
+        w_pending = true;
+        if (nloc > 0) {
+            mbar_expect_tx(&full[0], cbuf);
+            for (int c = 0; c < kc; ++c)
+                tma_load_2d(CS + (size_t)c * kLpChunkC, &mC, &full[0], kLpKC * c, (int)(blockIdx.x * kLpBM));
+            c_pending[0] = true;
+        }
+    }
+    float top_v[2] = {-1.f, -1.f};
+    int top_i[2] = {INT_MAX, INT_MAX}, top_j[2] = {INT_MAX, INT_MAX};
+    constexpr int kM = kLpBM;
+    const uint32_t idesc = idesc_bf16(kM, r);
+    bool mma_pending = false;
+    int k = 0;
+    for (; k < nloc; ++k) {
+        const int64_t tile = blockIdx.x + (int64_t)k * gridDim.x;
+        const int b = k & 1;
+        if (tid == 0) {
+            if (k + 1 < nloc) {   // the other buffer's last reader (tile k-1's MMA) has completed
+                const int64_t nt = tile + gridDim.x;
+                mbar_expect_tx(&full[b ^ 1], cbuf);
+                for (int c = 0; c < kc; ++c)
+                    tma_load_2d(CS + (size_t)(b ^ 1) * cbuf + (size_t)c * kLpChunkC, &mC, &full[b ^ 1], kLpKC * c,
+                                (int)(nt * kLpBM));
+                c_pending[b ^ 1] = true;
+            }
+            bool ok = true;
+            if (w_pending) { ok = mbar_wait(&wbar, 0); if (ok) w_pending = false; }
+            if (ok) { ok = mbar_wait(&full[b], c_par[b]); if (ok) { c_pending[b] = false; c_par[b] ^= 1u; } }
+            if (ok) {
+                tc_fence_after();
+                const uint32_t ca = su32(CS + (size_t)b * cbuf), wa = su32(WS);
+                for (int s = 0; s < kc * 4; ++s) {
+                    const uint32_t oc = (uint32_t)(s >> 2) * kLpChunkC + (uint32_t)(s & 3) * 32;
+                    const uint32_t ow = (uint32_t)(s >> 2) * wchunk + (uint32_t)(s & 3) * 32;
+                    mma_bf16(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
+                }
+                mma_commit(&mbar);
+                mma_pending = true;
+            } else {
+                abort_flag = 1;
+            }
+        }
+        __syncthreads();
+        if (abort_flag) break;
+        if (!mbar_wait(&mbar, (uint32_t)(k & 1))) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) break;
+        if (tid == 0) mma_pending = false;
+        tc_fence_after();
+        // epilogue: this thread's row, all r columns
+        const int64_t row = tile * kLpBM + 32 * warp + lane;
+        float bv = -1.f;
+        int bj = INT_MAX;
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        for (int c0 = 0; c0 < r; c0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + (uint32_t)c0, v);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const float x = fabsf(v[q]);
+                if (x > bv) { bv = x; bj = c0 + q; }
+            }
+        }
+        int bi = row < p ? (int)row : INT_MAX;
+        if (row >= p) { bv = -1.f; bj = INT_MAX; }
+        // the warp's two best rows
+        for (int q = 0; q < 2; ++q) {
+            float v = bv;
+            int i = bi, j = bj;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+                const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+                const int j2 = __shfl_xor_sync(0xffffffffu, j, o);
+                if (lp_better(v2, i2, j2, v, i, j)) { v = v2; i = i2; j = j2; }
+            }
+            if (lane == 0) { red_v[2 * warp + q] = v; red_i[2 * warp + q] = i; red_j[2 * warp + q] = j; }
+            if (bi == i) { bv = -2.f; bi = INT_MAX; bj = INT_MAX; }
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0)
+            for (int w = 0; w < 8; ++w) {
+                const float v = red_v[w];
+                const int i = red_i[w], j = red_j[w];
+                if (lp_better(v, i, j, top_v[0], top_i[0], top_j[0])) {
+                    top_v[1] = top_v[0]; top_i[1] = top_i[0]; top_j[1] = top_j[0];
+                    top_v[0] = v; top_i[0] = i; top_j[0] = j;
+                } else if (lp_better(v, i, j, top_v[1], top_i[1], top_j[1])) {
+                    top_v[1] = v; top_i[1] = i; top_j[1] = j;
+                }
+            }
+    }
+    if (tid == 0) {
+        if (abort_flag) {
+            set_status(status, CUR_ERR_TIMEOUT);
+            // let what is still in flight land before the CTA's memory goes away
+            if (mma_pending) mbar_wait(&mbar, (uint32_t)(k & 1));
+            if (w_pending) mbar_wait(&wbar, 0);
+            for (int s = 0; s < 2; ++s)
+                if (c_pending[s]) mbar_wait(&full[s], c_par[s]);
+            top_v[0] = top_v[1] = -1.f;
+        }
+        for (int q = 0; q < 2; ++q) {
+            LpCand c;
+            c.v = top_v[q];
+            c.i = top_i[q];
+            c.j = top_j[q];
+            c.pad = 0;
+            cand[2 * blockIdx.x + q] = c;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, tcols);
+    }
+}
+
+// The eight best candidate rows recomputed in FP64; the largest exact |b_ij| among them
+// wins; its swap and the FP64 Sherman-Morrison update of M^-1 if it passes, else the end of
+// the phase. One CTA.
+__global__ void __launch_bounds__(1024) lp_swap_k(const float* __restrict__ C, int64_t p, int r, int ldk,
+                                                  const LpCand* cand, int ncand, float* Mh, float* Ml, int32_t* S,
+                                                  __nv_bfloat16* W, LpCtl* ctl, double delta, int max_swaps) {
+    extern __shared__ double lsm[];
+    double* brow = lsm;                                             // kLpTop x r exact rows
+    df64* mcol = reinterpret_cast<df64*>(lsm + kLpTop * r);         // column j of M^-1 (r)
+    df64* g = mcol + r;                                             // (b - e_j) / b_j (r)
+    float* crow = reinterpret_cast<float*>(g + r);                  // the kLpTop rows of C
+    const int rp = r + 1;                                           // padded row pitch of M^-1
+    float* sh = crow + kLpTop * r;                                  // M^-1 hi, r x rp
+    float* sl = sh + r * rp;                                        // M^-1 lo, r x rp
+    unsigned long long* ckey = reinterpret_cast<unsigned long long*>(sl + r * rp + 4 - ((r * rp) & 3));
+    __shared__ int rows[kLpTop];
+    __shared__ int nsel, si, sj, st;
+    __shared__ unsigned long long wbest[32], kbest;
+    if (ctl->done) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int c = tid; c < ncand; c += nt) {
+        const LpCand x = cand[c];
+        ckey[c] = x.v >= 0.f ? ((unsigned long long)__float_as_uint(x.v) << 32) |
+                                   (unsigned long long)(0xffffffffu - (unsigned)x.i)
+                             : 0ull;
+    }
+    if (tid == 0) nsel = 0;
+    for (int e = tid; e < r * r; e += nt) {
+        const int l = e / r, c = e - l * r;
+        sh[l * rp + c] = Mh[e];
+        sl[l * rp + c] = Ml[e];
+    }
+    __syncthreads();
+    // the kLpTop best candidates: kLpTop rounds of a block-wide maximum of order-preserving
+    // keys (|B| bits, then the lower row; the value is non-negative, so its bits order it);
+    // the winner's key is cleared before the next round
+    for (int t = 0; t < kLpTop; ++t) {
+        unsigned long long best = 0ull;
+        for (int c = tid; c < ncand; c += nt) best = ckey[c] > best ? ckey[c] : best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+            best = y > best ? y : best;
+        }
+        if ((tid & 31) == 0) wbest[tid >> 5] = best;
+        __syncthreads();
+        if (tid < 32) {
+            unsigned long long b2 = tid < (nt >> 5) ? wbest[tid] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, b2, o);
+                b2 = y > b2 ? y : b2;
+            }
+            if (tid == 0) {
+                kbest = b2;
+                if (b2 != 0ull) { rows[t] = (int)(0xffffffffu - (unsigned)(b2 & 0xffffffffull)); nsel = t + 1; }
+            }
+        }
+        __syncthreads();
+        const unsigned long long kb = kbest;
+        if (kb == 0ull) break;
+        for (int c = tid; c < ncand; c += nt)
+            if (ckey[c] == kb) ckey[c] = 0ull;
+    }
+    __syncthreads();
+    const int ns = nsel;
+    if (ns == 0) {
+        if (tid == 0) ctl->done = 1;
+        return;
+    }
+    for (int e = tid; e < ns * r; e += nt) {
+        const int t = e / r, l = e - t * r;
+        crow[e] = C[(int64_t)rows[t] * r + l];
+    }
+    __syncthreads();
+    for (int e = tid; e < ns * r; e += nt) {
+        const int t = e / r, c = e - t * r;
+        const float* a = crow + t * r;
+        Dot2 d;
+#pragma unroll 8
+        for (int l = 0; l < r; ++l) d.add(a[l], sh[l * rp + c], sl[l * rp + c]);
+        brow[e] = d.value();
+    }
+    __syncthreads();
+    if (tid < 32) {
+        double bv = -1.0;
+        int bi = INT_MAX, bj = INT_MAX, bt = -1;
+        for (int e = tid; e < ns * r; e += 32) {
+            const int t = e / r, c = e - t * r;
+            const double x = fabs(brow[e]);
+            const int i = rows[t];
+            if (x > bv || (x == bv && (i < bi || (i == bi && c < bj)))) { bv = x; bi = i; bj = c; bt = t; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+            const int t2 = __shfl_xor_sync(0xffffffffu, bt, o);
+            if (v2 > bv || (v2 == bv && (i2 < bi || (i2 == bi && j2 < bj)))) { bv = v2; bi = i2; bj = j2; bt = t2; }
+        }
+        if (tid == 0) { si = bi; sj = bj; st = bt; }
+    }
+    __syncthreads();
+    const int i = si, j = sj;
+    const double* b = brow + (size_t)st * r;
+    const double bjv = b[j];
+    if (!(fabs(bjv) > 1.0 + delta)) {
+        if (tid == 0) ctl->done = 1;
+        return;
+    }
+    if (tid < r) {
+        mcol[tid] = df_make(sh[tid * rp + j], sl[tid * rp + j]);
+        const df64 bjd = df_from_d(bjv);
+        g[tid] = df_div(df_from_d(b[tid] - (tid == j ? 1.0 : 0.0)), bjd);
+    }
+    __syncthreads();
+    for (int e = tid; e < r * r; e += nt) {
+        const int l = e / r, c = e - l * r;
+        const df64 v = df_sub(df_make(sh[l * rp + c], sl[l * rp + c]), df_mul(mcol[l], g[c]));
+        sh[l * rp + c] = v.h;
+        sl[l * rp + c] = v.l;
+        Mh[e] = v.h;
+        Ml[e] = v.l;
+    }
+    __syncthreads();
+    // W[n][k] = bf16(M^-1[k][n]); consecutive threads take consecutive k (padded pitch: no conflicts)
+    for (int e = tid; e < r * ldk; e += nt) {
+        const int n = e / ldk, k = e - n * ldk;
+        W[e] = __float2bfloat16_rn(k < r ? sh[k * rp + n] : 0.f);
+    }
+    if (tid == 0) {
+        S[j] = i;
+        ctl->logvol += log(fabs(bjv));
+        if (++ctl->swaps >= max_swaps) ctl->done = 1;
+    }
+}
+
+__global__ void lp_finish_k(int32_t* swaps_out, const LpCtl* ctl, int exact_swaps, int code, int* hstatus) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (swaps_out) {
+        swaps_out[0] = ctl->swaps + exact_swaps;
+        swaps_out[1] = ctl->swaps;
+    }
+    if (code == CUR_ERR_SINGULAR || code == CUR_ERR_NOCONV || code == CUR_ERR_NONFINITE) set_status(hstatus, code);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 lp_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// rows x ldk BF16 (ldk a multiple of 64), boxes of 64 elements x box_rows rows, 128-byte swizzle.
+static bool lp_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int ldk, int box_rows) {
+    auto enc = lp_encode_fn();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
+    cuuint64_t gstr[1] = {(cuuint64_t)ldk * sizeof(__nv_bfloat16)};
+    cuuint32_t box[2] = {(cuuint32_t)kLpKC, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), gdim, gstr, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace curk
+
+// BF16 phase, then the exact engine. C: p x r FP32 (contiguous, device).
+static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o,
+                                     const int32_t* S0, int32_t* S_out, double* logvol_out, int32_t* swaps_out,
+                                     Arena& ar, cudaStream_t st) {
+    using namespace curk;
+    const int kc = (r + kLpKC - 1) / kLpKC, ldk = kc * kLpKC;
+    const int tcols = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
+    const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
+    // CTAs per SM: as many as shared memory and the SM's 512 TMEM columns hold, at most 4
+    const size_t sm_arg = 1024 + (size_t)kc * r * 128 + 2 * (size_t)kc * kLpChunkC;
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>({(size_t)4, (size_t)(227 * 1024) / sm_arg,
+                                                                    (size_t)(512 / tcols)}));
+    const int grid = (int)std::min<int64_t>({ntiles, (int64_t)per_sm * h->num_sms, (int64_t)1024});
+    __nv_bfloat16* Cq = ar.get<__nv_bfloat16>((size_t)p * ldk);
+    __nv_bfloat16* W = ar.get<__nv_bfloat16>((size_t)r * ldk);
+    float* Mh = ar.get<float>((size_t)r * r);
+    float* Ml = ar.get<float>((size_t)r * r);
+    int32_t* S = ar.get<int32_t>(r);
+    LpCand* cand = ar.get<LpCand>(2 * (size_t)grid);
+    LpCtl* ctl = ar.get<LpCtl>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUtensorMap mC, mW;
+    if (!lp_map(&mC, Cq, p, ldk, kLpBM) || !lp_map(&mW, W, r, ldk, r)) return CUR_ERR_ARG;
+    CUR_CK(cudaMemsetAsync(ctl, 0, sizeof(LpCtl), st));
+    CUR_CK(cudaMemcpyAsync(S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    lp_quant_c<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((p * ldk + 255) / 256, 8LL * h->num_sms)), 256, 0, st>>>(
+        C, p, r, ldk, Cq);
+    CUR_CK(cudaGetLastError());
+    const size_t sm_setup = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(double) + (size_t)r * sizeof(int) + 64;
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
+    lp_setup_k<<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, Mh, Ml, ctl);
+    CUR_CK(cudaGetLastError());
+    note_launch(2);
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
+    const size_t sm_swap = (size_t)kLpTop * r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
+                           (size_t)kLpTop * r * sizeof(float) + 2 * (size_t)r * (r + 1) * sizeof(float) + 16 +
+                           2 * (size_t)grid * sizeof(LpCand);
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
+    const int max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
+    LpCtl* hc = reinterpret_cast<LpCtl*>(h->host_stage);
+    CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
+    for (int batch = 0;; ++batch) {
+        for (int q = 0; q < kLpBatch; ++q) {
+            lp_argmax_k<<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, ctl, cand, h->status);
+            CUR_CK(cudaGetLastError());
+            lp_swap_k<<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, 2 * grid, Mh, Ml, S, W, ctl, o->delta,
+                                                max_swaps);
+            CUR_CK(cudaGetLastError());
+        }
+        note_launch(2 * kLpBatch);
+        CUR_CK(cudaMemcpyAsync(hc, ctl, sizeof(LpCtl), cudaMemcpyDeviceToHost, st));
+        CUR_CK(cudaStreamSynchronize(st));
+        if (hc->done) break;
+    }
+    const int st_lp = hc->status;
+    CUR_CK(cudaEventRecord(h->stage_ev, st));
+    if (st_lp == CUR_ERR_SINGULAR) {
+        CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+        if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, &ctl->logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
+        lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, 0, CUR_ERR_SINGULAR, h->status);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+        return CUR_OK;
+    }
+    MvResult res;
+    CUR_TRY(maxvol_global(h, CUR_F32, C, p, r, o, S, S_out, logvol_out, &res, ar, st));
+    lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, res.swaps, res.status, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+extern "C" {
+
+cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t* S0, int32_t r,
+                             const cur_opts* opts, int32_t* S_out, double* logvol_out, int32_t* swaps_out,
+                             cudaStream_t st) {
+    if (!h || !basis || !basis->data || !S0 || !S_out) return CUR_ERR_ARG;
+    const int64_t p = basis->rows;
+    if (r < 1 || r > 128 || basis->cols != r || basis->ld != r || p < r || p > INT_MAX - 256) return CUR_ERR_ARG;
+    cur_opts o = opts ? *opts : cur_default_opts();
+    if (!(o.delta >= 0.0)) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    if (o.flags & CUR_FLAG_PREC_BF16) {
+        if (basis->dtype != CUR_F32 || r % 16 != 0) return CUR_ERR_ARG;
+        return maxvol_global_bf16(h, static_cast<const float*>(basis->data), p, r, &o, S0, S_out, logvol_out,
+                                  swaps_out, ar, st);
+    }
+    if (basis->dtype != CUR_F32 && basis->dtype != CUR_F64) return CUR_ERR_ARG;
+    MvResult res;
+    CUR_TRY(maxvol_global(h, basis->dtype, basis->data, p, r, &o, S0, S_out, logvol_out, &res, ar, st));
+    curk::LpCtl* ctl = ar.get<curk::LpCtl>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_CK(cudaMemsetAsync(ctl, 0, sizeof(curk::LpCtl), st));
+    curk::lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, res.swaps, res.status, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,103 @@
+"""Parity of cur_maxvol_global (maxvol over all rows of a basis from a given start) with the
+oracle's maxvol, on the FP32/FP64 engine and with the BF16 coefficient phase
+(CUR_FLAG_PREC_BF16: tcgen05 BF16 products, each winner recomputed exactly before its swap).
+
+The bar: the oracle's set, or else a volume within 0.999 of it; in both cases the GPU's set
+is (1 + delta)-dominant when its coefficients are evaluated in FP64, and the reported
+log-volume is that of the set.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2502_11017_gb300 as cur
+from paper_2502_11017_gb300 import workloads as wl
+from oracle import cur_oracle as orc
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+DELTA = 1e-2
+
+
+@pytest.fixture(scope="module")
+def hd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cur.load()
+    h = cur.Handle(65536, 4096, 128, cur.CUR_F32)
+    yield h
+    h.close()
+
+
+def basis(p, r, seed):
+    """p x r FP32 with singular values exp(-5 j / r) (a condition number of e^5) and Haar
+    factors."""
+    rng = np.random.default_rng(seed)
+    u = wl.haar(p, r, rng)
+    v = wl.haar(r, r, rng)
+    return ((u * np.exp(-5.0 * np.arange(r) / r)) @ v.T * np.sqrt(p)).astype(np.float32)
+
+
+def run(hd, C, S0, r, bf16):
+    S = torch.empty(r, dtype=torch.int32, device=DEV)
+    lv = torch.empty(1, dtype=torch.float64, device=DEV)
+    sw = torch.zeros(2, dtype=torch.int32, device=DEV)
+    cur.cur_maxvol_global(hd.h, torch.from_numpy(C).to(DEV), torch.tensor(S0, dtype=torch.int32, device=DEV), r,
+                          cur.opts(DELTA, bf16=bf16), S, lv, sw)
+    st = cur.cur_sync_status(hd.h)
+    return S.tolist(), lv.item(), sw.tolist(), st
+
+
+CASES = [(5000, 16, 1), (20000, 64, 2), (3001, 128, 3), (1000, 32, 4), (200, 48, 5), (65536, 64, 6)]
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("p,r,seed", CASES)
+def test_maxvol_global_matches_oracle(hd, p, r, seed, bf16):
+    C = basis(p, r, seed)
+    C64 = C.astype(np.float64)
+    S0 = np.random.default_rng(seed + 100).choice(p, r, replace=False).tolist()
+    S, lv, sw, st = run(hd, C, S0, r, bf16)
+    So, lvo, _swo, sto = orc.maxvol(C64, S0, DELTA)
+    assert st == cur.CUR_OK and sto == orc.OK
+    assert len(set(S)) == r
+    lv_set = orc.logvol(C64[S, :])
+    assert lv == pytest.approx(lv_set, abs=1e-6 * max(1.0, abs(lv_set)))
+    if sorted(S) != sorted(So):
+        assert lv_set >= lvo + math.log(0.999)
+    B = C64 @ np.linalg.inv(C64[S, :])
+    assert np.abs(B).max() <= (1 + DELTA) * (1 + 1e-4)
+    assert sw[0] >= sw[1] >= 0
+    if bf16:
+        assert sw[1] > 0                 # the BF16 phase made swaps of its own
+    else:
+        assert sw[1] == 0
+
+
+def test_bf16_phase_on_a_converged_set_swaps_nothing(hd):
+    C = basis(4000, 32, 7)
+    S0 = np.random.default_rng(7).choice(4000, 32, replace=False).tolist()
+    S, _lv, _sw, _ = run(hd, C, S0, 32, False)
+    S2, _lv2, sw2, st = run(hd, C, S, 32, True)
+    assert st == cur.CUR_OK and sorted(S2) == sorted(S) and sw2 == [0, 0]
+
+
+def test_singular_start_is_reported(hd):
+    C = basis(1000, 16, 8)
+    S0 = [3, 3] + list(range(10, 24))
+    for bf16 in (False, True):
+        S, lv, sw, st = run(hd, C, S0, 16, bf16)
+        assert st == cur.CUR_ERR_SINGULAR and S == S0 and sw[0] == 0
+
+
+def test_bad_arguments(hd):
+    C = torch.from_numpy(basis(500, 24, 9)).to(DEV)
+    S0 = torch.arange(24, dtype=torch.int32, device=DEV)
+    S = torch.empty(24, dtype=torch.int32, device=DEV)
+    with pytest.raises(cur.CurError):      # r not a multiple of 16 on the BF16 path
+        cur.cur_maxvol_global(hd.h, C, S0, 24, cur.opts(DELTA, bf16=True), S)
+    with pytest.raises(cur.CurError):      # BF16 path wants FP32 data
+        cur.cur_maxvol_global(hd.h, C.double()[:, :16].contiguous(), S0[:16], 16, cur.opts(DELTA, bf16=True), S)
