@@ -108,6 +108,15 @@ __global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const in
     if (tid == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = lv; }
 }
 
+// The same from a given FP64 inverse of C(S,:) (r x r, row-major): split and rounded only.
+__global__ void lp_setup_from_k(const double* __restrict__ minv, int r, int ldk, __nv_bfloat16* W, float* Mh,
+                                float* Ml, LpCtl* ctl) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) split_d(minv[e], Mh[e], Ml[e]);
+    __syncthreads();
+    lp_requant(Mh, r, ldk, W);
+    if (threadIdx.x == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = 0.0; }
+}
+
 // argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles.
 // Thread 0 issues the TMA loads (the next tile's while the current one is multiplied) and
 // the MMAs; all four warps read the accumulator (warp w: rows 32w..32w+31 of the tile).
@@ -443,11 +452,17 @@ static bool lp_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, in
 
 }  // namespace curk
 
-// BF16 phase, then the exact engine. C: p x r FP32 (contiguous, device).
-static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o,
-                                     const int32_t* S0, int32_t* S_out, double* logvol_out, int32_t* swaps_out,
-                                     Arena& ar, cudaStream_t st) {
+// The stages of cur_cross take the BF16 phase only where its product has at least this many
+// 128-row tiles per SM; below that the FP32 engine's shared-memory B is faster.
+constexpr int64_t kBf16MinTilesPerSm = 4;
+
+// The BF16 phase alone from S0 (device r ints) to S_out (device; may alias S0). *swaps: the
+// swaps it took; *status: CUR_OK or CUR_ERR_SINGULAR (a singular C(S0,:); S_out = S0).
+// Synchronises the stream. C: p x r FP32 (contiguous, device), r a multiple of 16.
+cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
+                      int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st, const double* minv_in) {
     using namespace curk;
+    const size_t mark = ar.off;
     const int kc = (r + kLpKC - 1) / kLpKC, ldk = kc * kLpKC;
     const int tcols = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
@@ -471,9 +486,13 @@ static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, i
     lp_quant_c<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((p * ldk + 255) / 256, 8LL * h->num_sms)), 256, 0, st>>>(
         C, p, r, ldk, Cq);
     CUR_CK(cudaGetLastError());
-    const size_t sm_setup = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(double) + (size_t)r * sizeof(int) + 64;
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
-    lp_setup_k<<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, Mh, Ml, ctl);
+    if (minv_in) {
+        lp_setup_from_k<<<1, 256, 0, st>>>(minv_in, r, ldk, W, Mh, Ml, ctl);
+    } else {
+        const size_t sm_setup = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(double) + (size_t)r * sizeof(int) + 64;
+        CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
+        lp_setup_k<<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, Mh, Ml, ctl);
+    }
     CUR_CK(cudaGetLastError());
     note_launch(2);
     CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
@@ -484,7 +503,7 @@ static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, i
     const int max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
     LpCtl* hc = reinterpret_cast<LpCtl*>(h->host_stage);
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
-    for (int batch = 0;; ++batch) {
+    for (;;) {
         for (int q = 0; q < kLpBatch; ++q) {
             lp_argmax_k<<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, ctl, cand, h->status);
             CUR_CK(cudaGetLastError());
@@ -497,21 +516,49 @@ static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, i
         CUR_CK(cudaStreamSynchronize(st));
         if (hc->done) break;
     }
-    const int st_lp = hc->status;
+    *swaps = hc->swaps;
+    *status = hc->status;
     CUR_CK(cudaEventRecord(h->stage_ev, st));
-    if (st_lp == CUR_ERR_SINGULAR) {
-        CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(S_out, *status == CUR_ERR_SINGULAR ? S0 : S, sizeof(int32_t) * r,
+                           cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaStreamSynchronize(st));
+    ar.off = mark;
+    ar.ok = true;
+    return CUR_OK;
+}
+
+bool bf16_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r) {
+    return (o->flags & CUR_FLAG_PREC_BF16) && dt == CUR_F32 && r % 16 == 0 && r >= 16 && r <= 128 &&
+           p >= (int64_t)kBf16MinTilesPerSm * curk::kLpBM * h->num_sms && p <= INT_MAX - 256;
+}
+
+// BF16 phase, then the exact engine from the set it reached.
+static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o,
+                                     const int32_t* S0, int32_t* S_out, double* logvol_out, int32_t* swaps_out,
+                                     Arena& ar, cudaStream_t st) {
+    using namespace curk;
+    int lp_swaps = 0, lp_status = CUR_OK;
+    CUR_TRY(bf16_phase(h, C, p, r, o, S0, S_out, &lp_swaps, &lp_status, ar, st, nullptr));
+    LpCtl* ctl = ar.get<LpCtl>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    LpCtl hv{};
+    hv.swaps = lp_swaps;
+    hv.logvol = -INFINITY;
+    CUR_CK(cudaMemcpyAsync(ctl, &hv, sizeof(LpCtl), cudaMemcpyHostToDevice, st));
+    if (lp_status == CUR_ERR_SINGULAR) {
         if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, &ctl->logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
         lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, 0, CUR_ERR_SINGULAR, h->status);
         CUR_CK(cudaGetLastError());
         note_launch();
+        CUR_CK(cudaStreamSynchronize(st));
         return CUR_OK;
     }
     MvResult res;
-    CUR_TRY(maxvol_global(h, CUR_F32, C, p, r, o, S, S_out, logvol_out, &res, ar, st));
+    CUR_TRY(maxvol_global(h, CUR_F32, C, p, r, o, S_out, S_out, logvol_out, &res, ar, st));
     lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, res.swaps, res.status, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
+    CUR_CK(cudaStreamSynchronize(st));
     return CUR_OK;
 }
 

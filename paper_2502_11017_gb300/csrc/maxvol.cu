@@ -1521,8 +1521,19 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
     int mvalid = 0;
     if (o->flags & CUR_FLAG_POLISH) {
         MvResult gr;
-        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st,
-                             mv.empty() ? nullptr : mv[0], lvp.empty() ? nullptr : lvp[0], false,
+        const double* minv_in = mv.empty() ? nullptr : mv[0];
+        const double* lv_in = lvp.empty() ? nullptr : lvp[0];
+        if constexpr (std::is_same<TB, float>::value) {
+            // with CUR_FLAG_PREC_BF16 on a large basis, BF16 products take the polish's swaps
+            // first; the FP32 engine then finishes (from a fresh factorisation if any were taken)
+            if (bf16_phase_applies(h, o, CUR_F32, p, r)) {
+                int bsw = 0, bst = CUR_OK;
+                CUR_TRY(bf16_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, minv_in));
+                total += bsw;
+                if (bsw > 0) { minv_in = nullptr; lv_in = nullptr; }
+            }
+        }
+        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st, minv_in, lv_in, false,
                              minv_out));
         total += gr.swaps;
         fstat = gr.status;

@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--b_r", type=int, default=16)
     ap.add_argument("--b_c", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--bf16", action="store_true", help="CUR_FLAG_PREC_BF16 on the cross / row / column stages")
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=11019)
     ap.add_argument("--data", choices=["gaussian", "bf16product", "haar"], default="gaussian",
@@ -60,7 +61,7 @@ def main():
     rc = torch.empty(1, dtype=torch.float64, device=dev)
     cheb = torch.empty(1, dtype=torch.float64, device=dev)
     fro = torch.empty(1, dtype=torch.float64, device=dev)
-    o = cur.opts()
+    o = cur.opts(bf16=a.bf16)
     Rw = torch.empty((m, n), dtype=torch.float64 if A.dtype == torch.float64 else torch.float32,
                      device=dev) if a.call == "alg1" else None
     piv = torch.empty(r, dtype=torch.float64, device=dev)
@@ -77,9 +78,9 @@ def main():
         elif a.call == "cross":
             cur.cur_cross(h, A, r, a.b_r, a.b_c, o, I, J)
         elif a.call == "rows":
-            cur.cur_maxvol_rows(h, A, idx, r, cur.opts(nblocks=a.b_r), I)
+            cur.cur_maxvol_rows(h, A, idx, r, cur.opts(nblocks=a.b_r, bf16=a.bf16), I)
         elif a.call == "cols":
-            cur.cur_maxvol_cols(h, A, I, r, cur.opts(nblocks=a.b_c), J)
+            cur.cur_maxvol_cols(h, A, I, r, cur.opts(nblocks=a.b_c, bf16=a.bf16), J)
         elif a.call == "alg1":
             cur.cur_aca_full(h, A, r, Rw, I, J, piv)
 

@@ -101,3 +101,30 @@ def test_bad_arguments(hd):
         cur.cur_maxvol_global(hd.h, C, S0, 24, cur.opts(DELTA, bf16=True), S)
     with pytest.raises(cur.CurError):      # BF16 path wants FP32 data
         cur.cur_maxvol_global(hd.h, C.double()[:, :16].contiguous(), S0[:16], 16, cur.opts(DELTA, bf16=True), S)
+
+
+def test_row_selection_with_bf16_polish_matches_oracle(hd):
+    """cur_maxvol_rows with CUR_FLAG_PREC_BF16 on a basis large enough for the polish to take
+    the BF16 phase (81957 rows: over four 128-row tiles per SM, ragged)."""
+    m, n, r, b_r = 81957, 1024, 64, 16
+    a = wl.gaussian_kernel(m, n, 0.25, seed=12)
+    A = torch.from_numpy(a).to(DEV)
+    J0 = torch.empty(r, dtype=torch.int32, device=DEV)
+    cur.cur_aca_select(hd.h, A, 1, r, 1, J0)
+    I = {}
+    for bf16 in (False, True):
+        out = torch.empty(r, dtype=torch.int32, device=DEV)
+        lv = torch.empty(1, dtype=torch.float64, device=DEV)
+        cur.cur_maxvol_rows(hd.h, A, J0, r, cur.opts(DELTA, nblocks=b_r, bf16=bf16), out, lv)
+        assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+        I[bf16] = (out.tolist(), lv.item())
+    Jl = J0.tolist()
+    Io, lvo, _sw, st, _ = orc.maxvol_rows(a, Jl, b_r, DELTA)
+    assert st == orc.OK
+    Cb = a[:, Jl].astype(np.float64)
+    for bf16, (Il, lv) in I.items():
+        lv_set = orc.logvol(Cb[Il, :])
+        assert lv == pytest.approx(lv_set, abs=1e-6 * max(1.0, abs(lv_set)))
+        if sorted(Il) != sorted(Io):
+            assert lv_set >= lvo + math.log(0.999)
+        assert np.abs(Cb @ np.linalg.inv(Cb[Il, :])).max() <= (1 + DELTA) * (1 + 1e-4)
