@@ -130,6 +130,40 @@ __global__ void __launch_bounds__(256) aca_cols_pass(const TA* __restrict__ A, i
     const bool full = VEC && (col + CPL - 1 < n);
     AccOf<TA> acc[CPL];
     int64_t i = r0 + warp;
+    if constexpr (std::is_same<TA, __nv_bfloat16>::value && MODE == kDot) {
+        // BF16: about 12 FP32 operations per 2-byte element, so the sums of four rows take
+        // long enough that the next four rows' loads are issued before them (same order of
+        // summation as the loop below)
+        if (full && i + 24 < r1) {
+            uint4 xr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xr[u] = __ldcs(reinterpret_cast<const uint4*>(A + (i + 8 * u) * ld + col));
+            while (true) {
+                const int64_t inext = i + 32;
+                const bool more = inext + 24 < r1;
+                uint4 xn[4];
+                if (more) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        xn[u] = __ldcs(reinterpret_cast<const uint4*>(A + (inext + 8 * u) * ld + col));
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float h = qh[i + 8 * u], l = ql[i + 8 * u];
+                    const uint32_t w[4] = {xr[u].x, xr[u].y, xr[u].z, xr[u].w};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        acc_add(acc[2 * k], __uint_as_float(w[k] << 16), MODE, 0.0, h, l);
+                        acc_add(acc[2 * k + 1], __uint_as_float(w[k] & 0xffff0000u), MODE, 0.0, h, l);
+                    }
+                }
+                i = inext;
+                if (!more) break;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xr[u] = xn[u];
+            }
+        }
+    }
     for (; i + 24 < r1; i += 32) {
         V x[4][CPL];
 #pragma unroll
