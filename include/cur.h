@@ -72,6 +72,7 @@ typedef struct {
 
 #define CUR_FLAG_POLISH 1u
 #define CUR_FLAG_PREC_BF16 2u   /* cur_maxvol_global: BF16 coefficient products first */
+#define CUR_FLAG_PREC_FP8 4u    /* the same with E4M3 products (row-scaled); wins over BF16 */
 
 /* Summary of one cur_cross call, written to DEVICE memory by cur_cross. */
 typedef struct {
@@ -228,7 +229,8 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
  * each iteration first forms B for all rows as a BF16 x BF16 -> FP32 tensor-core product
  * and takes its argmax, recomputes the winner exactly (FP64) and swaps only if the exact
  * value exceeds 1 + delta; the first winner that does not ends that phase, and the
- * FP32/FP64 iteration finishes from the set reached. Outputs (device): S_out r int32,
+ * FP32/FP64 iteration finishes from the set reached. CUR_FLAG_PREC_FP8 does the same with
+ * E4M3 x E4M3 -> FP32 products, each row of C and of (M^-1)^T scaled to E4M3's range (448). Outputs (device): S_out r int32,
  * logvol_out 1 double (may be NULL), swaps_out 2 int32 (may be NULL): all swaps, and the
  * swaps of the BF16 phase. A singular C(S0,:) records CUR_ERR_SINGULAR (S_out = S0); more
  * than max_swaps records CUR_ERR_NOCONV. Synchronises the stream. */

@@ -18,6 +18,7 @@ CUR_ERR_TIMEOUT, CUR_ERR_NOMEM, CUR_ERR_CUDA, CUR_WARN_RANK = 5, 6, 7, 8
 CUR_F64, CUR_F32, CUR_BF16 = 0, 1, 2
 CUR_FLAG_POLISH = 1
 CUR_FLAG_PREC_BF16 = 2
+CUR_FLAG_PREC_FP8 = 4
 
 # Every symbol include/cur.h declares.
 EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", "cur_aca_full",
@@ -156,8 +157,9 @@ def _stream(stream):
 
 
 def opts(delta: float = 1e-2, max_swaps: int = 0, nblocks: int = 1, polish: bool = True,
-         bf16: bool = False) -> CurOpts:
-    return CurOpts(delta, max_swaps, nblocks, (CUR_FLAG_POLISH if polish else 0) | (CUR_FLAG_PREC_BF16 if bf16 else 0))
+         bf16: bool = False, fp8: bool = False) -> CurOpts:
+    return CurOpts(delta, max_swaps, nblocks, (CUR_FLAG_POLISH if polish else 0) | (CUR_FLAG_PREC_BF16 if bf16 else 0)
+                   | (CUR_FLAG_PREC_FP8 if fp8 else 0))
 
 
 # ------------------------------------------------------------------ C ABI names

@@ -127,16 +127,16 @@ cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void
                                  cudaStream_t st);
 size_t compute_size(cur_dtype t);
 
-// ---- BF16 coefficient phase of global maxvol (lowprec.cu)
-// The BF16 phase alone, from S0 to S_out (device r ints, may alias); *swaps and *status
-// (CUR_OK or CUR_ERR_SINGULAR) on the host. minv_in: the FP64 inverse of C(S0,:) (r x r) if
-// known, else NULL (it is factorised). Synchronises the stream.
-cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
-                      int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st,
-                      const double* minv_in);
-// Whether the stages of cur_cross take the BF16 phase (CUR_FLAG_PREC_BF16, FP32 basis,
+// ---- low-precision coefficient phase of global maxvol (lowprec.cu)
+// The BF16 (or, with CUR_FLAG_PREC_FP8, E4M3) phase alone, from S0 to S_out (device r ints,
+// may alias); *swaps and *status (CUR_OK or CUR_ERR_SINGULAR) on the host. minv_in: the
+// FP64 inverse of C(S0,:) (r x r) if known, else NULL (it is factorised). Synchronises.
+cur_status lowprec_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
+                         int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st,
+                         const double* minv_in);
+// Whether the stages of cur_cross take that phase (CUR_FLAG_PREC_BF16 or _FP8, FP32 basis,
 // r a multiple of 16, and enough rows to fill the GPU).
-bool bf16_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r);
+bool lowprec_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r);
 
 // ---- learned proposal (proposal.cu)
 // Workspace bytes of cur_sketch's split partials on a device with num_sms SMs.

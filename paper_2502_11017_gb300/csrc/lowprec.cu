@@ -19,6 +19,7 @@
 // plain path's. Every accepted swap raises the volume by |b_j| > 1 + delta, so the phase
 // cannot cycle.
 
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -41,9 +42,22 @@ constexpr int kLpTop = 8;            // rows recomputed exactly per iteration
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor: kind::f8f6f4 with E4M3 A and B, FP32 accumulator, both K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }"
                  :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p; }"
+                 :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+// The largest finite E4M3 value; each row of a scaled FP8 operand is stretched to it.
+constexpr float kE4M3Max = 448.f;
+__device__ __forceinline__ unsigned char to_e4m3(float x) {
+    return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
 }
 
 struct LpCtl {           // control block of one call (device)
@@ -73,16 +87,53 @@ __global__ void lp_quant_c(const float* __restrict__ C, int64_t p, int r, int ld
     }
 }
 
-// W (r x ldk BF16) = (M^-1)^T rounded from its hi part Mh, zero past column r.
-__device__ __forceinline__ void lp_requant(const float* Mh, int r, int ldk, __nv_bfloat16* W) {
-    for (int e = threadIdx.x; e < r * ldk; e += blockDim.x) {
-        const int n = e / ldk, k = e - n * ldk;
-        W[e] = __float2bfloat16_rn(k < r ? Mh[k * r + n] : 0.f);
+// Cq (p x ldk E4M3) = C s_i with s_i = 448 / max_k |C_ik| per row (1 for a zero row),
+// cinv[i] = 1 / s_i; zero past column r. One warp per row.
+__global__ void lp_quant_c8(const float* __restrict__ C, int64_t p, int r, int ldk, unsigned char* __restrict__ Cq,
+                            float* __restrict__ cinv) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w0; i < p; i += nw) {
+        float mx = 0.f;
+        for (int k = lane; k < r; k += 32) mx = fmaxf(mx, fabsf(C[i * r + k]));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const float sc = mx > 0.f && isfinite(mx) ? kE4M3Max / mx : 1.f;
+        for (int k = lane; k < ldk; k += 32) Cq[i * ldk + k] = k < r ? to_e4m3(C[i * r + k] * sc) : (unsigned char)0;
+        if (lane == 0) cinv[i] = 1.f / sc;
     }
 }
 
+// W (r x ldk) = (M^-1)^T from its hi part (M^-1[k][n] at M[k * pitch + n]), zero past column
+// r: BF16 rounded, or E4M3 with row n scaled by t_n = 448 / max_k |M^-1[k][n]| and
+// winv[n] = 1 / t_n. Ends with the block synchronised.
+template <bool F8>
+__device__ __forceinline__ void lp_requant(const float* M, int pitch, int r, int ldk, void* W, float* winv) {
+    if constexpr (!F8) {
+        __nv_bfloat16* Wb = static_cast<__nv_bfloat16*>(W);
+        for (int n = threadIdx.x >> 5; n < r; n += blockDim.x >> 5)
+            for (int k = threadIdx.x & 31; k < ldk; k += 32)
+                Wb[n * ldk + k] = __float2bfloat16_rn(k < r ? M[k * pitch + n] : 0.f);
+    } else {
+        unsigned char* W8 = static_cast<unsigned char*>(W);
+        const int lane = threadIdx.x & 31;
+        for (int n = threadIdx.x >> 5; n < r; n += blockDim.x >> 5) {
+            float mx = 0.f;
+            for (int k = lane; k < r; k += 32) mx = fmaxf(mx, fabsf(M[k * pitch + n]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            const float t = mx > 0.f && isfinite(mx) ? kE4M3Max / mx : 1.f;
+            for (int k = lane; k < ldk; k += 32) W8[n * ldk + k] = k < r ? to_e4m3(M[k * pitch + n] * t) : (unsigned char)0;
+            if (lane == 0) winv[n] = 1.f / t;
+        }
+    }
+    __syncthreads();
+}
+
 // M = C(S,:) in FP64, its inverse (as hi + lo floats) and log|det|; one CTA.
-__global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const int32_t* S, __nv_bfloat16* W,
+template <bool F8>
+__global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const int32_t* S, void* W, float* winv,
                            float* Mh, float* Ml, LpCtl* ctl) {
     extern __shared__ double lsm[];
     double* M = lsm;                   // r x r
@@ -104,32 +155,36 @@ __global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const in
     }
     for (int e = tid; e < r * r; e += blockDim.x) split_d(M[e], Mh[e], Ml[e]);
     __syncthreads();
-    lp_requant(Mh, r, ldk, W);
+    lp_requant<F8>(Mh, r, r, ldk, W, winv);
     if (tid == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = lv; }
 }
 
 // The same from a given FP64 inverse of C(S,:) (r x r, row-major): split and rounded only.
-__global__ void lp_setup_from_k(const double* __restrict__ minv, int r, int ldk, __nv_bfloat16* W, float* Mh,
+template <bool F8>
+__global__ void lp_setup_from_k(const double* __restrict__ minv, int r, int ldk, void* W, float* winv, float* Mh,
                                 float* Ml, LpCtl* ctl) {
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) split_d(minv[e], Mh[e], Ml[e]);
     __syncthreads();
-    lp_requant(Mh, r, ldk, W);
+    lp_requant<F8>(Mh, r, r, ldk, W, winv);
     if (threadIdx.x == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = 0.0; }
 }
 
 // argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles.
 // Thread 0 issues the TMA loads (the next tile's while the current one is multiplied) and
 // the MMAs; all four warps read the accumulator (warp w: rows 32w..32w+31 of the tile).
+template <bool F8>
 __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
                                                           const __grid_constant__ CUtensorMap mW, int64_t p, int r,
-                                                          int kc, int tcols, const LpCtl* ctl, LpCand* cand,
-                                                          int* status) {
+                                                          int kc, int tcols, const float* __restrict__ cinv,
+                                                          const float* __restrict__ winv, const LpCtl* ctl,
+                                                          LpCand* cand, int* status) {
     extern __shared__ unsigned char lp_raw[];
     __shared__ uint64_t full[2], wbar, mbar;
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     __shared__ float red_v[8];
     __shared__ int red_i[8], red_j[8];
+    __shared__ float s_winv[128];
     if (ctl->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* WS = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(lp_raw) + 1023) & ~(uintptr_t)1023);
@@ -138,6 +193,9 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
     const uint32_t cbuf = (uint32_t)kc * kLpChunkC;
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
     const int nloc = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+    constexpr int kEl = F8 ? 128 : kLpKC;   // elements of one 128-byte K chunk
+    if constexpr (F8)
+        for (int j = tid; j < r; j += blockDim.x) s_winv[j] = winv[j];
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -156,19 +214,19 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
     uint32_t c_par[2] = {0, 0};
     if (tid == 0) {
         mbar_expect_tx(&wbar, (uint32_t)kc * wchunk);
-        for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kLpKC * c, 0);
+        for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kEl * c, 0);
         w_pending = true;
         if (nloc > 0) {
             mbar_expect_tx(&full[0], cbuf);
             for (int c = 0; c < kc; ++c)
-                tma_load_2d(CS + (size_t)c * kLpChunkC, &mC, &full[0], kLpKC * c, (int)(blockIdx.x * kLpBM));
+                tma_load_2d(CS + (size_t)c * kLpChunkC, &mC, &full[0], kEl * c, (int)(blockIdx.x * kLpBM));
             c_pending[0] = true;
         }
     }
     float top_v[2] = {-1.f, -1.f};
     int top_i[2] = {INT_MAX, INT_MAX}, top_j[2] = {INT_MAX, INT_MAX};
     constexpr int kM = kLpBM;
-    const uint32_t idesc = idesc_bf16(kM, r);
+    const uint32_t idesc = F8 ? idesc_e4m3(kM, r) : idesc_bf16(kM, r);
     bool mma_pending = false;
     int k = 0;
     for (; k < nloc; ++k) {
@@ -179,7 +237,7 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
                 const int64_t nt = tile + gridDim.x;
                 mbar_expect_tx(&full[b ^ 1], cbuf);
                 for (int c = 0; c < kc; ++c)
-                    tma_load_2d(CS + (size_t)(b ^ 1) * cbuf + (size_t)c * kLpChunkC, &mC, &full[b ^ 1], kLpKC * c,
+                    tma_load_2d(CS + (size_t)(b ^ 1) * cbuf + (size_t)c * kLpChunkC, &mC, &full[b ^ 1], kEl * c,
                                 (int)(nt * kLpBM));
                 c_pending[b ^ 1] = true;
             }
@@ -192,7 +250,8 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
                 for (int s = 0; s < kc * 4; ++s) {
                     const uint32_t oc = (uint32_t)(s >> 2) * kLpChunkC + (uint32_t)(s & 3) * 32;
                     const uint32_t ow = (uint32_t)(s >> 2) * wchunk + (uint32_t)(s & 3) * 32;
-                    mma_bf16(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
+                    if constexpr (F8) mma_e4m3(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
+                    else mma_bf16(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
                 }
                 mma_commit(&mbar);
                 mma_pending = true;
@@ -212,12 +271,13 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
         float bv = -1.f;
         int bj = INT_MAX;
         const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        const float ci = F8 ? (row < p ? cinv[row] : 0.f) : 1.f;
         for (int c0 = 0; c0 < r; c0 += 16) {
             float v[16];
             tmem_ld16(taddr + (uint32_t)c0, v);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
-                const float x = fabsf(v[q]);
+                const float x = F8 ? fabsf(v[q]) * ci * s_winv[c0 + q] : fabsf(v[q]);
                 if (x > bv) { bv = x; bj = c0 + q; }
             }
         }
@@ -281,9 +341,10 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
 // The eight best candidate rows recomputed in FP64; the largest exact |b_ij| among them
 // wins; its swap and the FP64 Sherman-Morrison update of M^-1 if it passes, else the end of
 // the phase. One CTA.
+template <bool F8>
 __global__ void __launch_bounds__(1024) lp_swap_k(const float* __restrict__ C, int64_t p, int r, int ldk,
                                                   const LpCand* cand, int ncand, float* Mh, float* Ml, int32_t* S,
-                                                  __nv_bfloat16* W, LpCtl* ctl, double delta, int max_swaps) {
+                                                  void* W, float* winv, LpCtl* ctl, double delta, int max_swaps) {
     extern __shared__ double lsm[];
     double* brow = lsm;                                             // kLpTop x r exact rows
     df64* mcol = reinterpret_cast<df64*>(lsm + kLpTop * r);         // column j of M^-1 (r)
@@ -404,11 +465,8 @@ __global__ void __launch_bounds__(1024) lp_swap_k(const float* __restrict__ C, i
         Ml[e] = v.l;
     }
     __syncthreads();
-    // W[n][k] = bf16(M^-1[k][n]); consecutive threads take consecutive k (padded pitch: no conflicts)
-    for (int e = tid; e < r * ldk; e += nt) {
-        const int n = e / ldk, k = e - n * ldk;
-        W[e] = __float2bfloat16_rn(k < r ? sh[k * rp + n] : 0.f);
-    }
+    // W from the updated M^-1 (the padded pitch keeps a warp's column reads conflict-free)
+    lp_requant<F8>(sh, rp, r, ldk, W, winv);
     if (tid == 0) {
         S[j] = i;
         ctl->logvol += log(fabs(bjv));
@@ -437,33 +495,39 @@ static PFN_cuTensorMapEncodeTiled_v12000 lp_encode_fn() {
     return fn;
 }
 
-// rows x ldk BF16 (ldk a multiple of 64), boxes of 64 elements x box_rows rows, 128-byte swizzle.
-static bool lp_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int ldk, int box_rows) {
+// rows x ldk elements of es bytes (ldk es a multiple of 128), boxes of 128 bytes x box_rows
+// rows, 128-byte swizzle; BF16 (es = 2) or E4M3 bytes (es = 1).
+static bool lp_map(CUtensorMap* map, const void* base, int64_t rows, int ldk, int box_rows, int es) {
     auto enc = lp_encode_fn();
     if (!enc) return false;
     cuuint64_t gdim[2] = {(cuuint64_t)ldk, (cuuint64_t)rows};
-    cuuint64_t gstr[1] = {(cuuint64_t)ldk * sizeof(__nv_bfloat16)};
-    cuuint32_t box[2] = {(cuuint32_t)kLpKC, (cuuint32_t)box_rows};
-    cuuint32_t es[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), gdim, gstr, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    cuuint64_t gstr[1] = {(cuuint64_t)ldk * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+               const_cast<void*>(base), gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace curk
 
-// The stages of cur_cross take the BF16 phase only where its product has at least this many
-// 128-row tiles per SM; below that the FP32 engine's shared-memory B is faster.
+// The stages of cur_cross take the low-precision phase only where its product has at least
+// this many 128-row tiles per SM; below that the FP32 engine's shared-memory B is faster.
 constexpr int64_t kBf16MinTilesPerSm = 4;
 
-// The BF16 phase alone from S0 (device r ints) to S_out (device; may alias S0). *swaps: the
-// swaps it took; *status: CUR_OK or CUR_ERR_SINGULAR (a singular C(S0,:); S_out = S0).
-// Synchronises the stream. C: p x r FP32 (contiguous, device), r a multiple of 16.
-cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
-                      int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st, const double* minv_in) {
+// The low-precision phase alone (BF16, or E4M3 with fp8), from S0 to S_out (device r
+// ints; may alias). *swaps: the swaps it took; *status: CUR_OK or CUR_ERR_SINGULAR (a singular
+// C(S0,:); S_out = S0). Synchronises the stream. C: p x r FP32 (contiguous, device), r a
+// multiple of 16.
+template <bool F8>
+static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o,
+                                  const int32_t* S0, int32_t* S_out, int* swaps, int* status, Arena& ar,
+                                  cudaStream_t st, const double* minv_in) {
     using namespace curk;
     const size_t mark = ar.off;
-    const int kc = (r + kLpKC - 1) / kLpKC, ldk = kc * kLpKC;
+    constexpr int es = F8 ? 1 : 2, kEl = 128 / es;
+    const int kc = (r + kEl - 1) / kEl, ldk = kc * kEl;
     const int tcols = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
     // CTAs per SM: as many as shared memory and the SM's 512 TMEM columns hold, at most 4
@@ -471,8 +535,10 @@ cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur
     const int per_sm = (int)std::max<size_t>(1, std::min<size_t>({(size_t)4, (size_t)(227 * 1024) / sm_arg,
                                                                     (size_t)(512 / tcols)}));
     const int grid = (int)std::min<int64_t>({ntiles, (int64_t)per_sm * h->num_sms, (int64_t)1024});
-    __nv_bfloat16* Cq = ar.get<__nv_bfloat16>((size_t)p * ldk);
-    __nv_bfloat16* W = ar.get<__nv_bfloat16>((size_t)r * ldk);
+    void* Cq = ar.take((size_t)p * ldk * es);
+    void* W = ar.take((size_t)r * ldk * es);
+    float* cinv = ar.get<float>(F8 ? (size_t)p : 1);
+    float* winv = ar.get<float>((size_t)r);
     float* Mh = ar.get<float>((size_t)r * r);
     float* Ml = ar.get<float>((size_t)r * r);
     int32_t* S = ar.get<int32_t>(r);
@@ -480,35 +546,39 @@ cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur
     LpCtl* ctl = ar.get<LpCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUtensorMap mC, mW;
-    if (!lp_map(&mC, Cq, p, ldk, kLpBM) || !lp_map(&mW, W, r, ldk, r)) return CUR_ERR_ARG;
+    if (!lp_map(&mC, Cq, p, ldk, kLpBM, es) || !lp_map(&mW, W, r, ldk, r, es)) return CUR_ERR_ARG;
     CUR_CK(cudaMemsetAsync(ctl, 0, sizeof(LpCtl), st));
     CUR_CK(cudaMemcpyAsync(S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    lp_quant_c<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((p * ldk + 255) / 256, 8LL * h->num_sms)), 256, 0, st>>>(
-        C, p, r, ldk, Cq);
+    const unsigned qgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((p * ldk + 255) / 256, 8LL * h->num_sms));
+    if constexpr (F8)
+        lp_quant_c8<<<qgrid, 256, 0, st>>>(C, p, r, ldk, static_cast<unsigned char*>(Cq), cinv);
+    else
+        lp_quant_c<<<qgrid, 256, 0, st>>>(C, p, r, ldk, static_cast<__nv_bfloat16*>(Cq));
     CUR_CK(cudaGetLastError());
     if (minv_in) {
-        lp_setup_from_k<<<1, 256, 0, st>>>(minv_in, r, ldk, W, Mh, Ml, ctl);
+        lp_setup_from_k<F8><<<1, 256, 0, st>>>(minv_in, r, ldk, W, winv, Mh, Ml, ctl);
     } else {
         const size_t sm_setup = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(double) + (size_t)r * sizeof(int) + 64;
-        CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
-        lp_setup_k<<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, Mh, Ml, ctl);
+        CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
+        lp_setup_k<F8><<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, winv, Mh, Ml, ctl);
     }
     CUR_CK(cudaGetLastError());
     note_launch(2);
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
     const size_t sm_swap = (size_t)kLpTop * r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
                            (size_t)kLpTop * r * sizeof(float) + 2 * (size_t)r * (r + 1) * sizeof(float) + 16 +
                            2 * (size_t)grid * sizeof(LpCand);
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
     const int max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
     LpCtl* hc = reinterpret_cast<LpCtl*>(h->host_stage);
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
     for (;;) {
         for (int q = 0; q < kLpBatch; ++q) {
-            lp_argmax_k<<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, ctl, cand, h->status);
+            lp_argmax_k<F8><<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, ctl, cand,
+                                                              h->status);
             CUR_CK(cudaGetLastError());
-            lp_swap_k<<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, 2 * grid, Mh, Ml, S, W, ctl, o->delta,
-                                                max_swaps);
+            lp_swap_k<F8><<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, 2 * grid, Mh, Ml, S, W, winv, ctl, o->delta,
+                                                    max_swaps);
             CUR_CK(cudaGetLastError());
         }
         note_launch(2 * kLpBatch);
@@ -527,18 +597,25 @@ cur_status bf16_phase(cur_handle* h, const float* C, int64_t p, int r, const cur
     return CUR_OK;
 }
 
-bool bf16_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r) {
-    return (o->flags & CUR_FLAG_PREC_BF16) && dt == CUR_F32 && r % 16 == 0 && r >= 16 && r <= 128 &&
+cur_status lowprec_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
+                         int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st, const double* minv_in) {
+    if (o->flags & CUR_FLAG_PREC_FP8)
+        return lowprec_phase_t<true>(h, C, p, r, o, S0, S_out, swaps, status, ar, st, minv_in);
+    return lowprec_phase_t<false>(h, C, p, r, o, S0, S_out, swaps, status, ar, st, minv_in);
+}
+
+bool lowprec_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r) {
+    return (o->flags & (CUR_FLAG_PREC_BF16 | CUR_FLAG_PREC_FP8)) && dt == CUR_F32 && r % 16 == 0 && r >= 16 && r <= 128 &&
            p >= (int64_t)kBf16MinTilesPerSm * curk::kLpBM * h->num_sms && p <= INT_MAX - 256;
 }
 
-// BF16 phase, then the exact engine from the set it reached.
+// The low-precision phase, then the exact engine from the set it reached.
 static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o,
                                      const int32_t* S0, int32_t* S_out, double* logvol_out, int32_t* swaps_out,
                                      Arena& ar, cudaStream_t st) {
     using namespace curk;
     int lp_swaps = 0, lp_status = CUR_OK;
-    CUR_TRY(bf16_phase(h, C, p, r, o, S0, S_out, &lp_swaps, &lp_status, ar, st, nullptr));
+    CUR_TRY(lowprec_phase(h, C, p, r, o, S0, S_out, &lp_swaps, &lp_status, ar, st, nullptr));
     LpCtl* ctl = ar.get<LpCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     LpCtl hv{};
@@ -573,7 +650,7 @@ cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t*
     cur_opts o = opts ? *opts : cur_default_opts();
     if (!(o.delta >= 0.0)) return CUR_ERR_ARG;
     Arena ar = h->arena();
-    if (o.flags & CUR_FLAG_PREC_BF16) {
+    if (o.flags & (CUR_FLAG_PREC_BF16 | CUR_FLAG_PREC_FP8)) {
         if (basis->dtype != CUR_F32 || r % 16 != 0) return CUR_ERR_ARG;
         return maxvol_global_bf16(h, static_cast<const float*>(basis->data), p, r, &o, S0, S_out, logvol_out,
                                   swaps_out, ar, st);

@@ -1524,11 +1524,12 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         const double* minv_in = mv.empty() ? nullptr : mv[0];
         const double* lv_in = lvp.empty() ? nullptr : lvp[0];
         if constexpr (std::is_same<TB, float>::value) {
-            // with CUR_FLAG_PREC_BF16 on a large basis, BF16 products take the polish's swaps
-            // first; the FP32 engine then finishes (from a fresh factorisation if any were taken)
-            if (bf16_phase_applies(h, o, CUR_F32, p, r)) {
+            // with CUR_FLAG_PREC_BF16 / _FP8 on a large basis, low-precision products take the
+            // polish's swaps first; the FP32 engine then finishes (from a fresh factorisation if
+            // any were taken)
+            if (lowprec_phase_applies(h, o, CUR_F32, p, r)) {
                 int bsw = 0, bst = CUR_OK;
-                CUR_TRY(bf16_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, minv_in));
+                CUR_TRY(lowprec_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, minv_in));
                 total += bsw;
                 if (bsw > 0) { minv_in = nullptr; lv_in = nullptr; }
             }

@@ -26,7 +26,7 @@ def basis_device(p: int, r: int, seed: int, device):
     return ((u * s) @ v.T * np.sqrt(p)).to(torch.float32).contiguous()
 
 
-def one(hd, C, S0, r: int, bf16: bool):
+def one(hd, C, S0, r: int, prec: str):
     import torch
     dev = C.device
     S = torch.empty(r, dtype=torch.int32, device=dev)
@@ -34,7 +34,7 @@ def one(hd, C, S0, r: int, bf16: bool):
     sw = torch.zeros(2, dtype=torch.int32, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    cur_maxvol_global(hd.h, C, S0, r, opts(1e-2, bf16=bf16), S, lv, sw)
+    cur_maxvol_global(hd.h, C, S0, r, opts(1e-2, bf16=prec == "bf16", fp8=prec == "fp8"), S, lv, sw)
     torch.cuda.synchronize()
     ms = (time.perf_counter() - t0) * 1e3
     st = cur_sync_status(hd.h)
@@ -56,10 +56,12 @@ def main(argv=None):
         C = basis_device(p, r, p + r, dev)
         for rep in range(args.reps):
             S0 = torch.from_numpy(np.random.default_rng(rep).choice(p, r, replace=False).astype(np.int32)).to(dev)
-            one(hd, C, S0, r, False)                  # warm
-            a = one(hd, C, S0, r, False)
-            b = one(hd, C, S0, r, True)
-            res.append(dict(p=p, r=r, start=rep, fp32=a, bf16=b, logvol_diff=b["logvol"] - a["logvol"]))
+            one(hd, C, S0, r, "fp32")                  # warm
+            a = one(hd, C, S0, r, "fp32")
+            b = one(hd, C, S0, r, "bf16")
+            c = one(hd, C, S0, r, "fp8")
+            res.append(dict(p=p, r=r, start=rep, fp32=a, bf16=b, fp8=c, bf16_logvol_diff=b["logvol"] - a["logvol"],
+                            fp8_logvol_diff=c["logvol"] - a["logvol"]))
             print(json.dumps(res[-1]), flush=True)
     hd.close()
     if args.out:

@@ -1,6 +1,7 @@
 """Parity of cur_maxvol_global (maxvol over all rows of a basis from a given start) with the
-oracle's maxvol, on the FP32/FP64 engine and with the BF16 coefficient phase
-(CUR_FLAG_PREC_BF16: tcgen05 BF16 products, each winner recomputed exactly before its swap).
+oracle's maxvol, on the FP32/FP64 engine and with the low-precision coefficient phases
+(CUR_FLAG_PREC_BF16 / CUR_FLAG_PREC_FP8: tcgen05 BF16 or row-scaled E4M3 products, each
+winner recomputed exactly before its swap).
 
 The bar: the oracle's set, or else a volume within 0.999 of it; in both cases the GPU's set
 is (1 + delta)-dominant when its coefficients are evaluated in FP64, and the reported
@@ -41,12 +42,12 @@ def basis(p, r, seed):
     return ((u * np.exp(-5.0 * np.arange(r) / r)) @ v.T * np.sqrt(p)).astype(np.float32)
 
 
-def run(hd, C, S0, r, bf16):
+def run(hd, C, S0, r, prec):
     S = torch.empty(r, dtype=torch.int32, device=DEV)
     lv = torch.empty(1, dtype=torch.float64, device=DEV)
     sw = torch.zeros(2, dtype=torch.int32, device=DEV)
     cur.cur_maxvol_global(hd.h, torch.from_numpy(C).to(DEV), torch.tensor(S0, dtype=torch.int32, device=DEV), r,
-                          cur.opts(DELTA, bf16=bf16), S, lv, sw)
+                          cur.opts(DELTA, bf16=prec == "bf16", fp8=prec == "fp8"), S, lv, sw)
     st = cur.cur_sync_status(hd.h)
     return S.tolist(), lv.item(), sw.tolist(), st
 
@@ -54,25 +55,30 @@ def run(hd, C, S0, r, bf16):
 CASES = [(5000, 16, 1), (20000, 64, 2), (3001, 128, 3), (1000, 32, 4), (200, 48, 5), (65536, 64, 6)]
 
 
-@pytest.mark.parametrize("bf16", [False, True])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 @pytest.mark.parametrize("p,r,seed", CASES)
-def test_maxvol_global_matches_oracle(hd, p, r, seed, bf16):
+def test_maxvol_global_matches_oracle(hd, p, r, seed, prec):
     C = basis(p, r, seed)
     C64 = C.astype(np.float64)
     S0 = np.random.default_rng(seed + 100).choice(p, r, replace=False).tolist()
-    S, lv, sw, st = run(hd, C, S0, r, bf16)
+    S, lv, sw, st = run(hd, C, S0, r, prec)
     So, lvo, _swo, sto = orc.maxvol(C64, S0, DELTA)
     assert st == cur.CUR_OK and sto == orc.OK
     assert len(set(S)) == r
     lv_set = orc.logvol(C64[S, :])
     assert lv == pytest.approx(lv_set, abs=1e-6 * max(1.0, abs(lv_set)))
-    if sorted(S) != sorted(So):
+    if prec == "fp8":
+        # E4M3 products (relative error 2^-4) reorder the candidates, so the swap path and
+        # the local maximum reached differ from the oracle's; the set is still dominant and
+        # its volume is within a small factor (reported, not a parity claim)
+        assert abs(lv_set - lvo) <= 0.1 * abs(lvo)
+    elif sorted(S) != sorted(So):
         assert lv_set >= lvo + math.log(0.999)
     B = C64 @ np.linalg.inv(C64[S, :])
     assert np.abs(B).max() <= (1 + DELTA) * (1 + 1e-4)
     assert sw[0] >= sw[1] >= 0
-    if bf16:
-        assert sw[1] > 0                 # the BF16 phase made swaps of its own
+    if prec != "fp32":
+        assert sw[1] > 0                 # the low-precision phase made swaps of its own
     else:
         assert sw[1] == 0
 
@@ -80,16 +86,17 @@ def test_maxvol_global_matches_oracle(hd, p, r, seed, bf16):
 def test_bf16_phase_on_a_converged_set_swaps_nothing(hd):
     C = basis(4000, 32, 7)
     S0 = np.random.default_rng(7).choice(4000, 32, replace=False).tolist()
-    S, _lv, _sw, _ = run(hd, C, S0, 32, False)
-    S2, _lv2, sw2, st = run(hd, C, S, 32, True)
-    assert st == cur.CUR_OK and sorted(S2) == sorted(S) and sw2 == [0, 0]
+    S, _lv, _sw, _ = run(hd, C, S0, 32, "fp32")
+    for prec in ("bf16", "fp8"):
+        S2, _lv2, sw2, st = run(hd, C, S, 32, prec)
+        assert st == cur.CUR_OK and sorted(S2) == sorted(S) and sw2 == [0, 0]
 
 
 def test_singular_start_is_reported(hd):
     C = basis(1000, 16, 8)
     S0 = [3, 3] + list(range(10, 24))
-    for bf16 in (False, True):
-        S, lv, sw, st = run(hd, C, S0, 16, bf16)
+    for prec in ("fp32", "bf16", "fp8"):
+        S, lv, sw, st = run(hd, C, S0, 16, prec)
         assert st == cur.CUR_ERR_SINGULAR and S == S0 and sw[0] == 0
 
 
@@ -112,19 +119,22 @@ def test_row_selection_with_bf16_polish_matches_oracle(hd):
     J0 = torch.empty(r, dtype=torch.int32, device=DEV)
     cur.cur_aca_select(hd.h, A, 1, r, 1, J0)
     I = {}
-    for bf16 in (False, True):
+    for prec in ("fp32", "bf16", "fp8"):
         out = torch.empty(r, dtype=torch.int32, device=DEV)
         lv = torch.empty(1, dtype=torch.float64, device=DEV)
-        cur.cur_maxvol_rows(hd.h, A, J0, r, cur.opts(DELTA, nblocks=b_r, bf16=bf16), out, lv)
+        cur.cur_maxvol_rows(hd.h, A, J0, r, cur.opts(DELTA, nblocks=b_r, bf16=prec == "bf16", fp8=prec == "fp8"),
+                            out, lv)
         assert cur.cur_sync_status(hd.h) == cur.CUR_OK
-        I[bf16] = (out.tolist(), lv.item())
+        I[prec] = (out.tolist(), lv.item())
     Jl = J0.tolist()
     Io, lvo, _sw, st, _ = orc.maxvol_rows(a, Jl, b_r, DELTA)
     assert st == orc.OK
     Cb = a[:, Jl].astype(np.float64)
-    for bf16, (Il, lv) in I.items():
+    for prec, (Il, lv) in I.items():
         lv_set = orc.logvol(Cb[Il, :])
         assert lv == pytest.approx(lv_set, abs=1e-6 * max(1.0, abs(lv_set)))
-        if sorted(Il) != sorted(Io):
+        if prec == "fp8":
+            assert abs(lv_set - lvo) <= 0.1 * abs(lvo)
+        elif sorted(Il) != sorted(Io):
             assert lv_set >= lvo + math.log(0.999)
         assert np.abs(Cb @ np.linalg.inv(Cb[Il, :])).max() <= (1 + DELTA) * (1 + 1e-4)
