@@ -4,13 +4,13 @@
 // Each iteration forms B = C M^-1 for all p rows of the basis as a BF16 x BF16 -> FP32
 // tcgen05 GEMM (C and M^-1 rounded to BF16 once; TMA-staged 128-row tiles of C, M^-1^T
 // resident in shared memory, the accumulator in TMEM) and reduces argmax |B_ij| in the
-// epilogue, without writing B (each CTA keeps its two best rows). The eight best rows of all
-// CTAs are then recomputed exactly, b = C(i,:) M^-1 with M^-1 held as a double-float pair
-// (hi + lo floats, about 2^-48 relative), the products formed by the error-free Dot2 sums on
-// the FP32 pipes and read out in FP64 (GB300's FP64 rate is a small fraction of its FP32
-// rate, so FP64-class arithmetic runs on the FP32 pipes, as in the swap engine), the
-// largest exact |b_j| among
-// them is the winner (the exact argmax unless rounding pushed its row below eight others),
+// epilogue, without writing B. Each CTA then recomputes the entries of its two best rows
+// exactly, b_ij = C(i,:) M^-1(:,j) with M^-1 held as a double-float pair (hi + lo floats,
+// about 2^-48 relative), the products formed by the error-free Dot2 sums on the FP32 pipes
+// and read out in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate, so
+// FP64-class arithmetic runs on the FP32 pipes, as in the swap engine); the row of the
+// largest exact entry over all CTAs is recomputed in full and its largest entry is the
+// winner (the exact argmax unless rounding pushed it below its CTA's two best rows),
 // and the swap is taken only if |b_j| > 1 + delta; M^-1 gets its Sherman-Morrison
 // update in double-float and is rounded to BF16 again for the next product. The start is
 // factorised in FP64. The first winner whose
@@ -36,7 +36,6 @@ constexpr int kLpKC = 64;            // BF16 elements per 128-byte swizzled K ch
 constexpr int kLpChunkC = kLpBM * 128;  // bytes of one K chunk of a C tile
 constexpr int kLpThreads = 128;
 constexpr int kLpBatch = 16;         // iterations launched between two reads of the control block
-constexpr int kLpTop = 8;            // rows recomputed exactly per iteration
 
 // Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -68,9 +67,9 @@ struct LpCtl {           // control block of one call (device)
     double logvol;       // log|det C(S,:)|
 };
 
-struct LpCand {          // a row's largest |B_ij| (approximate); two per CTA
-    float v;
-    int i, j, pad;
+struct LpCand {          // a CTA's largest exact |b_ij| over its two candidate entries (-1: none)
+    double v;
+    int i, j;
 };
 
 __device__ __forceinline__ bool lp_better(float v, int i, int j, float v2, int i2, int j2) {
@@ -176,8 +175,9 @@ template <bool F8>
 __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
                                                           const __grid_constant__ CUtensorMap mW, int64_t p, int r,
                                                           int kc, int tcols, const float* __restrict__ cinv,
-                                                          const float* __restrict__ winv, const LpCtl* ctl,
-                                                          LpCand* cand, int* status) {
+                                                          const float* __restrict__ winv, const float* __restrict__ C,
+                                                          const float* __restrict__ Mh, const float* __restrict__ Ml,
+                                                          const LpCtl* ctl, LpCand* cand, int* status) {
     extern __shared__ unsigned char lp_raw[];
     __shared__ uint64_t full[2], wbar, mbar;
     __shared__ uint32_t tslot;
@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
     __shared__ float red_v[8];
     __shared__ int red_i[8], red_j[8];
     __shared__ float s_winv[128];
+    __shared__ int s_rows[2], s_cols[2];
+    __shared__ double s_ev[4];
+    __shared__ int s_ei[4], s_ej[4];
     if (ctl->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* WS = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(lp_raw) + 1023) & ~(uintptr_t)1023);
@@ -321,14 +324,48 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
                 if (c_pending[s]) mbar_wait(&full[s], c_par[s]);
             top_v[0] = top_v[1] = -1.f;
         }
-        for (int q = 0; q < 2; ++q) {
-            LpCand c;
-            c.v = top_v[q];
-            c.i = top_i[q];
-            c.j = top_j[q];
-            c.pad = 0;
-            cand[2 * blockIdx.x + q] = c;
-        }
+        s_rows[0] = top_v[0] >= 0.f ? top_i[0] : -1;
+        s_rows[1] = top_v[1] >= 0.f ? top_i[1] : -1;
+        s_cols[0] = top_j[0];
+        s_cols[1] = top_j[1];
+    }
+    __syncthreads();
+    // the exact value of each candidate entry, b_ij = C(i,:) M^-1(:,j) with M^-1 as hi + lo
+    // floats (one warp per entry, Dot2 partial sums per lane, double-float warp reduction)
+    double ev = -1.0;
+    int ei = INT_MAX, ej = INT_MAX;
+    if (warp < 2 && s_rows[warp] >= 0) {
+        const int row = s_rows[warp], col = s_cols[warp];
+        const float* a = C + (int64_t)row * r;
+        Dot2 d;
+        for (int l = lane; l < r; l += 32) d.add(__ldg(a + l), Mh[l * r + col], Ml[l * r + col]);
+        df64 v = fast_two_sum(d.s, d.c);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            v = df_add(v, df64{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+        ev = fabs(df_to_d(v));
+        ei = row;
+        ej = col;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, ev, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, ei, o);
+        const int j2 = __shfl_xor_sync(0xffffffffu, ej, o);
+        if (v2 > ev || (v2 == ev && (i2 < ei || (i2 == ei && j2 < ej)))) { ev = v2; ei = i2; ej = j2; }
+    }
+    if (lane == 0) { s_ev[warp] = ev; s_ei[warp] = ei; s_ej[warp] = ej; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < 4; ++w)
+            if (s_ev[w] > ev || (s_ev[w] == ev && (s_ei[w] < ei || (s_ei[w] == ei && s_ej[w] < ej)))) {
+                ev = s_ev[w]; ei = s_ei[w]; ej = s_ej[w];
+            }
+        LpCand c;
+        c.v = ev;
+        c.i = ei;
+        c.j = ej;
+        cand[blockIdx.x] = c;
     }
     tc_fence_before();
     __syncthreads();
@@ -338,113 +375,90 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
     }
 }
 
-// The eight best candidate rows recomputed in FP64; the largest exact |b_ij| among them
-// wins; its swap and the FP64 Sherman-Morrison update of M^-1 if it passes, else the end of
-// the phase. One CTA.
+// The winner of the CTAs' exact candidates; its swap and the double-float Sherman-Morrison
+// update of M^-1 if it passes, else the end of the phase. One CTA.
 template <bool F8>
 __global__ void __launch_bounds__(1024) lp_swap_k(const float* __restrict__ C, int64_t p, int r, int ldk,
                                                   const LpCand* cand, int ncand, float* Mh, float* Ml, int32_t* S,
                                                   void* W, float* winv, LpCtl* ctl, double delta, int max_swaps) {
     extern __shared__ double lsm[];
-    double* brow = lsm;                                             // kLpTop x r exact rows
-    df64* mcol = reinterpret_cast<df64*>(lsm + kLpTop * r);         // column j of M^-1 (r)
+    double* b = lsm;                                                // exact row i of B (r)
+    df64* mcol = reinterpret_cast<df64*>(lsm + r);                  // column j of M^-1 (r)
     df64* g = mcol + r;                                             // (b - e_j) / b_j (r)
-    float* crow = reinterpret_cast<float*>(g + r);                  // the kLpTop rows of C
     const int rp = r + 1;                                           // padded row pitch of M^-1
-    float* sh = crow + kLpTop * r;                                  // M^-1 hi, r x rp
+    float* sh = reinterpret_cast<float*>(g + r);                    // M^-1 hi, r x rp
     float* sl = sh + r * rp;                                        // M^-1 lo, r x rp
-    unsigned long long* ckey = reinterpret_cast<unsigned long long*>(sl + r * rp + 4 - ((r * rp) & 3));
-    __shared__ int rows[kLpTop];
-    __shared__ int nsel, si, sj, st;
-    __shared__ unsigned long long wbest[32], kbest;
+    __shared__ double wv[32];
+    __shared__ int wi[32], wj[32];
+    __shared__ int si, sj;
+    __shared__ double sv;
     if (ctl->done) return;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    for (int l = warp; l < r; l += nt >> 5)
+        for (int c = lane; c < r; c += 32) {
+            sh[l * rp + c] = Mh[l * r + c];
+            sl[l * rp + c] = Ml[l * r + c];
+        }
+    double bv = -1.0;
+    int bi = INT_MAX, bj = INT_MAX;
     for (int c = tid; c < ncand; c += nt) {
         const LpCand x = cand[c];
-        ckey[c] = x.v >= 0.f ? ((unsigned long long)__float_as_uint(x.v) << 32) |
-                                   (unsigned long long)(0xffffffffu - (unsigned)x.i)
-                             : 0ull;
+        if (x.v > bv || (x.v == bv && (x.i < bi || (x.i == bi && x.j < bj)))) { bv = x.v; bi = x.i; bj = x.j; }
     }
-    if (tid == 0) nsel = 0;
-    for (int e = tid; e < r * r; e += nt) {
-        const int l = e / r, c = e - l * r;
-        sh[l * rp + c] = Mh[e];
-        sl[l * rp + c] = Ml[e];
-    }
-    __syncthreads();
-    // the kLpTop best candidates: kLpTop rounds of a block-wide maximum of order-preserving
-    // keys (|B| bits, then the lower row; the value is non-negative, so its bits order it);
-    // the winner's key is cleared before the next round
-    for (int t = 0; t < kLpTop; ++t) {
-        unsigned long long best = 0ull;
-        for (int c = tid; c < ncand; c += nt) best = ckey[c] > best ? ckey[c] : best;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
-            best = y > best ? y : best;
-        }
-        if ((tid & 31) == 0) wbest[tid >> 5] = best;
-        __syncthreads();
-        if (tid < 32) {
-            unsigned long long b2 = tid < (nt >> 5) ? wbest[tid] : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, b2, o);
-                b2 = y > b2 ? y : b2;
-            }
-            if (tid == 0) {
-                kbest = b2;
-                if (b2 != 0ull) { rows[t] = (int)(0xffffffffu - (unsigned)(b2 & 0xffffffffull)); nsel = t + 1; }
-            }
-        }
-        __syncthreads();
-        const unsigned long long kb = kbest;
-        if (kb == 0ull) break;
-        for (int c = tid; c < ncand; c += nt)
-            if (ckey[c] == kb) ckey[c] = 0ull;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (v2 > bv || (v2 == bv && (i2 < bi || (i2 == bi && j2 < bj)))) { bv = v2; bi = i2; bj = j2; }
     }
-    __syncthreads();
-    const int ns = nsel;
-    if (ns == 0) {
-        if (tid == 0) ctl->done = 1;
-        return;
-    }
-    for (int e = tid; e < ns * r; e += nt) {
-        const int t = e / r, l = e - t * r;
-        crow[e] = C[(int64_t)rows[t] * r + l];
-    }
-    __syncthreads();
-    for (int e = tid; e < ns * r; e += nt) {
-        const int t = e / r, c = e - t * r;
-        const float* a = crow + t * r;
-        Dot2 d;
-#pragma unroll 8
-        for (int l = 0; l < r; ++l) d.add(a[l], sh[l * rp + c], sl[l * rp + c]);
-        brow[e] = d.value();
-    }
+    if (lane == 0) { wv[warp] = bv; wi[warp] = bi; wj[warp] = bj; }
     __syncthreads();
     if (tid < 32) {
-        double bv = -1.0;
-        int bi = INT_MAX, bj = INT_MAX, bt = -1;
-        for (int e = tid; e < ns * r; e += 32) {
-            const int t = e / r, c = e - t * r;
-            const double x = fabs(brow[e]);
-            const int i = rows[t];
-            if (x > bv || (x == bv && (i < bi || (i == bi && c < bj)))) { bv = x; bi = i; bj = c; bt = t; }
-        }
+        bv = tid < (nt >> 5) ? wv[tid] : -1.0;
+        bi = tid < (nt >> 5) ? wi[tid] : INT_MAX;
+        bj = tid < (nt >> 5) ? wj[tid] : INT_MAX;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
             const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
             const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
-            const int t2 = __shfl_xor_sync(0xffffffffu, bt, o);
-            if (v2 > bv || (v2 == bv && (i2 < bi || (i2 == bi && j2 < bj)))) { bv = v2; bi = i2; bj = j2; bt = t2; }
+            if (v2 > bv || (v2 == bv && (i2 < bi || (i2 == bi && j2 < bj)))) { bv = v2; bi = i2; bj = j2; }
         }
-        if (tid == 0) { si = bi; sj = bj; st = bt; }
+        if (tid == 0) { sv = bv; si = bi; sj = bj; }
     }
     __syncthreads();
-    const int i = si, j = sj;
-    const double* b = brow + (size_t)st * r;
+    const int i = si;
+    if (!(sv >= 0.0) || i < 0 || (int64_t)i >= p) {
+        if (tid == 0) ctl->done = 1;
+        return;
+    }
+    // the winner's row, exactly, and its largest entry (lowest column on ties)
+    for (int c = tid; c < r; c += nt) {
+        const float* a = C + (int64_t)i * r;
+        Dot2 d;
+#pragma unroll 4
+        for (int l = 0; l < r; ++l) d.add(a[l], sh[l * rp + c], sl[l * rp + c]);
+        b[c] = d.value();
+    }
+    __syncthreads();
+    if (tid < 32) {
+        double bv2 = -1.0;
+        int bj2 = INT_MAX;
+        for (int c = tid; c < r; c += 32) {
+            const double x = fabs(b[c]);
+            if (x > bv2) { bv2 = x; bj2 = c; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v2 = __shfl_xor_sync(0xffffffffu, bv2, o);
+            const int j2 = __shfl_xor_sync(0xffffffffu, bj2, o);
+            if (v2 > bv2 || (v2 == bv2 && j2 < bj2)) { bv2 = v2; bj2 = j2; }
+        }
+        if (tid == 0) sj = bj2;
+    }
+    __syncthreads();
+    const int j = sj;
     const double bjv = b[j];
     if (!(fabs(bjv) > 1.0 + delta)) {
         if (tid == 0) ctl->done = 1;
@@ -452,18 +466,17 @@ __global__ void __launch_bounds__(1024) lp_swap_k(const float* __restrict__ C, i
     }
     if (tid < r) {
         mcol[tid] = df_make(sh[tid * rp + j], sl[tid * rp + j]);
-        const df64 bjd = df_from_d(bjv);
-        g[tid] = df_div(df_from_d(b[tid] - (tid == j ? 1.0 : 0.0)), bjd);
+        g[tid] = df_div(df_from_d(b[tid] - (tid == j ? 1.0 : 0.0)), df_from_d(bjv));
     }
     __syncthreads();
-    for (int e = tid; e < r * r; e += nt) {
-        const int l = e / r, c = e - l * r;
-        const df64 v = df_sub(df_make(sh[l * rp + c], sl[l * rp + c]), df_mul(mcol[l], g[c]));
-        sh[l * rp + c] = v.h;
-        sl[l * rp + c] = v.l;
-        Mh[e] = v.h;
-        Ml[e] = v.l;
-    }
+    for (int l = warp; l < r; l += nt >> 5)
+        for (int c = lane; c < r; c += 32) {
+            const df64 v = df_sub(df_make(sh[l * rp + c], sl[l * rp + c]), df_mul(mcol[l], g[c]));
+            sh[l * rp + c] = v.h;
+            sl[l * rp + c] = v.l;
+            Mh[l * r + c] = v.h;
+            Ml[l * r + c] = v.l;
+        }
     __syncthreads();
     // W from the updated M^-1 (the padded pitch keeps a warp's column reads conflict-free)
     lp_requant<F8>(sh, rp, r, ldk, W, winv);
@@ -542,7 +555,7 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     float* Mh = ar.get<float>((size_t)r * r);
     float* Ml = ar.get<float>((size_t)r * r);
     int32_t* S = ar.get<int32_t>(r);
-    LpCand* cand = ar.get<LpCand>(2 * (size_t)grid);
+    LpCand* cand = ar.get<LpCand>((size_t)grid);
     LpCtl* ctl = ar.get<LpCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUtensorMap mC, mW;
@@ -565,19 +578,18 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     CUR_CK(cudaGetLastError());
     note_launch(2);
     CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
-    const size_t sm_swap = (size_t)kLpTop * r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
-                           (size_t)kLpTop * r * sizeof(float) + 2 * (size_t)r * (r + 1) * sizeof(float) + 16 +
-                           2 * (size_t)grid * sizeof(LpCand);
+    const size_t sm_swap = (size_t)r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
+                           2 * (size_t)r * (r + 1) * sizeof(float) + 16;
     CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
     const int max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
     LpCtl* hc = reinterpret_cast<LpCtl*>(h->host_stage);
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
     for (;;) {
         for (int q = 0; q < kLpBatch; ++q) {
-            lp_argmax_k<F8><<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, ctl, cand,
-                                                              h->status);
+            lp_argmax_k<F8><<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml, ctl,
+                                                              cand, h->status);
             CUR_CK(cudaGetLastError());
-            lp_swap_k<F8><<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, 2 * grid, Mh, Ml, S, W, winv, ctl, o->delta,
+            lp_swap_k<F8><<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, grid, Mh, Ml, S, W, winv, ctl, o->delta,
                                                     max_swaps);
             CUR_CK(cudaGetLastError());
         }
