@@ -34,7 +34,9 @@ namespace curk {
 constexpr int kLpBM = 128;           // rows of C per tile (MMA M)
 constexpr int kLpKC = 64;            // BF16 elements per 128-byte swizzled K chunk
 constexpr int kLpChunkC = kLpBM * 128;  // bytes of one K chunk of a C tile
-constexpr int kLpThreads = 128;
+constexpr int kLpStages = 4;          // shared-memory stages of C tiles in flight per CTA
+constexpr int kLpEpiWarps = 4;        // warps reading the accumulators
+constexpr int kLpThreadsWS = 32 * (2 + kLpEpiWarps);
 constexpr int kLpBatch = 16;         // iterations launched between two reads of the control block
 
 // Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major.
@@ -168,42 +170,51 @@ __global__ void lp_setup_from_k(const double* __restrict__ minv, int r, int ldk,
     if (threadIdx.x == 0) { ctl->status = CUR_OK; ctl->done = 0; ctl->swaps = 0; ctl->logvol = 0.0; }
 }
 
-// argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles.
-// Thread 0 issues the TMA loads (the next tile's while the current one is multiplied) and
-// the MMAs; all four warps read the accumulator (warp w: rows 32w..32w+31 of the tile).
+// argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles, warp
+// specialised. Warp 0 (one lane) streams the tiles of C through a ring of kLpStages shared-
+// memory stages with TMA; warp 1 (one lane) issues the MMAs of each tile into one of two TMEM
+// accumulators; warps 2..5 read an accumulator back (warp w: TMEM lanes 32 (w % 4) ...) while
+// the next tile is loaded and multiplied, and keep the CTA's two best rows. At the end the
+// candidate entries of those two rows are evaluated exactly (warps 0 and 1).
 template <bool F8>
-__global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
-                                                          const __grid_constant__ CUtensorMap mW, int64_t p, int r,
-                                                          int kc, int tcols, const float* __restrict__ cinv,
-                                                          const float* __restrict__ winv, const float* __restrict__ C,
-                                                          const float* __restrict__ Mh, const float* __restrict__ Ml,
-                                                          const LpCtl* ctl, LpCand* cand, int* status) {
+__global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
+                                                            const __grid_constant__ CUtensorMap mW, int64_t p, int r,
+                                                            int kc, int tcols, const float* __restrict__ cinv,
+                                                            const float* __restrict__ winv, const float* __restrict__ C,
+                                                            const float* __restrict__ Mh, const float* __restrict__ Ml,
+                                                            const LpCtl* ctl, LpCand* cand, int* status) {
     extern __shared__ unsigned char lp_raw[];
-    __shared__ uint64_t full[2], wbar, mbar;
+    __shared__ uint64_t full[kLpStages], empty[kLpStages], accf[2], acce[2], wbar;
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    __shared__ float red_v[8];
-    __shared__ int red_i[8], red_j[8];
+    __shared__ float red_v[2 * kLpEpiWarps];
+    __shared__ int red_i[2 * kLpEpiWarps], red_j[2 * kLpEpiWarps];
     __shared__ float s_winv[128];
     __shared__ int s_rows[2], s_cols[2];
-    __shared__ double s_ev[4];
-    __shared__ int s_ei[4], s_ej[4];
+    __shared__ double s_ev[2];
+    __shared__ int s_ei[2], s_ej[2];
     if (ctl->done) return;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char* WS = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(lp_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t wchunk = (uint32_t)r * 128;
     unsigned char* CS = WS + (size_t)kc * wchunk;
-    const uint32_t cbuf = (uint32_t)kc * kLpChunkC;
+    const uint32_t cbuf = (uint32_t)kc * kLpChunkC;     // one stage: a 128-row tile of C
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
     const int nloc = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
     constexpr int kEl = F8 ? 128 : kLpKC;   // elements of one 128-byte K chunk
+    const int rpad = (r + 31) / 32 * 32;    // TMEM columns of one accumulator
     if constexpr (F8)
         for (int j = tid; j < r; j += blockDim.x) s_winv[j] = winv[j];
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
+        for (int s = 0; s < kLpStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], kLpEpiWarps);
+        }
         mbar_init(&wbar, 1);
-        mbar_init(&mbar, 1);
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -212,163 +223,168 @@ __global__ void __launch_bounds__(kLpThreads) lp_argmax_k(const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    // loads in flight that thread 0 has not waited for: W, and the C buffers
-    bool w_pending = false, c_pending[2] = {false, false};
-    uint32_t c_par[2] = {0, 0};
-    if (tid == 0) {
-        mbar_expect_tx(&wbar, (uint32_t)kc * wchunk);
-        for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kEl * c, 0);
-        w_pending = true;
-        if (nloc > 0) {
-            mbar_expect_tx(&full[0], cbuf);
-            for (int c = 0; c < kc; ++c)
-                tma_load_2d(CS + (size_t)c * kLpChunkC, &mC, &full[0], kEl * c, (int)(blockIdx.x * kLpBM));
-            c_pending[0] = true;
-        }
-    }
-    float top_v[2] = {-1.f, -1.f};
-    int top_i[2] = {INT_MAX, INT_MAX}, top_j[2] = {INT_MAX, INT_MAX};
-    constexpr int kM = kLpBM;
-    const uint32_t idesc = F8 ? idesc_e4m3(kM, r) : idesc_bf16(kM, r);
-    bool mma_pending = false;
-    int k = 0;
-    for (; k < nloc; ++k) {
-        const int64_t tile = blockIdx.x + (int64_t)k * gridDim.x;
-        const int b = k & 1;
-        if (tid == 0) {
-            if (k + 1 < nloc) {   // the other buffer's last reader (tile k-1's MMA) has completed
-                const int64_t nt = tile + gridDim.x;
-                mbar_expect_tx(&full[b ^ 1], cbuf);
+
+    if (warp == 0) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int issued[kLpStages] = {};
+            mbar_expect_tx(&wbar, (uint32_t)kc * wchunk);
+            for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kEl * c, 0);
+            for (int k = 0; k < nloc && !abort_flag; ++k) {
+                const int s = k % kLpStages, u = k / kLpStages;
+                if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { abort_flag = 1; break; }
+                const int64_t tile = blockIdx.x + (int64_t)k * gridDim.x;
+                mbar_expect_tx(&full[s], cbuf);
                 for (int c = 0; c < kc; ++c)
-                    tma_load_2d(CS + (size_t)(b ^ 1) * cbuf + (size_t)c * kLpChunkC, &mC, &full[b ^ 1], kEl * c,
-                                (int)(nt * kLpBM));
-                c_pending[b ^ 1] = true;
+                    tma_load_2d(CS + (size_t)s * cbuf + (size_t)c * kLpChunkC, &mC, &full[s], kEl * c,
+                                (int)(tile * kLpBM));
+                ++issued[s];
             }
-            bool ok = true;
-            if (w_pending) { ok = mbar_wait(&wbar, 0); if (ok) w_pending = false; }
-            if (ok) { ok = mbar_wait(&full[b], c_par[b]); if (ok) { c_pending[b] = false; c_par[b] ^= 1u; } }
-            if (ok) {
+            // every load issued has landed before the CTA's memory goes away
+            mbar_wait(&wbar, 0);
+            for (int s = 0; s < kLpStages; ++s)
+                if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1));
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = F8 ? idesc_e4m3(kLpBM, r) : idesc_bf16(kLpBM, r);
+            bool ok = mbar_wait(&wbar, 0);
+            int last = -1;
+            for (int k = 0; k < nloc && ok && !abort_flag; ++k) {
+                const int s = k % kLpStages, u = k / kLpStages, b = k & 1, v = k >> 1;
+                if (!mbar_wait(&full[s], (uint32_t)(u & 1))) { ok = false; break; }
+                if (v > 0 && !mbar_wait(&acce[b], (uint32_t)((v - 1) & 1))) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t ca = su32(CS + (size_t)b * cbuf), wa = su32(WS);
-                for (int s = 0; s < kc * 4; ++s) {
-                    const uint32_t oc = (uint32_t)(s >> 2) * kLpChunkC + (uint32_t)(s & 3) * 32;
-                    const uint32_t ow = (uint32_t)(s >> 2) * wchunk + (uint32_t)(s & 3) * 32;
-                    if constexpr (F8) mma_e4m3(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
-                    else mma_bf16(tmem, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, s != 0);
+                const uint32_t ca = su32(CS + (size_t)s * cbuf), wa = su32(WS);
+                const uint32_t d = tmem + (uint32_t)(b * rpad);
+                for (int q = 0; q < kc * 4; ++q) {
+                    const uint32_t oc = (uint32_t)(q >> 2) * kLpChunkC + (uint32_t)(q & 3) * 32;
+                    const uint32_t ow = (uint32_t)(q >> 2) * wchunk + (uint32_t)(q & 3) * 32;
+                    if constexpr (F8) mma_e4m3(d, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, q != 0);
+                    else mma_bf16(d, sdesc_k128(ca + oc), sdesc_k128(wa + ow), idesc, q != 0);
                 }
-                mma_commit(&mbar);
-                mma_pending = true;
-            } else {
-                abort_flag = 1;
+                mma_commit(&empty[s]);
+                mma_commit(&accf[b]);
+                last = k;
             }
+            if (!ok) abort_flag = 1;
+            // every MMA issued has completed once the last commit has arrived
+            if (last >= 0) mbar_wait(&accf[last & 1], (uint32_t)((last >> 1) & 1));
         }
-        __syncthreads();
-        if (abort_flag) break;
-        if (!mbar_wait(&mbar, (uint32_t)(k & 1))) abort_flag = 1;
-        __syncthreads();
-        if (abort_flag) break;
-        if (tid == 0) mma_pending = false;
-        tc_fence_after();
-        // epilogue: this thread's row, all r columns
-        const int64_t row = tile * kLpBM + 32 * warp + lane;
-        float bv = -1.f;
-        int bj = INT_MAX;
-        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-        const float ci = F8 ? (row < p ? cinv[row] : 0.f) : 1.f;
-        for (int c0 = 0; c0 < r; c0 += 16) {
-            float v[16];
-            tmem_ld16(taddr + (uint32_t)c0, v);
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int q = warp & 3;   // TMEM lane quarter of this warp
+        float tv[2] = {-1.f, -1.f};
+        int ti[2] = {INT_MAX, INT_MAX}, tj[2] = {INT_MAX, INT_MAX};
+        for (int k = 0; k < nloc; ++k) {
+            const int b = k & 1, v = k >> 1;
+            if (!mbar_wait(&accf[b], (uint32_t)(v & 1))) { abort_flag = 1; break; }
+            tc_fence_after();
+            const int64_t tile = blockIdx.x + (int64_t)k * gridDim.x;
+            const int64_t row = tile * kLpBM + 32 * q + lane;
+            const float ci = F8 ? (row < p ? cinv[row] : 0.f) : 1.f;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * rpad);
+            float bv = -1.f;
+            int bj = INT_MAX;
+            for (int c0 = 0; c0 < r; c0 += 16) {
+                float x[16];
+                tmem_ld16(taddr + (uint32_t)c0, x);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const float x = F8 ? fabsf(v[q]) * ci * s_winv[c0 + q] : fabsf(v[q]);
-                if (x > bv) { bv = x; bj = c0 + q; }
-            }
-        }
-        int bi = row < p ? (int)row : INT_MAX;
-        if (row >= p) { bv = -1.f; bj = INT_MAX; }
-        // the warp's two best rows
-        for (int q = 0; q < 2; ++q) {
-            float v = bv;
-            int i = bi, j = bj;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-                const int j2 = __shfl_xor_sync(0xffffffffu, j, o);
-                if (lp_better(v2, i2, j2, v, i, j)) { v = v2; i = i2; j = j2; }
-            }
-            if (lane == 0) { red_v[2 * warp + q] = v; red_i[2 * warp + q] = i; red_j[2 * warp + q] = j; }
-            if (bi == i) { bv = -2.f; bi = INT_MAX; bj = INT_MAX; }
-        }
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0)
-            for (int w = 0; w < 8; ++w) {
-                const float v = red_v[w];
-                const int i = red_i[w], j = red_j[w];
-                if (lp_better(v, i, j, top_v[0], top_i[0], top_j[0])) {
-                    top_v[1] = top_v[0]; top_i[1] = top_i[0]; top_j[1] = top_j[0];
-                    top_v[0] = v; top_i[0] = i; top_j[0] = j;
-                } else if (lp_better(v, i, j, top_v[1], top_i[1], top_j[1])) {
-                    top_v[1] = v; top_i[1] = i; top_j[1] = j;
+                for (int u = 0; u < 16; ++u) {
+                    const float a = F8 ? fabsf(x[u]) * ci * s_winv[c0 + u] : fabsf(x[u]);
+                    if (a > bv) { bv = a; bj = c0 + u; }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
+            int bi = row < p ? (int)row : INT_MAX;
+            if (row >= p) { bv = -1.f; bj = INT_MAX; }
+            // this tile's two best rows of the warp, merged into the warp's running two
+            for (int t = 0; t < 2; ++t) {
+                float wv = bv;
+                int wi = bi, wj = bj;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float v2 = __shfl_xor_sync(0xffffffffu, wv, o);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, wi, o);
+                    const int j2 = __shfl_xor_sync(0xffffffffu, wj, o);
+                    if (lp_better(v2, i2, j2, wv, wi, wj)) { wv = v2; wi = i2; wj = j2; }
+                }
+                if (bi == wi) { bv = -2.f; bi = INT_MAX; bj = INT_MAX; }
+                if (lp_better(wv, wi, wj, tv[0], ti[0], tj[0])) {
+                    tv[1] = tv[0]; ti[1] = ti[0]; tj[1] = tj[0];
+                    tv[0] = wv; ti[0] = wi; tj[0] = wj;
+                } else if (lp_better(wv, wi, wj, tv[1], ti[1], tj[1])) {
+                    tv[1] = wv; ti[1] = wi; tj[1] = wj;
+                }
+            }
+        }
+        if (lane == 0) {
+            const int e = 2 * (warp - 2);
+            red_v[e] = tv[0]; red_i[e] = ti[0]; red_j[e] = tj[0];
+            red_v[e + 1] = tv[1]; red_i[e + 1] = ti[1]; red_j[e + 1] = tj[1];
+        }
     }
+    tc_fence_before();
+    __syncthreads();
     if (tid == 0) {
+        float bv[2] = {-1.f, -1.f};
+        int bi[2] = {INT_MAX, INT_MAX}, bj[2] = {INT_MAX, INT_MAX};
         if (abort_flag) {
             set_status(status, CUR_ERR_TIMEOUT);
-            // let what is still in flight land before the CTA's memory goes away
-            if (mma_pending) mbar_wait(&mbar, (uint32_t)(k & 1));
-            if (w_pending) mbar_wait(&wbar, 0);
-            for (int s = 0; s < 2; ++s)
-                if (c_pending[s]) mbar_wait(&full[s], c_par[s]);
-            top_v[0] = top_v[1] = -1.f;
+        } else {
+            for (int e = 0; e < 2 * kLpEpiWarps; ++e) {
+                const float v = red_v[e];
+                const int i = red_i[e], j = red_j[e];
+                if (lp_better(v, i, j, bv[0], bi[0], bj[0])) {
+                    bv[1] = bv[0]; bi[1] = bi[0]; bj[1] = bj[0];
+                    bv[0] = v; bi[0] = i; bj[0] = j;
+                } else if (lp_better(v, i, j, bv[1], bi[1], bj[1])) {
+                    bv[1] = v; bi[1] = i; bj[1] = j;
+                }
+            }
         }
-        s_rows[0] = top_v[0] >= 0.f ? top_i[0] : -1;
-        s_rows[1] = top_v[1] >= 0.f ? top_i[1] : -1;
-        s_cols[0] = top_j[0];
-        s_cols[1] = top_j[1];
+        for (int t = 0; t < 2; ++t) {
+            s_rows[t] = bv[t] >= 0.f ? bi[t] : -1;
+            s_cols[t] = bj[t];
+        }
     }
     __syncthreads();
     // the exact value of each candidate entry, b_ij = C(i,:) M^-1(:,j) with M^-1 as hi + lo
     // floats (one warp per entry, Dot2 partial sums per lane, double-float warp reduction)
-    double ev = -1.0;
-    int ei = INT_MAX, ej = INT_MAX;
-    if (warp < 2 && s_rows[warp] >= 0) {
-        const int row = s_rows[warp], col = s_cols[warp];
-        const float* a = C + (int64_t)row * r;
-        Dot2 d;
-        for (int l = lane; l < r; l += 32) d.add(__ldg(a + l), Mh[l * r + col], Ml[l * r + col]);
-        df64 v = fast_two_sum(d.s, d.c);
+    if (warp < 2) {
+        double ev = -1.0;
+        int ei = INT_MAX, ej = INT_MAX;
+        if (s_rows[warp] >= 0) {
+            const int row = s_rows[warp], col = s_cols[warp];
+            const float* a = C + (int64_t)row * r;
+            Dot2 d;
+            for (int l = lane; l < r; l += 32) d.add(__ldg(a + l), Mh[l * r + col], Ml[l * r + col]);
+            df64 v = fast_two_sum(d.s, d.c);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-            v = df_add(v, df64{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
-        ev = fabs(df_to_d(v));
-        ei = row;
-        ej = col;
+            for (int o = 16; o > 0; o >>= 1)
+                v = df_add(v, df64{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)});
+            ev = fabs(df_to_d(v));
+            ei = row;
+            ej = col;
+        }
+        if (lane == 0) { s_ev[warp] = ev; s_ei[warp] = ei; s_ej[warp] = ej; }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, ev, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, ei, o);
-        const int j2 = __shfl_xor_sync(0xffffffffu, ej, o);
-        if (v2 > ev || (v2 == ev && (i2 < ei || (i2 == ei && j2 < ej)))) { ev = v2; ei = i2; ej = j2; }
-    }
-    if (lane == 0) { s_ev[warp] = ev; s_ei[warp] = ei; s_ej[warp] = ej; }
     __syncthreads();
     if (tid == 0) {
-        for (int w = 1; w < 4; ++w)
-            if (s_ev[w] > ev || (s_ev[w] == ev && (s_ei[w] < ei || (s_ei[w] == ei && s_ej[w] < ej)))) {
-                ev = s_ev[w]; ei = s_ei[w]; ej = s_ej[w];
-            }
+        double ev = s_ev[0];
+        int ei = s_ei[0], ej = s_ej[0];
+        if (s_ev[1] > ev || (s_ev[1] == ev && (s_ei[1] < ei || (s_ei[1] == ei && s_ej[1] < ej)))) {
+            ev = s_ev[1]; ei = s_ei[1]; ej = s_ej[1];
+        }
         LpCand c;
         c.v = ev;
         c.i = ei;
         c.j = ej;
         cand[blockIdx.x] = c;
     }
-    tc_fence_before();
-    __syncthreads();
     if (warp == 0) {
         tc_fence_after();
         tmem_dealloc(tmem, tcols);
@@ -541,11 +557,13 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     const size_t mark = ar.off;
     constexpr int es = F8 ? 1 : 2, kEl = 128 / es;
     const int kc = (r + kEl - 1) / kEl, ldk = kc * kEl;
-    const int tcols = r <= 32 ? 32 : (r <= 64 ? 64 : 128);
+    // two accumulators of rpad = r rounded up to 32 columns; TMEM is allocated in powers of 2
+    const int rpad = (r + 31) / 32 * 32;
+    const int tcols = 2 * rpad <= 64 ? 64 : (2 * rpad <= 128 ? 128 : 256);
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
-    // CTAs per SM: as many as shared memory and the SM's 512 TMEM columns hold, at most 4
-    const size_t sm_arg = 1024 + (size_t)kc * r * 128 + 2 * (size_t)kc * kLpChunkC;
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>({(size_t)4, (size_t)(227 * 1024) / sm_arg,
+    // CTAs per SM: as many as shared memory and the SM's 512 TMEM columns hold, at most 2
+    const size_t sm_arg = 1024 + (size_t)kc * r * 128 + (size_t)kLpStages * kc * kLpChunkC;
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>({(size_t)2, (size_t)(227 * 1024) / sm_arg,
                                                                     (size_t)(512 / tcols)}));
     const int grid = (int)std::min<int64_t>({ntiles, (int64_t)per_sm * h->num_sms, (int64_t)1024});
     void* Cq = ar.take((size_t)p * ldk * es);
@@ -586,7 +604,7 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
     for (;;) {
         for (int q = 0; q < kLpBatch; ++q) {
-            lp_argmax_k<F8><<<grid, kLpThreads, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml, ctl,
+            lp_argmax_k<F8><<<grid, kLpThreadsWS, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml, ctl,
                                                               cand, h->status);
             CUR_CK(cudaGetLastError());
             lp_swap_k<F8><<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, grid, Mh, Ml, S, W, winv, ctl, o->delta,
