@@ -238,34 +238,3 @@ def test_trained_network_beats_refinement_without_it(hd):
     assert all(math.isfinite(x) for x in short_l)
     assert max(short_l) < 5.0 and max(short_r) > 10.0 * max(max(short_l), 0.1)
     assert float(np.mean(gains)) > 1.0
-
-
-def prop_labels_path():
-    import os
-    return os.path.join(os.path.dirname(__file__), "golden", "proposal_labels_4096x1024_r16.npz")
-
-
-def test_trained_network_beats_refinement_without_it(hd):
-    """What the trained network gains: on held-out members of the training family, maxvol
-    refinement from the learned proposal ends at a larger volume than refinement from a
-    random start (the sweeps with no proposal), on average and on most matrices."""
-    lab = np.load(prop_labels_path())
-    F = wl.PROPOSAL_FAMILY
-    ntr, nte = 256, 12
-    items = list(zip(lab["seed"].tolist(), lab["h"].tolist()))
-    Xr, Xc = prop.family_features(hd, items[:ntr], DEV)
-    yr, yc = prop.labels(lab["I"][:ntr], lab["J"][:ntr])
-    rows, cols = prop.Net(1, DEV), prop.Net(2, DEV)
-    prop.train(hd, rows, Xr, torch.from_numpy(yr).to(DEV), (F["m"] - F["r"]) / F["r"], 8, 16384, 2e-3, 3)
-    prop.train(hd, cols, Xc, torch.from_numpy(yc).to(DEV), (F["n"] - F["r"]) / F["r"], 8, 16384, 2e-3, 4)
-    gains = []
-    for seed, h in items[-nte:]:
-        A = wl.gaussian_kernel_device(F["m"], F["n"], h, seed, DEV)
-        s, t = wl.sketch_matrices(F["m"], F["n"], 32, seed=seed + 1)
-        _, _, il, _fb = prop.propose_cross(hd, A, F["r"], rows, cols, torch.from_numpy(s).to(DEV),
-                                           torch.from_numpy(t).to(DEV), F["b_r"], F["b_c"])
-        _, _, ir = prop.random_cross(hd, A, F["r"], seed + 2)
-        lr = ir.logvol if math.isfinite(ir.logvol) else -1e3      # a singular random start counts as lost
-        gains.append(il.logvol - lr)
-    gains = np.array(gains)
-    assert gains.mean() > 1.0 and (gains > 0).mean() >= 0.75
