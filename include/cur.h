@@ -27,6 +27,10 @@
  *    recorded in the handle's device status word; cur_sync_status returns the
  *    first one recorded since the previous cur_sync_status.
  *  - A handle serves one stream at a time; calls on one handle do not overlap.
+ *  - Autotuning: cur_cross_batched (its Algorithm 3 launch: one or two CTAs per SM) and the
+ *    BF16 / FP8 phase of cur_maxvol_global (its product kernel: TMA stages and CTAs per SM)
+ *    time their candidate launch shapes on the first call of each shape class and keep the
+ *    fastest in the handle. Only shapes that leave every result unchanged are tuned.
  */
 #ifndef CUR_H
 #define CUR_H

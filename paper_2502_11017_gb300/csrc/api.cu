@@ -123,11 +123,14 @@ cur_status cur_create(cur_handle** hp, size_t workspace_bytes) {
     if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->host_stage, h->host_stage_bytes) != cudaSuccess ||
         cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&h->tune_ev[0]) != cudaSuccess || cudaEventCreate(&h->tune_ev[1]) != cudaSuccess) {
         if (h->ws) cudaFree(h->ws);
         if (h->status) cudaFree(h->status);
         if (h->host_stage) cudaFreeHost(h->host_stage);
         if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+        for (auto& e : h->tune_ev)
+            if (e) cudaEventDestroy(e);
         delete h;
         return CUR_ERR_CUDA;
     }
@@ -144,6 +147,8 @@ cur_status cur_destroy(cur_handle* h) {
     if (h->status) cudaFree(h->status);
     if (h->host_stage) cudaFreeHost(h->host_stage);
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    for (auto& e : h->tune_ev)
+        if (e) cudaEventDestroy(e);
     delete h;
     return CUR_OK;
 }

@@ -56,6 +56,15 @@ struct cur_handle {
     char* host_stage = nullptr;  // pinned host buffer for small transfers
     size_t host_stage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;  // recorded after the last copy that reads host_stage
+    // Autotuner: the launch shape chosen for each shape class (key), by timing the candidates
+    // on the first call of that class. Only shapes that leave results unchanged are tuned.
+    struct TuneEntry {
+        uint64_t key;
+        int choice;
+    };
+    TuneEntry tune[64] = {};
+    int ntune = 0;
+    cudaEvent_t tune_ev[2] = {};    // timing events of the tuning runs
     Arena arena() const {
         Arena a;
         a.base = ws;
@@ -63,6 +72,26 @@ struct cur_handle {
         return a;
     }
 };
+
+// The tuned choice for a shape class, or -1 if it has not been tuned yet.
+inline int tune_lookup(const cur_handle* h, uint64_t key) {
+    for (int i = 0; i < h->ntune; ++i)
+        if (h->tune[i].key == key) return h->tune[i].choice;
+    return -1;
+}
+inline void tune_store(cur_handle* h, uint64_t key, int choice) {
+    for (int i = 0; i < h->ntune; ++i)
+        if (h->tune[i].key == key) { h->tune[i].choice = choice; return; }
+    const int slot = h->ntune < 64 ? h->ntune++ : (int)(key % 64);   // a full table reuses slots
+    h->tune[slot].key = key;
+    h->tune[slot].choice = choice;
+}
+// floor(log2(x)) for x >= 1 (0 otherwise): the size buckets of the tuning keys.
+inline uint64_t tune_log2(uint64_t x) {
+    uint64_t b = 0;
+    while (x > 1) { x >>= 1; ++b; }
+    return b;
+}
 
 // Element size of a cur_dtype.
 inline size_t dtype_size(cur_dtype t) { return t == CUR_F64 ? 8 : (t == CUR_F32 ? 4 : 2); }

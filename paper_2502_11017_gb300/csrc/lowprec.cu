@@ -35,7 +35,6 @@ namespace curk {
 constexpr int kLpBM = 128;           // rows of C per tile (MMA M)
 constexpr int kLpKC = 64;            // BF16 elements per 128-byte swizzled K chunk
 constexpr int kLpChunkC = kLpBM * 128;  // bytes of one K chunk of a C tile
-constexpr int kLpStages = 4;          // shared-memory stages of C tiles in flight per CTA
 constexpr int kLpEpiWarps = 4;        // warps reading the accumulators
 constexpr int kLpThreadsWS = 32 * (2 + kLpEpiWarps);
 constexpr int kLpBatch = 16;         // iterations launched between two reads of the control block
@@ -172,12 +171,12 @@ __global__ void lp_setup_from_k(const double* __restrict__ minv, int r, int ldk,
 }
 
 // argmax |B_ij| over all rows of C for B = Cq Wq^T: persistent CTAs over 128-row tiles, warp
-// specialised. Warp 0 (one lane) streams the tiles of C through a ring of kLpStages shared-
+// specialised. Warp 0 (one lane) streams the tiles of C through a ring of NS shared-
 // memory stages with TMA; warp 1 (one lane) issues the MMAs of each tile into one of two TMEM
 // accumulators; warps 2..5 read an accumulator back (warp w: TMEM lanes 32 (w % 4) ...) while
 // the next tile is loaded and multiplied, and keep the CTA's two best rows. At the end the
 // candidate entries of those two rows are evaluated exactly (warps 0 and 1).
-template <bool F8>
+template <bool F8, int NS>
 __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constant__ CUtensorMap mC,
                                                             const __grid_constant__ CUtensorMap mW, int64_t p, int r,
                                                             int kc, int tcols, const float* __restrict__ cinv,
@@ -185,7 +184,7 @@ __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constan
                                                             const float* __restrict__ Mh, const float* __restrict__ Ml,
                                                             const LpCtl* ctl, LpCand* cand, int* status) {
     extern __shared__ unsigned char lp_raw[];
-    __shared__ uint64_t full[kLpStages], empty[kLpStages], accf[2], acce[2], wbar;
+    __shared__ uint64_t full[NS], empty[NS], accf[2], acce[2], wbar;
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     __shared__ float red_v[2 * kLpEpiWarps];
@@ -207,7 +206,7 @@ __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constan
     if constexpr (F8)
         for (int j = tid; j < r; j += blockDim.x) s_winv[j] = winv[j];
     if (tid == 0) {
-        for (int s = 0; s < kLpStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -228,11 +227,11 @@ __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constan
     if (warp == 0) {
         // ---------------------------------------------------------------- TMA producer
         if (lane == 0) {
-            int issued[kLpStages] = {};
+            int issued[NS] = {};
             mbar_expect_tx(&wbar, (uint32_t)kc * wchunk);
             for (int c = 0; c < kc; ++c) tma_load_2d(WS + (size_t)c * wchunk, &mW, &wbar, kEl * c, 0);
             for (int k = 0; k < nloc && !abort_flag; ++k) {
-                const int s = k % kLpStages, u = k / kLpStages;
+                const int s = k % NS, u = k / NS;
                 if (u > 0 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) { abort_flag = 1; break; }
                 const int64_t tile = blockIdx.x + (int64_t)k * gridDim.x;
                 mbar_expect_tx(&full[s], cbuf);
@@ -243,7 +242,7 @@ __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constan
             }
             // every load issued has landed before the CTA's memory goes away
             mbar_wait(&wbar, 0);
-            for (int s = 0; s < kLpStages; ++s)
+            for (int s = 0; s < NS; ++s)
                 if (issued[s] > 0) mbar_wait(&full[s], (uint32_t)((issued[s] - 1) & 1));
         }
     } else if (warp == 1) {
@@ -253,7 +252,7 @@ __global__ void __launch_bounds__(kLpThreadsWS) lp_argmax_k(const __grid_constan
             bool ok = mbar_wait(&wbar, 0);
             int last = -1;
             for (int k = 0; k < nloc && ok && !abort_flag; ++k) {
-                const int s = k % kLpStages, u = k / kLpStages, b = k & 1, v = k >> 1;
+                const int s = k % NS, u = k / NS, b = k & 1, v = k >> 1;
                 if (!mbar_wait(&full[s], (uint32_t)(u & 1))) { ok = false; break; }
                 if (v > 0 && !mbar_wait(&acce[b], (uint32_t)((v - 1) & 1))) { ok = false; break; }
                 tc_fence_after();
@@ -562,11 +561,17 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     const int rpad = (r + 31) / 32 * 32;
     const int tcols = 2 * rpad <= 64 ? 64 : (2 * rpad <= 128 ? 128 : 256);
     const int64_t ntiles = (p + kLpBM - 1) / kLpBM;
-    // CTAs per SM: as many as shared memory and the SM's 512 TMEM columns hold, at most 2
-    const size_t sm_arg = 1024 + (size_t)kc * r * 128 + (size_t)kLpStages * kc * kLpChunkC;
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>({(size_t)2, (size_t)(227 * 1024) / sm_arg,
-                                                                    (size_t)(512 / tcols)}));
-    const int grid = (int)std::min<int64_t>({ntiles, (int64_t)per_sm * h->num_sms, (int64_t)1024});
+    // launch shapes of the product kernel: TMA stages (2 or 4) and CTAs per SM (1 or 2), as far
+    // as shared memory (227 KB per SM) and TMEM (512 columns per SM) allow; the autotuner
+    // picks one per class of (precision, r, p) by timing them (the results do not depend on it)
+    struct Shape { int ns, per_sm; };
+    const Shape shapes[4] = {{4, 2}, {4, 1}, {2, 2}, {2, 1}};
+    auto smem_of = [&](int ns) { return 1024 + (size_t)kc * r * 128 + (size_t)ns * kc * kLpChunkC; };
+    auto fits = [&](Shape c) {
+        return (size_t)c.per_sm * smem_of(c.ns) <= (size_t)227 * 1024 && c.per_sm * tcols <= 512;
+    };
+    auto grid_of = [&](Shape c) { return (int)std::min<int64_t>({ntiles, (int64_t)c.per_sm * h->num_sms, 1024}); };
+    const int grid_max = (int)std::min<int64_t>({ntiles, 2LL * h->num_sms, 1024});
     void* Cq = ar.take((size_t)p * ldk * es);
     void* W = ar.take((size_t)r * ldk * es);
     float* cinv = ar.get<float>(F8 ? (size_t)p : 1);
@@ -574,7 +579,7 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     float* Mh = ar.get<float>((size_t)r * r);
     float* Ml = ar.get<float>((size_t)r * r);
     int32_t* S = ar.get<int32_t>(r);
-    LpCand* cand = ar.get<LpCand>((size_t)grid);
+    LpCand* cand = ar.get<LpCand>((size_t)grid_max);
     LpCtl* ctl = ar.get<LpCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUtensorMap mC, mW;
@@ -596,7 +601,43 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     }
     CUR_CK(cudaGetLastError());
     note_launch(2);
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_arg));
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_of(4)));
+    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem_of(2)));
+    auto launch_argmax = [&](Shape c) -> cur_status {
+        const int g = grid_of(c);
+        if (c.ns == 4)
+            lp_argmax_k<F8, 4><<<g, kLpThreadsWS, smem_of(4), st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml,
+                                                                   ctl, cand, h->status);
+        else
+            lp_argmax_k<F8, 2><<<g, kLpThreadsWS, smem_of(2), st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml,
+                                                                   ctl, cand, h->status);
+        CUR_CK(cudaGetLastError());
+        return CUR_OK;
+    };
+    const uint64_t tkey = (2ull << 56) | ((uint64_t)F8 << 48) | ((uint64_t)r << 16) | tune_log2((uint64_t)p);
+    int choice = tune_lookup(h, tkey);
+    if (choice < 0) {
+        // time each shape that fits over three launches on the current inverse, keep the fastest
+        float best_ms = 0.f;
+        choice = -1;
+        for (int c = 0; c < 4; ++c) {
+            if (!fits(shapes[c])) continue;
+            CUR_CK(cudaEventRecord(h->tune_ev[0], st));
+            for (int rep = 0; rep < 3; ++rep) CUR_TRY(launch_argmax(shapes[c]));
+            CUR_CK(cudaEventRecord(h->tune_ev[1], st));
+            CUR_CK(cudaEventSynchronize(h->tune_ev[1]));
+            float ms = 0.f;
+            CUR_CK(cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1]));
+            note_launch(3);
+            if (choice < 0 || ms < best_ms) { best_ms = ms; choice = c; }
+        }
+        if (choice < 0) return CUR_ERR_ARG;
+        tune_store(h, tkey, choice);
+    }
+    const Shape shape = shapes[choice];
+    const int grid = grid_of(shape);
     const size_t sm_swap = (size_t)r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
                            2 * (size_t)r * (r + 1) * sizeof(float) + 16;
     CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
@@ -605,9 +646,7 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
     for (;;) {
         for (int q = 0; q < kLpBatch; ++q) {
-            lp_argmax_k<F8><<<grid, kLpThreadsWS, sm_arg, st>>>(mC, mW, p, r, kc, tcols, cinv, winv, C, Mh, Ml, ctl,
-                                                              cand, h->status);
-            CUR_CK(cudaGetLastError());
+            CUR_TRY(launch_argmax(shape));
             lp_swap_k<F8><<<1, 1024, sm_swap, st>>>(C, p, r, ldk, cand, grid, Mh, Ml, S, W, winv, ctl, o->delta,
                                                     max_swaps);
             CUR_CK(cudaGetLastError());

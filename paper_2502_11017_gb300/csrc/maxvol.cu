@@ -2112,7 +2112,12 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     }
     static_assert(sizeof(AcaIt) == 48, "BatAcaItem layout");
     if (bat_aca_item_size() != sizeof(AcaIt)) return CUR_ERR_ARG;
-    const int grid = std::min(T, 2 * h->num_sms);
+    // Algorithm 3 launch shape: one or two CTAs per SM (a CTA runs a whole matrix, so the
+    // result does not depend on it), tuned per class of batch size and work per matrix
+    double work = 0.0;
+    for (int t = 0; t < T; ++t) work += (double)items[t].rows * items[t].cols * items[t].r;
+    const uint64_t tkey = (1ull << 56) | (tune_log2((uint64_t)T) << 8) | tune_log2((uint64_t)(work / T) + 1);
+    const int grid_max = std::min(T, 2 * h->num_sms);
     void* dai = ar.take(sizeof(AcaIt) * T);
     BatGItem* dgc = ar.get<BatGItem>(T);
     BatGItem* dgr = ar.get<BatGItem>(T);
@@ -2121,7 +2126,7 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     int32_t* drr = ar.get<int32_t>(T);
     int32_t* J0 = ar.get<int32_t>(sum_r);
     int32_t* cnt = ar.get<int32_t>(T);
-    float* Qws = static_cast<float*>(ar.take(bat_aca_workspace(grid)));
+    float* Qws = static_cast<float*>(ar.take(bat_aca_workspace(grid_max)));
     float* C = ar.get<float>(sum_mr);
     float* Rt = ar.get<float>(sum_nr);
     int32_t* I = ar.get<int32_t>((size_t)T * rs);
@@ -2145,7 +2150,26 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     CUR_TRY(bat_upload(h, dnn, nn.data(), sizeof(int64_t) * T, st));
     CUR_TRY(bat_upload(h, drr, rr.data(), sizeof(int32_t) * T, st));
     // ---- J0: Algorithm 3 on the columns of every matrix, padded per matrix
-    CUR_TRY(bat_aca_launch(data, dai, dorder, queue, T, J0, cnt, Qws, grid, h->status, st));
+    const int tuned = tune_lookup(h, tkey);
+    if (tuned >= 0) {
+        CUR_TRY(bat_aca_launch(data, dai, dorder, queue, T, J0, cnt, Qws, std::min(T, tuned * h->num_sms),
+                               h->status, st));
+    } else {
+        // first batch of this class: time both shapes (each computes the same J0), keep the faster
+        float best_ms = 0.f;
+        int best = 2;
+        for (int per_sm = 1; per_sm <= 2; ++per_sm) {
+            CUR_CK(cudaEventRecord(h->tune_ev[0], st));
+            CUR_TRY(bat_aca_launch(data, dai, dorder, queue, T, J0, cnt, Qws, std::min(T, per_sm * h->num_sms),
+                                   h->status, st));
+            CUR_CK(cudaEventRecord(h->tune_ev[1], st));
+            CUR_CK(cudaEventSynchronize(h->tune_ev[1]));
+            float ms = 0.f;
+            CUR_CK(cudaEventElapsedTime(&ms, h->tune_ev[0], h->tune_ev[1]));
+            if (per_sm == 1 || ms < best_ms) { best_ms = ms; best = per_sm; }
+        }
+        tune_store(h, tkey, best);
+    }
     std::vector<int32_t> hcnt(T);
     CUR_CK(cudaStreamSynchronize(st));
     CUR_CK(cudaMemcpy(hcnt.data(), cnt, sizeof(int32_t) * T, cudaMemcpyDeviceToHost));
