@@ -269,11 +269,12 @@ cur_status cur_mlp_forward(cur_handle* h, const float* X, int64_t N, int32_t k, 
 /* Gradient of the weighted mean binary cross-entropy
  *   L = (1/N) sum_s w_s [ y_s log(1 + e^-score_s) + (1 - y_s) log(1 + e^score_s) ],
  * w_s = pos_weight for y_s = 1 and 1 for y_s = 0, over the samples s = idx[0..N) (rows of
- * X and entries of y; idx NULL: 0..N-1). grads: same layout as params (device); loss: one
- * double (device, may be NULL). Deterministic. Asynchronous. */
-cur_status cur_mlp_grad(cur_handle* h, const float* X, const float* y, const int64_t* idx, int64_t N,
-                        int32_t k, int32_t H, const float* params, float pos_weight, float* grads,
-                        double* loss, cudaStream_t stream);
+ * X, nrows x k, and entries of y, nrows; idx NULL: 0..N-1, N <= nrows). A sample index
+ * outside [0, nrows) contributes nothing and records CUR_ERR_ARG. grads: same layout as
+ * params (device); loss: one double (device, may be NULL). Deterministic. Asynchronous. */
+cur_status cur_mlp_grad(cur_handle* h, const float* X, const float* y, int64_t nrows, const int64_t* idx,
+                        int64_t N, int32_t k, int32_t H, const float* params, float pos_weight,
+                        float* grads, double* loss, cudaStream_t stream);
 
 /* One Adam step (Kingma and Ba, 2015) at step t >= 1 on count parameters, in place:
  * m1 = b1 m1 + (1 - b1) g, m2 = b2 m2 + (1 - b2) g^2,

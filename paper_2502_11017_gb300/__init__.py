@@ -96,7 +96,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                            ctypes.POINTER(I64)], ctypes.c_int),
         "cur_sketch": ([P, pmat, P, P, I32, P, P, I32, P], ctypes.c_int),
         "cur_mlp_forward": ([P, P, I64, I32, I32, P, P, P], ctypes.c_int),
-        "cur_mlp_grad": ([P, P, P, P, I64, I32, I32, P, ctypes.c_float, P, P, P], ctypes.c_int),
+        "cur_mlp_grad": ([P, P, P, I64, P, I64, I32, I32, P, ctypes.c_float, P, P, P], ctypes.c_int),
         "cur_adam_step": ([P, P, P, P, P, I64, I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                            ctypes.c_float, P], ctypes.c_int),
         "cur_propose": ([P, P, I64, I32, P, P], ctypes.c_int),
@@ -348,7 +348,7 @@ def cur_mlp_grad(h, X, y, params, grads_out, loss_out=None, idx=None, N=None, po
                  H: int = 256, stream=None) -> int:
     """Gradient over the samples idx[0..N) (all rows of X when idx is None)."""
     n = (X.shape[0] if idx is None else idx.shape[0]) if N is None else N
-    return _check(load().cur_mlp_grad(h, _ptr(X), _ptr(y), _ptr(idx), n, X.shape[1], H, _ptr(params),
+    return _check(load().cur_mlp_grad(h, _ptr(X), _ptr(y), X.shape[0], _ptr(idx), n, X.shape[1], H, _ptr(params),
                                       pos_weight, _ptr(grads_out), _ptr(loss_out), _stream(stream)),
                   "cur_mlp_grad")
 

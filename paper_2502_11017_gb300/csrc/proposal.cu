@@ -274,16 +274,24 @@ struct MlpCtx {
     float b1, w2;
 };
 
-// Stages samples [s0, s0 + 32) (rows idx[s] of X, or s) in Xs; zeros past N.
+// The row of X for sample sg (idx[sg], or sg), or -1 if it lies outside [0, nrows).
+__device__ __forceinline__ int64_t mlp_row(const int64_t* idx, int64_t sg, int64_t nrows) {
+    const int64_t row = idx ? idx[sg] : sg;
+    return row >= 0 && row < nrows ? row : -1;
+}
+
+// Stages samples [s0, s0 + 32) (rows idx[s] of X, or s) in Xs; zeros past N and for a row
+// outside X (recorded as CUR_ERR_ARG).
 __device__ __forceinline__ void mlp_stage(float (*Xs)[kSkK], const float* __restrict__ X, const int64_t* idx,
-                                          int64_t N, int64_t s0) {
+                                          int64_t N, int64_t nrows, int64_t s0, int* status) {
     for (int e = threadIdx.x; e < 32 * (kSkK / 4); e += blockDim.x) {
         const int s = e / (kSkK / 4), c4 = e % (kSkK / 4);
         const int64_t sg = s0 + s;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (sg < N) {
-            const int64_t row = idx ? idx[sg] : sg;
-            v = __ldg(reinterpret_cast<const float4*>(X + row * kSkK) + c4);
+            const int64_t row = mlp_row(idx, sg, nrows);
+            if (row >= 0) v = __ldg(reinterpret_cast<const float4*>(X + row * kSkK) + c4);
+            else if (c4 == 0) set_status(status, CUR_ERR_ARG);
         }
         *reinterpret_cast<float4*>(&Xs[s][4 * c4]) = v;
     }
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(kMlpMaxH) mlp_fwd_k(const float* __restrict__ 
     float z[32];
     for (int64_t s0 = (int64_t)blockIdx.x * 32; s0 < N; s0 += (int64_t)gridDim.x * 32) {
         __syncthreads();
-        mlp_stage(Xs, X, nullptr, N, s0);
+        mlp_stage(Xs, X, nullptr, N, N, s0, nullptr);
         __syncthreads();
         mlp_hidden(Xs, c, z, red);
         __syncthreads();
@@ -343,8 +351,8 @@ __device__ __forceinline__ float softplus(float x) { return fmaxf(x, 0.f) + log1
 // Per-CTA partial gradients of the weighted mean cross-entropy; gp row = [dW1 (k x H),
 // db1 (H), dw2 (H), db2, loss]. blockDim = H.
 __global__ void __launch_bounds__(kMlpMaxH) mlp_grad_k(const float* __restrict__ X, const float* __restrict__ y, const int64_t* idx,
-                           int64_t N, const float* __restrict__ P, int H, float pos_weight, float invN,
-                           float* __restrict__ gp) {
+                           int64_t N, int64_t nrows, const float* __restrict__ P, int H, float pos_weight, float invN,
+                           float* __restrict__ gp, int* status) {
     __shared__ __align__(16) float Xs[32][kSkK];
     __shared__ float red[32][32];
     __shared__ float dss[32];
@@ -359,17 +367,18 @@ __global__ void __launch_bounds__(kMlpMaxH) mlp_grad_k(const float* __restrict__
     float z[32];
     for (int64_t s0 = (int64_t)blockIdx.x * 32; s0 < N; s0 += (int64_t)gridDim.x * 32) {
         __syncthreads();
-        mlp_stage(Xs, X, idx, N, s0);
+        mlp_stage(Xs, X, idx, N, nrows, s0, status);
         __syncthreads();
         mlp_hidden(Xs, c, z, red);
         __syncthreads();
         if (threadIdx.x < 32) {
             const int64_t sg = s0 + threadIdx.x;
             float ds = 0.f;
-            if (sg < N) {
+            const int64_t row = sg < N ? mlp_row(idx, sg, nrows) : -1;
+            if (row >= 0) {
                 float sc = b2;
                 for (int w = 0; w < nw; ++w) sc += red[w][threadIdx.x];
-                const float lab = y[idx ? idx[sg] : sg];
+                const float lab = y[row];
                 const float wt = lab > 0.5f ? pos_weight : 1.f;
                 const float sig = 1.f / (1.f + expf(-sc));
                 ds = wt * (sig - lab) * invN;
@@ -593,17 +602,20 @@ cur_status cur_mlp_forward(cur_handle* h, const float* X, int64_t N, int32_t k, 
     return CUR_OK;
 }
 
-cur_status cur_mlp_grad(cur_handle* h, const float* X, const float* y, const int64_t* idx, int64_t N, int32_t k,
-                        int32_t H, const float* params, float pos_weight, float* grads, double* loss,
+cur_status cur_mlp_grad(cur_handle* h, const float* X, const float* y, int64_t nrows, const int64_t* idx, int64_t N,
+                        int32_t k, int32_t H, const float* params, float pos_weight, float* grads, double* loss,
                         cudaStream_t st) {
-    if (!h || !X || !y || !params || !grads || N < 1 || !mlp_shape_ok(k, H) || !aligned16(X)) return CUR_ERR_ARG;
+    if (!h || !X || !y || !params || !grads || N < 1 || nrows < 1 || !mlp_shape_ok(k, H) || !aligned16(X))
+        return CUR_ERR_ARG;
+    if (!idx && N > nrows) return CUR_ERR_ARG;
     if (!(pos_weight > 0.f)) return CUR_ERR_ARG;
     const int nb = mlp_grid(h->num_sms, N);
     const int64_t Pn = (int64_t)k * H + 2 * H + 1;
     Arena ar = h->arena();
     float* gp = ar.get<float>((size_t)nb * (Pn + 1));
     if (!ar.ok) return CUR_ERR_NOMEM;
-    curk::mlp_grad_k<<<nb, H, 0, st>>>(X, y, idx, N, params, H, pos_weight, (float)(1.0 / (double)N), gp);
+    curk::mlp_grad_k<<<nb, H, 0, st>>>(X, y, idx, N, nrows, params, H, pos_weight, (float)(1.0 / (double)N), gp,
+                                       h->status);
     CUR_CK(cudaGetLastError());
     curk::mlp_grad_reduce_k<<<(unsigned)((Pn + 1 + 255) / 256), 256, 0, st>>>(gp, nb, Pn, grads, loss);
     CUR_CK(cudaGetLastError());

@@ -238,3 +238,22 @@ def test_trained_network_beats_refinement_without_it(hd):
     assert all(math.isfinite(x) for x in short_l)
     assert max(short_l) < 5.0 and max(short_r) > 10.0 * max(max(short_l), 0.1)
     assert float(np.mean(gains)) > 1.0
+
+
+def test_mlp_gradient_refuses_a_sample_outside_x(hd):
+    """A sample index outside X contributes nothing and is recorded as CUR_ERR_ARG; the
+    device reads nothing out of range."""
+    rng = np.random.default_rng(8)
+    X = (rng.standard_normal((100, 32)) * 0.3).astype(np.float32)
+    y = (rng.random(100) < 0.2).astype(np.float32)
+    p = _params(9)
+    idx = np.array([3, 150, 7, -2, 42], dtype=np.int64)
+    g = torch.empty(p.size, dtype=torch.float32, device=DEV)
+    cur.cur_mlp_grad(hd.h, torch.from_numpy(X).to(DEV), torch.from_numpy(y).to(DEV), torch.from_numpy(p).to(DEV),
+                     g, idx=torch.from_numpy(idx).to(DEV))
+    assert cur.cur_sync_status(hd.h) == cur.CUR_ERR_ARG
+    ok = np.array([3, 7, 42])
+    W1, b1, w2, b2 = _split(p)
+    _lo, dW1, db1, dw2, db2 = orc.mlp_loss_grad(X[ok], y[ok], W1, b1, w2, b2)
+    go = np.concatenate([dW1.ravel(), db1, dw2, [db2]]) * (len(ok) / len(idx))   # mean over all 5
+    np.testing.assert_allclose(g.cpu().numpy(), go, rtol=1e-3, atol=1e-4 * np.abs(go).max())
