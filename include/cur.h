@@ -208,8 +208,10 @@ cur_status cur_residual_cheb(cur_handle* h, const cur_mat* A, const void* C, con
  * launch. The array is shared by every call and keeps the last call's contents; calls
  * whose work overlaps on the GPU (other streams, other threads) race on it, so order
  * them. The first call on each device looks up the array's device address (with that
- * device current); make that first call before any stream capture. It calls no
- * cudaMalloc or cudaFree. A non-finite value in the data gives cheb_out = NaN (there
+ * device current) and keeps it for the life of the process; make that first call before
+ * any stream capture. Resetting the device (cudaDeviceReset, or releasing its primary
+ * context) after that first call is not supported: the kept address would be stale. It
+ * calls no cudaMalloc or cudaFree. A non-finite value in the data gives cheb_out = NaN (there
  * is no handle status word to record it). */
 cur_status cur_residual_cheb_noalloc(const cur_mat* A, const void* C, const double* U,
                                      const void* R, int32_t r, double* cheb_out,

@@ -475,7 +475,9 @@ cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const d
 // not hit cudaMalloc's implicit device synchronisation. For them
 // cur_residual_cheb_noalloc keeps its scratch (W = U R and the per-CTA partial sums) in
 // one array compiled into this library. The array's device address is looked up once
-// per device, on the first call made with that device current.
+// per device, on the first call made with that device current, and kept until the
+// process exits; a device reset after that first call is not supported (the kept
+// address would no longer be valid).
 
 #include <mutex>
 

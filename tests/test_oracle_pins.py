@@ -562,3 +562,108 @@ def test_adam_first_step_moves_by_lr_and_follows_its_recurrence():
     for t in range(1, 6):
         p, a, b = orc.adam_step(p, g, a, b, t, lr=0.01)
     np.testing.assert_allclose(p, -5 * 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- padding, features, merge chain
+
+def test_pad_indices_takes_the_lowest_unused_by_enumeration():
+    """Every short selection of range(6) (every subset, every order, up to length 3) is
+    filled up to r with the smallest indices not in it, in increasing order; the given
+    prefix is kept as it is and nothing repeats (rank-deficient start, reading 6)."""
+    size = 6
+    for k in range(0, 4):
+        for sel in itertools.permutations(range(size), k):
+            for r in range(k, size + 1):
+                out = orc.pad_indices(list(sel), size, r)
+                unused = [x for x in range(size) if x not in sel]
+                assert out == list(sel) + unused[:r - k]
+                assert len(set(out)) == len(out) == r
+
+
+def test_pad_indices_hand_cases():
+    assert orc.pad_indices([3, 0, 5], 8, 6) == [3, 0, 5, 1, 2, 4]
+    assert orc.pad_indices([0, 1, 2], 8, 5) == [0, 1, 2, 3, 4]      # low indices already held
+    assert orc.pad_indices([], 4, 2) == [0, 1]
+    assert orc.pad_indices([7, 2], 8, 2) == [7, 2]                    # nothing to add
+    assert orc.pad_indices([1], 2, 3) == [1, 0]                       # only `size` indices exist
+
+
+def test_proposal_features_divide_by_the_largest_row_norm():
+    """Closed form: rows (3,4), (0,1), (1,0), (0,0) have norms 5, 1, 1, 0, so every row is
+    divided by 5 (one global divisor: a per-row normalisation would give norms 1, 1, 1)."""
+    Y = np.array([[0.0, 1.0], [3.0, 4.0], [1.0, 0.0], [0.0, 0.0]])
+    F = orc.proposal_features(Y)
+    assert np.array_equal(F, Y / 5.0)
+    assert np.allclose(np.sqrt((F * F).sum(axis=1)), [0.2, 1.0, 0.2, 0.0], rtol=0, atol=1e-15)
+    # invariant to a positive scale of the sketch and equivariant to a row permutation
+    rng = np.random.default_rng(5)
+    Z = rng.standard_normal((50, 32))
+    perm = rng.permutation(50)
+    assert np.allclose(orc.proposal_features(7.5 * Z), orc.proposal_features(Z), rtol=1e-14, atol=0)
+    assert np.array_equal(orc.proposal_features(Z[perm]), orc.proposal_features(Z)[perm])
+    assert np.array_equal(orc.proposal_features(np.zeros((3, 2))), np.zeros((3, 2)))
+
+
+def _dominant(Cb, S, delta):
+    """No single swap of row i (outside S) into position j raises |det Cb(S,:)| by more
+    than 1 + delta: enumerated with numpy determinants."""
+    base = abs(np.linalg.det(Cb[S, :]))
+    for j in range(len(S)):
+        for i in range(Cb.shape[0]):
+            if i in S:
+                continue
+            T = list(S)
+            T[j] = i
+            if abs(np.linalg.det(Cb[T, :])) > (1 + delta) * base * (1 + 1e-12):
+                return False
+    return True
+
+
+def test_merge_singular_left_start_goes_to_the_right_set():
+    """Left set {(1,0), (1,0)} is singular. The right set {(0.995,0), (0,1)} is dominant in
+    the union (|det| 0.995; replacing (0.995,0) by (1,0) gains 1.005 < 1 + delta), so a
+    maxvol started there makes no swap and returns it. Algorithm 3 on the union would start
+    at {(1,0), (0,1)} instead (first maximum of the norms), so a chain that skipped the
+    right start returns a different set."""
+    C = np.array([[1.0, 0.0], [1.0, 0.0], [0.995, 0.0], [0.0, 1.0]])
+    left, right = [0, 1], [2, 3]
+    assert abs(np.linalg.det(C[left])) == 0.0
+    assert _dominant(C, right, 1e-2)
+    out, swaps = orc.merge(C, [left, right])
+    assert out == right and swaps == 0
+    aca, _ = orc.aca_select(C, 0, 2, 1)
+    assert sorted(aca) == [0, 3]
+
+
+def test_merge_both_starts_singular_uses_algorithm3_on_the_union():
+    """Left {(1,0), (2,0)} and right {(0,1), (0,3)} each have rank 1; their union has rank
+    2 and its unique maximal-volume pair is {(2,0), (0,3)} (|det| 6, by enumeration), which
+    Algorithm 3 on the union picks (norms 1, 4, 1, 9: first (0,3), then (2,0))."""
+    C = np.array([[1.0, 0.0], [2.0, 0.0], [0.0, 1.0], [0.0, 3.0]])
+    out, swaps = orc.merge(C, [[0, 1], [2, 3]])
+    best, vol = orc.bruteforce_rows(C, 2)
+    assert best == [1, 3] and vol == pytest.approx(6.0)
+    assert out == [3, 1] and swaps == 0
+
+
+def test_merge_singular_left_then_right_converges_to_bruteforce_maximum():
+    """Singular left start; the right start is not dominant and the swaps lead to the
+    union's maximal-volume set (tiny p, enumerated)."""
+    rng = np.random.default_rng(11)
+    for _ in range(20):
+        C = rng.standard_normal((6, 3))
+        C[1] = 2.0 * C[0]                      # left set rows 0, 1, 2 is singular
+        out, _sw = orc.merge(C, [[0, 1, 2], [3, 4, 5]])
+        U = C[[0, 1, 2, 3, 4, 5]]
+        assert _dominant(U, out, 1e-2)
+        best, vol = orc.bruteforce_rows(U, 3)
+        # Hadamard bound for a (1+delta)-dominant set of a 3-column basis
+        assert abs(np.linalg.det(U[out])) >= vol / ((1.01 * math.sqrt(3)) ** 3)
+
+
+def test_merge_union_of_rank_below_r_keeps_the_padded_start():
+    """Every row of the union lies on one line: Algorithm 3 stops after one pick, the pad
+    adds the lowest unused position, the start stays singular and is returned as is."""
+    C = np.array([[1.0, 0.0], [2.0, 0.0], [3.0, 0.0], [4.0, 0.0]])
+    out, swaps = orc.merge(C, [[0, 1], [2, 3]])
+    assert out == [3, 0] and swaps == 0
