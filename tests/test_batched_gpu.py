@@ -117,3 +117,38 @@ def test_batch_rejects_bad_items(dev):
     with pytest.raises(cur.CurError):
         cur.cur_cross_batched(hd.h, a.double(), cur.batch_items([(100, 100, 8, 1, 1)], [0]), cur.opts(), IJ)
     hd.close()
+
+
+def test_batch_extremes_match_oracle(dev):
+    """Members at the batched workload's extremes (m = 4096, n = 1024, r = 64; m = 256,
+    n = 128, r = 8; a tall-thin and a short-wide one), against the oracle's cross."""
+    shapes = [(4096, 1024, 64, 8, 2), (256, 128, 8, 1, 1), (4096, 128, 40, 8, 1),
+              (300, 1024, 64, 1, 2), (4000, 1000, 63, 8, 2)]
+    mats = [wl.uneven_batch_matrix(m, n, 12100 + t) for t, (m, n, _r, _br, _bc) in enumerate(shapes)]
+    st, out, infos = _run(shapes, mats, dev)
+    assert st in (cur.CUR_OK, cur.CUR_WARN_RANK)
+    for t, ((m, n, r, br, bc), a, (I, J), inf) in enumerate(zip(shapes, mats, out, infos)):
+        assert inf.status in (cur.CUR_OK, cur.CUR_WARN_RANK), t
+        assert len(set(I)) == r and len(set(J)) == r and max(I) < m and max(J) < n
+        _check_against_oracle(a, r, br, bc, I, J, inf)
+        assert inf.logvol == pytest.approx(orc.logvol(a.astype(np.float64)[np.ix_(I, J)]), abs=1e-6)
+
+
+def test_batch_with_global_memory_coefficients_matches_oracle(dev):
+    """A stage with more problems than twice the SM count puts the B of a problem too large
+    for one CTA's shared memory in global memory, on one CTA. 330 small members plus three
+    of 4096 rows at r = 64 make every polish stage such a stage; the large members and a
+    sample of the small ones are checked against the oracle."""
+    small = wl.uneven_batch_shapes(330, seed=12200, m_range=(256, 320), n_range=(128, 160),
+                                   r_range=(8, 12))
+    big = [(4096, 1024, 64, 8, 2), (3900, 900, 60, 8, 2), (4096, 700, 64, 8, 2)]
+    shapes = big + small
+    mats = [wl.uneven_batch_matrix(m, n, 12300 + t) for t, (m, n, _r, _br, _bc) in enumerate(shapes)]
+    st, out, infos = _run(shapes, mats, dev)
+    assert st in (cur.CUR_OK, cur.CUR_WARN_RANK)
+    check = list(range(len(big))) + list(range(len(big), len(shapes), 37))
+    for t in check:
+        (m, n, r, br, bc), a, (I, J), inf = shapes[t], mats[t], out[t], infos[t]
+        assert inf.status in (cur.CUR_OK, cur.CUR_WARN_RANK), t
+        assert len(set(I)) == r and len(set(J)) == r
+        _check_against_oracle(a, r, br, bc, I, J, inf)

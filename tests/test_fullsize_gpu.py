@@ -2,14 +2,19 @@
 FP32 Gaussian-kernel matrix (h = 0.2, seed 11019), r = 64, 64 row blocks, 8 column
 blocks, delta = 1e-2.
 
-The whole FP64 oracle cross takes minutes here (64 Algorithm 3 rounds of 2.6 s), so the
-oracle computes what it can in seconds: the first Algorithm 3 picks, and the row and
-column stages from the same inputs as the GPU's. The full cross is held to properties
-that hold at any size, evaluated in FP64 by the oracle on the GPU's sets: two-sided
-(1 + delta)-dominance, the reported log-volume, and the Chebyshev and Frobenius
-residuals of the assembled cross.
+The whole FP64 oracle cross takes minutes, so it is stored: tests/golden/fullsize_crosses.json
+is written by tests/golden/make_fullsize_crosses.py, which calls only the oracle and the
+seeded generator. The GPU cross must give the oracle's sets (sorted) or a volume ratio of
+at least 0.999 against the oracle's, and a Chebyshev residual within 1e-5 of ||A||_C of the
+oracle's. Live, the oracle also computes what it can in seconds: the first Algorithm 3
+picks, and the row and column stages from the same inputs as the GPU's. The cross is
+further held to properties that hold at any size, evaluated in FP64 by the oracle on the
+GPU's sets: two-sided (1 + delta)-dominance, the reported log-volume, and the Chebyshev
+and Frobenius residuals of the assembled cross.
 """
 import ctypes
+import json
+import os
 
 import numpy as np
 import pytest
@@ -53,10 +58,11 @@ def test_algorithm3_first_picks_match_oracle(setup):
 
 
 def test_row_and_column_stages_match_oracle(setup):
+    """Both stages start from the oracle's inputs: the stored oracle J0 for the rows, the
+    oracle's rows for the columns."""
     dev, a32, A, hd = setup
-    J0 = torch.empty(R, dtype=torch.int32, device=dev)
-    cur.cur_aca_select(hd.h, A, 1, R, B_C, J0)
-    J0l = J0.tolist()
+    J0l = _golden("gaussian_kernel_65536x8192_r64")["J0"]
+    J0 = _i32(J0l, dev)
     I = torch.empty(R, dtype=torch.int32, device=dev)
     lv = torch.empty(1, dtype=torch.float64, device=dev)
     cur.cur_maxvol_rows(hd.h, A, J0, R, cur.opts(DELTA, nblocks=B_R), I, lv)
@@ -105,3 +111,61 @@ def test_cross_is_dominant_with_its_reported_volume_and_residual(setup):
     cheb_o, fro_o = orc.residual(a32, Co, Uo, Ro)
     assert abs(cheb.item() - cheb_o) <= 1e-5 * np.abs(a32).max()
     assert fro.item() == pytest.approx(fro_o, rel=1e-4)
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "fullsize_crosses.json")
+
+
+def _golden(name):
+    with open(GOLDEN) as f:
+        return json.load(f)[name]
+
+
+def test_algorithm3_columns_match_stored_oracle(setup):
+    dev, a32, A, hd = setup
+    g = _golden("gaussian_kernel_65536x8192_r64")
+    J0 = torch.empty(R, dtype=torch.int32, device=dev)
+    cur.cur_aca_select(hd.h, A, 1, R, B_C, J0)
+    assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    assert J0.tolist() == g["J0"]
+
+
+def test_cross_matches_stored_oracle_cross(setup):
+    dev, a32, A, hd = setup
+    g = _golden("gaussian_kernel_65536x8192_r64")
+    assert (g["m"], g["n"], g["r"], g["b_r"], g["b_c"]) == (M, N, R, B_R, B_C)
+    I = torch.empty(R, dtype=torch.int32, device=dev)
+    J = torch.empty(R, dtype=torch.int32, device=dev)
+    info = torch.zeros(ctypes.sizeof(cur.CurCrossInfo), dtype=torch.uint8, device=dev)
+    cur.cur_cross(hd.h, A, R, B_R, B_C, cur.opts(DELTA), I, J, info)
+    C = torch.empty((M, R), dtype=torch.float32, device=dev)
+    Rm = torch.empty((R, N), dtype=torch.float32, device=dev)
+    U = torch.empty((R, R), dtype=torch.float64, device=dev)
+    rc = torch.empty(1, dtype=torch.float64, device=dev)
+    cheb = torch.empty(1, dtype=torch.float64, device=dev)
+    fro = torch.empty(1, dtype=torch.float64, device=dev)
+    cur.cur_assemble(hd.h, A, I, J, R, C, U, Rm, rc)
+    cur.cur_residual_cheb(hd.h, A, C, U, Rm, R, cheb, fro)
+    assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    inf = cur.info_from_tensor(info)
+    Il, Jl = I.tolist(), J.tolist()
+    lv_gpu = orc.logvol(a32[np.ix_(Il, Jl)].astype(np.float64))
+    if sorted(Il) == sorted(g["I"]) and sorted(Jl) == sorted(g["J"]):
+        assert lv_gpu == pytest.approx(g["logvol"], abs=1e-9 * max(1.0, abs(g["logvol"])))
+        assert inf.sweeps == g["sweeps"]
+    else:
+        assert lv_gpu >= g["logvol"] + np.log(0.999)
+    assert abs(cheb.item() - g["cheb"]) <= 1e-5 * g["norm_cheb"]
+    assert fro.item() == pytest.approx(g["fro_rel"], rel=1e-3)
+
+
+def test_lowrank_haar_cross_matches_stored_oracle_cross():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cur.load()
+    g = _golden("lowrank_haar_2000x1500_r16")
+    a = wl.lowrank_haar(2000, 1500)
+    A = torch.from_numpy(a).cuda()
+    I, J, inf = cur.cross(A, g["r"], g["b_r"], g["b_c"], g["delta"])
+    assert sorted(I.tolist()) == sorted(g["I"]) and sorted(J.tolist()) == sorted(g["J"])
+    assert inf.logvol == pytest.approx(g["logvol"], abs=1e-9 * abs(g["logvol"]))

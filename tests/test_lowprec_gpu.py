@@ -116,8 +116,10 @@ def test_row_selection_with_bf16_polish_matches_oracle(hd):
     m, n, r, b_r = 81957, 1024, 64, 16
     a = wl.gaussian_kernel(m, n, 0.25, seed=12)
     A = torch.from_numpy(a).to(DEV)
-    J0 = torch.empty(r, dtype=torch.int32, device=DEV)
-    cur.cur_aca_select(hd.h, A, 1, r, 1, J0)
+    # the columns: the oracle's Algorithm 3 on every 16th row (well-conditioned C; the
+    # oracle takes no input from the GPU path)
+    Jo0, _ = orc.aca_select(a[::16], 1, r, 1)
+    J0 = torch.tensor(Jo0, dtype=torch.int32, device=DEV)
     I = {}
     for prec in ("fp32", "bf16", "fp8"):
         out = torch.empty(r, dtype=torch.int32, device=DEV)
