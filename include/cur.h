@@ -302,6 +302,105 @@ cur_status cur_cross_from(cur_handle* h, const cur_mat* A, int32_t r, const int3
                           const int32_t* J0, const cur_opts* opts, int32_t* I_out, int32_t* J_out,
                           cur_cross_info* info_out, cudaStream_t stream);
 
+/* ---- Sharded cross: one process per GPU, each holding a contiguous slab of the rows of A
+ *
+ * The calls below are the per-rank steps of the cross when A is partitioned by rows over P
+ * processes (Section 2.2 divides A into blocks handled by separate processes; Algorithm 3
+ * reduces a (norm, index) pair over the blocks and broadcasts the pivot vector each round).
+ * Each call works on the caller's slab only and enqueues on `stream`; the caller makes the
+ * collectives between the calls (allreduce-sum, -max, -min of small device vectors) on its
+ * own transport (NCCL between GPUs). The driver that strings them together is
+ * paper_2502_11017_gb300.shard. BF16 slabs are accepted by the Algorithm 3 calls only. */
+
+/* Algorithm 3 on the columns of A over row slabs. state: a caller-owned device buffer of
+ * cur_shard_aca_state_bytes(h, A_k, r) bytes (the slab's share of the orthonormal basis Q,
+ * the replicated squared norms and W = Q^T A, the pivot vector). A round t = 0 .. r-1 is
+ *   pick(t, red) -> red2 ; allreduce-sum red2 (r doubles)
+ *   orth(t, red2) -> red3 ; allreduce-sum red3 (1 double)
+ *   commit(t, red3) -> red ; allreduce-sum red (n doubles)
+ * after begin (-> red, the slab's squared column norms; allreduce-sum it). pick takes the
+ * summed red (t = 0: the squared norms; t > 0: w = A^T q_{t-1}, so nu_j -= w_j^2), picks the
+ * unpicked column of largest residual norm (lowest index on ties) and forms the slab's part
+ * of v = a_p - Q (Q^T a_p); orth re-orthogonalises v once (CGS2); commit stops the selection
+ * when ||v||^2 <= (max(m,n) eps ||A||_F)^2 (CUR_WARN_RANK in the status word; later calls do
+ * nothing), else records p in idx_out[t] and, while t + 1 < r, streams the slab once for the
+ * next round's partial w. finish pads an early-stopped idx_out with the lowest unused columns.
+ * m_global: rows of the whole A. idx_out: r int32 (device), -1 until picked. red: n doubles,
+ * red2: r doubles, red3: 1 double (device). */
+size_t cur_shard_aca_state_bytes(cur_handle* h, const cur_mat* A_k, int32_t r);
+cur_status cur_shard_aca_begin(cur_handle* h, const cur_mat* A_k, int64_t m_global, int32_t r, void* state,
+                               int32_t* idx_out, double* red, cudaStream_t stream);
+cur_status cur_shard_aca_pick(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
+                              const double* red, double* red2, cudaStream_t stream);
+cur_status cur_shard_aca_orth(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
+                              const double* red2, double* red3, cudaStream_t stream);
+cur_status cur_shard_aca_commit(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
+                                const double* red3, int32_t* idx_out, double* red, cudaStream_t stream);
+cur_status cur_shard_aca_finish(cur_handle* h, const cur_mat* A_k, int32_t r, void* state, int32_t* idx_out,
+                                cudaStream_t stream);
+
+/* Maxvol over all rows of a basis C (p x r) distributed by row slabs: C_k (p_local x r,
+ * contiguous, CUR_F32 or CUR_F64) holds global rows offset .. offset + p_local - 1. Every
+ * rank holds the same S (r global row ids, position order) and M = C(S,:) (M_rows, r x r in
+ * C's dtype, device). state: cur_dmv_state_bytes(p_local, r, dtype) bytes (B = C_k M^-1 in
+ * C's dtype, M and its FP64 inverse, S, log|det M|, counters). The swap iteration:
+ *   begin / refresh -> keyv (the slab's max |B_ij|; -1 if M is numerically singular,
+ *       |u_kk| <= r eps max|M|, in which case the state's status is CUR_ERR_SINGULAR);
+ *       begin loads S and M; both factorise M afresh in FP64 and form B.
+ *   allreduce-max keyv; if it is <= 1 + delta the cycle ends (a cycle that ends with no swap
+ *       ends the iteration; otherwise refresh starts the next cycle; cycles are r swaps);
+ *   holder(keyv) -> keyi: the slab's flat index (global row * r + j) if it holds that value,
+ *       else INT64_MAX; allreduce-min keyi (the lowest index wins a tie);
+ *   fill(keyi) -> row: the winner's row of C if this slab owns it, else zeros; allreduce-sum;
+ *   swap(keyi, row) -> keyv: b = row M^-1 in FP64, M^-1 -= M^-1(:,j) (b - e_j)^T / b_j,
+ *       B -= B(:,j) (b - e_j)^T / b_j, S[j] = row id, log|det| += log|b_j|.
+ * result writes S (r int32), log|det M| (1 double) and counts (2 int32: swaps, status);
+ * any output may be NULL. Section 1.2's maximal-volume refinement; the same iteration as
+ * cur_maxvol_global, with the ranks' agreement made by the caller. */
+size_t cur_dmv_state_bytes(int64_t p_local, int32_t r, cur_dtype dtype);
+cur_status cur_dmv_begin(cur_handle* h, const cur_mat* C_k, int64_t offset, const int32_t* S, const void* M_rows,
+                         void* state, double* keyv_out, cudaStream_t stream);
+cur_status cur_dmv_refresh(cur_handle* h, const cur_mat* C_k, int64_t offset, void* state, double* keyv_out,
+                           cudaStream_t stream);
+cur_status cur_dmv_holder(cur_handle* h, const cur_mat* C_k, void* state, const double* keyv_glob,
+                          long long* keyi_out, cudaStream_t stream);
+cur_status cur_dmv_fill(cur_handle* h, const cur_mat* C_k, int64_t offset, const long long* keyi_glob, void* row_out,
+                        cudaStream_t stream);
+cur_status cur_dmv_swap(cur_handle* h, const cur_mat* C_k, int64_t offset, void* state, const long long* keyi_glob,
+                        const void* row, double* keyv_out, cudaStream_t stream);
+cur_status cur_dmv_result(cur_handle* h, const cur_mat* C_k, void* state, int32_t* S_out, double* logvol_out,
+                          int32_t* counts_out, cudaStream_t stream);
+
+/* One node of the binary merge given by the two sets' rows: rows (2r x r, contiguous,
+ * CUR_F32 or CUR_F64; the left set's r rows, then the right set's) and their ids (2r int32).
+ * Maxvol on the 2r rows started at the left set (the right set if the left one is singular,
+ * Algorithm 3 on the union if both are), as one node of cur_merge. ids_out: r int32; rows_out:
+ * r x r in rows' dtype (the merged set's rows, position order); swaps_out: 1 int32 (may be
+ * NULL). For a merge whose two sets live on different processes. */
+cur_status cur_merge_pair(cur_handle* h, const cur_mat* rows, const int32_t* ids, const cur_opts* opts,
+                          int32_t* ids_out, void* rows_out, int32_t* swaps_out, cudaStream_t stream);
+
+/* out (count x X.cols, X's dtype, contiguous) row j = X(ids[j] - offset, :) when that row
+ * lies in X (0 <= ids[j] - offset < X.rows), else zeros: the slab's share of A(I,:), whose
+ * sum over the ranks is A(I,:). CUR_F32 or CUR_F64. */
+cur_status cur_rows_at(cur_handle* h, const cur_mat* X, int64_t offset, const int32_t* ids, int32_t count,
+                       void* out, cudaStream_t stream);
+/* Xt_out (X.cols x X.rows, contiguous) = X^T. CUR_F32 or CUR_F64. */
+cur_status cur_transpose(cur_handle* h, const cur_mat* X, void* Xt_out, cudaStream_t stream);
+/* out[k] = ids[k] + offset (slab-local to global ids). */
+cur_status cur_offset_ids(cur_handle* h, const int32_t* ids, int32_t count, int64_t offset, int32_t* out,
+                          cudaStream_t stream);
+/* C_out = A(:,J) (A.rows x r, contiguous) in the compute type: FP64 for CUR_F64 data, FP32
+ * otherwise (Section 1.1's C). */
+cur_status cur_gather_cols(cur_handle* h, const cur_mat* A, const int32_t* J, int32_t r, void* C_out,
+                           cudaStream_t stream);
+/* The residual's parts on A (a slab): parts_out = {max |A - C U R|, sum (A - CUR)^2, sum A^2}
+ * (3 doubles, device), the terms of Theorem 1's Chebyshev norm and Section 3.1's relative
+ * Frobenius error before the reduction over slabs (max, sum, sum). Arguments as
+ * cur_residual_cheb. */
+cur_status cur_residual_parts(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                              const void* R, int32_t r, double* parts_out, cudaStream_t stream);
+
 /* Synchronise `stream` and return (and clear) the first device-side status. */
 cur_status cur_sync_status(cur_handle* h, cudaStream_t stream);
 

@@ -28,7 +28,12 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", 
            "cur_status_string", "cur_prof_enable", "cur_prof_read",
            "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout",
            "cur_sketch", "cur_mlp_forward", "cur_mlp_grad", "cur_adam_step", "cur_propose",
-           "cur_cross_from", "cur_maxvol_global"]
+           "cur_cross_from", "cur_maxvol_global",
+           "cur_shard_aca_state_bytes", "cur_shard_aca_begin", "cur_shard_aca_pick",
+           "cur_shard_aca_orth", "cur_shard_aca_commit", "cur_shard_aca_finish",
+           "cur_dmv_state_bytes", "cur_dmv_begin", "cur_dmv_refresh", "cur_dmv_holder", "cur_dmv_fill",
+           "cur_dmv_swap", "cur_dmv_result", "cur_merge_pair", "cur_rows_at", "cur_transpose",
+           "cur_offset_ids", "cur_gather_cols", "cur_residual_parts"]
 
 
 class CurMat(ctypes.Structure):
@@ -102,6 +107,25 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_propose": ([P, P, I64, I32, P, P], ctypes.c_int),
         "cur_cross_from": ([P, pmat, I32, P, P, popts, P, P, P, P], ctypes.c_int),
         "cur_maxvol_global": ([P, pmat, P, I32, popts, P, P, P, P], ctypes.c_int),
+        "cur_shard_aca_state_bytes": ([P, pmat, I32], ctypes.c_size_t),
+        "cur_shard_aca_begin": ([P, pmat, I64, I32, P, P, P, P], ctypes.c_int),
+        "cur_shard_aca_pick": ([P, pmat, I32, I32, P, P, P, P], ctypes.c_int),
+        "cur_shard_aca_orth": ([P, pmat, I32, I32, P, P, P, P], ctypes.c_int),
+        "cur_shard_aca_commit": ([P, pmat, I32, I32, P, P, P, P, P], ctypes.c_int),
+        "cur_shard_aca_finish": ([P, pmat, I32, P, P, P], ctypes.c_int),
+        "cur_dmv_state_bytes": ([I64, I32, ctypes.c_int], ctypes.c_size_t),
+        "cur_dmv_begin": ([P, pmat, I64, P, P, P, P, P], ctypes.c_int),
+        "cur_dmv_refresh": ([P, pmat, I64, P, P, P], ctypes.c_int),
+        "cur_dmv_holder": ([P, pmat, P, P, P, P], ctypes.c_int),
+        "cur_dmv_fill": ([P, pmat, I64, P, P, P], ctypes.c_int),
+        "cur_dmv_swap": ([P, pmat, I64, P, P, P, P, P], ctypes.c_int),
+        "cur_dmv_result": ([P, pmat, P, P, P, P, P], ctypes.c_int),
+        "cur_merge_pair": ([P, pmat, P, popts, P, P, P, P], ctypes.c_int),
+        "cur_rows_at": ([P, pmat, I64, P, I32, P, P], ctypes.c_int),
+        "cur_transpose": ([P, pmat, P, P], ctypes.c_int),
+        "cur_offset_ids": ([P, P, I32, I64, P, P], ctypes.c_int),
+        "cur_gather_cols": ([P, pmat, P, I32, P, P], ctypes.c_int),
+        "cur_residual_parts": ([P, pmat, P, P, P, I32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -272,6 +296,99 @@ def cur_prof_read(h, stream=None):
 def cur_selftest_wait_timeout(h, stream=None) -> None:
     """Launch a device wait that must run out; its timeout lands in the status word."""
     _check(load().cur_selftest_wait_timeout(h, _stream(stream)), "cur_selftest_wait_timeout")
+
+
+# ------------------------------------------------------------------ sharded cross (per-rank steps)
+
+def cur_shard_aca_state_bytes(h, A_k, r: int) -> int:
+    return load().cur_shard_aca_state_bytes(h, ctypes.byref(mat(A_k)), r)
+
+
+def cur_shard_aca_begin(h, A_k, m_global: int, r: int, state, idx_out, red, stream=None) -> int:
+    return _check(load().cur_shard_aca_begin(h, ctypes.byref(mat(A_k)), m_global, r, _ptr(state), _ptr(idx_out),
+                                             _ptr(red), _stream(stream)), "cur_shard_aca_begin")
+
+
+def cur_shard_aca_pick(h, A_k, r: int, t: int, state, red, red2, stream=None) -> int:
+    return _check(load().cur_shard_aca_pick(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red), _ptr(red2),
+                                            _stream(stream)), "cur_shard_aca_pick")
+
+
+def cur_shard_aca_orth(h, A_k, r: int, t: int, state, red2, red3, stream=None) -> int:
+    return _check(load().cur_shard_aca_orth(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red2), _ptr(red3),
+                                            _stream(stream)), "cur_shard_aca_orth")
+
+
+def cur_shard_aca_commit(h, A_k, r: int, t: int, state, red3, idx_out, red, stream=None) -> int:
+    return _check(load().cur_shard_aca_commit(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red3),
+                                              _ptr(idx_out), _ptr(red), _stream(stream)), "cur_shard_aca_commit")
+
+
+def cur_shard_aca_finish(h, A_k, r: int, state, idx_out, stream=None) -> int:
+    return _check(load().cur_shard_aca_finish(h, ctypes.byref(mat(A_k)), r, _ptr(state), _ptr(idx_out),
+                                              _stream(stream)), "cur_shard_aca_finish")
+
+
+def cur_dmv_state_bytes(p_local: int, r: int, dtype: int) -> int:
+    return load().cur_dmv_state_bytes(p_local, r, dtype)
+
+
+def cur_dmv_begin(h, C_k, offset: int, S, M_rows, state, keyv_out, stream=None) -> int:
+    return _check(load().cur_dmv_begin(h, ctypes.byref(mat(C_k)), offset, _ptr(S), _ptr(M_rows), _ptr(state),
+                                       _ptr(keyv_out), _stream(stream)), "cur_dmv_begin")
+
+
+def cur_dmv_refresh(h, C_k, offset: int, state, keyv_out, stream=None) -> int:
+    return _check(load().cur_dmv_refresh(h, ctypes.byref(mat(C_k)), offset, _ptr(state), _ptr(keyv_out),
+                                         _stream(stream)), "cur_dmv_refresh")
+
+
+def cur_dmv_holder(h, C_k, state, keyv_glob, keyi_out, stream=None) -> int:
+    return _check(load().cur_dmv_holder(h, ctypes.byref(mat(C_k)), _ptr(state), _ptr(keyv_glob), _ptr(keyi_out),
+                                        _stream(stream)), "cur_dmv_holder")
+
+
+def cur_dmv_fill(h, C_k, offset: int, keyi_glob, row_out, stream=None) -> int:
+    return _check(load().cur_dmv_fill(h, ctypes.byref(mat(C_k)), offset, _ptr(keyi_glob), _ptr(row_out),
+                                      _stream(stream)), "cur_dmv_fill")
+
+
+def cur_dmv_swap(h, C_k, offset: int, state, keyi_glob, row, keyv_out, stream=None) -> int:
+    return _check(load().cur_dmv_swap(h, ctypes.byref(mat(C_k)), offset, _ptr(state), _ptr(keyi_glob), _ptr(row),
+                                      _ptr(keyv_out), _stream(stream)), "cur_dmv_swap")
+
+
+def cur_dmv_result(h, C_k, state, S_out=None, logvol_out=None, counts_out=None, stream=None) -> int:
+    return _check(load().cur_dmv_result(h, ctypes.byref(mat(C_k)), _ptr(state), _ptr(S_out), _ptr(logvol_out),
+                                        _ptr(counts_out), _stream(stream)), "cur_dmv_result")
+
+
+def cur_merge_pair(h, rows, ids, o: CurOpts, ids_out, rows_out, swaps_out=None, stream=None) -> int:
+    return _check(load().cur_merge_pair(h, ctypes.byref(mat(rows)), _ptr(ids), ctypes.byref(o), _ptr(ids_out),
+                                        _ptr(rows_out), _ptr(swaps_out), _stream(stream)), "cur_merge_pair")
+
+
+def cur_rows_at(h, X, offset: int, ids, count: int, out, stream=None) -> int:
+    return _check(load().cur_rows_at(h, ctypes.byref(mat(X)), offset, _ptr(ids), count, _ptr(out),
+                                     _stream(stream)), "cur_rows_at")
+
+
+def cur_transpose(h, X, Xt_out, stream=None) -> int:
+    return _check(load().cur_transpose(h, ctypes.byref(mat(X)), _ptr(Xt_out), _stream(stream)), "cur_transpose")
+
+
+def cur_offset_ids(h, ids, count: int, offset: int, out, stream=None) -> int:
+    return _check(load().cur_offset_ids(h, _ptr(ids), count, offset, _ptr(out), _stream(stream)), "cur_offset_ids")
+
+
+def cur_gather_cols(h, A, J, r: int, C_out, stream=None) -> int:
+    return _check(load().cur_gather_cols(h, ctypes.byref(mat(A)), _ptr(J), r, _ptr(C_out), _stream(stream)),
+                  "cur_gather_cols")
+
+
+def cur_residual_parts(h, A, C, U, R, r: int, parts_out, stream=None) -> int:
+    return _check(load().cur_residual_parts(h, ctypes.byref(mat(A)), _ptr(C), _ptr(U), _ptr(R), r,
+                                            _ptr(parts_out), _stream(stream)), "cur_residual_parts")
 
 
 def info_from_tensor(t) -> CurCrossInfo:

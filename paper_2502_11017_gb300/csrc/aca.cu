@@ -720,3 +720,44 @@ cur_status aca_select_full(cur_handle* h, const cur_mat* A, int axis, int r, int
     }
     return CUR_ERR_ARG;
 }
+
+// ---- the column pass alone, for a row slab of A (the sharded Algorithm 3 in shard.cu)
+
+int aca_cols_chunks(int num_sms, int64_t m, int64_t n, cur_dtype dt, int64_t* chunk) {
+    const int cpl = dt == CUR_BF16 ? 8 : 4;
+    const int64_t coltiles = (n + 32 * cpl - 1) / (32 * cpl);
+    int64_t want = std::max<int64_t>(1, (int64_t)num_sms * 32 / coltiles);
+    want = std::min<int64_t>(want, std::max<int64_t>(1, m / 64));
+    want = std::min<int64_t>(want, 65535);
+    const int64_t c = (m + want - 1) / want;
+    *chunk = c;
+    return (int)((m + c - 1) / c);
+}
+
+cur_status aca_cols_partials(const cur_mat* M, int dot, const double* q64, const float* qh,
+                             const float* ql, void* part, int RC, int64_t chunk, const int* stop,
+                             cudaStream_t st) {
+    using namespace curk;
+    AcaParams P{};
+    P.A = M->data;
+    P.m = M->rows;
+    P.n = M->cols;
+    P.ld = M->ld;
+    P.axis = 1;
+    P.q64 = const_cast<double*>(q64);
+    P.qh = const_cast<float*>(qh);
+    P.ql = const_cast<float*>(ql);
+    P.part = part;
+    P.stop = const_cast<int*>(stop);
+    const uintptr_t base = reinterpret_cast<uintptr_t>(M->data);
+    const bool vec = (base % 16 == 0) && ((size_t)M->ld * dtype_size(M->dtype)) % 16 == 0;
+    const int mode = dot ? kDot : kNorm;
+    cur_status s = CUR_ERR_ARG;
+    switch (M->dtype) {
+        case CUR_F64: s = launch_pass<double>(P, mode, chunk, RC, vec, st); break;
+        case CUR_F32: s = launch_pass<float>(P, mode, chunk, RC, vec, st); break;
+        case CUR_BF16: s = launch_pass<__nv_bfloat16>(P, mode, chunk, RC, vec, st); break;
+    }
+    if (s == CUR_OK) note_launch();
+    return s;
+}

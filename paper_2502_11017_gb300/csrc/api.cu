@@ -320,6 +320,31 @@ cur_status cur_residual_cheb(cur_handle* h, const cur_mat* A, const void* C, con
     return residual_impl(h, A, C, U, R, r, cheb_out, fro_rel_out, ar, st);
 }
 
+cur_status cur_residual_parts(cur_handle* h, const cur_mat* A, const void* C, const double* U,
+                              const void* R, int32_t r, double* parts_out, cudaStream_t st) {
+    if (!h || !mat_ok(A) || !C || !U || !R || !parts_out) return CUR_ERR_ARG;
+    if (r < 1 || r > 128) return CUR_ERR_ARG;
+    Arena ar = h->arena();
+    return residual_impl(h, A, C, U, R, r, parts_out, nullptr, ar, st, parts_out + 1);
+}
+
+cur_status cur_merge_pair(cur_handle* h, const cur_mat* rows, const int32_t* ids, const cur_opts* opts,
+                          int32_t* ids_out, void* rows_out, int32_t* swaps_out, cudaStream_t st) {
+    if (!h || !mat_ok(rows) || !ids || !ids_out || !rows_out) return CUR_ERR_ARG;
+    if (rows->dtype == CUR_BF16) return CUR_ERR_ARG;
+    const int64_t r = rows->cols;
+    if (r < 1 || r > 128 || rows->ld != r || rows->rows != 2 * r) return CUR_ERR_ARG;
+    const cur_opts o = opts ? *opts : cur_default_opts();
+    Arena ar = h->arena();
+    return merge_pair_impl(h, rows->dtype, rows->data, ids, (int)r, &o, ids_out, rows_out, swaps_out, ar, st);
+}
+
+cur_status cur_gather_cols(cur_handle* h, const cur_mat* A, const int32_t* J, int32_t r, void* C_out,
+                           cudaStream_t st) {
+    if (!h || !mat_ok(A) || !J || !C_out || r < 1 || r > A->cols) return CUR_ERR_ARG;
+    return gather_cols_compute(A, J, r, C_out, st);
+}
+
 cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, int32_t b_c,
                      const cur_opts* opts, int32_t* I_out, int32_t* J_out,
                      cur_cross_info* info_out, cudaStream_t st) {

@@ -138,6 +138,11 @@ cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
                        int* swaps, Arena& ar, cudaStream_t st);
+// The merge of two candidate sets given by their rows (2r x r, left set first) and ids
+// (cur_merge_pair).
+cur_status merge_pair_impl(cur_handle* h, cur_dtype dt, const void* rows, const int32_t* ids, int r,
+                           const cur_opts* o, int32_t* ids_out, void* rows_out, int32_t* swaps_out, Arena& ar,
+                           cudaStream_t st);
 // Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r).
 cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st);
 // The cross of every matrix of a batch (cur_cross_batched), FP32 data.
@@ -175,15 +180,26 @@ size_t sketch_workspace_size(int num_sms, int64_t m, int64_t n);
 cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
                          int r, void* C_out, double* U_out, void* R_out, double* rcond_out,
                          Arena& ar, cudaStream_t st);
+// sums_out (2 doubles, device, may be NULL): sum (A - CUR)^2 and sum A^2 in FP64.
 cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
                          const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
-                         cudaStream_t st);
+                         cudaStream_t st, double* sums_out = nullptr);
 
 // tcgen05 residual for FP32 data, r = 32 or 64 (residual_tc.cu); CUR_ERR_ARG: not applicable.
 cur_status residual_tc_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
                             const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
-                            cudaStream_t st);
+                            cudaStream_t st, double* sums_out = nullptr);
 
 // Cooperative launch helper (all CTAs co-resident).
 cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
                        cudaStream_t st);
+
+// ---- the Algorithm 3 column pass alone (aca.cu), for the sharded selection (shard.cu)
+// Row chunks of the pass over an m x n matrix: returns RC and sets *chunk (rows per chunk).
+int aca_cols_chunks(int num_sms, int64_t m, int64_t n, cur_dtype dt, int64_t* chunk);
+// part[rc * n + j] = sum over the rows of chunk rc of a_ij * q_i (dot != 0) or a_ij^2 (dot = 0):
+// an FP64 value for FP64 data, a double-float pair (two floats) otherwise; q as q64 (FP64
+// data) or qh + ql (two floats). Nothing runs while *stop != 0.
+cur_status aca_cols_partials(const cur_mat* A, int dot, const double* q64, const float* qh,
+                             const float* ql, void* part, int RC, int64_t chunk, const int* stop,
+                             cudaStream_t st);

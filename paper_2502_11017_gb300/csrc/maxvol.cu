@@ -1608,6 +1608,43 @@ cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p
     return merge_one<float>(h, static_cast<const float*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
 }
 
+namespace curk {
+// ids_out[k] = ids[pos[k]], rows_out[k, :] = rows[pos[k], :] (the merged set's ids and rows).
+template <typename TB>
+__global__ void pair_emit_k(const TB* __restrict__ rows, const int32_t* __restrict__ ids,
+                            const int32_t* __restrict__ pos, int r, int32_t* __restrict__ ids_out,
+                            TB* __restrict__ rows_out, int32_t* swaps_out, int swaps) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int k = e / r, c = e - k * r;
+        rows_out[e] = rows[(int64_t)pos[k] * r + c];
+    }
+    for (int k = threadIdx.x; k < r; k += blockDim.x) ids_out[k] = ids[pos[k]];
+    if (threadIdx.x == 0 && swaps_out) *swaps_out = swaps;
+}
+}  // namespace curk
+
+cur_status merge_pair_impl(cur_handle* h, cur_dtype dt, const void* rows, const int32_t* ids, int r,
+                           const cur_opts* o, int32_t* ids_out, void* rows_out, int32_t* swaps_out, Arena& ar,
+                           cudaStream_t st) {
+    int32_t* cand = ar.get<int32_t>((size_t)2 * r);
+    int32_t* pos = ar.get<int32_t>((size_t)r);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    curk::mv_iota<<<1, 256, 0, st>>>(cand, 1, 2 * r, 0);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    int swaps = 0;
+    CUR_TRY(merge_level(h, dt, rows, 2 * r, r, cand, 2, o, pos, &swaps, ar, st));
+    if (dt == CUR_F64)
+        curk::pair_emit_k<double><<<1, 256, 0, st>>>(static_cast<const double*>(rows), ids, pos, r, ids_out,
+                                                     static_cast<double*>(rows_out), swaps_out, swaps);
+    else
+        curk::pair_emit_k<float><<<1, 256, 0, st>>>(static_cast<const float*>(rows), ids, pos, r, ids_out,
+                                                    static_cast<float*>(rows_out), swaps_out, swaps);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
 template <typename TA>
 static cur_status gather_cols_t(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st) {
     const TA* a = static_cast<const TA*>(A->data);

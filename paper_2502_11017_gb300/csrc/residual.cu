@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256, 2) residual_k(const TA* __restrict__ A, i
 
 // Combines the per-CTA partials in a fixed order (one CTA of 256 threads).
 __global__ void residual_final_k(const double* part, int64_t nparts, double* cheb, double* fro,
-                                 int* status) {
+                                 int* status, double* sums = nullptr) {
     __shared__ double s1[256], s2[256], s3[256];
     __shared__ int sb[256];
     const int tid = threadIdx.x;
@@ -365,6 +365,7 @@ __global__ void residual_final_k(const double* part, int64_t nparts, double* che
     }
     *cheb = a1;
     if (fro) *fro = s3[0] > 0.0 ? sqrt(s2[0] / s3[0]) : 0.0;
+    if (sums) { sums[0] = s2[0]; sums[1] = s3[0]; }
 }
 
 static inline unsigned nb(int64_t n, int t = 256) {
@@ -400,7 +401,7 @@ static cur_status assemble_t(cur_handle* h, const cur_mat* Am, const int32_t* I,
 template <typename TA, typename TW, int TM, int TN>
 static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, const double* U,
                              const void* R, int r, double* cheb, double* fro, Arena& ar,
-                             cudaStream_t st) {
+                             cudaStream_t st, double* sums) {
     const int64_t m = Am->rows, n = Am->cols;
     TW* W = ar.get<TW>((size_t)r * n);
     constexpr int BM = 16 * TM, BN = 16 * TN;
@@ -429,7 +430,7 @@ static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, co
         static_cast<const TA*>(Am->data), m, n, Am->ld, static_cast<const TA*>(C), W, r, part, vec);
     CUR_CK(cudaGetLastError());
     note_launch();
-    residual_final_k<<<1, 256, 0, st>>>(part, panels * segs, cheb, fro, h->status);
+    residual_final_k<<<1, 256, 0, st>>>(part, panels * segs, cheb, fro, h->status, sums);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
@@ -450,19 +451,19 @@ cur_status assemble_impl(cur_handle* h, const cur_mat* A, const int32_t* I, cons
 
 cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
                          const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
-                         cudaStream_t st) {
+                         cudaStream_t st, double* sums_out) {
     if (A->dtype == CUR_F32) {
         // tensor-core (tcgen05) form where it applies; CUR_ERR_ARG means it does not
         const size_t mark = ar.off;
-        const cur_status s = residual_tc_impl(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+        const cur_status s = residual_tc_impl(h, A, C, U, R, r, cheb_out, fro_out, ar, st, sums_out);
         if (s != CUR_ERR_ARG) return s;
         ar.off = mark;
         ar.ok = true;
     }
     switch (A->dtype) {
-        case CUR_F64: return curk::residual_t<double, double, 4, 4>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
-        case CUR_F32: return curk::residual_t<float, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
-        case CUR_BF16: return curk::residual_t<__nv_bfloat16, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st);
+        case CUR_F64: return curk::residual_t<double, double, 4, 4>(h, A, C, U, R, r, cheb_out, fro_out, ar, st, sums_out);
+        case CUR_F32: return curk::residual_t<float, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st, sums_out);
+        case CUR_BF16: return curk::residual_t<__nv_bfloat16, float, 8, 8>(h, A, C, U, R, r, cheb_out, fro_out, ar, st, sums_out);
     }
     return CUR_ERR_ARG;
 }

@@ -379,7 +379,8 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
 }
 
 // Combines the per-CTA partials (same as the SIMT path's final step).
-__global__ void tc_final_k(const double* part, int64_t nparts, double* cheb, double* fro, int* status) {
+__global__ void tc_final_k(const double* part, int64_t nparts, double* cheb, double* fro, int* status,
+                           double* sums) {
     __shared__ double s1[256], s2[256], s3[256];
     __shared__ int sb[256];
     const int tid = threadIdx.x;
@@ -410,6 +411,7 @@ __global__ void tc_final_k(const double* part, int64_t nparts, double* cheb, dou
     }
     *cheb = a1;
     if (fro) *fro = s3[0] > 0.0 ? sqrt(s2[0] / s3[0]) : 0.0;
+    if (sums) { sums[0] = s2[0]; sums[1] = s3[0]; }
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -462,7 +464,7 @@ static inline unsigned nbk(int64_t n, int t = 256) {
 // Returns CUR_ERR_ARG when this path does not apply (the caller then uses the SIMT path).
 cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, const double* U,
                             const void* R, int r, double* cheb, double* fro, Arena& ar,
-                            cudaStream_t st) {
+                            cudaStream_t st, double* sums) {
     using namespace curk;
     if (Am->dtype != CUR_F32 || (r != 32 && r != 64)) return CUR_ERR_ARG;
     const int64_t m = Am->rows, n = Am->cols;
@@ -511,7 +513,7 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     residual_tc_k<<<grid, 32 * (3 + kEpiWarps), sm, st>>>(mWh, mWl, mCh, mCl, mA, a);
     CUR_CK(cudaGetLastError());
     note_launch();
-    tc_final_k<<<1, 256, 0, st>>>(part, grid, cheb, fro, h->status);
+    tc_final_k<<<1, 256, 0, st>>>(part, grid, cheb, fro, h->status, sums);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
