@@ -15,11 +15,15 @@
  *  - Ownership: the caller allocates every input and output buffer. The library
  *    owns only the handle and the workspace allocated once by cur_create; no call
  *    allocates device memory.
- *  - Streams: work is enqueued on `stream`. cur_aca_select, cur_assemble and
- *    cur_residual_cheb are asynchronous. cur_maxvol_rows, cur_maxvol_cols,
- *    cur_merge and cur_cross read small per-cycle counters back to the host and
- *    therefore synchronise `stream` between refresh cycles; their outputs are
- *    complete when they return.
+ *  - Streams: every call enqueues its work on `stream` and returns without waiting
+ *    for the GPU. Where the next step depends on a result (a singular start set, an
+ *    inverse valid to inherit, a sweep that made no swap), a kernel takes the decision
+ *    on the device; later steps run as no-ops when they are not needed. Outputs are
+ *    complete once the stream reaches that point (cur_sync_status synchronises and
+ *    returns the status). Calls that do wait for the GPU: cur_sync_status,
+ *    cur_prof_read, cur_cross_batched, and the BF16 / FP8 options of
+ *    cur_maxvol_global and of the polish (CUR_FLAG_PREC_BF16 / CUR_FLAG_PREC_FP8),
+ *    whose swap loop reads a counter back from the device.
  *  - Errors: argument errors (CUR_ERR_ARG), workspace exhaustion (CUR_ERR_NOMEM)
  *    and CUDA launch errors (CUR_ERR_CUDA) are returned at once. Errors found on
  *    the device (CUR_ERR_SINGULAR, CUR_ERR_NONFINITE, CUR_ERR_NOCONV,
@@ -171,7 +175,10 @@ cur_status cur_maxvol_cols(cur_handle* h, const cur_mat* A, const int32_t* I, in
                            const cur_opts* opts, int32_t* J_out, double* logvol_out,
                            int32_t* swaps_out, cudaStream_t stream);
 
-/* One level of the binary merge. basis: p x r tall basis (device); cand: nsets x r
+/* One level of the binary merge: the "binary parallel selection process" of Section 2.1,
+ * which the paper names but does not define, read as a tournament of pairwise merges
+ * in which each node runs the maximal-volume swap iteration (Section 1.2) on the union
+ * of its two children. basis: p x r tall basis (device); cand: nsets x r
  * row indices of the basis (device, set t in row t). Node t merges sets 2t and
  * 2t+1 by maxvol on their 2r rows (left set first) started at the left set (the
  * right set if the left one is singular, Algorithm 3 on the union if both are);
@@ -239,7 +246,8 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
  * E4M3 x E4M3 -> FP32 products, each row of C and of (M^-1)^T scaled to E4M3's range (448). Outputs (device): S_out r int32,
  * logvol_out 1 double (may be NULL), swaps_out 2 int32 (may be NULL): all swaps, and the
  * swaps of the BF16 phase. A singular C(S0,:) records CUR_ERR_SINGULAR (S_out = S0); more
- * than max_swaps records CUR_ERR_NOCONV. Synchronises the stream. */
+ * than max_swaps records CUR_ERR_NOCONV. With CUR_FLAG_PREC_BF16 / _FP8 the call
+ * synchronises the stream (its low-precision swap loop reads a counter back). */
 cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t* S0, int32_t r,
                              const cur_opts* opts, int32_t* S_out, double* logvol_out,
                              int32_t* swaps_out, cudaStream_t stream);
@@ -297,7 +305,7 @@ cur_status cur_propose(cur_handle* h, const float* scores, int64_t N, int32_t r,
  * J = J0, info logvol = -inf, and CUR_ERR_SINGULAR is recorded (the caller falls back to
  * cur_cross). A sweep stage that ends SINGULAR or NOCONV records that status. info_out:
  * one cur_cross_info (device, may be NULL; aca_selected = 0, status = the end status).
- * 1 <= r <= 128, r < min(m, n). Synchronises the stream. */
+ * 1 <= r <= 128, r < min(m, n). */
 cur_status cur_cross_from(cur_handle* h, const cur_mat* A, int32_t r, const int32_t* I0,
                           const int32_t* J0, const cur_opts* opts, int32_t* I_out, int32_t* J_out,
                           cur_cross_info* info_out, cudaStream_t stream);

@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -13,21 +15,12 @@ cur_status pad_indices_dev(int32_t* idx, const int32_t* count, int r, int64_t si
 
 namespace curk {
 
-__global__ void set_status_k(int* st, int code) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(st, code);
+__global__ void iota_k(int32_t* x, int r) {
+    for (int k = threadIdx.x; k < r; k += blockDim.x) x[k] = k;
 }
 
-__global__ void fill_info_k(cur_cross_info* info, const double* logvol, int sweeps, int swaps_total,
-                            int s0, int s1, int s2, int s3, int s4, int s5, int s6, int s7,
-                            const int32_t* aca_count, const int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    info->logvol = *logvol;
-    info->sweeps = sweeps;
-    info->swaps_total = swaps_total;
-    const int s[8] = {s0, s1, s2, s3, s4, s5, s6, s7};
-    for (int k = 0; k < 8; ++k) info->sweep_swaps[k] = s[k];
-    info->aca_selected = *aca_count;
-    info->status = *status;
+__global__ void set_status_k(int* st, int code) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(st, code);
 }
 
 // One CTA waits at a group barrier for a second CTA that is never launched: the
@@ -40,6 +33,19 @@ __global__ void selftest_wait_k(unsigned* ctr, int* status, long long limit) {
 
 static std::atomic<long long> g_launches{0};
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+cur_status smem_attr(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    CUR_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& cur = limit[std::make_pair(dev, fn)];
+    if (bytes <= cur) return CUR_OK;
+    CUR_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return CUR_OK;
+}
 
 cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
                        cudaStream_t st) {
@@ -254,6 +260,11 @@ cur_status cur_aca_full(cur_handle* h, const cur_mat* A, int32_t r, void* R_work
     return aca_full_impl(h, A, r, R_work, I_out, J_out, piv_out, ar, st);
 }
 
+// NOCONV of a row or column selection goes to the status word.
+__global__ void noconv_status_k(const MvDevResult* res, int* hstatus) {
+    if (threadIdx.x == 0 && res->status == CUR_ERR_NOCONV) curk::set_status(hstatus, CUR_ERR_NOCONV);
+}
+
 static cur_status rows_common(cur_handle* h, const cur_mat* A, const int32_t* idx, int32_t r,
                               const cur_opts* opts, int32_t* out, double* logvol_out,
                               int32_t* swaps_out, bool cols, cudaStream_t st) {
@@ -266,16 +277,14 @@ static cur_status rows_common(cur_handle* h, const cur_mat* A, const int32_t* id
     Arena ar = h->arena();
     const cur_dtype cdt = A->dtype == CUR_F64 ? CUR_F64 : CUR_F32;
     void* basis = ar.take((size_t)p * r * compute_size(cdt));
+    MvDevResult* res = ar.get<MvDevResult>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     if (cols) CUR_TRY(gather_rows_t_compute(A, idx, r, basis, st));
     else CUR_TRY(gather_cols_compute(A, idx, r, basis, st));
-    MvResult res;
-    CUR_TRY(maxvol_basis_rows(h, cdt, basis, p, r, &o, out, logvol_out, swaps_out, &res, ar, st));
-    if (res.status == CUR_ERR_NOCONV) {
-        curk::set_status_k<<<1, 32, 0, st>>>(h->status, CUR_ERR_NOCONV);
-        CUR_CK(cudaGetLastError());
-        note_launch();
-    }
+    CUR_TRY(maxvol_basis_rows(h, cdt, basis, p, r, &o, out, logvol_out, swaps_out, res, ar, st));
+    noconv_status_k<<<1, 32, 0, st>>>(res, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch();
     return CUR_OK;
 }
 
@@ -298,8 +307,10 @@ cur_status cur_merge(cur_handle* h, const cur_mat* basis, const int32_t* cand, i
     if (r < 1 || r > 128 || basis->cols != r || basis->ld != r || basis->rows < r) return CUR_ERR_ARG;
     const cur_opts o = opts ? *opts : cur_default_opts();
     Arena ar = h->arena();
-    int swaps = 0;
-    return merge_level(h, basis->dtype, basis->data, basis->rows, r, cand, nsets, &o, out, &swaps, ar, st);
+    int* acc = ar.get<int>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_CK(cudaMemsetAsync(acc, 0, sizeof(int), st));
+    return merge_level(h, basis->dtype, basis->data, basis->rows, r, cand, nsets, &o, out, acc, ar, st);
 }
 
 cur_status cur_assemble(cur_handle* h, const cur_mat* A, const int32_t* I, const int32_t* J,
@@ -365,78 +376,38 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
     double* lv = ar.get<double>(1);
     void* Cb = ar.take((size_t)m * r * cs);
     void* Rb = ar.take((size_t)n * r * cs);
-    if (!ar.ok) return CUR_ERR_NOMEM;
-
-    // J0: Algorithm 3 on the columns
-    CUR_TRY(aca_select_full(h, A, 1, r, J0, cnt, ar, st));
-    int stv = 0;
-    CUR_TRY(peek_status(h, st, &stv));
-    if (stv != CUR_OK && stv != CUR_WARN_RANK) return (cur_status)stv;
-    CUR_TRY(pad_indices_dev(J0, cnt, r, n, st));
-
-    int sweep_swaps[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int total = 0;
-    // sweep 1: blockwise rows on A(:,J0), then blockwise columns on A(I,:)^T
-    cur_opts orow = o;
-    orow.nblocks = b_r;
-    cur_opts ocol = o;
-    ocol.nblocks = b_c;
     // M^-1 of the last row stage (Mr = C(I,:)^-1) and column stage (Mc = R^T(J,:)^-1 =
     // (A(I,J)^T)^-1); each stage of a sweep starts from the other's inverse, transposed.
     double* Mr = ar.get<double>((size_t)minv_stride(r));
     double* Mc = ar.get<double>((size_t)minv_stride(r));
     double* lvr = ar.get<double>(1);
+    CrossCtl* ctl = ar.get<CrossCtl>(1);
+    MvDevResult* res = ar.get<MvDevResult>(2);
     if (!ar.ok) return CUR_ERR_NOMEM;
-    MvResult res;
-    CUR_TRY(gather_cols_compute(A, J0, r, Cb, st));
-    // status of the cross: a stage that ends NOCONV or SINGULAR marks it (the later
-    // stage's mark wins within sweep 1; a later sweep that does so ends the loop)
-    int last_status = CUR_OK;
-    CUR_TRY(maxvol_basis_rows(h, cdt, Cb, m, r, &orow, I, nullptr, nullptr, &res, ar, st));
-    sweep_swaps[0] += res.swaps;
-    if (res.status != CUR_OK) last_status = res.status;
-    CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
-    CUR_TRY(maxvol_basis_rows(h, cdt, Rb, n, r, &ocol, J, lv, nullptr, &res, ar, st, Mc));
-    sweep_swaps[0] += res.swaps;
-    if (res.status != CUR_OK) last_status = res.status;
-    int mc_valid = res.minv_valid;
-    int sweeps = 1;
-    while (sweeps < max_sweeps) {
-        ++sweeps;
-        MvResult r1, r2;
-        CUR_TRY(gather_cols_compute(A, J, r, Cb, st));
-        CUR_TRY(maxvol_global(h, cdt, Cb, m, r, &o, I, I, lvr, &r1, ar, st,
-                              mc_valid ? Mc : nullptr, mc_valid ? lv : nullptr, true, Mr, true));
-        CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
-        CUR_TRY(maxvol_global(h, cdt, Rb, n, r, &o, J, J, lv, &r2, ar, st,
-                              r1.minv_valid ? Mr : nullptr, r1.minv_valid ? lvr : nullptr, true, Mc, true));
-        mc_valid = r2.minv_valid;
-        sweep_swaps[sweeps - 1] = r1.swaps + r2.swaps;
-        if (r1.status != CUR_OK || r2.status != CUR_OK) {
-            last_status = r1.status != CUR_OK ? r1.status : r2.status;
-            break;
-        }
-        if (r1.swaps + r2.swaps == 0) break;
-    }
-    for (int k = 0; k < 8; ++k) total += sweep_swaps[k];
-    // A stage that ended singular leaves no log|det| of its own: the log-volume of the
-    // returned cross, |det A(I,J)| = |det Rb(J,:)| with Rb = A(I,:)^T, is taken directly.
-    if (last_status != CUR_OK) CUR_TRY(logvol_rows(cdt, Rb, r, J, lv, st));
-    if (last_status == CUR_ERR_NOCONV || last_status == CUR_ERR_SINGULAR) {
-        curk::set_status_k<<<1, 32, 0, st>>>(h->status, last_status);
-        CUR_CK(cudaGetLastError());
-        note_launch();
-    }
-    CUR_CK(cudaMemcpyAsync(I_out, I, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    CUR_CK(cudaMemcpyAsync(J_out, J, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    if (info_out) {
-        curk::fill_info_k<<<1, 32, 0, st>>>(info_out, lv, sweeps, total, sweep_swaps[0], sweep_swaps[1],
-                                            sweep_swaps[2], sweep_swaps[3], sweep_swaps[4], sweep_swaps[5],
-                                            sweep_swaps[6], sweep_swaps[7], cnt, h->status);
-        CUR_CK(cudaGetLastError());
-        note_launch();
-    }
-    return CUR_OK;
+    // index sets start as 0..r-1, so that every gather reads inside A even when a stage idles
+    curk::iota_k<<<1, 128, 0, st>>>(I, r);
+    curk::iota_k<<<1, 128, 0, st>>>(J, r);
+    CUR_CK(cudaGetLastError());
+    note_launch(2);
+
+    // J0: Algorithm 3 on the columns; an error it records makes everything after it idle
+    CUR_TRY(aca_select_full(h, A, 1, r, J0, cnt, ar, st));
+    CUR_TRY(cross_begin(ctl, h->status, true, st));
+    CUR_TRY(pad_indices_dev(J0, cnt, r, n, st));
+
+    // sweep 1: blockwise rows on A(:,J0), then blockwise columns on A(I,:)^T
+    cur_opts orow = o;
+    orow.nblocks = b_r;
+    cur_opts ocol = o;
+    ocol.nblocks = b_c;
+    CUR_TRY(gather_cols_compute(A, J0, r, Cb, st, &ctl->abort));
+    CUR_TRY(maxvol_basis_rows(h, cdt, Cb, m, r, &orow, I, nullptr, nullptr, &res[0], ar, st, nullptr, &ctl->abort));
+    CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st, &ctl->abort));
+    CUR_TRY(maxvol_basis_rows(h, cdt, Rb, n, r, &ocol, J, lv, nullptr, &res[1], ar, st, Mc, &ctl->abort));
+    CUR_TRY(cross_sweep_one(ctl, &res[0], &res[1], st));
+    // sweeps 2 .. 8: global maxvol on the rows, then on the columns, until one swaps nothing
+    CUR_TRY(cross_sweeps(h, A, r, &o, 2, max_sweeps, false, I, J, Cb, Rb, Mr, Mc, lvr, lv, ctl, ar, st));
+    return cross_end(h, A, r, false, I, J, Rb, lv, ctl, cnt, I_out, J_out, info_out, ar, st);
 }
 
 }  // extern "C"

@@ -267,7 +267,7 @@ cur_status bat_aca_launch(const float* data, const void* items_dev, const int32_
                           int32_t* J, int32_t* counts, float* Qws, int grid, int* status, cudaStream_t st) {
     using namespace curk;
     const size_t sm = bat_aca_smem();
-    CUR_CK(cudaFuncSetAttribute((const void*)bat_aca_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUR_TRY(smem_attr((const void*)bat_aca_k, sm));
     CUR_CK(cudaMemsetAsync(queue, 0, sizeof(int), st));
     bat_aca_k<<<grid, kBA_T, sm, st>>>(data, static_cast<const BatAcaItem*>(items_dev), order, queue, count, J,
                                        counts, Qws, status);

@@ -103,10 +103,16 @@ cur_status aca_select_full(cur_handle* h, const cur_mat* A, int axis, int r, int
                            int32_t* count_dev, Arena& ar, cudaStream_t st);
 
 // ---- maxvol pipelines (maxvol.cu)
-struct MvResult {
-    int swaps = 0;
-    int status = CUR_OK;
-    int minv_valid = 0;   // minv_out holds the final FP64 M^-1
+//
+// The pipelines only enqueue: every decision that depends on a result (a singular start, an
+// inverse valid to inherit, the end of the sweeps) is taken by a kernel on the device.
+
+// A maxvol call's result, written on the device for later kernels (the host never reads it).
+struct MvDevResult {
+    int32_t swaps;
+    int32_t status;
+    int32_t minv_valid;   // minv_out holds the final FP64 M^-1
+    int32_t pad;
 };
 // An inverse handed between stages is minv_stride(r) doubles: M^-1 (r x r, row-major),
 // then a bound on the rounding drift that Sherman-Morrison updates have added to it since
@@ -116,35 +122,64 @@ inline __host__ __device__ int64_t minv_stride(int r) { return (int64_t)r * r + 
 // Row selection on the tall basis `basis` (p x r, compute type of A's dtype,
 // contiguous) with nblocks blocks, merge and optional polish. I_out: device r ints.
 // With minv_out (minv_stride(r) doubles, device), the final FP64 M^-1 = C(I,:)^-1 is written
-// there (res->minv_valid says whether it is valid).
+// there (res->minv_valid says whether it is valid). res: device, may be null. Nothing runs
+// while *idle != 0 (device flag, may be null).
 cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                              const cur_opts* o, int32_t* I_out, double* logvol_out,
-                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st,
-                             double* minv_out = nullptr);
+                             int32_t* swaps_out, MvDevResult* res, Arena& ar, cudaStream_t st,
+                             double* minv_out = nullptr, const int* idle = nullptr);
 // Maxvol over all rows of a basis from the start rows S0 (device r ints, global
 // rows). Writes the result to S_out (device, may alias S0).
 // minv_in / lv_in (optional): M^-1 and log|det| of the start rows, given as is or as the
 // transpose of the inverse (transpose_in) — a column stage's M^-1 is the transpose of the
-// next row stage's; no factorisation is made then. minv_out as for maxvol_basis_rows.
+// next row stage's; valid while *minv_in_valid != 0 (device; null: valid); no factorisation is
+// made then. minv_out as for maxvol_basis_rows.
 // If the set turns numerically singular, S_out is the start set, or with
 // keep_singular_set the set reached at that point (the swap iteration's own result).
 cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
-                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
+                         double* logvol_out, MvDevResult* res, Arena& ar, cudaStream_t st,
                          const double* minv_in = nullptr, const double* lv_in = nullptr,
-                         bool transpose_in = false, double* minv_out = nullptr,
-                         bool keep_singular_set = false);
-// One merge level (cur_merge).
+                         const int* minv_in_valid = nullptr, bool transpose_in = false,
+                         double* minv_out = nullptr, bool keep_singular_set = false,
+                         const int* idle = nullptr);
+// One merge level (cur_merge); its swaps are added to *acc_dev (device int).
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
-                       int* swaps, Arena& ar, cudaStream_t st);
+                       int* acc_dev, Arena& ar, cudaStream_t st);
+
+// The sweeps of a cross on the device (cur_cross, cur_cross_from).
+struct CrossCtl {
+    int idle;             // nonzero: the remaining sweeps do nothing
+    int abort;            // Algorithm 3 met an error: nothing after it runs
+    int sweeps;
+    int sweep_swaps[8];
+    int last_status;      // a stage that ended NOCONV or SINGULAR
+    int mc_valid;         // the last column stage's inverse is valid
+    int singular_start;   // cur_cross_from: the proposed A(I0, J0) is singular
+};
+// Starts the control block; with check_status, an error already in the status word (from
+// Algorithm 3) makes every later stage idle.
+cur_status cross_begin(CrossCtl* ctl, const int* hstatus, bool check_status, cudaStream_t st);
+// Sweep 1 of cur_cross (blockwise rows and columns) ended with these results.
+cur_status cross_sweep_one(CrossCtl* ctl, const MvDevResult* rr, const MvDevResult* rc, cudaStream_t st);
+// Sweeps first .. max_sweeps (all enqueued; idle once one makes no swap or ends with an error).
+cur_status cross_sweeps(cur_handle* h, const cur_mat* A, int r, const cur_opts* o, int first, int max_sweeps,
+                        bool from, int32_t* I, int32_t* J, void* Cb, void* Rb, double* Mr, double* Mc, double* lvr,
+                        double* lv, CrossCtl* ctl, Arena& ar, cudaStream_t st);
+// The cross's log-volume, status, outputs and info.
+cur_status cross_end(cur_handle* h, const cur_mat* A, int r, bool from, const int32_t* I, const int32_t* J,
+                     void* Rb, double* lv, CrossCtl* ctl, const int32_t* aca_count, int32_t* I_out, int32_t* J_out,
+                     cur_cross_info* info_out, Arena& ar, cudaStream_t st);
+// Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r); nothing runs
+// while *idle != 0.
+cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st,
+                               const int* idle = nullptr);
 // The merge of two candidate sets given by their rows (2r x r, left set first) and ids
 // (cur_merge_pair).
 cur_status merge_pair_impl(cur_handle* h, cur_dtype dt, const void* rows, const int32_t* ids, int r,
                            const cur_opts* o, int32_t* ids_out, void* rows_out, int32_t* swaps_out, Arena& ar,
                            cudaStream_t st);
-// Gathers into the compute type: C = A(:,J) (m x r) and Rt = A(I,:)^T (n x r).
-cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st);
 // The cross of every matrix of a batch (cur_cross_batched), FP32 data.
 cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_item* items, int T,
                               const cur_opts* o, int32_t* IJ_out, cur_cross_info* info_out, Arena& ar,
@@ -154,11 +189,12 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
 cur_status aca_full_impl(cur_handle* h, const cur_mat* A, int r, void* R, int32_t* I, int32_t* J,
                          double* piv, Arena& ar, cudaStream_t st);
 // log|det basis(rows,:)| (rows: device r ints) into *out (device), -inf for an exactly
-// singular matrix; basis p x r contiguous in the compute type of dt.
-cur_status logvol_rows(cur_dtype dt, const void* basis, int r, const int32_t* rows, double* out,
+// singular matrix; basis p x r contiguous in the compute type of dt (a row id outside
+// [0, p) reads as a zero row).
+cur_status logvol_rows(cur_dtype dt, const void* basis, int64_t p, int r, const int32_t* rows, double* out,
                        cudaStream_t st);
 cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void* Rt,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const int* idle = nullptr);
 size_t compute_size(cur_dtype t);
 
 // ---- low-precision coefficient phase of global maxvol (lowprec.cu)
@@ -189,6 +225,15 @@ cur_status residual_impl(cur_handle* h, const cur_mat* A, const void* C, const d
 cur_status residual_tc_impl(cur_handle* h, const cur_mat* A, const void* C, const double* U,
                             const void* R, int r, double* cheb_out, double* fro_out, Arena& ar,
                             cudaStream_t st, double* sums_out = nullptr);
+
+// Raises a kernel's dynamic shared-memory limit (on the current device) to at least `bytes`
+// and never lowers it, so that calls from several host threads cannot shrink the limit
+// under another thread's launch.
+cur_status smem_attr(const void* fn, size_t bytes);
+
+// Small host tables to device memory as kernel parameters (no host buffer outlives the
+// call, the host never waits): maxvol.cu.
+cur_status upload_table(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
 // Cooperative launch helper (all CTAs co-resident).
 cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,

@@ -512,6 +512,17 @@ __global__ void lp_finish_k(int32_t* swaps_out, const LpCtl* ctl, int exact_swap
     if (code == CUR_ERR_SINGULAR || code == CUR_ERR_NOCONV || code == CUR_ERR_NONFINITE) set_status(hstatus, code);
 }
 
+// The same with the exact engine's result on the device.
+__global__ void lp_finish_dev_k(int32_t* swaps_out, const LpCtl* ctl, const MvDevResult* res, int* hstatus) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (swaps_out) {
+        swaps_out[0] = ctl->swaps + res->swaps;
+        swaps_out[1] = ctl->swaps;
+    }
+    const int code = res->status;
+    if (code == CUR_ERR_SINGULAR || code == CUR_ERR_NOCONV || code == CUR_ERR_NONFINITE) set_status(hstatus, code);
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 lp_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -596,15 +607,13 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
         lp_setup_from_k<F8><<<1, 256, 0, st>>>(minv_in, r, ldk, W, winv, Mh, Ml, ctl);
     } else {
         const size_t sm_setup = (size_t)r * r * sizeof(double) + (size_t)r * sizeof(double) + (size_t)r * sizeof(int) + 64;
-        CUR_CK(cudaFuncSetAttribute((const void*)lp_setup_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_setup));
+        CUR_TRY(smem_attr((const void*)lp_setup_k<F8>, sm_setup));
         lp_setup_k<F8><<<1, 256, sm_setup, st>>>(C, r, ldk, S, W, winv, Mh, Ml, ctl);
     }
     CUR_CK(cudaGetLastError());
     note_launch(2);
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_of(4)));
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_argmax_k<F8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem_of(2)));
+    CUR_TRY(smem_attr((const void*)lp_argmax_k<F8, 4>, smem_of(4)));
+    CUR_TRY(smem_attr((const void*)lp_argmax_k<F8, 2>, smem_of(2)));
     auto launch_argmax = [&](Shape c) -> cur_status {
         const int g = grid_of(c);
         if (c.ns == 4)
@@ -640,7 +649,7 @@ static cur_status lowprec_phase_t(cur_handle* h, const float* C, int64_t p, int 
     const int grid = grid_of(shape);
     const size_t sm_swap = (size_t)r * sizeof(double) + 2 * (size_t)r * sizeof(df64) +
                            2 * (size_t)r * (r + 1) * sizeof(float) + 16;
-    CUR_CK(cudaFuncSetAttribute((const void*)lp_swap_k<F8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_swap));
+    CUR_TRY(smem_attr((const void*)lp_swap_k<F8>, sm_swap));
     const int max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
     LpCtl* hc = reinterpret_cast<LpCtl*>(h->host_stage);
     CUR_CK(cudaEventSynchronize(h->stage_ev));   // host_stage is free once its last copy has run
@@ -700,12 +709,12 @@ static cur_status maxvol_global_bf16(cur_handle* h, const float* C, int64_t p, i
         CUR_CK(cudaStreamSynchronize(st));
         return CUR_OK;
     }
-    MvResult res;
-    CUR_TRY(maxvol_global(h, CUR_F32, C, p, r, o, S_out, S_out, logvol_out, &res, ar, st));
-    lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, res.swaps, res.status, h->status);
+    MvDevResult* res = ar.get<MvDevResult>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(maxvol_global(h, CUR_F32, C, p, r, o, S_out, S_out, logvol_out, res, ar, st));
+    lp_finish_dev_k<<<1, 32, 0, st>>>(swaps_out, ctl, res, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
-    CUR_CK(cudaStreamSynchronize(st));
     return CUR_OK;
 }
 
@@ -726,12 +735,12 @@ cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t*
                                   swaps_out, ar, st);
     }
     if (basis->dtype != CUR_F32 && basis->dtype != CUR_F64) return CUR_ERR_ARG;
-    MvResult res;
-    CUR_TRY(maxvol_global(h, basis->dtype, basis->data, p, r, &o, S0, S_out, logvol_out, &res, ar, st));
+    MvDevResult* res = ar.get<MvDevResult>(1);
     curk::LpCtl* ctl = ar.get<curk::LpCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(maxvol_global(h, basis->dtype, basis->data, p, r, &o, S0, S_out, logvol_out, res, ar, st));
     CUR_CK(cudaMemsetAsync(ctl, 0, sizeof(curk::LpCtl), st));
-    curk::lp_finish_k<<<1, 32, 0, st>>>(swaps_out, ctl, res.swaps, res.status, h->status);
+    curk::lp_finish_dev_k<<<1, 32, 0, st>>>(swaps_out, ctl, res, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;

@@ -88,7 +88,8 @@ struct MvArgs {
 template <typename TA, typename TB>
 __global__ void gather_cols_k(const TA* __restrict__ A, int64_t m, int64_t n, int64_t ld,
                               const int32_t* __restrict__ J, int r, TB* __restrict__ C,
-                              int* status) {
+                              int* status, const int* idle) {
+    if (idle && *idle) return;
     const int64_t total = m * r;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -109,8 +110,9 @@ template <typename TA, typename TB>
 __global__ void __launch_bounds__(256) gather_rows_t_k(const TA* __restrict__ A, int64_t m,
                                                        int64_t n, int64_t ld,
                                                        const int32_t* __restrict__ I, int r,
-                                                       TB* __restrict__ Rt, int* status) {
+                                                       TB* __restrict__ Rt, int* status, const int* idle) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (idle && *idle) return;
     TB* tile = reinterpret_cast<TB*>(smem_raw);  // r x 33
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t j0 = (int64_t)blockIdx.x * 32;
@@ -210,6 +212,7 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
+    if (a.done[pb]) return;   // every CTA of the group leaves together: no barrier is left waiting
     const MvProb pr = a.prob[pb];
     const int r = pr.r, rs = a.r, G = pr.G;
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
@@ -969,7 +972,7 @@ __global__ void mv_iota(int32_t* S, int P, int r, int off) {
 // i >= k), the log-volume of Definition 1 for a set that may be numerically singular:
 // a pivot that is exactly zero gives -inf, any other pivot counts however small.
 template <typename TB>
-__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int r, const int32_t* rows,
+__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int64_t p, int r, const int32_t* rows,
                                                      double* out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* M = reinterpret_cast<double*>(smem_raw);
@@ -978,7 +981,8 @@ __global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int r, con
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < r * r; e += nt) {
         const int k = e / r, c = e - k * r;
-        M[e] = to_d(basis[(int64_t)rows[k] * r + c]);
+        const int64_t i = rows[k];
+        M[e] = (i >= 0 && i < p) ? to_d(basis[i * r + c]) : 0.0;   // a row outside: a zero row
     }
     if (tid == 0) { s_zero = 0; s_acc.init(); }
     __syncthreads();
@@ -1052,7 +1056,7 @@ static int rows_cap(int r) {
 
 template <typename K>
 static cur_status set_smem_attr(K* fn, size_t bytes) {
-    CUR_CK(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    CUR_TRY(smem_attr((const void*)fn, bytes));
     return CUR_OK;
 }
 
@@ -1060,10 +1064,51 @@ static inline unsigned nblk(int64_t n, int t = 256) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
 }
 
+// ---------------------------------------------------------------- uploads without waiting
+//
+// The stage tables (problem descriptors, CTA slots) are known on the host from the shapes
+// alone. They reach the device as the parameters of a copy kernel: the launch takes its
+// own copy of the parameters, so no host buffer has to outlive the call and the host
+// never waits for the GPU before reusing one.
+// Two parameter sizes: one short launch for the common small table, few launches of nearly
+// the 32 KB parameter limit for the tables of large batches.
+template <int N>
+struct Blob {
+    unsigned char* dst;
+    int bytes;
+    int pad;
+    unsigned char data[N];
+};
+template <int N>
+__global__ void blob_k(const Blob<N> b) {
+    for (int i = threadIdx.x; i < b.bytes; i += blockDim.x) b.dst[i] = b.data[i];
+}
+template <int N>
+static cur_status upload_n(unsigned char* dst, const unsigned char* src, size_t bytes, cudaStream_t st) {
+    Blob<N> b;
+    for (size_t off = 0; off < bytes; off += N) {
+        const size_t n = std::min<size_t>(N, bytes - off);
+        b.dst = dst + off;
+        b.bytes = (int)n;
+        std::memcpy(b.data, src + off, n);
+        blob_k<N><<<1, 256, 0, st>>>(b);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
+    return CUR_OK;
+}
+static cur_status upload(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    unsigned char* d = static_cast<unsigned char*>(dst);
+    const unsigned char* s = static_cast<const unsigned char*>(src);
+    if (bytes <= 2048) return upload_n<2048>(d, s, bytes, st);
+    return upload_n<30720>(d, s, bytes, st);
+}
+
 // One stage: a set of problems on one basis buffer. The caller fills probs (base,
 // gid_base, gid_arr, p); stage_setup plans the CTA groups and allocates per-problem
-// state; stage_run runs the optional Algorithm 3 start, the FP64 inverse where
-// lu_mask is set, and the engine.
+// state; stage_tables uploads the plan; stage_init sets the per-problem flags; decision
+// kernels may then change them on the device; stage_launch runs the optional Algorithm 3
+// start, the FP64 inverse where lu_mask is set, and the engine, for problems not done.
 template <typename TB>
 struct Stage {
     std::vector<MvProb> probs;
@@ -1077,12 +1122,13 @@ struct Stage {
     int32_t* swaps = nullptr;
     int32_t* pstatus = nullptr;
     int32_t* done = nullptr;
+    int32_t* retry = nullptr;  // merge levels: which start a problem is on
     unsigned* bar = nullptr;
     double* keyv = nullptr;
     long long* keyi = nullptr;
     TB* pub = nullptr;
     double* aux = nullptr;
-    std::vector<int> stat, sw;  // host copies after read()
+    std::vector<int> stat, sw;  // host copies after stage_read (batches only)
     int coop_slots = 0;         // slots [0, coop_slots) hold groups of several CTAs
     bool keep_singular_set = false;
     TB* bglob = nullptr;        // B in global memory when it cannot live in shared memory
@@ -1151,6 +1197,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar, bo
     sg.swaps = ar.get<int32_t>(P);
     sg.pstatus = ar.get<int32_t>(P);
     sg.done = ar.get<int32_t>(P);
+    sg.retry = ar.get<int32_t>(P);
     sg.bar = ar.get<unsigned>(P);
     sg.keyv = ar.get<double>((size_t)2 * slots);
     sg.keyi = ar.get<long long>((size_t)2 * slots);
@@ -1161,36 +1208,50 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar, bo
     return CUR_OK;
 }
 
-// lu_mask / skip: host vectors of length P (empty = all 1 / all 0).
+// The stage plan to the device: problem descriptors and the CTA slot tables.
 template <typename TB>
-static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opts* o, Stage<TB>& sg,
-                            bool aca_start, const std::vector<int>& lu_mask,
-                            const std::vector<int>& skip, cudaStream_t st) {
+static cur_status stage_tables(Stage<TB>& sg, cudaStream_t st) {
     const int P = sg.P, slots = sg.slots;
-    const size_t tab_bytes = sizeof(int32_t) * (2 * (size_t)slots + P);
-    const size_t need = sizeof(MvProb) * P + tab_bytes + sizeof(int32_t) * P + 64;
-    if (need > h->host_stage_bytes) return CUR_ERR_NOMEM;
-    // the staging buffer may still feed the previous stage's table copy: wait for that
-    // copy only, not for the kernels queued since
-    CUR_CK(cudaEventSynchronize(h->stage_ev));
-    char* hs = h->host_stage;
-    std::memcpy(hs, sg.probs.data(), sizeof(MvProb) * P);
-    int32_t* ht = reinterpret_cast<int32_t*>(hs + sizeof(MvProb) * P);
+    std::vector<int32_t> tab((size_t)2 * slots);
     for (int pb = 0; pb < P; ++pb)
         for (int g = 0; g < sg.probs[pb].G; ++g) {
-            ht[sg.probs[pb].group0 + g] = pb;
-            ht[slots + sg.probs[pb].group0 + g] = g;
+            tab[sg.probs[pb].group0 + g] = pb;
+            tab[slots + sg.probs[pb].group0 + g] = g;
         }
-    for (int pb = 0; pb < P; ++pb) ht[2 * slots + pb] = lu_mask.empty() ? 1 : lu_mask[pb];
-    int32_t* hdone = ht + 2 * slots + P;
-    for (int pb = 0; pb < P; ++pb) hdone[pb] = (!skip.empty() && skip[pb]) ? 1 : 0;
-    CUR_CK(cudaMemcpyAsync(sg.dprob, hs, sizeof(MvProb) * P, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaMemcpyAsync(sg.dtab, ht, tab_bytes, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaMemcpyAsync(sg.done, hdone, sizeof(int32_t) * P, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaEventRecord(h->stage_ev, st));
-    CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
-    CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
+    CUR_TRY(upload(sg.dprob, sg.probs.data(), sizeof(MvProb) * P, st));
+    CUR_TRY(upload(sg.dtab, tab.data(), sizeof(int32_t) * tab.size(), st));
+    return CUR_OK;
+}
 
+// Per-problem defaults: factorise (lu_mask 1), not done (or all done while *idle != 0),
+// no swaps, status OK.
+__global__ void stage_init_k(int32_t* lu_mask, int32_t* done, int32_t* swaps, int32_t* pstatus, int32_t* retry,
+                             int P, const int* idle) {
+    const int sk = idle ? (*idle != 0) : 0;
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
+        lu_mask[pb] = 1;
+        done[pb] = sk;
+        swaps[pb] = 0;
+        pstatus[pb] = 0;
+        retry[pb] = 0;
+    }
+}
+
+template <typename TB>
+static cur_status stage_init(Stage<TB>& sg, const int* idle, cudaStream_t st) {
+    stage_init_k<<<nblk(sg.P), 256, 0, st>>>(sg.dtab + 2 * sg.slots, sg.done, sg.swaps, sg.pstatus, sg.retry, sg.P,
+                                            idle);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+// The stage's kernels: the Algorithm 3 start (aca_start), the FP64 inverses where lu_mask is
+// set, the swap engine; every kernel skips the problems marked done.
+template <typename TB>
+static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_opts* o, Stage<TB>& sg,
+                               bool aca_start, cudaStream_t st) {
+    const int P = sg.P, slots = sg.slots;
     MvArgs a{};
     a.basis = basis;
     a.minv64 = sg.minv64;
@@ -1239,7 +1300,6 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     const int cap_start = std::max(1, occ_start) * h->num_sms;
     for (auto& pr : sg.probs)
         if (pr.G > cap_eng || (aca_start && pr.G > cap_start)) return CUR_ERR_ARG;
-    // waves: consecutive whole groups within the co-residency capacity
     // cooperative waves of whole multi-CTA groups, then one plain launch of the rest
     auto waves = [&](int capc) {
         std::vector<std::pair<int, int>> w;
@@ -1292,7 +1352,27 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     return CUR_OK;
 }
 
-// Per-problem statuses and swap counts to the host (synchronises the stream).
+// Batches (below) decide between their stages on the host: lu_mask / skip are host vectors
+// of length P (empty = all 1 / all 0), uploaded with the plan.
+template <typename TB>
+static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opts* o, Stage<TB>& sg,
+                            bool aca_start, const std::vector<int>& lu_mask,
+                            const std::vector<int>& skip, cudaStream_t st) {
+    const int P = sg.P;
+    CUR_TRY(stage_tables(sg, st));
+    std::vector<int32_t> lm(P), dn(P);
+    for (int pb = 0; pb < P; ++pb) {
+        lm[pb] = lu_mask.empty() ? 1 : lu_mask[pb];
+        dn[pb] = (!skip.empty() && skip[pb]) ? 1 : 0;
+    }
+    CUR_TRY(upload(sg.dtab + 2 * sg.slots, lm.data(), sizeof(int32_t) * P, st));
+    CUR_TRY(upload(sg.done, dn.data(), sizeof(int32_t) * P, st));
+    CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
+    CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
+    return stage_launch<TB>(h, basis, r, o, sg, aca_start, st);
+}
+
+// Per-problem statuses and swap counts to the host (synchronises the stream; batches only).
 template <typename TB>
 static cur_status stage_read(cur_handle* h, Stage<TB>& sg, cudaStream_t st) {
     const int P = sg.P;
@@ -1306,30 +1386,166 @@ static cur_status stage_read(cur_handle* h, Stage<TB>& sg, cudaStream_t st) {
     return CUR_OK;
 }
 
-// One merge level on `basis` (p x r): sets in cand (nsets x r, global rows). in_minv /
-// in_lv give, per input set, the device address of its M^-1 (rows in set order) and
-// log|det| when known (null otherwise); node t then starts from its left set's M^-1
-// instead of a new factorisation. out_minv / out_lv describe the output sets.
+// ---------------------------------------------------------------- decisions on the device
+//
+// Where the next step depends on a result (a singular start, a valid inverse to inherit,
+// whether a sweep swapped), a small kernel reads the result and sets the next stage's
+// flags; nothing returns to the host, so the calls only enqueue.
+
+// Where an inherited inverse comes from: M^-1 (minv_stride doubles) and log|det| of the
+// start rows, valid when flag says so (mode 0: *flag != 0; mode 1: *flag is CUR_OK or
+// CUR_ERR_NOCONV, the status of the stage that produced it; no flag: valid).
+struct InheritSrc {
+    const double* minv;
+    const double* lv;
+    const int* flag;
+    int mode;
+    int transpose;
+};
+
+// Problem t (one CTA each) starts from src[t]'s inverse when it is valid: copy (or transpose)
+// it, take its log|det|, and skip the factorisation.
+__global__ void inherit_k(const InheritSrc* __restrict__ src, int r, double* minv64, double* logvol,
+                          int32_t* lu_mask, const int32_t* done) {
+    const int t = blockIdx.x;
+    const InheritSrc s = src[t];
+    if (done[t] || !s.minv || !s.lv) return;
+    const bool valid = !s.flag || (s.mode == 0 ? *s.flag != 0 : (*s.flag == CUR_OK || *s.flag == CUR_ERR_NOCONV));
+    if (!valid) return;
+    const int64_t stride = minv_stride(r);
+    double* dst = minv64 + (int64_t)t * stride;
+    for (int e = threadIdx.x; e <= r * r; e += blockDim.x) {
+        const int a = e / r, b = e - a * r;
+        dst[e] = (e == r * r || !s.transpose) ? s.minv[e] : s.minv[b * r + a];
+    }
+    if (threadIdx.x == 0) {
+        logvol[t] = *s.lv;
+        lu_mask[t] = 0;
+    }
+}
+
+static cur_status launch_inherit(const std::vector<InheritSrc>& src, int r, double* minv64, double* logvol,
+                                 int32_t* lu_mask, const int32_t* done, InheritSrc* dsrc, cudaStream_t st) {
+    if (src.empty()) return CUR_OK;
+    CUR_TRY(upload(dsrc, src.data(), sizeof(InheritSrc) * src.size(), st));
+    inherit_k<<<(unsigned)src.size(), 128, 0, st>>>(dsrc, r, minv64, logvol, lu_mask, done);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+// After attempt `attempt` of a merge level: a node whose start was singular moves on to the
+// next start (after attempt 0: the right set, positions r..2r-1 of its union; after attempt
+// 1: Algorithm 3 on the union, formed by mv_start); the swaps of a node that finished are
+// added to *acc, those of an abandoned attempt are not counted.
+__global__ void merge_retry_k(int attempt, int P, int r, int32_t* pstatus, int32_t* swaps, int32_t* done,
+                              int32_t* lu_mask, int32_t* S, int32_t* retry, int* acc) {
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
+        if (attempt > 0 && retry[pb] != attempt) continue;
+        const bool sing = pstatus[pb] == CUR_ERR_SINGULAR;
+        if (attempt < 2 && sing) {
+            retry[pb] = attempt + 1;
+            pstatus[pb] = CUR_OK;
+            swaps[pb] = 0;
+            done[pb] = 0;
+            lu_mask[pb] = 1;
+            if (attempt == 0)
+                for (int k = 0; k < r; ++k) S[(int64_t)pb * r + k] = r + k;
+        } else {
+            retry[pb] = 0;
+            atomicAdd(acc, swaps[pb]);
+        }
+    }
+}
+
+// acc += sum of swaps[0..P)
+__global__ void acc_swaps_k(const int32_t* swaps, int P, int* acc) {
+    int s = 0;
+    for (int pb = threadIdx.x; pb < P; pb += blockDim.x) s += swaps[pb];
+    atomicAdd(acc, s);
+}
+
+// The end of a global maxvol stage: the set (the start set again if the iteration turned
+// singular, unless keep), log|det|, the final inverse and the device result.
+__global__ void global_finish_k(const int32_t* pstatus, const int32_t* swaps, const int32_t* Sst, const int32_t* S0,
+                                int r, int keep, int32_t* S_out, const double* lv_st, double* logvol_out,
+                                const double* minv64, double* minv_out, MvDevResult* res, const int* idle) {
+    if (idle && *idle) return;
+    const int stv = pstatus[0];
+    const bool ok = stv != CUR_ERR_SINGULAR && stv != CUR_ERR_ARG && stv != CUR_ERR_NONFINITE && stv != CUR_ERR_TIMEOUT;
+    const bool use_stage = (stv != CUR_ERR_SINGULAR || keep) && stv != CUR_ERR_ARG;
+    for (int k = threadIdx.x; k < r; k += blockDim.x) S_out[k] = use_stage ? Sst[k] : S0[k];
+    if (minv_out && ok)
+        for (int e = threadIdx.x; e <= r * r; e += blockDim.x) minv_out[e] = minv64[e];
+    if (threadIdx.x == 0) {
+        if (logvol_out) *logvol_out = *lv_st;
+        if (res) {
+            res->swaps = swaps[0];
+            res->status = stv;
+            res->minv_valid = (ok && minv_out) ? 1 : 0;
+        }
+    }
+}
+
+// Row selection without the polish: the merged set, its inverse and log|det| (when the root
+// problem's status makes them valid; else the log-volume taken directly, lv_direct).
+__global__ void rows_root_k(const int32_t* root, int r, int32_t* I_out, const double* root_minv, const double* root_lv,
+                            const int* root_stat, const double* lv_direct, double* logvol_out, double* minv_out,
+                            const int* acc, int32_t* swaps_out, MvDevResult* res, const int* idle) {
+    if (idle && *idle) return;
+    const bool valid = root_minv && root_lv && (!root_stat || *root_stat == CUR_OK || *root_stat == CUR_ERR_NOCONV);
+    for (int k = threadIdx.x; k < r; k += blockDim.x) I_out[k] = root[k];
+    if (minv_out && valid)
+        for (int e = threadIdx.x; e <= r * r; e += blockDim.x) minv_out[e] = root_minv[e];
+    if (threadIdx.x == 0) {
+        if (logvol_out) *logvol_out = valid ? *root_lv : *lv_direct;
+        if (swaps_out) *swaps_out = *acc;
+        if (res) {
+            res->swaps = *acc;
+            res->status = CUR_OK;
+            res->minv_valid = (valid && minv_out) ? 1 : 0;
+        }
+    }
+}
+
+// Row selection with the polish: the counts add up.
+__global__ void rows_polish_k(const int* acc, const MvDevResult* pol, int32_t* swaps_out, MvDevResult* res,
+                              const int* idle) {
+    if (idle && *idle) return;
+    if (threadIdx.x != 0) return;
+    const int tot = *acc + pol->swaps;
+    if (swaps_out) *swaps_out = tot;
+    if (res) {
+        res->swaps = tot;
+        res->status = pol->status;
+        res->minv_valid = pol->minv_valid;
+    }
+}
+
+__global__ void add_int_k(int* p, int v) {
+    if (threadIdx.x == 0) *p += v;
+}
+
+// One merge level on `basis` (p x r): sets in cand (nsets x r, global rows). in_src[k]
+// describes, per input set, where its M^-1 and log|det| are (when known) and whether they
+// are valid; node t then starts from its left set's M^-1 instead of a new factorisation.
+// out_src describes the output sets. Swaps are added to *acc (device).
 template <typename TB>
 static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r,
                                 const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
-                                int* swaps, const std::vector<const double*>& in_minv,
-                                const std::vector<const double*>& in_lv, Stage<TB>& lv,
-                                std::vector<const double*>& out_minv,
-                                std::vector<const double*>& out_lv, Arena& ar, cudaStream_t st) {
+                                int* acc, const std::vector<InheritSrc>& in_src, Stage<TB>& lv,
+                                std::vector<InheritSrc>& out_src, const int* idle, Arena& ar,
+                                cudaStream_t st) {
     const int npairs = nsets / 2;
-    *swaps = 0;
-    out_minv.clear();
-    out_lv.clear();
+    out_src.clear();
     if (npairs == 0) {
         CUR_CK(cudaMemcpyAsync(out, cand, sizeof(int32_t) * r * nsets, cudaMemcpyDeviceToDevice, st));
-        out_minv = in_minv;
-        out_lv = in_lv;
+        out_src = in_src;
         return CUR_OK;
     }
     const int64_t nrows = (int64_t)npairs * 2 * r;
     TB* U = ar.get<TB>((size_t)nrows * r);
-    int32_t* S2 = ar.get<int32_t>((size_t)npairs * r);
+    InheritSrc* dsrc = ar.get<InheritSrc>(npairs);
     if (!ar.ok) return CUR_ERR_NOMEM;
     gather_union_k<TB><<<nblk(nrows * r), 256, 0, st>>>(basis, p, r, cand, nrows, U, h->status);
     CUR_CK(cudaGetLastError());
@@ -1346,77 +1562,51 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
         lv.probs.push_back(pr);
     }
     CUR_TRY(stage_setup<TB>(h, r, lv, ar));
+    CUR_TRY(stage_tables(lv, st));
+    CUR_TRY(stage_init(lv, idle, st));
     mv_iota<<<nblk(npairs * r), 256, 0, st>>>(lv.S, npairs, r, 0);
     CUR_CK(cudaGetLastError());
     note_launch();
-    std::vector<int> lu_mask(npairs, 1), none;
+    // node t starts from its left set (2t) with that set's inverse when it is valid
+    std::vector<InheritSrc> src(npairs);
     for (int t = 0; t < npairs; ++t) {
         const int k = 2 * t;
-        if (k < (int)in_minv.size() && in_minv[k] && in_lv[k]) {
-            lu_mask[t] = 0;
-            CUR_CK(cudaMemcpyAsync(lv.minv64 + (int64_t)t * minv_stride(r), in_minv[k], sizeof(double) * minv_stride(r),
-                                   cudaMemcpyDeviceToDevice, st));
-            CUR_CK(cudaMemcpyAsync(lv.logvol + t, in_lv[k], sizeof(double), cudaMemcpyDeviceToDevice, st));
-        }
+        src[t] = k < (int)in_src.size() ? in_src[k] : InheritSrc{nullptr, nullptr, nullptr, 0, 0};
+        src[t].transpose = 0;
     }
-    CUR_TRY(stage_run<TB>(h, U, r, o, lv, false, lu_mask, none, st));
-    CUR_TRY(stage_read<TB>(h, lv, st));
-    // singular left start: start at the right set; then Algorithm 3 on the union. The
-    // swaps of an attempt that is abandoned for the next one are not counted.
-    std::vector<int> skip(npairs, 1);
-    bool any = false;
-    for (int t = 0; t < npairs; ++t) {
-        if (lv.stat[t] == CUR_ERR_SINGULAR) { skip[t] = 0; any = true; }
-        else *swaps += lv.sw[t];
-    }
-    for (int attempt = 0; attempt < 2 && any; ++attempt) {
-        if (attempt == 0) {
-            mv_iota<<<nblk(npairs * r), 256, 0, st>>>(S2, npairs, r, r);
-            CUR_CK(cudaGetLastError());
-            note_launch();
-            for (int t = 0; t < npairs; ++t)
-                if (!skip[t])
-                    CUR_CK(cudaMemcpyAsync(lv.S + (int64_t)t * r, S2 + (int64_t)t * r,
-                                           sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-        }
-        const std::vector<int> save = lv.stat, savesw = lv.sw;
-        CUR_TRY(stage_run<TB>(h, U, r, o, lv, attempt == 1, none, skip, st));
-        CUR_TRY(stage_read<TB>(h, lv, st));
-        any = false;
-        for (int t = 0; t < npairs; ++t) {
-            if (skip[t]) { lv.stat[t] = save[t]; lv.sw[t] = savesw[t]; continue; }
-            if (lv.stat[t] == CUR_ERR_SINGULAR && attempt == 0) { any = true; continue; }
-            *swaps += lv.sw[t];
-            skip[t] = 1;
-        }
+    CUR_TRY(launch_inherit(src, r, lv.minv64, lv.logvol, lv.dtab + 2 * lv.slots, lv.done, dsrc, st));
+    // attempt 0: the left set; 1: the right set where the left one is singular; 2: Algorithm 3
+    // on the union where both are
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        CUR_TRY(stage_launch<TB>(h, U, r, o, lv, attempt == 2, st));
+        merge_retry_k<<<nblk(npairs), 256, 0, st>>>(attempt, npairs, r, lv.pstatus, lv.swaps, lv.done,
+                                                    lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc);
+        CUR_CK(cudaGetLastError());
+        note_launch();
     }
     mv_emit<<<nblk(npairs * r), 256, 0, st>>>(lv.dprob, lv.S, npairs, r, out);
     CUR_CK(cudaGetLastError());
     note_launch();
-    for (int t = 0; t < npairs; ++t) {
-        const bool ok = lv.stat[t] == CUR_OK || lv.stat[t] == CUR_ERR_NOCONV;
-        out_minv.push_back(ok ? lv.minv64 + (int64_t)t * minv_stride(r) : nullptr);
-        out_lv.push_back(ok ? lv.logvol + t : nullptr);
-    }
+    for (int t = 0; t < npairs; ++t)
+        out_src.push_back(InheritSrc{lv.minv64 + (int64_t)t * minv_stride(r), lv.logvol + t, lv.pstatus + t, 1, 0});
     if (nsets % 2 == 1) {
         CUR_CK(cudaMemcpyAsync(out + (int64_t)npairs * r, cand + (int64_t)(nsets - 1) * r,
                                sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-        out_minv.push_back(nsets - 1 < (int)in_minv.size() ? in_minv[nsets - 1] : nullptr);
-        out_lv.push_back(nsets - 1 < (int)in_lv.size() ? in_lv[nsets - 1] : nullptr);
+        out_src.push_back(nsets - 1 < (int)in_src.size() ? in_src[nsets - 1]
+                                                         : InheritSrc{nullptr, nullptr, nullptr, 0, 0});
     }
     return CUR_OK;
 }
 
-// Maxvol over all p rows of the basis, started at S0 (global rows). With `inherit`
-// (M^-1 and log|det| of exactly the rows S0 in that order, or the transpose of that
-// inverse) no new factorisation is made. minv_out receives the final M^-1.
+// Maxvol over all p rows of the basis, started at S0 (global rows). With `inherit` (M^-1
+// and log|det| of exactly the rows S0 in that order, or the transpose of that inverse, valid
+// per its flag) no new factorisation is made. minv_out receives the final M^-1; res (device)
+// the swaps, the status and whether minv_out is valid. Nothing runs while *idle != 0.
 template <typename TB>
 static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, const cur_opts* o,
-                           const int32_t* S0, int32_t* S_out, double* logvol_out, MvResult* res,
-                           Arena& ar, cudaStream_t st, const double* inherit_minv = nullptr,
-                           const double* inherit_lv = nullptr, bool transpose = false,
-                           double* minv_out = nullptr, bool keep_singular_set = false) {
-    const size_t mark = ar.off;
+                           const int32_t* S0, int32_t* S_out, double* logvol_out, MvDevResult* res,
+                           Arena& ar, cudaStream_t st, InheritSrc inherit, double* minv_out,
+                           bool keep_singular_set, const int* idle) {
     Stage<TB> sg;
     sg.keep_singular_set = keep_singular_set;
     MvProb pr{};
@@ -1428,47 +1618,36 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     pr.p = (int32_t)p;
     sg.probs.push_back(pr);
     CUR_TRY(stage_setup<TB>(h, r, sg, ar));
+    InheritSrc* dsrc = ar.get<InheritSrc>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(stage_tables(sg, st));
+    CUR_TRY(stage_init(sg, idle, st));
     CUR_CK(cudaMemcpyAsync(sg.S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    std::vector<int> lu_mask(1, 1), none;
-    if (inherit_minv && inherit_lv) {
-        lu_mask[0] = 0;
-        if (transpose) {
-            mv_transpose<<<nblk(minv_stride(r)), 256, 0, st>>>(inherit_minv, r, sg.minv64);
-            CUR_CK(cudaGetLastError());
-            note_launch();
-        } else {
-            CUR_CK(cudaMemcpyAsync(sg.minv64, inherit_minv, sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
-        }
-        CUR_CK(cudaMemcpyAsync(sg.logvol, inherit_lv, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-    CUR_TRY(stage_run<TB>(h, basis, r, o, sg, false, lu_mask, none, st));
-    CUR_TRY(stage_read<TB>(h, sg, st));
-    const bool ok = sg.stat[0] != CUR_ERR_SINGULAR && sg.stat[0] != CUR_ERR_ARG &&
-                    sg.stat[0] != CUR_ERR_NONFINITE && sg.stat[0] != CUR_ERR_TIMEOUT;
-    if (res) { res->swaps = sg.sw[0]; res->status = sg.stat[0]; res->minv_valid = ok && minv_out; }
-    if ((sg.stat[0] != CUR_ERR_SINGULAR || keep_singular_set) && sg.stat[0] != CUR_ERR_ARG)
-        CUR_CK(cudaMemcpyAsync(S_out, sg.S, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    else if (S_out != S0)
-        CUR_CK(cudaMemcpyAsync(S_out, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    if (logvol_out) CUR_CK(cudaMemcpyAsync(logvol_out, sg.logvol, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (minv_out && ok) CUR_CK(cudaMemcpyAsync(minv_out, sg.minv64, sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
-    CUR_CK(cudaStreamSynchronize(st));
-    ar.off = mark;
-    ar.ok = true;
+    if (inherit.minv && inherit.lv)
+        CUR_TRY(launch_inherit(std::vector<InheritSrc>{inherit}, r, sg.minv64, sg.logvol, sg.dtab + 2 * sg.slots,
+                               sg.done, dsrc, st));
+    CUR_TRY(stage_launch<TB>(h, basis, r, o, sg, false, st));
+    global_finish_k<<<1, 256, 0, st>>>(sg.pstatus, sg.swaps, sg.S, S0, r, keep_singular_set ? 1 : 0, S_out, sg.logvol,
+                                       logvol_out, sg.minv64, minv_out, res, idle);
+    CUR_CK(cudaGetLastError());
+    note_launch();
     return CUR_OK;
 }
 
 template <typename TB>
 static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const cur_opts* o,
-                         int32_t* I_out, double* logvol_out, int32_t* swaps_out, MvResult* res,
-                         Arena& ar, cudaStream_t st, double* minv_out = nullptr) {
+                         int32_t* I_out, double* logvol_out, int32_t* swaps_out, MvDevResult* res,
+                         Arena& ar, cudaStream_t st, double* minv_out, const int* idle) {
     const int nb = std::max(1, o->nblocks);
     const int64_t base_sz = p / nb, extra = p % nb;
     if (base_sz < r) return CUR_ERR_ARG;
-    const size_t mark = ar.off;
     int32_t* setsA = ar.get<int32_t>((size_t)nb * r);
     int32_t* setsB = ar.get<int32_t>((size_t)nb * r);
+    int* acc = ar.get<int>(1);
+    MvDevResult* pol = ar.get<MvDevResult>(1);
+    double* lv_direct = ar.get<double>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_CK(cudaMemsetAsync(acc, 0, sizeof(int), st));
     // Stage objects (and their workspace) stay alive until the end of the call, so a
     // merge node can start from its left set's M^-1.
     std::vector<Stage<TB>> stages;
@@ -1489,81 +1668,66 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         s0 += sz;
     }
     CUR_TRY(stage_setup<TB>(h, r, sb, ar, true));
-    std::vector<int> none;
-    CUR_TRY(stage_run<TB>(h, basis, r, o, sb, true, none, none, st));
-    CUR_TRY(stage_read<TB>(h, sb, st));
-    int total = 0;
-    for (int v : sb.sw) total += v;
-    mv_emit<<<nblk(nb * r), 256, 0, st>>>(sb.dprob, sb.S, nb, r, setsA);
+    CUR_TRY(stage_tables(sb, st));
+    CUR_TRY(stage_init(sb, idle, st));
+    mv_iota<<<nblk(nb * r), 256, 0, st>>>(sb.S, nb, r, 0);   // valid rows even when nothing runs
     CUR_CK(cudaGetLastError());
     note_launch();
-    std::vector<const double*> mv, lvp, mv2, lvp2;
-    for (int k = 0; k < nb; ++k) {
-        const bool ok = sb.stat[k] == CUR_OK || sb.stat[k] == CUR_ERR_NOCONV;
-        mv.push_back(ok ? sb.minv64 + (int64_t)k * minv_stride(r) : nullptr);
-        lvp.push_back(ok ? sb.logvol + k : nullptr);
-    }
+    CUR_TRY(stage_launch<TB>(h, basis, r, o, sb, true, st));
+    acc_swaps_k<<<1, 256, 0, st>>>(sb.swaps, nb, acc);
+    CUR_CK(cudaGetLastError());
+    mv_emit<<<nblk(nb * r), 256, 0, st>>>(sb.dprob, sb.S, nb, r, setsA);
+    CUR_CK(cudaGetLastError());
+    note_launch(2);
+    std::vector<InheritSrc> src, src2;
+    for (int k = 0; k < nb; ++k)
+        src.push_back(InheritSrc{sb.minv64 + (int64_t)k * minv_stride(r), sb.logvol + k, sb.pstatus + k, 1, 0});
     int nsets = nb;
     int32_t* cur = setsA;
     int32_t* nxt = setsB;
     while (nsets > 1) {
-        int msw = 0;
         stages.emplace_back();
-        CUR_TRY(merge_level_t<TB>(h, basis, p, r, cur, nsets, o, nxt, &msw, mv, lvp, stages.back(),
-                                  mv2, lvp2, ar, st));
-        total += msw;
+        CUR_TRY(merge_level_t<TB>(h, basis, p, r, cur, nsets, o, nxt, acc, src, stages.back(), src2, idle, ar, st));
         nsets = (nsets + 1) / 2;
         std::swap(cur, nxt);
-        mv.swap(mv2);
-        lvp.swap(lvp2);
+        src.swap(src2);
     }
-    int fstat = CUR_OK;
-    int mvalid = 0;
+    const InheritSrc root = src.empty() ? InheritSrc{nullptr, nullptr, nullptr, 0, 0} : src[0];
     if (o->flags & CUR_FLAG_POLISH) {
-        MvResult gr;
-        const double* minv_in = mv.empty() ? nullptr : mv[0];
-        const double* lv_in = lvp.empty() ? nullptr : lvp[0];
+        InheritSrc start = root;
         if constexpr (std::is_same<TB, float>::value) {
             // with CUR_FLAG_PREC_BF16 / _FP8 on a large basis, low-precision products take the
-            // polish's swaps first; the FP32 engine then finishes (from a fresh factorisation if
-            // any were taken)
+            // polish's swaps first (that phase synchronises the stream); the FP32 engine then
+            // finishes (from a fresh factorisation if any were taken)
             if (lowprec_phase_applies(h, o, CUR_F32, p, r)) {
-                int bsw = 0, bst = CUR_OK;
-                CUR_TRY(lowprec_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, minv_in));
-                total += bsw;
-                if (bsw > 0) { minv_in = nullptr; lv_in = nullptr; }
+                CUR_CK(cudaStreamSynchronize(st));
+                int hv[2] = {CUR_OK, 0};
+                if (root.flag) CUR_CK(cudaMemcpy(&hv[0], root.flag, sizeof(int), cudaMemcpyDeviceToHost));
+                if (idle) CUR_CK(cudaMemcpy(&hv[1], idle, sizeof(int), cudaMemcpyDeviceToHost));
+                if (!hv[1]) {
+                    const bool valid = root.minv && root.lv && (hv[0] == CUR_OK || hv[0] == CUR_ERR_NOCONV);
+                    int bsw = 0, bst = CUR_OK;
+                    CUR_TRY(lowprec_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, valid ? root.minv : nullptr));
+                    if (bsw > 0) {
+                        start = InheritSrc{nullptr, nullptr, nullptr, 0, 0};   // a fresh factorisation
+                        add_int_k<<<1, 32, 0, st>>>(acc, bsw);
+                        CUR_CK(cudaGetLastError());
+                        note_launch();
+                    }
+                }
             }
         }
-        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, &gr, ar, st, minv_in, lv_in, false,
-                             minv_out));
-        total += gr.swaps;
-        fstat = gr.status;
-        mvalid = gr.minv_valid;
+        CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, pol, ar, st, start, minv_out, false, idle));
+        rows_polish_k<<<1, 32, 0, st>>>(acc, pol, swaps_out, res, idle);
+        CUR_CK(cudaGetLastError());
+        note_launch();
     } else {
-        if (minv_out && !mv.empty() && mv[0]) {
-            CUR_CK(cudaMemcpyAsync(minv_out, mv[0], sizeof(double) * minv_stride(r), cudaMemcpyDeviceToDevice, st));
-            mvalid = 1;
-        }
-        CUR_CK(cudaMemcpyAsync(I_out, cur, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-        if (logvol_out) {
-            if (!mv.empty() && lvp[0]) {
-                CUR_CK(cudaMemcpyAsync(logvol_out, lvp[0], sizeof(double), cudaMemcpyDeviceToDevice, st));
-            } else {
-                CUR_TRY(logvol_rows(std::is_same<TB, double>::value ? CUR_F64 : CUR_F32, basis, r, cur,
-                                    logvol_out, st));
-            }
-        }
+        CUR_TRY(logvol_rows(std::is_same<TB, double>::value ? CUR_F64 : CUR_F32, basis, p, r, cur, lv_direct, st));
+        rows_root_k<<<1, 256, 0, st>>>(cur, r, I_out, root.minv, root.lv, root.flag, lv_direct, logvol_out,
+                                       minv_out, acc, swaps_out, res, idle);
+        CUR_CK(cudaGetLastError());
+        note_launch();
     }
-    if (swaps_out) {
-        int32_t* hs = reinterpret_cast<int32_t*>(h->host_stage);
-        CUR_CK(cudaStreamSynchronize(st));
-        hs[0] = total;
-        CUR_CK(cudaMemcpyAsync(swaps_out, hs, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        CUR_CK(cudaStreamSynchronize(st));
-    }
-    if (res) { res->swaps = total; res->status = fstat; res->minv_valid = mvalid; }
-    ar.off = mark;
-    ar.ok = true;
     return CUR_OK;
 }
 
@@ -1573,53 +1737,214 @@ size_t compute_size(cur_dtype t) { return t == CUR_F64 ? 8 : 4; }
 
 cur_status maxvol_basis_rows(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                              const cur_opts* o, int32_t* I_out, double* logvol_out,
-                             int32_t* swaps_out, MvResult* res, Arena& ar, cudaStream_t st,
-                             double* minv_out) {
+                             int32_t* swaps_out, MvDevResult* res, Arena& ar, cudaStream_t st,
+                             double* minv_out, const int* idle) {
+    // the workspace a call takes is free again for the next call on the stream (stream order)
+    const size_t mark = ar.off;
+    cur_status s;
     if (dt == CUR_F64)
-        return curk::rows_t<double>(h, static_cast<const double*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st, minv_out);
-    return curk::rows_t<float>(h, static_cast<const float*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar, st, minv_out);
+        s = curk::rows_t<double>(h, static_cast<const double*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar,
+                                 st, minv_out, idle);
+    else
+        s = curk::rows_t<float>(h, static_cast<const float*>(basis), p, r, o, I_out, logvol_out, swaps_out, res, ar,
+                                st, minv_out, idle);
+    ar.off = mark;
+    ar.ok = true;
+    return s;
 }
 
 cur_status maxvol_global(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                          const cur_opts* o, const int32_t* S0, int32_t* S_out,
-                         double* logvol_out, MvResult* res, Arena& ar, cudaStream_t st,
-                         const double* minv_in, const double* lv_in, bool transpose_in,
-                         double* minv_out, bool keep_singular_set) {
+                         double* logvol_out, MvDevResult* res, Arena& ar, cudaStream_t st,
+                         const double* minv_in, const double* lv_in, const int* minv_in_valid,
+                         bool transpose_in, double* minv_out, bool keep_singular_set, const int* idle) {
+    const curk::InheritSrc src{minv_in, lv_in, minv_in_valid, 0, transpose_in ? 1 : 0};
+    const size_t mark = ar.off;
+    cur_status s;
     if (dt == CUR_F64)
-        return curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out, keep_singular_set);
-    return curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st, minv_in, lv_in, transpose_in, minv_out, keep_singular_set);
+        s = curk::global_t<double>(h, static_cast<const double*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st,
+                                   src, minv_out, keep_singular_set, idle);
+    else
+        s = curk::global_t<float>(h, static_cast<const float*>(basis), p, r, o, S0, S_out, logvol_out, res, ar, st,
+                                  src, minv_out, keep_singular_set, idle);
+    ar.off = mark;
+    ar.ok = true;
+    return s;
 }
 
 template <typename TB>
 static cur_status merge_one(cur_handle* h, const TB* basis, int64_t p, int r, const int32_t* cand,
-                            int nsets, const cur_opts* o, int32_t* out, int* swaps, Arena& ar,
+                            int nsets, const cur_opts* o, int32_t* out, int* acc, Arena& ar,
                             cudaStream_t st) {
     curk::Stage<TB> lv;
-    std::vector<const double*> none, om, ol;
-    return curk::merge_level_t<TB>(h, basis, p, r, cand, nsets, o, out, swaps, none, none, lv, om, ol,
-                                   ar, st);
+    std::vector<curk::InheritSrc> none, os;
+    return curk::merge_level_t<TB>(h, basis, p, r, cand, nsets, o, out, acc, none, lv, os, nullptr, ar, st);
+}
+
+cur_status upload_table(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return curk::upload(dst, src, bytes, st);
 }
 
 cur_status merge_level(cur_handle* h, cur_dtype dt, const void* basis, int64_t p, int r,
                        const int32_t* cand, int nsets, const cur_opts* o, int32_t* out,
-                       int* swaps, Arena& ar, cudaStream_t st) {
+                       int* acc_dev, Arena& ar, cudaStream_t st) {
     if (dt == CUR_F64)
-        return merge_one<double>(h, static_cast<const double*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
-    return merge_one<float>(h, static_cast<const float*>(basis), p, r, cand, nsets, o, out, swaps, ar, st);
+        return merge_one<double>(h, static_cast<const double*>(basis), p, r, cand, nsets, o, out, acc_dev, ar, st);
+    return merge_one<float>(h, static_cast<const float*>(basis), p, r, cand, nsets, o, out, acc_dev, ar, st);
 }
+
+
+// ---------------------------------------------------------------- the sweeps of a cross
+//
+// Sweeps of global maxvol on the rows of A(:,J) from I, then on the columns of A(I,:)^T
+// from J, until a sweep makes no swap (reading 17). Every sweep up to the cap is enqueued;
+// the control block's idle flag, set on the device by the sweep that ends the loop, makes
+// the later sweeps' kernels return at once.
+
+namespace curk {
+
+__global__ void cross_begin_k(CrossCtl* ctl, const int* hstatus, int check_status) {
+    if (threadIdx.x != 0) return;
+    int idle = 0;
+    if (check_status) {
+        const int s = *hstatus;
+        idle = (s != CUR_OK && s != CUR_WARN_RANK) ? 1 : 0;   // Algorithm 3 met an error
+    }
+    ctl->idle = idle;
+    ctl->abort = idle;
+    ctl->sweeps = 0;
+    for (int k = 0; k < 8; ++k) ctl->sweep_swaps[k] = 0;
+    ctl->last_status = CUR_OK;
+    ctl->mc_valid = 0;
+    ctl->singular_start = 0;
+}
+
+// Sweep 1 of cur_cross (the blockwise row and column selections) is over.
+__global__ void sweep_one_k(CrossCtl* ctl, const MvDevResult* rr, const MvDevResult* rc) {
+    if (threadIdx.x != 0 || ctl->abort) return;
+    ctl->sweeps = 1;
+    ctl->sweep_swaps[0] = rr->swaps + rc->swaps;
+    if (rr->status != CUR_OK) ctl->last_status = rr->status;
+    if (rc->status != CUR_OK) ctl->last_status = rc->status;
+    ctl->mc_valid = rc->minv_valid;
+}
+
+// cur_cross_from, sweep 1: a singular proposed A(I0, J0) (the row stage's start, no swap)
+// leaves nothing to refine.
+__global__ void from_start_k(CrossCtl* ctl, const MvDevResult* r1) {
+    if (threadIdx.x != 0 || ctl->idle) return;
+    if (r1->status == CUR_ERR_SINGULAR && r1->swaps == 0) {
+        ctl->last_status = CUR_ERR_SINGULAR;
+        ctl->singular_start = 1;
+        ctl->sweeps = 1;
+        ctl->idle = 1;
+    }
+}
+
+__global__ void sweep_end_k(CrossCtl* ctl, const MvDevResult* r1, const MvDevResult* r2, int s) {
+    if (threadIdx.x != 0 || ctl->idle) return;
+    ctl->sweeps = s;
+    ctl->sweep_swaps[s - 1] = r1->swaps + r2->swaps;
+    ctl->mc_valid = r2->minv_valid;
+    if (r1->status != CUR_OK || r2->status != CUR_OK) {
+        ctl->last_status = r1->status != CUR_OK ? r1->status : r2->status;
+        ctl->idle = 1;
+    } else if (r1->swaps + r2->swaps == 0) {
+        ctl->idle = 1;
+    }
+}
+
+// The cross's log-volume (taken directly when a stage ended with an error: such a stage
+// leaves no log|det| of its own; -inf for a singular proposal), its status and its info.
+__global__ void cross_end_k(CrossCtl* ctl, double* lv, const double* lv_direct, cur_cross_info* info,
+                            const int32_t* aca_count, int* hstatus, int from) {
+    if (threadIdx.x != 0) return;
+    if (ctl->singular_start) *lv = -INFINITY;
+    else if (ctl->last_status != CUR_OK) *lv = *lv_direct;
+    if (ctl->last_status == CUR_ERR_NOCONV || ctl->last_status == CUR_ERR_SINGULAR)
+        set_status(hstatus, ctl->last_status);
+    if (!info) return;
+    int tot = 0;
+    for (int k = 0; k < 8; ++k) tot += ctl->sweep_swaps[k];
+    info->logvol = *lv;
+    info->sweeps = ctl->sweeps;
+    info->swaps_total = tot;
+    for (int k = 0; k < 8; ++k) info->sweep_swaps[k] = ctl->sweep_swaps[k];
+    info->aca_selected = aca_count ? *aca_count : 0;
+    info->status = from ? ctl->last_status : *hstatus;
+}
+
+}  // namespace curk
+
+cur_status cross_begin(CrossCtl* ctl, const int* hstatus, bool check_status, cudaStream_t st) {
+    curk::cross_begin_k<<<1, 32, 0, st>>>(ctl, hstatus, check_status ? 1 : 0);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+cur_status cross_sweep_one(CrossCtl* ctl, const MvDevResult* rr, const MvDevResult* rc, cudaStream_t st) {
+    curk::sweep_one_k<<<1, 32, 0, st>>>(ctl, rr, rc);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+
+cur_status cross_sweeps(cur_handle* h, const cur_mat* A, int r, const cur_opts* o, int first, int max_sweeps,
+                        bool from, int32_t* I, int32_t* J, void* Cb, void* Rb, double* Mr, double* Mc, double* lvr,
+                        double* lv, CrossCtl* ctl, Arena& ar, cudaStream_t st) {
+    const cur_dtype cdt = A->dtype == CUR_F64 ? CUR_F64 : CUR_F32;
+    const int64_t m = A->rows, n = A->cols;
+    MvDevResult* res = ar.get<MvDevResult>(2);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    for (int s = first; s <= max_sweeps; ++s) {
+        CUR_TRY(gather_cols_compute(A, J, r, Cb, st, &ctl->idle));
+        CUR_TRY(maxvol_global(h, cdt, Cb, m, r, o, I, I, lvr, &res[0], ar, st, Mc, lv, &ctl->mc_valid, true, Mr, true,
+                              &ctl->idle));
+        if (from && s == 1) {
+            curk::from_start_k<<<1, 32, 0, st>>>(ctl, &res[0]);
+            CUR_CK(cudaGetLastError());
+            note_launch();
+        }
+        CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st, &ctl->idle));
+        CUR_TRY(maxvol_global(h, cdt, Rb, n, r, o, J, J, lv, &res[1], ar, st, Mr, lvr, &res[0].minv_valid, true, Mc,
+                              true, &ctl->idle));
+        curk::sweep_end_k<<<1, 32, 0, st>>>(ctl, &res[0], &res[1], s);
+        CUR_CK(cudaGetLastError());
+        note_launch();
+    }
+    return CUR_OK;
+}
+
+cur_status cross_end(cur_handle* h, const cur_mat* A, int r, bool from, const int32_t* I, const int32_t* J,
+                     void* Rb, double* lv, CrossCtl* ctl, const int32_t* aca_count, int32_t* I_out, int32_t* J_out,
+                     cur_cross_info* info_out, Arena& ar, cudaStream_t st) {
+    const cur_dtype cdt = A->dtype == CUR_F64 ? CUR_F64 : CUR_F32;
+    double* lv_direct = ar.get<double>(1);
+    if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
+    CUR_TRY(logvol_rows(cdt, Rb, A->cols, r, J, lv_direct, st));
+    curk::cross_end_k<<<1, 32, 0, st>>>(ctl, lv, lv_direct, info_out, aca_count, h->status, from ? 1 : 0);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    CUR_CK(cudaMemcpyAsync(I_out, I, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(J_out, J, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    return CUR_OK;
+}
+
 
 namespace curk {
 // ids_out[k] = ids[pos[k]], rows_out[k, :] = rows[pos[k], :] (the merged set's ids and rows).
 template <typename TB>
 __global__ void pair_emit_k(const TB* __restrict__ rows, const int32_t* __restrict__ ids,
                             const int32_t* __restrict__ pos, int r, int32_t* __restrict__ ids_out,
-                            TB* __restrict__ rows_out, int32_t* swaps_out, int swaps) {
+                            TB* __restrict__ rows_out, int32_t* swaps_out, const int* acc) {
     for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
         const int k = e / r, c = e - k * r;
         rows_out[e] = rows[(int64_t)pos[k] * r + c];
     }
     for (int k = threadIdx.x; k < r; k += blockDim.x) ids_out[k] = ids[pos[k]];
-    if (threadIdx.x == 0 && swaps_out) *swaps_out = swaps;
+    if (threadIdx.x == 0 && swaps_out) *swaps_out = *acc;
 }
 }  // namespace curk
 
@@ -1628,81 +1953,82 @@ cur_status merge_pair_impl(cur_handle* h, cur_dtype dt, const void* rows, const 
                            cudaStream_t st) {
     int32_t* cand = ar.get<int32_t>((size_t)2 * r);
     int32_t* pos = ar.get<int32_t>((size_t)r);
+    int* acc = ar.get<int>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     curk::mv_iota<<<1, 256, 0, st>>>(cand, 1, 2 * r, 0);
     CUR_CK(cudaGetLastError());
     note_launch();
-    int swaps = 0;
-    CUR_TRY(merge_level(h, dt, rows, 2 * r, r, cand, 2, o, pos, &swaps, ar, st));
+    CUR_CK(cudaMemsetAsync(acc, 0, sizeof(int), st));
+    CUR_TRY(merge_level(h, dt, rows, 2 * r, r, cand, 2, o, pos, acc, ar, st));
     if (dt == CUR_F64)
         curk::pair_emit_k<double><<<1, 256, 0, st>>>(static_cast<const double*>(rows), ids, pos, r, ids_out,
-                                                     static_cast<double*>(rows_out), swaps_out, swaps);
+                                                     static_cast<double*>(rows_out), swaps_out, acc);
     else
         curk::pair_emit_k<float><<<1, 256, 0, st>>>(static_cast<const float*>(rows), ids, pos, r, ids_out,
-                                                    static_cast<float*>(rows_out), swaps_out, swaps);
+                                                    static_cast<float*>(rows_out), swaps_out, acc);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
 }
 
 template <typename TA>
-static cur_status gather_cols_t(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st) {
+static cur_status gather_cols_t(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st, const int* idle) {
     const TA* a = static_cast<const TA*>(A->data);
     const int64_t total = A->rows * r;
     if (A->dtype == CUR_F64)
-        curk::gather_cols_k<TA, double><<<curk::nblk(total), 256, 0, st>>>(a, A->rows, A->cols, A->ld, J, r, static_cast<double*>(C), nullptr);
+        curk::gather_cols_k<TA, double><<<curk::nblk(total), 256, 0, st>>>(a, A->rows, A->cols, A->ld, J, r, static_cast<double*>(C), nullptr, idle);
     else
-        curk::gather_cols_k<TA, float><<<curk::nblk(total), 256, 0, st>>>(a, A->rows, A->cols, A->ld, J, r, static_cast<float*>(C), nullptr);
+        curk::gather_cols_k<TA, float><<<curk::nblk(total), 256, 0, st>>>(a, A->rows, A->cols, A->ld, J, r, static_cast<float*>(C), nullptr, idle);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
 }
 
-cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st) {
+cur_status gather_cols_compute(const cur_mat* A, const int32_t* J, int r, void* C, cudaStream_t st, const int* idle) {
     switch (A->dtype) {
-        case CUR_F64: return gather_cols_t<double>(A, J, r, C, st);
-        case CUR_F32: return gather_cols_t<float>(A, J, r, C, st);
-        case CUR_BF16: return gather_cols_t<__nv_bfloat16>(A, J, r, C, st);
+        case CUR_F64: return gather_cols_t<double>(A, J, r, C, st, idle);
+        case CUR_F32: return gather_cols_t<float>(A, J, r, C, st, idle);
+        case CUR_BF16: return gather_cols_t<__nv_bfloat16>(A, J, r, C, st, idle);
     }
     return CUR_ERR_ARG;
 }
 
 template <typename TA>
-static cur_status gather_rows_t_t(const cur_mat* A, const int32_t* I, int r, void* Rt, cudaStream_t st) {
+static cur_status gather_rows_t_t(const cur_mat* A, const int32_t* I, int r, void* Rt, cudaStream_t st, const int* idle) {
     const TA* a = static_cast<const TA*>(A->data);
     const unsigned grid = (unsigned)((A->cols + 31) / 32);
     if (A->dtype == CUR_F64) {
         const size_t sm = (size_t)r * 33 * sizeof(double);
-        CUR_CK(cudaFuncSetAttribute((const void*)curk::gather_rows_t_k<TA, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        curk::gather_rows_t_k<TA, double><<<grid, 256, sm, st>>>(a, A->rows, A->cols, A->ld, I, r, static_cast<double*>(Rt), nullptr);
+        CUR_TRY(smem_attr((const void*)curk::gather_rows_t_k<TA, double>, sm));
+        curk::gather_rows_t_k<TA, double><<<grid, 256, sm, st>>>(a, A->rows, A->cols, A->ld, I, r, static_cast<double*>(Rt), nullptr, idle);
     } else {
         const size_t sm = (size_t)r * 33 * sizeof(float);
-        CUR_CK(cudaFuncSetAttribute((const void*)curk::gather_rows_t_k<TA, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        curk::gather_rows_t_k<TA, float><<<grid, 256, sm, st>>>(a, A->rows, A->cols, A->ld, I, r, static_cast<float*>(Rt), nullptr);
+        CUR_TRY(smem_attr((const void*)curk::gather_rows_t_k<TA, float>, sm));
+        curk::gather_rows_t_k<TA, float><<<grid, 256, sm, st>>>(a, A->rows, A->cols, A->ld, I, r, static_cast<float*>(Rt), nullptr, idle);
     }
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
 }
 
-cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void* Rt, cudaStream_t st) {
+cur_status gather_rows_t_compute(const cur_mat* A, const int32_t* I, int r, void* Rt, cudaStream_t st, const int* idle) {
     switch (A->dtype) {
-        case CUR_F64: return gather_rows_t_t<double>(A, I, r, Rt, st);
-        case CUR_F32: return gather_rows_t_t<float>(A, I, r, Rt, st);
-        case CUR_BF16: return gather_rows_t_t<__nv_bfloat16>(A, I, r, Rt, st);
+        case CUR_F64: return gather_rows_t_t<double>(A, I, r, Rt, st, idle);
+        case CUR_F32: return gather_rows_t_t<float>(A, I, r, Rt, st, idle);
+        case CUR_BF16: return gather_rows_t_t<__nv_bfloat16>(A, I, r, Rt, st, idle);
     }
     return CUR_ERR_ARG;
 }
 
-cur_status logvol_rows(cur_dtype dt, const void* basis, int r, const int32_t* rows, double* out,
+cur_status logvol_rows(cur_dtype dt, const void* basis, int64_t p, int r, const int32_t* rows, double* out,
                        cudaStream_t st) {
     const size_t sm = (size_t)r * r * sizeof(double);
     if (dt == CUR_F64) {
         CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<double>, sm));
-        curk::logvol_rows_k<double><<<1, 256, sm, st>>>(static_cast<const double*>(basis), r, rows, out);
+        curk::logvol_rows_k<double><<<1, 256, sm, st>>>(static_cast<const double*>(basis), p, r, rows, out);
     } else {
         CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<float>, sm));
-        curk::logvol_rows_k<float><<<1, 256, sm, st>>>(static_cast<const float*>(basis), r, rows, out);
+        curk::logvol_rows_k<float><<<1, 256, sm, st>>>(static_cast<const float*>(basis), p, r, rows, out);
     }
     CUR_CK(cudaGetLastError());
     note_launch();
@@ -2287,7 +2613,7 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     // a matrix whose cross did not end OK reports log|det A(I,J)| taken directly
     for (int t = 0; t < T; ++t)
         if (status[t] != CUR_OK && status[t] != CUR_WARN_RANK)
-            CUR_TRY(logvol_rows(CUR_F32, Rt + brt[t].boff, items[t].r, J + (int64_t)t * rs, lvc + t, st));
+            CUR_TRY(logvol_rows(CUR_F32, Rt + brt[t].boff, brt[t].p, items[t].r, J + (int64_t)t * rs, lvc + t, st));
     std::vector<double> lvf(T);
     CUR_CK(cudaStreamSynchronize(st));
     CUR_CK(cudaMemcpy(lvf.data(), lvc, sizeof(double) * T, cudaMemcpyDeviceToHost));

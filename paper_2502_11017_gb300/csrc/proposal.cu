@@ -488,22 +488,6 @@ __global__ void __launch_bounds__(1024) propose_k(const float* __restrict__ scor
 
 // Closes cur_cross_from: records a SINGULAR / NOCONV end in the status word, sets the
 // log-volume of a singular proposal to -inf, and fills the caller's info.
-__global__ void cross_from_end_k(cur_cross_info* info, double* logvol, int sweeps, int total, int s0, int s1,
-                                 int s2, int s3, int s4, int s5, int s6, int s7, int status, int singular_start,
-                                 int* hstatus) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (singular_start) *logvol = -INFINITY;
-    if (status == CUR_ERR_SINGULAR || status == CUR_ERR_NOCONV) set_status(hstatus, status);
-    if (!info) return;
-    info->logvol = *logvol;
-    info->sweeps = sweeps;
-    info->swaps_total = total;
-    const int s[8] = {s0, s1, s2, s3, s4, s5, s6, s7};
-    for (int k = 0; k < 8; ++k) info->sweep_swaps[k] = s[k];
-    info->aca_selected = 0;
-    info->status = status;
-}
-
 }  // namespace curk
 
 namespace {
@@ -667,50 +651,14 @@ cur_status cur_cross_from(cur_handle* h, const cur_mat* A, int32_t r, const int3
     double* Mc = ar.get<double>((size_t)minv_stride(r));
     void* Cb = ar.take((size_t)m * r * cs);
     void* Rb = ar.take((size_t)n * r * cs);
+    CrossCtl* ctl = ar.get<CrossCtl>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUR_CK(cudaMemcpyAsync(I, I0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     CUR_CK(cudaMemcpyAsync(J, J0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    int sweep_swaps[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int sweeps = 0, last_status = CUR_OK, mc_valid = 0;
-    while (sweeps < max_sweeps) {
-        ++sweeps;
-        MvResult r1, r2;
-        CUR_TRY(gather_cols_compute(A, J, r, Cb, st));
-        CUR_TRY(maxvol_global(h, cdt, Cb, m, r, &o, I, I, lvr, &r1, ar, st, mc_valid ? Mc : nullptr,
-                              mc_valid ? lv : nullptr, true, Mr, true));
-        if (sweeps == 1 && r1.status == CUR_ERR_SINGULAR && r1.swaps == 0) {
-            // the proposed A(I0, J0) is singular: nothing to refine from
-            last_status = CUR_ERR_SINGULAR;
-            break;
-        }
-        CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
-        CUR_TRY(maxvol_global(h, cdt, Rb, n, r, &o, J, J, lv, &r2, ar, st, r1.minv_valid ? Mr : nullptr,
-                              r1.minv_valid ? lvr : nullptr, true, Mc, true));
-        mc_valid = r2.minv_valid;
-        sweep_swaps[sweeps - 1] = r1.swaps + r2.swaps;
-        if (r1.status != CUR_OK || r2.status != CUR_OK) {
-            last_status = r1.status != CUR_OK ? r1.status : r2.status;
-            break;
-        }
-        if (r1.swaps + r2.swaps == 0) break;
-    }
-    int total = 0;
-    for (int q = 0; q < 8; ++q) total += sweep_swaps[q];
-    const bool singular_start = last_status == CUR_ERR_SINGULAR && total == 0;
-    if (last_status != CUR_OK && !singular_start) {
-        // a stage that ended singular leaves no log|det| of its own: take it directly
-        CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
-        CUR_TRY(logvol_rows(cdt, Rb, r, J, lv, st));
-    }
-    CUR_CK(cudaMemcpyAsync(I_out, I, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    CUR_CK(cudaMemcpyAsync(J_out, J, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    curk::cross_from_end_k<<<1, 32, 0, st>>>(info_out, lv, sweeps, total, sweep_swaps[0], sweep_swaps[1],
-                                             sweep_swaps[2], sweep_swaps[3], sweep_swaps[4], sweep_swaps[5],
-                                             sweep_swaps[6], sweep_swaps[7], last_status, singular_start ? 1 : 0,
-                                             h->status);
-    CUR_CK(cudaGetLastError());
-    note_launch();
-    return CUR_OK;
+    // sweeps 1 .. 8 from the proposal (no inverse to inherit at first: mc_valid starts at 0)
+    CUR_TRY(cross_begin(ctl, h->status, false, st));
+    CUR_TRY(cross_sweeps(h, A, r, &o, 1, max_sweeps, true, I, J, Cb, Rb, Mr, Mc, lvr, lv, ctl, ar, st));
+    return cross_end(h, A, r, true, I, J, Rb, lv, ctl, nullptr, I_out, J_out, info_out, ar, st);
 }
 
 }  // extern "C"

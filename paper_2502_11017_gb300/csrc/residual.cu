@@ -390,8 +390,7 @@ static cur_status assemble_t(cur_handle* h, const cur_mat* Am, const int32_t* I,
     note_launch();
     }
     const size_t sm = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
-    CUR_CK(cudaFuncSetAttribute((const void*)assemble_inv_k<TA>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUR_TRY(smem_attr((const void*)assemble_inv_k<TA>, sm));
     assemble_inv_k<TA><<<1, 256, sm, st>>>(A, Am->rows, Am->cols, Am->ld, I, J, r, U_out, rcond_out, work, h->status);
     CUR_CK(cudaGetLastError());
     note_launch();
@@ -408,8 +407,7 @@ static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, co
     const int64_t panels = (m + BM - 1) / BM;
     const int64_t ntile = (n + BN - 1) / BN;
     const size_t sm = (size_t)r * (BM + BN) * sizeof(TW);
-    CUR_CK(cudaFuncSetAttribute((const void*)residual_k<TA, TW, TM, TN>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUR_TRY(smem_attr((const void*)residual_k<TA, TW, TM, TN>, sm));
     int occ = 1;
     CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, residual_k<TA, TW, TM, TN>, 256, sm));
     const int64_t want = (int64_t)h->num_sms * std::max(1, occ) * 4;
@@ -419,8 +417,7 @@ static cur_status residual_t(cur_handle* h, const cur_mat* Am, const void* C, co
     double* part = ar.get<double>((size_t)panels * segs * 4);
     if (!ar.ok) return CUR_ERR_NOMEM;
     const size_t smw = (size_t)r * r * sizeof(double);
-    CUR_CK(cudaFuncSetAttribute((const void*)residual_w_k<TA, TW>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    CUR_TRY(smem_attr((const void*)residual_w_k<TA, TW>, smw));
     residual_w_k<TA, TW><<<nb(n), 256, smw, st>>>(U, static_cast<const TA*>(R), r, n, W);
     CUR_CK(cudaGetLastError());
     note_launch();
@@ -519,8 +516,7 @@ static cur_status residual_noalloc_t(const cur_mat* Am, const void* C, const dou
     CUR_CK(cudaGetDevice(&dev));
     CUR_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const size_t sm = (size_t)r * (BM + BN) * sizeof(TW);
-    CUR_CK(cudaFuncSetAttribute((const void*)residual_k<TA, TW, TM, TN>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUR_TRY(smem_attr((const void*)residual_k<TA, TW, TM, TN>, sm));
     int occ = 1;
     CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, residual_k<TA, TW, TM, TN>, 256, sm));
     const int64_t want = (int64_t)sms * std::max(1, occ) * 4;
@@ -536,8 +532,7 @@ static cur_status residual_noalloc_t(const cur_mat* Am, const void* C, const dou
     TW* W = static_cast<TW*>(base);
     double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + w_bytes);
     const size_t smw = (size_t)r * r * sizeof(double);
-    CUR_CK(cudaFuncSetAttribute((const void*)residual_w_k<TA, TW>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    CUR_TRY(smem_attr((const void*)residual_w_k<TA, TW>, smw));
     residual_w_k<TA, TW><<<nb(n), 256, smw, st>>>(U, static_cast<const TA*>(R), r, n, W);
     CUR_CK(cudaGetLastError());
     const uintptr_t abase = reinterpret_cast<uintptr_t>(Am->data);

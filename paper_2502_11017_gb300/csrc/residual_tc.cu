@@ -484,7 +484,7 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
         !make_map(&mCl, Cl, m, r, ldk))
         return CUR_ERR_ARG;
     const size_t smw = (size_t)r * r * sizeof(df64);
-    CUR_CK(cudaFuncSetAttribute((const void*)tc_prep_w<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw));
+    CUR_TRY(smem_attr((const void*)tc_prep_w<float>, smw));
     tc_prep_w<float><<<(unsigned)std::min<int64_t>((n * ldk + 255) / 256, 8 * G), 256, smw, st>>>(
         U, static_cast<const float*>(R), r, n, ldk, Wh, Wl);
     CUR_CK(cudaGetLastError());
@@ -509,7 +509,7 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     a.na = (int)std::min<size_t>(kNAMax, (budget - fixed) / kASub);
     if (a.na < 4) return CUR_ERR_ARG;
     const size_t sm = fixed + (size_t)a.na * kASub;
-    CUR_CK(cudaFuncSetAttribute((const void*)residual_tc_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUR_TRY(smem_attr((const void*)residual_tc_k, sm));
     residual_tc_k<<<grid, 32 * (3 + kEpiWarps), sm, st>>>(mWh, mWl, mCh, mCl, mA, a);
     CUR_CK(cudaGetLastError());
     note_launch();

@@ -533,12 +533,12 @@ static cur_status dmv_coef_launch(const cur_mat* C, int64_t off, const DmvLayout
     const int r = L.r;
     DmvHdr* hdr = reinterpret_cast<DmvHdr*>(base + L.hdr);
     const size_t smf = ((size_t)r * r + r) * sizeof(double) + (size_t)r * sizeof(int) + 64;
-    CUR_CK(cudaFuncSetAttribute((const void*)dmv_factor_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf));
+    CUR_TRY(smem_attr((const void*)dmv_factor_k, smf));
     dmv_factor_k<<<1, 256, smf, st>>>(reinterpret_cast<const double*>(base + L.M), r,
                                       reinterpret_cast<double*>(base + L.Minv), hdr);
     CUR_CK(cudaGetLastError());
     const size_t smc = (size_t)r * r * sizeof(double);
-    CUR_CK(cudaFuncSetAttribute((const void*)dmv_coef_k<TB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc));
+    CUR_TRY(smem_attr((const void*)dmv_coef_k<TB>, smc));
     dmv_coef_k<TB><<<kShardG, 256, smc, st>>>(static_cast<const TB*>(C->data), L.p, off, r,
                                              reinterpret_cast<const double*>(base + L.Minv),
                                              reinterpret_cast<TB*>(base + L.B), reinterpret_cast<double*>(base + L.ckv),
