@@ -252,6 +252,16 @@ cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t*
                              const cur_opts* opts, int32_t* S_out, double* logvol_out,
                              int32_t* swaps_out, cudaStream_t stream);
 
+/* The swap coefficients of the maximal-volume iteration (Section 1.2: B = C M^-1, whose entry
+ * B_ij is the factor by which |det M| changes when row i replaces position j) on the tensor
+ * cores: B_out (p x r FP32, contiguous) = basis (p x r FP32, contiguous) times minv (r x r
+ * FP64, row-major, device), as 3xTF32 tcgen05 products (C and M^-1 each split into a TF32
+ * high and low part; the low x low term is dropped, ~2^-22 relative). r must be 32 or 64,
+ * else CUR_ERR_ARG. The swap engine forms the first cycle's B this way on FP32 stages of
+ * at least 8192 rows with r = 32 or 64; this call exposes the product alone. Asynchronous. */
+cur_status cur_coef_tf32(cur_handle* h, const cur_mat* basis, const double* minv, float* B_out,
+                         cudaStream_t stream);
+
 /* ---- Learned proposal (where the maxvol sweeps of Algorithm 2 start)
  *
  * A scoring network ranks the rows and the columns of A from a Gaussian sketch; the

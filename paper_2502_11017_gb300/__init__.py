@@ -33,7 +33,7 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", 
            "cur_shard_aca_orth", "cur_shard_aca_commit", "cur_shard_aca_finish",
            "cur_dmv_state_bytes", "cur_dmv_begin", "cur_dmv_refresh", "cur_dmv_holder", "cur_dmv_fill",
            "cur_dmv_swap", "cur_dmv_result", "cur_merge_pair", "cur_rows_at", "cur_transpose",
-           "cur_offset_ids", "cur_gather_cols", "cur_residual_parts"]
+           "cur_offset_ids", "cur_gather_cols", "cur_residual_parts", "cur_coef_tf32"]
 
 
 class CurMat(ctypes.Structure):
@@ -126,6 +126,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_offset_ids": ([P, P, I32, I64, P, P], ctypes.c_int),
         "cur_gather_cols": ([P, pmat, P, I32, P, P], ctypes.c_int),
         "cur_residual_parts": ([P, pmat, P, P, P, I32, P, P], ctypes.c_int),
+        "cur_coef_tf32": ([P, pmat, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -389,6 +390,12 @@ def cur_gather_cols(h, A, J, r: int, C_out, stream=None) -> int:
 def cur_residual_parts(h, A, C, U, R, r: int, parts_out, stream=None) -> int:
     return _check(load().cur_residual_parts(h, ctypes.byref(mat(A)), _ptr(C), _ptr(U), _ptr(R), r,
                                             _ptr(parts_out), _stream(stream)), "cur_residual_parts")
+
+
+def cur_coef_tf32(h, basis, minv, B_out, stream=None) -> int:
+    """B_out = basis minv on the tensor cores (3xTF32); basis p x r FP32, minv r x r FP64."""
+    return _check(load().cur_coef_tf32(h, ctypes.byref(mat(basis)), _ptr(minv), _ptr(B_out), _stream(stream)),
+                  "cur_coef_tf32")
 
 
 def info_from_tensor(t) -> CurCrossInfo:

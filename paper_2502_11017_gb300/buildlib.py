@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcur.so")
-SOURCES = ["api.cu", "aca.cu", "aca_full.cu", "batched_aca.cu", "maxvol.cu", "residual.cu", "residual_tc.cu", "proposal.cu", "lowprec.cu", "shard.cu"]
+SOURCES = ["api.cu", "aca.cu", "aca_full.cu", "batched_aca.cu", "maxvol.cu", "residual.cu", "residual_tc.cu", "proposal.cu", "lowprec.cu", "shard.cu", "coef_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

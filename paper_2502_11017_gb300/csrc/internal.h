@@ -235,6 +235,23 @@ cur_status smem_attr(const void* fn, size_t bytes);
 // call, the host never waits): maxvol.cu.
 cur_status upload_table(void* dst, const void* src, size_t bytes, cudaStream_t st);
 
+// ---- the coefficient product on the tensor cores (coef_tc.cu)
+// A 128-row tile (rows row0 .. row0 + nrows - 1 of the basis) of problem prob.
+struct CoefTile {
+    int32_t prob;
+    int32_t nrows;
+    int64_t row0;
+};
+// FP32 bases with r = 32 or 64.
+bool coef_tc_applies(cur_dtype dt, int r);
+size_t coef_tc_smem(int r);
+// B (prows x r, the basis's layout) = C M_prob^-1 on each tile, 3xTF32 tcgen05; minv64: P
+// inverses (FP64, r x r, minv_stride apart); Wh, Wl: P r^2 floats of scratch; tiles of done
+// problems are skipped.
+cur_status coef_tc_launch(cur_handle* h, const float* basis, int64_t prows, int r, const double* minv64,
+                          int64_t minv_stride_, int P, const CoefTile* tiles_dev, int ntiles, const int32_t* done,
+                          float* Wh, float* Wl, float* B, cudaStream_t st);
+
 // Cooperative launch helper (all CTAs co-resident).
 cur_status launch_coop(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
                        cudaStream_t st);

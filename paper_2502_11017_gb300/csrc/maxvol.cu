@@ -66,6 +66,7 @@ struct MvArgs {
     double drift_max;          // refactorise once sum(swaps * kappa(M)) since the last factorisation exceeds it
     int keep_singular_set;     // 1: a set that turns singular stays as it is; 0: back to the start set
     void* bglob;               // rows x r B in global memory (compute type), or null: B in shared memory
+    const void* bpre;          // rows x r: the first cycle's B from the tensor-core product, or null
     const int32_t* cta_prob;   // per CTA slot
     const int32_t* cta_part;
     int cta_base;              // first slot of this launch (waves)
@@ -735,6 +736,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
     long long bi;
     int nan;
     int par = 0, total = a.swaps[pb], made_last = 0;
+    bool first_cycle = true;
     unsigned epoch = 0;
     int fin = 0, fstat = CUR_OK;
     auto publish = [&](int pp) {
@@ -757,7 +759,11 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
             for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)Mg[e];
         }
         __syncthreads();
-        {
+        if (a.bpre && first_cycle) {
+            // the first cycle's B slice was formed on the tensor cores from the same M^-1
+            const TB* src = static_cast<const TB*>(a.bpre) + pr.boff + (int64_t)lo * r;
+            for (int e = tid; e < nloc * r; e += nt) Bs[e] = src[e];
+        } else {
             // C rows pass through shared memory a chunk at a time (coalesced loads), then
             // B rows = C rows M^-1 with 8 outputs per thread in registers; the chunk's
             // own rows of Bs serve as the staging area (a separate one when B is global).
@@ -790,6 +796,7 @@ __global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
                 __syncthreads();
             }
         }
+        first_cycle = false;
         __syncthreads();
         engine_scan(Bs, nloc, r, lo, bv, bi, nan);
         nan = __syncthreads_or(nan);
@@ -1104,6 +1111,10 @@ static cur_status upload(void* dst, const void* src, size_t bytes, cudaStream_t 
     return upload_n<30720>(d, s, bytes, st);
 }
 
+// Stages whose first B comes from the tensor-core product: FP32, r = 32 or 64, at least this
+// many rows in all (below it the tiles are too few to pay for the extra launches).
+constexpr int64_t kCoefMinRows = 8192;
+
 // One stage: a set of problems on one basis buffer. The caller fills probs (base,
 // gid_base, gid_arr, p); stage_setup plans the CTA groups and allocates per-problem
 // state; stage_tables uploads the plan; stage_init sets the per-problem flags; decision
@@ -1132,6 +1143,13 @@ struct Stage {
     int coop_slots = 0;         // slots [0, coop_slots) hold groups of several CTAs
     bool keep_singular_set = false;
     TB* bglob = nullptr;        // B in global memory when it cannot live in shared memory
+    // the first cycle's B on the tensor cores (FP32, r = 32 or 64, large stages)
+    float* bpre = nullptr;
+    float* wh = nullptr;
+    float* wl = nullptr;
+    CoefTile* dtiles = nullptr;
+    std::vector<CoefTile> tiles;
+    int64_t rows_total = 0;
 };
 
 template <typename TB>
@@ -1205,6 +1223,28 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar, bo
     sg.aux = ar.get<double>((size_t)2 * slots);
     sg.bglob = anyg ? ar.get<TB>((size_t)elems_end) : nullptr;
     if (!ar.ok) return CUR_ERR_NOMEM;
+    sg.tiles.clear();
+    sg.bpre = nullptr;
+    sg.rows_total = elems_end / std::max(1, r);
+    bool same_r = true;
+    for (auto& pr : sg.probs) same_r &= pr.r == r && pr.boff % r == 0;
+    if (std::is_same<TB, float>::value && coef_tc_applies(CUR_F32, r) && same_r && sg.rows_total >= kCoefMinRows) {
+        for (int pb = 0; pb < P; ++pb)
+            for (int64_t i = 0; i < sg.probs[pb].p; i += 128)
+                sg.tiles.push_back(CoefTile{pb, (int32_t)std::min<int64_t>(128, sg.probs[pb].p - i),
+                                            sg.probs[pb].boff / r + i});
+        const size_t mark = ar.off;
+        sg.bpre = ar.get<float>((size_t)sg.rows_total * r);
+        sg.wh = ar.get<float>((size_t)P * r * r);
+        sg.wl = ar.get<float>((size_t)P * r * r);
+        sg.dtiles = ar.get<CoefTile>(sg.tiles.size());
+        if (!ar.ok) {   // no room: this stage forms its first B on the CUDA cores as the later ones
+            ar.off = mark;
+            ar.ok = true;
+            sg.bpre = nullptr;
+            sg.tiles.clear();
+        }
+    }
     return CUR_OK;
 }
 
@@ -1220,6 +1260,7 @@ static cur_status stage_tables(Stage<TB>& sg, cudaStream_t st) {
         }
     CUR_TRY(upload(sg.dprob, sg.probs.data(), sizeof(MvProb) * P, st));
     CUR_TRY(upload(sg.dtab, tab.data(), sizeof(int32_t) * tab.size(), st));
+    if (sg.bpre) CUR_TRY(upload(sg.dtiles, sg.tiles.data(), sizeof(CoefTile) * sg.tiles.size(), st));
     return CUR_OK;
 }
 
@@ -1334,6 +1375,12 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
     mv_lu<TB><<<P, 256, sm_lu, st>>>(a);
     CUR_CK(cudaGetLastError());
     note_launch();
+    if (sg.bpre) {
+        // the first cycle's B = C M^-1 of every problem on the tensor cores
+        CUR_TRY(coef_tc_launch(h, reinterpret_cast<const float*>(basis), sg.rows_total, r, sg.minv64, minv_stride(r), P,
+                               sg.dtiles, (int)sg.tiles.size(), sg.done, sg.wh, sg.wl, sg.bpre, st));
+        a.bpre = sg.bpre;
+    }
     CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
     if (solo_slots > 0) {
         MvArgs aw = a;
