@@ -105,6 +105,56 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The metric's comparison ("vs plain FP32 maxvol at equal volume"): the mixed-precision
+# workload, A = X diag(exp(-j/20)) Y^T + N(0, 1e-4) rounded to BF16, 262144 x 16384, r = 128.
+FORMS_WORKLOAD = dict(name="bf16_factor_product_262144x16384_r128", m=262144, n=16384, r=128, b_r=256, b_c=16,
+                      delta=1e-2, noise_std=1e-2)
+
+
+def forms_comparison(dev, reps: int = 2) -> dict:
+    """Crosses per second of the same cross with the coefficient products of the swap
+    iteration in FP32 (the plain engine), BF16 and FP8 (E4M3, row-scaled), each with its
+    volume ratio |det A(I,J)| / |det A(I_fp32, J_fp32)| (log-volumes from the library's FP64
+    factorisation of A(I,J)). One warm-up cross per form, then `reps` timed with CUDA events."""
+    import torch
+    import paper_2502_11017_gb300 as cur
+    from paper_2502_11017_gb300 import workloads as wl
+    w = FORMS_WORKLOAD
+    m, n, r = w["m"], w["n"], w["r"]
+    A = wl.bf16_factor_product(m, n, r, w["noise_std"], device=dev)
+    hd = cur.Handle(m, n, r, cur.CUR_BF16)
+    I = torch.empty(r, dtype=torch.int32, device=dev)
+    J = torch.empty(r, dtype=torch.int32, device=dev)
+    info = torch.zeros(64, dtype=torch.uint8, device=dev)
+    out = {}
+    try:
+        for form, kw in (("fp32", {}), ("bf16", {"bf16": True}), ("fp8", {"fp8": True})):
+            o = cur.opts(delta=w["delta"], **kw)
+            cur.cur_cross(hd.h, A, r, w["b_r"], w["b_c"], o, I, J, info)
+            st = cur.cur_sync_status(hd.h)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                cur.cur_cross(hd.h, A, r, w["b_r"], w["b_c"], o, I, J, info)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            st2 = cur.cur_sync_status(hd.h)
+            ms = e0.elapsed_time(e1) / reps
+            inf = cur.info_from_tensor(info)
+            out[form] = {"selections_per_s": 1000.0 / ms, "ms_per_cross": ms, "logvol": inf.logvol,
+                         "swaps": inf.swaps_total, "sweeps": inf.sweeps, "status": max(st, st2)}
+        for form in out:
+            out[form]["vol_ratio_vs_fp32"] = math.exp(out[form]["logvol"] - out["fp32"]["logvol"])
+    finally:
+        hd.close()
+        del A
+        torch.cuda.empty_cache()
+    return {"workload": w["name"], "dtype_data": "bf16", "forms": out,
+            "note": "coefficient products of the row polish (262144 rows) in each form; the other stages "
+                    "run the FP32 engine in all three"}
+
+
 def make_input():
     from paper_2502_11017_gb300 import workloads as wl
     w = WORKLOAD
@@ -362,6 +412,11 @@ def run_ours(args):
             "quality": {"logvol": inf.logvol, "sweeps": inf.sweeps, "swaps": inf.swaps_total,
                         "cheb": cheb.item(), "fro_rel": fro.item()},
         }
+        if world == 1 and not args.no_forms:
+            try:
+                line["comparison"] = forms_comparison(dev)
+            except Exception as e:  # the GPU line still stands
+                line["comparison"] = {"error": str(e)[-300:]}
         if world == 1 and not args.no_cpu:
             try:
                 line["cpu_baseline"] = cpu_baseline_estimate()
@@ -380,6 +435,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP32 / BF16 / FP8 comparison on the 262144 x 16384 BF16 workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

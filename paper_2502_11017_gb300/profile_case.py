@@ -5,6 +5,11 @@
     python -m paper_2502_11017_gb300.profile_case --call cross --m 65536 --n 8192 --r 64
     python -m paper_2502_11017_gb300.profile_case --call alg1 --m 65536 --n 8192 --r 64
     python -m paper_2502_11017_gb300.profile_case --call batch --count 4096
+    python -m paper_2502_11017_gb300.profile_case --call coef --m 262144 --r 64
+
+(--call coef: B = C M^-1 on the tensor cores for C = the first r columns of the matrix and
+M^-1 the inverse of the rows Algorithm 3 picks in C, the product the swap engine's first
+cycle takes; prints the HBM rate of its algorithmic bytes, read C + write B.)
 
 The matrix is exp(-|x_i - y_j|^2 / h^2) with uniform points (the generator of the
 65536 x 8192 workload, at any size). --reps calls are made after --warmup calls;
@@ -24,7 +29,8 @@ from paper_2502_11017_gb300 import workloads as wl
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols", "alg1", "batch"], required=True)
+    ap.add_argument("--call", choices=["aca", "residual", "cross", "rows", "cols", "alg1", "batch", "coef"],
+                    required=True)
     ap.add_argument("--count", type=int, default=4096, help="matrices of the batched workload (--call batch)")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=8192)
@@ -42,6 +48,8 @@ def main():
     dev = torch.device("cuda:0")
     if a.call == "batch":
         return batch(a)
+    if a.call == "coef":
+        return coef(a)
     if a.data == "bf16product":
         A = wl.bf16_factor_product(a.m, a.n, a.r, 1e-2, device=dev)
     elif a.data == "haar":
@@ -107,6 +115,35 @@ def main():
             gbs = 2 * m * n * 4 / (avg * 1e-3) / 1e9
             print(f"alg1 update pass: {npass} launches, {avg:.4f} ms average, {gbs:.0f} GB/s (2 m n 4 bytes)")
     st = cur.cur_sync_status(h)
+    if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
+        raise SystemExit(f"device status {st}")
+    hd.close()
+
+
+def coef(a):
+    """cur_coef_tf32 on an m x r FP32 basis (the Gaussian kernel's first r columns)."""
+    dev = torch.device("cuda:0")
+    m, r = a.m, a.r
+    C = torch.from_numpy(np.ascontiguousarray(wl.gaussian_kernel(m, r, 0.2, seed=a.seed, chunk_rows=4096))).to(dev)
+    hd = cur.Handle(m, r, r, cur.CUR_F32)
+    idx = torch.empty(r, dtype=torch.int32, device=dev)
+    cur.cur_aca_select(hd.h, C, 0, r, 1, idx)
+    # M^-1 = C(S,:)^-1 by the library's assembly of the cross (S, all r columns)
+    Mi = torch.empty((r, r), dtype=torch.float64, device=dev)
+    rc = torch.empty(1, dtype=torch.float64, device=dev)
+    cur.cur_assemble(hd.h, C, idx, torch.arange(r, dtype=torch.int32, device=dev), r, None, Mi, None, rc)
+    B = torch.empty((m, r), dtype=torch.float32, device=dev)
+    for rep in range(a.warmup + a.reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cur.cur_coef_tf32(hd.h, C, Mi, B)
+        e1.record()
+        torch.cuda.synchronize()
+        if rep >= a.warmup:
+            ms = e0.elapsed_time(e1)
+            print(f"coef m={m} r={r}: {ms:.4f} ms, {2 * m * r * 4 / (ms * 1e-3) / 1e9:.0f} GB/s of read C + write B")
+    st = cur.cur_sync_status(hd.h)
     if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
         raise SystemExit(f"device status {st}")
     hd.close()
