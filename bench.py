@@ -316,8 +316,30 @@ def run_ours(args):
     st = cur.cur_sync_status(h)
     if st != cur.CUR_OK:
         raise RuntimeError(f"device status {st} during warm-up")
-    cur.cur_prof_enable(h, True)
+
+    # Every call of the step only enqueues (decisions are taken on the device), so the step
+    # is captured once in a CUDA graph and replayed: the same kernels with the same device
+    # control flow, without the host launch gaps. The launches per step are counted at capture.
     cur.cur_prof_read(h)
+    graphs = {}
+
+    def capture(Ain):
+        g = torch.cuda.CUDAGraph()
+        cs_ = torch.cuda.Stream(dev)
+        cs_.wait_stream(stream)
+        with torch.cuda.stream(cs_):
+            with torch.cuda.graph(g, stream=cs_):
+                step(Ain)
+        stream.wait_stream(cs_)
+        torch.cuda.synchronize(dev)
+        return g
+
+    graphs["A"] = capture(A)
+    _pm, _pn, launches_per_step = cur.cur_prof_read(h)
+    graphs["A"].replay()
+    torch.cuda.synchronize(dev)
+    if cur.cur_sync_status(h) != cur.CUR_OK:
+        raise RuntimeError("device status after the first graph replay")
 
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] or 0) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
@@ -327,16 +349,31 @@ def run_ours(args):
     with ClockSampler(gpu_index) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
-            step(A)
+            graphs["A"].replay()
         ev1.record(stream)
         barrier()
     ms = ev0.elapsed_time(ev1)
-    pass_ms, pass_n, launches = cur.cur_prof_read(h)
-    cur.cur_prof_enable(h, False)
+    launches = launches_per_step * args.steps
     st = cur.cur_sync_status(h)
     if st != cur.CUR_OK:
         raise RuntimeError(f"device status {st} in the timed region")
     ms_max, value = aggregate(ms, args.steps, world, dev)
+
+    # the same steps launched one call at a time, with the Algorithm 3 pass bracketed by CUDA
+    # events on the stream (the roofline of the dominant kernel)
+    cur.cur_prof_enable(h, True)
+    cur.cur_prof_read(h)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(A)
+    ev1.record(stream)
+    barrier()
+    eager_ms = ev0.elapsed_time(ev1)
+    pass_ms, pass_n, _launches = cur.cur_prof_read(h)
+    cur.cur_prof_enable(h, False)
+    if cur.cur_sync_status(h) != cur.CUR_OK:
+        raise RuntimeError("device status in the eager steps")
 
     # end to end: each step's A copied from pinned host memory, I, J and the residual read
     # back. The copy of step k + 1 runs on a second stream into the other of two device
@@ -354,7 +391,6 @@ def run_ours(args):
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
 
     def fetch(k):
         cs.wait_event(e0)
@@ -364,6 +400,8 @@ def run_ours(args):
             bufs[k % 2].copy_(a_pin, non_blocking=True)
         copied[k].record(cs)
 
+    barrier()
+    e0.record(stream)
     fetch(0)
     for k in range(e2e_steps):
         if k + 1 < e2e_steps:
@@ -390,7 +428,8 @@ def run_ours(args):
             "peak_kind": kind, "traffic": traffic_record(),
             "algorithmic_bytes_per_launch": bytes_per_pass, "launches": pass_n,
             "avg_launch_ms": avg_pass_ms,
-            "share_of_step": pass_ms / ms if ms > 0 else None}
+            "share_of_step": pass_ms / eager_ms if eager_ms > 0 else None,
+            "timed_in": "the eager steps (events around each pass launch)"}
 
     if rank == 0:
         line = {
@@ -402,11 +441,14 @@ def run_ours(args):
                        "delta": w["delta"], "h": w["h"], "seed": w["seed"],
                        "parallelism": f"replicas x{world} (independent crosses per GPU)",
                        "l2": "A is 2.15 GB (> 129 MB L2) and is streamed each step; no flush",
-                       "step": "cur_cross + cur_assemble + cur_residual_cheb"},
+                       "step": "cur_cross + cur_assemble + cur_residual_cheb",
+                       "launch": "the step captured once in a CUDA graph, replayed per step",
+                       "eager_ms_per_step": eager_ms / args.steps},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": 2 * r * 4 + 8,
-                    "copy": "pinned host to device on a second stream, step k + 1's copy overlapping step k"},
+                    "copy": "pinned host to device on a second stream, step k + 1's copy overlapping step k; "
+                    "each step's calls launched one by one (no graph)"},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "quality": {"logvol": inf.logvol, "sweeps": inf.sweeps, "swaps": inf.swaps_total,

@@ -21,7 +21,8 @@
  *    on the device; later steps run as no-ops when they are not needed. Outputs are
  *    complete once the stream reaches that point (cur_sync_status synchronises and
  *    returns the status). Calls that do wait for the GPU: cur_sync_status,
- *    cur_prof_read, cur_cross_batched, and the BF16 / FP8 options of
+ *    cur_prof_read, the first cur_cross_batched of each class of batch (its
+ *    launch-shape tuning), and the BF16 / FP8 options of
  *    cur_maxvol_global and of the polish (CUR_FLAG_PREC_BF16 / CUR_FLAG_PREC_FP8),
  *    whose swap loop reads a counter back from the device.
  *  - Errors: argument errors (CUR_ERR_ARG), workspace exhaustion (CUR_ERR_NOMEM)
@@ -151,8 +152,11 @@ size_t cur_batch_workspace_size(const cur_batch_item* items, int32_t count);
  * info_out: device array of count cur_cross_info (may be NULL), each with that matrix's
  * status, log-volume, sweeps and swaps. The handle's status word records
  * CUR_ERR_SINGULAR or CUR_ERR_NOCONV if any matrix ended so, else CUR_WARN_RANK if
- * Algorithm 3 ran out early on any. Synchronises the stream; outputs are complete on
- * return. */
+ * Algorithm 3 ran out early on any. Every decision per matrix (a merge node's next start,
+ * the end of its sweeps, its status) is taken on the device and all sweeps are enqueued, so
+ * the call only enqueues — except the first call of each class of batch (batch size and work
+ * per matrix), which times the two launch shapes of Algorithm 3 and waits for them. After
+ * that first call a batch of the same class can be captured in a CUDA graph and replayed. */
 cur_status cur_cross_batched(cur_handle* h, const void* data, cur_dtype dtype,
                              const cur_batch_item* items, int32_t count, const cur_opts* opts,
                              int32_t* IJ_out, cur_cross_info* info_out, cudaStream_t stream);

@@ -682,8 +682,12 @@ __device__ double engine_kappa(const MinvKeeper<TB>& keep, const TB* basis, cons
     return sm * sx;
 }
 
+// Problems that one CTA holds alone run with kSoloThreads threads (their swaps never wait on
+// another CTA, so more threads only shorten each swap); groups of CTAs with 256 each.
+constexpr int kSoloThreads = 512;
+
 template <typename TB>
-__global__ void __launch_bounds__(256) mv_engine(MvArgs a) {
+__global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
@@ -979,8 +983,7 @@ __global__ void mv_iota(int32_t* S, int P, int r, int off) {
 // i >= k), the log-volume of Definition 1 for a set that may be numerically singular:
 // a pivot that is exactly zero gives -inf, any other pivot counts however small.
 template <typename TB>
-__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int64_t p, int r, const int32_t* rows,
-                                                     double* out) {
+__device__ void logvol_rows_dev(const TB* basis, int64_t p, int r, const int32_t* rows, double* out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* M = reinterpret_cast<double*>(smem_raw);
     __shared__ int s_p, s_zero;
@@ -1036,6 +1039,12 @@ __global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int64_t p,
     if (tid == 0) *out = s_zero ? -INFINITY : s_acc.log_value();
 }
 
+template <typename TB>
+__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int64_t p, int r, const int32_t* rows,
+                                                     double* out) {
+    logvol_rows_dev<TB>(basis, p, r, rows, out);
+}
+
 __global__ void pad_indices_k(int32_t* idx, const int32_t* count, int r, int64_t size) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     int fill = *count;
@@ -1080,15 +1089,21 @@ static inline unsigned nblk(int64_t n, int t = 256) {
 // Two parameter sizes: one short launch for the common small table, few launches of nearly
 // the 32 KB parameter limit for the tables of large batches.
 template <int N>
-struct Blob {
+struct __align__(16) Blob {
     unsigned char* dst;
     int bytes;
     int pad;
     unsigned char data[N];
 };
+// 16-byte words where the destination allows (every table is 16-byte aligned in the arena),
+// so a 30 KB parameter takes ~2000 reads instead of 30000.
 template <int N>
 __global__ void blob_k(const Blob<N> b) {
-    for (int i = threadIdx.x; i < b.bytes; i += blockDim.x) b.dst[i] = b.data[i];
+    const int nw = ((uintptr_t)b.dst % 16 == 0) ? b.bytes / 16 : 0;
+    const uint4* src = reinterpret_cast<const uint4*>(b.data);
+    uint4* dst = reinterpret_cast<uint4*>(b.dst);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    for (int i = 16 * nw + threadIdx.x; i < b.bytes; i += blockDim.x) b.dst[i] = b.data[i];
 }
 template <int N>
 static cur_status upload_n(unsigned char* dst, const unsigned char* src, size_t bytes, cudaStream_t st) {
@@ -1139,7 +1154,6 @@ struct Stage {
     long long* keyi = nullptr;
     TB* pub = nullptr;
     double* aux = nullptr;
-    std::vector<int> stat, sw;  // host copies after stage_read (batches only)
     int coop_slots = 0;         // slots [0, coop_slots) hold groups of several CTAs
     bool keep_singular_set = false;
     TB* bglob = nullptr;        // B in global memory when it cannot live in shared memory
@@ -1385,7 +1399,7 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
     if (solo_slots > 0) {
         MvArgs aw = a;
         aw.cta_base = sg.coop_slots;
-        mv_engine<TB><<<solo_slots, 256, sm_eng, st>>>(aw);
+        mv_engine<TB><<<solo_slots, kSoloThreads, sm_eng, st>>>(aw);
         CUR_CK(cudaGetLastError());
         note_launch();
     }
@@ -1417,20 +1431,6 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
     CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
     CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
     return stage_launch<TB>(h, basis, r, o, sg, aca_start, st);
-}
-
-// Per-problem statuses and swap counts to the host (synchronises the stream; batches only).
-template <typename TB>
-static cur_status stage_read(cur_handle* h, Stage<TB>& sg, cudaStream_t st) {
-    const int P = sg.P;
-    if ((size_t)P * 8 + 64 > h->host_stage_bytes) return CUR_ERR_NOMEM;
-    int32_t* hs = reinterpret_cast<int32_t*>(h->host_stage);
-    CUR_CK(cudaMemcpyAsync(hs, sg.pstatus, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
-    CUR_CK(cudaMemcpyAsync(hs + P, sg.swaps, sizeof(int32_t) * P, cudaMemcpyDeviceToHost, st));
-    CUR_CK(cudaStreamSynchronize(st));
-    sg.stat.assign(hs, hs + P);
-    sg.sw.assign(hs + P, hs + 2 * P);
-    return CUR_OK;
 }
 
 // ---------------------------------------------------------------- decisions on the device
@@ -2225,39 +2225,150 @@ struct BatBasis {
     int32_t p, r, nb;   // rows, rank, blocks
 };
 
-__global__ void bat_set_status_k(int* status, int code) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) set_status(status, code);
-}
-static cur_status set_status_host(cur_handle* h, int code, cudaStream_t st) {
-    bat_set_status_k<<<1, 32, 0, st>>>(h->status, code);
-    CUR_CK(cudaGetLastError());
-    note_launch();
-    return CUR_OK;
+// Tables of a batch reach the device as kernel parameters (upload_table): no host wait.
+static cur_status bat_upload(cur_handle*, void* dst, const void* src, size_t bytes, cudaStream_t st) {
+    return upload(dst, src, bytes, st);
 }
 
-// Uploads `bytes` from host memory through the handle's pinned staging buffer.
-static cur_status bat_upload(cur_handle* h, void* dst, const void* src, size_t bytes, cudaStream_t st) {
-    if (bytes > h->host_stage_bytes) return CUR_ERR_NOMEM;
-    CUR_CK(cudaStreamSynchronize(st));
-    std::memcpy(h->host_stage, src, bytes);
-    CUR_CK(cudaMemcpyAsync(dst, h->host_stage, bytes, cudaMemcpyHostToDevice, st));
-    CUR_CK(cudaStreamSynchronize(st));
-    return CUR_OK;
+// ---- per-matrix bookkeeping on the device: every decision of the batched cross (a merge
+// node's next start, the end of a matrix's sweeps, its status) is taken by these kernels,
+// so cur_cross_batched only enqueues (once its launch shape is tuned).
+
+// acc_m[item[pb]] += swaps[pb]
+__global__ void bat_acc_k(const int32_t* swaps, const int32_t* item, int P, int32_t* acc_m) {
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x)
+        atomicAdd(&acc_m[item[pb]], swaps[pb]);
+}
+
+// merge_retry_k for nodes of per-problem rank rr and per-matrix swap counts.
+__global__ void bat_merge_retry_k(int attempt, int P, int rs, const int32_t* rr, const int32_t* item,
+                                  int32_t* pstatus, int32_t* swaps, int32_t* done, int32_t* lu_mask, int32_t* S,
+                                  int32_t* retry, int32_t* acc_m) {
+    for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
+        if (attempt > 0 && retry[pb] != attempt) continue;
+        if (attempt < 2 && pstatus[pb] == CUR_ERR_SINGULAR) {
+            retry[pb] = attempt + 1;
+            pstatus[pb] = CUR_OK;
+            swaps[pb] = 0;
+            done[pb] = 0;
+            lu_mask[pb] = 1;
+            if (attempt == 0)
+                for (int k = 0; k < rr[pb]; ++k) S[(int64_t)pb * rs + k] = rr[pb] + k;
+        } else {
+            retry[pb] = 0;
+            atomicAdd(&acc_m[item[pb]], swaps[pb]);
+        }
+    }
+}
+
+// The polish of each matrix: its status, and its swaps added.
+__global__ void bat_polish_end_k(const int32_t* pstatus, const int32_t* swaps, int T, int32_t* side_stat,
+                                 int32_t* acc_m) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        side_stat[t] = pstatus[t];
+        acc_m[t] += swaps[t];
+    }
+}
+
+// A sweep stage runs only the matrices still sweeping.
+__global__ void bat_live_done_k(const int32_t* live, int T, int32_t* done) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) done[t] = live[t] ? 0 : 1;
+}
+
+__global__ void bat_copy_lv_k(const double* src, const int32_t* live, int T, double* lv) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        if (live[t]) lv[t] = src[t];
+}
+
+// Algorithm 3 ran out before r picks: CUR_WARN_RANK for that matrix.
+__global__ void bat_warn_k(const int32_t* cnt, const int32_t* rr, int T, int32_t* mstat) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x)
+        mstat[t] = cnt[t] < rr[t] ? CUR_WARN_RANK : CUR_OK;
+}
+
+// Sweep 1 (blockwise rows, then columns) of every matrix is over.
+__global__ void bat_sweep1_k(int T, const int32_t* st_r, const int32_t* sw_r, const int32_t* st_c,
+                             const int32_t* sw_c, int32_t* mstat, int32_t* msw, int32_t* msweeps, int32_t* live) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        for (int k = 0; k < 8; ++k) msw[t * 8 + k] = 0;
+        msw[t * 8] = sw_r[t] + sw_c[t];
+        msweeps[t] = 1;
+        if (st_r[t] != CUR_OK) mstat[t] = st_r[t];
+        if (st_c[t] != CUR_OK) mstat[t] = st_c[t];
+        live[t] = 1;
+    }
+}
+
+// A later sweep of the matrices still sweeping: it ends a matrix's sweeps if a stage ended
+// with an error or nothing was swapped.
+__global__ void bat_sweep_end_k(int sweep, int T, const int32_t* q1, const int32_t* s1, const int32_t* q2,
+                                const int32_t* s2, int32_t* live, int32_t* msweeps, int32_t* msw, int32_t* mstat) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        if (!live[t]) continue;
+        msweeps[t] = sweep;
+        msw[t * 8 + sweep - 1] = s1[t] + s2[t];
+        if (q1[t] != CUR_OK || q2[t] != CUR_OK) {
+            mstat[t] = q1[t] != CUR_OK ? q1[t] : q2[t];
+            live[t] = 0;
+        } else if (s1[t] + s2[t] == 0) {
+            live[t] = 0;
+        }
+    }
+}
+
+// log|det A(I,J)| of each matrix whose cross ended with an error (one CTA per matrix): such a
+// stage leaves no log|det| of its own.
+__global__ void __launch_bounds__(256) bat_logvol_k(const float* Rt, const BatBasis* brt, const int32_t* J, int rs,
+                                                    const int32_t* mstat, double* lvf) {
+    const int t = blockIdx.x;
+    const int sv = mstat[t];
+    if (sv == CUR_OK || sv == CUR_WARN_RANK) return;
+    const BatBasis b = brt[t];
+    logvol_rows_dev<float>(Rt + b.boff, b.p, b.r, J + (int64_t)t * rs, lvf + t);
+}
+
+// The host-visible outcome: the status word (the last SINGULAR / NOCONV in matrix order, else
+// CUR_WARN_RANK if any matrix's Algorithm 3 ran out) and each matrix's cur_cross_info.
+__global__ void bat_finish_k(int T, const int32_t* mstat, const int32_t* cnt, const int32_t* msweeps,
+                             const int32_t* msw, const double* lvc, const double* lvf, cur_cross_info* info,
+                             int* hstatus) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int worst = CUR_OK, warn = 0;
+        for (int t = 0; t < T; ++t) {
+            if (mstat[t] == CUR_ERR_SINGULAR || mstat[t] == CUR_ERR_NOCONV) worst = mstat[t];
+            if (mstat[t] == CUR_WARN_RANK) warn = 1;
+        }
+        if (worst != CUR_OK) set_status(hstatus, worst);
+        else if (warn) set_status(hstatus, CUR_WARN_RANK);
+    }
+    if (!info) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        cur_cross_info f;
+        const int sv = mstat[t];
+        f.logvol = (sv != CUR_OK && sv != CUR_WARN_RANK) ? lvf[t] : lvc[t];
+        f.sweeps = msweeps[t];
+        f.swaps_total = 0;
+        for (int k = 0; k < 8; ++k) {
+            f.sweep_swaps[k] = msw[t * 8 + k];
+            f.swaps_total += msw[t * 8 + k];
+        }
+        f.aca_selected = cnt[t];
+        f.status = sv;
+        info[t] = f;
+    }
 }
 
 // Maxvol row selection (blocks, binary merge, polish) on every basis of `bs`. out: device,
-// row t at t rs (local row ids); logvol: device, one double per matrix. stat and swaps
-// receive each matrix's polish status and its swaps.
+// row t at t rs (local row ids); logvol: device, one double per matrix; side_stat: device,
+// the polish's status per matrix; acc_m: device, swaps added per matrix.
 static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<BatBasis>& bs, int rs,
-                           const cur_opts* o, int32_t* out, double* logvol, std::vector<int>& stat,
-                           std::vector<int>& swaps, Arena& ar, cudaStream_t st) {
+                           const cur_opts* o, int32_t* out, double* logvol, int32_t* side_stat, int32_t* acc_m,
+                           Arena& ar, cudaStream_t st) {
     const int T = (int)bs.size();
     const size_t mark = ar.off;
-    std::vector<int> none;
-    stat.assign(T, CUR_OK);
-    swaps.assign(T, 0);
     // ---- blocks: Algorithm 3 start and maxvol on each block of each matrix
     std::vector<std::vector<int>> sets(T);
+    std::vector<int32_t> item;
     Stage<float> sb;
     for (int t = 0; t < T; ++t) {
         const int64_t base_sz = bs[t].p / bs[t].nb, extra = bs[t].p % bs[t].nb;
@@ -2272,25 +2383,28 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
             pr.gid_base = s0;
             sets[t].push_back((int)sb.probs.size());
             sb.probs.push_back(pr);
+            item.push_back(t);
             s0 += sz;
         }
     }
     CUR_TRY(stage_setup<float>(h, rs, sb, ar, true));
-    CUR_TRY(stage_run<float>(h, basis, rs, o, sb, true, none, none, st));
-    CUR_TRY(stage_read<float>(h, sb, st));
-    for (int t = 0; t < T; ++t)
-        for (int q : sets[t]) swaps[t] += sb.sw[q];
+    int32_t* ditem = ar.get<int32_t>(item.size());
     int32_t* cur = ar.get<int32_t>((size_t)sb.P * rs);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(stage_tables(sb, st));
+    CUR_TRY(stage_init(sb, nullptr, st));
+    CUR_TRY(stage_launch<float>(h, basis, rs, o, sb, true, st));
+    CUR_TRY(bat_upload(h, ditem, item.data(), sizeof(int32_t) * item.size(), st));
+    bat_acc_k<<<nblk(sb.P), 256, 0, st>>>(sb.swaps, ditem, sb.P, acc_m);
     bat_emit_k<<<nblk((int64_t)sb.P * rs), 256, 0, st>>>(sb.dprob, sb.S, sb.P, rs, cur);
     CUR_CK(cudaGetLastError());
-    note_launch();
+    note_launch(2);
     // ---- merge levels: node (2u, 2u+1) of every matrix that still has two sets or more
     std::vector<Stage<float>> keep;   // stages stay alive while their memory is in use
     keep.reserve(16);
     while (true) {
         std::vector<BatUnion> un;
-        std::vector<int> node_item, pass_src;
+        std::vector<int32_t> node_item, pass_src, hr;
         std::vector<std::vector<int>> nsets(T);
         int64_t uoff = 0;
         for (int t = 0; t < T; ++t) {
@@ -2306,6 +2420,7 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
                 nsets[t].push_back((int)un.size());
                 un.push_back(b);
                 node_item.push_back(t);
+                hr.push_back(b.r);
                 uoff += (int64_t)2 * b.r * b.r;
             }
         }
@@ -2323,16 +2438,13 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
         int32_t* cand = ar.get<int32_t>((size_t)Q * 2 * rs);
         float* U = ar.get<float>((size_t)uoff);
         int32_t* rr = ar.get<int32_t>(Q);
-        int32_t* flag = ar.get<int32_t>(Q);
+        int32_t* nitem = ar.get<int32_t>(Q);
         int32_t* nxt = ar.get<int32_t>((size_t)(Q + pass_src.size()) * rs);
         int32_t* psrc = ar.get<int32_t>(pass_src.size() + 1);
         if (!ar.ok) return CUR_ERR_NOMEM;
         CUR_TRY(bat_upload(h, dun, un.data(), sizeof(BatUnion) * Q, st));
-        {
-            std::vector<int32_t> hr(Q);
-            for (int q = 0; q < Q; ++q) hr[q] = un[q].r;
-            CUR_TRY(bat_upload(h, rr, hr.data(), sizeof(int32_t) * Q, st));
-        }
+        CUR_TRY(bat_upload(h, rr, hr.data(), sizeof(int32_t) * Q, st));
+        CUR_TRY(bat_upload(h, nitem, node_item.data(), sizeof(int32_t) * Q, st));
         bat_union_k<<<dim3(4, Q), 256, 0, st>>>(basis, dun, cur, rs, cand, U, h->status);
         CUR_CK(cudaGetLastError());
         note_launch();
@@ -2348,36 +2460,19 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
             lv.probs.push_back(pr);
         }
         CUR_TRY(stage_setup<float>(h, rs, lv, ar));
+        CUR_TRY(stage_tables(lv, st));
+        CUR_TRY(stage_init(lv, nullptr, st));
         bat_iota_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(rr, nullptr, Q, rs, 0, lv.S);
         CUR_CK(cudaGetLastError());
         note_launch();
-        CUR_TRY(stage_run<float>(h, U, rs, o, lv, false, none, none, st));
-        CUR_TRY(stage_read<float>(h, lv, st));
-        // a singular left start: the right set, then Algorithm 3 on the union; the swaps of
-        // an abandoned attempt are not counted
-        std::vector<int> skip(Q, 1), fl(Q, 0);
-        bool any = false;
-        for (int q = 0; q < Q; ++q) {
-            if (lv.stat[q] == CUR_ERR_SINGULAR) { skip[q] = 0; fl[q] = 1; any = true; }
-            else swaps[node_item[q]] += lv.sw[q];
-        }
-        for (int attempt = 0; attempt < 2 && any; ++attempt) {
-            if (attempt == 0) {
-                CUR_TRY(bat_upload(h, flag, fl.data(), sizeof(int32_t) * Q, st));
-                bat_iota_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(rr, flag, Q, rs, 1, lv.S);
-                CUR_CK(cudaGetLastError());
-                note_launch();
-            }
-            const std::vector<int> save = lv.stat, savesw = lv.sw;
-            CUR_TRY(stage_run<float>(h, U, rs, o, lv, attempt == 1, none, skip, st));
-            CUR_TRY(stage_read<float>(h, lv, st));
-            any = false;
-            for (int q = 0; q < Q; ++q) {
-                if (skip[q]) { lv.stat[q] = save[q]; lv.sw[q] = savesw[q]; continue; }
-                if (lv.stat[q] == CUR_ERR_SINGULAR && attempt == 0) { any = true; continue; }
-                swaps[node_item[q]] += lv.sw[q];
-                skip[q] = 1;
-            }
+        // the left set; where it is singular, the right set; where both are, Algorithm 3 on
+        // the union (the swaps of an abandoned attempt are not counted)
+        for (int attempt = 0; attempt < 3; ++attempt) {
+            CUR_TRY(stage_launch<float>(h, U, rs, o, lv, attempt == 2, st));
+            bat_merge_retry_k<<<nblk(Q), 256, 0, st>>>(attempt, Q, rs, rr, nitem, lv.pstatus, lv.swaps, lv.done,
+                                                       lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc_m);
+            CUR_CK(cudaGetLastError());
+            note_launch();
         }
         bat_emit_k<<<nblk((int64_t)Q * rs), 256, 0, st>>>(lv.dprob, lv.S, Q, rs, nxt);
         CUR_CK(cudaGetLastError());
@@ -2407,71 +2502,58 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
     CUR_TRY(stage_setup<float>(h, rs, sp, ar));
     int32_t* dsrc = ar.get<int32_t>(T);
     if (!ar.ok) return CUR_ERR_NOMEM;
+    CUR_TRY(stage_tables(sp, st));
+    CUR_TRY(stage_init(sp, nullptr, st));
     CUR_TRY(bat_upload(h, dsrc, src.data(), sizeof(int32_t) * T, st));
     bat_rows_copy_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(cur, dsrc, T, rs, sp.S);
     CUR_CK(cudaGetLastError());
     note_launch();
-    if (o->flags & CUR_FLAG_POLISH) {
-        CUR_TRY(stage_run<float>(h, basis, rs, o, sp, false, none, none, st));
-    } else {
-        cur_opts o2 = *o;
-        o2.delta = 1e300;   // no swap: one factorisation for log|det|
-        CUR_TRY(stage_run<float>(h, basis, rs, &o2, sp, false, none, none, st));
-    }
-    CUR_TRY(stage_read<float>(h, sp, st));
-    for (int t = 0; t < T; ++t) {
-        stat[t] = sp.stat[t];
-        swaps[t] += sp.sw[t];
-    }
+    cur_opts o2 = *o;
+    if (!(o->flags & CUR_FLAG_POLISH)) o2.delta = 1e300;   // no swap: one factorisation for log|det|
+    CUR_TRY(stage_launch<float>(h, basis, rs, &o2, sp, false, st));
+    bat_polish_end_k<<<nblk(T), 256, 0, st>>>(sp.pstatus, sp.swaps, T, side_stat, acc_m);
+    CUR_CK(cudaGetLastError());
+    note_launch();
     CUR_CK(cudaMemcpyAsync(out, sp.S, sizeof(int32_t) * T * rs, cudaMemcpyDeviceToDevice, st));
     CUR_CK(cudaMemcpyAsync(logvol, sp.logvol, sizeof(double) * T, cudaMemcpyDeviceToDevice, st));
-    CUR_CK(cudaStreamSynchronize(st));
     ar.off = mark;
     ar.ok = true;
     return CUR_OK;
 }
 
-// Global maxvol over all rows of the active bases from S (device, row t at t rs), in place;
-// a set that turns singular stays as reached (the swap iteration's own result).
-static cur_status bat_global(cur_handle* h, const float* basis, const std::vector<BatBasis>& bs,
-                             const std::vector<int>& active, int rs, const cur_opts* o, int32_t* S,
-                             double* logvol, std::vector<int>& stat, std::vector<int>& swaps, Arena& ar,
-                             cudaStream_t st) {
-    const int D = (int)active.size();
-    if (D == 0) return CUR_OK;
+// Global maxvol over all rows of every basis from S (device, row t at t rs), in place, for
+// the matrices still sweeping (live); a set that turns singular stays as reached (the swap
+// iteration's own result). stat, swaps: device, per matrix; lv (may be null): log|det| of the
+// live matrices.
+static cur_status bat_global(cur_handle* h, const float* basis, const std::vector<BatBasis>& bs, int rs,
+                             const cur_opts* o, int32_t* S, double* lv, const int32_t* live, int32_t* stat,
+                             int32_t* swaps, Arena& ar, cudaStream_t st) {
+    const int T = (int)bs.size();
     const size_t mark = ar.off;
     Stage<float> sg;
     sg.keep_singular_set = true;
-    for (int d = 0; d < D; ++d) {
-        const BatBasis& b = bs[active[d]];
+    for (int t = 0; t < T; ++t) {
         MvProb pr{};
-        pr.boff = b.boff;
-        pr.r = b.r;
-        pr.p = b.p;
+        pr.boff = bs[t].boff;
+        pr.r = bs[t].r;
+        pr.p = bs[t].p;
         sg.probs.push_back(pr);
     }
     CUR_TRY(stage_setup<float>(h, rs, sg, ar));
-    int32_t* idx = ar.get<int32_t>(D);
-    double* lvd = ar.get<double>(D);
-    if (!ar.ok) return CUR_ERR_NOMEM;
-    CUR_TRY(bat_upload(h, idx, active.data(), sizeof(int32_t) * D, st));
-    bat_rows_copy_k<<<nblk((int64_t)D * rs), 256, 0, st>>>(S, idx, D, rs, sg.S);
+    CUR_TRY(stage_tables(sg, st));
+    CUR_TRY(stage_init(sg, nullptr, st));
+    bat_live_done_k<<<nblk(T), 256, 0, st>>>(live, T, sg.done);
     CUR_CK(cudaGetLastError());
     note_launch();
-    std::vector<int> none;
-    CUR_TRY(stage_run<float>(h, basis, rs, o, sg, false, none, none, st));
-    CUR_TRY(stage_read<float>(h, sg, st));
-    bat_rows_scatter_k<<<nblk((int64_t)D * rs), 256, 0, st>>>(sg.S, idx, D, rs, S);
-    CUR_CK(cudaGetLastError());
-    note_launch();
-    CUR_CK(cudaMemcpyAsync(lvd, sg.logvol, sizeof(double) * D, cudaMemcpyDeviceToDevice, st));
-    std::vector<double> hl(D);
-    CUR_CK(cudaStreamSynchronize(st));
-    CUR_CK(cudaMemcpy(hl.data(), lvd, sizeof(double) * D, cudaMemcpyDeviceToHost));
-    for (int d = 0; d < D; ++d) {
-        stat[active[d]] = sg.stat[d];
-        swaps[active[d]] = sg.sw[d];
-        if (logvol) logvol[active[d]] = hl[d];
+    CUR_CK(cudaMemcpyAsync(sg.S, S, sizeof(int32_t) * T * rs, cudaMemcpyDeviceToDevice, st));
+    CUR_TRY(stage_launch<float>(h, basis, rs, o, sg, false, st));
+    CUR_CK(cudaMemcpyAsync(S, sg.S, sizeof(int32_t) * T * rs, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(stat, sg.pstatus, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, st));
+    CUR_CK(cudaMemcpyAsync(swaps, sg.swaps, sizeof(int32_t) * T, cudaMemcpyDeviceToDevice, st));
+    if (lv) {
+        bat_copy_lv_k<<<nblk(T), 256, 0, st>>>(sg.logvol, live, T, lv);
+        CUR_CK(cudaGetLastError());
+        note_launch();
     }
     ar.off = mark;
     ar.ok = true;
@@ -2503,13 +2585,15 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     std::vector<AcaIt> ai(T);
     std::vector<BatGItem> gc(T), gr(T);
     std::vector<BatBasis> bc(T), brt(T);
-    std::vector<int64_t> joff(T), nn(T);
+    std::vector<int64_t> joff(T), nn(T), io(T), jo2(T);
     std::vector<int32_t> rr(T);
     int64_t jo = 0, co = 0, ro = 0;
     for (int t = 0; t < T; ++t) {
         const cur_batch_item& b = items[t];
         ai[t] = AcaIt{b.offset, b.rows, b.cols, b.ld, b.r, jo};
         joff[t] = jo;
+        io[t] = 2 * jo;
+        jo2[t] = 2 * jo + b.r;
         nn[t] = b.cols;
         rr[t] = b.r;
         gc[t] = BatGItem{b.offset, b.rows, b.cols, b.ld, b.r, co, (int64_t)t * rs};
@@ -2531,8 +2615,11 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     void* dai = ar.take(sizeof(AcaIt) * T);
     BatGItem* dgc = ar.get<BatGItem>(T);
     BatGItem* dgr = ar.get<BatGItem>(T);
+    BatBasis* dbrt = ar.get<BatBasis>(T);
     int64_t* djoff = ar.get<int64_t>(T);
     int64_t* dnn = ar.get<int64_t>(T);
+    int64_t* dio = ar.get<int64_t>(T);
+    int64_t* djo = ar.get<int64_t>(T);
     int32_t* drr = ar.get<int32_t>(T);
     int32_t* J0 = ar.get<int32_t>(sum_r);
     int32_t* cnt = ar.get<int32_t>(T);
@@ -2542,8 +2629,18 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     int32_t* I = ar.get<int32_t>((size_t)T * rs);
     int32_t* J = ar.get<int32_t>((size_t)T * rs);
     double* lvc = ar.get<double>(T);
+    double* lvf = ar.get<double>(T);
     int32_t* dorder = ar.get<int32_t>(T);
     int* queue = ar.get<int>(1);
+    // per-matrix state on the device: status, sweeps, swaps per sweep, still sweeping; the
+    // two sides' polish statuses and swap counts; the sweep stages' statuses and swaps
+    int32_t* mstat = ar.get<int32_t>(T);
+    int32_t* msweeps = ar.get<int32_t>(T);
+    int32_t* msw = ar.get<int32_t>((size_t)8 * T);
+    int32_t* live = ar.get<int32_t>(T);
+    int32_t* acc = ar.get<int32_t>((size_t)2 * T);   // swaps of sweep 1: rows, columns
+    int32_t* sst = ar.get<int32_t>((size_t)2 * T);   // polish statuses of sweep 1: rows, columns
+    int32_t* qs = ar.get<int32_t>((size_t)4 * T);    // a later sweep: q1, s1, q2, s2
     if (!ar.ok) return CUR_ERR_NOMEM;
     {
         std::vector<int32_t> order(T);
@@ -2556,8 +2653,11 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
     CUR_TRY(bat_upload(h, dai, ai.data(), sizeof(AcaIt) * T, st));
     CUR_TRY(bat_upload(h, dgc, gc.data(), sizeof(BatGItem) * T, st));
     CUR_TRY(bat_upload(h, dgr, gr.data(), sizeof(BatGItem) * T, st));
+    CUR_TRY(bat_upload(h, dbrt, brt.data(), sizeof(BatBasis) * T, st));
     CUR_TRY(bat_upload(h, djoff, joff.data(), sizeof(int64_t) * T, st));
     CUR_TRY(bat_upload(h, dnn, nn.data(), sizeof(int64_t) * T, st));
+    CUR_TRY(bat_upload(h, dio, io.data(), sizeof(int64_t) * T, st));
+    CUR_TRY(bat_upload(h, djo, jo2.data(), sizeof(int64_t) * T, st));
     CUR_TRY(bat_upload(h, drr, rr.data(), sizeof(int32_t) * T, st));
     // ---- J0: Algorithm 3 on the columns of every matrix, padded per matrix
     const int tuned = tune_lookup(h, tkey);
@@ -2565,7 +2665,8 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
         CUR_TRY(bat_aca_launch(data, dai, dorder, queue, T, J0, cnt, Qws, std::min(T, tuned * h->num_sms),
                                h->status, st));
     } else {
-        // first batch of this class: time both shapes (each computes the same J0), keep the faster
+        // first batch of this class: time both shapes (each computes the same J0), keep the
+        // faster; this first call waits for the two timed launches
         float best_ms = 0.f;
         int best = 2;
         for (int per_sm = 1; per_sm <= 2; ++per_sm) {
@@ -2580,21 +2681,11 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
         }
         tune_store(h, tkey, best);
     }
-    std::vector<int32_t> hcnt(T);
-    CUR_CK(cudaStreamSynchronize(st));
-    CUR_CK(cudaMemcpy(hcnt.data(), cnt, sizeof(int32_t) * T, cudaMemcpyDeviceToHost));
+    bat_warn_k<<<nblk(T), 256, 0, st>>>(cnt, drr, T, mstat);
     bat_pad_k<<<nblk(T, 128), 128, 0, st>>>(J0, djoff, drr, dnn, cnt, T);
-    CUR_CK(cudaGetLastError());
-    note_launch();
     bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(J0, djoff, drr, T, rs, J, 0);
     CUR_CK(cudaGetLastError());
-    note_launch();
-    std::vector<int> status(T, CUR_OK), sw_r, sw_c, st_r, st_c;
-    std::vector<std::array<int, 8>> ssw(T);
-    for (auto& a : ssw) a.fill(0);
-    bool any_warn = false;
-    for (int t = 0; t < T; ++t)
-        if (hcnt[t] < items[t].r) { status[t] = CUR_WARN_RANK; any_warn = true; }
+    note_launch(3);
     auto gather_c = [&](const int32_t* Jd) -> cur_status {
         bat_gather_cols_k<<<dim3(8, T), 256, 0, st>>>(data, dgc, Jd, C);
         CUR_CK(cudaGetLastError());
@@ -2608,82 +2699,35 @@ cur_status cross_batched_impl(cur_handle* h, const float* data, const cur_batch_
         return CUR_OK;
     };
     // ---- sweep 1: blockwise rows on A(:,J0), then blockwise columns on A(I,:)^T
-    cur_opts orow = *o, ocol = *o;
+    CUR_CK(cudaMemsetAsync(acc, 0, sizeof(int32_t) * 2 * T, st));
     CUR_TRY(gather_c(J));
-    CUR_TRY(bat_rows(h, C, bc, rs, &orow, I, lvc, st_r, sw_r, ar, st));
+    CUR_TRY(bat_rows(h, C, bc, rs, o, I, lvc, sst, acc, ar, st));
     CUR_TRY(gather_r(I));
-    CUR_TRY(bat_rows(h, Rt, brt, rs, &ocol, J, lvc, st_c, sw_c, ar, st));
-    std::vector<double> lv(T);
-    CUR_CK(cudaMemcpy(lv.data(), lvc, sizeof(double) * T, cudaMemcpyDeviceToHost));
-    std::vector<int> sweeps(T, 1), active;
-    for (int t = 0; t < T; ++t) {
-        ssw[t][0] = sw_r[t] + sw_c[t];
-        if (st_r[t] != CUR_OK) status[t] = st_r[t];
-        if (st_c[t] != CUR_OK) status[t] = st_c[t];
-        active.push_back(t);
-    }
-    // ---- sweeps 2..8: global rows from I, global columns from J
-    std::vector<int> s1(T, 0), s2(T, 0), q1(T, CUR_OK), q2(T, CUR_OK);
-    for (int sweep = 2; sweep <= 8 && !active.empty(); ++sweep) {
+    CUR_TRY(bat_rows(h, Rt, brt, rs, o, J, lvc, sst + T, acc + T, ar, st));
+    bat_sweep1_k<<<nblk(T), 256, 0, st>>>(T, sst, acc, sst + T, acc + T, mstat, msw, msweeps, live);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    // ---- sweeps 2..8: global rows from I, global columns from J, for the matrices still
+    // sweeping (every sweep is enqueued; a matrix that has stopped takes no part)
+    for (int sweep = 2; sweep <= 8; ++sweep) {
         CUR_TRY(gather_c(J));
-        CUR_TRY(bat_global(h, C, bc, active, rs, o, I, nullptr, q1, s1, ar, st));
+        CUR_TRY(bat_global(h, C, bc, rs, o, I, nullptr, live, qs, qs + T, ar, st));
         CUR_TRY(gather_r(I));
-        CUR_TRY(bat_global(h, Rt, brt, active, rs, o, J, lv.data(), q2, s2, ar, st));
-        std::vector<int> still;
-        for (int t : active) {
-            sweeps[t] = sweep;
-            ssw[t][sweep - 1] = s1[t] + s2[t];
-            if (q1[t] != CUR_OK || q2[t] != CUR_OK) {
-                status[t] = q1[t] != CUR_OK ? q1[t] : q2[t];
-                continue;
-            }
-            if (s1[t] + s2[t] == 0) continue;
-            still.push_back(t);
-        }
-        active.swap(still);
+        CUR_TRY(bat_global(h, Rt, brt, rs, o, J, lvc, live, qs + 2 * T, qs + 3 * T, ar, st));
+        bat_sweep_end_k<<<nblk(T), 256, 0, st>>>(sweep, T, qs, qs + T, qs + 2 * T, qs + 3 * T, live, msweeps, msw,
+                                                 mstat);
+        CUR_CK(cudaGetLastError());
+        note_launch();
     }
-    // ---- outputs
-    int32_t* ptmp = ar.get<int32_t>(2 * sum_r);
-    int64_t* dio = ar.get<int64_t>(T);
-    int64_t* djo = ar.get<int64_t>(T);
-    if (!ar.ok) return CUR_ERR_NOMEM;
-    {
-        std::vector<int64_t> io(T), jo2(T);
-        for (int t = 0; t < T; ++t) { io[t] = 2 * joff[t]; jo2[t] = 2 * joff[t] + items[t].r; }
-        CUR_TRY(bat_upload(h, dio, io.data(), sizeof(int64_t) * T, st));
-        CUR_TRY(bat_upload(h, djo, jo2.data(), sizeof(int64_t) * T, st));
-    }
+    // ---- outputs; a matrix whose cross did not end OK reports log|det A(I,J)| taken directly
     bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(I, dio, drr, T, rs, IJ_out, 1);
     bat_pack_k<<<nblk((int64_t)T * rs), 256, 0, st>>>(J, djo, drr, T, rs, IJ_out, 1);
     CUR_CK(cudaGetLastError());
-    note_launch(2);
-    // a matrix whose cross did not end OK reports log|det A(I,J)| taken directly
-    for (int t = 0; t < T; ++t)
-        if (status[t] != CUR_OK && status[t] != CUR_WARN_RANK)
-            CUR_TRY(logvol_rows(CUR_F32, Rt + brt[t].boff, brt[t].p, items[t].r, J + (int64_t)t * rs, lvc + t, st));
-    std::vector<double> lvf(T);
-    CUR_CK(cudaStreamSynchronize(st));
-    CUR_CK(cudaMemcpy(lvf.data(), lvc, sizeof(double) * T, cudaMemcpyDeviceToHost));
-    int worst = CUR_OK;
-    for (int t = 0; t < T; ++t)
-        if (status[t] == CUR_ERR_SINGULAR || status[t] == CUR_ERR_NOCONV) worst = status[t];
-    if (worst != CUR_OK) {
-        CUR_TRY(set_status_host(h, worst, st));
-    } else if (any_warn) {
-        CUR_TRY(set_status_host(h, CUR_WARN_RANK, st));
-    }
-    if (info_out) {
-        std::vector<cur_cross_info> inf(T);
-        for (int t = 0; t < T; ++t) {
-            cur_cross_info& f = inf[t];
-            std::memset(&f, 0, sizeof(f));
-            f.logvol = (status[t] != CUR_OK && status[t] != CUR_WARN_RANK) ? lvf[t] : lv[t];
-            f.sweeps = sweeps[t];
-            for (int k = 0; k < 8; ++k) { f.sweep_swaps[k] = ssw[t][k]; f.swaps_total += ssw[t][k]; }
-            f.aca_selected = hcnt[t];
-            f.status = status[t];
-        }
-        CUR_TRY(bat_upload(h, info_out, inf.data(), sizeof(cur_cross_info) * T, st));
-    }
+    CUR_TRY(smem_attr((const void*)bat_logvol_k, (size_t)rs * rs * sizeof(double)));
+    bat_logvol_k<<<T, 256, (size_t)rs * rs * sizeof(double), st>>>(Rt, dbrt, J, rs, mstat, lvf);
+    CUR_CK(cudaGetLastError());
+    bat_finish_k<<<nblk(T), 256, 0, st>>>(T, mstat, cnt, msweeps, msw, lvc, lvf, info_out, h->status);
+    CUR_CK(cudaGetLastError());
+    note_launch(4);
     return CUR_OK;
 }

@@ -152,3 +152,35 @@ def test_batch_with_global_memory_coefficients_matches_oracle(dev):
         assert inf.status in (cur.CUR_OK, cur.CUR_WARN_RANK), t
         assert len(set(I)) == r and len(set(J)) == r
         _check_against_oracle(a, r, br, bc, I, J, inf)
+
+
+def test_batch_replays_as_one_cuda_graph(dev):
+    """After the first call of its class (which tunes the Algorithm 3 launch shape), the
+    batched cross only enqueues work, so the whole batch is captured in one CUDA graph; a
+    replay gives the eager call's sets, statuses and log-volumes."""
+    shapes = wl.uneven_batch_shapes(40, seed=12400, m_range=(256, 1500), n_range=(128, 700), r_range=(4, 32))
+    mats = [wl.uneven_batch_matrix(m, n, 12500 + t) for t, (m, n, _r, _br, _bc) in enumerate(shapes)]
+    data, offs = _pack(mats, dev)
+    items = cur.batch_items(shapes, offs)
+    hd = cur.Handle(1, 1, 1, workspace_bytes=cur.cur_batch_workspace_size(items))
+    total = sum(s[2] for s in shapes)
+    IJ = torch.full((2 * total,), -7, dtype=torch.int32, device=dev)
+    info = torch.zeros(len(shapes) * ctypes.sizeof(cur.CurCrossInfo), dtype=torch.uint8, device=dev)
+    cur.cur_cross_batched(hd.h, data, items, cur.opts(DELTA), IJ, info)      # tunes, then runs
+    st0 = cur.cur_sync_status(hd.h)
+    ref_ij, ref_info = IJ.clone(), info.clone()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            cur.cur_cross_batched(hd.h, data, items, cur.opts(DELTA), IJ, info)
+    torch.cuda.current_stream().wait_stream(s)
+    IJ.fill_(-7)
+    info.zero_()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(IJ, ref_ij) and torch.equal(info, ref_info)
+        assert cur.cur_sync_status(hd.h) == st0
+    hd.close()

@@ -4,6 +4,7 @@ Index work (picks of Algorithm 3, maxvol sets, merges) must match exactly on
 inputs whose decisions are well separated; floating-point outputs match within
 the tolerances stated per test (1e-5 of ||A||_C for FP32 residuals).
 """
+import ctypes
 import math
 
 import numpy as np
@@ -361,3 +362,33 @@ def test_cross_bf16(dev, handle):
     lv = orc.logvol(a_bf.astype(np.float64)[np.ix_(Ig, Jg)])
     same = sorted(Ig) == sorted(I_ref) and sorted(Jg) == sorted(J_ref)
     assert same or math.exp(lv - info_ref["logvol"]) >= 0.999
+
+
+def test_cross_replays_as_one_cuda_graph(dev):
+    """cur_cross only enqueues work, so a whole cross (with its data-dependent merge fallbacks
+    and sweeps decided on the device) is captured in a CUDA graph; replays give the eager
+    call's sets and info."""
+    a = wl.gaussian_kernel(3000, 1200, 0.25, seed=31).astype(np.float32)
+    A = to_dev(a, dev)
+    hd = cur.Handle(3000, 1200, 24, cur.CUR_F32)
+    I = torch.empty(24, dtype=torch.int32, device=dev)
+    J = torch.empty(24, dtype=torch.int32, device=dev)
+    info = torch.zeros(ctypes.sizeof(cur.CurCrossInfo), dtype=torch.uint8, device=dev)
+    cur.cur_cross(hd.h, A, 24, 6, 3, cur.opts(), I, J, info)
+    assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    ref = (I.clone(), J.clone(), info.clone())
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            cur.cur_cross(hd.h, A, 24, 6, 3, cur.opts(), I, J, info)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        I.fill_(-1)
+        J.fill_(-1)
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(I, ref[0]) and torch.equal(J, ref[1]) and torch.equal(info, ref[2])
+        assert cur.cur_sync_status(hd.h) == cur.CUR_OK
+    hd.close()
