@@ -21,7 +21,7 @@
  *    on the device; later steps run as no-ops when they are not needed. Outputs are
  *    complete once the stream reaches that point (cur_sync_status synchronises and
  *    returns the status). Calls that do wait for the GPU: cur_sync_status,
- *    cur_prof_read, the first cur_cross_batched of each class of batch (its
+ *    cur_prof_read, cur_prof_refactors, the first cur_cross_batched of each class of batch (its
  *    launch-shape tuning), and the BF16 / FP8 options of
  *    cur_maxvol_global and of the polish (CUR_FLAG_PREC_BF16 / CUR_FLAG_PREC_FP8),
  *    whose swap loop reads a counter back from the device.
@@ -82,6 +82,11 @@ typedef struct {
 #define CUR_FLAG_POLISH 1u
 #define CUR_FLAG_PREC_BF16 2u   /* cur_maxvol_global: BF16 coefficient products first */
 #define CUR_FLAG_PREC_FP8 4u    /* the same with E4M3 products (row-scaled); wins over BF16 */
+/* FP32/BF16 data: factorise C(S,:) afresh at the start of every cycle of the swap iteration,
+ * as the iteration of Section 1.2 is stated. Without it the kept double-float inverse is
+ * carried across cycles while its drift bound, the sum over swaps of kappa_inf(C(S,:)), stays
+ * at or below 2^18 (drift <= 2^-30 of an FP32 coefficient); FP64 data always factorises. */
+#define CUR_FLAG_REFACTOR_ALWAYS 8u
 
 /* Summary of one cur_cross call, written to DEVICE memory by cur_cross. */
 typedef struct {
@@ -435,6 +440,12 @@ cur_status cur_sync_status(cur_handle* h, cudaStream_t stream);
 cur_status cur_prof_enable(cur_handle* h, int on);
 cur_status cur_prof_read(cur_handle* h, cudaStream_t stream, double* pass_ms,
                          int32_t* pass_launches, int64_t* kernel_launches);
+
+/* Instrumentation: the number of factorisations of C(S,:) made at cycle boundaries of the
+ * swap iteration (every cycle for FP64 data or with CUR_FLAG_REFACTOR_ALWAYS; for FP32/BF16
+ * data otherwise only when the drift bound exceeds 2^18) by this handle's calls since the
+ * last read. Synchronises `stream`, writes the count to *count (host) and resets it. */
+cur_status cur_prof_refactors(cur_handle* h, cudaStream_t stream, int64_t* count);
 
 /* Self-test of the bounded device waits (no counterpart in the paper): launches one CTA
  * that waits at a group barrier for a partner that does not exist. The wait gives up

@@ -19,13 +19,14 @@ CUR_F64, CUR_F32, CUR_BF16 = 0, 1, 2
 CUR_FLAG_POLISH = 1
 CUR_FLAG_PREC_BF16 = 2
 CUR_FLAG_PREC_FP8 = 4
+CUR_FLAG_REFACTOR_ALWAYS = 8
 
 # Every symbol include/cur.h declares.
 EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", "cur_aca_full",
            "cur_batch_workspace_size", "cur_cross_batched",
            "cur_maxvol_rows", "cur_maxvol_cols", "cur_merge", "cur_assemble",
            "cur_residual_cheb", "cur_cross", "cur_sync_status", "cur_default_opts",
-           "cur_status_string", "cur_prof_enable", "cur_prof_read",
+           "cur_status_string", "cur_prof_enable", "cur_prof_read", "cur_prof_refactors",
            "cur_residual_cheb_noalloc", "cur_selftest_wait_timeout",
            "cur_sketch", "cur_mlp_forward", "cur_mlp_grad", "cur_adam_step", "cur_propose",
            "cur_cross_from", "cur_maxvol_global",
@@ -99,6 +100,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_selftest_wait_timeout": ([P, P], ctypes.c_int),
         "cur_prof_read": ([P, P, ctypes.POINTER(D), ctypes.POINTER(I32),
                            ctypes.POINTER(I64)], ctypes.c_int),
+        "cur_prof_refactors": ([P, P, ctypes.POINTER(I64)], ctypes.c_int),
         "cur_sketch": ([P, pmat, P, P, I32, P, P, I32, P], ctypes.c_int),
         "cur_mlp_forward": ([P, P, I64, I32, I32, P, P, P], ctypes.c_int),
         "cur_mlp_grad": ([P, P, P, I64, P, I64, I32, I32, P, ctypes.c_float, P, P, P], ctypes.c_int),
@@ -182,9 +184,9 @@ def _stream(stream):
 
 
 def opts(delta: float = 1e-2, max_swaps: int = 0, nblocks: int = 1, polish: bool = True,
-         bf16: bool = False, fp8: bool = False) -> CurOpts:
+         bf16: bool = False, fp8: bool = False, refactor_always: bool = False) -> CurOpts:
     return CurOpts(delta, max_swaps, nblocks, (CUR_FLAG_POLISH if polish else 0) | (CUR_FLAG_PREC_BF16 if bf16 else 0)
-                   | (CUR_FLAG_PREC_FP8 if fp8 else 0))
+                   | (CUR_FLAG_PREC_FP8 if fp8 else 0) | (CUR_FLAG_REFACTOR_ALWAYS if refactor_always else 0))
 
 
 # ------------------------------------------------------------------ C ABI names
@@ -292,6 +294,13 @@ def cur_prof_read(h, stream=None):
     _check(load().cur_prof_read(h, _stream(stream), ctypes.byref(ms), ctypes.byref(n),
                                 ctypes.byref(k)), "cur_prof_read")
     return ms.value, n.value, k.value
+
+
+def cur_prof_refactors(h, stream=None) -> int:
+    """Cycle refactorisations of C(S,:) made by the handle's calls since the last read."""
+    n = ctypes.c_int64()
+    _check(load().cur_prof_refactors(h, _stream(stream), ctypes.byref(n)), "cur_prof_refactors")
+    return n.value
 
 
 def cur_selftest_wait_timeout(h, stream=None) -> None:

@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     // P0: reduce partials, downdate squared norms, local argmax over unpicked. The RC
     // partials of each column are summed by 4 threads in fixed order (deterministic).
     const int64_t j0 = P.nsel * g / G, j1 = P.nsel * (g + 1) / G;
-    double bv = -INFINITY;
+    unsigned long long bk = dkey(-INFINITY);
     long long bi = LLONG_MAX;
     double fs = 0.0;
     int bad = 0;
@@ -364,32 +364,34 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
                     nu = P.nu[j] - wd * wd;
                 }
                 P.nu[j] = nu;
-                if (!P.mask[j] && better(nu, (long long)j, bv, bi)) { bv = nu; bi = j; }
+                const unsigned long long kj = dkey(nu);
+                if (!P.mask[j] && better_key(kj, (long long)j, bk, bi)) { bk = kj; bi = j; }
             }
             __syncthreads();
         }
     }
-    block_argmax(bv, bi);
+    block_argmax_key(bk, bi);
     bad = __syncthreads_or(bad);
     if (t < 0) fs = block_sum(fs);
     if (tid == 0) {
-        P.keyv[g] = bv;
+        P.keyv[g] = dkey_value(bk);
         P.keyi[g] = bad ? -2LL : bi;
         P.redf[g] = fs;
     }
     if (!group_barrier(P.bar, (unsigned)G, P.status)) return;
 
     // P1: the global pick, identical in every CTA.
-    double pv = -INFINITY;
+    unsigned long long pk = dkey(-INFINITY);
     long long pi = LLONG_MAX;
     int anybad = 0;
     for (int gg = tid; gg < G; gg += nt) {
         const long long ki = P.keyi[gg];
+        const unsigned long long kg = dkey(P.keyv[gg]);
         if (ki == -2LL) anybad = 1;
-        else if (better(P.keyv[gg], ki, pv, pi)) { pv = P.keyv[gg]; pi = ki; }
+        else if (better_key(kg, ki, pk, pi)) { pk = kg; pi = ki; }
     }
     anybad = __syncthreads_or(anybad);
-    block_argmax(pv, pi);
+    block_argmax_key(pk, pi);
     if (anybad) {
         if (g == 0 && tid == 0) { *P.stop = 1; set_status(P.status, CUR_ERR_NONFINITE); }
         return;

@@ -126,9 +126,10 @@ cur_status cur_create(cur_handle** hp, size_t workspace_bytes) {
         return CUR_ERR_NOMEM;
     }
     h->host_stage_bytes = (size_t)4 << 20;
-    if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess ||
+    // two device words: the status word, then the count of cycle refactorisations
+    if (cudaMalloc(&h->status, 2 * sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&h->host_stage, h->host_stage_bytes) != cudaSuccess ||
-        cudaMemset(h->status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(h->status, 0, 2 * sizeof(int)) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&h->tune_ev[0]) != cudaSuccess || cudaEventCreate(&h->tune_ev[1]) != cudaSuccess) {
         if (h->ws) cudaFree(h->ws);
@@ -183,6 +184,16 @@ cur_status cur_prof_read(cur_handle* h, cudaStream_t st, double* pass_ms, int32_
     const long long nl = g_launches.exchange(0);
     if (kernel_launches) *kernel_launches = nl;
     h->prof_n = 0;
+    return CUR_OK;
+}
+
+cur_status cur_prof_refactors(cur_handle* h, cudaStream_t st, int64_t* count) {
+    if (!h || !count) return CUR_ERR_ARG;
+    CUR_CK(cudaStreamSynchronize(st));
+    int v = 0;
+    CUR_CK(cudaMemcpy(&v, h->status + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    CUR_CK(cudaMemset(h->status + 1, 0, sizeof(int)));
+    *count = v;
     return CUR_OK;
 }
 

@@ -42,32 +42,11 @@ __host__ __device__ constexpr size_t bat_aca_smem() {
            (size_t)kBA_MaxR * 8 + kBA_MaxN + 64;
 }
 
-__device__ __forceinline__ void bat_argmax(double& v, int& i) {
-    __shared__ double sv[32];
-    __shared__ int si[32];
-    for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
-    }
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) { sv[w] = v; si[w] = i; }
-    __syncthreads();
-    if (w == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sv[lane] : -INFINITY;
-        i = lane < (int)(blockDim.x >> 5) ? si[lane] : INT_MAX;
-        for (int o = 16; o > 0; o >>= 1) {
-            const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-            const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
-            if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
-        }
-        if (lane == 0) { sv[0] = v; si[0] = i; }
-    }
-    __syncthreads();
-    v = sv[0];
-    i = si[0];
-    __syncthreads();
+// (key, index) maximum over the CTA, integer keys (dkey order): no FP64 comparisons.
+__device__ __forceinline__ void bat_argmax(unsigned long long& k, int& i) {
+    long long li = i;
+    block_argmax_key(k, li);
+    i = (int)li;
 }
 
 __device__ __forceinline__ df64 bat_df_sum(df64 x) {
@@ -191,7 +170,7 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
                     if (c0 + c < n) part[rg * kBA_MaxN + c0 + c] = fast_two_sum(acc[c].s, acc[c].c);
             __syncthreads();
             // ---- pick
-            double bv = -INFINITY;
+            unsigned long long bk = dkey(-INFINITY);
             int bi = INT_MAX;
             double fs = 0.0;
             for (int j = tid; j < n; j += blockDim.x) {
@@ -208,14 +187,15 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
                     nuj = nu[j] - wd * wd;
                 }
                 nu[j] = nuj;
-                if (!mask[j] && (nuj > bv || (nuj == bv && j < bi))) { bv = nuj; bi = j; }
+                const unsigned long long kj = dkey(nuj);
+                if (!mask[j] && (kj > bk || (kj == bk && j < bi))) { bk = kj; bi = j; }
             }
             bad = __syncthreads_or(bad);
             if (t < 0) {
                 const df64 f = bat_df_sum(df64{(float)fs, (float)(fs - (double)(float)fs)});
                 if (tid == 0) s_frob2 = df_to_d(f);
             }
-            bat_argmax(bv, bi);
+            bat_argmax(bk, bi);
             if (bad) {
                 if (tid == 0) set_status(status, CUR_ERR_NONFINITE);
                 break;

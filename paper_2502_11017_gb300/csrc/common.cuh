@@ -91,36 +91,80 @@ __device__ __forceinline__ bool better(double v1, long long i1, double v2, long 
     return v1 > v2 || (v1 == v2 && i1 < i2);
 }
 
-__device__ __forceinline__ void warp_argmax(double& v, long long& i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-        long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
-        if (better(v2, i2, v, i)) { v = v2; i = i2; }
-    }
+// Order-preserving integer key of a double: dkey(a) < dkey(b) iff a < b, for numbers a, b
+// (-0 and +0 share one key); NaN takes key 0, below -inf, so it is never a maximum. Only
+// integer operations: GB300's FP64 pipe runs at about 1/64 of the FP32 rate, and the
+// comparisons of a (value, index) reduction in FP64 were the slow part of every argmax.
+__device__ __forceinline__ unsigned long long dkey(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if ((b << 1) == 0ull) return 1ull << 63;
+    if ((b & 0x7ff0000000000000ull) == 0x7ff0000000000000ull && (b & 0x000fffffffffffffull) != 0ull) return 0ull;
+    return (b >> 63) ? ~b : (b | (1ull << 63));
+}
+__device__ __forceinline__ double dkey_value(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & ~(1ull << 63)) : ~k;
+    return __longlong_as_double((long long)b);
+}
+// Key of a float, in the same order (for values that never meet a double's key).
+__device__ __forceinline__ unsigned fkey(float v) {
+    const unsigned b = __float_as_uint(v);
+    if ((b << 1) == 0u) return 1u << 31;
+    if ((b & 0x7f800000u) == 0x7f800000u && (b & 0x007fffffu) != 0u) return 0u;
+    return (b >> 31) ? ~b : (b | (1u << 31));
+}
+__device__ __forceinline__ bool better_key(unsigned long long k1, long long i1, unsigned long long k2, long long i2) {
+    return k1 > k2 || (k1 == k2 && i1 < i2);
 }
 
-// Block-wide argmax; every thread gets the result. blockDim.x must be a multiple
-// of 32 and at most 1024. Uses 2 x 32 words of static shared memory.
-__device__ __forceinline__ void block_argmax(double& v, long long& i) {
-    __shared__ double sv[32];
+// Warp-wide (key, index) maximum by four redux.sync steps: the largest key, then among its
+// holders the smallest index (signed order). All 32 lanes call it; every lane gets the result.
+__device__ __forceinline__ void warp_argmax_key(unsigned long long& k, long long& i) {
+    const unsigned full = 0xffffffffu;
+    const unsigned kh = (unsigned)(k >> 32), kl = (unsigned)k;
+    const unsigned mh = __reduce_max_sync(full, kh);
+    const unsigned ml = __reduce_max_sync(full, kh == mh ? kl : 0u);
+    const bool cand = kh == mh && kl == ml;
+    const unsigned long long u = cand ? ((unsigned long long)i ^ (1ull << 63)) : ~0ull;
+    const unsigned uh = __reduce_min_sync(full, (unsigned)(u >> 32));
+    const unsigned ul = __reduce_min_sync(full, (unsigned)(u >> 32) == uh ? (unsigned)u : ~0u);
+    k = ((unsigned long long)mh << 32) | ml;
+    i = (long long)((((unsigned long long)uh << 32) | ul) ^ (1ull << 63));
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, long long& i) {
+    unsigned long long k = dkey(v);
+    warp_argmax_key(k, i);
+    v = dkey_value(k);
+}
+
+// Block-wide (key, index) maximum; every thread gets the result. blockDim.x must be a
+// multiple of 32 and at most 1024. Uses 2 x 32 words of static shared memory.
+__device__ __forceinline__ void block_argmax_key(unsigned long long& k, long long& i) {
+    __shared__ unsigned long long sk[32];
     __shared__ long long si[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
-    warp_argmax(v, i);
+    warp_argmax_key(k, i);
     __syncthreads();
-    if (lane == 0) { sv[warp] = v; si[warp] = i; }
+    if (lane == 0) { sk[warp] = k; si[warp] = i; }
     __syncthreads();
     if (warp == 0) {
-        v = lane < nw ? sv[lane] : -INFINITY;
+        k = lane < nw ? sk[lane] : 0ull;
         i = lane < nw ? si[lane] : (long long)0x7fffffffffffffffLL;
-        warp_argmax(v, i);
-        if (lane == 0) { sv[0] = v; si[0] = i; }
+        warp_argmax_key(k, i);
+        if (lane == 0) { sk[0] = k; si[0] = i; }
     }
     __syncthreads();
-    v = sv[0];
+    k = sk[0];
     i = si[0];
     __syncthreads();
+}
+
+// Block-wide (value, index) maximum of doubles (larger value, then smaller index).
+__device__ __forceinline__ void block_argmax(double& v, long long& i) {
+    unsigned long long k = dkey(v);
+    block_argmax_key(k, i);
+    v = dkey_value(k);
 }
 
 __device__ __forceinline__ double block_sum(double v) {
@@ -238,25 +282,22 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
                                           double thresh, double* logabsdet) {
     __shared__ int s_p, s_sing;
-    __shared__ double s_d;
+    __shared__ double s_d, s_dinv;
     __shared__ LogAcc s_lacc;   // log|det| without a logarithm per step
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) { s_sing = 0; s_lacc.init(); }
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (tid < 32) {
-            double bv = -1.0;
-            int bi = k;
+            // first maximum |a_ik|, compared as integer keys (no FP64 comparisons)
+            unsigned long long bk = 0ull;
+            long long bi = k;
             for (int i = k + tid; i < r; i += 32) {
-                const double x = fabs(A[i * r + k]);
-                if (x > bv) { bv = x; bi = i; }
+                const unsigned long long x = dkey(fabs(A[i * r + k]));
+                if (x > bk) { bk = x; bi = i; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
-            }
-            if (tid == 0) s_p = bi;
+            warp_argmax_key(bk, bi);
+            if (tid == 0) s_p = (int)bi;
         }
         __syncthreads();
         const int p = s_p;
@@ -272,11 +313,11 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
             const double d = A[k * r + k];
             s_d = d;
             if (!(fabs(d) > thresh)) s_sing = 1;
-            else s_lacc.mul(df_from_d(d));
+            else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }   // one FP64 division, not one per thread
         }
         __syncthreads();
         if (s_sing) return 1;
-        const double dinv = 1.0 / s_d;
+        const double dinv = s_dinv;
         for (int i = tid; i < r; i += nt) {
             colk[i] = A[i * r + k];
             if (i != k) A[i * r + k] = 0.0;
@@ -286,7 +327,12 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
         __syncthreads();
         for (int j = tid; j < r; j += nt) A[k * r + j] *= dinv;
         __syncthreads();
-        {
+        if (nt % r == 0) {   // one column per thread: its pivot-row entry is read once
+            const int c = tid % r, di = nt / r;
+            const double akc = A[k * r + c];
+            for (int i = tid / r; i < r; i += di)
+                if (i != k) A[i * r + c] = fma(-colk[i], akc, A[i * r + c]);
+        } else {
             Walk2 w(tid, nt, r);
             for (int e = tid; e < r * r; e += nt, w.next())
                 if (w.i != k) A[e] = fma(-colk[w.i], A[k * r + w.c], A[e]);

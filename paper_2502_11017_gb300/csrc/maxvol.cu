@@ -82,6 +82,7 @@ struct MvArgs {
     void* pub;                 // slots x 2 x r (compute type)
     double* aux;               // slots x 2 (start: frob partials)
     int* status;               // handle status word
+    int* nrefactor;            // count of cycle refactorisations (instrumentation)
 };
 
 // ---------------------------------------------------------------- gathers
@@ -157,10 +158,14 @@ __global__ void gather_union_k(const TB* __restrict__ basis, int64_t p, int r,
 
 // ---------------------------------------------------------------- start: Algorithm 3 on rows
 
+// The problem's rows sit in shared memory with an odd row stride, so that the 32 lanes of
+// a warp, one row each, read 32 different banks.
+__host__ __device__ __forceinline__ int start_ld(int r) { return r | 1; }
+
 template <typename TB>
 struct StartSmem {
     static size_t bytes(int nloc, int r) {
-        size_t b = (size_t)nloc * r * sizeof(TB);
+        size_t b = (size_t)nloc * start_ld(r) * sizeof(TB);
         b = (b + 15) / 16 * 16 + (size_t)nloc * sizeof(double);
         b += (size_t)r * r * sizeof(double);        // Q (FP64 data) or the projector P
         b += (size_t)6 * r * sizeof(double);        // v, sd, partial sums (4 r)
@@ -170,46 +175,34 @@ struct StartSmem {
     }
 };
 
-// nu[i] = sum_c rows(i,c) * q(c) (mode 1) or rows(i,c)^2 (mode 0), each row split over 8
-// consecutive lanes (Dot2 for FP32 data, FP64 for FP64 data), combined by shuffles.
+// nu[i] = sum_c rows(i,c) * q(c) (mode 1: nu[i] -= that squared) or rows(i,c)^2 (mode 0),
+// one thread per row, the columns in order (Dot2 for FP32 data, FP64 for FP64 data); the
+// row's sum meets the FP64 pipe once, for the downdate.
 template <typename TB>
-__device__ __forceinline__ void rows_dot4(const TB* rows, int nloc, int r, const double* q64,
-                                          const float* qh, const float* ql, int mode,
-                                          double* out, bool downdate) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int it0 = 0; it0 < 8 * nloc; it0 += nt) {
-        const int it = it0 + tid;
-        const int row = it >> 3, qt = it & 7;
-        double v = 0.0;
-        if (row < nloc) {
-            const int c0 = r * qt / 8, c1 = r * (qt + 1) / 8;
-            const TB* x = rows + (size_t)row * r;
-            if (std::is_same<TB, double>::value) {
-                DotD d;
-                for (int c = c0; c < c1; ++c) {
-                    if (mode == 0) d.add_sq(to_d(x[c])); else d.add(to_d(x[c]), q64[c]);
-                }
-                v = d.value();
-            } else {
-                Dot2 d;
-                for (int c = c0; c < c1; ++c) {
-                    if (mode == 0) d.add_sq(to_f(x[c])); else d.add(to_f(x[c]), qh[c], ql[c]);
-                }
-                v = d.value();
-            }
+__device__ __forceinline__ void rows_dot(const TB* rows, int ld, int nloc, int r, const double* q64,
+                                         const float* qh, const float* ql, int mode,
+                                         double* out, bool downdate) {
+    for (int row = threadIdx.x; row < nloc; row += blockDim.x) {
+        const TB* x = rows + (size_t)row * ld;
+        double v;
+        if constexpr (std::is_same<TB, double>::value) {
+            DotD d;
+            if (mode == 0) for (int c = 0; c < r; ++c) d.add_sq(x[c]);
+            else for (int c = 0; c < r; ++c) d.add(x[c], q64[c]);
+            v = d.value();
+        } else {
+            Dot2 d;
+            if (mode == 0) for (int c = 0; c < r; ++c) d.add_sq(to_f(x[c]));
+            else for (int c = 0; c < r; ++c) d.add(to_f(x[c]), qh[c], ql[c]);
+            v = d.value();
         }
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        v += __shfl_xor_sync(0xffffffffu, v, 4);
-        if (row < nloc && qt == 0) {
-            if (downdate) out[row] -= v * v;
-            else out[row] = v;
-        }
+        if (downdate) out[row] -= v * v;
+        else out[row] = v;
     }
 }
 
 template <typename TB>
-__global__ void __launch_bounds__(256) mv_start(MvArgs a) {
+__global__ void __launch_bounds__(256, 1) mv_start(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
@@ -219,7 +212,8 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     const int lo = part * pr.rpc, hi = min(pr.p, lo + pr.rpc), nloc = max(0, hi - lo);
     const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
     TB* rows = reinterpret_cast<TB*>(smem_raw);
-    size_t off = ((size_t)nloc * r * sizeof(TB) + 15) / 16 * 16;
+    const int ld = start_ld(r);
+    size_t off = ((size_t)nloc * ld * sizeof(TB) + 15) / 16 * 16;
     double* nu = reinterpret_cast<double*>(smem_raw + off); off += (size_t)nloc * sizeof(double);
     double* Q = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * r * sizeof(double);
     double* v = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * sizeof(double);
@@ -234,10 +228,13 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     int32_t* Sout = a.S + (int64_t)pb * rs;
 
-    for (int e = tid; e < nloc * r; e += nt) rows[e] = basis[(int64_t)lo * r + e];
+    {
+        Walk2 w(tid, nt, r);
+        for (int e = tid; e < nloc * r; e += nt, w.next()) rows[w.i * ld + w.c] = basis[(int64_t)lo * r + e];
+    }
     for (int i = tid; i < nloc; i += nt) msk[i] = 0;
     __syncthreads();
-    rows_dot4<TB>(rows, nloc, r, v, qh, ql, 0, nu, false);
+    rows_dot<TB>(rows, ld, nloc, r, v, qh, ql, 0, nu, false);
     if constexpr (!std::is_same<TB, double>::value) {
         df64* Pd = reinterpret_cast<df64*>(Q);
         for (int e = tid; e < r * r; e += nt) Pd[e] = df64{(e / r == e % r) ? 1.f : 0.f, 0.f};
@@ -248,27 +245,29 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     fs = block_sum(fs);
     int picked = 0;
     for (int k = 0; k < r; ++k) {
-        double bv = -INFINITY;
+        unsigned long long bk = dkey(-INFINITY);
         long long bi = LLONG_MAX;
-        for (int i = tid; i < nloc; i += nt)
-            if (!msk[i] && better(nu[i], (long long)(lo + i), bv, bi)) { bv = nu[i]; bi = lo + i; }
-        block_argmax(bv, bi);
+        for (int i = tid; i < nloc; i += nt) {
+            const unsigned long long kk = dkey(nu[i]);
+            if (!msk[i] && better_key(kk, (long long)(lo + i), bk, bi)) { bk = kk; bi = lo + i; }
+        }
+        block_argmax_key(bk, bi);
         const int par = k & 1;
         if (tid == 0) {
-            a.keyv[(pr.group0 + part) * 2 + par] = bv;
+            a.keyv[(pr.group0 + part) * 2 + par] = dkey_value(bk);
             a.keyi[(pr.group0 + part) * 2 + par] = bi;
             if (k == 0) a.aux[(pr.group0 + part) * 2] = fs;
         }
         if (!group_barrier(&a.bar[pb], (unsigned)(G * (k + 1)), a.status)) return;
         if (warp == 0) {
-            double pv = -INFINITY;
+            unsigned long long pk = dkey(-INFINITY);
             long long pi = LLONG_MAX;
             for (int g = lane; g < G; g += 32) {
-                const double kv = a.keyv[(pr.group0 + g) * 2 + par];
+                const unsigned long long kv = dkey(a.keyv[(pr.group0 + g) * 2 + par]);
                 const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
-                if (better(kv, ki, pv, pi)) { pv = kv; pi = ki; }
+                if (better_key(kv, ki, pk, pi)) { pk = kv; pi = ki; }
             }
-            warp_argmax(pv, pi);
+            warp_argmax_key(pk, pi);
             if (k == 0) {
                 const double f = warp_sum_strided(a.aux + (int64_t)pr.group0 * 2, G, 2);
                 if (lane == 0) s_frob = f;
@@ -397,7 +396,7 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
             __syncthreads();
         }
         // downdate: nu_i -= (c_i . q_k)^2
-        rows_dot4<TB>(rows, nloc, r, v, qh, ql, 1, nu, true);
+        rows_dot<TB>(rows, ld, nloc, r, v, qh, ql, 1, nu, true);
         __syncthreads();
     }
     // pad a short selection with the lowest unselected local rows
@@ -411,10 +410,94 @@ __global__ void __launch_bounds__(256) mv_start(MvArgs a) {
     }
 }
 
-// ---------------------------------------------------------------- FP64 inverse of C(S,:)
+// ---------------------------------------------------------------- inverse of C(S,:)
+//
+// FP64 data: gj_inverse (FP64). FP32/BF16 data: the same Gauss-Jordan steps in double-float
+// (about 48 bits, on the FP32 pipes): the coefficients B are FP32 and the kept inverse is
+// double-float already, and an FP64 elimination of a 64 x 64 matrix on one SM is bound by
+// GB300's FP64 pipe (about 1/64 of the FP32 rate). Partial pivoting by rows (first maximum
+// |a_ik|, i >= k, compared exactly as double-float keys); |pivot| <= thresh flags a
+// numerically singular matrix as in the FP64 form; log|det| from the pivots.
+__device__ __forceinline__ unsigned long long df_abs_key(df64 x) {
+    if (x.h < 0.f) x = df_neg(x);
+    return ((unsigned long long)fkey(x.h) << 32) | fkey(x.l);
+}
+
+__device__ int gj_inverse_df(df64* A, int r, df64* colk, int* piv, double thresh, double* logabsdet) {
+    __shared__ int s_p, s_sing;
+    __shared__ df64 s_dinv;
+    __shared__ LogAcc s_lacc;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) { s_sing = 0; s_lacc.init(); }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        if (tid < 32) {
+            unsigned long long bk = 0ull;
+            long long bi = k;
+            for (int i = k + tid; i < r; i += 32) {
+                const unsigned long long x = df_abs_key(A[i * r + k]);
+                if (x > bk) { bk = x; bi = i; }
+            }
+            warp_argmax_key(bk, bi);
+            if (tid == 0) s_p = (int)bi;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k)
+            for (int j = tid; j < r; j += nt) {
+                const df64 t = A[k * r + j];
+                A[k * r + j] = A[p * r + j];
+                A[p * r + j] = t;
+            }
+        __syncthreads();
+        if (tid == 0) {
+            piv[k] = p;
+            const df64 d = A[k * r + k];
+            if (!(fabs(df_to_d(d)) > thresh)) s_sing = 1;
+            else { s_lacc.mul(d); s_dinv = df_div(df64{1.f, 0.f}, d); }
+        }
+        __syncthreads();
+        if (s_sing) return 1;
+        const df64 d = A[k * r + k], dinv = s_dinv;
+        // multipliers l_i = a_ik / a_kk (a row equal to the pivot row, or an exact multiple,
+        // then cancels to exact zeros, as in LU), rows i != k updated with the unscaled
+        // pivot row, then the pivot row scaled: the Gauss-Jordan step in the order of LU
+        for (int i = tid; i < r; i += nt) colk[i] = i == k ? dinv : df_div(A[i * r + k], d);
+        __syncthreads();
+        if (nt % r == 0) {   // one column per thread: its pivot-row entry is read once
+            const int c = tid % r, di = nt / r;
+            const df64 akc = A[k * r + c];
+            for (int i = tid / r; i < r; i += di) {
+                if (i == k) continue;
+                A[i * r + c] = c == k ? df_neg(colk[i]) : df_sub(A[i * r + c], df_mul(colk[i], akc));
+            }
+        } else {
+            Walk2 w(tid, nt, r);
+            for (int e = tid; e < r * r; e += nt, w.next()) {
+                if (w.i == k) continue;
+                A[e] = w.c == k ? df_neg(colk[w.i]) : df_sub(A[e], df_mul(colk[w.i], A[k * r + w.c]));
+            }
+        }
+        __syncthreads();
+        for (int j = tid; j < r; j += nt) A[k * r + j] = j == k ? dinv : df_mul(A[k * r + j], dinv);
+        __syncthreads();
+    }
+    for (int k = r - 1; k >= 0; --k) {
+        const int p = piv[k];
+        if (p != k)
+            for (int i = tid; i < r; i += nt) {
+                const df64 t = A[i * r + k];
+                A[i * r + k] = A[i * r + p];
+                A[i * r + p] = t;
+            }
+        __syncthreads();
+    }
+    if (logabsdet) *logabsdet = s_lacc.log_value();
+    return 0;
+}
 
 template <typename TB>
-__global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
+__global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pb = blockIdx.x;
     if (a.done[pb] || !a.lu_mask[pb]) return;
@@ -426,27 +509,30 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
     __shared__ double s_max;
     const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
     const int32_t* S = a.S + (int64_t)pb * rs;
-    double mx = 0.0;
+    // C(S,:) in FP64 (FP64 data) or as exact double-float pairs (FP32/BF16 data: no FP64 work)
+    using TS = typename std::conditional<std::is_same<TB, double>::value, double, float>::type;
+    TS mx = 0;
     int bad = 0;
     for (int e = tid; e < r * r; e += nt) {
         const int k = e / r, c = e - k * r;
         const int s = S[k];
-        double x = 0.0;
-        if (s < 0 || s >= pr.p) bad = 1; else x = to_d(basis[(int64_t)s * r + c]);
+        TS x = 0;
+        if (s < 0 || s >= pr.p) bad = 1; else x = (TS)basis[(int64_t)s * r + c];
         if (!isfinite(x)) bad = 2;
-        M[e] = x;
+        if constexpr (std::is_same<TB, double>::value) M[e] = x;
+        else reinterpret_cast<df64*>(M)[e] = df64{x, 0.f};
         mx = fmax(mx, fabs(x));
     }
     bad = __syncthreads_or(bad);
     {
-        __shared__ double sm[32];
+        __shared__ TS sm[32];
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         if ((tid & 31) == 0) sm[tid >> 5] = mx;
         __syncthreads();
         if (tid == 0) {
-            double t = 0.0;
+            TS t = 0;
             for (int w = 0; w < (nt >> 5); ++w) t = fmax(t, sm[w]);
-            s_max = t;
+            s_max = (double)t;
         }
         __syncthreads();
     }
@@ -459,7 +545,17 @@ __global__ void __launch_bounds__(256) mv_lu(MvArgs a) {
         return;
     }
     double lv = 0.0;
-    const int sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
+    int sing;
+    if constexpr (std::is_same<TB, double>::value) {
+        sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
+    } else {
+        df64* Md = reinterpret_cast<df64*>(M);
+        sing = gj_inverse_df(Md, r, reinterpret_cast<df64*>(colk), piv, (double)r * kEps * s_max, &lv);
+        if (!sing) {
+            for (int e = tid; e < r * r; e += nt) M[e] = df_to_d(Md[e]);
+            __syncthreads();
+        }
+    }
     if (sing) {
         if (tid == 0) { a.pstatus[pb] = CUR_ERR_SINGULAR; a.done[pb] = 1; a.logvol[pb] = -INFINITY; }
         return;
@@ -497,9 +593,20 @@ struct EngineSmem {
     }
 };
 
+// Key of a coefficient magnitude (x >= 0, or -1 for none) in the order of its value: FP32
+// coefficients compare by their bits in the high word, FP64 ones by dkey. No FP64
+// arithmetic either way.
+__device__ __forceinline__ unsigned long long coef_key(float x) { return (unsigned long long)fkey(x) << 32; }
+__device__ __forceinline__ unsigned long long coef_key(double x) { return dkey(x); }
+__device__ __forceinline__ double coef_key_value(unsigned long long k, float) {
+    const unsigned f = (unsigned)(k >> 32);
+    return (double)__uint_as_float((f >> 31) ? (f & 0x7fffffffu) : ~f);
+}
+__device__ __forceinline__ double coef_key_value(unsigned long long k, double) { return dkey_value(k); }
+
 // Local argmax of |B| over the slice in the compute type; ties to the lowest index.
 template <typename TB>
-__device__ __forceinline__ void engine_scan(const TB* Bs, int nloc, int r, int lo, double& bv,
+__device__ __forceinline__ void engine_scan(const TB* Bs, int nloc, int r, int lo, unsigned long long& bk,
                                             long long& bi, int& nan) {
     TB v = (TB)-1;
     int idx = INT_MAX;
@@ -511,7 +618,7 @@ __device__ __forceinline__ void engine_scan(const TB* Bs, int nloc, int r, int l
         const int id = (lo + w.i) * r + w.c;
         if (x > v || (x == v && id < idx)) { v = x; idx = id; }
     }
-    bv = idx == INT_MAX ? -INFINITY : (double)v;
+    bk = idx == INT_MAX ? coef_key((TB)-INFINITY) : coef_key(v);
     bi = idx == INT_MAX ? LLONG_MAX : (long long)idx;
     nan = bad;
 }
@@ -548,6 +655,12 @@ struct MinvKeeper<float> {
             Ml[e] = v.l;
         }
     }
+    __device__ void load_df(const df64* W, int r) {
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            Mh[e] = W[e].h;
+            Ml[e] = W[e].l;
+        }
+    }
     __device__ void store(double* Mg, int r) const {
         for (int e = threadIdx.x; e < r * r; e += blockDim.x) Mg[e] = df_to_d(df64{Mh[e], Ml[e]});
     }
@@ -575,12 +688,23 @@ struct MinvKeeper<float> {
         for (int k = tid; k < r; k += nt) cj[k] = df_div(cj[k], bb);
         __syncthreads();
         // M^-1 <- M^-1 - (M^-1(:,j) / B_ij) (B(i,:) - e_j^T)
-        Walk2 w(tid, nt, r);
-        for (int e = tid; e < r * r; e += nt, w.next()) {
-            const df64 wv = w.c == jstar ? df_sub(brow[w.c], df64{1.f, 0.f}) : brow[w.c];
-            const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[w.i], wv));
-            Mh[e] = mv.h;
-            Ml[e] = mv.l;
+        if (nt % r == 0) {   // one column per thread
+            const int c = tid % r, di = nt / r;
+            const df64 wv = c == jstar ? df_sub(brow[c], df64{1.f, 0.f}) : brow[c];
+            for (int i = tid / r; i < r; i += di) {
+                const int e = i * r + c;
+                const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[i], wv));
+                Mh[e] = mv.h;
+                Ml[e] = mv.l;
+            }
+        } else {
+            Walk2 w(tid, nt, r);
+            for (int e = tid; e < r * r; e += nt, w.next()) {
+                const df64 wv = w.c == jstar ? df_sub(brow[w.c], df64{1.f, 0.f}) : brow[w.c];
+                const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[w.i], wv));
+                Mh[e] = mv.h;
+                Ml[e] = mv.l;
+            }
         }
         if (tid == 0) lacc.mul(bb);
     }
@@ -645,41 +769,91 @@ struct MinvKeeper<double> {
 template <typename TB>
 __device__ int engine_refactor(MinvKeeper<TB>& keep, const TB* basis, const int32_t* S, int r,
                                double* W, double* colk, int* piv, double* lv) {
-    double mx = 0.0;
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        const int k = e / r, c = e - k * r;
-        const double x = to_d(basis[(int64_t)S[k] * r + c]);
-        W[e] = x;
-        mx = fmax(mx, fabs(x));
+    if constexpr (std::is_same<TB, double>::value) {
+        double mx = 0.0;
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const int k = e / r, c = e - k * r;
+            const double x = basis[(int64_t)S[k] * r + c];
+            W[e] = x;
+            mx = fmax(mx, fabs(x));
+        }
+        mx = block_max(mx);
+        const int sing = gj_inverse(W, r, colk, piv, (double)r * kEps * mx, lv);
+        if (!sing) {
+            keep.load(W, r);
+            if (threadIdx.x == 0) keep.lacc.init();
+        }
+        __syncthreads();
+        return sing;
+    } else {
+        // double-float elimination (gj_inverse_df), straight into the keeper's two words
+        df64* Wd = reinterpret_cast<df64*>(W);
+        float mx = 0.f;
+        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+            const int k = e / r, c = e - k * r;
+            const float x = basis[(int64_t)S[k] * r + c];
+            Wd[e] = df64{x, 0.f};
+            mx = fmaxf(mx, fabsf(x));
+        }
+        __shared__ float s_mx[32];
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float t = 0.f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, s_mx[w]);
+            s_mx[0] = t;
+        }
+        __syncthreads();
+        const double thresh = (double)r * kEps * (double)s_mx[0];
+        const int sing = gj_inverse_df(Wd, r, reinterpret_cast<df64*>(colk), piv, thresh, lv);
+        if (!sing) {
+            keep.load_df(Wd, r);
+            if (threadIdx.x == 0) keep.lacc.init();
+        }
+        __syncthreads();
+        return sing;
     }
-    mx = block_max(mx);
-    const int sing = gj_inverse(W, r, colk, piv, (double)r * kEps * mx, lv);
-    if (!sing) {
-        keep.load(W, r);
-        if (threadIdx.x == 0) keep.lacc.init();
-    }
-    __syncthreads();
-    return sing;
 }
 
 // kappa_inf(M) = ||C(S,:)||_inf ||M^-1||_inf with the kept inverse (all threads call it).
+// It only scales the drift bound, so FP32 data sums in FP32 (no FP64 pipe work).
 template <typename TB>
 __device__ double engine_kappa(const MinvKeeper<TB>& keep, const TB* basis, const int32_t* S, int r) {
-    double sm = 0.0, sx = 0.0;
+    using TS = typename std::conditional<std::is_same<TB, double>::value, double, float>::type;
+    TS sm = 0, sx = 0;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     for (int k = threadIdx.x >> 5; k < r; k += nw) {   // a warp per row
-        double a = 0.0, x = 0.0;
+        TS a = 0, x = 0;
         const TB* row = basis + (int64_t)S[k] * r;
         for (int c = lane; c < r; c += 32) {
-            a += fabs(to_d(row[c]));
-            x += fabs((double)keep.value(k * r + c));
+            a += fabs((TS)row[c]);
+            x += fabs((TS)keep.value(k * r + c));
         }
-        sm = fmax(sm, warp_sum(a));
-        sx = fmax(sx, warp_sum(x));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+        }
+        sm = fmax(sm, a);
+        sx = fmax(sx, x);
     }
-    sm = block_max(sm);
-    sx = block_max(sx);
-    return sm * sx;
+    __shared__ TS s_m[32], s_x[32];
+    const int warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { s_m[warp] = sm; s_x[warp] = sx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        TS m = 0, x = 0;
+        for (int w = 0; w < nw; ++w) { m = fmax(m, s_m[w]); x = fmax(x, s_x[w]); }
+        s_m[0] = m;
+        s_x[0] = x;
+    }
+    __syncthreads();
+    const double kap = (double)s_m[0] * (double)s_x[0];
+    __syncthreads();
+    return kap;
 }
 
 // Problems that one CTA holds alone run with kSoloThreads threads (their swaps never wait on
@@ -707,7 +881,7 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
     double* Mg = a.minv64 + (int64_t)pb * minv_stride(rs);      // M^-1 in global memory (FP64)
     __shared__ double s_b;
     __shared__ long long s_w;
-    __shared__ int s_nan;
+    __shared__ int s_nan, s_go;
     __shared__ MinvKeeper<TB> keep;
     __shared__ int32_t S0[128];      // the start set, restored if C(S,:) turns singular (unless kept)
     __shared__ double s_lv0;         // log|det| of the last factorisation
@@ -732,11 +906,12 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
         const int sing = engine_refactor(keep, basis, Sg, r, gjw, gjw + (size_t)r * r,
                                          reinterpret_cast<int*>(gjw + (size_t)r * r + r), &lv);
         if (tid == 0 && !sing) { s_lv0 = lv; s_drift = 0.0; }
+        if (tid == 0 && a.nrefactor) atomicAdd(a.nrefactor, 1);
         __syncthreads();
         return sing;
     };
 
-    double bv;
+    unsigned long long bk;   // argmax |B_ij| as an order key (coef_key), its flat index, a NaN seen
     long long bi;
     int nan;
     int par = 0, total = a.swaps[pb], made_last = 0;
@@ -746,7 +921,7 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
     auto publish = [&](int pp) {
         if (solo) return;
         if (tid == 0) {
-            a.keyv[myslot * 2 + pp] = bv;
+            a.keyv[myslot * 2 + pp] = coef_key_value(bk, TB{});
             a.keyi[myslot * 2 + pp] = nan ? -2LL : bi;
         }
         if (!nan && bi != LLONG_MAX) {
@@ -802,43 +977,50 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
         }
         first_cycle = false;
         __syncthreads();
-        engine_scan(Bs, nloc, r, lo, bv, bi, nan);
+        engine_scan(Bs, nloc, r, lo, bk, bi, nan);
         nan = __syncthreads_or(nan);
-        block_argmax(bv, bi);
+        block_argmax_key(bk, bi);
         publish(par);
         int made = 0;
         while (true) {
+            // One thread reads the group's winner and takes the decision (no FP64 work on the
+            // other threads): s_go = 1 swap, 0 converged, -1 swap cap reached.
             if (solo) {
                 // the CTA's own argmax is the group's
-                if (tid == 0) { s_nan = nan; s_w = bi; s_b = bv; }
+                if (tid == 0) {
+                    s_nan = nan;
+                    s_w = bi;
+                    s_b = coef_key_value(bk, TB{});
+                    s_go = (bi == LLONG_MAX || !(s_b > 1.0 + a.delta)) ? 0 : (total >= a.max_swaps ? -1 : 1);
+                }
             } else {
                 ++epoch;
                 if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
                 if (tid < 32) {
-                    double wv = -INFINITY;
+                    unsigned long long wk = dkey(-INFINITY);
                     long long wi = LLONG_MAX;
                     int anynan = 0;
                     for (int g = tid; g < G; g += 32) {
                         const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
-                        const double kv = a.keyv[(pr.group0 + g) * 2 + par];
+                        const unsigned long long kv = dkey(a.keyv[(pr.group0 + g) * 2 + par]);
                         if (ki == -2LL) anynan = 1;
-                        else if (better(kv, ki, wv, wi)) { wv = kv; wi = ki; }
+                        else if (better_key(kv, ki, wk, wi)) { wk = kv; wi = ki; }
                     }
                     anynan = __any_sync(0xffffffffu, anynan);
-                    warp_argmax(wv, wi);
+                    warp_argmax_key(wk, wi);
                     if (tid == 0) {
                         s_nan = anynan;
                         s_w = wi;
-                        s_b = wv;
+                        s_b = dkey_value(wk);
+                        s_go = (wi == LLONG_MAX || !(s_b > 1.0 + a.delta)) ? 0 : (total >= a.max_swaps ? -1 : 1);
                     }
                 }
             }
             __syncthreads();
             if (s_nan) { fin = 3; fstat = CUR_ERR_NONFINITE; break; }
             const long long wi = s_w;
-            const double wv = s_b;
-            if (wi == LLONG_MAX || !(wv > 1.0 + a.delta)) { fin = made == 0 ? 1 : 2; break; }
-            if (total >= a.max_swaps) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
+            if (s_go == 0) { fin = made == 0 ? 1 : 2; break; }
+            if (s_go < 0) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
             const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
             const int owner = istar / pr.rpc;
             const TB* wsrc = solo ? Bs + (size_t)(istar - lo) * r
@@ -859,21 +1041,37 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
             {
                 TB v = (TB)-1;
                 int idx = INT_MAX, bad = 0;
-                Walk2 w(tid, nt, r);
-                for (int e = tid; e < nloc * r; e += nt, w.next()) {
-                    const TB x = fma(-colj[w.i], wrow[w.c], Bs[e]);
-                    Bs[e] = x;
-                    const TB ax = fabs(x);
-                    if (!(ax <= (TB)INFINITY)) bad = 1;
-                    const int id = (lo + w.i) * r + w.c;
-                    if (ax > v || (ax == v && id < idx)) { v = ax; idx = id; }
+                if (nt % r == 0) {
+                    // each thread keeps one column (r divides the block): B(i,:) - e_j is read
+                    // once, and its ids only grow, so the first maximum is the lowest id
+                    const int c = tid % r, di = nt / r;
+                    const TB wc = wrow[c];
+                    int i = tid / r, id = (lo + i) * r + c;
+                    TB* bp = Bs + (size_t)i * r + c;
+                    for (; i < nloc; i += di, id += di * r, bp += (size_t)di * r) {
+                        const TB x = fma(-colj[i], wc, *bp);
+                        *bp = x;
+                        const TB ax = fabs(x);
+                        bad |= !(ax <= (TB)INFINITY);
+                        if (ax > v) { v = ax; idx = id; }
+                    }
+                } else {
+                    Walk2 w(tid, nt, r);
+                    for (int e = tid; e < nloc * r; e += nt, w.next()) {
+                        const TB x = fma(-colj[w.i], wrow[w.c], Bs[e]);
+                        Bs[e] = x;
+                        const TB ax = fabs(x);
+                        if (!(ax <= (TB)INFINITY)) bad = 1;
+                        const int id = (lo + w.i) * r + w.c;
+                        if (ax > v || (ax == v && id < idx)) { v = ax; idx = id; }
+                    }
                 }
-                bv = idx == INT_MAX ? -INFINITY : (double)v;
+                bk = idx == INT_MAX ? coef_key((TB)-INFINITY) : coef_key(v);
                 bi = idx == INT_MAX ? LLONG_MAX : (long long)idx;
                 nan = bad;
             }
             nan = __syncthreads_or(nan);
-            block_argmax(bv, bi);
+            block_argmax_key(bk, bi);
             par ^= 1;
             publish(par);
             if (made == r) { fin = 2; break; }
@@ -987,6 +1185,7 @@ __device__ void logvol_rows_dev(const TB* basis, int64_t p, int r, const int32_t
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* M = reinterpret_cast<double*>(smem_raw);
     __shared__ int s_p, s_zero;
+    __shared__ double s_dinv;
     __shared__ LogAcc s_acc;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < r * r; e += nt) {
@@ -998,18 +1197,15 @@ __device__ void logvol_rows_dev(const TB* basis, int64_t p, int r, const int32_t
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (tid < 32) {
-            double bv = -1.0;
-            int bi = k;
+            // first maximum |m_ik|, compared as integer keys (no FP64 comparisons)
+            unsigned long long bk = 0ull;
+            long long bi = k;
             for (int i = k + tid; i < r; i += 32) {
-                const double x = fabs(M[i * r + k]);
-                if (x > bv) { bv = x; bi = i; }
+                const unsigned long long x = dkey(fabs(M[i * r + k]));
+                if (x > bk) { bk = x; bi = i; }
             }
-            for (int o = 16; o > 0; o >>= 1) {
-                const double v2 = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (v2 > bv || (v2 == bv && i2 < bi)) { bv = v2; bi = i2; }
-            }
-            if (tid == 0) s_p = bi;
+            warp_argmax_key(bk, bi);
+            if (tid == 0) s_p = (int)bi;
         }
         __syncthreads();
         const int p = s_p;
@@ -1025,13 +1221,23 @@ __device__ void logvol_rows_dev(const TB* basis, int64_t p, int r, const int32_t
             if (tid == 0) s_zero = 1;
             continue;   // no elimination past a zero pivot (uniform: d is read by all)
         }
-        if (tid == 0) s_acc.mul(df_from_d(d));
-        for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] /= d;
+        if (tid == 0) { s_acc.mul(df_from_d(d)); s_dinv = 1.0 / d; }   // multipliers by the reciprocal, as LAPACK's LU
         __syncthreads();
-        const int w = r - k - 1;
-        for (int e = tid; e < w * w; e += nt) {
-            const int i = k + 1 + e / w, j = k + 1 + e % w;
-            M[i * r + j] = fma(-M[i * r + k], M[k * r + j], M[i * r + j]);
+        const double dinv = s_dinv;
+        for (int i = k + 1 + tid; i < r; i += nt) M[i * r + k] *= dinv;
+        __syncthreads();
+        if (nt % r == 0) {   // one column per thread
+            const int c = tid % r, di = nt / r;
+            if (c > k) {
+                const double akc = M[k * r + c];
+                for (int i = k + 1 + (tid / r); i < r; i += di) M[i * r + c] = fma(-M[i * r + k], akc, M[i * r + c]);
+            }
+        } else {
+            const int w = r - k - 1;
+            for (int e = tid; e < w * w; e += nt) {
+                const int i = k + 1 + e / w, j = k + 1 + e % w;
+                M[i * r + j] = fma(-M[i * r + k], M[k * r + j], M[i * r + j]);
+            }
         }
         __syncthreads();
     }
@@ -1040,7 +1246,7 @@ __device__ void logvol_rows_dev(const TB* basis, int64_t p, int r, const int32_t
 }
 
 template <typename TB>
-__global__ void __launch_bounds__(256) logvol_rows_k(const TB* basis, int64_t p, int r, const int32_t* rows,
+__global__ void __launch_bounds__(512) logvol_rows_k(const TB* basis, int64_t p, int r, const int32_t* rows,
                                                      double* out) {
     logvol_rows_dev<TB>(basis, p, r, rows, out);
 }
@@ -1058,6 +1264,7 @@ __global__ void pad_indices_k(int32_t* idx, const int32_t* count, int r, int64_t
 // ---------------------------------------------------------------- host side
 
 static const size_t kSmemBudget = 200 * 1024;
+static const int kSpreadRows = 64;   // fewest rows per CTA of a spread group
 
 template <typename TB>
 static int rows_cap(int r) {
@@ -1194,7 +1401,7 @@ static cur_status stage_setup(cur_handle* h, int r, Stage<TB>& sg, Arena& ar, bo
             G = 1;
         } else if (G > 1 || pr.gmode) {
             // spread large problems over the SMs in proportion to their size
-            const int64_t spread = std::min<int64_t>((pr.p + 63) / 64,
+            const int64_t spread = std::min<int64_t>((pr.p + kSpreadRows - 1) / kSpreadRows,
                                                      (int64_t)h->num_sms * pr.p / std::max<int64_t>(1, tot_p));
             G = std::max<int64_t>(pr.gmode ? 1 : G, spread);
             G = std::min<int64_t>(G, h->num_sms);
@@ -1316,9 +1523,11 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
     a.r = r;
     a.delta = o->delta;
     a.max_swaps = o->max_swaps > 0 ? o->max_swaps : 100 * r;
-    // FP64 data: a fresh factorisation every cycle. FP32 B (double-float inverse,
-    // u = 2^-48): the carried inverse while sum(swaps * kappa) <= 2^18, i.e. drift <= 2^-30.
-    a.drift_max = std::is_same<TB, double>::value ? 0.0 : 262144.0;
+    // FP64 data (and CUR_FLAG_REFACTOR_ALWAYS): a fresh factorisation every cycle. FP32 B
+    // (double-float inverse, u = 2^-48): the carried inverse while sum(swaps * kappa) <= 2^18,
+    // i.e. drift <= 2^-30.
+    a.drift_max = (std::is_same<TB, double>::value || (o->flags & CUR_FLAG_REFACTOR_ALWAYS)) ? 0.0 : 262144.0;
+    a.nrefactor = h->status + 1;
     a.keep_singular_set = sg.keep_singular_set ? 1 : 0;
     a.bglob = sg.bglob;
     a.cta_prob = sg.dtab;
@@ -1386,7 +1595,7 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
             note_launch();
         }
     }
-    mv_lu<TB><<<P, 256, sm_lu, st>>>(a);
+    mv_lu<TB><<<P, 512, sm_lu, st>>>(a);
     CUR_CK(cudaGetLastError());
     note_launch();
     if (sg.bpre) {
@@ -1475,7 +1684,7 @@ static cur_status launch_inherit(const std::vector<InheritSrc>& src, int r, doub
                                  int32_t* lu_mask, const int32_t* done, InheritSrc* dsrc, cudaStream_t st) {
     if (src.empty()) return CUR_OK;
     CUR_TRY(upload(dsrc, src.data(), sizeof(InheritSrc) * src.size(), st));
-    inherit_k<<<(unsigned)src.size(), 128, 0, st>>>(dsrc, r, minv64, logvol, lu_mask, done);
+    inherit_k<<<(unsigned)src.size(), 1024, 0, st>>>(dsrc, r, minv64, logvol, lu_mask, done);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
@@ -2072,10 +2281,10 @@ cur_status logvol_rows(cur_dtype dt, const void* basis, int64_t p, int r, const 
     const size_t sm = (size_t)r * r * sizeof(double);
     if (dt == CUR_F64) {
         CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<double>, sm));
-        curk::logvol_rows_k<double><<<1, 256, sm, st>>>(static_cast<const double*>(basis), p, r, rows, out);
+        curk::logvol_rows_k<double><<<1, 512, sm, st>>>(static_cast<const double*>(basis), p, r, rows, out);
     } else {
         CUR_TRY(curk::set_smem_attr(curk::logvol_rows_k<float>, sm));
-        curk::logvol_rows_k<float><<<1, 256, sm, st>>>(static_cast<const float*>(basis), p, r, rows, out);
+        curk::logvol_rows_k<float><<<1, 512, sm, st>>>(static_cast<const float*>(basis), p, r, rows, out);
     }
     CUR_CK(cudaGetLastError());
     note_launch();

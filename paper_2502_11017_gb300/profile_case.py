@@ -95,6 +95,7 @@ def main():
     for _ in range(a.warmup):
         call()
     torch.cuda.synchronize()
+    cur.cur_prof_refactors(h)
     for _ in range(a.reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -114,6 +115,7 @@ def main():
             avg = tot_ms / npass
             gbs = 2 * m * n * 4 / (avg * 1e-3) / 1e9
             print(f"alg1 update pass: {npass} launches, {avg:.4f} ms average, {gbs:.0f} GB/s (2 m n 4 bytes)")
+    print(f"cycle refactorisations in the timed calls: {cur.cur_prof_refactors(h)}")
     st = cur.cur_sync_status(h)
     if st not in (cur.CUR_OK, cur.CUR_WARN_RANK):
         raise SystemExit(f"device status {st}")

@@ -197,6 +197,18 @@ def uneven_batch_device(shapes, seed: int = SEED_BASE + 3, rank: int = 96, noise
     return out, offs
 
 
+def graded_basis(p: int, r: int, sigma_min: float, seed: int) -> np.ndarray:
+    """A tall basis with a graded column space: X diag(sigma) Q, X (p x r) standard normal,
+    sigma geometric from 1 to sigma_min, Q a Haar orthogonal r x r; rounded once to FP32
+    (returned as FP32). Its best r x r submatrices have kappa ~ 1/sigma_min, so the swap
+    iteration's drift bound (sum over swaps of kappa) runs out within one cycle."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((p, r))
+    sig = np.geomspace(1.0, sigma_min, r)
+    Q = haar(r, r, rng)
+    return ((X * sig) @ Q).astype(np.float32)
+
+
 def hilbert(n: int) -> np.ndarray:
     """H_ij = 1/(i+j-1) with 1-based i, j (Section 3.1, Hilbert experiment)."""
     i = np.arange(1, n + 1, dtype=np.float64)

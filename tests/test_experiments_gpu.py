@@ -72,10 +72,27 @@ def test_hilbert_up_to_rank_12_valid_and_close(dev):
     assert all(b < x for x, b in zip(errs, errs[1:]))
 
 
+def _order_spread(a, I, J, count=200, seed=5):
+    """(min, max) of the oracle's error of C U R over orders of the same cross: the cross is
+    the pair of sets (I, J), and the order in which its rows and columns are listed is
+    arbitrary, but at the rounding floor the computed error depends on it."""
+    rng = np.random.default_rng(seed)
+    es = []
+    for t in range(count):
+        Ip = list(I) if t == 0 else list(rng.permutation(I))
+        Jp = list(J) if t == 0 else list(rng.permutation(J))
+        C, U, R, _, _ = orc.assemble(a, Ip, Jp)
+        es.append(orc.residual(a, C, U, R)[1])
+    return min(es), max(es)
+
+
 @pytest.mark.parametrize("k,rmax", [(5, 5), (10, 4)])
 def test_lowrank_product_matches_oracle(dev, k, rmax):
-    # an error below 1e-6 sits at the rounding floor of C U R (rcond A(I,J) <= 1e-9
-    # there), so the two evaluations of the same cross agree to 1 %, not to 1e-6
+    # The sets must be the oracle's. Above 1e-6 the errors agree to 1e-6; below, C U R is at
+    # its rounding floor (rcond A(I,J) <= 1e-9) and its error depends on the arbitrary order
+    # of the selected rows and columns (on the rank-5 product it spans a factor of about 4
+    # over orders of the oracle's own cross), so the GPU's error must lie within the
+    # oracle's spread over orders of the same sets.
     h = wl.cauchy_product(256, k)
     H = torch.from_numpy(h).to(dev)
     hd = cur.Handle(256, 256, 32, cur.CUR_F64)
@@ -84,17 +101,25 @@ def test_lowrank_product_matches_oracle(dev, k, rmax):
         Io, Jo, info, eo = _oracle(h, r)
         assert st == cur.CUR_OK
         assert sorted(I.tolist()) == Io and sorted(J.tolist()) == Jo, r
-        assert e == pytest.approx(eo, rel=1e-6 if eo > 1e-6 else 1e-2)
+        if eo > 1e-6:
+            assert e == pytest.approx(eo, rel=1e-6)
+        else:
+            lo, hi = _order_spread(h, Io, Jo)
+            assert lo / 1.5 <= e <= 1.5 * hi, (r, e, lo, hi)
     hd.close()
 
 
 def test_rank_5_product_beyond_its_rank_reports_singular(dev):
     # A(I,J) of a rank-5 matrix with r = 6 is singular: both sides say so, and the
-    # assembled cross (pseudo-inverse U) is still exact to rounding.
+    # assembled cross (pseudo-inverse U) is still exact to rounding. Every 6-set has volume
+    # zero, so the maximal-volume iteration does not fix the cross: past the start, which
+    # rows and columns end in it is decided by rounding, and the rank-5 core of such a cross
+    # has kappa ~ 1e10 - 1e11 (sigma_1 ~ 1, sigma_5 ~ 2e-11 - 7e-11 for the crosses the two
+    # sides return). The rounding floor of C U R, eps kappa, is then ~1e-5.
     h = wl.cauchy_product(256, 5)
     hd = cur.Handle(256, 256, 32, cur.CUR_F64)
-    e, _, st, _, _ = ex.rel_error(torch.from_numpy(h).to(dev), 6, hd)
+    e, _, st, I, J = ex.rel_error(torch.from_numpy(h).to(dev), 6, hd)
     hd.close()
-    _, _, info, eo = _oracle(h, 6)
+    Io, Jo, info, eo = _oracle(h, 6)
     assert st == cur.CUR_ERR_SINGULAR and info["status"] == orc.ERR_SINGULAR
-    assert e < 1e-6 and eo < 1e-6
+    assert e < 1e-5 and eo < 1e-5, (e, eo, I.tolist(), J.tolist(), Io, Jo)
