@@ -282,7 +282,7 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
                                           double thresh, double* logabsdet) {
     __shared__ int s_p, s_sing;
-    __shared__ double s_d, s_dinv;
+    __shared__ double s_dinv;
     __shared__ LogAcc s_lacc;   // log|det| without a logarithm per step
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) { s_sing = 0; s_lacc.init(); }
@@ -311,7 +311,6 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
         if (tid == 0) {
             piv[k] = p;
             const double d = A[k * r + k];
-            s_d = d;
             if (!(fabs(d) > thresh)) s_sing = 1;
             else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }   // one FP64 division, not one per thread
         }

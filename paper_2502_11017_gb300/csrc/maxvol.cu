@@ -665,33 +665,47 @@ struct MinvKeeper<float> {
         for (int e = threadIdx.x; e < r * r; e += blockDim.x) Mg[e] = df_to_d(df64{Mh[e], Ml[e]});
     }
     __device__ float value(int e) const { return __fadd_rn(Mh[e], Ml[e]); }
-    // winner (i*, j*) with C row `ci`: updates M^-1 and the |det| product
-    __device__ void swap(const float* ci, int r, int jstar) {
-        const int tid = threadIdx.x, nt = blockDim.x;
-        for (int c = tid; c < r; c += nt) crow[c] = df64{ci[c], 0.f};
-        __syncthreads();
-        // brow = crow M^-1: eight partial sums per column, so each dependent chain is r/8 long
-        for (int it = tid; it < 8 * r; it += nt) {
+    // The update for the winner (i*, j*) with C row `ci`, in four phases that the engine
+    // separates by barriers and overlaps with its own work: load the row and column j* of
+    // M^-1; the partial sums of the row i* of B = C(i*,:) M^-1; that row, B(i*,j*) and the
+    // column divided by it (and the |det| factor); the rank-1 update of M^-1.
+    __device__ void swap_load(const float* ci, int r, int jstar) {
+        for (int c = threadIdx.x; c < r; c += blockDim.x) {
+            crow[c] = df64{ci[c], 0.f};
+            cj[c] = df64{Mh[c * r + jstar], Ml[c * r + jstar]};
+        }
+    }
+    // brow = crow M^-1: eight partial sums per column, so each dependent chain is r/8 long
+    __device__ void swap_partials(int r) {
+        for (int it = threadIdx.x; it < 8 * r; it += blockDim.x) {
             const int c = it % r, qt = it / r;
             df64 s{0.f, 0.f};
             for (int k = r * qt / 8; k < r * (qt + 1) / 8; ++k)
                 s = df_add(s, df_mul_f(df64{Mh[k * r + c], Ml[k * r + c]}, crow[k].h));
             red[qt * r + c] = s;
         }
-        for (int k = tid; k < r; k += nt) cj[k] = df64{Mh[k * r + jstar], Ml[k * r + jstar]};
-        __syncthreads();
-        for (int c = tid; c < r; c += nt)
-            brow[c] = df_add(df_add(df_add(red[c], red[r + c]), df_add(red[2 * r + c], red[3 * r + c])),
-                             df_add(df_add(red[4 * r + c], red[5 * r + c]), df_add(red[6 * r + c], red[7 * r + c])));
-        __syncthreads();
-        const df64 bb = brow[jstar];
-        for (int k = tid; k < r; k += nt) cj[k] = df_div(cj[k], bb);
-        __syncthreads();
-        // M^-1 <- M^-1 - (M^-1(:,j) / B_ij) (B(i,:) - e_j^T)
+    }
+    __device__ df64 row_sum(int r, int c) const {
+        return df_add(df_add(df_add(red[c], red[r + c]), df_add(red[2 * r + c], red[3 * r + c])),
+                      df_add(df_add(red[4 * r + c], red[5 * r + c]), df_add(red[6 * r + c], red[7 * r + c])));
+    }
+    // every thread that needs B(i*,j*) forms the same sum as the thread of column j*
+    __device__ void swap_finish_row(int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        for (int c = tid; c < r; c += nt) {
+            brow[c] = row_sum(r, c);
+            cj[c] = df_div(cj[c], row_sum(r, jstar));
+        }
+        if (tid == nt - 1) lacc.mul(row_sum(r, jstar));
+    }
+    // M^-1 <- M^-1 - (M^-1(:,j) / B_ij) (B(i,:) - e_j^T)
+    __device__ void swap_update(int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
         if (nt % r == 0) {   // one column per thread
             const int c = tid % r, di = nt / r;
             const df64 wv = c == jstar ? df_sub(brow[c], df64{1.f, 0.f}) : brow[c];
-            for (int i = tid / r; i < r; i += di) {
+            int i = tid / r;
+            for (; i < r; i += di) {
                 const int e = i * r + c;
                 const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[i], wv));
                 Mh[e] = mv.h;
@@ -706,7 +720,6 @@ struct MinvKeeper<float> {
                 Ml[e] = mv.l;
             }
         }
-        if (tid == 0) lacc.mul(bb);
     }
     __device__ double dlog() const { return lacc.log_value(); }
 };
@@ -736,29 +749,37 @@ struct MinvKeeper<double> {
             for (int e = threadIdx.x; e < r * r; e += blockDim.x) Mg[e] = M[e];
     }
     __device__ double value(int e) const { return M[e]; }
-    __device__ void swap(const double* ci, int r, int jstar) {
-        const int tid = threadIdx.x, nt = blockDim.x;
-        for (int c = tid; c < r; c += nt) crow[c] = ci[c];
-        __syncthreads();
-        for (int it = tid; it < 8 * r; it += nt) {
+    __device__ void swap_load(const double* ci, int r, int jstar) {
+        for (int c = threadIdx.x; c < r; c += blockDim.x) {
+            crow[c] = ci[c];
+            cj[c] = M[c * r + jstar];
+        }
+    }
+    __device__ void swap_partials(int r) {
+        for (int it = threadIdx.x; it < 8 * r; it += blockDim.x) {
             const int c = it % r, qt = it / r;
             double s = 0.0;
             for (int k = r * qt / 8; k < r * (qt + 1) / 8; ++k) s = fma(crow[k], M[k * r + c], s);
             red[qt * r + c] = s;
         }
-        for (int k = tid; k < r; k += nt) cj[k] = M[k * r + jstar];
-        __syncthreads();
-        for (int c = tid; c < r; c += nt)
-            brow[c] = (((red[c] + red[r + c]) + (red[2 * r + c] + red[3 * r + c])) +
-                       ((red[4 * r + c] + red[5 * r + c]) + (red[6 * r + c] + red[7 * r + c])));
-        __syncthreads();
+    }
+    __device__ double row_sum(int r, int c) const {
+        return (((red[c] + red[r + c]) + (red[2 * r + c] + red[3 * r + c])) +
+                ((red[4 * r + c] + red[5 * r + c]) + (red[6 * r + c] + red[7 * r + c])));
+    }
+    __device__ void swap_finish_row(int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
+        for (int c = tid; c < r; c += nt) brow[c] = row_sum(r, c);
+        if (tid == nt - 1) lacc.mul(df_from_d(row_sum(r, jstar)));
+    }
+    __device__ void swap_update(int r, int jstar) {
+        const int tid = threadIdx.x, nt = blockDim.x;
         const double bb = brow[jstar];
         Walk2 w(tid, nt, r);
         for (int e = tid; e < r * r; e += nt, w.next()) {
             const double wv = brow[w.c] - (w.c == jstar ? 1.0 : 0.0);
             M[e] -= cj[w.i] * wv / bb;
         }
-        if (tid == 0) lacc.mul(df_from_d(bb));
     }
     __device__ double dlog() const { return lacc.log_value(); }
 };
@@ -856,6 +877,65 @@ __device__ double engine_kappa(const MinvKeeper<TB>& keep, const TB* basis, cons
     return kap;
 }
 
+// Refresh of an FP32 B slice: B = C M^-1 for nloc rows (r = 32 or 64), the
+// product of the engine's cycles after the first. C rows pass through shared memory
+// (coalesced loads) in chunks of 8 rows per warp, staged in the chunk's own rows of B; each
+// thread forms an 8 x (r/32) register tile (rows warp-uniform, columns lane + 32 j) with the
+// C values read four k at a time as one broadcast 16-byte load, so a warp issues 8 + 4 r/32
+// shared loads per 32 r/32 FMAs instead of two loads per FMA. Each entry is still one FMA
+// chain over k in order, as a dot product.
+template <int TN>
+__device__ __noinline__ void refresh_tiled_tn(float* Bs, const float* Mi, const float* Cs, int nloc, int r) {
+    constexpr int TM = 8;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int chunk = TM * nw;
+    for (int i0 = 0; i0 < nloc; i0 += chunk) {
+        const int nr = min(chunk, nloc - i0);
+        float* stage = Bs + (size_t)i0 * r;
+        for (int e = tid; e < nr * r; e += nt) stage[e] = Cs[(int64_t)i0 * r + e];
+        __syncthreads();
+        float acc[TM][TN];
+#pragma unroll
+        for (int q = 0; q < TM; ++q)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[q][j] = 0.f;
+        const float* crow[TM];
+#pragma unroll
+        for (int q = 0; q < TM; ++q) crow[q] = stage + (size_t)min(warp * TM + q, nr - 1) * r;   // rows past nr: not stored
+        for (int k = 0; k < r; k += 4) {
+            float4 cv[TM];
+#pragma unroll
+            for (int q = 0; q < TM; ++q) cv[q] = *reinterpret_cast<const float4*>(crow[q] + k);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                float mv[TN];
+#pragma unroll
+                for (int j = 0; j < TN; ++j) mv[j] = Mi[(k + kk) * r + lane + 32 * j];
+#pragma unroll
+                for (int q = 0; q < TM; ++q) {
+                    const float c = kk == 0 ? cv[q].x : kk == 1 ? cv[q].y : kk == 2 ? cv[q].z : cv[q].w;
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[q][j] = fmaf(c, mv[j], acc[q][j]);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TM; ++q) {
+            const int i = warp * TM + q;
+            if (i < nr)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) stage[(size_t)i * r + lane + 32 * j] = acc[q][j];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void engine_refresh_tiled(float* Bs, const float* Mi, const float* Cs, int nloc, int r) {
+    if (r == 32) refresh_tiled_tn<1>(Bs, Mi, Cs, nloc, r);
+    else refresh_tiled_tn<2>(Bs, Mi, Cs, nloc, r);
+}
+
 // Problems that one CTA holds alone run with kSoloThreads threads (their swaps never wait on
 // another CTA, so more threads only shorten each swap); groups of CTAs with 256 each.
 constexpr int kSoloThreads = 512;
@@ -879,7 +959,6 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
     TB* cstage = wrow + r;                      // global-memory mode: kEngStage C rows
     const size_t off = EngineSmem<TB>::head(nloc, r, gmode);
     double* Mg = a.minv64 + (int64_t)pb * minv_stride(rs);      // M^-1 in global memory (FP64)
-    __shared__ double s_b;
     __shared__ long long s_w;
     __shared__ int s_nan, s_go;
     __shared__ MinvKeeper<TB> keep;
@@ -929,6 +1008,69 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
             for (int c = tid; c < r; c += nt) pub[((int64_t)myslot * 2 + pp) * rs + c] = Bs[il * r + c];
         }
     };
+    // The swap test max|B_ij| > 1 + delta on order keys: for FP32 coefficients x > t holds
+    // exactly when x exceeds the largest float <= t; group keys are of the published doubles.
+    const unsigned long long thr_own = std::is_same<TB, double>::value
+                                           ? dkey(1.0 + a.delta) : coef_key((TB)__double2float_rd(1.0 + a.delta));
+    const unsigned long long thr_grp = dkey(1.0 + a.delta);
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    __shared__ unsigned long long r_k[32];
+    __shared__ long long r_i[32];
+    __shared__ int r_n[32];
+    // The CTA's argmax of the threads' (bk, bi) and its NaN flag, then the decision for the
+    // next swap in s_go (1 swap, 0 converged, -1 swap cap), s_w (winner) and s_nan: a solo
+    // CTA decides on its own argmax (two barriers in all); a group publishes it, meets at
+    // the group barrier and decides on the group's. False if the group barrier timed out.
+    auto reduce_decide = [&]() -> bool {
+        warp_argmax_key(bk, bi);
+        const int wn = __any_sync(0xffffffffu, nan);
+        if (lane == 0) { r_k[warp] = bk; r_i[warp] = bi; r_n[warp] = wn; }
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long k = lane < nw ? r_k[lane] : 0ull;
+            long long i = lane < nw ? r_i[lane] : LLONG_MAX;
+            const int n = __any_sync(0xffffffffu, lane < nw ? r_n[lane] : 0);
+            warp_argmax_key(k, i);
+            if (lane == 0) {
+                r_k[0] = k;
+                r_i[0] = i;
+                r_n[0] = n;
+                if (solo) {
+                    s_nan = n;
+                    s_w = i;
+                    s_go = (i == LLONG_MAX || !(k > thr_own)) ? 0 : (total >= a.max_swaps ? -1 : 1);
+                }
+            }
+        }
+        __syncthreads();
+        if (solo) return true;
+        bk = r_k[0];
+        bi = r_i[0];
+        nan = r_n[0];
+        publish(par);
+        ++epoch;
+        if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) return false;
+        if (tid < 32) {
+            unsigned long long wk = dkey(-INFINITY);
+            long long wi = LLONG_MAX;
+            int anynan = 0;
+            for (int g = tid; g < G; g += 32) {
+                const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
+                const unsigned long long kv = dkey(a.keyv[(pr.group0 + g) * 2 + par]);
+                if (ki == -2LL) anynan = 1;
+                else if (better_key(kv, ki, wk, wi)) { wk = kv; wi = ki; }
+            }
+            anynan = __any_sync(0xffffffffu, anynan);
+            warp_argmax_key(wk, wi);
+            if (tid == 0) {
+                s_nan = anynan;
+                s_w = wi;
+                s_go = (wi == LLONG_MAX || !(wk > thr_grp)) ? 0 : (total >= a.max_swaps ? -1 : 1);
+            }
+        }
+        __syncthreads();
+        return true;
+    };
     while (true) {
         // refresh: B slice = C slice M^-1
         __syncthreads();
@@ -938,7 +1080,13 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
             for (int e = tid; e < r * r; e += nt) Mi[e] = (TB)Mg[e];
         }
         __syncthreads();
-        if (a.bpre && first_cycle) {
+        bool tiled = false;
+        if constexpr (std::is_same<TB, float>::value) {
+            tiled = !(a.bpre && first_cycle) && !gmode && (r == 32 || r == 64);
+            if (tiled) engine_refresh_tiled(Bs, Mi, basis + (int64_t)lo * r, nloc, r);
+        }
+        if (tiled) {
+        } else if (a.bpre && first_cycle) {
             // the first cycle's B slice was formed on the tensor cores from the same M^-1
             const TB* src = static_cast<const TB*>(a.bpre) + pr.boff + (int64_t)lo * r;
             for (int e = tid; e < nloc * r; e += nt) Bs[e] = src[e];
@@ -978,65 +1126,34 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
         first_cycle = false;
         __syncthreads();
         engine_scan(Bs, nloc, r, lo, bk, bi, nan);
-        nan = __syncthreads_or(nan);
-        block_argmax_key(bk, bi);
-        publish(par);
+        if (!reduce_decide()) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
         int made = 0;
         while (true) {
-            // One thread reads the group's winner and takes the decision (no FP64 work on the
-            // other threads): s_go = 1 swap, 0 converged, -1 swap cap reached.
-            if (solo) {
-                // the CTA's own argmax is the group's
-                if (tid == 0) {
-                    s_nan = nan;
-                    s_w = bi;
-                    s_b = coef_key_value(bk, TB{});
-                    s_go = (bi == LLONG_MAX || !(s_b > 1.0 + a.delta)) ? 0 : (total >= a.max_swaps ? -1 : 1);
-                }
-            } else {
-                ++epoch;
-                if (!group_barrier(&a.bar[pb], (unsigned)G * epoch, a.status)) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
-                if (tid < 32) {
-                    unsigned long long wk = dkey(-INFINITY);
-                    long long wi = LLONG_MAX;
-                    int anynan = 0;
-                    for (int g = tid; g < G; g += 32) {
-                        const long long ki = a.keyi[(pr.group0 + g) * 2 + par];
-                        const unsigned long long kv = dkey(a.keyv[(pr.group0 + g) * 2 + par]);
-                        if (ki == -2LL) anynan = 1;
-                        else if (better_key(kv, ki, wk, wi)) { wk = kv; wi = ki; }
-                    }
-                    anynan = __any_sync(0xffffffffu, anynan);
-                    warp_argmax_key(wk, wi);
-                    if (tid == 0) {
-                        s_nan = anynan;
-                        s_w = wi;
-                        s_b = dkey_value(wk);
-                        s_go = (wi == LLONG_MAX || !(s_b > 1.0 + a.delta)) ? 0 : (total >= a.max_swaps ? -1 : 1);
-                    }
-                }
-            }
-            __syncthreads();
             if (s_nan) { fin = 3; fstat = CUR_ERR_NONFINITE; break; }
-            const long long wi = s_w;
             if (s_go == 0) { fin = made == 0 ? 1 : 2; break; }
             if (s_go < 0) { fin = 3; fstat = CUR_ERR_NOCONV; break; }
+            const long long wi = s_w;
             const int istar = (int)(wi / r), jstar = (int)(wi - (long long)istar * r);
             const int owner = istar / pr.rpc;
             const TB* wsrc = solo ? Bs + (size_t)(istar - lo) * r
                                   : pub + ((int64_t)(pr.group0 + owner) * 2 + par) * rs;
+            // the winner's row of B; the first CTA's update of M^-1 runs in four phases
+            // between these barriers (see MinvKeeper)
             for (int c = tid; c < r; c += nt) wrow[c] = wsrc[c];
+            if (part == 0) {
+                keep.swap_load(basis + (int64_t)istar * r, r, jstar);
+                if (tid == 0) a.S[(int64_t)pb * rs + jstar] = istar;
+            }
             __syncthreads();
             const TB b = wrow[jstar];
             for (int i = tid; i < nloc; i += nt) colj[i] = Bs[i * r + jstar] / b;
-            if (part == 0) {
-                keep.swap(basis + (int64_t)istar * r, r, jstar);
-                if (tid == 0) a.S[(int64_t)pb * rs + jstar] = istar;
-            }
-            if (tid == 0) wrow[jstar] = wrow[jstar] - (TB)1;
+            if (part == 0) keep.swap_partials(r);
+            __syncthreads();
+            if (part == 0) keep.swap_finish_row(r, jstar);
             __syncthreads();
             ++made;
             ++total;
+            if (part == 0) keep.swap_update(r, jstar);
             // B <- B - (B(:,j) / B_ij) (B(i,:) - e_j^T), fused with the next local argmax
             {
                 TB v = (TB)-1;
@@ -1045,7 +1162,7 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
                     // each thread keeps one column (r divides the block): B(i,:) - e_j is read
                     // once, and its ids only grow, so the first maximum is the lowest id
                     const int c = tid % r, di = nt / r;
-                    const TB wc = wrow[c];
+                    const TB wc = c == jstar ? wrow[c] - (TB)1 : wrow[c];
                     int i = tid / r, id = (lo + i) * r + c;
                     TB* bp = Bs + (size_t)i * r + c;
                     for (; i < nloc; i += di, id += di * r, bp += (size_t)di * r) {
@@ -1058,7 +1175,8 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
                 } else {
                     Walk2 w(tid, nt, r);
                     for (int e = tid; e < nloc * r; e += nt, w.next()) {
-                        const TB x = fma(-colj[w.i], wrow[w.c], Bs[e]);
+                        const TB wc = w.c == jstar ? wrow[w.c] - (TB)1 : wrow[w.c];
+                        const TB x = fma(-colj[w.i], wc, Bs[e]);
                         Bs[e] = x;
                         const TB ax = fabs(x);
                         if (!(ax <= (TB)INFINITY)) bad = 1;
@@ -1070,10 +1188,8 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
                 bi = idx == INT_MAX ? LLONG_MAX : (long long)idx;
                 nan = bad;
             }
-            nan = __syncthreads_or(nan);
-            block_argmax_key(bk, bi);
             par ^= 1;
-            publish(par);
+            if (!reduce_decide()) { fin = 3; fstat = CUR_ERR_TIMEOUT; break; }
             if (made == r) { fin = 2; break; }
         }
         made_last = made;
