@@ -27,6 +27,9 @@ namespace curk {
 
 enum { kNorm = 0, kDot = 1 };
 
+// Threads of the pivot CTA (one per SM).
+constexpr int kPivotThreads = 256;
+
 template <typename TA>
 using AccOf = typename std::conditional<std::is_same<TA, double>::value, DotD, Dot2>::type;
 
@@ -279,24 +282,32 @@ __device__ __forceinline__ double pivot_elem(const AcaParams& P, int64_t i, int6
 }
 
 // acc_a -= sum_kk Q(kk, ia) s(kk) and acc_b likewise for row ib. The Q values of eight
-// directions are loaded before any arithmetic (32 loads in flight per thread), and two
-// interleaved chains per row (even and odd kk) keep four dependency chains in flight.
+// directions are loaded before any arithmetic (32 loads in flight per thread), the next
+// eight while the current ones are used (the sum is a chain over kk, so each batch would
+// otherwise wait for its loads), and two interleaved chains per row (even and odd kk)
+// keep four dependency chains in flight.
 constexpr int kQB = 8;
+__device__ __forceinline__ void qsub_load(const float* Qh, const float* Ql, int64_t len, int k, int k0,
+                                          int64_t ia, int64_t ibb, float* ha, float* la, float* hb, float* lb) {
+#pragma unroll
+    for (int u = 0; u < kQB; ++u) {
+        const int64_t o = (int64_t)min(k0 + u, k - 1) * len;   // past k: a valid row, not used
+        ha[u] = Qh[o + ia];
+        la[u] = Ql[o + ia];
+        hb[u] = Qh[o + ibb];
+        lb[u] = Ql[o + ibb];
+    }
+}
 __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int64_t len, int k,
                                           const df64* s, int64_t ia, int64_t ib, bool vb,
                                           df64& acc_a, df64& acc_b) {
     df64 a1{0.f, 0.f}, b1{0.f, 0.f};
     const int64_t ibb = vb ? ib : ia;
+    float ha[kQB], la[kQB], hb[kQB], lb[kQB];
+    qsub_load(Qh, Ql, len, k, 0, ia, ibb, ha, la, hb, lb);
     for (int k0 = 0; k0 < k; k0 += kQB) {
-        float ha[kQB], la[kQB], hb[kQB], lb[kQB];
-#pragma unroll
-        for (int u = 0; u < kQB; ++u) {
-            const int64_t o = (int64_t)min(k0 + u, k - 1) * len;
-            ha[u] = Qh[o + ia];
-            la[u] = Ql[o + ia];
-            hb[u] = Qh[o + ibb];
-            lb[u] = Ql[o + ibb];
-        }
+        float nha[kQB], nla[kQB], nhb[kQB], nlb[kQB];
+        if (k0 + kQB < k) qsub_load(Qh, Ql, len, k, k0 + kQB, ia, ibb, nha, nla, nhb, nlb);
 #pragma unroll
         for (int u = 0; u < kQB; u += 2) {
             const df64 s0 = k0 + u < k ? s[k0 + u] : df64{0.f, 0.f};
@@ -305,6 +316,13 @@ __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int6
             acc_b = df_sub(acc_b, df_mul(df64{hb[u], lb[u]}, s0));
             a1 = df_sub(a1, df_mul(df64{ha[u + 1], la[u + 1]}, s1));
             b1 = df_sub(b1, df_mul(df64{hb[u + 1], lb[u + 1]}, s1));
+        }
+#pragma unroll
+        for (int u = 0; u < kQB; ++u) {
+            ha[u] = nha[u];
+            la[u] = nla[u];
+            hb[u] = nhb[u];
+            lb[u] = nlb[u];
         }
     }
     acc_a = df_add(acc_a, a1);
@@ -315,7 +333,7 @@ __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int6
 // squared norms (t = -1). Picks index k = t + 1; with `build`, also forms q_k.
 // Cooperative launch; grid G <= co-resident CTAs, block 256.
 template <typename TA>
-__global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) {
+__global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, int build) {
     using PT = PartT<TA>;
     __shared__ double s_w[128];
     __shared__ PT s_q[4][64];
@@ -334,11 +352,11 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
     double fs = 0.0;
     int bad = 0;
     {
-        const int lane64 = tid & 63, q4 = tid >> 6;   // 64 columns x 4 quarter-sums per pass
+        const int lane64 = tid & 63, q4 = tid >> 6;   // 64 columns x 4 quarter-sums per pass (first 256 threads)
         for (int64_t jb = j0; jb < j1; jb += 64) {
             const int64_t j = jb + lane64;
             PT w0 = part_zero(PT{}), w1 = part_zero(PT{});
-            if (j < j1) {
+            if (j < j1 && q4 < 4) {
                 const int rc0 = P.RC * q4 / 4, rc1 = P.RC * (q4 + 1) / 4;
                 const PT* src = part + j;
                 int rc = rc0;
@@ -348,7 +366,7 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
                 }
                 if (rc < rc1) w0 = part_add(w0, src[(int64_t)rc * P.nsel]);
             }
-            s_q[q4][lane64] = part_add(w0, w1);
+            if (q4 < 4) s_q[q4][lane64] = part_add(w0, w1);
             __syncthreads();
             if (q4 == 0 && j < j1) {
                 const PT w = part_add(part_add(s_q[0][lane64], s_q[1][lane64]),
@@ -419,7 +437,7 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
         float* vl = vh + len;
         df64* red1 = reinterpret_cast<df64*>(P.red1);
         __shared__ df64 s_df[128];
-        __shared__ df64 s_wred[8];
+        __shared__ df64 s_wred[kPivotThreads / 32];
         for (int kk = tid; kk < k; kk += nt) s_df[kk] = W[(int64_t)kk * P.nsel + p];
         __syncthreads();
         // P1b: v = a_p - Q W(:,p), two rows per thread
@@ -443,15 +461,21 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
             const float* qh1 = Qh + (int64_t)(two ? kk + 1 : kk) * len;
             const float* ql1 = Ql + (int64_t)(two ? kk + 1 : kk) * len;
             df64 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
-            for (int64_t i = i0 + lane; i < i1; i += 128) {
-                float xh[4], xl[4], ph[4], pl[4], qh_[4], ql_[4];
+            // four rows per lane and step; the next step's loads issue before this step's sums
+            float xh[4], xl[4], ph[4], pl[4], qh_[4], ql_[4];
+            auto dload = [&](int64_t i, float* xh_, float* xl_, float* ph_, float* pl_, float* qa, float* qb) {
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int64_t ii = i + 32 * u < i1 ? i + 32 * u : i;
-                    xh[u] = vh[ii]; xl[u] = vl[ii];
-                    ph[u] = qh0[ii]; pl[u] = ql0[ii];
-                    qh_[u] = qh1[ii]; ql_[u] = ql1[ii];
+                    const int64_t ii = i + 32 * u < i1 ? i + 32 * u : (i < i1 ? i : i0);
+                    xh_[u] = vh[ii]; xl_[u] = vl[ii];
+                    ph_[u] = qh0[ii]; pl_[u] = ql0[ii];
+                    qa[u] = qh1[ii]; qb[u] = ql1[ii];
                 }
+            };
+            if (i0 + lane < i1) dload(i0 + lane, xh, xl, ph, pl, qh_, ql_);
+            for (int64_t i = i0 + lane; i < i1; i += 128) {
+                float nxh[4], nxl[4], nph[4], npl[4], nqh[4], nql[4];
+                if (i + 128 < i1) dload(i + 128, nxh, nxl, nph, npl, nqh, nql);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     if (i + 32 * u >= i1) break;
@@ -464,6 +488,12 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
                         b0 = df_add(b0, df_mul(df64{qh_[u], ql_[u]}, x));
                     }
                 }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    xh[u] = nxh[u]; xl[u] = nxl[u];
+                    ph[u] = nph[u]; pl[u] = npl[u];
+                    qh_[u] = nqh[u]; ql_[u] = nql[u];
+                }
             }
             const df64 acc0 = warp_sum_t(df_add(a0, a1));
             const df64 acc1 = warp_sum_t(df_add(b0, b1));
@@ -473,17 +503,33 @@ __global__ void __launch_bounds__(256) aca_pivot(AcaParams P, int t, int build) 
             }
         }
         if (!group_barrier(P.bar, 2u * G, P.status)) return;
-        // P2: second pass v -= Q (Q^T v); partial ||v||^2
-        for (int kk = warp; kk < k; kk += nw) {
-            df64 a0{0.f, 0.f}, a1{0.f, 0.f};
+        // P2: second pass v -= Q (Q^T v); partial ||v||^2. The CTAs' partial dots are
+        // summed per direction in a fixed order, two directions per warp at a time so that
+        // their loads are in flight together.
+        for (int kk = warp; kk < k; kk += 2 * nw) {
+            const int kb = kk + nw;
+            const bool hb = kb < k;
+            df64 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
             int gg = lane;
             for (; gg + 32 < G; gg += 64) {
-                a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
-                a1 = df_add(a1, red1[(int64_t)(gg + 32) * r + kk]);
+                const df64 x0 = red1[(int64_t)gg * r + kk], x1 = red1[(int64_t)(gg + 32) * r + kk];
+                const df64 y0 = hb ? red1[(int64_t)gg * r + kb] : df64{0.f, 0.f};
+                const df64 y1 = hb ? red1[(int64_t)(gg + 32) * r + kb] : df64{0.f, 0.f};
+                a0 = df_add(a0, x0);
+                a1 = df_add(a1, x1);
+                b0 = df_add(b0, y0);
+                b1 = df_add(b1, y1);
             }
-            if (gg < G) a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
-            const df64 sk = warp_sum_t(df_add(a0, a1));
-            if (lane == 0) s_df[kk] = sk;
+            if (gg < G) {
+                a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
+                if (hb) b0 = df_add(b0, red1[(int64_t)gg * r + kb]);
+            }
+            const df64 sa = warp_sum_t(df_add(a0, a1));
+            const df64 sb = warp_sum_t(df_add(b0, b1));
+            if (lane == 0) {
+                s_df[kk] = sa;
+                if (hb) s_df[kb] = sb;
+            }
         }
         __syncthreads();
         df64 nv{0.f, 0.f};
@@ -704,7 +750,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
         CUR_CK(cudaMemsetAsync(P.bar, 0, sizeof(unsigned), st));
         int build = (t + 1 < r - 1) ? 1 : 0;
         void* args[] = {&P, &t, &build};
-        CUR_TRY(launch_coop((const void*)aca_pivot<TA>, dim3(G), dim3(256), args, 0, st));
+        CUR_TRY(launch_coop((const void*)aca_pivot<TA>, dim3(G), dim3(kPivotThreads), args, 0, st));
         note_launch();
     }
     return CUR_OK;

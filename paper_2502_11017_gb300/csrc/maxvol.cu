@@ -201,8 +201,13 @@ __device__ __forceinline__ void rows_dot(const TB* rows, int ld, int nloc, int r
     }
 }
 
+// Threads of a block-start CTA: 16 warps for FP32/BF16 data (one row per thread for the
+// 512-row slices of the row stage), 8 for FP64 data (its FP64 row sums need the registers).
+template <typename TB> struct StartThreads { static constexpr int v = 512; };
+template <> struct StartThreads<double> { static constexpr int v = 256; };
+
 template <typename TB>
-__global__ void __launch_bounds__(256, 1) mv_start(MvArgs a) {
+__global__ void __launch_bounds__(StartThreads<TB>::v, 1) mv_start(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int slot = a.cta_base + blockIdx.x;
     const int pb = a.cta_prob[slot], part = a.cta_part[slot];
@@ -701,10 +706,26 @@ struct MinvKeeper<float> {
     // M^-1 <- M^-1 - (M^-1(:,j) / B_ij) (B(i,:) - e_j^T)
     __device__ void swap_update(int r, int jstar) {
         const int tid = threadIdx.x, nt = blockDim.x;
-        if (nt % r == 0) {   // one column per thread
+        if (nt % r == 0) {   // one column per thread, four rows at a time
             const int c = tid % r, di = nt / r;
             const df64 wv = c == jstar ? df_sub(brow[c], df64{1.f, 0.f}) : brow[c];
             int i = tid / r;
+            for (; i + 3 * di < r; i += 4 * di) {
+                df64 m[4], q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = (i + u * di) * r + c;
+                    m[u] = df64{Mh[e], Ml[e]};
+                    q[u] = cj[i + u * di];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = (i + u * di) * r + c;
+                    const df64 mv = df_sub(m[u], df_mul(q[u], wv));
+                    Mh[e] = mv.h;
+                    Ml[e] = mv.l;
+                }
+            }
             for (; i < r; i += di) {
                 const int e = i * r + c;
                 const df64 mv = df_sub(df64{Mh[e], Ml[e]}, df_mul(cj[i], wv));
@@ -1165,7 +1186,24 @@ __global__ void __launch_bounds__(kSoloThreads, 1) mv_engine(MvArgs a) {
                     const TB wc = c == jstar ? wrow[c] - (TB)1 : wrow[c];
                     int i = tid / r, id = (lo + i) * r + c;
                     TB* bp = Bs + (size_t)i * r + c;
-                    for (; i < nloc; i += di, id += di * r, bp += (size_t)di * r) {
+                    const size_t step = (size_t)di * r;
+                    // four rows at a time: their loads issue before the arithmetic
+                    for (; i + 3 * di < nloc; i += 4 * di, id += 4 * di * r, bp += 4 * step) {
+                        const TB c0 = colj[i], c1 = colj[i + di], c2 = colj[i + 2 * di], c3 = colj[i + 3 * di];
+                        const TB b0 = bp[0], b1 = bp[step], b2 = bp[2 * step], b3 = bp[3 * step];
+                        const TB x0 = fma(-c0, wc, b0), x1 = fma(-c1, wc, b1), x2 = fma(-c2, wc, b2), x3 = fma(-c3, wc, b3);
+                        bp[0] = x0;
+                        bp[step] = x1;
+                        bp[2 * step] = x2;
+                        bp[3 * step] = x3;
+                        const TB a0 = fabs(x0), a1 = fabs(x1), a2 = fabs(x2), a3 = fabs(x3);
+                        bad |= !(a0 <= (TB)INFINITY) | !(a1 <= (TB)INFINITY) | !(a2 <= (TB)INFINITY) | !(a3 <= (TB)INFINITY);
+                        if (a0 > v) { v = a0; idx = id; }
+                        if (a1 > v) { v = a1; idx = id + di * r; }
+                        if (a2 > v) { v = a2; idx = id + 2 * di * r; }
+                        if (a3 > v) { v = a3; idx = id + 3 * di * r; }
+                    }
+                    for (; i < nloc; i += di, id += di * r, bp += step) {
                         const TB x = fma(-colj[i], wc, *bp);
                         *bp = x;
                         const TB ax = fabs(x);
@@ -1674,7 +1712,7 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
     CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_eng, mv_engine<TB>, 256, sm_eng));
     if (aca_start) {
         CUR_TRY(set_smem_attr(mv_start<TB>, sm_start));
-        CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_start, mv_start<TB>, 256, sm_start));
+        CUR_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_start, mv_start<TB>, StartThreads<TB>::v, sm_start));
     }
     const int cap_eng = std::max(1, occ_eng) * h->num_sms;
     const int cap_start = std::max(1, occ_start) * h->num_sms;
@@ -1700,13 +1738,13 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
             MvArgs aw = a;
             aw.cta_base = w.first;
             void* args[] = {&aw};
-            CUR_TRY(launch_coop((const void*)mv_start<TB>, dim3(w.second), dim3(256), args, sm_start, st));
+            CUR_TRY(launch_coop((const void*)mv_start<TB>, dim3(w.second), dim3(StartThreads<TB>::v), args, sm_start, st));
             note_launch();
         }
         if (solo_slots > 0) {
             MvArgs aw = a;
             aw.cta_base = sg.coop_slots;
-            mv_start<TB><<<solo_slots, 256, sm_start, st>>>(aw);
+            mv_start<TB><<<solo_slots, StartThreads<TB>::v, sm_start, st>>>(aw);
             CUR_CK(cudaGetLastError());
             note_launch();
         }
