@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <array>
 #include <climits>
+#include <initializer_list>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -1459,7 +1460,7 @@ struct __align__(16) Blob {
 // 16-byte words where the destination allows (every table is 16-byte aligned in the arena),
 // so a 30 KB parameter takes ~2000 reads instead of 30000.
 template <int N>
-__global__ void blob_k(const Blob<N> b) {
+__global__ void blob_k(const __grid_constant__ Blob<N> b) {
     const int nw = ((uintptr_t)b.dst % 16 == 0) ? b.bytes / 16 : 0;
     const uint4* src = reinterpret_cast<const uint4*>(b.data);
     uint4* dst = reinterpret_cast<uint4*>(b.dst);
@@ -1485,6 +1486,67 @@ static cur_status upload(void* dst, const void* src, size_t bytes, cudaStream_t 
     const unsigned char* s = static_cast<const unsigned char*>(src);
     if (bytes <= 2048) return upload_n<2048>(d, s, bytes, st);
     return upload_n<30720>(d, s, bytes, st);
+}
+
+// Several small tables in one launch: segment q goes to dst[q] from data + off[q] (offsets
+// 16-byte aligned, so 16-byte words wherever the destination is aligned too).
+constexpr int kUpSegs = 6;
+template <int N>
+struct __align__(16) BlobM {
+    unsigned char* dst[kUpSegs];
+    int off[kUpSegs];
+    int bytes[kUpSegs];
+    int nseg;
+    int pad[3];
+    unsigned char data[N];
+};
+template <int N>
+__global__ void blobm_k(const __grid_constant__ BlobM<N> b) {
+    for (int q = 0; q < b.nseg; ++q) {
+        const int nw = ((uintptr_t)b.dst[q] % 16 == 0) ? b.bytes[q] / 16 : 0;
+        const uint4* src = reinterpret_cast<const uint4*>(b.data + b.off[q]);
+        uint4* dst = reinterpret_cast<uint4*>(b.dst[q]);
+        for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+        for (int i = 16 * nw + threadIdx.x; i < b.bytes[q]; i += blockDim.x) b.dst[q][i] = b.data[b.off[q] + i];
+    }
+}
+struct UpSeg {
+    void* dst;
+    const void* src;
+    size_t bytes;
+};
+template <int N>
+static cur_status upload_multi_n(const UpSeg* seg, int n, cudaStream_t st) {
+    BlobM<N> b;
+    b.nseg = n;
+    int off = 0;
+    for (int q = 0; q < n; ++q) {
+        b.dst[q] = static_cast<unsigned char*>(seg[q].dst);
+        b.off[q] = off;
+        b.bytes[q] = (int)seg[q].bytes;
+        std::memcpy(b.data + off, seg[q].src, seg[q].bytes);
+        off += (int)((seg[q].bytes + 15) / 16 * 16);
+    }
+    blobm_k<N><<<1, 256, 0, st>>>(b);
+    CUR_CK(cudaGetLastError());
+    note_launch();
+    return CUR_OK;
+}
+static cur_status upload_multi(std::initializer_list<UpSeg> segs, cudaStream_t st) {
+    UpSeg v[kUpSegs];
+    int n = 0;
+    size_t tot = 0;
+    for (const UpSeg& q : segs) {
+        if (q.bytes == 0) continue;
+        if (n == kUpSegs) return CUR_ERR_ARG;
+        v[n++] = q;
+        tot += (q.bytes + 15) / 16 * 16;
+    }
+    if (n == 0) return CUR_OK;
+    if (tot <= 2048) return upload_multi_n<2048>(v, n, st);
+    if (tot <= 30720) return upload_multi_n<30720>(v, n, st);
+    for (int q = 0; q < n; ++q) CUR_TRY(upload(v[q].dst, v[q].src, v[q].bytes, st));
+    return CUR_OK;
 }
 
 // Stages whose first B comes from the tensor-core product: FP32, r = 32 or 64, at least this
@@ -1633,10 +1695,10 @@ static cur_status stage_tables(Stage<TB>& sg, cudaStream_t st) {
             tab[sg.probs[pb].group0 + g] = pb;
             tab[slots + sg.probs[pb].group0 + g] = g;
         }
-    CUR_TRY(upload(sg.dprob, sg.probs.data(), sizeof(MvProb) * P, st));
-    CUR_TRY(upload(sg.dtab, tab.data(), sizeof(int32_t) * tab.size(), st));
-    if (sg.bpre) CUR_TRY(upload(sg.dtiles, sg.tiles.data(), sizeof(CoefTile) * sg.tiles.size(), st));
-    return CUR_OK;
+    return upload_multi({{sg.dprob, sg.probs.data(), sizeof(MvProb) * P},
+                         {sg.dtab, tab.data(), sizeof(int32_t) * tab.size()},
+                         {sg.dtiles, sg.tiles.data(), sg.bpre ? sizeof(CoefTile) * sg.tiles.size() : 0}},
+                        st);
 }
 
 // Per-problem defaults: factorise (lu_mask 1), not done (or all done while *idle != 0),
@@ -1789,8 +1851,8 @@ static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opt
         lm[pb] = lu_mask.empty() ? 1 : lu_mask[pb];
         dn[pb] = (!skip.empty() && skip[pb]) ? 1 : 0;
     }
-    CUR_TRY(upload(sg.dtab + 2 * sg.slots, lm.data(), sizeof(int32_t) * P, st));
-    CUR_TRY(upload(sg.done, dn.data(), sizeof(int32_t) * P, st));
+    CUR_TRY(upload_multi({{sg.dtab + 2 * sg.slots, lm.data(), sizeof(int32_t) * P},
+                          {sg.done, dn.data(), sizeof(int32_t) * P}}, st));
     CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
     CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
     return stage_launch<TB>(h, basis, r, o, sg, aca_start, st);
