@@ -169,7 +169,7 @@ struct StartSmem {
         size_t b = (size_t)nloc * start_ld(r) * sizeof(TB);
         b = (b + 15) / 16 * 16 + (size_t)nloc * sizeof(double);
         b += (size_t)r * r * sizeof(double);        // Q (FP64 data) or the projector P
-        b += (size_t)6 * r * sizeof(double);        // v, sd, partial sums (4 r)
+        b += (size_t)10 * r * sizeof(double);       // v, sd, partial sums (8 r)
         b += (size_t)2 * r * sizeof(float);         // qh, ql
         b += (size_t)nloc + 16;                     // mask
         return b;
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(StartThreads<TB>::v, 1) mv_start(MvArgs a) {
     double* Q = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * r * sizeof(double);
     double* v = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * sizeof(double);
     double* sd = reinterpret_cast<double*>(smem_raw + off); off += (size_t)r * sizeof(double);
-    double* red = reinterpret_cast<double*>(smem_raw + off); off += (size_t)4 * r * sizeof(double);
+    double* red = reinterpret_cast<double*>(smem_raw + off); off += (size_t)8 * r * sizeof(double);
     float* qh = reinterpret_cast<float*>(smem_raw + off); off += (size_t)r * sizeof(float);
     float* ql = reinterpret_cast<float*>(smem_raw + off); off += (size_t)r * sizeof(float);
     unsigned char* msk = smem_raw + off;
@@ -346,21 +346,42 @@ __global__ void __launch_bounds__(StartThreads<TB>::v, 1) mv_start(MvArgs a) {
             for (int c = tid; c < r; c += nt) vd[c] = df64{to_f(cp[c]), 0.f};
             __syncthreads();
             for (int pass = 0; pass < 2 && k > 0; ++pass) {
-                for (int it = tid; it < 4 * r; it += nt) {
-                    const int c = it % r, qt = it / r;
-                    df64 s0{0.f, 0.f}, s1{0.f, 0.f};
-                    const int d0 = r * qt / 4, d1 = r * (qt + 1) / 4;
-                    int d = d0;
-                    for (; d + 1 < d1; d += 2) {   // P symmetric: column c read as row c
-                        s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
-                        s1 = df_add(s1, df_mul(Pd[(d + 1) * r + c], vd[d + 1]));
+                // quarter qt of the rows of P for column c, as two interleaved chains (even and
+                // odd d); with 8 r threads or more each chain has its own thread
+                if (nt >= 8 * r) {
+                    df64* half = redd + 4 * r;   // the odd chains
+                    for (int it = tid; it < 8 * r; it += nt) {
+                        const int c = it % r, qt = (it / r) & 3, odd = it / (4 * r);
+                        const int d0 = r * qt / 4, d1 = r * (qt + 1) / 4;
+                        df64 sx{0.f, 0.f};
+                        for (int d = d0 + odd; d < d1; d += 2)   // P symmetric: column c read as row c
+                            sx = df_add(sx, df_mul(Pd[d * r + c], vd[d]));
+                        (odd ? half : redd)[qt * r + c] = sx;
                     }
-                    if (d < d1) s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
-                    redd[qt * r + c] = df_add(s0, s1);
+                    __syncthreads();
+                    for (int c = tid; c < r; c += nt) {
+                        df64 q[4];
+#pragma unroll
+                        for (int qt = 0; qt < 4; ++qt) q[qt] = df_add(redd[qt * r + c], half[qt * r + c]);
+                        vd[c] = df_add(df_add(q[0], q[1]), df_add(q[2], q[3]));
+                    }
+                } else {
+                    for (int it = tid; it < 4 * r; it += nt) {
+                        const int c = it % r, qt = it / r;
+                        df64 s0{0.f, 0.f}, s1{0.f, 0.f};
+                        const int d0 = r * qt / 4, d1 = r * (qt + 1) / 4;
+                        int d = d0;
+                        for (; d + 1 < d1; d += 2) {   // P symmetric: column c read as row c
+                            s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
+                            s1 = df_add(s1, df_mul(Pd[(d + 1) * r + c], vd[d + 1]));
+                        }
+                        if (d < d1) s0 = df_add(s0, df_mul(Pd[d * r + c], vd[d]));
+                        redd[qt * r + c] = df_add(s0, s1);
+                    }
+                    __syncthreads();
+                    for (int c = tid; c < r; c += nt)
+                        vd[c] = df_add(df_add(redd[c], redd[r + c]), df_add(redd[2 * r + c], redd[3 * r + c]));
                 }
-                __syncthreads();
-                for (int c = tid; c < r; c += nt)
-                    vd[c] = df_add(df_add(redd[c], redd[r + c]), df_add(redd[2 * r + c], redd[3 * r + c]));
                 __syncthreads();
             }
             if (warp == 0) {
@@ -395,9 +416,15 @@ __global__ void __launch_bounds__(StartThreads<TB>::v, 1) mv_start(MvArgs a) {
                 ql[c] = q.l;
             }
             __syncthreads();
-            for (int e = tid; e < r * r; e += nt) {   // P -= q q^T
-                const int i = e / r, c = e - i * r;
-                Pd[e] = df_sub(Pd[e], df_mul(vd[i], vd[c]));
+            if (nt % r == 0) {   // P -= q q^T, one column per thread
+                const int c = tid % r, di = nt / r;
+                const df64 qc = vd[c];
+                for (int i = tid / r; i < r; i += di) Pd[i * r + c] = df_sub(Pd[i * r + c], df_mul(vd[i], qc));
+            } else {
+                for (int e = tid; e < r * r; e += nt) {   // P -= q q^T
+                    const int i = e / r, c = e - i * r;
+                    Pd[e] = df_sub(Pd[e], df_mul(vd[i], vd[c]));
+                }
             }
             __syncthreads();
         }
