@@ -243,6 +243,7 @@ size_t cur_batch_workspace_size(const cur_batch_item* items, int32_t count) {
         b += 512;
     }
     b += (size_t)std::min(count, 512) * 2 * 64 * 4096 * sizeof(float);   // Algorithm 3's Q slices
+    b += (size_t)std::min(count, 512) * 64 * 1024 * sizeof(double);      // and its W slices
     return b;
 }
 

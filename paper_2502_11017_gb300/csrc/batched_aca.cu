@@ -6,10 +6,13 @@
 // synchronisation. The rounds are those of the full-matrix kernels (the implicit
 // residual nu_j = ||a_j||^2 - sum_k (q_k^T a_j)^2, one read of the matrix per round):
 //   pass   : w_j = a_j^T q_t for every column (Dot2 with q as FP32 hi/lo pairs), the
-//            512 threads split into 2 row groups x 256 four-column groups; two CTAs
+//            512 threads split into n/4 four-column groups x as many row groups as fit
+//            (2 for n = 1024, 16 for n = 128), every thread streaming; two CTAs
 //            per SM, so one streams its matrix while the other runs its pivot step
 //   pick   : nu_j -= w_j^2, masked argmax (lowest index on ties)
-//   vector : v = a_p orthogonalised twice against q_1..q_t (double-float), the early stop
+//   vector : v = a_p - Q W(:,p) with W = the passes' q^T a (the first Gram-Schmidt sweep
+//            needs no Q^T a_p of its own), orthogonalised once more against q_1..q_t
+//            (double-float), the early stop
 //            on the recomputed ||v||^2 <= (max(m,n) eps ||A||_F)^2, q = v / ||v||
 // Q lives in the CTA's slice of the workspace (r x m hi and lo floats); everything else
 // in shared memory. Supports FP32 data, r <= 64, m <= 4096, n <= 1024.
@@ -24,7 +27,7 @@
 namespace curk {
 
 constexpr int kBA_T = 512;      // threads per CTA (two CTAs per SM: one streams while the other pivots)
-constexpr int kBA_RG = kBA_T / 256;   // row groups of the pass
+constexpr int kBA_RG = kBA_T / 256;   // partial-sum rows per column in shared memory: RG n <= kBA_RG kBA_MaxN
 constexpr int kBA_MaxM = 4096;
 constexpr int kBA_MaxN = 1024;
 constexpr int kBA_MaxR = 64;
@@ -117,6 +120,9 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
     const int tid = threadIdx.x;
     float* Qh = Qws + (int64_t)blockIdx.x * 2 * kBA_MaxR * kBA_MaxM;
     float* Ql = Qh + (int64_t)kBA_MaxR * kBA_MaxM;
+    // W(t, j) = q_t^T a_j from the passes (the CTA's slice after all CTAs' Q slices)
+    df64* W = reinterpret_cast<df64*>(Qws + (int64_t)gridDim.x * 2 * kBA_MaxR * kBA_MaxM) +
+              (int64_t)blockIdx.x * kBA_MaxR * kBA_MaxN;
 
     while (true) {
         if (tid == 0) s_next = atomicAdd(queue, 1);
@@ -130,20 +136,25 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
         const int64_t m = b.m, n = b.n, ld = b.ld;
         const int r = b.r;
         const bool vec = (n % 4 == 0) && (ld % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-        const int cg = tid & 255, rg = tid >> 8;        // column group (4 columns), row group
+        // column groups of 4 columns; as many row groups as the CTA's threads cover, so every
+        // thread streams (a narrow matrix would otherwise leave most of them idle)
+        const int cgn = (int)((n + 3) / 4);
+        const int RG = max(1, min((int)blockDim.x / cgn, (int)(kBA_RG * kBA_MaxN / n)));
+        const int cg = tid % cgn, rg = tid / cgn;
+        const bool active = rg < RG;
         for (int j = tid; j < n; j += blockDim.x) mask[j] = 0;
         int picked = 0, bad = 0;
         for (int t = -1; t < r - 1; ++t) {
             // ---- pass: squared norms (t = -1) or w = A^T q_t
             const int64_t c0 = 4 * (int64_t)cg;
             Dot2 acc[4];
-            if (c0 < n) {
+            if (active && c0 < n) {
                 // four rows loaded before they are folded: 64 bytes in flight per thread
-                for (int64_t i0 = rg; i0 < m; i0 += 4 * kBA_RG) {
+                for (int64_t i0 = rg; i0 < m; i0 += 4 * RG) {
                     float x[4][4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int64_t i = i0 + kBA_RG * u;
+                        const int64_t i = i0 + RG * u;
                         const float* row = A + (i < m ? i : i0) * ld + c0;
                         if (vec) {
                             const float4 y = __ldcs(reinterpret_cast<const float4*>(row));
@@ -155,7 +166,7 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
-                        const int64_t i = i0 + kBA_RG * u;
+                        const int64_t i = i0 + RG * u;
                         if (i >= m) break;
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
@@ -164,10 +175,10 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
                     }
                 }
             }
-            if (c0 < n)
+            if (active && c0 < n)
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    if (c0 + c < n) part[rg * kBA_MaxN + c0 + c] = fast_two_sum(acc[c].s, acc[c].c);
+                    if (c0 + c < n) part[rg * n + c0 + c] = fast_two_sum(acc[c].s, acc[c].c);
             __syncthreads();
             // ---- pick
             unsigned long long bk = dkey(-INFINITY);
@@ -175,8 +186,7 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
             double fs = 0.0;
             for (int j = tid; j < n; j += blockDim.x) {
                 df64 w = part[j];
-#pragma unroll
-                for (int g = 1; g < kBA_RG; ++g) w = df_add(w, part[g * kBA_MaxN + j]);
+                for (int g = 1; g < RG; ++g) w = df_add(w, part[g * n + j]);
                 const double wd = df_to_d(w);
                 double nuj;
                 if (t < 0) {
@@ -185,6 +195,7 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
                     if (!isfinite(wd)) bad = 1;
                 } else {
                     nuj = nu[j] - wd * wd;
+                    W[(int64_t)t * n + j] = w;
                 }
                 nu[j] = nuj;
                 const unsigned long long kj = dkey(nuj);
@@ -202,11 +213,22 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
             }
             if (bi == INT_MAX) break;
             const int p = bi;
-            // ---- vector: v = a_p, orthogonalised twice against q_1 .. q_k
+            // ---- vector: v = a_p - Q W(:,p) (the first projection's coefficients q^T a_p are
+            // the passes' w, as in the full-matrix kernel), then orthogonalised once more
             const int k = t + 1;
-            for (int64_t i = tid; i < m; i += blockDim.x) v[i] = df64{A[i * ld + p], 0.f};
+            for (int kk = tid; kk < k; kk += blockDim.x) qs[kk] = W[(int64_t)kk * n + p];
             __syncthreads();
-            bat_project(Qh, Ql, m, k, v, qs);
+            for (int64_t i = tid; i < m; i += blockDim.x) {
+                df64 a0{A[i * ld + p], 0.f}, a1{0.f, 0.f};
+                int kk = 0;
+                for (; kk + 1 < k; kk += 2) {
+                    a0 = df_sub(a0, df_mul(df64{Qh[(int64_t)kk * m + i], Ql[(int64_t)kk * m + i]}, qs[kk]));
+                    a1 = df_sub(a1, df_mul(df64{Qh[(int64_t)(kk + 1) * m + i], Ql[(int64_t)(kk + 1) * m + i]}, qs[kk + 1]));
+                }
+                if (kk < k) a0 = df_sub(a0, df_mul(df64{Qh[(int64_t)kk * m + i], Ql[(int64_t)kk * m + i]}, qs[kk]));
+                v[i] = df_add(a0, a1);
+            }
+            __syncthreads();
             bat_project(Qh, Ql, m, k, v, qs);
             df64 nv{0.f, 0.f};
             for (int64_t i = tid; i < m; i += blockDim.x) nv = df_add(nv, df_mul(v[i], v[i]));
@@ -240,7 +262,8 @@ __global__ void __launch_bounds__(kBA_T, 2) bat_aca_k(const float* __restrict__ 
 }  // namespace curk
 
 size_t bat_aca_workspace(int grid) {
-    return (size_t)grid * 2 * curk::kBA_MaxR * curk::kBA_MaxM * sizeof(float);
+    return (size_t)grid * 2 * curk::kBA_MaxR * curk::kBA_MaxM * sizeof(float) +
+           (size_t)grid * curk::kBA_MaxR * curk::kBA_MaxN * sizeof(double);
 }
 
 cur_status bat_aca_launch(const float* data, const void* items_dev, const int32_t* order, int* queue, int count,
