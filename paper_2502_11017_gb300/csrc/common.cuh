@@ -281,60 +281,57 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 // of shared memory. Returns 1 if singular (A then holds no inverse).
 __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
                                           double thresh, double* logabsdet) {
-    __shared__ int s_p, s_sing;
+    __shared__ int s_sing;
     __shared__ double s_dinv;
-    __shared__ LogAcc s_lacc;   // log|det| without a logarithm per step
-    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ double s_prow[128];   // the step's pivot row, scaled (r <= 128)
+    __shared__ LogAcc s_lacc;        // log|det| without a logarithm per step
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     if (tid == 0) { s_sing = 0; s_lacc.init(); }
     __syncthreads();
     for (int k = 0; k < r; ++k) {
+        // One warp: the pivot (first maximum |a_ik|, compared as integer keys), the row
+        // interchange, the pivot's test and reciprocal (one FP64 division), the column k
+        // and the scaled pivot row.
         if (tid < 32) {
-            // first maximum |a_ik|, compared as integer keys (no FP64 comparisons)
             unsigned long long bk = 0ull;
             long long bi = k;
-            for (int i = k + tid; i < r; i += 32) {
+            for (int i = k + lane; i < r; i += 32) {
                 const unsigned long long x = dkey(fabs(A[i * r + k]));
                 if (x > bk) { bk = x; bi = i; }
             }
             warp_argmax_key(bk, bi);
-            if (tid == 0) s_p = (int)bi;
-        }
-        __syncthreads();
-        const int p = s_p;
-        if (p != k)
-            for (int j = tid; j < r; j += nt) {
-                const double t = A[k * r + j];
-                A[k * r + j] = A[p * r + j];
-                A[p * r + j] = t;
+            const int p = (int)bi;
+            if (p != k)
+                for (int j = lane; j < r; j += 32) {
+                    const double t = A[k * r + j];
+                    A[k * r + j] = A[p * r + j];
+                    A[p * r + j] = t;
+                }
+            __syncwarp();
+            if (lane == 0) {
+                piv[k] = p;
+                const double d = A[k * r + k];
+                if (!(fabs(d) > thresh)) s_sing = 1;
+                else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }
             }
-        __syncthreads();
-        if (tid == 0) {
-            piv[k] = p;
-            const double d = A[k * r + k];
-            if (!(fabs(d) > thresh)) s_sing = 1;
-            else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }   // one FP64 division, not one per thread
+            __syncwarp();
+            if (!s_sing) {
+                const double dinv = s_dinv;
+                for (int i = lane; i < r; i += 32) colk[i] = A[i * r + k];
+                for (int c = lane; c < r; c += 32) s_prow[c] = (c == k ? 1.0 : A[k * r + c]) * dinv;
+            }
         }
         __syncthreads();
         if (s_sing) return 1;
-        const double dinv = s_dinv;
-        for (int i = tid; i < r; i += nt) {
-            colk[i] = A[i * r + k];
-            if (i != k) A[i * r + k] = 0.0;
-        }
-        __syncthreads();
-        if (tid == 0) A[k * r + k] = 1.0;
-        __syncthreads();
-        for (int j = tid; j < r; j += nt) A[k * r + j] *= dinv;
-        __syncthreads();
         if (nt % r == 0) {   // one column per thread: its pivot-row entry is read once
             const int c = tid % r, di = nt / r;
-            const double akc = A[k * r + c];
+            const double akc = s_prow[c];
             for (int i = tid / r; i < r; i += di)
-                if (i != k) A[i * r + c] = fma(-colk[i], akc, A[i * r + c]);
+                A[i * r + c] = i == k ? akc : fma(-colk[i], akc, c == k ? 0.0 : A[i * r + c]);
         } else {
             Walk2 w(tid, nt, r);
             for (int e = tid; e < r * r; e += nt, w.next())
-                if (w.i != k) A[e] = fma(-colk[w.i], A[k * r + w.c], A[e]);
+                A[e] = w.i == k ? s_prow[w.c] : fma(-colk[w.i], s_prow[w.c], w.c == k ? 0.0 : A[e]);
         }
         __syncthreads();
     }
