@@ -386,36 +386,49 @@ def run_ours(args):
     c_h = torch.empty(1, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 10))
     cs = torch.cuda.Stream(dev)
-    copied = [torch.cuda.Event() for _ in range(e2e_steps)]
-    done = [torch.cuda.Event() for _ in range(e2e_steps)]
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # the step captured once per device buffer: the same API calls, replayed
+    bgraphs = [capture(bufs[0]), capture(bufs[1])]
 
-    def fetch(k):
-        cs.wait_event(e0)
-        if k >= 2:
-            cs.wait_event(done[k - 2])
-        with torch.cuda.stream(cs):
-            bufs[k % 2].copy_(a_pin, non_blocking=True)
-        copied[k].record(cs)
+    def run_e2e(use_graph):
+        copied = [torch.cuda.Event() for _ in range(e2e_steps)]
+        done = [torch.cuda.Event() for _ in range(e2e_steps)]
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
 
-    barrier()
-    e0.record(stream)
-    fetch(0)
-    for k in range(e2e_steps):
-        if k + 1 < e2e_steps:
-            fetch(k + 1)
-        stream.wait_event(copied[k])
-        step(bufs[k % 2])
-        I_h.copy_(I, non_blocking=True)
-        J_h.copy_(J, non_blocking=True)
-        c_h.copy_(cheb, non_blocking=True)
-        done[k].record(stream)
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
+        def fetch(k):
+            cs.wait_event(e0)
+            if k >= 2:
+                cs.wait_event(done[k - 2])
+            with torch.cuda.stream(cs):
+                bufs[k % 2].copy_(a_pin, non_blocking=True)
+            copied[k].record(cs)
+
+        barrier()
+        e0.record(stream)
+        fetch(0)
+        for k in range(e2e_steps):
+            if k + 1 < e2e_steps:
+                fetch(k + 1)
+            stream.wait_event(copied[k])
+            if use_graph:
+                bgraphs[k % 2].replay()
+            else:
+                step(bufs[k % 2])
+            I_h.copy_(I, non_blocking=True)
+            J_h.copy_(J, non_blocking=True)
+            c_h.copy_(cheb, non_blocking=True)
+            done[k].record(stream)
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1)
+
+    e2e_eager_ms = run_e2e(False)
+    e2e_ms = run_e2e(True)
+    if cur.cur_sync_status(h) != cur.CUR_OK:
+        raise RuntimeError("device status in the end-to-end steps")
     _e2e_max, e2e_value = aggregate(e2e_ms, e2e_steps, world, dev)
+    _e2e_max, e2e_eager_value = aggregate(e2e_eager_ms, e2e_steps, world, dev)
 
     inf = cur.info_from_tensor(info)
     peaks, kind = measured_peaks()
@@ -448,7 +461,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
                     "h2d_bytes_per_step": m * n * 4, "d2h_bytes_per_step": 2 * r * 4 + 8,
                     "copy": "pinned host to device on a second stream, step k + 1's copy overlapping step k; "
-                    "each step's calls launched one by one (no graph)"},
+                    "each step's API calls replayed from a CUDA graph captured per device buffer",
+                    "eager_value": e2e_eager_value},
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "quality": {"logvol": inf.logvol, "sweeps": inf.sweeps, "swaps": inf.swaps_total,
