@@ -443,91 +443,7 @@ __global__ void __launch_bounds__(StartThreads<TB>::v, 1) mv_start(MvArgs a) {
     }
 }
 
-// ---------------------------------------------------------------- inverse of C(S,:)
-//
-// FP64 data: gj_inverse (FP64). FP32/BF16 data: the same Gauss-Jordan steps in double-float
-// (about 48 bits, on the FP32 pipes): the coefficients B are FP32 and the kept inverse is
-// double-float already, and an FP64 elimination of a 64 x 64 matrix on one SM is bound by
-// GB300's FP64 pipe (about 1/64 of the FP32 rate). Partial pivoting by rows (first maximum
-// |a_ik|, i >= k, compared exactly as double-float keys); |pivot| <= thresh flags a
-// numerically singular matrix as in the FP64 form; log|det| from the pivots.
-__device__ __forceinline__ unsigned long long df_abs_key(df64 x) {
-    if (x.h < 0.f) x = df_neg(x);
-    return ((unsigned long long)fkey(x.h) << 32) | fkey(x.l);
-}
-
-__device__ int gj_inverse_df(df64* A, int r, df64* colk, int* piv, double thresh, double* logabsdet) {
-    __shared__ int s_p, s_sing;
-    __shared__ df64 s_dinv;
-    __shared__ LogAcc s_lacc;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) { s_sing = 0; s_lacc.init(); }
-    __syncthreads();
-    for (int k = 0; k < r; ++k) {
-        if (tid < 32) {
-            unsigned long long bk = 0ull;
-            long long bi = k;
-            for (int i = k + tid; i < r; i += 32) {
-                const unsigned long long x = df_abs_key(A[i * r + k]);
-                if (x > bk) { bk = x; bi = i; }
-            }
-            warp_argmax_key(bk, bi);
-            if (tid == 0) s_p = (int)bi;
-        }
-        __syncthreads();
-        const int p = s_p;
-        if (p != k)
-            for (int j = tid; j < r; j += nt) {
-                const df64 t = A[k * r + j];
-                A[k * r + j] = A[p * r + j];
-                A[p * r + j] = t;
-            }
-        __syncthreads();
-        if (tid == 0) {
-            piv[k] = p;
-            const df64 d = A[k * r + k];
-            if (!(fabs(df_to_d(d)) > thresh)) s_sing = 1;
-            else { s_lacc.mul(d); s_dinv = df_div(df64{1.f, 0.f}, d); }
-        }
-        __syncthreads();
-        if (s_sing) return 1;
-        const df64 d = A[k * r + k], dinv = s_dinv;
-        // multipliers l_i = a_ik / a_kk (a row equal to the pivot row, or an exact multiple,
-        // then cancels to exact zeros, as in LU), rows i != k updated with the unscaled
-        // pivot row, then the pivot row scaled: the Gauss-Jordan step in the order of LU
-        for (int i = tid; i < r; i += nt) colk[i] = i == k ? dinv : df_div(A[i * r + k], d);
-        __syncthreads();
-        if (nt % r == 0) {   // one column per thread: its pivot-row entry is read once
-            const int c = tid % r, di = nt / r;
-            const df64 akc = A[k * r + c];
-            for (int i = tid / r; i < r; i += di) {
-                if (i == k) continue;
-                A[i * r + c] = c == k ? df_neg(colk[i]) : df_sub(A[i * r + c], df_mul(colk[i], akc));
-            }
-        } else {
-            Walk2 w(tid, nt, r);
-            for (int e = tid; e < r * r; e += nt, w.next()) {
-                if (w.i == k) continue;
-                A[e] = w.c == k ? df_neg(colk[w.i]) : df_sub(A[e], df_mul(colk[w.i], A[k * r + w.c]));
-            }
-        }
-        __syncthreads();
-        for (int j = tid; j < r; j += nt) A[k * r + j] = j == k ? dinv : df_mul(A[k * r + j], dinv);
-        __syncthreads();
-    }
-    for (int k = r - 1; k >= 0; --k) {
-        const int p = piv[k];
-        if (p != k)
-            for (int i = tid; i < r; i += nt) {
-                const df64 t = A[i * r + k];
-                A[i * r + k] = A[i * r + p];
-                A[i * r + p] = t;
-            }
-        __syncthreads();
-    }
-    if (logabsdet) *logabsdet = s_lacc.log_value();
-    return 0;
-}
+// ---------------------------------------------------------------- FP64 inverse of C(S,:)
 
 template <typename TB>
 __global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
@@ -542,7 +458,7 @@ __global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
     __shared__ double s_max;
     const TB* basis = static_cast<const TB*>(a.basis) + pr.boff;
     const int32_t* S = a.S + (int64_t)pb * rs;
-    // C(S,:) in FP64 (FP64 data) or as exact double-float pairs (FP32/BF16 data: no FP64 work)
+    // C(S,:) in FP64; its maximum magnitude in the data's type (no FP64 comparisons)
     using TS = typename std::conditional<std::is_same<TB, double>::value, double, float>::type;
     TS mx = 0;
     int bad = 0;
@@ -552,8 +468,7 @@ __global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
         TS x = 0;
         if (s < 0 || s >= pr.p) bad = 1; else x = (TS)basis[(int64_t)s * r + c];
         if (!isfinite(x)) bad = 2;
-        if constexpr (std::is_same<TB, double>::value) M[e] = x;
-        else reinterpret_cast<df64*>(M)[e] = df64{x, 0.f};
+        M[e] = (double)x;
         mx = fmax(mx, fabs(x));
     }
     bad = __syncthreads_or(bad);
@@ -578,17 +493,7 @@ __global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
         return;
     }
     double lv = 0.0;
-    int sing;
-    if constexpr (std::is_same<TB, double>::value) {
-        sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
-    } else {
-        df64* Md = reinterpret_cast<df64*>(M);
-        sing = gj_inverse_df(Md, r, reinterpret_cast<df64*>(colk), piv, (double)r * kEps * s_max, &lv);
-        if (!sing) {
-            for (int e = tid; e < r * r; e += nt) M[e] = df_to_d(Md[e]);
-            __syncthreads();
-        }
-    }
+    const int sing = gj_inverse(M, r, colk, piv, (double)r * kEps * s_max, &lv);
     if (sing) {
         if (tid == 0) { a.pstatus[pb] = CUR_ERR_SINGULAR; a.done[pb] = 1; a.logvol[pb] = -INFINITY; }
         return;
@@ -686,12 +591,6 @@ struct MinvKeeper<float> {
             const df64 v = df_from_d(Mg[e]);
             Mh[e] = v.h;
             Ml[e] = v.l;
-        }
-    }
-    __device__ void load_df(const df64* W, int r) {
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-            Mh[e] = W[e].h;
-            Ml[e] = W[e].l;
         }
     }
     __device__ void store(double* Mg, int r) const {
@@ -839,52 +738,21 @@ struct MinvKeeper<double> {
 template <typename TB>
 __device__ int engine_refactor(MinvKeeper<TB>& keep, const TB* basis, const int32_t* S, int r,
                                double* W, double* colk, int* piv, double* lv) {
-    if constexpr (std::is_same<TB, double>::value) {
-        double mx = 0.0;
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-            const int k = e / r, c = e - k * r;
-            const double x = basis[(int64_t)S[k] * r + c];
-            W[e] = x;
-            mx = fmax(mx, fabs(x));
-        }
-        mx = block_max(mx);
-        const int sing = gj_inverse(W, r, colk, piv, (double)r * kEps * mx, lv);
-        if (!sing) {
-            keep.load(W, r);
-            if (threadIdx.x == 0) keep.lacc.init();
-        }
-        __syncthreads();
-        return sing;
-    } else {
-        // double-float elimination (gj_inverse_df), straight into the keeper's two words
-        df64* Wd = reinterpret_cast<df64*>(W);
-        float mx = 0.f;
-        for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-            const int k = e / r, c = e - k * r;
-            const float x = basis[(int64_t)S[k] * r + c];
-            Wd[e] = df64{x, 0.f};
-            mx = fmaxf(mx, fabsf(x));
-        }
-        __shared__ float s_mx[32];
-        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            float t = 0.f;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, s_mx[w]);
-            s_mx[0] = t;
-        }
-        __syncthreads();
-        const double thresh = (double)r * kEps * (double)s_mx[0];
-        const int sing = gj_inverse_df(Wd, r, reinterpret_cast<df64*>(colk), piv, thresh, lv);
-        if (!sing) {
-            keep.load_df(Wd, r);
-            if (threadIdx.x == 0) keep.lacc.init();
-        }
-        __syncthreads();
-        return sing;
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+        const int k = e / r, c = e - k * r;
+        const double x = to_d(basis[(int64_t)S[k] * r + c]);
+        W[e] = x;
+        mx = fmax(mx, fabs(x));
     }
+    mx = block_max(mx);
+    const int sing = gj_inverse(W, r, colk, piv, (double)r * kEps * mx, lv);
+    if (!sing) {
+        keep.load(W, r);
+        if (threadIdx.x == 0) keep.lacc.init();
+    }
+    __syncthreads();
+    return sing;
 }
 
 // kappa_inf(M) = ||C(S,:)||_inf ||M^-1||_inf with the kept inverse (all threads call it).
