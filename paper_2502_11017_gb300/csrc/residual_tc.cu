@@ -4,24 +4,29 @@
 //
 // The product D = C W (m x n, K = r) runs as 3xTF32 on tcgen05.mma (kind::tf32):
 // C = Ch + Cl and W = Wh + Wl with Ch, Wh rounded to TF32 and Cl, Wl the rounded
-// remainders; D = Ch Wh + Ch Wl + Cl Wh keeps ~22 bits, i.e. FP32-level accuracy
-// (the dropped Cl Wl term is ~2^-22 relative). The MMA computes D^T tile by tile
-// (M = 128 columns of A, N = 128 rows, K = r) so that a TMEM lane is a column of A.
+// remainders; D = Ch Wh + Cl Wh + Ch Wl keeps ~22 bits, i.e. FP32-level accuracy
+// (the dropped Cl Wl term is ~2^-22 relative). Tile by tile (M = 128 rows of A,
+// N = 128 columns, K = r) the C panel is the MMA's A operand, read from tensor memory,
+// and the tile's W^T the B operand, read from shared memory; a TMEM lane is a row of A.
 //
-// Per CTA (persistent, one per SM, 608 threads):
-//   warp 0       TMA producer: the C panel (128 rows x r, hi and lo, resident while
-//                the CTA stays on the panel) and the tile's W^T (128 x r) as two
-//                buffers, hi (released after MMA passes 0 and 1) and lo (after pass 2),
-//                128-byte swizzled, K-major
-//   warp 1       MMA issuer (one thread): 3 passes x r/8 MMAs per tile into one of two
-//                TMEM accumulators (128 lanes x 128 FP32 columns each)
-//   warp 18      TMA producer of A: 32-row x 128-column sub-tiles (16 KB, unswizzled)
-//                into a ring of up to 8 slots (6 for r = 64), so A stays in flight
-//                while earlier ones are folded; A is read from HBM exactly once
-//   warps 2..17  epilogue: warp (sub-tile k, column quarter q) reads its 32 accumulator
-//                columns with tcgen05.ld, its column of the staged A rows from shared
-//                memory (conflict-free), and folds max|E|, sum E^2, sum A^2 with
-//                independent chains
+// Per CTA (persistent, one per SM, 608 threads; its tiles run along row panels):
+//   TMEM         two accumulators (128 columns each) and two C panels (hi in 64
+//                columns, lo in the next 64): the next panel is split and stored while
+//                the current one is in use
+//   warp 0       TMA producer of W^T (128 columns of A x r, hi and lo, 128-byte swizzle,
+//                K-major) into two stages, so the next tile's W loads during this one's MMAs
+//   warp 1       MMA issuer (one thread): 3 passes x r/8 MMAs per tile into one of the
+//                two accumulators
+//   warp 18      TMA producer of A: 32-row x 128-column sub-tiles (16 KB, four 32 x 32
+//                boxes with 128-byte swizzle) into a ring of up to 10 slots; A is read
+//                from HBM exactly once
+//   warps 2..17  epilogue: warp (lane quarter q, column group g) reads its 32 rows x 32
+//                accumulator columns with tcgen05.ld and the same block of A from shared
+//                memory (16-byte loads, conflict-free through the swizzle), and folds
+//                max|E|, sum E^2, sum A^2; the same warps split C rows into TF32 hi and
+//                lo and store them into TMEM with tcgen05.st when a panel begins
+// Out-of-range rows and columns read as zeros from every operand (TMA fill; zero C rows),
+// so E = 0 there and no element needs a mask.
 // Waits are bounded; on a timeout the CTA records CUR_ERR_TIMEOUT, waits (bounded) for
 // the copies and MMAs it issued, frees its TMEM and returns.
 
@@ -38,97 +43,141 @@
 
 namespace curk {
 
-constexpr int kTcBM = 128;            // rows of A per tile (MMA N)
-constexpr int kTcBN = 128;            // columns of A per tile (MMA M)
-constexpr int kChunk = 16384;         // one 128-row x 32-element FP32 swizzled chunk
+constexpr int kTcBM = 128;            // rows of A per tile (MMA M, TMEM lanes)
+constexpr int kTcBN = 128;            // columns of A per tile (MMA N)
+constexpr int kChunk = 16384;         // one 128-row x 32-element FP32 swizzled chunk of W^T
 
-// Wt[j][k] = (U R)(k, j), split into TF32 hi and lo, rows padded to ldk. One thread per
-// entry (k fastest, so the stores are coalesced); the r-term sum runs in double-float
-// (U converted once per CTA), i.e. on the FP32 pipes with ~48-bit accuracy.
+// Wt[j][k] = (U R)(k, j) = sum_l U(k, l) R(l, j), split into TF32 hi and lo, rows padded
+// to ldk. A block (256 threads) takes 2 * (256 / ceil(r/4)) columns j and every k: U (as
+// double-float, l-major) and the block's columns of R are staged in shared memory, and
+// each thread sums 4 k x 2 j entries over l in double-float (eight independent chains on
+// the FP32 pipes, ~48-bit accuracy).
+__host__ __device__ constexpr int prep_w_cols(int r) { return 2 * (256 / ((r + 3) / 4)); }
+__host__ __device__ constexpr size_t prep_w_smem(int r) {
+    return (size_t)r * (4 * ((r + 3) / 4)) * sizeof(df64) + (size_t)r * prep_w_cols(r) * sizeof(float);
+}
 template <typename TA>
 __global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, const TA* __restrict__ R,
                                                  int r, int64_t n, int ldk, float* __restrict__ Wh,
                                                  float* __restrict__ Wl) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    df64* Ut = reinterpret_cast<df64*>(smem_raw);   // U^T: lanes with consecutive k read consecutive words
-    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-        const int k = e / r, l = e - k * r;
-        Ut[l * r + k] = df_from_d(U[e]);
+    const int kgn = (r + 3) >> 2, kp = 4 * kgn, jt = prep_w_cols(r);
+    df64* Us = reinterpret_cast<df64*>(smem_raw);                      // Us[l * kp + k] = U(k, l)
+    float* Rs = reinterpret_cast<float*>(Us + (size_t)r * kp);          // Rs[l * jt + jj] = R(l, j0 + jj)
+    const int64_t j0 = (int64_t)blockIdx.x * jt;
+    for (int e = threadIdx.x; e < r * kp; e += blockDim.x) {
+        const int l = e / kp, k = e - l * kp;
+        Us[e] = k < r ? df_from_d(U[(int64_t)k * r + l]) : df64{0.f, 0.f};
+    }
+    for (int e = threadIdx.x; e < r * jt; e += blockDim.x) {
+        const int l = e / jt, jj = e - l * jt;
+        Rs[e] = j0 + jj < n ? to_f(R[(int64_t)l * n + j0 + jj]) : 0.f;
     }
     __syncthreads();
-    const int64_t total = n * ldk;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / ldk;
-        const int k = (int)(e - j * ldk);
-        float hi = 0.f, lo = 0.f;
-        if (k < r) {
-            df64 s0{0.f, 0.f}, s1{0.f, 0.f};
-            int l = 0;
-            for (; l + 1 < r; l += 2) {
-                s0 = df_add(s0, df_mul_f(Ut[l * r + k], to_f(R[(int64_t)l * n + j])));
-                s1 = df_add(s1, df_mul_f(Ut[(l + 1) * r + k], to_f(R[(int64_t)(l + 1) * n + j])));
+    const int kg = threadIdx.x % kgn, jg = threadIdx.x / kgn;
+    if (2 * jg >= jt) return;
+    df64 acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[0][i] = acc[1][i] = df64{0.f, 0.f};
+    for (int l = 0; l < r; ++l) {
+        const df64* ul = Us + l * kp + 4 * kg;
+        const float r0 = Rs[l * jt + 2 * jg], r1 = Rs[l * jt + 2 * jg + 1];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const df64 u = ul[i];
+            acc[0][i] = df_add(acc[0][i], df_mul_f(u, r0));
+            acc[1][i] = df_add(acc[1][i], df_mul_f(u, r1));
+        }
+    }
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+        const int64_t j = j0 + 2 * jg + jj;
+        if (j >= n) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * kg + i;
+            if (k >= ldk) continue;
+            float hi = 0.f, lo = 0.f;
+            if (k < r) {
+                const df64 w = acc[jj][i];
+                hi = to_tf32(__fadd_rn(w.h, w.l));
+                const df64 rem = df_sub(w, df64{hi, 0.f});
+                lo = to_tf32(__fadd_rn(rem.h, rem.l));
             }
-            if (l < r) s0 = df_add(s0, df_mul_f(Ut[l * r + k], to_f(R[(int64_t)l * n + j])));
-            const df64 w = df_add(s0, s1);
-            hi = to_tf32(__fadd_rn(w.h, w.l));
-            const df64 rem = df_sub(w, df64{hi, 0.f});
-            lo = to_tf32(__fadd_rn(rem.h, rem.l));
+            Wh[j * ldk + k] = hi;
+            Wl[j * ldk + k] = lo;
         }
-        Wh[e] = hi;
-        Wl[e] = lo;
     }
 }
 
-// Ch/Cl (m x ldk): C split into TF32 hi and lo, rows padded to ldk.
-template <typename TA>
-__global__ void tc_prep_c(const TA* __restrict__ C, int64_t m, int r, int ldk, float* __restrict__ Ch,
-                          float* __restrict__ Cl) {
-    const int64_t total = m * ldk;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / ldk;
-        const int k = (int)(e - i * ldk);
-        float hi = 0.f, lo = 0.f;
-        if (k < r) {
-            const float c = to_f(C[i * r + k]);
-            hi = to_tf32(c);
-            lo = to_tf32(c - hi);
-        }
-        Ch[e] = hi;
-        Cl[e] = lo;
-    }
-}
-
-constexpr int kAR = 32;                     // rows of A per staged sub-tile
-constexpr int kASub = kAR * kTcBN * 4;      // 16 KB: 32 rows x 128 columns, FP32
-constexpr int kNAMax = 8;                   // A ring slots at most
-constexpr int kEpiWarps = 16;               // epilogue: 4 row sub-tiles x 4 column quarters
+constexpr int kAR = 32;                     // rows of A per staged sub-tile (one lane quarter)
+constexpr int kABox = kAR * 32 * 4;         // 4 KB: 32 rows x 32 columns FP32, 128-byte swizzle
+constexpr int kASub = 4 * kABox;            // 16 KB: 32 rows x 128 columns
+constexpr int kNAMax = 10;                  // A ring slots at most
+constexpr int kEpiWarps = 16;               // epilogue: 4 lane quarters x 4 column groups
+constexpr int kTmemCols = 512;              // accumulators at 0 and 128, C panels at 256 and 384
+constexpr int kCLo = 64;                    // TMEM column offset of a panel's lo words
 
 struct TcArgs {
     int64_t m, n;
+    const float* C;   // m x r, row-major
     int r, nch, ksteps, na;
     int64_t ntile_n, ntiles;
     double* part;   // 4 doubles per CTA
     int* status;
 };
 
+// 8 consecutive TMEM columns of this thread's lane (32x32b shape); no wait.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])),
+                    "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])),
+                    "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+// D (+)= A B with A (M x K, K-major) in tensor memory and B described in shared memory.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc) {
+    asm volatile("{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }"
+                 :: "r"(dtmem), "r"(atmem), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+
+// One epilogue warp's share of a C panel: its lane quarter's 32 rows, K columns
+// [kq, kq + r/4), split into TF32 hi (TMEM column cbase + k) and lo (cbase + kCLo + k).
+// Rows past m are zeros. Ends with the stores complete and fenced for the MMA thread.
+__device__ __forceinline__ void store_c_panel(const TcArgs& a, int64_t panel, uint32_t trow, uint32_t cbase,
+                                              int q, int g, int lane) {
+    const int64_t row = panel * kTcBM + 32 * q + lane;
+    const bool rv = row < a.m;
+    const int kw = a.r >> 2;   // 8 or 16 columns per warp
+    const float* src = a.C + (rv ? row : 0) * a.r;
+    for (int k0 = g * kw; k0 < (g + 1) * kw; k0 += 8) {
+        float hi[8], lo[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float c = rv ? __ldg(src + k0 + i) : 0.f;
+            hi[i] = to_tf32(c);
+            lo[i] = to_tf32(c - hi[i]);
+        }
+        tmem_st8(trow + cbase + (uint32_t)k0, hi);
+        tmem_st8(trow + cbase + (uint32_t)(kCLo + k0), lo);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+}
+
 __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ CUtensorMap mWh,
                                                         const __grid_constant__ CUtensorMap mWl,
-                                                        const __grid_constant__ CUtensorMap mCh,
-                                                        const __grid_constant__ CUtensorMap mCl,
                                                         const __grid_constant__ CUtensorMap mA,
                                                         TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int nch = a.nch, na = a.na;
-    unsigned char* CH = sm;                     // C panel, TF32 hi (resident per row panel)
-    unsigned char* CL = CH + nch * kChunk;      // C panel, TF32 lo
-    unsigned char* WH = CL + nch * kChunk;      // W^T tile, hi (released after MMA passes 0, 1)
-    unsigned char* WL = WH + nch * kChunk;      // W^T tile, lo (released after pass 2)
-    unsigned char* AS = WL + nch * kChunk;      // ring of na A sub-tiles (32 x 128 FP32)
-    __shared__ __align__(8) uint64_t whf, whe, wlf, wle, cfull, cempty, accf[2], acce[2], af[kNAMax],
-        ae[kNAMax];
+    const uint32_t half_bytes = (uint32_t)nch * kChunk;   // W^T hi (or lo) of one tile
+    unsigned char* WB = sm;                     // 2 stages x (hi, lo)
+    unsigned char* AS = WB + 4 * (size_t)half_bytes;   // ring of na A sub-tiles
+    __shared__ __align__(8) uint64_t wfull[2], wempty[2], cfull[2], accf[2], acce[2], af[kNAMax], ae[kNAMax];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     __shared__ double rmx[kEpiWarps], rse[kEpiWarps], rsa[kEpiWarps];
@@ -136,112 +185,84 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t G = gridDim.x;
     const int64_t t0 = a.ntiles * blockIdx.x / G, t1 = a.ntiles * (blockIdx.x + 1) / G;
-    const uint32_t half_bytes = (uint32_t)nch * kChunk;
 
     if (tid == 0) {
-        mbar_init(&whf, 1);
-        mbar_init(&whe, 1);
-        mbar_init(&wlf, 1);
-        mbar_init(&wle, 1);
-        mbar_init(&cfull, 1);
-        mbar_init(&cempty, 1);
         for (int s = 0; s < 2; ++s) {
+            mbar_init(&wfull[s], 1);
+            mbar_init(&wempty[s], 1);
+            mbar_init(&cfull[s], kEpiWarps);
             mbar_init(&accf[s], 1);
             mbar_init(&acce[s], kEpiWarps);
         }
         for (int s = 0; s < na; ++s) {
             mbar_init(&af[s], 1);
-            mbar_init(&ae[s], 4);   // the four column-quarter warps of one row sub-tile
+            mbar_init(&ae[s], 4);   // the four column-group warps of one lane quarter
         }
         abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(&tslot, 256);
+    if (warp == 1) tmem_alloc(&tslot, kTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
 
     if (warp == 0) {
-        // ------------------------------------------------------------ C panel and W^T producer
+        // ------------------------------------------------------------ W^T producer
         if (lane == 0) {
-            int64_t cur_panel = -1, it = 0, nwh = 0, nwl = 0;   // tiles, hi and lo loads issued
-            int cuse = 0;
+            int64_t nw = 0;   // tiles whose W was issued
             bool ok = true;
-            for (int64_t t = t0; t < t1 && ok && !abort_flag; ++t, ++it) {
-                const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
-                if (panel != cur_panel) {
-                    if (cuse > 0 && !mbar_wait(&cempty, (cuse - 1) & 1)) { ok = false; break; }
-                    mbar_expect_tx(&cfull, 2 * half_bytes);
-                    for (int c = 0; c < nch; ++c) {
-                        tma_load_2d(CH + c * kChunk, &mCh, &cfull, 32 * c, (int)(panel * kTcBM));
-                        tma_load_2d(CL + c * kChunk, &mCl, &cfull, 32 * c, (int)(panel * kTcBM));
-                    }
-                    ++cuse;
-                    cur_panel = panel;
-                }
-                // hi, then lo, in the order the MMAs free them
-                for (int part = 0; part < 2; ++part) {
-                    uint64_t* fb = part ? &wlf : &whf;
-                    uint64_t* eb = part ? &wle : &whe;
-                    if (it > 0 && !mbar_wait(eb, (uint32_t)((it - 1) & 1))) { ok = false; break; }
-                    mbar_expect_tx(fb, half_bytes);
-                    for (int c = 0; c < nch; ++c)
-                        tma_load_2d((part ? WL : WH) + c * kChunk, part ? &mWl : &mWh, fb, 32 * c, (int)(ct * kTcBN));
-                    ++(part ? nwl : nwh);
+            for (int64_t t = t0; t < t1 && !abort_flag; ++t, ++nw) {
+                const int64_t ct = t % a.ntile_n;
+                const int s = (int)(nw & 1);
+                const int64_t u = nw >> 1;
+                if (u > 0 && !mbar_wait(&wempty[s], (uint32_t)((u - 1) & 1))) { ok = false; break; }
+                unsigned char* dst = WB + (size_t)s * 2 * half_bytes;
+                mbar_expect_tx(&wfull[s], 2 * half_bytes);
+                for (int c = 0; c < nch; ++c) {
+                    tma_load_2d(dst + c * kChunk, &mWh, &wfull[s], 32 * c, (int)(ct * kTcBN));
+                    tma_load_2d(dst + half_bytes + c * kChunk, &mWl, &wfull[s], 32 * c, (int)(ct * kTcBN));
                 }
             }
             if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
-            // after an abort, wait (bounded) for the last copy into each buffer: the MMA
+            // after an abort, wait (bounded) for the last copy into each stage: the MMA
             // warp consumed every full barrier otherwise
-            if (abort_flag) {
-                if (nwh > 0) mbar_wait(&whf, (uint32_t)((nwh - 1) & 1));
-                if (nwl > 0) mbar_wait(&wlf, (uint32_t)((nwl - 1) & 1));
-                if (cuse > 0) mbar_wait(&cfull, (uint32_t)((cuse - 1) & 1));
-            }
+            if (abort_flag)
+                for (int64_t q = nw - 1; q >= 0 && q >= nw - 2; --q) mbar_wait(&wfull[q & 1], (uint32_t)((q >> 1) & 1));
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(kTcBN, kTcBM);
-            int64_t cur_panel = -1, it = 0;
-            int cuse = 0;
+            constexpr uint32_t idesc = idesc_tf32(kTcBM, kTcBN);
+            int64_t cur_panel = -1, pc = -1, it = 0;
             bool ok = true;
-            const uint32_t ch = su32(CH), cl = su32(CL), wh = su32(WH), wl = su32(WL);
             uint64_t* last_bar = nullptr;   // the barrier of the last commit and its phase
             uint32_t last_par = 0;
             for (int64_t t = t0; t < t1 && !abort_flag; ++t, ++it) {
                 const int64_t panel = t / a.ntile_n;
                 if (panel != cur_panel) {
-                    if (cuse > 0) mma_commit(&cempty);
-                    if (!mbar_wait(&cfull, cuse & 1)) { ok = false; break; }
-                    ++cuse;
+                    ++pc;
                     cur_panel = panel;
+                    if (!mbar_wait(&cfull[pc & 1], (uint32_t)((pc >> 1) & 1))) { ok = false; break; }
                 }
                 const int b = (int)(it & 1);
                 const int64_t u = it >> 1;
                 if (u > 0 && !mbar_wait(&acce[b], (uint32_t)((u - 1) & 1))) { ok = false; break; }
-                const uint32_t d = tmem + (uint32_t)(b * kTcBM);
-                bool fine = true;
-                // passes 0 and 1 (Wh Ch, Wh Cl) release the hi buffer; pass 2 (Wl Ch) the lo
-                for (int part = 0; part < 2; ++part) {
-                    uint64_t* fb = part ? &wlf : &whf;
-                    uint64_t* eb = part ? &wle : &whe;
-                    if (!mbar_wait(fb, (uint32_t)(it & 1))) { fine = false; break; }
-                    tc_fence_after();
-                    const uint32_t wop = part ? wl : wh;
-                    for (int pass = part ? 2 : 0; pass < (part ? 3 : 2); ++pass) {
-                        const uint32_t bop = pass == 1 ? cl : ch;
-                        for (int k = 0; k < a.ksteps; ++k) {
-                            const uint32_t off = (uint32_t)((k >> 2) * kChunk + (k & 3) * 32);
-                            mma_tf32(d, sdesc_k128(wop + off), sdesc_k128(bop + off), idesc, (pass | k) != 0);
-                        }
+                if (!mbar_wait(&wfull[b], (uint32_t)(u & 1))) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kTcBN);
+                const uint32_t cpan = tmem + 256u + (uint32_t)((pc & 1) * 128);
+                const uint32_t wh = su32(WB + (size_t)b * 2 * half_bytes), wl = wh + half_bytes;
+                // Ch Wh, Cl Wh, Ch Wl
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t aop = cpan + (pass == 1 ? (uint32_t)kCLo : 0u);
+                    const uint32_t bop = pass == 2 ? wl : wh;
+                    for (int k = 0; k < a.ksteps; ++k) {
+                        const uint32_t off = (uint32_t)((k >> 2) * kChunk + (k & 3) * 32);
+                        mma_tf32_ts(d, aop + (uint32_t)(8 * k), sdesc_k128(bop + off), idesc, (pass | k) != 0);
                     }
-                    mma_commit(eb);
-                    last_bar = eb;
-                    last_par = (uint32_t)(it & 1);
                 }
-                if (!fine) { ok = false; break; }
+                mma_commit(&wempty[b]);
                 mma_commit(&accf[b]);
                 last_bar = &accf[b];
                 last_par = (uint32_t)(u & 1);
@@ -262,8 +283,9 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
                     const int64_t use = idx / na;
                     if (use > 0 && !mbar_wait(&ae[slot], (uint32_t)((use - 1) & 1))) { ok = false; break; }
                     mbar_expect_tx(&af[slot], (uint32_t)kASub);
-                    tma_load_2d(AS + (size_t)slot * kASub, &mA, &af[slot], (int)(ct * kTcBN),
-                                (int)(panel * kTcBM + kAR * k));
+                    for (int g = 0; g < 4; ++g)
+                        tma_load_2d(AS + (size_t)slot * kASub + g * kABox, &mA, &af[slot],
+                                    (int)(ct * kTcBN + 32 * g), (int)(panel * kTcBM + kAR * k));
                 }
             }
             if (!ok) { abort_flag = 1; set_status(a.status, CUR_ERR_TIMEOUT); }
@@ -273,27 +295,46 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
         }
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..17)
-        const int q = warp & 3;              // TMEM lane quarter of this warp = column quarter
-        const int k = (warp - 2) >> 2;       // row sub-tile: rows 32 k .. 32 k + 31 of the tile
-        const int jl = 32 * q + lane;        // column within the tile = TMEM lane
+        const int q = warp & 3;              // TMEM lane quarter of this warp = rows 32 q .. 32 q + 31
+        const int g = (warp - 2) >> 2;       // column group: columns 32 g .. 32 g + 31 of the tile
         const int ew = warp - 2;
+        const uint32_t trow = (uint32_t)(32 * q) << 16;
         float mx = 0.f;
         double se = 0.0, sa = 0.0;
         int bad = 0;
-        int64_t it = 0;
+        if (t0 < t1) {
+            // the first two panels; later ones are stored when the panel before them begins
+            const int64_t p0 = t0 / a.ntile_n, plast = (t1 - 1) / a.ntile_n;
+            store_c_panel(a, p0, trow, 256u, q, g, lane);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cfull[0]);
+            if (plast > p0) {
+                store_c_panel(a, p0 + 1, trow, 384u, q, g, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&cfull[1]);
+            }
+        }
+        int64_t it = 0, cur_panel = -1, pc = -1;
+        const int64_t plast = t1 > t0 ? (t1 - 1) / a.ntile_n : -1;
         for (int64_t t = t0; t < t1; ++t, ++it) {
-            const int64_t panel = t / a.ntile_n, ct = t - panel * a.ntile_n;
-            const int64_t j = ct * kTcBN + jl;
-            const int64_t rbase = panel * kTcBM + kAR * k;
-            const bool jv = j < a.n;
-            const bool full = jv && rbase + kAR <= a.m;   // every row of the sub-tile exists
+            const int64_t panel = t / a.ntile_n;
+            const bool fresh = panel != cur_panel;
+            if (fresh) { ++pc; cur_panel = panel; }
             const int b = (int)(it & 1);
             if (!mbar_wait(&accf[b], (uint32_t)((it >> 1) & 1))) {
                 abort_flag = 1;
                 set_status(a.status, CUR_ERR_TIMEOUT);
                 break;
             }
-            const int64_t idx = 4 * it + k;
+            tc_fence_after();
+            if (fresh && pc >= 1 && panel + 1 <= plast) {
+                // every MMA of the panel before this one has completed (this tile's commit
+                // follows them), so its TMEM columns take the panel after this one
+                store_c_panel(a, panel + 1, trow, 256u + (uint32_t)(((pc + 1) & 1) * 128), q, g, lane);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&cfull[(pc + 1) & 1]);
+            }
+            const int64_t idx = 4 * it + q;
             const int slot = (int)(idx % na);
             if (!mbar_wait(&af[slot], (uint32_t)((idx / na) & 1))) {
                 abort_flag = 1;
@@ -301,51 +342,33 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
                 break;
             }
             __syncwarp();
-            tc_fence_after();
-            const float* As = reinterpret_cast<const float*>(AS + (size_t)slot * kASub) + jl;
-            float tse = 0.f, tsa = 0.f;
-            // the sub-tile's 32 accumulator columns in one TMEM load (one wait)
+            // the 32 x 32 block: accumulator columns b*128 + 32 g .. + 31 of this warp's
+            // lanes, and row `lane` of A box g (16-byte chunk c stored at c ^ (lane & 7))
             float dall[32];
-            tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcBM + kAR * k), dall);
+            tmem_ld32(tmem + trow + (uint32_t)(b * kTcBN + 32 * g), dall);
+            const unsigned char* arow = AS + (size_t)slot * kASub + g * kABox + lane * 128;
+            // four independent chains per sum; a NaN anywhere makes the group's sum of
+            // squares NaN (fmaxf alone would drop it)
+            float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f}, a4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const float* dv = dall + 16 * c;
-                if (full) {
-                    // four independent chains per sum; a NaN anywhere makes the group's
-                    // sum of squares NaN (fmaxf alone would drop it)
-                    float m4[4] = {0.f, 0.f, 0.f, 0.f}, s4[4] = {0.f, 0.f, 0.f, 0.f},
-                          a4[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int c = 0; c < 8; ++c) {
+                const float4 x4 = *reinterpret_cast<const float4*>(arow + ((c ^ (lane & 7)) << 4));
+                const float xs[4] = {x4.x, x4.y, x4.z, x4.w};
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float x = As[(16 * c + i) * kTcBN];
-                        const float e = x - dv[i];
-                        m4[i & 3] = fmaxf(m4[i & 3], fabsf(e));
-                        s4[i & 3] = fmaf(e, e, s4[i & 3]);
-                        a4[i & 3] = fmaf(x, x, a4[i & 3]);
-                    }
-                    const float gs = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-                    if (gs != gs) bad = 1;
-                    mx = fmaxf(mx, fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])));
-                    tse += gs;
-                    tsa += (a4[0] + a4[1]) + (a4[2] + a4[3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float x = As[(16 * c + i) * kTcBN];
-                        if (jv && rbase + 16 * c + i < a.m) {
-                            const float e = x - dv[i];
-                            if (!(fabsf(e) <= INFINITY)) bad = 1;
-                            mx = fmaxf(mx, fabsf(e));
-                            tse = fmaf(e, e, tse);
-                            tsa = fmaf(x, x, tsa);
-                        }
-                    }
+                for (int i = 0; i < 4; ++i) {
+                    const float e = xs[i] - dall[4 * c + i];
+                    m4[i] = fmaxf(m4[i], fabsf(e));
+                    s4[i] = fmaf(e, e, s4[i]);
+                    a4[i] = fmaf(xs[i], xs[i], a4[i]);
                 }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&ae[slot]);
-            se += (double)tse;
-            sa += (double)tsa;
+            const float gs = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+            if (gs != gs) bad = 1;
+            mx = fmaxf(mx, fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])));
+            se += (double)gs;
+            sa += (double)((a4[0] + a4[1]) + (a4[2] + a4[3]));
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
@@ -374,7 +397,7 @@ __global__ void __launch_bounds__(608, 1) residual_tc_k(const __grid_constant__ 
     }
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, 256);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -426,19 +449,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// A (m x n FP32, leading dimension ld), boxes of 128 columns x 32 rows, no swizzle:
-// a staged sub-tile is row-major 32 x 128 in shared memory. Needs a 16-byte aligned base
-// and ld % 4 == 0.
+// A (m x n FP32, leading dimension ld), boxes of 32 columns x 32 rows with 128-byte
+// swizzle: in a staged box, row i's 16-byte chunk c sits at chunk c ^ (i & 7) of its
+// 128-byte row. Needs a 16-byte aligned base and ld % 4 == 0.
 static bool make_map_a(CUtensorMap* map, const float* base, int64_t m, int64_t n, int64_t ld) {
     auto enc = encode_fn();
     if (!enc) return false;
     if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (ld & 3) != 0) return false;
     cuuint64_t gdim[2] = {(cuuint64_t)n, (cuuint64_t)m};
     cuuint64_t gstr[1] = {(cuuint64_t)ld * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)kTcBN, (cuuint32_t)kAR};
+    cuuint32_t box[2] = {32, (cuuint32_t)kAR};
     cuuint32_t es[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim, gstr, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -455,10 +478,6 @@ static bool make_map(CUtensorMap* map, const float* base, int64_t rows, int r, i
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-static inline unsigned nbk(int64_t n, int t = 256) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + t - 1) / t, 65535));
-}
-
 }  // namespace curk
 
 // Returns CUR_ERR_ARG when this path does not apply (the caller then uses the SIMT path).
@@ -473,28 +492,22 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     const int nch = (r + 31) / 32;
     float* Wh = ar.get<float>((size_t)n * ldk);
     float* Wl = ar.get<float>((size_t)n * ldk);
-    float* Ch = ar.get<float>((size_t)m * ldk);
-    float* Cl = ar.get<float>((size_t)m * ldk);
     const int G = h->num_sms;
     double* part = ar.get<double>((size_t)G * 4);
     if (!ar.ok) return CUR_ERR_NOMEM;
-    CUtensorMap mWh, mWl, mCh, mCl, mA;
+    CUtensorMap mWh, mWl, mA;
     if (!make_map_a(&mA, static_cast<const float*>(Am->data), m, n, Am->ld)) return CUR_ERR_ARG;
-    if (!make_map(&mWh, Wh, n, r, ldk) || !make_map(&mWl, Wl, n, r, ldk) || !make_map(&mCh, Ch, m, r, ldk) ||
-        !make_map(&mCl, Cl, m, r, ldk))
-        return CUR_ERR_ARG;
-    const size_t smw = (size_t)r * r * sizeof(df64);
+    if (!make_map(&mWh, Wh, n, r, ldk) || !make_map(&mWl, Wl, n, r, ldk)) return CUR_ERR_ARG;
+    const size_t smw = prep_w_smem(r);
     CUR_TRY(smem_attr((const void*)tc_prep_w<float>, smw));
-    tc_prep_w<float><<<(unsigned)std::min<int64_t>((n * ldk + 255) / 256, 8 * G), 256, smw, st>>>(
+    tc_prep_w<float><<<(unsigned)((n + prep_w_cols(r) - 1) / prep_w_cols(r)), 256, smw, st>>>(
         U, static_cast<const float*>(R), r, n, ldk, Wh, Wl);
-    CUR_CK(cudaGetLastError());
-    note_launch();
-    tc_prep_c<float><<<nbk(m * ldk), 256, 0, st>>>(static_cast<const float*>(C), m, r, ldk, Ch, Cl);
     CUR_CK(cudaGetLastError());
     note_launch();
     TcArgs a{};
     a.m = m;
     a.n = n;
+    a.C = static_cast<const float*>(C);
     a.r = r;
     a.nch = nch;
     a.ksteps = (r + 7) / 8;
@@ -503,14 +516,14 @@ cur_status residual_tc_impl(cur_handle* h, const cur_mat* Am, const void* C, con
     a.part = part;
     a.status = h->status;
     const int grid = (int)std::min<int64_t>(G, a.ntiles);
-    // C panel and W^T tile (hi and lo each), then as many 16 KB A slots as fit
+    // two stages of the W^T tile (hi and lo each), then as many 16 KB A slots as fit
     const size_t fixed = (size_t)4 * nch * kChunk + 1024;
     const size_t budget = 225 * 1024;
     a.na = (int)std::min<size_t>(kNAMax, (budget - fixed) / kASub);
     if (a.na < 4) return CUR_ERR_ARG;
     const size_t sm = fixed + (size_t)a.na * kASub;
     CUR_TRY(smem_attr((const void*)residual_tc_k, sm));
-    residual_tc_k<<<grid, 32 * (3 + kEpiWarps), sm, st>>>(mWh, mWl, mCh, mCl, mA, a);
+    residual_tc_k<<<grid, 32 * (3 + kEpiWarps), sm, st>>>(mWh, mWl, mA, a);
     CUR_CK(cudaGetLastError());
     note_launch();
     tc_final_k<<<1, 256, 0, st>>>(part, grid, cheb, fro, h->status, sums);
