@@ -331,15 +331,23 @@ __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int6
 
 // One round of Algorithm 3 after its pass. `part` holds A^T q_t (t >= 0) or the
 // squared norms (t = -1). Picks index k = t + 1; with `build`, also forms q_k.
-// Cooperative launch; grid G <= co-resident CTAs, block 256.
+// Cooperative launch; grid G <= co-resident CTAs, block 256. The group barrier's counter
+// is not reset between rounds: this round's three barriers wait for bb + G, bb + 2G and
+// bb + 3G arrivals (bb = 3 G (t + 1)). A barrier that runs out of time stops the
+// selection, so that no later round waits on a count that cannot be reached.
 template <typename TA>
-__global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, int build) {
+__global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, int build, unsigned bb) {
     using PT = PartT<TA>;
     __shared__ double s_w[128];
     __shared__ PT s_q[4][64];
     __shared__ double s_tot;
     if (*P.stop) return;
     const int G = gridDim.x, g = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    auto barrier = [&](unsigned n) {
+        if (group_barrier(P.bar, bb + n * (unsigned)G, P.status)) return true;
+        if (threadIdx.x == 0) *P.stop = 1;
+        return false;
+    };
     const int k = t + 1;
     const PT* part = static_cast<const PT*>(P.part);
     PT* W = static_cast<PT*>(P.W);
@@ -360,9 +368,21 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
                 const int rc0 = P.RC * q4 / 4, rc1 = P.RC * (q4 + 1) / 4;
                 const PT* src = part + j;
                 int rc = rc0;
-                for (; rc + 1 < rc1; rc += 2) {
-                    w0 = part_add(w0, src[(int64_t)rc * P.nsel]);
-                    w1 = part_add(w1, src[(int64_t)(rc + 1) * P.nsel]);
+                // even offsets into w0, odd into w1; up to kP0B loads in flight at a time
+                constexpr int kP0B = 10;
+                while (rc + 1 < rc1) {
+                    const int nb = min(kP0B, (rc1 - rc) & ~1);
+                    PT x[kP0B];
+#pragma unroll
+                    for (int i = 0; i < kP0B; ++i)
+                        if (i < nb) x[i] = src[(int64_t)(rc + i) * P.nsel];
+#pragma unroll
+                    for (int i = 0; i < kP0B; i += 2)
+                        if (i < nb) {
+                            w0 = part_add(w0, x[i]);
+                            w1 = part_add(w1, x[i + 1]);
+                        }
+                    rc += nb;
                 }
                 if (rc < rc1) w0 = part_add(w0, src[(int64_t)rc * P.nsel]);
             }
@@ -396,7 +416,7 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
         P.keyi[g] = bad ? -2LL : bi;
         P.redf[g] = fs;
     }
-    if (!group_barrier(P.bar, (unsigned)G, P.status)) return;
+    if (!barrier(1u)) return;
 
     // P1: the global pick, identical in every CTA.
     unsigned long long pk = dkey(-INFINITY);
@@ -502,36 +522,42 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
                 if (two) red1[(int64_t)g * r + kk + 1] = acc1;
             }
         }
-        if (!group_barrier(P.bar, 2u * G, P.status)) return;
+        if (!barrier(2u)) return;
         // P2: second pass v -= Q (Q^T v); partial ||v||^2. The CTAs' partial dots are
-        // summed per direction in a fixed order, two directions per warp at a time so that
-        // their loads are in flight together.
-        for (int kk = warp; kk < k; kk += 2 * nw) {
-            const int kb = kk + nw;
-            const bool hb = kb < k;
-            df64 a0{0.f, 0.f}, a1{0.f, 0.f}, b0{0.f, 0.f}, b1{0.f, 0.f};
-            int gg = lane;
-            for (; gg + 32 < G; gg += 64) {
-                const df64 x0 = red1[(int64_t)gg * r + kk], x1 = red1[(int64_t)(gg + 32) * r + kk];
-                const df64 y0 = hb ? red1[(int64_t)gg * r + kb] : df64{0.f, 0.f};
-                const df64 y1 = hb ? red1[(int64_t)(gg + 32) * r + kb] : df64{0.f, 0.f};
-                a0 = df_add(a0, x0);
-                a1 = df_add(a1, x1);
-                b0 = df_add(b0, y0);
-                b1 = df_add(b1, y1);
-            }
-            if (gg < G) {
-                a0 = df_add(a0, red1[(int64_t)gg * r + kk]);
-                if (hb) b0 = df_add(b0, red1[(int64_t)gg * r + kb]);
-            }
-            const df64 sa = warp_sum_t(df_add(a0, a1));
-            const df64 sb = warp_sum_t(df_add(b0, b1));
-            if (lane == 0) {
-                s_df[kk] = sa;
-                if (hb) s_df[kb] = sb;
+        // summed per direction in a fixed order (the same in every CTA): D directions at
+        // a time, 256 / D threads per direction each summing every (256 / D)-th CTA with
+        // up to kRB loads in flight, then the subsets in order.
+        {
+            constexpr int kRB = 10;
+            __shared__ df64 s_sub[kPivotThreads];
+            const int D = k <= 32 ? 32 : 64, S = nt / D;
+            const int dl = tid % D, gs = tid / D;
+            for (int kb = 0; kb < k; kb += D) {
+                const int kk = kb + dl;
+                df64 acc{0.f, 0.f};
+                if (kk < k) {
+                    int gg = gs;
+                    while (gg < G) {
+                        df64 x[kRB];
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i)
+                            if (gg + i * S < G) x[i] = red1[(int64_t)(gg + i * S) * r + kk];
+#pragma unroll
+                        for (int i = 0; i < kRB; ++i)
+                            if (gg + i * S < G) acc = df_add(acc, x[i]);
+                        gg += kRB * S;
+                    }
+                }
+                s_sub[tid] = acc;
+                __syncthreads();
+                if (gs == 0 && kk < k) {
+                    df64 t = s_sub[dl];
+                    for (int q = 1; q < S; ++q) t = df_add(t, s_sub[q * D + dl]);
+                    s_df[kk] = t;
+                }
+                __syncthreads();
             }
         }
-        __syncthreads();
         df64 nv{0.f, 0.f};
         for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
             const int64_t ib = ia + nt;
@@ -556,7 +582,7 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
             for (int w = 0; w < nw; ++w) s = df_add(s, s_wred[w]);
             P.red2[g] = df_to_d(s);
         }
-        if (!group_barrier(P.bar, 3u * G, P.status)) return;
+        if (!barrier(3u)) return;
         // P3: early-stop test on the recomputed norm, record p, q_k = v / ||v||
         if (tid < 32) {
             const double sv = warp_sum_strided(P.red2, G);
@@ -602,7 +628,7 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
             acc = warp_sum(acc);
             if (lane == 0) P.red1[(int64_t)g * r + kk] = acc;
         }
-        if (!group_barrier(P.bar, 2u * G, P.status)) return;
+        if (!barrier(2u)) return;
         for (int kk = warp; kk < k; kk += nw) {
             const double sk = warp_sum_strided(P.red1 + kk, G, r);
             if (lane == 0) s_w[kk] = sk;
@@ -618,7 +644,7 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
         }
         nv = block_sum(nv);
         if (tid == 0) P.red2[g] = nv;
-        if (!group_barrier(P.bar, 3u * G, P.status)) return;
+        if (!barrier(3u)) return;
         if (tid < 32) {
             const double sv = warp_sum_strided(P.red2, G);
             if (tid == 0) s_tot = sv;
@@ -678,6 +704,21 @@ static cur_status launch_pass(const AcaParams& P, int mode, int64_t chunk, int r
     return CUR_OK;
 }
 
+// The selection's state before its first pass: no index picked, no stop, the pivots'
+// group-barrier counter at zero, idx_out[0..r) = -1.
+__global__ void aca_init_k(unsigned char* mask, int64_t nsel, int* stop, int32_t* count, int32_t* idx_out, int r,
+                           unsigned* bar) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nsel; j += (int64_t)gridDim.x * blockDim.x)
+        mask[j] = 0;
+    if (blockIdx.x != 0) return;
+    for (int k = threadIdx.x; k < r; k += blockDim.x) idx_out[k] = -1;
+    if (threadIdx.x == 0) {
+        *stop = 0;
+        *count = 0;
+        *bar = 0u;
+    }
+}
+
 template <typename TA>
 static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int32_t* idx_out,
                           int32_t* count_dev, Arena& ar, cudaStream_t st) {
@@ -731,10 +772,10 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
     const size_t va = 16;   // 16-byte vector loads on every row (8 columns of BF16, 4 of FP32)
     const bool vec = (base % va == 0) && ((size_t)(M->ld * es) % va == 0);
 
-    CUR_CK(cudaMemsetAsync(P.mask, 0, P.nsel, st));
-    CUR_CK(cudaMemsetAsync(P.stop, 0, sizeof(int), st));
-    CUR_CK(cudaMemsetAsync(count_dev, 0, sizeof(int), st));
-    CUR_CK(cudaMemsetAsync(idx_out, 0xff, sizeof(int32_t) * r, st));
+    aca_init_k<<<(unsigned)std::min<int64_t>((P.nsel + 255) / 256, 4LL * G), 256, 0, st>>>(
+        P.mask, P.nsel, P.stop, count_dev, idx_out, r, P.bar);
+    CUR_CK(cudaGetLastError());
+    note_launch();
 
     CUR_TRY(launch_pass<TA>(P, kNorm, chunk, RC, vec, st));
     note_launch();
@@ -747,9 +788,9 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
             if (ev) ++h->prof_n;
             note_launch();
         }
-        CUR_CK(cudaMemsetAsync(P.bar, 0, sizeof(unsigned), st));
         int build = (t + 1 < r - 1) ? 1 : 0;
-        void* args[] = {&P, &t, &build};
+        unsigned bb = 3u * (unsigned)G * (unsigned)(t + 1);
+        void* args[] = {&P, &t, &build, &bb};
         CUR_TRY(launch_coop((const void*)aca_pivot<TA>, dim3(G), dim3(kPivotThreads), args, 0, st));
         note_launch();
     }

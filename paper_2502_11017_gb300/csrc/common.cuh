@@ -191,7 +191,16 @@ __device__ __forceinline__ double block_sum(double v) {
 __device__ __forceinline__ double warp_sum_strided(const double* x, int n, int64_t stride = 1) {
     const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int g = lane; g < n; g += 32) s += x[(int64_t)g * stride];
+    int g = lane;
+    for (; g + 96 < n; g += 128) {   // four loads in flight, summed in index order
+        const double x0 = x[(int64_t)g * stride], x1 = x[(int64_t)(g + 32) * stride];
+        const double x2 = x[(int64_t)(g + 64) * stride], x3 = x[(int64_t)(g + 96) * stride];
+        s += x0;
+        s += x1;
+        s += x2;
+        s += x3;
+    }
+    for (; g < n; g += 32) s += x[(int64_t)g * stride];
     return warp_sum(s);
 }
 

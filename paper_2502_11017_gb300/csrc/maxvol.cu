@@ -449,6 +449,7 @@ template <typename TB>
 __global__ void __launch_bounds__(512) mv_lu(MvArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int pb = blockIdx.x;
+    if (threadIdx.x == 0) a.bar[pb] = 0u;   // the swap engine's group barrier starts from zero
     if (a.done[pb] || !a.lu_mask[pb]) return;
     const MvProb pr = a.prob[pb];
     const int r = pr.r, rs = a.r, tid = threadIdx.x, nt = blockDim.x;
@@ -1598,8 +1599,10 @@ static cur_status stage_tables(Stage<TB>& sg, cudaStream_t st) {
 
 // Per-problem defaults: factorise (lu_mask 1), not done (or all done while *idle != 0),
 // no swaps, status OK.
+// Per-problem flags and counters of a stage, its group-barrier counters, and (with S0) the
+// start set S0[0..ns) copied into S.
 __global__ void stage_init_k(int32_t* lu_mask, int32_t* done, int32_t* swaps, int32_t* pstatus, int32_t* retry,
-                             int P, const int* idle) {
+                             unsigned* bar, int P, const int* idle, const int32_t* S0, int32_t* S, int ns) {
     const int sk = idle ? (*idle != 0) : 0;
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
         lu_mask[pb] = 1;
@@ -1607,13 +1610,17 @@ __global__ void stage_init_k(int32_t* lu_mask, int32_t* done, int32_t* swaps, in
         swaps[pb] = 0;
         pstatus[pb] = 0;
         retry[pb] = 0;
+        bar[pb] = 0u;
     }
+    if (S0)
+        for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ns; k += gridDim.x * blockDim.x) S[k] = S0[k];
 }
 
 template <typename TB>
-static cur_status stage_init(Stage<TB>& sg, const int* idle, cudaStream_t st) {
-    stage_init_k<<<nblk(sg.P), 256, 0, st>>>(sg.dtab + 2 * sg.slots, sg.done, sg.swaps, sg.pstatus, sg.retry, sg.P,
-                                            idle);
+static cur_status stage_init(Stage<TB>& sg, const int* idle, cudaStream_t st, const int32_t* S0 = nullptr,
+                             int ns = 0) {
+    stage_init_k<<<nblk(std::max(sg.P, ns)), 256, 0, st>>>(sg.dtab + 2 * sg.slots, sg.done, sg.swaps, sg.pstatus,
+                                                          sg.retry, sg.bar, sg.P, idle, S0, sg.S, ns);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
@@ -1689,8 +1696,9 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
         return w;
     };
     const int solo_slots = slots - sg.coop_slots;
+    // the group-barrier counters are zero here: stage_init_k and the merge retry kernels
+    // clear them before the Algorithm 3 start, mv_lu before the swap engine
     if (aca_start) {
-        CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
         for (auto& w : waves(cap_start)) {
             MvArgs aw = a;
             aw.cta_base = w.first;
@@ -1715,7 +1723,6 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
                                sg.dtiles, (int)sg.tiles.size(), sg.done, sg.wh, sg.wl, sg.bpre, st));
         a.bpre = sg.bpre;
     }
-    CUR_CK(cudaMemsetAsync(sg.bar, 0, sizeof(unsigned) * P, st));
     if (solo_slots > 0) {
         MvArgs aw = a;
         aw.cta_base = sg.coop_slots;
@@ -1731,26 +1738,6 @@ static cur_status stage_launch(cur_handle* h, const TB* basis, int r, const cur_
         note_launch();
     }
     return CUR_OK;
-}
-
-// Batches (below) decide between their stages on the host: lu_mask / skip are host vectors
-// of length P (empty = all 1 / all 0), uploaded with the plan.
-template <typename TB>
-static cur_status stage_run(cur_handle* h, const TB* basis, int r, const cur_opts* o, Stage<TB>& sg,
-                            bool aca_start, const std::vector<int>& lu_mask,
-                            const std::vector<int>& skip, cudaStream_t st) {
-    const int P = sg.P;
-    CUR_TRY(stage_tables(sg, st));
-    std::vector<int32_t> lm(P), dn(P);
-    for (int pb = 0; pb < P; ++pb) {
-        lm[pb] = lu_mask.empty() ? 1 : lu_mask[pb];
-        dn[pb] = (!skip.empty() && skip[pb]) ? 1 : 0;
-    }
-    CUR_TRY(upload_multi({{sg.dtab + 2 * sg.slots, lm.data(), sizeof(int32_t) * P},
-                          {sg.done, dn.data(), sizeof(int32_t) * P}}, st));
-    CUR_CK(cudaMemsetAsync(sg.swaps, 0, sizeof(int32_t) * P, st));
-    CUR_CK(cudaMemsetAsync(sg.pstatus, 0, sizeof(int32_t) * P, st));
-    return stage_launch<TB>(h, basis, r, o, sg, aca_start, st);
 }
 
 // ---------------------------------------------------------------- decisions on the device
@@ -1806,8 +1793,9 @@ static cur_status launch_inherit(const std::vector<InheritSrc>& src, int r, doub
 // 1: Algorithm 3 on the union, formed by mv_start); the swaps of a node that finished are
 // added to *acc, those of an abandoned attempt are not counted.
 __global__ void merge_retry_k(int attempt, int P, int r, int32_t* pstatus, int32_t* swaps, int32_t* done,
-                              int32_t* lu_mask, int32_t* S, int32_t* retry, int* acc) {
+                              int32_t* lu_mask, int32_t* S, int32_t* retry, int* acc, unsigned* bar) {
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
+        bar[pb] = 0u;   // for the next attempt's Algorithm 3 start
         if (attempt > 0 && retry[pb] != attempt) continue;
         const bool sing = pstatus[pb] == CUR_ERR_SINGULAR;
         if (attempt < 2 && sing) {
@@ -1947,7 +1935,7 @@ static cur_status merge_level_t(cur_handle* h, const TB* basis, int64_t p, int r
     for (int attempt = 0; attempt < 3; ++attempt) {
         CUR_TRY(stage_launch<TB>(h, U, r, o, lv, attempt == 2, st));
         merge_retry_k<<<nblk(npairs), 256, 0, st>>>(attempt, npairs, r, lv.pstatus, lv.swaps, lv.done,
-                                                    lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc);
+                                                    lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc, lv.bar);
         CUR_CK(cudaGetLastError());
         note_launch();
     }
@@ -1988,8 +1976,7 @@ static cur_status global_t(cur_handle* h, const TB* basis, int64_t p, int r, con
     InheritSrc* dsrc = ar.get<InheritSrc>(1);
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUR_TRY(stage_tables(sg, st));
-    CUR_TRY(stage_init(sg, idle, st));
-    CUR_CK(cudaMemcpyAsync(sg.S, S0, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
+    CUR_TRY(stage_init(sg, idle, st, S0, r));
     if (inherit.minv && inherit.lv)
         CUR_TRY(launch_inherit(std::vector<InheritSrc>{inherit}, r, sg.minv64, sg.logvol, sg.dtab + 2 * sg.slots,
                                sg.done, dsrc, st));
@@ -2224,7 +2211,12 @@ __global__ void sweep_end_k(CrossCtl* ctl, const MvDevResult* r1, const MvDevRes
 // The cross's log-volume (taken directly when a stage ended with an error: such a stage
 // leaves no log|det| of its own; -inf for a singular proposal), its status and its info.
 __global__ void cross_end_k(CrossCtl* ctl, double* lv, const double* lv_direct, cur_cross_info* info,
-                            const int32_t* aca_count, int* hstatus, int from) {
+                            const int32_t* aca_count, int* hstatus, int from, const int32_t* I, const int32_t* J,
+                            int r, int32_t* I_out, int32_t* J_out) {
+    for (int k = threadIdx.x; k < r; k += blockDim.x) {
+        I_out[k] = I[k];
+        J_out[k] = J[k];
+    }
     if (threadIdx.x != 0) return;
     if (ctl->singular_start) *lv = -INFINITY;
     else if (ctl->last_status != CUR_OK) *lv = *lv_direct;
@@ -2291,11 +2283,10 @@ cur_status cross_end(cur_handle* h, const cur_mat* A, int r, bool from, const in
     if (!ar.ok) return CUR_ERR_NOMEM;
     CUR_TRY(gather_rows_t_compute(A, I, r, Rb, st));
     CUR_TRY(logvol_rows(cdt, Rb, A->cols, r, J, lv_direct, st));
-    curk::cross_end_k<<<1, 32, 0, st>>>(ctl, lv, lv_direct, info_out, aca_count, h->status, from ? 1 : 0);
+    curk::cross_end_k<<<1, 128, 0, st>>>(ctl, lv, lv_direct, info_out, aca_count, h->status, from ? 1 : 0, I, J, r,
+                                         I_out, J_out);
     CUR_CK(cudaGetLastError());
     note_launch();
-    CUR_CK(cudaMemcpyAsync(I_out, I, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
-    CUR_CK(cudaMemcpyAsync(J_out, J, sizeof(int32_t) * r, cudaMemcpyDeviceToDevice, st));
     return CUR_OK;
 }
 
@@ -2563,8 +2554,9 @@ __global__ void bat_acc_k(const int32_t* swaps, const int32_t* item, int P, int3
 // merge_retry_k for nodes of per-problem rank rr and per-matrix swap counts.
 __global__ void bat_merge_retry_k(int attempt, int P, int rs, const int32_t* rr, const int32_t* item,
                                   int32_t* pstatus, int32_t* swaps, int32_t* done, int32_t* lu_mask, int32_t* S,
-                                  int32_t* retry, int32_t* acc_m) {
+                                  int32_t* retry, int32_t* acc_m, unsigned* bar) {
     for (int pb = blockIdx.x * blockDim.x + threadIdx.x; pb < P; pb += gridDim.x * blockDim.x) {
+        bar[pb] = 0u;   // for the next attempt's Algorithm 3 start
         if (attempt > 0 && retry[pb] != attempt) continue;
         if (attempt < 2 && pstatus[pb] == CUR_ERR_SINGULAR) {
             retry[pb] = attempt + 1;
@@ -2790,7 +2782,7 @@ static cur_status bat_rows(cur_handle* h, const float* basis, const std::vector<
         for (int attempt = 0; attempt < 3; ++attempt) {
             CUR_TRY(stage_launch<float>(h, U, rs, o, lv, attempt == 2, st));
             bat_merge_retry_k<<<nblk(Q), 256, 0, st>>>(attempt, Q, rs, rr, nitem, lv.pstatus, lv.swaps, lv.done,
-                                                       lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc_m);
+                                                       lv.dtab + 2 * lv.slots, lv.S, lv.retry, acc_m, lv.bar);
             CUR_CK(cudaGetLastError());
             note_launch();
         }
