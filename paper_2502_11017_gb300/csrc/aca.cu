@@ -331,10 +331,12 @@ __device__ __forceinline__ void qsub_pair(const float* Qh, const float* Ql, int6
 
 // One round of Algorithm 3 after its pass. `part` holds A^T q_t (t >= 0) or the
 // squared norms (t = -1). Picks index k = t + 1; with `build`, also forms q_k.
-// Cooperative launch; grid G <= co-resident CTAs, block 256. The group barrier's counter
-// is not reset between rounds: this round's three barriers wait for bb + G, bb + 2G and
-// bb + 3G arrivals (bb = 3 G (t + 1)). A barrier that runs out of time stops the
-// selection, so that no later round waits on a count that cannot be reached.
+// Cooperative launch; grid G <= co-resident CTAs, block 256. Two group barriers: after
+// the partial sums of the pass (the pick), and after the partial dots of the first
+// Gram-Schmidt projection. The barrier's counter is not reset between rounds: this
+// round's barriers wait for bb + G and bb + 2G arrivals (bb = 2 G (t + 1)). A barrier that
+// runs out of time stops the selection, so that no later round waits on a count that
+// cannot be reached.
 template <typename TA>
 __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, int build, unsigned bb) {
     using PT = PartT<TA>;
@@ -458,20 +460,36 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
         df64* red1 = reinterpret_cast<df64*>(P.red1);
         __shared__ df64 s_df[128];
         __shared__ df64 s_wred[kPivotThreads / 32];
+        __shared__ df64 s_inv;
         for (int kk = tid; kk < k; kk += nt) s_df[kk] = W[(int64_t)kk * P.nsel + p];
         __syncthreads();
-        // P1b: v = a_p - Q W(:,p), two rows per thread
-        for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
-            const int64_t ib = ia + nt;
-            const bool vb = ib < i1;
-            df64 acc_a{(float)pivot_elem<TA>(P, ia, p), 0.f};
-            df64 acc_b{vb ? (float)pivot_elem<TA>(P, ib, p) : 0.f, 0.f};
-            qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
-            vh[ia] = acc_a.h;
-            vl[ia] = acc_a.l;
-            if (vb) { vh[ib] = acc_b.h; vl[ib] = acc_b.l; }
+        // P1b: v = a_p - Q W(:,p), two rows per thread, and this CTA's part of ||v||^2
+        {
+            df64 nv{0.f, 0.f};
+            for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
+                const int64_t ib = ia + nt;
+                const bool vb = ib < i1;
+                df64 acc_a{(float)pivot_elem<TA>(P, ia, p), 0.f};
+                df64 acc_b{vb ? (float)pivot_elem<TA>(P, ib, p) : 0.f, 0.f};
+                qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
+                vh[ia] = acc_a.h;
+                vl[ia] = acc_a.l;
+                nv = df_add(nv, df_mul(acc_a, acc_a));
+                if (vb) {
+                    vh[ib] = acc_b.h;
+                    vl[ib] = acc_b.l;
+                    nv = df_add(nv, df_mul(acc_b, acc_b));
+                }
+            }
+            nv = warp_sum_t(nv);
+            if (lane == 0) s_wred[warp] = nv;
+            __syncthreads();
+            if (tid == 0) {
+                df64 sv{0.f, 0.f};
+                for (int w = 0; w < nw; ++w) sv = df_add(sv, s_wred[w]);
+                P.red2[g] = df_to_d(sv);
+            }
         }
-        __syncthreads();
         // partial dots Q^T v: one warp per pair of directions; per iteration a lane loads
         // four rows of v and of both directions before the arithmetic (24 loads in flight)
         for (int kk = 2 * warp; kk < k; kk += 2 * nw) {
@@ -523,10 +541,10 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
             }
         }
         if (!barrier(2u)) return;
-        // P2: second pass v -= Q (Q^T v); partial ||v||^2. The CTAs' partial dots are
-        // summed per direction in a fixed order (the same in every CTA): D directions at
-        // a time, 256 / D threads per direction each summing every (256 / D)-th CTA with
-        // up to kRB loads in flight, then the subsets in order.
+        // P2: s = Q^T v, the CTAs' partial dots summed per direction in a fixed order (the
+        // same in every CTA): D directions at a time, 256 / D threads per direction each
+        // summing every (256 / D)-th CTA with up to kRB loads in flight, then the subsets
+        // in order.
         {
             constexpr int kRB = 10;
             __shared__ df64 s_sub[kPivotThreads];
@@ -558,35 +576,15 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
                 __syncthreads();
             }
         }
-        df64 nv{0.f, 0.f};
-        for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
-            const int64_t ib = ia + nt;
-            const bool vb = ib < i1;
-            df64 acc_a{vh[ia], vl[ia]};
-            df64 acc_b = vb ? df64{vh[ib], vl[ib]} : df64{0.f, 0.f};
-            qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
-            vh[ia] = acc_a.h;
-            vl[ia] = acc_a.l;
-            nv = df_add(nv, df_mul(acc_a, acc_a));
-            if (vb) {
-                vh[ib] = acc_b.h;
-                vl[ib] = acc_b.l;
-                nv = df_add(nv, df_mul(acc_b, acc_b));
-            }
-        }
-        nv = warp_sum_t(nv);
-        if (lane == 0) s_wred[warp] = nv;
-        __syncthreads();
-        if (tid == 0) {
-            df64 s{0.f, 0.f};
-            for (int w = 0; w < nw; ++w) s = df_add(s, s_wred[w]);
-            P.red2[g] = df_to_d(s);
-        }
-        if (!barrier(3u)) return;
-        // P3: early-stop test on the recomputed norm, record p, q_k = v / ||v||
+        // P3: ||v - Q s||^2 = ||v||^2 - ||s||^2 (Q orthonormal; s is ~eps ||a_p|| after the
+        // first projection, so the difference loses nothing): the early-stop test and the
+        // norm of q_k need no further reduction over the CTAs
         if (tid < 32) {
-            const double sv = warp_sum_strided(P.red2, G);
-            if (tid == 0) s_tot = sv;
+            const double vv = warp_sum_strided(P.red2, G);
+            df64 ss{0.f, 0.f};
+            for (int kk = tid; kk < k; kk += 32) ss = df_add(ss, df_mul(s_df[kk], s_df[kk]));
+            ss = warp_sum_t(ss);
+            if (tid == 0) s_tot = vv - df_to_d(ss);
         }
         __syncthreads();
         const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
@@ -600,27 +598,44 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
             *P.count = k + 1;
         }
         if (!build) return;
-        if (tid == 0) s_df[0] = df_from_d(1.0 / sqrt(s_tot));
+        if (tid == 0) s_inv = df_from_d(1.0 / sqrt(s_tot));
         __syncthreads();
-        const df64 inv = s_df[0];
-        for (int64_t i = i0 + tid; i < i1; i += nt) {
-            const df64 q = df_mul(df64{vh[i], vl[i]}, inv);
-            Qh[(int64_t)k * len + i] = q.h;
-            Ql[(int64_t)k * len + i] = q.l;
-            P.qh[i] = q.h;
-            P.ql[i] = q.l;
+        const df64 inv = s_inv;
+        // second projection v -= Q s and q_k = v / ||v|| in one sweep
+        for (int64_t ia = i0 + tid; ia < i1; ia += 2 * nt) {
+            const int64_t ib = ia + nt;
+            const bool vb = ib < i1;
+            df64 acc_a{vh[ia], vl[ia]};
+            df64 acc_b = vb ? df64{vh[ib], vl[ib]} : df64{0.f, 0.f};
+            qsub_pair(Qh, Ql, len, k, s_df, ia, ib, vb, acc_a, acc_b);
+            const df64 qa = df_mul(acc_a, inv);
+            Qh[(int64_t)k * len + ia] = qa.h;
+            Ql[(int64_t)k * len + ia] = qa.l;
+            P.qh[ia] = qa.h;
+            P.ql[ia] = qa.l;
+            if (vb) {
+                const df64 qb = df_mul(acc_b, inv);
+                Qh[(int64_t)k * len + ib] = qb.h;
+                Ql[(int64_t)k * len + ib] = qb.l;
+                P.qh[ib] = qb.h;
+                P.ql[ib] = qb.l;
+            }
         }
     } else {
         // FP64 data: the same steps in FP64.
         const double* Wd = reinterpret_cast<const double*>(W);
         for (int kk = tid; kk < k; kk += nt) s_w[kk] = Wd[(int64_t)kk * P.nsel + p];
         __syncthreads();
+        double nv = 0.0;
         for (int64_t i = i0 + tid; i < i1; i += nt) {
             double s = 0.0;
             for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
-            P.v[i] = pivot_elem<TA>(P, i, p) - s;
+            const double vi = pivot_elem<TA>(P, i, p) - s;
+            P.v[i] = vi;
+            nv = fma(vi, vi, nv);
         }
-        __syncthreads();
+        nv = block_sum(nv);
+        if (tid == 0) P.red2[g] = nv;
         for (int kk = warp; kk < k; kk += nw) {
             const double* qk = P.Q + (int64_t)kk * len;
             double acc = 0.0;
@@ -634,20 +649,13 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
             if (lane == 0) s_w[kk] = sk;
         }
         __syncthreads();
-        double nv = 0.0;
-        for (int64_t i = i0 + tid; i < i1; i += nt) {
-            double s = 0.0;
-            for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
-            const double vi = P.v[i] - s;
-            P.v[i] = vi;
-            nv = fma(vi, vi, nv);
-        }
-        nv = block_sum(nv);
-        if (tid == 0) P.red2[g] = nv;
-        if (!barrier(3u)) return;
+        // ||v - Q s||^2 = ||v||^2 - ||s||^2, as above
         if (tid < 32) {
-            const double sv = warp_sum_strided(P.red2, G);
-            if (tid == 0) s_tot = sv;
+            const double vv = warp_sum_strided(P.red2, G);
+            double ss = 0.0;
+            for (int kk = tid; kk < k; kk += 32) ss = fma(s_w[kk], s_w[kk], ss);
+            ss = warp_sum(ss);
+            if (tid == 0) s_tot = vv - ss;
         }
         __syncthreads();
         const double mx = (double)max(P.m, P.n) * 2.220446049250313e-16;
@@ -663,7 +671,9 @@ __global__ void __launch_bounds__(kPivotThreads) aca_pivot(AcaParams P, int t, i
         if (!build) return;
         const double inv = 1.0 / sqrt(s_tot);
         for (int64_t i = i0 + tid; i < i1; i += nt) {
-            const double q = P.v[i] * inv;
+            double s = 0.0;
+            for (int kk = 0; kk < k; ++kk) s = fma(P.Q[(int64_t)kk * len + i], s_w[kk], s);
+            const double q = (P.v[i] - s) * inv;
             P.Q[(int64_t)k * len + i] = q;
             P.q64[i] = q;
             float hi, lo;
@@ -789,7 +799,7 @@ static cur_status aca_run(cur_handle* h, const cur_mat* M, int axis, int r, int3
             note_launch();
         }
         int build = (t + 1 < r - 1) ? 1 : 0;
-        unsigned bb = 3u * (unsigned)G * (unsigned)(t + 1);
+        unsigned bb = 2u * (unsigned)G * (unsigned)(t + 1);
         void* args[] = {&P, &t, &build, &bb};
         CUR_TRY(launch_coop((const void*)aca_pivot<TA>, dim3(G), dim3(kPivotThreads), args, 0, st));
         note_launch();
