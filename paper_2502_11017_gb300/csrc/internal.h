@@ -199,11 +199,13 @@ size_t compute_size(cur_dtype t);
 
 // ---- low-precision coefficient phase of global maxvol (lowprec.cu)
 // The BF16 (or, with CUR_FLAG_PREC_FP8, E4M3) phase alone, from S0 to S_out (device r ints,
-// may alias); *swaps and *status (CUR_OK or CUR_ERR_SINGULAR) on the host. minv_in: the
-// FP64 inverse of C(S0,:) (r x r) if known, else NULL (it is factorised). Synchronises.
+// may alias), enqueued only. minv_in: the FP64 inverse of C(S0,:) (r x r), used when
+// minv_flag is NULL or reads CUR_OK / CUR_ERR_NOCONV on the device, else (or when NULL)
+// C(S0,:) is factorised; a singular start leaves S_out = S0. idle: a device word that skips the
+// phase when set (may be NULL). *swaps_dev (device): the swaps the phase took.
 cur_status lowprec_phase(cur_handle* h, const float* C, int64_t p, int r, const cur_opts* o, const int32_t* S0,
-                         int32_t* S_out, int* swaps, int* status, Arena& ar, cudaStream_t st,
-                         const double* minv_in);
+                         int32_t* S_out, int32_t* swaps_dev, Arena& ar, cudaStream_t st,
+                         const double* minv_in, const int* minv_flag, const int* idle);
 // Whether the stages of cur_cross take that phase (CUR_FLAG_PREC_BF16 or _FP8, FP32 basis,
 // r a multiple of 16, and enough rows to fill the GPU).
 bool lowprec_phase_applies(const cur_handle* h, const cur_opts* o, cur_dtype dt, int64_t p, int r);

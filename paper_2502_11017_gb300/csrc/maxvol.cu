@@ -1877,8 +1877,15 @@ __global__ void rows_polish_k(const int* acc, const MvDevResult* pol, int32_t* s
     }
 }
 
-__global__ void add_int_k(int* p, int v) {
-    if (threadIdx.x == 0) *p += v;
+// After the polish's low-precision phase: its swaps into *acc; *iflag = CUR_OK while the
+// merge's inverse of the set still holds (no swap taken and its status word valid), else
+// CUR_ERR_SINGULAR (the finish factorises afresh).
+__global__ void lp_after_k(const int32_t* lp_swaps, const int* root_flag, int* acc, int* iflag) {
+    if (threadIdx.x != 0) return;
+    const int n = *lp_swaps;
+    *acc += n;
+    const bool valid = n == 0 && (!root_flag || *root_flag == CUR_OK || *root_flag == CUR_ERR_NOCONV);
+    *iflag = valid ? CUR_OK : CUR_ERR_SINGULAR;
 }
 
 // One merge level on `basis` (p x r): sets in cand (nsets x r, global rows). in_src[k]
@@ -2051,24 +2058,17 @@ static cur_status rows_t(cur_handle* h, const TB* basis, int64_t p, int r, const
         InheritSrc start = root;
         if constexpr (std::is_same<TB, float>::value) {
             // with CUR_FLAG_PREC_BF16 / _FP8 on a large basis, low-precision products take the
-            // polish's swaps first (that phase synchronises the stream); the FP32 engine then
-            // finishes (from a fresh factorisation if any were taken)
+            // polish's swaps first; the FP32 engine then finishes, from the merge's inverse if
+            // that phase took no swap, else from a fresh factorisation (decided on the device)
             if (lowprec_phase_applies(h, o, CUR_F32, p, r)) {
-                CUR_CK(cudaStreamSynchronize(st));
-                int hv[2] = {CUR_OK, 0};
-                if (root.flag) CUR_CK(cudaMemcpy(&hv[0], root.flag, sizeof(int), cudaMemcpyDeviceToHost));
-                if (idle) CUR_CK(cudaMemcpy(&hv[1], idle, sizeof(int), cudaMemcpyDeviceToHost));
-                if (!hv[1]) {
-                    const bool valid = root.minv && root.lv && (hv[0] == CUR_OK || hv[0] == CUR_ERR_NOCONV);
-                    int bsw = 0, bst = CUR_OK;
-                    CUR_TRY(lowprec_phase(h, basis, p, r, o, cur, cur, &bsw, &bst, ar, st, valid ? root.minv : nullptr));
-                    if (bsw > 0) {
-                        start = InheritSrc{nullptr, nullptr, nullptr, 0, 0};   // a fresh factorisation
-                        add_int_k<<<1, 32, 0, st>>>(acc, bsw);
-                        CUR_CK(cudaGetLastError());
-                        note_launch();
-                    }
-                }
+                int32_t* lp_swaps = ar.get<int32_t>(1);
+                int* iflag = ar.get<int>(1);
+                if (!ar.ok) return CUR_ERR_NOMEM;
+                CUR_TRY(lowprec_phase(h, basis, p, r, o, cur, cur, lp_swaps, ar, st, root.minv, root.flag, idle));
+                lp_after_k<<<1, 32, 0, st>>>(lp_swaps, root.flag, acc, iflag);
+                CUR_CK(cudaGetLastError());
+                note_launch();
+                start = InheritSrc{root.minv, root.lv, iflag, 1, 0};
             }
         }
         CUR_TRY(global_t<TB>(h, basis, p, r, o, cur, I_out, logvol_out, pol, ar, st, start, minv_out, false, idle));
