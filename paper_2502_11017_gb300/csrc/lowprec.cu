@@ -35,7 +35,7 @@ namespace curk {
 constexpr int kLpBM = 128;           // rows of C per tile (MMA M)
 constexpr int kLpKC = 64;            // BF16 elements per 128-byte swizzled K chunk
 constexpr int kLpChunkC = kLpBM * 128;  // bytes of one K chunk of a C tile
-constexpr int kLpEpiWarps = 4;        // warps reading the accumulators
+constexpr int kLpEpiWarps = 8;        // warps reading the accumulators (lane quarter x column half)
 constexpr int kLpThreadsWS = 32 * (2 + kLpEpiWarps);
 
 // Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator, both K-major.
@@ -181,15 +181,15 @@ __global__ void lp_setup_k(const float* __restrict__ C, int r, int ldk, const in
     lp_requant<F8>(Mh, r, r, ldk, W, winv);
 }
 
-// Barrier of the four epilogue warps (named barrier 1, 128 threads); returns the OR of v over
+// Barrier of the eight epilogue warps (named barrier 1, 256 threads); returns the OR of v over
 // them, so that every one of them takes the same branch after it.
 __device__ __forceinline__ bool epi_sync_or(bool v) {
     int res;
-    asm volatile("{ .reg .pred p, q; setp.ne.b32 q, %1, 0; bar.red.or.pred p, 1, 128, q; selp.u32 %0, 1, 0, p; }"
+    asm volatile("{ .reg .pred p, q; setp.ne.b32 q, %1, 0; bar.red.or.pred p, 1, 256, q; selp.u32 %0, 1, 0, p; }"
                  : "=r"(res) : "r"((int)v) : "memory");
     return res != 0;
 }
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 // Grid barrier of the loop: the calling thread (one per CTA) arrives on the counter and waits
 // for `target` arrivals (G times the barrier's ordinal, counted alike in every CTA). False
@@ -239,8 +239,10 @@ struct LpLoop {          // arguments of the swap loop
 // Each iteration: B = Cq Wq^T for all p rows with the argmax |B_ij| in the epilogue (warp 0,
 // one lane: TMA loads of W and of the CTA's 128-row tiles of C through a ring of NS stages,
 // the first NS tiles of the next iteration loaded during this one's swap; warp 1, one lane:
-// the MMAs into two TMEM accumulators; warps 2..5: the accumulators read back, the CTA's two
-// best rows, their candidate entries evaluated exactly). Then, on the epilogue warps of every
+// the MMAs into two TMEM accumulators; warps 2..9: the accumulators read back, each warp a lane
+// quarter and half of the columns, each thread keeping the two best of its rows over the
+// iteration; then the CTA's two best rows, their candidate entries evaluated exactly). Then,
+// on the epilogue warps of every
 // CTA, between grid barriers: the winner over all CTAs' candidates (every CTA alike); its
 // exact row b = C(i,:) M^-1, one entry per CTA; the swap test |b_j| > 1 + delta on its largest
 // entry; the double-float Sherman-Morrison update of the rows of M^-1 each CTA owns, with
@@ -374,15 +376,19 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
     } else {
         // ---------------------------------------------------------------- epilogue and swap
         const int q = warp & 3;        // TMEM lane quarter of this warp
-        const int ew = warp - 2;       // 0..3
-        const int et = tid - 64;       // 0..127
+        const int ew = warp - 2;       // 0..7
+        const int et = tid - 64;       // 0..255
+        // this warp's columns: the first or second half of the 16-column groups
+        const int ng = (r + 15) / 16, hsplit = (ng + 1) / 2;
+        const int cb = ew < 4 ? 0 : 16 * hsplit, ce = ew < 4 ? min(r, 16 * hsplit) : r;
         int64_t gk = 0;
         unsigned ep = 0;               // grid barriers passed
         int swaps = 0;
         for (int64_t it = 0;; ++it) {
             if constexpr (F8)
-                for (int j = et; j < r; j += 128) s_winv[j] = __ldcg(a.winv + j);
+                for (int j = et; j < r; j += 256) s_winv[j] = __ldcg(a.winv + j);
             epi_sync();
+            // the two best (|b|, row, column) of this thread's rows and columns
             float tv[2] = {-1.f, -1.f};
             int ti[2] = {INT_MAX, INT_MAX}, tj[2] = {INT_MAX, INT_MAX};
             bool ok = true;
@@ -396,24 +402,45 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
                 const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * rpad);
                 float bv = -1.f;
                 int bj = INT_MAX;
-                for (int c0 = 0; c0 < r; c0 += 16) {
-                    float x[16];
-                    tmem_ld16(taddr + (uint32_t)c0, x);
+                for (int c0 = cb; c0 < ce; c0 += 32) {
+                    if (c0 + 32 <= ce) {
+                        float x[32];
+                        tmem_ld32(taddr + (uint32_t)c0, x);
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
-                        const float av = F8 ? fabsf(x[u]) * ci * s_winv[c0 + u] : fabsf(x[u]);
-                        if (av > bv) { bv = av; bj = c0 + u; }
+                        for (int u = 0; u < 32; ++u) {
+                            const float av = F8 ? fabsf(x[u]) * ci * s_winv[c0 + u] : fabsf(x[u]);
+                            if (av > bv) { bv = av; bj = c0 + u; }
+                        }
+                    } else {
+                        float x[16];
+                        tmem_ld16(taddr + (uint32_t)c0, x);
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const float av = F8 ? fabsf(x[u]) * ci * s_winv[c0 + u] : fabsf(x[u]);
+                            if (av > bv) { bv = av; bj = c0 + u; }
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&acce[b]);
-                int bi = row < a.p ? (int)row : INT_MAX;
-                if (row >= a.p) { bv = -1.f; bj = INT_MAX; }
-                // this tile's two best rows of the warp, merged into the warp's running two
+                if (row < a.p && bj != INT_MAX) {
+                    const int bi = (int)row;
+                    if (lp_better(bv, bi, bj, tv[0], ti[0], tj[0])) {
+                        tv[1] = tv[0]; ti[1] = ti[0]; tj[1] = tj[0];
+                        tv[0] = bv; ti[0] = bi; tj[0] = bj;
+                    } else if (lp_better(bv, bi, bj, tv[1], ti[1], tj[1])) {
+                        tv[1] = bv; ti[1] = bi; tj[1] = bj;
+                    }
+                }
+            }
+            // the warp's two best entries (its rows are distinct: one per lane and tile)
+            {
+                int row1 = -1;
                 for (int t = 0; t < 2; ++t) {
-                    float wv = bv;
-                    int wi = bi, wj = bj;
+                    const int u = (t == 1 && ti[0] == row1) ? 1 : 0;
+                    float wv = tv[u];
+                    int wi = ti[u], wj = tj[u];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float v2 = __shfl_xor_sync(0xffffffffu, wv, o);
@@ -421,36 +448,35 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
                         const int j2 = __shfl_xor_sync(0xffffffffu, wj, o);
                         if (lp_better(v2, i2, j2, wv, wi, wj)) { wv = v2; wi = i2; wj = j2; }
                     }
-                    if (bi == wi) { bv = -2.f; bi = INT_MAX; bj = INT_MAX; }
-                    if (lp_better(wv, wi, wj, tv[0], ti[0], tj[0])) {
-                        tv[1] = tv[0]; ti[1] = ti[0]; tj[1] = tj[0];
-                        tv[0] = wv; ti[0] = wi; tj[0] = wj;
-                    } else if (lp_better(wv, wi, wj, tv[1], ti[1], tj[1])) {
-                        tv[1] = wv; ti[1] = wi; tj[1] = wj;
-                    }
+                    if (lane == 0) { red_v[2 * ew + t] = wv; red_i[2 * ew + t] = wi; red_j[2 * ew + t] = wj; }
+                    row1 = wi;
                 }
-            }
-            if (lane == 0) {
-                red_v[2 * ew] = tv[0]; red_i[2 * ew] = ti[0]; red_j[2 * ew] = tj[0];
-                red_v[2 * ew + 1] = tv[1]; red_i[2 * ew + 1] = ti[1]; red_j[2 * ew + 1] = tj[1];
             }
             if (epi_sync_or(!ok)) { set_status(a.status, CUR_ERR_TIMEOUT); break; }
-            if (et == 0) {
-                float bv[2] = {-1.f, -1.f};
-                int bi[2] = {INT_MAX, INT_MAX}, bj[2] = {INT_MAX, INT_MAX};
-                for (int e = 0; e < 2 * kLpEpiWarps; ++e) {
-                    const float v = red_v[e];
-                    const int i = red_i[e], j = red_j[e];
-                    if (lp_better(v, i, j, bv[0], bi[0], bj[0])) {
-                        bv[1] = bv[0]; bi[1] = bi[0]; bj[1] = bj[0];
-                        bv[0] = v; bi[0] = i; bj[0] = j;
-                    } else if (lp_better(v, i, j, bv[1], bi[1], bj[1])) {
-                        bv[1] = v; bi[1] = i; bj[1] = j;
-                    }
-                }
+            // the CTA's two best rows (distinct), each with its best column: every row's best
+            // entry over the two column halves is among the warps' two best
+            if (ew == 0) {
+                int row1 = -1;
                 for (int t = 0; t < 2; ++t) {
-                    s_rows[t] = bv[t] >= 0.f ? bi[t] : -1;
-                    s_cols[t] = bj[t];
+                    float wv = -1.f;
+                    int wi = INT_MAX, wj = INT_MAX;
+                    for (int e = lane; e < 2 * kLpEpiWarps; e += 32) {
+                        const float v = red_v[e];
+                        const int i = red_i[e], j = red_j[e];
+                        if (v >= 0.f && i != row1 && lp_better(v, i, j, wv, wi, wj)) { wv = v; wi = i; wj = j; }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float v2 = __shfl_xor_sync(0xffffffffu, wv, o);
+                        const int i2 = __shfl_xor_sync(0xffffffffu, wi, o);
+                        const int j2 = __shfl_xor_sync(0xffffffffu, wj, o);
+                        if (lp_better(v2, i2, j2, wv, wi, wj)) { wv = v2; wi = i2; wj = j2; }
+                    }
+                    if (lane == 0) {
+                        s_rows[t] = wv >= 0.f ? wi : -1;
+                        s_cols[t] = wj;
+                    }
+                    row1 = wv >= 0.f ? wi : -2;
                 }
             }
             epi_sync();
@@ -494,7 +520,7 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
             {
                 double bv = -1.0;
                 int bi = INT_MAX, bj = INT_MAX;
-                for (int c = et; c < G; c += 128) {
+                for (int c = et; c < G; c += 256) {
                     const double xv = __ldcg(&a.cand[c].v);
                     const int xi = __ldcg(&a.cand[c].i), xj = __ldcg(&a.cand[c].j);
                     if (xv > bv || (xv == bv && (xi < bi || (xi == bi && xj < bj)))) { bv = xv; bi = xi; bj = xj; }
@@ -538,7 +564,7 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
             if (et == 0) gfail = !lp_grid_sync(a.gbar, (unsigned)G * ++ep);
             if (epi_sync_or(gfail)) { set_status(a.status, CUR_ERR_TIMEOUT); break; }
             // its largest entry (lowest column on ties) and the swap test
-            for (int c = et; c < r; c += 128) s_b[c] = __ldcg(a.brow + c);
+            for (int c = et; c < r; c += 256) s_b[c] = __ldcg(a.brow + c);
             epi_sync();
             if (ew == 0) {
                 double bv2 = -1.0;
@@ -561,12 +587,12 @@ __global__ void __launch_bounds__(kLpThreadsWS, 1) lp_loop_k(const __grid_consta
             if (!(fabs(bjv) > 1.0 + a.delta)) break;   // the winner does not pass: the phase ends
             // Sherman-Morrison on the rows l = blockIdx.x, blockIdx.x + G, ... of M^-1 (double-
             // float) and, for BF16, their columns of W = (M^-1)^T
-            for (int c = et; c < r; c += 128) s_g[c] = df_div(df_from_d(s_b[c] - (c == j ? 1.0 : 0.0)), df_from_d(bjv));
+            for (int c = et; c < r; c += 256) s_g[c] = df_div(df_from_d(s_b[c] - (c == j ? 1.0 : 0.0)), df_from_d(bjv));
             epi_sync();
             for (int l = blockIdx.x; l < r; l += G) {
                 const df64 ml = df_make(__ldcg(a.Mh + l * r + j), __ldcg(a.Ml + l * r + j));
                 epi_sync();   // every thread has M^-1(l, j) before it is overwritten
-                for (int c = et; c < r; c += 128) {
+                for (int c = et; c < r; c += 256) {
                     const df64 v = df_sub(df_make(__ldcg(a.Mh + l * r + c), __ldcg(a.Ml + l * r + c)), df_mul(ml, s_g[c]));
                     a.Mh[l * r + c] = v.h;
                     a.Ml[l * r + c] = v.l;
