@@ -21,10 +21,8 @@
  *    on the device; later steps run as no-ops when they are not needed. Outputs are
  *    complete once the stream reaches that point (cur_sync_status synchronises and
  *    returns the status). Calls that do wait for the GPU: cur_sync_status,
- *    cur_prof_read, cur_prof_refactors, the first cur_cross_batched of each class of batch (its
- *    launch-shape tuning), and the BF16 / FP8 options of
- *    cur_maxvol_global and of the polish (CUR_FLAG_PREC_BF16 / CUR_FLAG_PREC_FP8),
- *    whose swap loop reads a counter back from the device.
+ *    cur_prof_read, cur_prof_refactors, and the first cur_cross_batched of each class of
+ *    batch (its launch-shape tuning).
  *  - Errors: argument errors (CUR_ERR_ARG), workspace exhaustion (CUR_ERR_NOMEM)
  *    and CUDA launch errors (CUR_ERR_CUDA) are returned at once. Errors found on
  *    the device (CUR_ERR_SINGULAR, CUR_ERR_NONFINITE, CUR_ERR_NOCONV,
@@ -32,10 +30,9 @@
  *    recorded in the handle's device status word; cur_sync_status returns the
  *    first one recorded since the previous cur_sync_status.
  *  - A handle serves one stream at a time; calls on one handle do not overlap.
- *  - Autotuning: cur_cross_batched (its Algorithm 3 launch: one or two CTAs per SM) and the
- *    BF16 / FP8 phase of cur_maxvol_global (its product kernel: TMA stages and CTAs per SM)
- *    time their candidate launch shapes on the first call of each shape class and keep the
- *    fastest in the handle. Only shapes that leave every result unchanged are tuned.
+ *  - Autotuning: cur_cross_batched (its Algorithm 3 launch: one or two CTAs per SM) times its
+ *    candidate launch shapes on the first call of each shape class and keeps the fastest in
+ *    the handle. Only shapes that leave every result unchanged are tuned.
  */
 #ifndef CUR_H
 #define CUR_H
@@ -255,8 +252,8 @@ cur_status cur_cross(cur_handle* h, const cur_mat* A, int32_t r, int32_t b_r, in
  * E4M3 x E4M3 -> FP32 products, each row of C and of (M^-1)^T scaled to E4M3's range (448). Outputs (device): S_out r int32,
  * logvol_out 1 double (may be NULL), swaps_out 2 int32 (may be NULL): all swaps, and the
  * swaps of the BF16 phase. A singular C(S0,:) records CUR_ERR_SINGULAR (S_out = S0); more
- * than max_swaps records CUR_ERR_NOCONV. With CUR_FLAG_PREC_BF16 / _FP8 the call
- * synchronises the stream (its low-precision swap loop reads a counter back). */
+ * than max_swaps records CUR_ERR_NOCONV. Asynchronous, with or without the low-precision
+ * flags (their swap loop is one cooperative launch that ends itself on the device). */
 cur_status cur_maxvol_global(cur_handle* h, const cur_mat* basis, const int32_t* S0, int32_t r,
                              const cur_opts* opts, int32_t* S_out, double* logvol_out,
                              int32_t* swaps_out, cudaStream_t stream);

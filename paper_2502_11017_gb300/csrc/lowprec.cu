@@ -4,21 +4,23 @@
 // Each iteration forms B = C M^-1 for all p rows of the basis as a BF16 x BF16 -> FP32
 // tcgen05 product (kind::f16), or E4M3 x E4M3 -> FP32 (kind::f8f6f4) with every row of C and
 // of (M^-1)^T scaled to E4M3's range, and reduces argmax |B_ij| in the epilogue without
-// writing B. C is rounded once; (M^-1)^T after every swap. The product kernel is warp
-// specialised: one lane streams 128-row tiles of C through a ring of TMA stages, one lane
-// issues the MMAs into two TMEM accumulators, four warps read them back. Each CTA then
-// evaluates its two candidate entries exactly, b_ij = C(i,:) M^-1(:,j) with M^-1 held as a
-// double-float pair (hi + lo floats, about 2^-48 relative), the products formed by the
-// error-free Dot2 sums on the FP32 pipes and read out in FP64 (GB300's FP64 rate is a small
-// fraction of its FP32 rate, so FP64-class arithmetic runs on the FP32 pipes, as in the swap
-// engine). One CTA takes the row of the largest exact entry over all CTAs, recomputes it in
-// full, and swaps on its largest entry only if |b_j| > 1 + delta (the exact argmax unless
-// rounding pushed it below its CTA's two best rows); M^-1 gets its Sherman-Morrison update in
-// double-float. The start is factorised in FP64 (or handed over). The first winner whose
-// exact value does not pass ends this phase, and the FP32/FP64 swap engine (maxvol.cu)
-// finishes from the set reached, so the result is dominant to the same standard as the
-// plain path's. Every accepted swap raises the volume by |b_j| > 1 + delta, so the phase
-// cannot cycle.
+// writing B. C is rounded once; (M^-1)^T after every swap. The whole loop is one persistent
+// cooperative launch (one CTA per SM, warp specialised): one lane streams the CTA's 128-row
+// tiles of C through a ring of TMA stages, one lane issues the MMAs into two TMEM
+// accumulators, eight warps read them back and keep their threads' two best rows. Each CTA
+// then evaluates its two best candidate entries exactly, b_ij = C(i,:) M^-1(:,j) with M^-1
+// held as a double-float pair (hi + lo floats, about 2^-48 relative), the products formed by
+// the error-free Dot2 sums on the FP32 pipes and read out in FP64 (GB300's FP64 rate is a
+// small fraction of its FP32 rate, so FP64-class arithmetic runs on the FP32 pipes, as in the
+// swap engine). Between grid barriers every CTA takes the row of the largest exact entry
+// over all CTAs, the CTAs recompute that row in full (an entry each), and the swap is made on
+// its largest entry only if |b_j| > 1 + delta (the exact argmax unless rounding pushed it
+// below its CTA's two best rows): each CTA updates the rows of M^-1 it owns by
+// Sherman-Morrison in double-float, with their part of W = (M^-1)^T. The start is factorised
+// in FP64 (or handed over) on the device. The first winner whose exact value does not pass
+// ends the loop, and the FP32/FP64 swap engine (maxvol.cu) finishes from the set reached, so
+// the result is dominant to the same standard as the plain path's. Every accepted swap raises
+// the volume by |b_j| > 1 + delta, so the phase cannot cycle. Nothing waits on the host.
 
 #include <cuda_fp8.h>
 #include <cudaTypedefs.h>
