@@ -290,26 +290,40 @@ __device__ __forceinline__ bool group_barrier(unsigned* ctr, unsigned target, in
 // of shared memory. Returns 1 if singular (A then holds no inverse).
 __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* piv,
                                           double thresh, double* logabsdet) {
-    __shared__ int s_sing;
+    __shared__ int s_sing, s_p;
     __shared__ double s_dinv;
     __shared__ double s_prow[128];   // the step's pivot row, scaled (r <= 128)
     __shared__ LogAcc s_lacc;        // log|det| without a logarithm per step
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    // One warp: the pivot of column k (its first maximum |a_ik|, i >= k, compared as integer
+    // keys), its test, the log|det| factor and its reciprocal (one FP64 division). Step k's
+    // elimination runs this for column k + 1 as soon as that column is final, so it overlaps
+    // the rest of the elimination.
+    auto pivot_of = [&](int k) {
+        unsigned long long bk = 0ull;
+        long long bi = k;
+        for (int i = k + lane; i < r; i += 32) {
+            const unsigned long long x = dkey(fabs(A[i * r + k]));
+            if (x > bk) { bk = x; bi = i; }
+        }
+        warp_argmax_key(bk, bi);
+        if (lane == 0) {
+            const double d = A[(int)bi * r + k];
+            s_p = (int)bi;
+            if (!(fabs(d) > thresh)) s_sing = 1;
+            else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }
+        }
+        __syncwarp();
+    };
     if (tid == 0) { s_sing = 0; s_lacc.init(); }
     __syncthreads();
+    if (tid < 32) pivot_of(0);
+    __syncthreads();
     for (int k = 0; k < r; ++k) {
-        // One warp: the pivot (first maximum |a_ik|, compared as integer keys), the row
-        // interchange, the pivot's test and reciprocal (one FP64 division), the column k
-        // and the scaled pivot row.
+        if (s_sing) return 1;
+        // One warp: the row interchange, the column k and the scaled pivot row.
         if (tid < 32) {
-            unsigned long long bk = 0ull;
-            long long bi = k;
-            for (int i = k + lane; i < r; i += 32) {
-                const unsigned long long x = dkey(fabs(A[i * r + k]));
-                if (x > bk) { bk = x; bi = i; }
-            }
-            warp_argmax_key(bk, bi);
-            const int p = (int)bi;
+            const int p = s_p;
             if (p != k)
                 for (int j = lane; j < r; j += 32) {
                     const double t = A[k * r + j];
@@ -317,30 +331,27 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
                     A[p * r + j] = t;
                 }
             __syncwarp();
-            if (lane == 0) {
-                piv[k] = p;
-                const double d = A[k * r + k];
-                if (!(fabs(d) > thresh)) s_sing = 1;
-                else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }
-            }
-            __syncwarp();
-            if (!s_sing) {
-                const double dinv = s_dinv;
-                for (int i = lane; i < r; i += 32) colk[i] = A[i * r + k];
-                for (int c = lane; c < r; c += 32) s_prow[c] = (c == k ? 1.0 : A[k * r + c]) * dinv;
-            }
+            if (lane == 0) piv[k] = p;
+            const double dinv = s_dinv;
+            for (int i = lane; i < r; i += 32) colk[i] = A[i * r + k];
+            for (int c = lane; c < r; c += 32) s_prow[c] = (c == k ? 1.0 : A[k * r + c]) * dinv;
         }
         __syncthreads();
-        if (s_sing) return 1;
-        if (nt % r == 0) {   // one column per thread: its pivot-row entry is read once
-            const int c = tid % r, di = nt / r;
-            const double akc = s_prow[c];
-            for (int i = tid / r; i < r; i += di)
-                A[i * r + c] = i == k ? akc : fma(-colk[i], akc, c == k ? 0.0 : A[i * r + c]);
+        // elimination: warp 0 finishes column k + 1 and finds the next pivot while the
+        // other warps eliminate every other column
+        const int kn = k + 1;
+        if (tid < 32) {
+            if (kn < r) {
+                const double akc = s_prow[kn];
+                for (int i = lane; i < r; i += 32)
+                    A[i * r + kn] = i == k ? akc : fma(-colk[i], akc, A[i * r + kn]);
+                __syncwarp();
+                pivot_of(kn);
+            }
         } else {
-            Walk2 w(tid, nt, r);
-            for (int e = tid; e < r * r; e += nt, w.next())
-                A[e] = w.i == k ? s_prow[w.c] : fma(-colk[w.i], s_prow[w.c], w.c == k ? 0.0 : A[e]);
+            Walk2 w(tid - 32, nt - 32, r);
+            for (int e = tid - 32; e < r * r; e += nt - 32, w.next())
+                if (w.c != kn) A[e] = w.i == k ? s_prow[w.c] : fma(-colk[w.i], s_prow[w.c], w.c == k ? 0.0 : A[e]);
         }
         __syncthreads();
     }
