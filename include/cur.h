@@ -340,26 +340,25 @@ cur_status cur_cross_from(cur_handle* h, const cur_mat* A, int32_t r, const int3
  * cur_shard_aca_state_bytes(h, A_k, r) bytes (the slab's share of the orthonormal basis Q,
  * the replicated squared norms and W = Q^T A, the pivot vector). A round t = 0 .. r-1 is
  *   pick(t, red) -> red2 ; allreduce-sum red2 (r doubles)
- *   orth(t, red2) -> red3 ; allreduce-sum red3 (1 double)
- *   commit(t, red3) -> red ; allreduce-sum red (n doubles)
+ *   commit(t, red2) -> red ; allreduce-sum red (n doubles)
  * after begin (-> red, the slab's squared column norms; allreduce-sum it). pick takes the
  * summed red (t = 0: the squared norms; t > 0: w = A^T q_{t-1}, so nu_j -= w_j^2), picks the
- * unpicked column of largest residual norm (lowest index on ties) and forms the slab's part
- * of v = a_p - Q (Q^T a_p); orth re-orthogonalises v once (CGS2); commit stops the selection
- * when ||v||^2 <= (max(m,n) eps ||A||_F)^2 (CUR_WARN_RANK in the status word; later calls do
- * nothing), else records p in idx_out[t] and, while t + 1 < r, streams the slab once for the
- * next round's partial w. finish pads an early-stopped idx_out with the lowest unused columns.
- * m_global: rows of the whole A. idx_out: r int32 (device), -1 until picked. red: n doubles,
- * red2: r doubles, red3: 1 double (device). */
+ * unpicked column of largest residual norm (lowest index on ties), forms the slab's part of
+ * v = a_p - Q (Q^T a_p) and returns its partials of Q^T v (red2[0..t)) and of ||v||^2
+ * (red2[t]). commit re-orthogonalises v once (CGS2: v -= Q (Q^T v)), whose squared norm is
+ * red2[t] - ||red2[0..t)||^2 for orthonormal Q, stops the selection when that is <=
+ * (max(m,n) eps ||A||_F)^2 (CUR_WARN_RANK in the status word; later calls do nothing), else
+ * records p in idx_out[t], stores q_t = v / ||v|| and, while t + 1 < r, streams the slab once
+ * for the next round's partial w. finish pads an early-stopped idx_out with the lowest unused
+ * columns. m_global: rows of the whole A. idx_out: r int32 (device), -1 until picked. red: n
+ * doubles, red2: r doubles (device). */
 size_t cur_shard_aca_state_bytes(cur_handle* h, const cur_mat* A_k, int32_t r);
 cur_status cur_shard_aca_begin(cur_handle* h, const cur_mat* A_k, int64_t m_global, int32_t r, void* state,
                                int32_t* idx_out, double* red, cudaStream_t stream);
 cur_status cur_shard_aca_pick(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
                               const double* red, double* red2, cudaStream_t stream);
-cur_status cur_shard_aca_orth(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
-                              const double* red2, double* red3, cudaStream_t stream);
 cur_status cur_shard_aca_commit(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
-                                const double* red3, int32_t* idx_out, double* red, cudaStream_t stream);
+                                const double* red2, int32_t* idx_out, double* red, cudaStream_t stream);
 cur_status cur_shard_aca_finish(cur_handle* h, const cur_mat* A_k, int32_t r, void* state, int32_t* idx_out,
                                 cudaStream_t stream);
 

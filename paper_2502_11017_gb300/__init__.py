@@ -31,7 +31,7 @@ EXPORTS = ["cur_create", "cur_destroy", "cur_workspace_size", "cur_aca_select", 
            "cur_sketch", "cur_mlp_forward", "cur_mlp_grad", "cur_adam_step", "cur_propose",
            "cur_cross_from", "cur_maxvol_global",
            "cur_shard_aca_state_bytes", "cur_shard_aca_begin", "cur_shard_aca_pick",
-           "cur_shard_aca_orth", "cur_shard_aca_commit", "cur_shard_aca_finish",
+           "cur_shard_aca_commit", "cur_shard_aca_finish",
            "cur_dmv_state_bytes", "cur_dmv_begin", "cur_dmv_refresh", "cur_dmv_holder", "cur_dmv_fill",
            "cur_dmv_swap", "cur_dmv_result", "cur_merge_pair", "cur_rows_at", "cur_transpose",
            "cur_offset_ids", "cur_gather_cols", "cur_residual_parts", "cur_coef_tf32"]
@@ -112,7 +112,6 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "cur_shard_aca_state_bytes": ([P, pmat, I32], ctypes.c_size_t),
         "cur_shard_aca_begin": ([P, pmat, I64, I32, P, P, P, P], ctypes.c_int),
         "cur_shard_aca_pick": ([P, pmat, I32, I32, P, P, P, P], ctypes.c_int),
-        "cur_shard_aca_orth": ([P, pmat, I32, I32, P, P, P, P], ctypes.c_int),
         "cur_shard_aca_commit": ([P, pmat, I32, I32, P, P, P, P, P], ctypes.c_int),
         "cur_shard_aca_finish": ([P, pmat, I32, P, P, P], ctypes.c_int),
         "cur_dmv_state_bytes": ([I64, I32, ctypes.c_int], ctypes.c_size_t),
@@ -324,13 +323,8 @@ def cur_shard_aca_pick(h, A_k, r: int, t: int, state, red, red2, stream=None) ->
                                             _stream(stream)), "cur_shard_aca_pick")
 
 
-def cur_shard_aca_orth(h, A_k, r: int, t: int, state, red2, red3, stream=None) -> int:
-    return _check(load().cur_shard_aca_orth(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red2), _ptr(red3),
-                                            _stream(stream)), "cur_shard_aca_orth")
-
-
-def cur_shard_aca_commit(h, A_k, r: int, t: int, state, red3, idx_out, red, stream=None) -> int:
-    return _check(load().cur_shard_aca_commit(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red3),
+def cur_shard_aca_commit(h, A_k, r: int, t: int, state, red2, idx_out, red, stream=None) -> int:
+    return _check(load().cur_shard_aca_commit(h, ctypes.byref(mat(A_k)), r, t, _ptr(state), _ptr(red2),
                                               _ptr(idx_out), _ptr(red), _stream(stream)), "cur_shard_aca_commit")
 
 

@@ -5,11 +5,13 @@
 // statistics are sums over the ranks, so a round is
 //   pick   : red = sum over ranks of the slab partials (the caller's allreduce);
 //            W(t-1,:) = red, nu -= red^2 (t = 0: nu = red, the squared norms), masked
-//            argmax (lowest index) -> p; v_k = A_k(:,p) - Q_k^T W(:t,p); red2 = Q_k v_k
-//   orth   : v_k -= Q_k^T (sum of red2); red3 = ||v_k||^2           (CGS2, second pass)
-//   commit : rank-stop test on sum(red3); q_t = v_k / ||v||; red = A_k^T q_t (the next
-//            round's pass: the HBM stream, Dot2 accuracy as on one GPU)
-// with three allreduces per round (n, r and 1 doubles) made by the caller between calls.
+//            argmax (lowest index) -> p; v_k = A_k(:,p) - Q_k^T W(:t,p);
+//            red2 = (Q_k v_k, ||v_k||^2)
+//   commit : c = sum of red2[0..t); rank-stop test on ||v - Q^T c||^2 = sum of red2[t] -
+//            ||c||^2 (Q orthonormal); q_t = (v_k - Q_k^T c) / ||v|| (CGS2, second pass);
+//            red = A_k^T q_t (the next round's pass: the HBM stream, Dot2 accuracy as on
+//            one GPU)
+// with two allreduces per round (n and r doubles) made by the caller between calls.
 //
 // Maxvol over all rows of a basis distributed by row slabs (the polish and the sweeps):
 // every rank keeps the r x r matrix M = C(S,:) and its FP64 inverse (identical on every
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(1024) sa_pick_k(const double* __restrict__ red
     hdr->p = (int)bi;
 }
 
-// v = A_k(:,p) - Q^T W(:t,p) over the slab's rows; per-CTA partials of Q v (t values).
+// v = A_k(:,p) - Q^T W(:t,p) over the slab's rows; per-CTA partials of Q v (t values) and
+// of ||v||^2 (at index t).
 template <typename TA>
 __global__ void __launch_bounds__(256) sa_vec_k(const TA* __restrict__ A, int64_t m, int64_t n, int64_t ld,
                                                 int t, int r, const double* __restrict__ Q,
@@ -140,12 +143,16 @@ __global__ void __launch_bounds__(256) sa_vec_k(const TA* __restrict__ A, int64_
     for (int k = tid; k < t; k += blockDim.x) s_w[k] = W[(int64_t)k * n + p];
     __syncthreads();
     const int64_t i0 = m * g / G, i1 = m * (g + 1) / G;
+    double nv = 0.0;
     for (int64_t i = i0 + tid; i < i1; i += blockDim.x) {
         double s = 0.0;
         for (int k = 0; k < t; ++k) s = fma(Q[(int64_t)k * m + i], s_w[k], s);
-        v[i] = to_d(A[i * ld + p]) - s;
+        const double vi = to_d(A[i * ld + p]) - s;
+        v[i] = vi;
+        nv = fma(vi, vi, nv);
     }
-    __syncthreads();
+    nv = block_sum(nv);
+    if (tid == 0) cta[(int64_t)g * r + t] = nv;
     const int warp = tid >> 5, lane = tid & 31;
     for (int k = warp; k < t; k += blockDim.x >> 5) {
         double acc = 0.0;
@@ -167,38 +174,28 @@ __global__ void sa_sum_k(const double* __restrict__ cta, int G, int stride, int 
     }
 }
 
-// v -= Q^T c (the second Gram-Schmidt pass); per-CTA partial ||v||^2 at cta[g].
-__global__ void __launch_bounds__(256) sa_orth_k(int64_t m, int t, const double* __restrict__ Q,
-                                                 const double* __restrict__ c, double* __restrict__ v,
-                                                 double* __restrict__ cta, const AcaHdr* hdr) {
-    __shared__ double s_c[128];
-    if (hdr->stop) return;
-    const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    for (int k = tid; k < t; k += blockDim.x) s_c[k] = c[k];
-    __syncthreads();
-    const int64_t i0 = m * g / G, i1 = m * (g + 1) / G;
-    double nv = 0.0;
-    for (int64_t i = i0 + tid; i < i1; i += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < t; ++k) s = fma(Q[(int64_t)k * m + i], s_c[k], s);
-        const double vi = v[i] - s;
-        v[i] = vi;
-        nv = fma(vi, vi, nv);
-    }
-    nv = block_sum(nv);
-    if (tid == 0) cta[g] = nv;
-}
-
-// Rank-stop test on s = ||v||^2 (summed over ranks), then the pick and q_t = v / sqrt(s).
-__global__ void __launch_bounds__(256) sa_commit_k(int64_t m, int64_t n, int t, const double* s_sum,
+// The round's end from red2 (summed over the ranks: Q^T v at [0, t), ||v||^2 at t): the
+// rank-stop test on ||v - Q c||^2 = ||v||^2 - ||c||^2 (c = Q^T v, Q orthonormal), then the
+// pick, the second Gram-Schmidt pass v -= Q^T c and q_t = v / ||v|| in one sweep.
+__global__ void __launch_bounds__(256) sa_commit_k(int64_t m, int64_t n, int t, const double* __restrict__ red2,
                                                    const double* __restrict__ v, double* __restrict__ Q,
                                                    double* __restrict__ q64, float* __restrict__ qh,
                                                    float* __restrict__ ql, unsigned char* mask, int32_t* idx_out,
                                                    AcaHdr* hdr, int* status) {
+    __shared__ double s_c[128];
+    __shared__ double s_s;
     if (hdr->stop) return;
-    const double s = *s_sum;
-    const double mx = (double)max(hdr->m_global, n) * 2.220446049250313e-16;
     const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
+    for (int k = tid; k < t; k += blockDim.x) s_c[k] = red2[k];
+    if (tid < 32) {
+        double cc = 0.0;
+        for (int k = tid; k < t; k += 32) cc = fma(red2[k], red2[k], cc);
+        cc = warp_sum(cc);
+        if (tid == 0) s_s = red2[t] - cc;
+    }
+    __syncthreads();
+    const double s = s_s;
+    const double mx = (double)max(hdr->m_global, n) * 2.220446049250313e-16;
     if (!(s > mx * mx * hdr->frob2)) {
         __syncthreads();
         if (g == 0 && tid == 0) { hdr->stop = 1; set_status(status, CUR_WARN_RANK); }
@@ -214,7 +211,9 @@ __global__ void __launch_bounds__(256) sa_commit_k(int64_t m, int64_t n, int t, 
     const double inv = 1.0 / sqrt(s);
     const int64_t i0 = m * g / G, i1 = m * (g + 1) / G;
     for (int64_t i = i0 + tid; i < i1; i += blockDim.x) {
-        const double q = v[i] * inv;
+        double sq = 0.0;
+        for (int k = 0; k < t; ++k) sq = fma(Q[(int64_t)k * m + i], s_c[k], sq);
+        const double q = (v[i] - sq) * inv;
         Q[(int64_t)t * m + i] = q;
         q64[i] = q;
         float hi, lo;
@@ -614,39 +613,22 @@ cur_status cur_shard_aca_pick(cur_handle* h, const cur_mat* A_k, int32_t r, int3
         case CUR_F32: CUR_TRY(sa_vec_launch<float>(A_k, L, base, t, stream)); break;
         case CUR_BF16: CUR_TRY(sa_vec_launch<__nv_bfloat16>(A_k, L, base, t, stream)); break;
     }
-    sa_sum_k<<<1, 128, 0, stream>>>(reinterpret_cast<const double*>(base + L.cta), kShardG, r, t, r, red2, hdr);
+    sa_sum_k<<<1, 128, 0, stream>>>(reinterpret_cast<const double*>(base + L.cta), kShardG, r, t + 1, r, red2, hdr);
     CUR_CK(cudaGetLastError());
     note_launch();
     return CUR_OK;
 }
 
-cur_status cur_shard_aca_orth(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
-                              const double* red2, double* red3, cudaStream_t stream) {
-    SH_ENTER(h);
-    if (!slab_ok(A_k) || !state || !red2 || !red3 || r < 1 || r > 128 || t < 0 || t >= r) return CUR_ERR_ARG;
-    const AcaLayout L = aca_layout(h, A_k, r);
-    char* base = static_cast<char*>(state);
-    const AcaHdr* hdr = reinterpret_cast<const AcaHdr*>(base + L.hdr);
-    sa_orth_k<<<kShardG, 256, 0, stream>>>(L.m, t, reinterpret_cast<const double*>(base + L.Q), red2,
-                                           reinterpret_cast<double*>(base + L.v),
-                                           reinterpret_cast<double*>(base + L.cta), hdr);
-    CUR_CK(cudaGetLastError());
-    sa_sum_k<<<1, 32, 0, stream>>>(reinterpret_cast<const double*>(base + L.cta), kShardG, 1, 1, 1, red3, hdr);
-    CUR_CK(cudaGetLastError());
-    note_launch(2);
-    return CUR_OK;
-}
-
 cur_status cur_shard_aca_commit(cur_handle* h, const cur_mat* A_k, int32_t r, int32_t t, void* state,
-                                const double* red3, int32_t* idx_out, double* red, cudaStream_t stream) {
+                                const double* red2, int32_t* idx_out, double* red, cudaStream_t stream) {
     SH_ENTER(h);
-    if (!slab_ok(A_k) || !state || !red3 || !idx_out || !red || r < 1 || r > 128 || t < 0 || t >= r)
+    if (!slab_ok(A_k) || !state || !red2 || !idx_out || !red || r < 1 || r > 128 || t < 0 || t >= r)
         return CUR_ERR_ARG;
     const AcaLayout L = aca_layout(h, A_k, r);
     char* base = static_cast<char*>(state);
     AcaHdr* hdr = reinterpret_cast<AcaHdr*>(base + L.hdr);
     // the rounding-level test uses max(m, n) of the whole matrix (m from the header)
-    sa_commit_k<<<kShardG, 256, 0, stream>>>(L.m, L.n, t, red3, reinterpret_cast<const double*>(base + L.v),
+    sa_commit_k<<<kShardG, 256, 0, stream>>>(L.m, L.n, t, red2, reinterpret_cast<const double*>(base + L.v),
                                              reinterpret_cast<double*>(base + L.Q),
                                              reinterpret_cast<double*>(base + L.q64),
                                              reinterpret_cast<float*>(base + L.qh),

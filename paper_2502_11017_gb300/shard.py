@@ -8,8 +8,9 @@ k b_r/P .. (k+1) b_r/P - 1 of the single-process cross (b_r/P a power of two, so
 rank's blocks are one subtree of the binary merge), and for the column selection the
 column blocks k b_c/P .. (k+1) b_c/P - 1 of R^T = A(I,:)^T. The steps:
 
-* J0 (Algorithm 3 on the columns): per round three allreduce-sums (the slab partials of
-  A^T q, of Q^T v for the second Gram-Schmidt pass, and of ||v||^2).
+* J0 (Algorithm 3 on the columns): per round two allreduce-sums, the slab partials of
+  A^T q, and those of Q^T v (the second Gram-Schmidt pass) together with ||v||^2 (the norm
+  of the re-orthogonalised vector is ||v||^2 - ||Q^T v||^2, so it needs no third).
 * Row selection: every rank runs its blocks and its part of the merge tree alone
   (cur_maxvol_rows without the polish); the top log2 P levels of the tree cross ranks: the
   right child's owner sends its r ids and r x r rows of C to the left child's owner, which
@@ -262,16 +263,10 @@ class CudaRankOps:
         cur_shard_aca_pick(self.h, self.A, self.r, t, self.aca_state, red, red2, self.stream)
         return red2
 
-    def aca_orth(self, t: int, red2):
-        from . import cur_shard_aca_orth
-        red3 = self.empty(1, self.torch.float64)
-        cur_shard_aca_orth(self.h, self.A, self.r, t, self.aca_state, red2, red3, self.stream)
-        return red3
-
-    def aca_commit(self, t: int, red3):
+    def aca_commit(self, t: int, red2):
         from . import cur_shard_aca_commit
         red = self.empty(self.A.shape[1], self.torch.float64)
-        cur_shard_aca_commit(self.h, self.A, self.r, t, self.aca_state, red3, self.idx, red, self.stream)
+        cur_shard_aca_commit(self.h, self.A, self.r, t, self.aca_state, red2, self.idx, red, self.stream)
         return red
 
     def aca_finish(self):
@@ -387,8 +382,7 @@ def aca_columns(T: Transport, ops, m: int, r: int):
     red = T.allreduce(ops.aca_begin(m), "sum")
     for t in range(r):
         red2 = T.allreduce(ops.aca_pick(t, red), "sum")
-        red3 = T.allreduce(ops.aca_orth(t, red2), "sum")
-        red = ops.aca_commit(t, red3)
+        red = ops.aca_commit(t, red2)
         if t + 1 < r:
             T.allreduce(red, "sum")
     return ops.aca_finish()

@@ -82,26 +82,23 @@ class NumpyRankOps:
         out = np.zeros(self.r)
         if t:
             out[:t] = np.array(self.Q) @ self.v
+        out[t] = self.v @ self.v
         return _t(out)
 
-    def aca_orth(self, t, red2):
-        if self.stop:
-            return _t(np.zeros(1))
-        c = red2.numpy()[:t]
-        if t:
-            self.v = self.v - np.array(self.Q).T @ c
-        return _t(np.array([self.v @ self.v]))
-
-    def aca_commit(self, t, red3):
+    def aca_commit(self, t, red2):
         n = self.a.shape[1]
         if self.stop:
             return _t(np.zeros(n))
-        s = float(red3.numpy()[0])
+        red2 = red2.numpy()
+        c = red2[:t]
+        s = float(red2[t] - c @ c)   # ||v - Q^T c||^2 = ||v||^2 - ||c||^2
         mx = max(self.mg, n) * orc.EPS
         if not s > mx * mx * self.frob2:
             self.stop = True
             self._warn(WARN_RANK)
             return _t(np.zeros(n))
+        if t:
+            self.v = self.v - np.array(self.Q).T @ c
         self.idx[t] = self.p
         self.mask[self.p] = True
         self.count = t + 1
