@@ -60,9 +60,9 @@ template <typename TA>
 __global__ void __launch_bounds__(256) tc_prep_w(const double* __restrict__ U, const TA* __restrict__ R,
                                                  int r, int64_t n, int ldk, float* __restrict__ Wh,
                                                  float* __restrict__ Wl) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char prep_raw[];
     const int kgn = (r + 3) >> 2, kp = 4 * kgn, jt = prep_w_cols(r);
-    df64* Us = reinterpret_cast<df64*>(smem_raw);                      // Us[l * kp + k] = U(k, l)
+    df64* Us = reinterpret_cast<df64*>(prep_raw);                      // Us[l * kp + k] = U(k, l)
     float* Rs = reinterpret_cast<float*>(Us + (size_t)r * kp);          // Rs[l * jt + jj] = R(l, j0 + jj)
     const int64_t j0 = (int64_t)blockIdx.x * jt;
     for (int e = threadIdx.x; e < r * kp; e += blockDim.x) {
