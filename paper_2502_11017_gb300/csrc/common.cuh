@@ -293,13 +293,14 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
     __shared__ int s_sing, s_p;
     __shared__ double s_dinv;
     __shared__ double s_prow[128];   // the step's pivot row, scaled (r <= 128)
+    __shared__ double s_colk[128];   // the other buffer of the pivot column (steps alternate)
     __shared__ LogAcc s_lacc;        // log|det| without a logarithm per step
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
     // One warp: the pivot of column k (its first maximum |a_ik|, i >= k, compared as integer
-    // keys), its test, the log|det| factor and its reciprocal (one FP64 division). Step k's
-    // elimination runs this for column k + 1 as soon as that column is final, so it overlaps
-    // the rest of the elimination.
-    auto pivot_of = [&](int k) {
+    // keys), its test, the log|det| factor and its reciprocal (one FP64 division), and the
+    // column k as it will be after the row interchange. Step k's elimination runs this for
+    // column k + 1 as soon as that column is final, so it overlaps the rest of the elimination.
+    auto pivot_of = [&](int k, double* ck) {
         unsigned long long bk = 0ull;
         long long bi = k;
         for (int i = k + lane; i < r; i += 32) {
@@ -307,9 +308,11 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
             if (x > bk) { bk = x; bi = i; }
         }
         warp_argmax_key(bk, bi);
+        const int p = (int)bi;
+        for (int i = lane; i < r; i += 32) ck[i] = A[(i == k ? p : (i == p ? k : i)) * r + k];
         if (lane == 0) {
-            const double d = A[(int)bi * r + k];
-            s_p = (int)bi;
+            const double d = A[p * r + k];
+            s_p = p;
             if (!(fabs(d) > thresh)) s_sing = 1;
             else { s_lacc.mul(df_from_d(d)); s_dinv = 1.0 / d; }
         }
@@ -317,25 +320,23 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
     };
     if (tid == 0) { s_sing = 0; s_lacc.init(); }
     __syncthreads();
-    if (tid < 32) pivot_of(0);
+    if (tid < 32) pivot_of(0, colk);
     __syncthreads();
     for (int k = 0; k < r; ++k) {
         if (s_sing) return 1;
-        // One warp: the row interchange, the column k and the scaled pivot row.
-        if (tid < 32) {
-            const int p = s_p;
-            if (p != k)
-                for (int j = lane; j < r; j += 32) {
-                    const double t = A[k * r + j];
-                    A[k * r + j] = A[p * r + j];
-                    A[p * r + j] = t;
-                }
-            __syncwarp();
-            if (lane == 0) piv[k] = p;
-            const double dinv = s_dinv;
-            for (int i = lane; i < r; i += 32) colk[i] = A[i * r + k];
-            for (int c = lane; c < r; c += 32) s_prow[c] = (c == k ? 1.0 : A[k * r + c]) * dinv;
+        const int p = s_p;
+        const double dinv = s_dinv;
+        const double* ck = (k & 1) ? s_colk : colk;   // the column k after the interchange
+        // every thread: rows k and p interchanged, and the scaled pivot row (from row p)
+        for (int c = tid; c < r; c += nt) {
+            const double ak = A[k * r + c], ap = A[p * r + c];
+            s_prow[c] = (c == k ? 1.0 : ap) * dinv;
+            if (p != k) {
+                A[k * r + c] = ap;
+                A[p * r + c] = ak;
+            }
         }
+        if (tid == 0) piv[k] = p;
         __syncthreads();
         // elimination: warp 0 finishes column k + 1 and finds the next pivot while the
         // other warps eliminate every other column
@@ -344,14 +345,14 @@ __device__ __forceinline__ int gj_inverse(double* A, int r, double* colk, int* p
             if (kn < r) {
                 const double akc = s_prow[kn];
                 for (int i = lane; i < r; i += 32)
-                    A[i * r + kn] = i == k ? akc : fma(-colk[i], akc, A[i * r + kn]);
+                    A[i * r + kn] = i == k ? akc : fma(-ck[i], akc, A[i * r + kn]);
                 __syncwarp();
-                pivot_of(kn);
+                pivot_of(kn, (kn & 1) ? s_colk : colk);
             }
         } else {
             Walk2 w(tid - 32, nt - 32, r);
             for (int e = tid - 32; e < r * r; e += nt - 32, w.next())
-                if (w.c != kn) A[e] = w.i == k ? s_prow[w.c] : fma(-colk[w.i], s_prow[w.c], w.c == k ? 0.0 : A[e]);
+                if (w.c != kn) A[e] = w.i == k ? s_prow[w.c] : fma(-ck[w.i], s_prow[w.c], w.c == k ? 0.0 : A[e]);
         }
         __syncthreads();
     }
