@@ -92,6 +92,26 @@ def test_bf16_phase_on_a_converged_set_swaps_nothing(hd):
         assert st == cur.CUR_OK and sorted(S2) == sorted(S) and sw2 == [0, 0]
 
 
+def test_low_precision_loop_stops_at_max_swaps(hd):
+    """The persistent loop ends itself on every CTA once it has made max_swaps swaps; the
+    exact engine then continues from that set under the same cap."""
+    p, r = 20000, 64
+    C = basis(p, r, 2)
+    S0 = np.random.default_rng(102).choice(p, r, replace=False).tolist()
+    for prec in ("bf16", "fp8"):
+        S = torch.empty(r, dtype=torch.int32, device=DEV)
+        lv = torch.empty(1, dtype=torch.float64, device=DEV)
+        sw = torch.zeros(2, dtype=torch.int32, device=DEV)
+        o = cur.opts(DELTA, max_swaps=3, bf16=prec == "bf16", fp8=prec == "fp8")
+        cur.cur_maxvol_global(hd.h, torch.from_numpy(C).to(DEV), torch.tensor(S0, dtype=torch.int32, device=DEV),
+                              r, o, S, lv, sw)
+        st = cur.cur_sync_status(hd.h)
+        s, n = S.tolist(), sw.tolist()
+        assert n[1] == 3 and n[0] >= 3          # the loop's own swaps: exactly the cap
+        assert st in (cur.CUR_OK, cur.CUR_ERR_NOCONV)
+        assert len(set(s)) == r and all(0 <= i < p for i in s)
+
+
 def test_singular_start_is_reported(hd):
     C = basis(1000, 16, 8)
     S0 = [3, 3] + list(range(10, 24))
