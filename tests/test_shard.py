@@ -152,3 +152,59 @@ def test_gloo_rank_leaving_between_steps_gives_timeout_status():
     out = _run_gloo(2, B_R, B_C, leave_after_j0=True)
     assert list(out) == [0]
     assert out[0]["status"] == shard.CUR_ERR_TIMEOUT and "error" in out[0]
+
+
+class _CountingTransport:
+    """A rank's transport that counts the collectives it makes (by operation)."""
+
+    def __init__(self, inner):
+        self.inner = inner
+        self.calls = []
+
+    def allreduce(self, t, op):
+        self.calls.append(("allreduce", op, int(t.numel())))
+        return self.inner.allreduce(t, op)
+
+    def send(self, t, dst):
+        self.calls.append(("send", dst, int(t.numel())))
+        return self.inner.send(t, dst)
+
+    def recv(self, t, src):
+        self.calls.append(("recv", src, int(t.numel())))
+        return self.inner.recv(t, src)
+
+    def broadcast(self, t, src):
+        self.calls.append(("broadcast", src, int(t.numel())))
+        return self.inner.broadcast(t, src)
+
+
+def test_algorithm3_over_slabs_takes_two_allreduces_per_round():
+    """J0 over row slabs: one allreduce of the squared norms, then per round an allreduce of
+    the pick's r partials (Q^T v and ||v||^2 together) and, before every later round, one of
+    the n partials of A^T q: 2 r collectives in all, and the oracle's J0."""
+    a = _lowrank()
+    m, n = a.shape
+    P = 2
+    group = shard.ThreadGroup(P, timeout=120)
+    out = [None] * P
+    cnt = [None] * P
+
+    def rank(k):
+        s, e = shard.slab(m, B_R, P, k)
+        T = _CountingTransport(group.transport(k))
+        out[k] = shard.aca_columns(T, NumpyRankOps(a[s:e], R), m, R)
+        cnt[k] = T.calls
+
+    ths = [threading.Thread(target=rank, args=(k,)) for k in range(P)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    for k in range(P):
+        calls = cnt[k]
+        assert all(c[0] == "allreduce" and c[1] == "sum" for c in calls)
+        assert len(calls) == 2 * R
+        assert [c[2] for c in calls] == [n] + [R, n] * (R - 1) + [R]
+        assert out[k].tolist() == out[0].tolist()
+    J0, _ = orc.aca_select(a, 1, R, 1)
+    assert out[0].tolist()[:len(J0)] == list(J0)
